@@ -1,0 +1,182 @@
+"""Seeded synthetic scenes shaped like the paper's manipulation workloads.
+
+This module only places particles and rigid bodies with a seeded RNG; it holds
+none of the method's arithmetic (no transfer weights, stresses, SDFs or contact
+terms), so both the CUDA path and the CPU oracle can consume its output.
+
+A scene is a plain dict:
+  grid:    {dx, res[3], origin[3], gravity[3], bc_layers}
+  groups:  list of {x: float32[n,3], v: float32[n,3], vol: float (rest volume
+           per particle), material: {model, E, nu, rho, friction_angle_deg}}
+  bodies:  list of {shape, params[4], R[3,3], p[3], omega[3], v[3], mu, k, d,
+           kinematic}
+  h:       substep size [s];  substeps: substeps per rigid time step
+Shapes: 0 half-space (plane z=0 of the body frame, +z outward), 1 sphere
+(params[0] = radius), 2 box (params[0:3] = half extents), 3 capsule
+(params[0] = half length along body z, params[1] = radius).
+Materials: model 0 fixed corotated, model 1 Drucker-Prager sand.
+"""
+import numpy as np
+
+HALFSPACE, SPHERE, BOX, CAPSULE = 0, 1, 2, 3
+COROTATED, DRUCKER_PRAGER = 0, 1
+
+SEED_BASE = 20250307
+
+# contact-model defaults (the paper names the lagged model but prints no values)
+CONTACT_K = 1.0e4      # N/m per contact point
+CONTACT_D = 10.0       # s/m Hunt-Crossley dissipation
+EPS_S = 1.0e-4         # m/s friction regularisation
+
+SAND = {"model": DRUCKER_PRAGER, "E": 3.5e5, "nu": 0.3, "rho": 1600.0,
+        "friction_angle_deg": 30.0}
+
+
+def elastic(E=1.0e5, nu=0.3, rho=1000.0):
+    return {"model": COROTATED, "E": float(E), "nu": float(nu), "rho": float(rho),
+            "friction_angle_deg": 0.0}
+
+
+def body(shape, params=(0, 0, 0, 0), p=(0, 0, 0), R=None, v=(0, 0, 0), omega=(0, 0, 0),
+         mu=0.5, k=CONTACT_K, d=CONTACT_D, kinematic=0):
+    prm = np.zeros(4)
+    prm[:len(params)] = params
+    return {"shape": int(shape), "params": prm,
+            "R": np.eye(3) if R is None else np.asarray(R, np.float64).reshape(3, 3),
+            "p": np.asarray(p, np.float64), "omega": np.asarray(omega, np.float64),
+            "v": np.asarray(v, np.float64), "mu": float(mu), "k": float(k), "d": float(d),
+            "kinematic": int(kinematic)}
+
+
+def rot_y(theta):
+    c, s = np.cos(theta), np.sin(theta)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+def lattice_cube(n_side, spacing, center, jitter, rng):
+    """n_side^3 lattice points, x fastest, with uniform jitter of +-jitter."""
+    idx = np.arange(n_side, dtype=np.float64)
+    gx, gy, gz = np.meshgrid(idx, idx, idx, indexing="ij")
+    pts = np.stack([gx.transpose(2, 1, 0).ravel(), gy.transpose(2, 1, 0).ravel(),
+                    gz.transpose(2, 1, 0).ravel()], 1)
+    pts = (pts - (n_side - 1) / 2.0) * spacing + np.asarray(center, np.float64)
+    if jitter > 0:
+        pts = pts + rng.uniform(-jitter, jitter, pts.shape)
+    return pts
+
+
+def cube_group(n_side, spacing, center, v0=(0, 0, 0), material=None, jitter=0.0, rng=None):
+    rng = rng if rng is not None else np.random.default_rng(SEED_BASE)
+    x = lattice_cube(n_side, spacing, center, jitter, rng).astype(np.float32)
+    v = np.tile(np.asarray(v0, np.float32), (len(x), 1))
+    return {"x": x, "v": v, "vol": float(spacing ** 3),
+            "material": material if material is not None else elastic()}
+
+
+def cube_drop(seed=SEED_BASE + 0, n_side=20, drop_height=0.2, v0=(0.0, 0.0, 0.0),
+              sphere_x=0.12, sphere_v=0.1, mu=0.5, h=1e-4, substeps=10):
+    """Elastic cube (n_side^3 particles at 2 per dx, side n_side*dx/2) dropped onto
+    a static half-space at z = 0, beside a kinematic sphere (r = 0.05 m) rolling
+    towards it along -x. dx = 0.01 m on a 64^3 grid. The default is the 8,000
+    particle, 0.1 m cube dropped from 0.2 m (bottom face height)."""
+    rng = np.random.default_rng(seed)
+    dx = 0.01
+    spacing = dx / 2.0
+    side = n_side * spacing
+    center = (0.0, 0.0, drop_height + side / 2.0)
+    g = cube_group(n_side, spacing, center, v0, elastic(1.0e5, 0.3, 1000.0),
+                   jitter=1e-4 * dx, rng=rng)
+    bodies = [body(HALFSPACE, mu=mu),
+              body(SPHERE, (0.05,), p=(sphere_x, 0.0, 0.05), v=(-sphere_v, 0.0, 0.0), mu=mu,
+                   kinematic=1)]
+    grid = {"dx": dx, "res": (64, 64, 64), "origin": (-0.32, -0.32, -0.08),
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    return {"name": "cube_drop_%d" % len(g["x"]), "grid": grid, "groups": [g],
+            "bodies": bodies, "h": h, "substeps": substeps}
+
+
+def granular_scoop(n_particles=1_000_000, seed=SEED_BASE + 1, h=5e-5, substeps=10,
+                   paddle_speed=0.2, mu=0.4, res=128):
+    """Drucker-Prager sand (friction angle 30 deg, rho 1600) seeded uniformly in a
+    0.3 m box that sits in a static bin of five SDF boxes (floor + 4 walls), with
+    two kinematic box paddles (0.02 x 0.1 x 0.15 m) moving along +x at
+    `paddle_speed` through the sand; dx = 3e-3 m; block-sparse 128^3 grid."""
+    rng = np.random.default_rng(seed)
+    dx = 3e-3
+    L = 0.15          # bin half width
+    H = 0.3           # sand height
+    t = 0.0075        # half wall thickness
+    paddles = [((-0.09, -0.06, 0.2), (0.01, 0.05, 0.075)),
+               ((-0.09, 0.06, 0.2), (0.01, 0.05, 0.075))]
+    # rejection sampling against the paddles' axis-aligned boxes
+    pts = np.empty((0, 3))
+    need = n_particles
+    while need > 0:
+        cand = rng.uniform((-L, -L, 0.0), (L, L, H), (int(need * 1.15) + 64, 3))
+        keep = np.ones(len(cand), bool)
+        for c, hx in paddles:
+            inside = np.all(np.abs(cand - np.asarray(c)) < np.asarray(hx), axis=1)
+            keep &= ~inside
+        cand = cand[keep][:need]
+        pts = np.concatenate([pts, cand], 0)
+        need = n_particles - len(pts)
+    pad_vol = sum(8 * hx[0] * hx[1] * hx[2] for _, hx in paddles)
+    vol = ((2 * L) ** 2 * H - pad_vol) / n_particles
+    g = {"x": pts.astype(np.float32), "v": np.zeros((n_particles, 3), np.float32),
+         "vol": float(vol), "material": dict(SAND)}
+    bodies = [body(BOX, (L + 2 * t, L + 2 * t, t), p=(0, 0, -t), mu=mu),
+              body(BOX, (t, L + 2 * t, H / 2 + 0.03), p=(-(L + t), 0, H / 2), mu=mu),
+              body(BOX, (t, L + 2 * t, H / 2 + 0.03), p=((L + t), 0, H / 2), mu=mu),
+              body(BOX, (L + 2 * t, t, H / 2 + 0.03), p=(0, -(L + t), H / 2), mu=mu),
+              body(BOX, (L + 2 * t, t, H / 2 + 0.03), p=(0, (L + t), H / 2), mu=mu)]
+    for c, hx in paddles:
+        bodies.append(body(BOX, hx, p=c, v=(paddle_speed, 0, 0), mu=mu, kinematic=1))
+    origin = (-res * dx / 2.0, -res * dx / 2.0, -0.03)
+    grid = {"dx": dx, "res": (res, res, res), "origin": origin,
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    return {"name": "granular_scoop_%d" % n_particles, "grid": grid, "groups": [g],
+            "bodies": bodies, "h": h, "substeps": substeps}
+
+
+def sand_column(n_side=12, seed=SEED_BASE + 11, dx=0.01, h=1e-4, with_paddle=True):
+    """Small sand block resting on a half-space with a kinematic box pushing
+    into its side: the granular scooping workload at a size the oracle runs in
+    seconds."""
+    rng = np.random.default_rng(seed)
+    spacing = dx / 2.0
+    side = n_side * spacing
+    center = (0.0, 0.0, side / 2.0 + 0.2 * spacing)
+    g = cube_group(n_side, spacing, center, (0, 0, 0), dict(SAND), jitter=0.25 * spacing,
+                   rng=rng)
+    bodies = [body(HALFSPACE, mu=0.4)]
+    if with_paddle:
+        bodies.append(body(BOX, (0.01, 0.02, 0.02), p=(-side / 2 - 0.0115, 0, 0.02),
+                           v=(0.2, 0, 0), mu=0.4, kinematic=1))
+    grid = {"dx": dx, "res": (32, 32, 32), "origin": (-0.16, -0.16, -0.04),
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    return {"name": "sand_column_%d" % len(g["x"]), "grid": grid, "groups": [g],
+            "bodies": bodies, "h": h, "substeps": 10}
+
+
+def n_particles(scene):
+    return int(sum(len(g["x"]) for g in scene["groups"]))
+
+
+def incline_block(theta_deg=30.0, mu=0.3, n_side=6, dx=0.01, E=1.0e6, seed=SEED_BASE + 21,
+                  h=1e-4):
+    """Elastic block sitting flat on a half-space tilted by theta about y
+    (outward normal (sin t, 0, cos t)); downhill is +x."""
+    rng = np.random.default_rng(seed)
+    t = np.radians(theta_deg)
+    R = rot_y(t)
+    spacing = dx / 2.0
+    local = lattice_cube(n_side, spacing, (0, 0, 0), 1e-4 * dx, rng)
+    # bottom particle layer on the plane (contacts register for particles inside)
+    center = R @ np.array([0.0, 0.0, (n_side - 1) * spacing / 2.0])
+    x = (local @ R.T + center).astype(np.float32)
+    g = {"x": x, "v": np.zeros_like(x), "vol": spacing ** 3,
+         "material": elastic(E, 0.3, 1000.0)}
+    grid = {"dx": dx, "res": (40, 16, 24), "origin": (-0.12, -0.08, -0.12),
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    return {"name": "incline", "grid": grid, "groups": [g],
+            "bodies": [body(HALFSPACE, R=R, mu=mu)], "h": h, "substeps": 10}
