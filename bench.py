@@ -1,0 +1,353 @@
+"""Throughput of the coupled MPM / rigid-body convex-contact substep on GB300.
+
+Workload (the paper's granular manipulation shape): 1M Drucker-Prager sand
+particles in a 0.3 m box inside a static five-box bin, two kinematic box
+paddles moving through the sand, dx = 3e-3 m on a block-sparse 128^3 grid,
+h = 5e-5 s, N = 10 substeps per rigid time step, solver at the paper's default
+tolerance (eps_r = 5e-2). One bench step is one rigid time step (radix sort +
+10 substeps, each P2G + grid update + quasi-Newton contact solve + G2P).
+
+Metric: particle-substeps per second including the contact solve.
+  value  device-resident: state in HBM, CUDA events around each mpm_step on the
+         library's stream, L2 flushed (256 MB write) between timed steps.
+  e2e    through the C ABI with host buffers: every step uploads the rigid
+         bodies from host memory, runs mpm_step and reads back the particle
+         positions and the body impulses to host memory.
+Rank r of a torchrun job runs an independent replica on its own GPU (a single
+scene does not shard); value sums the replicas over the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle (oracle/) on the host cores on a
+bounded sample of the same workload (one octant of the sand, one substep per
+bench step).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "particle-substeps/sec incl. contact solve"
+UNIT = "particle-substeps/s"
+WORKLOAD = "granular_scoop_1M"
+N_PARTICLES = 1_000_000
+# algorithmic bytes per particle per launch (FP32 SoA planes)
+P2G_BYTES_PER_PARTICLE = 12 + 12 + 36 + 36 + 2      # read x, v, C, F, group
+G2P_BYTES_PER_PARTICLE = 12 + 36 + 2 + 12 + 12 + 36 + 36  # read x, F, group; write x, v, C, F
+GRID_NODE_BYTES_P2G = 16                              # one (m, p) write per active node
+GRID_NODE_BYTES_G2P = 16                              # one v read per active node
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value, ws):
+    """Max of a float over the ranks of the default process group (identity at ws = 1)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, ws, max_seconds):
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return units_per_rank * ws / max_seconds
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if one exists for
+    the current kernel build (line 'traffic_bytes_per_launch <kernel> <bytes> <n>'
+    with n the particle count of the capture); scaled to the bench's size."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 4 and parts[0] == "traffic_bytes_per_launch" and parts[1] == kernel:
+            return float(parts[2]) * N_PARTICLES / float(parts[3])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "bench_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [q.strip() for q in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_scene(n=N_PARTICLES):
+    from paper_2503_05046_gb300 import scenes
+    return scenes.granular_scoop(n_particles=n)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2503_05046_gb300 import native
+    sc = make_scene()
+    n = sum(len(g["x"]) for g in sc["groups"])
+    N = sc["substeps"]
+    sim = native.Sim(sc, max_contacts=2 * n)
+    stream = torch.cuda.current_stream()
+    solver = native.solver_params(eps_r=5e-2, max_iters=args.max_iters)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        sim.step(solver=solver, stats=False, check=False)
+    sim.step(n_substeps=0, solver=solver, check=False)  # drain warm-up status
+    native.mpm_set_option(sim.ctx, native.OPT_PROFILE, 1)
+    native.mpm_get_phase_times(sim.ctx, reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    iters, contacts, status_bits, resid = 0, 0, 0, 0.0
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        code, stt = native.mpm_step(sim.ctx, sc["h"], N, solver, want_stats=False)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    phase_ms, phase_n = native.mpm_get_phase_times(sim.ctx, reset=True)
+    native.mpm_set_option(sim.ctx, native.OPT_PROFILE, 0)
+    code_timed, _ = sim.step(n_substeps=0, solver=solver, check=False)
+    seconds = max_over_ranks(ms / 1e3, ws)
+    units = float(n) * N * args.steps
+    value = whole_job_value(units, ws, seconds)
+    # one more step with statistics (not timed) for the report
+    code_stats, st = sim.step(solver=solver, check=False)
+    act_nodes = st.active_blocks_max * 64
+
+    # --- e2e through the C ABI with host buffers
+    bodies = [native.make_body(b) for b in sc["bodies"]]
+    arr = (native.RigidBody * len(bodies))(*bodies)
+    x_host = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
+    imp_host = np.zeros(6 * len(bodies))
+    e2e_steps = max(3, min(args.steps, 10))
+    for k in range(e2e_steps + 1):
+        if k == 1:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        native.lib.mpm_set_rigid_bodies(sim.ctx, len(bodies), arr)
+        native.mpm_step(sim.ctx, sc["h"], N, solver, want_stats=False)
+        native.mpm_get_particles(sim.ctx, x_host, None, None, None)
+        native.lib.mpm_get_rigid_impulses(sim.ctx, imp_host.ctypes.data_as(native._dp), 1)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e_value = whole_job_value(float(n) * N * e2e_steps, ws, e2e_s)
+
+    peak, peak_kind = measured_peak_hbm()
+    kern = {}
+    for name, per_p, per_node in (("p2g", P2G_BYTES_PER_PARTICLE, GRID_NODE_BYTES_P2G),
+                                  ("g2p", G2P_BYTES_PER_PARTICLE, GRID_NODE_BYTES_G2P)):
+        launches = max(int(phase_n[name]), 1)
+        avg_s = phase_ms[name] / launches / 1e3
+        bytes_launch = per_p * n + per_node * act_nodes
+        kern[name] = {"avg_us": avg_s * 1e6, "launches": int(phase_n[name]),
+                      "bytes_per_launch": bytes_launch,
+                      "GBps": bytes_launch / avg_s / 1e9 if avg_s > 0 else 0.0}
+    dom = max(("p2g", "g2p"), key=lambda k: phase_ms[k])
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GBps"], "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": kern[dom]["GBps"] / peak,
+            "traffic": profiled_traffic(dom)}
+    sort_passes = (3 * 5 + 7) // 8  # 32^3 blocks -> 5 Morton bits per axis
+    launches_per_step = (1 + 5 * sort_passes + 1) + N * 5
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": n, "material": "drucker_prager_sand",
+                   "bodies": len(sc["bodies"]), "dx": sc["grid"]["dx"], "grid": list(sc["grid"]["res"]),
+                   "h": sc["h"], "substeps_per_step": N, "eps_r": 5e-2,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replica per GPU" if ws > 1 else "single GPU"},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(len(bodies) * C_sizeof_body(native)),
+                "d2h_bytes_per_step": int(12 * n + 48 * len(bodies))},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roof,
+        "kernels": kern,
+        "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
+        "solver": {"iters_per_substep": st.iters_total / max(st.substeps, 1),
+                   "contacts_max": st.contacts_max, "residual_max": st.residual_max,
+                   "active_blocks_max": st.active_blocks_max, "status_bits": st.status_bits,
+                   "p2g_global_chunks": st.p2g_global_chunks,
+                   "status_timed": native.STATUS_NAMES[code_timed]},
+    }
+    if clk:
+        line["clocks"] = clk
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc, sim, native)
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def C_sizeof_body(native):
+    import ctypes
+    return ctypes.sizeof(native.RigidBody)
+
+
+def octant_sample(sc, state=None):
+    """One octant of the sand (x < 0, y < 0, z < 0.15) with every body: a
+    bounded sample of the workload for the CPU oracle."""
+    x = np.asarray(state["x"] if state is not None else sc["groups"][0]["x"])
+    sel = (x[:, 0] < 0) & (x[:, 1] < 0) & (x[:, 2] < 0.15)
+    return sel
+
+
+def oracle_time(sc, state, sel, n_substeps=1):
+    import oracle as O
+    g = sc["groups"][0]
+    m = int(sel.sum())
+    V = float(np.float32(g["vol"]))
+    st = O.Sim.state({"x": state["x"][sel], "v": state["v"][sel], "C": state["C"][sel],
+                      "F": state["F"][sel], "mass": np.full(m, V * float(np.float32(g["material"]["rho"]))),
+                      "vol": np.full(m, V), "mat": np.zeros(m, np.int32)})
+    _, mats = O.from_scene({"groups": [g]})
+    osim = O.Sim(sc["grid"])
+    bodies = [O.make_body(b) for b in O.bodies_from_scene(sc)]
+    S = O.solver(eps_r=5e-2, max_iters=1000)
+    t0 = time.perf_counter()
+    for _ in range(n_substeps):
+        osim.substep(st, mats, bodies, sc["h"], S)
+    return m, time.perf_counter() - t0
+
+
+def cpu_baseline(sc, sim, native):
+    state = sim.get_particles()
+    sel = octant_sample(sc, state)
+    m, secs = oracle_time(sc, state, sel, n_substeps=2)
+    return {"value": m * 2 / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 oracle, 1 thread: 2 substeps of the %d particles in one octant "
+                      "(x<0, y<0, z<0.15 m) of the bench state, all bodies; %.1f s" % (m, secs)}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    sc = make_scene()
+    state = {"x": sc["groups"][0]["x"], "v": sc["groups"][0]["v"],
+             "C": np.zeros((N_PARTICLES, 3, 3), np.float32),
+             "F": np.tile(np.eye(3, dtype=np.float32), (N_PARTICLES, 1, 1))}
+    sel = octant_sample(sc, state)
+    for _ in range(min(args.warmup, 1)):
+        oracle_time(sc, state, sel, 1)
+    total_units, total_s = 0.0, 0.0
+    for _ in range(args.steps):
+        m, s = oracle_time(sc, state, sel, 1)
+        total_units += m
+        total_s += s
+    value = total_units / total_s
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "particles": N_PARTICLES,
+                       "sample": "one octant (%d particles), one substep per step" % int(sel.sum())},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "FP64 oracle on one octant of the initial sand state, "
+                                       "one substep per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--max-iters", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/*
+ * mpmcr.h -- C ABI of the GB300 (sm_103a) MPM / rigid-body convex-contact
+ * substep library.
+ *
+ * The library advances material points (MPM) coupled to rigid bodies through
+ * the convex frictional-contact formulation of Yu et al., "A Convex
+ * Formulation of Material Points and Rigid Bodies with GPU-Accelerated
+ * Async-Coupling for Interactive Simulation" (arXiv 2503.05046):
+ *
+ *   - one call to mpm_step is one rigid time step of the asynchronous time
+ *     splitting (Sec. IV-A, Eq. (3)-(4)): the rigid bodies' poses and spatial
+ *     velocities are frozen while N MPM substeps of size h run, and the
+ *     contact impulses of all substeps are accumulated for the caller's rigid
+ *     solver;
+ *   - one substep (Eq. (5)) is the free motion of Eq. (6) (an explicit
+ *     MLS-MPM step: particle-to-grid, grid update, later grid-to-particle with
+ *     the constitutive update) followed by the contact solve of Eq. (7)-(8),
+ *     the convex problem min_v 1/2 ||v - v*||_M^2 + l_c(v_c), solved by the
+ *     block-diagonal quasi-Newton iteration with exact line search of Alg. 1
+ *     (Sec. IV-C, V-B).
+ *
+ * Conventions shared by every entry point:
+ *   - Units are SI; z is up in the examples but gravity is a parameter.
+ *   - Particle arrays are float32, row-major per particle: x, v are [n][3];
+ *     C (affine velocity) and F (deformation gradient) are [n][3][3]
+ *     row-major. Particles are identified by the order in which they were
+ *     added (id 0, 1, ...); the library reorders them internally (a radix sort
+ *     by grid block once per time step, Sec. V-A) but every input and output
+ *     is in id order.
+ *   - `mem_kind` selects where a caller buffer lives: MPM_MEM_HOST (0) or
+ *     MPM_MEM_DEVICE (1, a pointer on the context's device).
+ *   - Caller buffers are only read or written during the call (inputs are
+ *     copied); the context owns all of its device memory.
+ *   - Work is ordered on the context's CUDA stream. Calls that return data to
+ *     the host (mpm_get_*, mpm_step with a stats pointer, mpm_synchronize)
+ *     synchronise that stream; the others are asynchronous.
+ *   - No exception crosses the ABI. Every entry point returns an mpm_status.
+ *     Device-side failures (a particle leaving the domain, a capacity
+ *     overflow, a solve that did not converge) are recorded on the device and
+ *     reported by the next synchronising call; they stay set until read.
+ *     mpm_last_error gives a message for the last failure.
+ */
+#ifndef MPMCR_H
+#define MPMCR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpm_ctx mpm_ctx;
+
+typedef enum {
+  MPM_OK = 0,
+  MPM_ERR_INVALID_ARG = 1,    /* bad argument; nothing was done */
+  MPM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  MPM_ERR_OOM = 3,            /* device allocation failed */
+  MPM_ERR_CAPACITY = 4,       /* more particles or contacts than the context holds */
+  MPM_ERR_NOT_CONVERGED = 5,  /* a contact solve hit max_iters (Alg. 1) */
+  MPM_ERR_OUT_OF_DOMAIN = 6,  /* a particle's stencil left the grid */
+  MPM_ERR_NAN = 7,            /* a non-finite value appeared in the solve */
+  MPM_ERR_STATE = 8,          /* call not valid in the context's state */
+  MPM_ERR_TIMEOUT = 9,        /* a device-wide barrier gave up waiting */
+  MPM_ERR_LINE_SEARCH = 10    /* the line-search bracket could not be formed */
+} mpm_status;
+
+enum { MPM_MEM_HOST = 0, MPM_MEM_DEVICE = 1 };
+
+/* Material models: fixed corotated elasticity, and Drucker-Prager sand
+   (Hencky strain, the granular model the paper cites, Sec. II-A). */
+enum { MPM_COROTATED = 0, MPM_DRUCKER_PRAGER = 1 };
+
+/* Rigid geometry (analytic signed distance functions, body frame):
+   HALFSPACE  the plane z = 0, outward normal +z (no parameters);
+   SPHERE     params[0] = radius;
+   BOX        params[0..2] = half extents;
+   CAPSULE    params[0] = half length along z, params[1] = radius. */
+enum { MPM_HALFSPACE = 0, MPM_SPHERE = 1, MPM_BOX = 2, MPM_CAPSULE = 3 };
+
+/* Eulerian grid (Sec. V-A). Node (i,j,k) sits at origin + dx*(i,j,k). The
+   grid is block-sparse in time (only 4^3 blocks touched by particles are
+   swept) over a dense address space of res[0]*res[1]*res[2] nodes; each
+   res[a] must be a positive multiple of 4. Nodes within bc_layers of a domain
+   face are Dirichlet nodes held at zero velocity (the paper is silent on
+   domain walls; this is the reading taken). */
+typedef struct {
+  double dx;
+  int32_t res[3];
+  double origin[3];
+  double gravity[3];
+  int32_t bc_layers;
+  int64_t max_particles;  /* capacity of the context */
+  int64_t max_contacts;   /* contact points per substep (Sec. V-B) */
+} mpm_grid_spec;
+
+/* Per particle group material. Lame parameters come from (E, nu);
+   friction_angle_deg is used by MPM_DRUCKER_PRAGER only. */
+typedef struct {
+  int32_t model;
+  float E;
+  float nu;
+  float rho;
+  float friction_angle_deg;
+} mpm_material;
+
+/* A rigid body as seen by one time step (Sec. IV-A: pose and spatial
+   velocity are frozen for the N substeps). R is the body-to-world rotation
+   (row-major), p the body origin; omega and v are the angular velocity and
+   the velocity of the body origin, world frame. mu is the friction
+   coefficient; k [N/m] and d [s/m] are the stiffness and Hunt-Crossley
+   dissipation of the compliant normal law of the lagged contact model
+   (Sec. IV-B). If kinematic is nonzero the library advances the pose with
+   the frozen velocity after each mpm_step; otherwise the pose is the
+   caller's to update (static, or integrated by the caller's rigid solver
+   from the impulses of mpm_get_rigid_impulses, Eq. (3)). */
+typedef struct {
+  int32_t shape;
+  float params[4];
+  float R[9];
+  float p[3];
+  float omega[3];
+  float v[3];
+  float mu;
+  float k;
+  float d;
+  int32_t kinematic;
+} mpm_rigid_body;
+
+/* Settings of the contact solve (Alg. 1). The iteration stops when
+   ||M^-1/2 grad l_p|| < eps_a + eps_r max(||M^1/2 v||, ||M^-1/2 J^T gamma||);
+   the paper's defaults are eps_r = 5e-2 and eps_a = machine epsilon (Sec. VI).
+   eps_s [m/s] is the friction regularisation velocity of the lagged model.
+   The exact line search stops when |f'(alpha)| <= ls_rel_tol |f'(0)| or
+   after ls_max_iters evaluations. */
+typedef struct {
+  double eps_r;
+  double eps_a;
+  int32_t max_iters;
+  float eps_s;
+  float ls_rel_tol;
+  int32_t ls_max_iters;
+} mpm_solver_params;
+
+/* Statistics of one mpm_step (all substeps). */
+typedef struct {
+  int32_t substeps;
+  int32_t iters_total;       /* quasi-Newton iterations, summed over substeps */
+  int32_t iters_max;
+  int32_t ls_evals_total;    /* line-search evaluation passes */
+  int32_t contacts_max;      /* contact points in one substep */
+  int32_t active_blocks_max; /* 4^3 grid blocks swept in one substep */
+  int64_t contacts_total;
+  double residual_max;       /* max over substeps of the final
+                                ||M^-1/2 grad|| / max(||M^1/2 v||, ||M^-1/2 J^T gamma||) */
+  int32_t status_bits;       /* OR of (1 << mpm_status) seen on the device */
+  int32_t p2g_global_chunks; /* P2G particle chunks that bypassed the shared tile */
+} mpm_step_stats;
+
+/* Create a context on the current CUDA device. `cuda_stream` is a
+   cudaStream_t (NULL: the context creates its own stream). All device memory
+   (particles, grid, contacts, sort buffers) is allocated here. */
+mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** out);
+
+/* Free the context and all of its device memory. NULL is accepted. */
+mpm_status mpm_destroy(mpm_ctx* ctx);
+
+/* Message of the last failure on this context (static storage owned by the
+   context; "" if none). Safe with ctx == NULL (returns a generic message). */
+const char* mpm_last_error(const mpm_ctx* ctx);
+
+/* Append n particles of one material with rest volume `particle_volume`
+   (mass = rho * volume), positions x[n][3] and velocities v[n][3]; C = 0,
+   F = I. Their ids are first_id .. first_id + n - 1 (first_id may be NULL).
+   At most 65535 groups (calls) per context. */
+mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v,
+                             float particle_volume, const mpm_material* material,
+                             int32_t mem_kind, int64_t* first_id);
+
+/* Number of particles in the context. */
+mpm_status mpm_num_particles(const mpm_ctx* ctx, int64_t* n);
+
+/* Overwrite the state of all particles, in id order. Any of x, v, C, F may be
+   NULL to keep that field (used for checkpoint restore and for starting a
+   substep from a given state). */
+mpm_status mpm_set_particles(mpm_ctx* ctx, const float* x, const float* v, const float* C,
+                             const float* F, int32_t mem_kind);
+
+/* Read the state of all particles, in id order. NULL skips a field. */
+mpm_status mpm_get_particles(mpm_ctx* ctx, float* x, float* v, float* C, float* F,
+                             int32_t mem_kind);
+
+/* Replace the rigid bodies (at most 16). They apply from the next mpm_step. */
+mpm_status mpm_set_rigid_bodies(mpm_ctx* ctx, int32_t n, const mpm_rigid_body* bodies);
+
+/* Current rigid bodies (kinematic ones after their pose updates). */
+mpm_status mpm_get_rigid_bodies(const mpm_ctx* ctx, int32_t n, mpm_rigid_body* out);
+
+/* One rigid time step: n_substeps MPM substeps of size h with the rigid
+   bodies frozen (Eq. (4)). The particle order is refreshed (radix sort) at
+   the start of the step and reused by all substeps (Sec. V-A). Kinematic
+   bodies then advance by n_substeps*h. `solver` may be NULL for the paper's
+   defaults (eps_r = 5e-2, eps_a = DBL_EPSILON, eps_s = 1e-4 m/s). With
+   `stats` non-NULL the call synchronises, fills it and returns the first
+   device-side failure; with NULL it returns without waiting. */
+mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps,
+                    const mpm_solver_params* solver, mpm_step_stats* stats);
+
+/* Per body, the impulse on the body (3) and its moment about the body origin
+   p (3), summed over the substeps since the last reset (the sum over k of
+   J_r^T gamma_d^{n,k} in Eq. (3)); out has 6*n_bodies doubles, host memory.
+   reset != 0 zeroes the accumulators after reading. */
+mpm_status mpm_get_rigid_impulses(mpm_ctx* ctx, double* out, int32_t reset);
+
+/* Grid of the last substep: the nodes with mass, as linear ids
+   i + res[0]*(j + res[1]*k), their mass, free-motion velocity v* (Eq. (6))
+   and post-contact velocity v^{k+1} (Eq. (8)). Host arrays of capacity `cap`
+   (ids may not come sorted); *count receives the number of nodes even when
+   it exceeds cap. Any array may be NULL. Diagnostic / testing call. */
+mpm_status mpm_get_grid(mpm_ctx* ctx, int64_t cap, int64_t* count, int32_t* node_ids,
+                        float* m, float* vstar, float* v);
+
+/* Contacts of the last substep (one per particle inside a body, Sec. V-B):
+   particle id, body index, impulse on the particle (world frame, 3),
+   penetration depth and lagged normal impulse. Host arrays, as above. */
+mpm_status mpm_get_contacts(mpm_ctx* ctx, int64_t cap, int64_t* count, int32_t* particle,
+                            int32_t* body, float* gamma, float* phi0, float* n0);
+
+/* Wait for the context's stream and report any device-side failure. */
+mpm_status mpm_synchronize(mpm_ctx* ctx);
+
+/* Options. MPM_OPT_PROFILE: nonzero records CUDA events around each phase of
+   each substep (read with mpm_get_phase_times). MPM_OPT_SORT_EVERY: sort the
+   particles every k-th time step (default 1). MPM_OPT_P2G_CHUNK: particles
+   per P2G thread block (256, 512 or 1024). */
+enum { MPM_OPT_PROFILE = 1, MPM_OPT_SORT_EVERY = 2, MPM_OPT_P2G_CHUNK = 3 };
+mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value);
+
+/* Phases timed when profiling is on. */
+enum {
+  MPM_PHASE_SORT = 0,       /* key, radix sort, permute (once per step) */
+  MPM_PHASE_P2G = 1,        /* particle-to-grid + contact registration */
+  MPM_PHASE_GRID = 2,       /* block compaction + grid update */
+  MPM_PHASE_SOLVE = 3,      /* quasi-Newton contact solve */
+  MPM_PHASE_G2P = 4,        /* grid-to-particle + constitutive update */
+  MPM_NUM_PHASES = 5
+};
+
+/* Accumulated milliseconds and launch counts per phase since the last reset
+   (arrays of MPM_NUM_PHASES; either may be NULL). Synchronises. */
+mpm_status mpm_get_phase_times(mpm_ctx* ctx, double* ms, int64_t* launches, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPMCR_H */

@@ -1,0 +1,721 @@
+// api.cu -- the C ABI of include/mpmcr.h: context and device memory, the
+// substep schedule of one rigid time step (Eq. (3)-(4)), state I/O in particle
+// id order, diagnostics and phase timing.
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace mpmcr;
+
+struct mpm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  mpm_grid_spec spec{};
+  GridDev g{};
+  int64_t cap = 0, n = 0;
+  int num_sms = 0, solve_blocks = 0;
+  float* pbuf[2] = {nullptr, nullptr};
+  uint32_t* pidbuf[2] = {nullptr, nullptr};
+  uint16_t* grpbuf[2] = {nullptr, nullptr};
+  Particles P[2];
+  int cur = 0;
+  std::vector<DevGroup> groups;
+  DevGroup* groups_d = nullptr;
+  int groups_cap = 0;
+  std::vector<mpm_rigid_body> bodies;
+  DevBody* bodies_d = nullptr;
+  bool bodies_dirty = true;
+  GridArrays G{};
+  size_t n_nodes = 0;
+  int n_blocks = 0;
+  Contacts C{};
+  double* red = nullptr;
+  unsigned* bar = nullptr;
+  uint32_t* status = nullptr;
+  DevStats* stats = nullptr;
+  double* impulses = nullptr;
+  SortBuffers sb{};
+  float* stage = nullptr;  // 24 floats per particle
+  bool profile = false;
+  int sort_every = 1;
+  int p2g_chunk = 256;
+  int64_t step_count = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, cudaEvent_t>> ev_marks;  // (phase starting at this event, event)
+  double phase_ms[MPM_NUM_PHASES] = {0};
+  int64_t phase_n[MPM_NUM_PHASES] = {0};
+  std::string err;
+};
+
+namespace {
+
+const char* kGenericError = "invalid mpm context";
+
+mpm_status fail(mpm_ctx* c, mpm_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+#define CU(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? MPM_ERR_OOM : MPM_ERR_CUDA, \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
+}
+
+Particles make_particles(float* buf, uint32_t* pid, uint16_t* grp, int64_t cap) {
+  Particles P;
+  for (int c = 0; c < 3; ++c) P.x[c] = buf + (size_t)c * cap;
+  for (int c = 0; c < 3; ++c) P.v[c] = buf + (size_t)(3 + c) * cap;
+  for (int c = 0; c < 9; ++c) P.C[c] = buf + (size_t)(6 + c) * cap;
+  for (int c = 0; c < 9; ++c) P.F[c] = buf + (size_t)(15 + c) * cap;
+  P.pid = pid;
+  P.grp = grp;
+  return P;
+}
+
+__global__ void k_append(Particles P, int64_t offset, int64_t n, const float* __restrict__ x,
+                         const float* __restrict__ v, uint16_t grp) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int64_t i = offset + j;
+  for (int c = 0; c < 3; ++c) {
+    P.x[c][i] = x[3 * j + c];
+    P.v[c][i] = v[3 * j + c];
+  }
+  for (int c = 0; c < 9; ++c) {
+    P.C[c][i] = 0.f;
+    P.F[c][i] = (c % 4 == 0) ? 1.f : 0.f;
+  }
+  P.pid[i] = (uint32_t)i;
+  P.grp[i] = grp;
+}
+
+__global__ void k_grid_out(GridDev g, GridArrays G, int n_act, int* __restrict__ count,
+                           int* __restrict__ ids, float* __restrict__ m, float* __restrict__ vs,
+                           float* __restrict__ v) {
+  long long total = (long long)n_act * kBlockNodes;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int blk = G.act[t >> 6], cell = (int)(t & 63);
+    int node = blk * kBlockNodes + cell;
+    float4 a = G.vs[node];
+    if (!(a.w > 0.f)) continue;
+    float4 b = G.v[node];
+    int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
+    int i = bx * 4 + (cell & 3), j = by * 4 + ((cell >> 2) & 3), k = bz * 4 + (cell >> 4);
+    int slot = atomicAdd(count, 1);
+    ids[slot] = i + g.rx * (j + g.ry * k);
+    m[slot] = a.w;
+    vs[3 * slot] = a.x; vs[3 * slot + 1] = a.y; vs[3 * slot + 2] = a.z;
+    v[3 * slot] = b.x; v[3 * slot + 1] = b.y; v[3 * slot + 2] = b.z;
+  }
+}
+
+DevBody to_dev(const mpm_rigid_body& b) {
+  DevBody d;
+  memset(&d, 0, sizeof(d));
+  d.shape = b.shape;
+  for (int i = 0; i < 4; ++i) d.prm[i] = b.params[i];
+  for (int i = 0; i < 9; ++i) d.R[i] = b.R[i];
+  for (int i = 0; i < 3; ++i) {
+    d.p[i] = b.p[i];
+    d.w[i] = b.omega[i];
+    d.v[i] = b.v[i];
+  }
+  d.mu = b.mu;
+  d.k = b.k;
+  d.d = b.d;
+  d.bound = INFINITY;
+  return d;
+}
+
+// R <- exp(dt [omega]x) R, p <- p + dt v (kinematic bodies between time steps)
+void advance_kinematic(mpm_rigid_body& b, double dt) {
+  for (int i = 0; i < 3; ++i) b.p[i] = (float)((double)b.p[i] + dt * b.v[i]);
+  double w[3] = {dt * b.omega[0], dt * b.omega[1], dt * b.omega[2]};
+  double th = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  if (th == 0.0) return;
+  double a[3] = {w[0] / th, w[1] / th, w[2] / th};
+  double c = std::cos(th), s = std::sin(th), t = 1.0 - c;
+  double Q[9] = {c + t * a[0] * a[0],        t * a[0] * a[1] - s * a[2], t * a[0] * a[2] + s * a[1],
+                 t * a[1] * a[0] + s * a[2], c + t * a[1] * a[1],        t * a[1] * a[2] - s * a[0],
+                 t * a[2] * a[0] - s * a[1], t * a[2] * a[1] + s * a[0], c + t * a[2] * a[2]};
+  double R[9];
+  for (int r = 0; r < 3; ++r)
+    for (int cc = 0; cc < 3; ++cc)
+      R[3 * r + cc] = Q[3 * r] * b.R[cc] + Q[3 * r + 1] * b.R[3 + cc] + Q[3 * r + 2] * b.R[6 + cc];
+  for (int i = 0; i < 9; ++i) b.R[i] = (float)R[i];
+}
+
+mpm_status first_error(mpm_ctx* ctx, uint32_t bits) {
+  static const mpm_status order[] = {MPM_ERR_TIMEOUT, MPM_ERR_NAN, MPM_ERR_OUT_OF_DOMAIN,
+                                     MPM_ERR_CAPACITY, MPM_ERR_LINE_SEARCH,
+                                     MPM_ERR_NOT_CONVERGED};
+  static const char* msg[] = {"a device-wide barrier of the contact solve timed out",
+                              "a non-finite value appeared in the contact solve",
+                              "a particle's B-spline stencil left the grid domain",
+                              "more contact points than max_contacts in one substep",
+                              "the line-search bracket could not be formed",
+                              "a contact solve reached max_iters before converging"};
+  for (int i = 0; i < 6; ++i)
+    if (bits & (1u << order[i])) return fail(ctx, order[i], msg[i]);
+  return MPM_OK;
+}
+
+// read and clear the device status word (synchronises)
+mpm_status drain_status(mpm_ctx* ctx, uint32_t* bits_out = nullptr) {
+  CU(cudaStreamSynchronize(ctx->stream));
+  uint32_t bits = 0;
+  CU(cudaMemcpy(&bits, ctx->status, sizeof(bits), cudaMemcpyDeviceToHost));
+  if (bits) CU(cudaMemset(ctx->status, 0, sizeof(uint32_t)));
+  if (bits_out) *bits_out = bits;
+  return first_error(ctx, bits);
+}
+
+cudaEvent_t take_event(mpm_ctx* ctx) {
+  cudaEvent_t e = nullptr;
+  if (!ctx->ev_pool.empty()) {
+    e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  return e;
+}
+
+void mark_phase(mpm_ctx* ctx, int phase) {
+  if (!ctx->profile) return;
+  cudaEvent_t e = take_event(ctx);
+  cudaEventRecord(e, ctx->stream);
+  ctx->ev_marks.emplace_back(phase, e);
+}
+
+// fold recorded events into per-phase totals (after a synchronise); a mark
+// with phase -1 only closes the previous interval
+void fold_events(mpm_ctx* ctx) {
+  for (size_t i = 0; i + 1 < ctx->ev_marks.size(); ++i) {
+    int ph = ctx->ev_marks[i].first;
+    if (ph < 0) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev_marks[i].second, ctx->ev_marks[i + 1].second) ==
+        cudaSuccess) {
+      ctx->phase_ms[ph] += ms;
+      ctx->phase_n[ph] += 1;
+    }
+  }
+  if (!ctx->ev_marks.empty()) {
+    // keep the last mark's event as the open end only if it starts a phase
+    for (size_t i = 0; i < ctx->ev_marks.size(); ++i) ctx->ev_pool.push_back(ctx->ev_marks[i].second);
+    ctx->ev_marks.clear();
+  }
+}
+
+void release(mpm_ctx* c) {
+  void* ptrs[] = {c->pbuf[0], c->pbuf[1], c->pidbuf[0], c->pidbuf[1], c->grpbuf[0], c->grpbuf[1],
+                  c->groups_d, c->bodies_d, c->G.mp, c->G.vs, c->G.v, c->G.acc0, c->G.acc1,
+                  c->G.acc2, c->G.dv, c->G.mark, c->G.act, c->G.n_act, c->C.xp, c->C.nrm,
+                  c->C.bias, c->C.id, c->C.vc, c->C.dvc, c->C.gamma, c->C.count, c->red, c->bar,
+                  c->status, c->stats, c->impulses, c->sb.keys[0], c->sb.keys[1], c->sb.vals[0],
+                  c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& e : c->ev_marks) cudaEventDestroy(e.second);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+int ceil_log2(int v) {
+  int b = 0;
+  while ((1 << b) < v) ++b;
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** out) {
+  mpm_ctx* ctx = nullptr;
+  if (!spec || !out) return MPM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!(spec->dx > 0.0) || spec->max_particles <= 0 || spec->max_particles >= (1LL << 31) ||
+      spec->max_contacts <= 0 || spec->max_contacts >= (1LL << 31) || spec->bc_layers < 0)
+    return MPM_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (spec->res[a] <= 0 || spec->res[a] % 4 != 0 || spec->res[a] > 4096) return MPM_ERR_INVALID_ARG;
+  ctx = new mpm_ctx();
+  ctx->spec = *spec;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return MPM_ERR_CUDA;
+  }
+  auto bail = [&](mpm_status st) {
+    release(ctx);
+    delete ctx;
+    return st;
+  };
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
+    return bail(MPM_ERR_CUDA);
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(MPM_ERR_CUDA);
+    ctx->own_stream = true;
+  }
+  GridDev& g = ctx->g;
+  g.dx = (float)spec->dx;
+  g.inv_dx = (float)(1.0 / spec->dx);
+  g.ox = (float)spec->origin[0]; g.oy = (float)spec->origin[1]; g.oz = (float)spec->origin[2];
+  g.gx = (float)spec->gravity[0]; g.gy = (float)spec->gravity[1]; g.gz = (float)spec->gravity[2];
+  g.rx = spec->res[0]; g.ry = spec->res[1]; g.rz = spec->res[2];
+  g.nbx = g.rx / 4; g.nby = g.ry / 4; g.nbz = g.rz / 4;
+  g.bc = spec->bc_layers;
+  int mb = g.nbx > g.nby ? g.nbx : g.nby;
+  mb = mb > g.nbz ? mb : g.nbz;
+  g.morton_bits = ceil_log2(mb) > 0 ? ceil_log2(mb) : 1;
+  ctx->cap = spec->max_particles;
+  ctx->n_blocks = g.nbx * g.nby * g.nbz;
+  ctx->n_nodes = (size_t)ctx->n_blocks * kBlockNodes;
+  const int64_t cap = ctx->cap;
+  const int64_t ccap = spec->max_contacts;
+  bool ok = true;
+  for (int s = 0; s < 2; ++s) {
+    ok = ok && dalloc(&ctx->pbuf[s], (size_t)24 * cap) == cudaSuccess;
+    ok = ok && dalloc(&ctx->pidbuf[s], cap) == cudaSuccess;
+    ok = ok && dalloc(&ctx->grpbuf[s], cap) == cudaSuccess;
+    if (ok) ctx->P[s] = make_particles(ctx->pbuf[s], ctx->pidbuf[s], ctx->grpbuf[s], cap);
+  }
+  const size_t nn = ctx->n_nodes;
+  ok = ok && dalloc(&ctx->G.mp, nn) == cudaSuccess && dalloc(&ctx->G.vs, nn) == cudaSuccess &&
+       dalloc(&ctx->G.v, nn) == cudaSuccess && dalloc(&ctx->G.acc0, nn) == cudaSuccess &&
+       dalloc(&ctx->G.acc1, nn) == cudaSuccess && dalloc(&ctx->G.acc2, nn) == cudaSuccess &&
+       dalloc(&ctx->G.dv, nn) == cudaSuccess && dalloc(&ctx->G.mark, ctx->n_blocks) == cudaSuccess &&
+       dalloc(&ctx->G.act, ctx->n_blocks) == cudaSuccess && dalloc(&ctx->G.n_act, 1) == cudaSuccess;
+  ok = ok && dalloc(&ctx->C.xp, ccap) == cudaSuccess && dalloc(&ctx->C.nrm, ccap) == cudaSuccess &&
+       dalloc(&ctx->C.bias, ccap) == cudaSuccess && dalloc(&ctx->C.id, ccap) == cudaSuccess &&
+       dalloc(&ctx->C.vc, ccap) == cudaSuccess && dalloc(&ctx->C.dvc, ccap) == cudaSuccess &&
+       dalloc(&ctx->C.gamma, ccap) == cudaSuccess && dalloc(&ctx->C.count, 1) == cudaSuccess;
+  ctx->C.cap = (int)ccap;
+  ok = ok && dalloc(&ctx->red, 32) == cudaSuccess && dalloc(&ctx->bar, 2) == cudaSuccess &&
+       dalloc(&ctx->status, 1) == cudaSuccess && dalloc(&ctx->stats, 1) == cudaSuccess &&
+       dalloc(&ctx->impulses, 6 * kMaxBodies) == cudaSuccess &&
+       dalloc(&ctx->bodies_d, kMaxBodies) == cudaSuccess;
+  const int hist_len = sort_hist_len((int)cap);
+  ok = ok && dalloc(&ctx->sb.keys[0], cap) == cudaSuccess && dalloc(&ctx->sb.keys[1], cap) == cudaSuccess &&
+       dalloc(&ctx->sb.vals[0], cap) == cudaSuccess && dalloc(&ctx->sb.vals[1], cap) == cudaSuccess &&
+       dalloc(&ctx->sb.hist, hist_len) == cudaSuccess &&
+       dalloc(&ctx->sb.partial, hist_len / 4096 + 2) == cudaSuccess;
+  ctx->sb.hist_cap = hist_len;
+  ok = ok && dalloc(&ctx->stage, (size_t)24 * cap) == cudaSuccess;
+  if (!ok) return bail(MPM_ERR_OOM);
+  // zero-invariant arrays and counters
+  ok = cudaMemset(ctx->G.mp, 0, nn * sizeof(float4)) == cudaSuccess &&
+       cudaMemset(ctx->G.acc0, 0, nn * sizeof(float4)) == cudaSuccess &&
+       cudaMemset(ctx->G.acc1, 0, nn * sizeof(float4)) == cudaSuccess &&
+       cudaMemset(ctx->G.acc2, 0, nn * sizeof(float)) == cudaSuccess &&
+       cudaMemset(ctx->G.vs, 0, nn * sizeof(float4)) == cudaSuccess &&
+       cudaMemset(ctx->G.v, 0, nn * sizeof(float4)) == cudaSuccess &&
+       cudaMemset(ctx->G.mark, 0, ctx->n_blocks) == cudaSuccess &&
+       cudaMemset(ctx->G.n_act, 0, sizeof(int)) == cudaSuccess &&
+       cudaMemset(ctx->C.count, 0, sizeof(int)) == cudaSuccess &&
+       cudaMemset(ctx->red, 0, 32 * sizeof(double)) == cudaSuccess &&
+       cudaMemset(ctx->bar, 0, 2 * sizeof(unsigned)) == cudaSuccess &&
+       cudaMemset(ctx->status, 0, sizeof(uint32_t)) == cudaSuccess &&
+       cudaMemset(ctx->stats, 0, sizeof(DevStats)) == cudaSuccess &&
+       cudaMemset(ctx->impulses, 0, 6 * kMaxBodies * sizeof(double)) == cudaSuccess &&
+       cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) return bail(MPM_ERR_CUDA);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_kernel_ptr(), solve_block_size(), 0) !=
+          cudaSuccess ||
+      occ < 1)
+    return bail(MPM_ERR_CUDA);
+  ctx->solve_blocks = ctx->num_sms * (occ < 2 ? occ : 2);
+  *out = ctx;
+  return MPM_OK;
+}
+
+mpm_status mpm_destroy(mpm_ctx* ctx) {
+  if (!ctx) return MPM_OK;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  release(ctx);
+  delete ctx;
+  return MPM_OK;
+}
+
+const char* mpm_last_error(const mpm_ctx* ctx) {
+  if (!ctx) return kGenericError;
+  return ctx->err.c_str();
+}
+
+mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v,
+                             float particle_volume, const mpm_material* mat, int32_t mem_kind,
+                             int64_t* first_id) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!x || !v)) || !mat || !(particle_volume > 0.f) ||
+      (mem_kind != MPM_MEM_HOST && mem_kind != MPM_MEM_DEVICE))
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_add_particles: bad argument");
+  if (mat->model != MPM_COROTATED && mat->model != MPM_DRUCKER_PRAGER)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_add_particles: unknown material model");
+  if (!(mat->E > 0.f) || !(mat->nu > -1.f && mat->nu < 0.5f) || !(mat->rho > 0.f))
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_add_particles: bad material constants");
+  if (ctx->n + n > ctx->cap) return fail(ctx, MPM_ERR_CAPACITY, "mpm_add_particles: max_particles exceeded");
+  if (ctx->groups.size() >= 65535) return fail(ctx, MPM_ERR_CAPACITY, "mpm_add_particles: too many groups");
+  if (first_id) *first_id = ctx->n;
+  DevGroup gr;
+  memset(&gr, 0, sizeof(gr));
+  double E = mat->E, nu = mat->nu;
+  gr.vol = particle_volume;
+  gr.mass = (float)((double)mat->rho * (double)particle_volume);
+  gr.mu_l = (float)(E / (2.0 * (1.0 + nu)));
+  gr.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+  double sphi = std::sin((double)mat->friction_angle_deg * 3.14159265358979323846 / 180.0);
+  gr.dp_alpha = (float)(std::sqrt(2.0 / 3.0) * 2.0 * sphi / (3.0 - sphi));
+  gr.model = mat->model;
+  ctx->groups.push_back(gr);
+  if ((int)ctx->groups.size() > ctx->groups_cap) {
+    int nc = ctx->groups_cap ? 2 * ctx->groups_cap : 64;
+    while (nc < (int)ctx->groups.size()) nc *= 2;
+    DevGroup* nd = nullptr;
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(dalloc(&nd, nc));
+    if (ctx->groups_d) cudaFree(ctx->groups_d);
+    ctx->groups_d = nd;
+    ctx->groups_cap = nc;
+  }
+  CU(cudaMemcpyAsync(ctx->groups_d, ctx->groups.data(), ctx->groups.size() * sizeof(DevGroup),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  if (n > 0) {
+    const float *dx = x, *dv = v;
+    if (mem_kind == MPM_MEM_HOST) {
+      CU(cudaMemcpyAsync(ctx->stage, x, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+      CU(cudaMemcpyAsync(ctx->stage + 3 * n, v, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice,
+                         ctx->stream));
+      dx = ctx->stage;
+      dv = ctx->stage + 3 * n;
+    }
+    k_append<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->P[ctx->cur], ctx->n, n, dx, dv, (uint16_t)(ctx->groups.size() - 1));
+    CU(cudaGetLastError());
+  }
+  ctx->n += n;
+  CU(cudaStreamSynchronize(ctx->stream));
+  return MPM_OK;
+}
+
+mpm_status mpm_num_particles(const mpm_ctx* ctx, int64_t* n) {
+  if (!ctx || !n) return MPM_ERR_INVALID_ARG;
+  *n = ctx->n;
+  return MPM_OK;
+}
+
+mpm_status mpm_set_particles(mpm_ctx* ctx, const float* x, const float* v, const float* C,
+                             const float* F, int32_t mem_kind) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (mem_kind != MPM_MEM_HOST && mem_kind != MPM_MEM_DEVICE)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_particles: bad mem_kind");
+  const int64_t n = ctx->n;
+  if (n == 0) return MPM_OK;
+  const float* src[4] = {x, v, C, F};
+  const int width[4] = {3, 3, 9, 9};
+  const float* dptr[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t off = 0;
+  for (int f = 0; f < 4; ++f) {
+    if (!src[f]) continue;
+    if (mem_kind == MPM_MEM_HOST) {
+      CU(cudaMemcpyAsync(ctx->stage + off, src[f], (size_t)n * width[f] * sizeof(float),
+                         cudaMemcpyHostToDevice, ctx->stream));
+      dptr[f] = ctx->stage + off;
+      off += (size_t)n * width[f];
+    } else {
+      dptr[f] = src[f];
+    }
+  }
+  launch_from_id_order(ctx->P[ctx->cur], (int)n, dptr[0], dptr[1], dptr[2], dptr[3], ctx->stream);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(ctx->stream));
+  return MPM_OK;
+}
+
+mpm_status mpm_get_particles(mpm_ctx* ctx, float* x, float* v, float* C, float* F, int32_t mem_kind) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (mem_kind != MPM_MEM_HOST && mem_kind != MPM_MEM_DEVICE)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_get_particles: bad mem_kind");
+  const int64_t n = ctx->n;
+  if (n == 0) return MPM_OK;
+  float* dst[4] = {x, v, C, F};
+  const int width[4] = {3, 3, 9, 9};
+  float* dptr[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t off = 0;
+  for (int f = 0; f < 4; ++f) {
+    if (!dst[f]) continue;
+    if (mem_kind == MPM_MEM_HOST) {
+      dptr[f] = ctx->stage + off;
+      off += (size_t)n * width[f];
+    } else {
+      dptr[f] = dst[f];
+    }
+  }
+  launch_to_id_order(ctx->P[ctx->cur], (int)n, dptr[0], dptr[1], dptr[2], dptr[3], ctx->stream);
+  CU(cudaGetLastError());
+  if (mem_kind == MPM_MEM_HOST)
+    for (int f = 0; f < 4; ++f)
+      if (dst[f])
+        CU(cudaMemcpyAsync(dst[f], dptr[f], (size_t)n * width[f] * sizeof(float), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return MPM_OK;
+}
+
+mpm_status mpm_set_rigid_bodies(mpm_ctx* ctx, int32_t n, const mpm_rigid_body* bodies) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (n < 0 || n > kMaxBodies || (n > 0 && !bodies))
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_rigid_bodies: at most 16 bodies");
+  for (int i = 0; i < n; ++i) {
+    const mpm_rigid_body& b = bodies[i];
+    if (b.shape < MPM_HALFSPACE || b.shape > MPM_CAPSULE || !(b.mu >= 0.f) || !(b.k > 0.f) ||
+        !(b.d >= 0.f))
+      return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_rigid_bodies: bad body");
+  }
+  ctx->bodies.assign(bodies, bodies + n);
+  ctx->bodies_dirty = true;
+  return MPM_OK;
+}
+
+mpm_status mpm_get_rigid_bodies(const mpm_ctx* ctx, int32_t n, mpm_rigid_body* out) {
+  if (!ctx || !out || n < 0 || n > (int32_t)ctx->bodies.size()) return MPM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) out[i] = ctx->bodies[i];
+  return MPM_OK;
+}
+
+mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver_params* solver,
+                    mpm_step_stats* stats) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (!(h > 0.0) || n_substeps < 0)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_step: h must be > 0 and n_substeps >= 0");
+  mpm_solver_params sp;
+  if (solver) {
+    sp = *solver;
+  } else {
+    sp.eps_r = 5e-2;
+    sp.eps_a = DBL_EPSILON;
+    sp.max_iters = 1000;
+    sp.eps_s = 1e-4f;
+    sp.ls_rel_tol = 1e-5f;
+    sp.ls_max_iters = 50;
+  }
+  if (!(sp.eps_r >= 0.0) || !(sp.eps_a >= 0.0) || sp.max_iters < 0 || !(sp.eps_s > 0.f) ||
+      !(sp.ls_rel_tol > 0.f) || sp.ls_max_iters < 1)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_step: bad solver parameters");
+  cudaStream_t s = ctx->stream;
+  const int nb = (int)ctx->bodies.size();
+  if (ctx->bodies_dirty) {
+    DevBody tmp[kMaxBodies];
+    for (int i = 0; i < nb; ++i) tmp[i] = to_dev(ctx->bodies[i]);
+    if (nb) CU(cudaMemcpyAsync(ctx->bodies_d, tmp, nb * sizeof(DevBody), cudaMemcpyHostToDevice, s));
+    ctx->bodies_dirty = false;
+  }
+  CU(cudaMemsetAsync(ctx->stats, 0, sizeof(DevStats), s));
+  const int n = (int)ctx->n;
+  if (n > 0 && ctx->step_count % ctx->sort_every == 0) {
+    mark_phase(ctx, MPM_PHASE_SORT);
+    launch_sort(ctx->g, ctx->P[ctx->cur], ctx->P[1 - ctx->cur], n, ctx->sb, s);
+    ctx->cur = 1 - ctx->cur;
+  }
+  const float hf = (float)h;
+  for (int k = 0; k < n_substeps; ++k) {
+    P2GArgs pa;
+    pa.g = ctx->g; pa.P = ctx->P[ctx->cur]; pa.n = n; pa.groups = ctx->groups_d;
+    pa.bodies = ctx->bodies_d; pa.nb = nb; pa.h = hf; pa.G = ctx->G; pa.C = ctx->C;
+    pa.status = ctx->status; pa.stats = ctx->stats;
+    mark_phase(ctx, MPM_PHASE_P2G);
+    launch_p2g(pa, ctx->p2g_chunk, s);
+    mark_phase(ctx, MPM_PHASE_GRID);
+    launch_grid(ctx->g, ctx->G, hf, ctx->num_sms, ctx->stats, s);
+    SolveArgs sa;
+    sa.g = ctx->g; sa.G = ctx->G; sa.C = ctx->C; sa.bodies = ctx->bodies_d; sa.nb = nb;
+    sa.h = hf; sa.eps_s = sp.eps_s; sa.ls_rel_tol = sp.ls_rel_tol; sa.ls_max_iters = sp.ls_max_iters;
+    sa.eps_r = sp.eps_r; sa.eps_a = sp.eps_a; sa.max_iters = sp.max_iters; sa.red = ctx->red;
+    sa.bar = ctx->bar; sa.status = ctx->status; sa.stats = ctx->stats; sa.impulses = ctx->impulses;
+    mark_phase(ctx, MPM_PHASE_SOLVE);
+    CU(launch_solve(sa, ctx->solve_blocks, s));
+    G2PArgs ga;
+    ga.g = ctx->g; ga.P = ctx->P[ctx->cur]; ga.n = n; ga.groups = ctx->groups_d; ga.G = ctx->G;
+    ga.C = ctx->C; ga.h = hf; ga.bar = ctx->bar; ga.red = ctx->red; ga.stats = ctx->stats;
+    mark_phase(ctx, MPM_PHASE_G2P);
+    launch_g2p(ga, s);
+    mark_phase(ctx, -1);
+  }
+  CU(cudaGetLastError());
+  // async splitting: kinematic bodies move with their frozen velocity
+  const double dt = h * n_substeps;
+  bool moved = false;
+  for (auto& b : ctx->bodies)
+    if (b.kinematic) {
+      advance_kinematic(b, dt);
+      moved = true;
+    }
+  if (moved) ctx->bodies_dirty = true;
+  ctx->step_count += 1;
+  if (!stats) return MPM_OK;
+  uint32_t bits = 0;
+  mpm_status st = drain_status(ctx, &bits);
+  DevStats ds;
+  cudaError_t e = cudaMemcpy(&ds, ctx->stats, sizeof(ds), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(ctx, MPM_ERR_CUDA, cudaGetErrorString(e));
+  memset(stats, 0, sizeof(*stats));
+  stats->substeps = ds.substeps;
+  stats->iters_total = ds.iters_total;
+  stats->iters_max = ds.iters_max;
+  stats->ls_evals_total = ds.ls_evals_total;
+  stats->contacts_max = ds.contacts_max;
+  stats->active_blocks_max = ds.active_blocks_max;
+  stats->contacts_total = (int64_t)ds.contacts_total;
+  stats->residual_max = ds.residual_max;
+  stats->status_bits = (int32_t)bits;
+  stats->p2g_global_chunks = ds.p2g_global_chunks;
+  return st;
+}
+
+mpm_status mpm_get_rigid_impulses(mpm_ctx* ctx, double* out, int32_t reset) {
+  if (!ctx || (!out && !ctx->bodies.empty())) return MPM_ERR_INVALID_ARG;
+  CU(cudaStreamSynchronize(ctx->stream));
+  const size_t nb = ctx->bodies.size();
+  if (nb) CU(cudaMemcpy(out, ctx->impulses, 6 * nb * sizeof(double), cudaMemcpyDeviceToHost));
+  if (reset) CU(cudaMemset(ctx->impulses, 0, 6 * kMaxBodies * sizeof(double)));
+  return MPM_OK;
+}
+
+mpm_status mpm_get_grid(mpm_ctx* ctx, int64_t cap, int64_t* count, int32_t* node_ids, float* m,
+                        float* vstar, float* v) {
+  if (!ctx || !count || cap < 0) return MPM_ERR_INVALID_ARG;
+  CU(cudaStreamSynchronize(ctx->stream));
+  DevStats ds;
+  CU(cudaMemcpy(&ds, ctx->stats, sizeof(ds), cudaMemcpyDeviceToHost));
+  const int n_act = ds.last_active;
+  const size_t max_nodes = (size_t)n_act * kBlockNodes;
+  // stage layout: [count | ids | m | vs(3) | v(3)], sized for the active nodes
+  std::vector<int> h_ids(max_nodes);
+  std::vector<float> h_m(max_nodes), h_vs(3 * max_nodes), h_v(3 * max_nodes);
+  int* d_count = nullptr;
+  int* d_ids = nullptr;
+  float *d_m = nullptr, *d_vs = nullptr, *d_v = nullptr;
+  CU(dalloc(&d_count, 1));
+  bool ok = dalloc(&d_ids, max_nodes + 1) == cudaSuccess && dalloc(&d_m, max_nodes + 1) == cudaSuccess &&
+            dalloc(&d_vs, 3 * max_nodes + 3) == cudaSuccess && dalloc(&d_v, 3 * max_nodes + 3) == cudaSuccess;
+  int got = 0;
+  if (ok) {
+    cudaMemset(d_count, 0, sizeof(int));
+    if (n_act > 0)
+      k_grid_out<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->g, ctx->G, n_act, d_count, d_ids, d_m,
+                                                           d_vs, d_v);
+    ok = cudaStreamSynchronize(ctx->stream) == cudaSuccess &&
+         cudaMemcpy(&got, d_count, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (ok && got > 0) {
+      ok = cudaMemcpy(h_ids.data(), d_ids, got * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
+           cudaMemcpy(h_m.data(), d_m, got * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess &&
+           cudaMemcpy(h_vs.data(), d_vs, 3 * got * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess &&
+           cudaMemcpy(h_v.data(), d_v, 3 * got * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+  }
+  cudaFree(d_count); cudaFree(d_ids); cudaFree(d_m); cudaFree(d_vs); cudaFree(d_v);
+  if (!ok) return fail(ctx, MPM_ERR_CUDA, "mpm_get_grid: device read failed");
+  *count = got;
+  const int64_t k = got < cap ? got : cap;
+  for (int64_t i = 0; i < k; ++i) {
+    if (node_ids) node_ids[i] = h_ids[i];
+    if (m) m[i] = h_m[i];
+    for (int c = 0; c < 3; ++c) {
+      if (vstar) vstar[3 * i + c] = h_vs[3 * i + c];
+      if (v) v[3 * i + c] = h_v[3 * i + c];
+    }
+  }
+  return MPM_OK;
+}
+
+mpm_status mpm_get_contacts(mpm_ctx* ctx, int64_t cap, int64_t* count, int32_t* particle, int32_t* body,
+                            float* gamma, float* phi0, float* n0) {
+  if (!ctx || !count || cap < 0) return MPM_ERR_INVALID_ARG;
+  CU(cudaStreamSynchronize(ctx->stream));
+  DevStats ds;
+  CU(cudaMemcpy(&ds, ctx->stats, sizeof(ds), cudaMemcpyDeviceToHost));
+  const int nc = ds.last_contacts;
+  *count = nc;
+  const int64_t k = nc < cap ? nc : cap;
+  if (k <= 0) return MPM_OK;
+  std::vector<int2> ids(k);
+  std::vector<float4> xp(k), nrm(k), gam(k);
+  CU(cudaMemcpy(ids.data(), ctx->C.id, k * sizeof(int2), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(xp.data(), ctx->C.xp, k * sizeof(float4), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(nrm.data(), ctx->C.nrm, k * sizeof(float4), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(gam.data(), ctx->C.gamma, k * sizeof(float4), cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < k; ++i) {
+    if (particle) particle[i] = ids[i].x;
+    if (body) body[i] = ids[i].y;
+    if (gamma) {
+      gamma[3 * i] = gam[i].x;
+      gamma[3 * i + 1] = gam[i].y;
+      gamma[3 * i + 2] = gam[i].z;
+    }
+    if (phi0) phi0[i] = xp[i].w;
+    if (n0) n0[i] = nrm[i].w;
+  }
+  return MPM_OK;
+}
+
+mpm_status mpm_synchronize(mpm_ctx* ctx) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  return drain_status(ctx);
+}
+
+mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  switch (option) {
+    case MPM_OPT_PROFILE:
+      ctx->profile = value != 0;
+      return MPM_OK;
+    case MPM_OPT_SORT_EVERY:
+      if (value < 1) return fail(ctx, MPM_ERR_INVALID_ARG, "sort interval must be >= 1");
+      ctx->sort_every = (int)value;
+      return MPM_OK;
+    case MPM_OPT_P2G_CHUNK:
+      if (value != 256 && value != 512 && value != 1024)
+        return fail(ctx, MPM_ERR_INVALID_ARG, "P2G chunk must be 256, 512 or 1024");
+      ctx->p2g_chunk = (int)value;
+      return MPM_OK;
+    default:
+      return fail(ctx, MPM_ERR_INVALID_ARG, "unknown option");
+  }
+}
+
+mpm_status mpm_get_phase_times(mpm_ctx* ctx, double* ms, int64_t* launches, int32_t reset) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  CU(cudaStreamSynchronize(ctx->stream));
+  fold_events(ctx);
+  for (int p = 0; p < MPM_NUM_PHASES; ++p) {
+    if (ms) ms[p] = ctx->phase_ms[p];
+    if (launches) launches[p] = ctx->phase_n[p];
+    if (reset) {
+      ctx->phase_ms[p] = 0.0;
+      ctx->phase_n[p] = 0;
+    }
+  }
+  return MPM_OK;
+}
+
+}  // extern "C"

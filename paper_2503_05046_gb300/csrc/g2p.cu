@@ -1,0 +1,95 @@
+// g2p.cu -- grid-to-particle transfer with the constitutive update (Sec. V-A
+// op (3), MLS-MPM): v_p = sum_i w v_i, C_p = (4/dx^2) sum_i w v_i (x_i - x_p)^T,
+// x_p += h v_p, F_p <- (I + h C_p) F_p, then the Drucker-Prager return map for
+// sand. One thread per particle; particle planes are read and written with
+// coalesced loads and stores, grid velocities are gathered from L2.
+//
+// Block 0 also closes the substep: it records the contact / active-block
+// counts for diagnostics and resets the per-substep counters, the solve's
+// barrier word and its reduction ring, so the next substep needs no memset.
+#include "kernels.h"
+
+namespace mpmcr {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads) k_g2p(G2PArgs a) {
+  const GridDev& g = a.g;
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) {
+      const int count = *a.C.count;
+      const int nc = count < a.C.cap ? count : a.C.cap;
+      a.stats->last_contacts = nc;
+      atomicMax(&a.stats->contacts_max, nc);
+      atomicAdd(&a.stats->contacts_total, (unsigned long long)nc);
+      atomicAdd(&a.stats->substeps, 1);
+      *a.C.count = 0;
+      *a.G.n_act = 0;
+      a.bar[0] = 0u;
+    }
+    if (threadIdx.x < 32) a.red[threadIdx.x] = 0.0;
+  }
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= a.n) return;
+  const float xp[3] = {a.P.x[0][i], a.P.x[1][i], a.P.x[2][i]};
+  Stencil s;
+  stencil(g, xp[0], xp[1], xp[2], s);
+  if (!stencil_inside(g, s)) return;  // reported by P2G
+  float vp[3] = {0.f, 0.f, 0.f}, Bm[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int cz = 0; cz < 3; ++cz) {
+    const float dz = (cz - s.fx[2]) * g.dx;
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy) {
+      const float dy = (cy - s.fx[1]) * g.dx;
+      const float wyz = s.w[1][cy] * s.w[2][cz];
+#pragma unroll
+      for (int cx = 0; cx < 3; ++cx) {
+        const float dxp = (cx - s.fx[0]) * g.dx;
+        const float w = s.w[0][cx] * wyz;
+        const float4 v = __ldg(a.G.v + node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz));
+        const float wx = w * v.x, wy = w * v.y, wz = w * v.z;
+        vp[0] += wx; vp[1] += wy; vp[2] += wz;
+        Bm[0] += wx * dxp; Bm[1] += wx * dy; Bm[2] += wx * dz;
+        Bm[3] += wy * dxp; Bm[4] += wy * dy; Bm[5] += wy * dz;
+        Bm[6] += wz * dxp; Bm[7] += wz * dy; Bm[8] += wz * dz;
+      }
+    }
+  }
+  const float dinv = 4.0f * g.inv_dx * g.inv_dx;
+  const float h = a.h;
+  float C[9], F[9], Fn[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    C[c] = dinv * Bm[c];
+    F[c] = a.P.F[c][i];
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      Fn[3 * r + c] = F[3 * r + c] + h * (C[3 * r] * F[c] + C[3 * r + 1] * F[3 + c] + C[3 * r + 2] * F[6 + c]);
+  const DevGroup gr = a.groups[a.P.grp[i]];
+  if (gr.model == MPM_DRUCKER_PRAGER) dp_project(gr, Fn);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    a.P.v[c][i] = vp[c];
+    a.P.x[c][i] = xp[c] + h * vp[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    a.P.C[c][i] = C[c];
+    a.P.F[c][i] = Fn[c];
+  }
+}
+
+}  // namespace
+
+void launch_g2p(const G2PArgs& a, cudaStream_t s) {
+  const int blocks = a.n > 0 ? (a.n + kThreads - 1) / kThreads : 1;
+  k_g2p<<<blocks, kThreads, 0, s>>>(a);
+}
+
+}  // namespace mpmcr

@@ -1,0 +1,77 @@
+// grid.cu -- active-block compaction and the grid update of the free-motion
+// solve (Sec. V-A op (2): v* = p / m + h g on every node with mass), with the
+// domain walls held at zero velocity.
+//
+// Only 4^3 blocks marked by P2G are swept. The update also clears the P2G
+// accumulator it consumed, so the accumulator is all zero between substeps
+// and no separate clearing pass is needed.
+#include "kernels.h"
+
+namespace mpmcr {
+
+namespace {
+
+__global__ void k_compact(uint8_t* __restrict__ mark, int n_blocks, int* __restrict__ act,
+                          int* __restrict__ n_act) {
+  int lane = threadIdx.x & 31;
+  for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < n_blocks;
+       base += gridDim.x * blockDim.x) {
+    int b = base + lane;
+    bool on = b < n_blocks && mark[b] != 0;
+    unsigned m = __ballot_sync(0xffffffffu, on);
+    if (m == 0u) continue;
+    int slot0 = 0;
+    if (lane == 0) slot0 = atomicAdd(n_act, __popc(m));
+    slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+    if (on) {
+      act[slot0 + __popc(m & ((1u << lane) - 1u))] = b;
+      mark[b] = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_grid_update(GridDev g, GridArrays G, float h,
+                                                     DevStats* stats) {
+  const int n_act = *G.n_act;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicMax(&stats->active_blocks_max, n_act);
+    stats->last_active = n_act;
+  }
+  const long long total = (long long)n_act * kBlockNodes;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int blk = G.act[t >> 6];
+    const int cell = (int)(t & 63);
+    const int node = blk * kBlockNodes + cell;
+    const float4 mp = G.mp[node];
+    float4 vs = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
+    const int i = bx * 4 + (cell & 3), j = by * 4 + ((cell >> 2) & 3), k = bz * 4 + (cell >> 4);
+    const bool wall = i < g.bc || j < g.bc || k < g.bc || i >= g.rx - g.bc ||
+                      j >= g.ry - g.bc || k >= g.rz - g.bc;
+    if (mp.x > 0.0f) {
+      const float inv_m = 1.0f / mp.x;
+      vs.x = wall ? 0.0f : mp.y * inv_m + h * g.gx;
+      vs.y = wall ? 0.0f : mp.z * inv_m + h * g.gy;
+      vs.z = wall ? 0.0f : mp.w * inv_m + h * g.gz;
+      vs.w = mp.x;
+    }
+    G.mp[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+    G.vs[node] = vs;
+    // .w flags a Dirichlet node for the contact solve
+    G.v[node] = make_float4(vs.x, vs.y, vs.z, wall ? 1.f : 0.f);
+  }
+}
+
+}  // namespace
+
+void launch_grid(const GridDev& g, const GridArrays& G, float h, int num_sms, DevStats* stats,
+                 cudaStream_t s) {
+  int n_blocks = g.nbx * g.nby * g.nbz;
+  int cb = (n_blocks + 255) / 256;
+  cb = cb > num_sms * 8 ? num_sms * 8 : cb;
+  k_compact<<<cb, 256, 0, s>>>(G.mark, n_blocks, G.act, G.n_act);
+  k_grid_update<<<num_sms * 8, 256, 0, s>>>(g, G, h, stats);
+}
+
+}  // namespace mpmcr

@@ -1,0 +1,105 @@
+// kernels.h -- host-side launchers of the substep kernels (internal to the
+// library; the public boundary is include/mpmcr.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mpmcr {
+
+// Statistics written by the device, read back by mpm_step.
+struct DevStats {
+  int iters_total;
+  int iters_max;
+  int ls_evals_total;
+  int contacts_max;
+  int active_blocks_max;
+  int substeps;
+  unsigned long long contacts_total;
+  float residual_max;
+  int p2g_global_chunks;
+  int last_contacts;     // contacts of the last substep
+  int last_active;       // active blocks of the last substep
+  int pad[2];
+};
+
+// Scratch of the radix sort.
+struct SortBuffers {
+  uint32_t* keys[2];
+  uint32_t* vals[2];
+  uint32_t* hist;     // 256 * n_tiles
+  uint32_t* partial;  // scan partials
+  int hist_cap;
+};
+
+int sort_hist_len(int n);
+// ---- sort.cu: block keys, LSD radix sort (8-bit digits), permutation ----
+void launch_sort(const GridDev& g, const Particles& src, const Particles& dst, int n,
+                 SortBuffers& sb, cudaStream_t s);
+// gather particles of `src` into id order (out[pid] = state) for mem reads
+void launch_to_id_order(const Particles& P, int n, float* out_x, float* out_v, float* out_C,
+                        float* out_F, cudaStream_t s);
+void launch_from_id_order(const Particles& P, int n, const float* in_x, const float* in_v,
+                          const float* in_C, const float* in_F, cudaStream_t s);
+
+// ---- p2g.cu: particle-to-grid with shared-memory tiles + contact registration ----
+struct P2GArgs {
+  GridDev g;
+  Particles P;
+  int n;
+  const DevGroup* groups;
+  const DevBody* bodies;
+  int nb;
+  float h;
+  GridArrays G;
+  Contacts C;
+  uint32_t* status;
+  DevStats* stats;
+};
+void launch_p2g(const P2GArgs& a, int chunk, cudaStream_t s);
+
+// ---- grid.cu: active-block compaction and grid update ----
+void launch_grid(const GridDev& g, const GridArrays& G, float h, int num_sms, DevStats* stats,
+                 cudaStream_t s);
+
+// ---- solve.cu: quasi-Newton contact solve (Alg. 1) in one cooperative launch ----
+struct SolveArgs {
+  GridDev g;
+  GridArrays G;
+  Contacts C;
+  const DevBody* bodies;
+  int nb;
+  float h;
+  float eps_s;
+  float ls_rel_tol;
+  int ls_max_iters;
+  double eps_r, eps_a;
+  int max_iters;
+  double* red;        // reduction ring [4][8]
+  unsigned* bar;      // grid barrier words [2]
+  uint32_t* status;
+  DevStats* stats;
+  double* impulses;   // [6 nb]
+};
+cudaError_t launch_solve(const SolveArgs& a, int grid_blocks, cudaStream_t s);
+int solve_block_size();
+const void* solve_kernel_ptr();
+
+// ---- g2p.cu: grid-to-particle with the constitutive update ----
+struct G2PArgs {
+  GridDev g;
+  Particles P;
+  int n;
+  const DevGroup* groups;
+  GridArrays G;
+  Contacts C;
+  float h;
+  unsigned* bar;     // solve barrier, reset here
+  double* red;       // solve reduction ring, reset here
+  DevStats* stats;
+};
+void launch_g2p(const G2PArgs& a, cudaStream_t s);
+
+}  // namespace mpmcr

@@ -1,0 +1,255 @@
+// p2g.cu -- particle-to-grid transfer of the free-motion solve (Eq. (6),
+// MLS-MPM with quadratic B-splines) fused with contact registration
+// (Sec. V-B: one contact point per particle inside a rigid geometry, at the
+// start of the substep).
+//
+// GB300 layout: each thread block takes a contiguous chunk of block-sorted
+// particles, finds the bounding box of their stencils and accumulates mass and
+// momentum into a shared-memory tile of that box (shared-memory atomics play
+// the role of the paper's warp-level pre-reduction, Sec. V-A). The tile is
+// then flushed with one 16-byte vector reduction (red.global.add.v4.f32) per
+// touched node. A chunk whose box does not fit the tile falls back to direct
+// vector reductions. Particle planes are read with coalesced 4-byte loads.
+#include "kernels.h"
+
+namespace mpmcr {
+
+namespace {
+
+constexpr int kTileCap = 2048;  // nodes in the shared tile (32 KB)
+constexpr int kThreads = 256;
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
+  __shared__ float t_m[kTileCap], t_px[kTileCap], t_py[kTileCap], t_pz[kTileCap];
+  __shared__ DevBody s_body[kMaxBodies];
+  __shared__ int s_min[3], s_max[3];
+  __shared__ unsigned s_cand;
+  const GridDev& g = a.g;
+  const int tid = threadIdx.x;
+  const int first = blockIdx.x * kThreads * ITEMS;
+
+  if (tid < 3) { s_min[tid] = 0x7fffffff; s_max[tid] = -0x7fffffff; }
+  for (int i = tid; i < a.nb * (int)(sizeof(DevBody) / 4); i += kThreads)
+    reinterpret_cast<float*>(s_body)[i] = reinterpret_cast<const float*>(a.bodies)[i];
+  __syncthreads();
+
+  // stencils of this thread's particles and the chunk's bounding box
+  Stencil st[ITEMS];
+  bool valid[ITEMS];
+  int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+#pragma unroll
+  for (int it = 0; it < ITEMS; ++it) {
+    int i = first + it * kThreads + tid;
+    valid[it] = i < a.n;
+    if (valid[it]) {
+      stencil(g, a.P.x[0][i], a.P.x[1][i], a.P.x[2][i], st[it]);
+      if (!stencil_inside(g, st[it])) {
+        valid[it] = false;
+        atomicOr(a.status, kStOutOfDomain);
+      }
+    }
+    if (valid[it]) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = min(lo[c], st[it].base[c]);
+        hi[c] = max(hi[c], st[it].base[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[c] = min(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+      hi[c] = max(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+    }
+  }
+  if ((tid & 31) == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { atomicMin(&s_min[c], lo[c]); atomicMax(&s_max[c], hi[c]); }
+  }
+  __syncthreads();
+  const int b0 = s_min[0], b1 = s_min[1], b2 = s_min[2];
+  const bool any = s_max[0] >= b0;
+  const int ex = any ? s_max[0] - b0 + 3 : 0, ey = any ? s_max[1] - b1 + 3 : 0,
+            ez = any ? s_max[2] - b2 + 3 : 0;
+  const int tile_n = ex * ey * ez;
+  const bool use_tile = any && tile_n <= kTileCap;
+  if (use_tile) {
+    for (int t = tid; t < tile_n; t += kThreads) { t_m[t] = 0.f; t_px[t] = 0.f; t_py[t] = 0.f; t_pz[t] = 0.f; }
+  } else if (any && tid == 0) {
+    atomicAdd(&a.stats->p2g_global_chunks, 1);
+  }
+  // bodies that may hold a particle of this chunk: the signed distance is
+  // 1-Lipschitz, so a body whose distance at the box centre exceeds the half
+  // diagonal cannot contain any point of the box
+  if (tid < 32) {
+    bool cand = false;
+    if (any && tid < a.nb) {
+      float c0 = g.ox + g.dx * (0.5f * (b0 + s_max[0]) + 1.0f);
+      float c1 = g.oy + g.dx * (0.5f * (b1 + s_max[1]) + 1.0f);
+      float c2 = g.oz + g.dx * (0.5f * (b2 + s_max[2]) + 1.0f);
+      float h0 = 0.5f * g.dx * (s_max[0] - b0 + 1), h1 = 0.5f * g.dx * (s_max[1] - b1 + 1),
+            h2 = 0.5f * g.dx * (s_max[2] - b2 + 1);
+      float nrm[3];
+      float phi = body_sdf(s_body[tid], c0, c1, c2, nrm);
+      cand = phi <= sqrtf(h0 * h0 + h1 * h1 + h2 * h2) * 1.001f + 1e-6f;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, cand);
+    if (tid == 0) s_cand = m;
+  }
+  __syncthreads();
+  const unsigned cand = s_cand;
+  const float h = a.h;
+  const float dinv = 4.0f * g.inv_dx * g.inv_dx;
+
+#pragma unroll
+  for (int it = 0; it < ITEMS; ++it) {
+    const int i = first + it * kThreads + tid;
+    if (valid[it]) {
+      const Stencil& s = st[it];
+      const DevGroup gr = a.groups[a.P.grp[i]];
+      float vp[3] = {a.P.v[0][i], a.P.v[1][i], a.P.v[2][i]};
+      float F[9], A[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) F[c] = a.P.F[c][i];
+      float tau[6];
+      kirchhoff(gr, F, tau);
+      const float sc = h * dinv * gr.vol;
+      const float tf[9] = {tau[0], tau[3], tau[4], tau[3], tau[1], tau[5], tau[4], tau[5], tau[2]};
+#pragma unroll
+      for (int c = 0; c < 9; ++c) A[c] = gr.mass * a.P.C[c][i] - sc * tf[c];
+      const float mvx = gr.mass * vp[0], mvy = gr.mass * vp[1], mvz = gr.mass * vp[2];
+      if (use_tile) {
+        const int l0 = s.base[0] - b0, l1 = s.base[1] - b1, l2 = s.base[2] - b2;
+#pragma unroll
+        for (int cz = 0; cz < 3; ++cz) {
+          const float dz = (cz - s.fx[2]) * g.dx;
+#pragma unroll
+          for (int cy = 0; cy < 3; ++cy) {
+            const float dy = (cy - s.fx[1]) * g.dx;
+            const float wyz = s.w[1][cy] * s.w[2][cz];
+            const int row = ((l2 + cz) * ey + (l1 + cy)) * ex + l0;
+#pragma unroll
+            for (int cx = 0; cx < 3; ++cx) {
+              const float dxp = (cx - s.fx[0]) * g.dx;
+              const float w = s.w[0][cx] * wyz;
+              const int t = row + cx;
+              atomicAdd(&t_m[t], w * gr.mass);
+              atomicAdd(&t_px[t], w * (mvx + A[0] * dxp + A[1] * dy + A[2] * dz));
+              atomicAdd(&t_py[t], w * (mvy + A[3] * dxp + A[4] * dy + A[5] * dz));
+              atomicAdd(&t_pz[t], w * (mvz + A[6] * dxp + A[7] * dy + A[8] * dz));
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int cz = 0; cz < 3; ++cz) {
+          const float dz = (cz - s.fx[2]) * g.dx;
+#pragma unroll
+          for (int cy = 0; cy < 3; ++cy) {
+            const float dy = (cy - s.fx[1]) * g.dx;
+            const float wyz = s.w[1][cy] * s.w[2][cz];
+#pragma unroll
+            for (int cx = 0; cx < 3; ++cx) {
+              const float dxp = (cx - s.fx[0]) * g.dx;
+              const float w = s.w[0][cx] * wyz;
+              const int node = node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz);
+              red_add_v4(a.G.mp + node, w * gr.mass, w * (mvx + A[0] * dxp + A[1] * dy + A[2] * dz),
+                         w * (mvy + A[3] * dxp + A[4] * dy + A[5] * dz),
+                         w * (mvz + A[6] * dxp + A[7] * dy + A[8] * dz));
+            }
+          }
+        }
+        // mark the (up to 8) blocks of this stencil
+#pragma unroll
+        for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+          for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+            for (int cx = 0; cx < 2; ++cx) {
+              int bi = (s.base[0] + 2 * cx) >> 2, bj = (s.base[1] + 2 * cy) >> 2,
+                  bk = (s.base[2] + 2 * cz) >> 2;
+              a.G.mark[(bk * g.nby + bj) * g.nbx + bi] = 1;
+            }
+      }
+    }
+    // contact registration: warp-aggregated append, one contact per
+    // (particle, body) pair with the particle strictly inside
+    if (cand) {
+      float xp[3] = {0.f, 0.f, 0.f}, vp[3] = {0.f, 0.f, 0.f};
+      if (valid[it]) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { xp[c] = a.P.x[c][i]; vp[c] = a.P.v[c][i]; }
+      }
+      for (int b = 0; b < a.nb; ++b) {
+        if (!((cand >> b) & 1u)) continue;
+        float nrm[3] = {0.f, 0.f, 1.f};
+        float phi = 1.0f;
+        if (valid[it]) phi = body_sdf(s_body[b], xp[0], xp[1], xp[2], nrm);
+        const bool hit = valid[it] && phi < 0.0f;
+        const unsigned mask = __ballot_sync(0xffffffffu, hit);
+        if (mask == 0u) continue;
+        const int lane = tid & 31;
+        const int leader = __ffs(mask) - 1;
+        int slot0 = 0;
+        if (lane == leader) slot0 = atomicAdd(a.C.count, __popc(mask));
+        slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+        if (hit) {
+          const int slot = slot0 + __popc(mask & ((1u << lane) - 1u));
+          if (slot < a.C.cap) {
+            const DevBody& bd = s_body[b];
+            float vr[3];
+            body_velocity(bd, xp[0], xp[1], xp[2], vr);
+            const float vn0 = nrm[0] * (vp[0] - vr[0]) + nrm[1] * (vp[1] - vr[1]) + nrm[2] * (vp[2] - vr[2]);
+            const float phi0 = -phi;
+            const float n0 = normal_impulse(phi0, bd.k, bd.d, h, vn0);
+            a.C.xp[slot] = make_float4(xp[0], xp[1], xp[2], phi0);
+            a.C.nrm[slot] = make_float4(nrm[0], nrm[1], nrm[2], n0);
+            a.C.bias[slot] = make_float4(-vr[0], -vr[1], -vr[2], 0.f);
+            a.C.id[slot] = make_int2((int)a.P.pid[i], b);
+          } else {
+            atomicOr(a.status, kStCapacity);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (use_tile) {
+    // flush: one vector reduction per touched node
+    for (int t = tid; t < tile_n; t += kThreads) {
+      float m = t_m[t];
+      if (m != 0.0f || t_px[t] != 0.0f || t_py[t] != 0.0f || t_pz[t] != 0.0f) {
+        int lx = t % ex, r = t / ex, ly = r % ey, lz = r / ey;
+        int node = node_index(g, b0 + lx, b1 + ly, b2 + lz);
+        red_add_v4(a.G.mp + node, m, t_px[t], t_py[t], t_pz[t]);
+      }
+    }
+    // mark the blocks overlapped by the tile
+    int bx0 = b0 >> 2, by0 = b1 >> 2, bz0 = b2 >> 2;
+    int bnx = ((b0 + ex - 1) >> 2) - bx0 + 1, bny = ((b1 + ey - 1) >> 2) - by0 + 1,
+        bnz = ((b2 + ez - 1) >> 2) - bz0 + 1;
+    for (int t = tid; t < bnx * bny * bnz; t += kThreads) {
+      int qx = t % bnx, r = t / bnx, qy = r % bny, qz = r / bny;
+      a.G.mark[((bz0 + qz) * g.nby + (by0 + qy)) * g.nbx + (bx0 + qx)] = 1;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_p2g(const P2GArgs& a, int chunk, cudaStream_t s) {
+  if (a.n <= 0) return;
+  int items = chunk / kThreads;
+  if (items <= 1) {
+    k_p2g<1><<<(a.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
+  } else if (items == 2) {
+    k_p2g<2><<<(a.n + 2 * kThreads - 1) / (2 * kThreads), kThreads, 0, s>>>(a);
+  } else {
+    k_p2g<4><<<(a.n + 4 * kThreads - 1) / (4 * kThreads), kThreads, 0, s>>>(a);
+  }
+}
+
+}  // namespace mpmcr

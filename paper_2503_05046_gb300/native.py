@@ -1,0 +1,383 @@
+"""Thin Python binding of the C ABI in ``include/mpmcr.h`` (``libmpmcr.so``).
+
+Argument marshalling only: every step of the substep runs in the library's
+CUDA kernels. Functions carry the C names (``mpm_create``, ``mpm_step``, ...);
+``Sim`` bundles them for convenience. Device buffers may be passed as torch
+CUDA tensors (``mem_kind=MEM_DEVICE``); host buffers as numpy arrays.
+
+There is no fallback: if the library is missing or fails to load, importing
+this module raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import scenes
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpmcr.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_CAPACITY, ERR_NOT_CONVERGED, ERR_OUT_OF_DOMAIN, \
+    ERR_NAN, ERR_STATE, ERR_TIMEOUT, ERR_LINE_SEARCH = range(11)
+STATUS_NAMES = ["MPM_OK", "MPM_ERR_INVALID_ARG", "MPM_ERR_CUDA", "MPM_ERR_OOM", "MPM_ERR_CAPACITY",
+                "MPM_ERR_NOT_CONVERGED", "MPM_ERR_OUT_OF_DOMAIN", "MPM_ERR_NAN", "MPM_ERR_STATE",
+                "MPM_ERR_TIMEOUT", "MPM_ERR_LINE_SEARCH"]
+MEM_HOST, MEM_DEVICE = 0, 1
+OPT_PROFILE, OPT_SORT_EVERY, OPT_P2G_CHUNK = 1, 2, 3
+PHASES = ["sort", "p2g", "grid", "solve", "g2p"]
+
+
+class GridSpec(C.Structure):
+    _fields_ = [("dx", C.c_double), ("res", C.c_int32 * 3), ("origin", C.c_double * 3),
+                ("gravity", C.c_double * 3), ("bc_layers", C.c_int32),
+                ("max_particles", C.c_int64), ("max_contacts", C.c_int64)]
+
+
+class Material(C.Structure):
+    _fields_ = [("model", C.c_int32), ("E", C.c_float), ("nu", C.c_float), ("rho", C.c_float),
+                ("friction_angle_deg", C.c_float)]
+
+
+class RigidBody(C.Structure):
+    _fields_ = [("shape", C.c_int32), ("params", C.c_float * 4), ("R", C.c_float * 9),
+                ("p", C.c_float * 3), ("omega", C.c_float * 3), ("v", C.c_float * 3),
+                ("mu", C.c_float), ("k", C.c_float), ("d", C.c_float), ("kinematic", C.c_int32)]
+
+
+class SolverParams(C.Structure):
+    _fields_ = [("eps_r", C.c_double), ("eps_a", C.c_double), ("max_iters", C.c_int32),
+                ("eps_s", C.c_float), ("ls_rel_tol", C.c_float), ("ls_max_iters", C.c_int32)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("substeps", C.c_int32), ("iters_total", C.c_int32), ("iters_max", C.c_int32),
+                ("ls_evals_total", C.c_int32), ("contacts_max", C.c_int32),
+                ("active_blocks_max", C.c_int32), ("contacts_total", C.c_int64),
+                ("residual_max", C.c_double), ("status_bits", C.c_int32),
+                ("p2g_global_chunks", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_vp = C.c_void_p
+_fp = C.POINTER(C.c_float)
+_dp = C.POINTER(C.c_double)
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+
+# name -> (argtypes) ; every entry point returns mpm_status except mpm_last_error
+SIGNATURES = {
+    "mpm_create": [C.POINTER(GridSpec), _vp, C.POINTER(_vp)],
+    "mpm_destroy": [_vp],
+    "mpm_last_error": [_vp],
+    "mpm_add_particles": [_vp, C.c_int64, _vp, _vp, C.c_float, C.POINTER(Material), C.c_int32,
+                          _i64p],
+    "mpm_num_particles": [_vp, _i64p],
+    "mpm_set_particles": [_vp, _vp, _vp, _vp, _vp, C.c_int32],
+    "mpm_get_particles": [_vp, _vp, _vp, _vp, _vp, C.c_int32],
+    "mpm_set_rigid_bodies": [_vp, C.c_int32, C.POINTER(RigidBody)],
+    "mpm_get_rigid_bodies": [_vp, C.c_int32, C.POINTER(RigidBody)],
+    "mpm_step": [_vp, C.c_double, C.c_int32, C.POINTER(SolverParams), C.POINTER(StepStats)],
+    "mpm_get_rigid_impulses": [_vp, _dp, C.c_int32],
+    "mpm_get_grid": [_vp, C.c_int64, _i64p, _i32p, _fp, _fp, _fp],
+    "mpm_get_contacts": [_vp, C.c_int64, _i64p, _i32p, _i32p, _fp, _fp, _fp],
+    "mpm_synchronize": [_vp],
+    "mpm_set_option": [_vp, C.c_int32, C.c_int64],
+    "mpm_get_phase_times": [_vp, _dp, _i64p, C.c_int32],
+}
+
+
+def load(path=LIB_PATH):
+    """Load libmpmcr.so and declare the C signatures. Raises if it is missing."""
+    if not os.path.exists(path):
+        raise ImportError("libmpmcr.so not found at %s: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    L = C.CDLL(path)
+    for name, args in SIGNATURES.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_char_p if name == "mpm_last_error" else C.c_int
+    return L
+
+
+lib = load()
+
+
+class MpmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[code] if 0 <= code < len(STATUS_NAMES) else code,
+                                     msg))
+        self.code = code
+
+
+def _check(ctx, code):
+    if code != OK:
+        msg = lib.mpm_last_error(ctx)
+        raise MpmError(code, msg.decode() if msg else "")
+    return code
+
+
+# ---------------------------------------------------------------- C-named calls
+
+def mpm_create(spec, stream=None):
+    out = _vp()
+    _check(None, lib.mpm_create(C.byref(spec), stream, C.byref(out)))
+    return out
+
+
+def mpm_destroy(ctx):
+    return lib.mpm_destroy(ctx)
+
+
+def mpm_last_error(ctx):
+    return lib.mpm_last_error(ctx).decode()
+
+
+def _ptr(a):
+    """(pointer, mem_kind, keepalive) for a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None, None, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        return a.ctypes.data, MEM_HOST, a
+    # torch tensor
+    if a.dtype.is_floating_point and a.element_size() != 4:
+        raise TypeError("float32 tensors required")
+    if not a.is_contiguous():
+        raise ValueError("contiguous tensors required")
+    return a.data_ptr(), (MEM_DEVICE if a.is_cuda else MEM_HOST), a
+
+
+def mpm_add_particles(ctx, x, v, volume, material):
+    n = len(x)
+    px, kx, kx_keep = _ptr(x)
+    pv, kv, kv_keep = _ptr(v)
+    if kx != kv:
+        raise ValueError("x and v must live in the same memory")
+    first = C.c_int64()
+    _check(ctx, lib.mpm_add_particles(ctx, n, px, pv, float(volume), C.byref(material), kx,
+                                      C.byref(first)))
+    return first.value
+
+
+def mpm_num_particles(ctx):
+    n = C.c_int64()
+    _check(ctx, lib.mpm_num_particles(ctx, C.byref(n)))
+    return n.value
+
+
+def mpm_set_particles(ctx, x=None, v=None, Cm=None, F=None):
+    ptrs = [_ptr(a) for a in (x, v, Cm, F)]
+    kinds = {k for _, k, _ in ptrs if k is not None}
+    if len(kinds) > 1:
+        raise ValueError("all buffers must live in the same memory")
+    kind = kinds.pop() if kinds else MEM_HOST
+    _check(ctx, lib.mpm_set_particles(ctx, *[p for p, _, _ in ptrs], kind))
+
+
+def mpm_get_particles(ctx, x=None, v=None, Cm=None, F=None, mem_kind=MEM_HOST):
+    ptrs = [(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()) if a is not None else None
+            for a in (x, v, Cm, F)]
+    _check(ctx, lib.mpm_get_particles(ctx, *ptrs, mem_kind))
+
+
+def mpm_set_rigid_bodies(ctx, bodies):
+    arr = (RigidBody * max(len(bodies), 1))()
+    for i, b in enumerate(bodies):
+        arr[i] = b if isinstance(b, RigidBody) else make_body(b)
+    _check(ctx, lib.mpm_set_rigid_bodies(ctx, len(bodies), arr))
+
+
+def mpm_get_rigid_bodies(ctx, n):
+    arr = (RigidBody * max(n, 1))()
+    _check(ctx, lib.mpm_get_rigid_bodies(ctx, n, arr))
+    return [arr[i] for i in range(n)]
+
+
+def mpm_step(ctx, h, n_substeps, solver=None, want_stats=True):
+    st = StepStats()
+    code = lib.mpm_step(ctx, float(h), int(n_substeps), C.byref(solver) if solver is not None else None,
+                        C.byref(st) if want_stats else None)
+    return code, (st if want_stats else None)
+
+
+def mpm_get_rigid_impulses(ctx, n_bodies, reset=False):
+    out = np.zeros(6 * max(n_bodies, 1))
+    _check(ctx, lib.mpm_get_rigid_impulses(ctx, out.ctypes.data_as(_dp), int(reset)))
+    return out[:6 * n_bodies].reshape(n_bodies, 6)
+
+
+def mpm_get_grid(ctx):
+    count = C.c_int64()
+    _check(ctx, lib.mpm_get_grid(ctx, 0, C.byref(count), None, None, None, None))
+    n = count.value
+    ids = np.zeros(max(n, 1), np.int32)
+    m = np.zeros(max(n, 1), np.float32)
+    vs = np.zeros((max(n, 1), 3), np.float32)
+    v = np.zeros((max(n, 1), 3), np.float32)
+    _check(ctx, lib.mpm_get_grid(ctx, n, C.byref(count), ids.ctypes.data_as(_i32p),
+                                 m.ctypes.data_as(_fp), vs.ctypes.data_as(_fp), v.ctypes.data_as(_fp)))
+    n = min(n, count.value)
+    order = np.argsort(ids[:n], kind="stable")
+    return ids[:n][order], m[:n][order], vs[:n][order], v[:n][order]
+
+
+def mpm_get_contacts(ctx):
+    count = C.c_int64()
+    _check(ctx, lib.mpm_get_contacts(ctx, 0, C.byref(count), None, None, None, None, None))
+    n = count.value
+    p = np.zeros(max(n, 1), np.int32)
+    b = np.zeros(max(n, 1), np.int32)
+    g = np.zeros((max(n, 1), 3), np.float32)
+    phi = np.zeros(max(n, 1), np.float32)
+    n0 = np.zeros(max(n, 1), np.float32)
+    _check(ctx, lib.mpm_get_contacts(ctx, n, C.byref(count), p.ctypes.data_as(_i32p),
+                                     b.ctypes.data_as(_i32p), g.ctypes.data_as(_fp),
+                                     phi.ctypes.data_as(_fp), n0.ctypes.data_as(_fp)))
+    return p[:n], b[:n], g[:n], phi[:n], n0[:n]
+
+
+def mpm_synchronize(ctx):
+    return lib.mpm_synchronize(ctx)
+
+
+def mpm_set_option(ctx, option, value):
+    _check(ctx, lib.mpm_set_option(ctx, int(option), int(value)))
+
+
+def mpm_get_phase_times(ctx, reset=False):
+    ms = np.zeros(len(PHASES))
+    n = np.zeros(len(PHASES), np.int64)
+    _check(ctx, lib.mpm_get_phase_times(ctx, ms.ctypes.data_as(_dp), n.ctypes.data_as(_i64p),
+                                        int(reset)))
+    return dict(zip(PHASES, ms)), dict(zip(PHASES, n))
+
+
+# ---------------------------------------------------------------- conversions
+
+def grid_spec(grid, max_particles, max_contacts):
+    s = GridSpec()
+    s.dx = float(grid["dx"])
+    for i in range(3):
+        s.res[i] = int(grid["res"][i])
+        s.origin[i] = float(grid["origin"][i])
+        s.gravity[i] = float(grid.get("gravity", (0.0, 0.0, -9.81))[i])
+    s.bc_layers = int(grid.get("bc_layers", 3))
+    s.max_particles = int(max_particles)
+    s.max_contacts = int(max_contacts)
+    return s
+
+
+def make_material(m):
+    return Material(int(m["model"]), float(m["E"]), float(m["nu"]), float(m["rho"]),
+                    float(m.get("friction_angle_deg", 0.0)))
+
+
+def make_body(b):
+    r = RigidBody()
+    r.shape = int(b["shape"])
+    prm = np.asarray(b.get("params", [0, 0, 0, 0]), np.float32).ravel()
+    for i in range(4):
+        r.params[i] = float(prm[i]) if i < len(prm) else 0.0
+    R = np.asarray(b.get("R", np.eye(3)), np.float32).reshape(9)
+    for i in range(9):
+        r.R[i] = float(R[i])
+    for key in ("p", "omega", "v"):
+        arr = getattr(r, key)
+        val = np.asarray(b.get(key, [0, 0, 0]), np.float32).reshape(3)
+        for i in range(3):
+            arr[i] = float(val[i])
+    r.mu = float(b.get("mu", 0.0))
+    r.k = float(b.get("k", scenes.CONTACT_K))
+    r.d = float(b.get("d", scenes.CONTACT_D))
+    r.kinematic = int(b.get("kinematic", 0))
+    return r
+
+
+def body_dict(r):
+    return {"shape": r.shape, "params": np.array(r.params[:], np.float64),
+            "R": np.array(r.R[:], np.float64).reshape(3, 3), "p": np.array(r.p[:], np.float64),
+            "omega": np.array(r.omega[:], np.float64), "v": np.array(r.v[:], np.float64),
+            "mu": r.mu, "k": r.k, "d": r.d, "kinematic": r.kinematic}
+
+
+def solver_params(eps_r=5e-2, eps_a=np.finfo(np.float64).eps, max_iters=1000, eps_s=scenes.EPS_S,
+                  ls_rel_tol=1e-5, ls_max_iters=50):
+    return SolverParams(eps_r, eps_a, max_iters, eps_s, ls_rel_tol, ls_max_iters)
+
+
+class Sim:
+    """One simulation context on the current CUDA device."""
+
+    def __init__(self, scene, max_particles=None, max_contacts=None, stream=None):
+        n = scenes.n_particles(scene)
+        self.scene = scene
+        self.max_particles = int(max_particles or max(n, 1))
+        self.max_contacts = int(max_contacts or max(4 * n, 1024))
+        spec = grid_spec(scene["grid"], self.max_particles, self.max_contacts)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except Exception:  # torch is optional for the binding
+                stream = None
+        self.ctx = mpm_create(spec, stream)
+        for g in scene["groups"]:
+            mpm_add_particles(self.ctx, np.asarray(g["x"], np.float32), np.asarray(g["v"], np.float32),
+                              g["vol"], make_material(g["material"]))
+        self.n_bodies = len(scene["bodies"])
+        mpm_set_rigid_bodies(self.ctx, scene["bodies"])
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            mpm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n(self):
+        return mpm_num_particles(self.ctx)
+
+    def step(self, h=None, n_substeps=None, solver=None, stats=True, check=True):
+        h = self.scene["h"] if h is None else h
+        n_substeps = self.scene["substeps"] if n_substeps is None else n_substeps
+        code, st = mpm_step(self.ctx, h, n_substeps, solver, want_stats=stats)
+        if check:
+            _check(self.ctx, code)
+        return (code, st) if not check else st
+
+    def get_particles(self):
+        n = self.n
+        x = np.zeros((n, 3), np.float32)
+        v = np.zeros((n, 3), np.float32)
+        Cm = np.zeros((n, 3, 3), np.float32)
+        F = np.zeros((n, 3, 3), np.float32)
+        mpm_get_particles(self.ctx, x, v, Cm, F)
+        return {"x": x, "v": v, "C": Cm, "F": F}
+
+    def set_particles(self, x=None, v=None, Cm=None, F=None):
+        mpm_set_particles(self.ctx, x, v, Cm, F)
+
+    def set_bodies(self, bodies):
+        self.n_bodies = len(bodies)
+        mpm_set_rigid_bodies(self.ctx, bodies)
+
+    def bodies(self):
+        return [body_dict(b) for b in mpm_get_rigid_bodies(self.ctx, self.n_bodies)]
+
+    def impulses(self, reset=False):
+        return mpm_get_rigid_impulses(self.ctx, self.n_bodies, reset)
+
+    def grid(self):
+        return mpm_get_grid(self.ctx)
+
+    def contacts(self):
+        return mpm_get_contacts(self.ctx)

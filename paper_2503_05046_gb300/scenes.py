@@ -180,3 +180,19 @@ def incline_block(theta_deg=30.0, mu=0.3, n_side=6, dx=0.01, E=1.0e6, seed=SEED_
             "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
     return {"name": "incline", "grid": grid, "groups": [g],
             "bodies": [body(HALFSPACE, R=R, mu=mu)], "h": h, "substeps": 10}
+
+
+def cube_contact(n_side=10, seed=SEED_BASE + 31, v0=(0.05, 0.0, -0.05), penetration=1e-4,
+                 sphere_overlap=2e-4, E=1.0e5, h=1e-4):
+    """The cube-drop workload caught at touch-down: the cube's bottom particle
+    layer sits `penetration` into the ground and the kinematic sphere (moving
+    along -x) overlaps its side by `sphere_overlap`; a small, contact-rich case
+    for per-substep parity."""
+    dx = 0.01
+    spacing = dx / 2.0
+    side = n_side * spacing
+    sc = cube_drop(seed=seed, n_side=n_side, drop_height=-spacing / 2.0 - penetration, v0=v0,
+                   sphere_x=(n_side - 1) * spacing / 2.0 + 0.05 - sphere_overlap, h=h)
+    sc["groups"][0]["material"] = elastic(E, 0.3, 1000.0)
+    sc["name"] = "cube_contact_%d" % (n_side ** 3)
+    return sc

@@ -1,0 +1,77 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point include/mpmcr.h declares; argument validation that happens before
+any device work is checked here too (no compute calls without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mpmcr.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(mpm_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2503_05046_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mpm_create", "mpm_add_particles", "mpm_set_rigid_bodies", "mpm_step",
+                     "mpm_get_particles", "mpm_get_rigid_impulses", "mpm_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), "libmpmcr.so does not export %s" % name
+
+
+def test_binding_covers_every_symbol():
+    from paper_2503_05046_gb300 import native
+    assert set(declared_functions()) <= set(native.SIGNATURES)
+
+
+def test_argument_validation_without_device(lib):
+    from paper_2503_05046_gb300 import native
+    out = C.c_void_p()
+    spec = native.GridSpec()
+    spec.dx = 0.01
+    spec.res[0], spec.res[1], spec.res[2] = 30, 32, 32  # not a multiple of 4
+    spec.max_particles = 10
+    spec.max_contacts = 10
+    assert native.lib.mpm_create(C.byref(spec), None, C.byref(out)) == native.ERR_INVALID_ARG
+    spec.res[0] = 32
+    spec.dx = -1.0
+    assert native.lib.mpm_create(C.byref(spec), None, C.byref(out)) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_create(None, None, C.byref(out)) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_num_particles(None, None) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_step(None, 1e-4, 1, None, None) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_destroy(None) == native.OK
+    assert native.lib.mpm_last_error(None) == b"invalid mpm context"
+
+
+def test_oracle_is_separate_from_the_cuda_library():
+    """The oracle shares no source with the CUDA path and neither includes the
+    other's headers."""
+    csrc = os.path.join(ROOT, "paper_2503_05046_gb300", "csrc")
+    for f in os.listdir(csrc):
+        text = open(os.path.join(csrc, f)).read()
+        assert "mpm_oracle" not in text and "orc_" not in text
+    otext = open(os.path.join(ROOT, "oracle", "mpm_oracle.c")).read()
+    assert "mpmcr.h" not in otext and "common.cuh" not in otext
+    for f in os.listdir(os.path.join(ROOT, "paper_2503_05046_gb300")):
+        if f.endswith(".py"):
+            text = open(os.path.join(ROOT, "paper_2503_05046_gb300", f)).read()
+            assert "import oracle" not in text and "from oracle" not in text
