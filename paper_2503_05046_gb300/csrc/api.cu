@@ -225,8 +225,8 @@ void fold_events(mpm_ctx* ctx) {
 
 void release(mpm_ctx* c) {
   void* ptrs[] = {c->pbuf[0], c->pbuf[1], c->pidbuf[0], c->pidbuf[1], c->grpbuf[0], c->grpbuf[1],
-                  c->groups_d, c->bodies_d, c->G.mp, c->G.vs, c->G.v, c->G.acc0, c->G.acc1,
-                  c->G.acc2, c->G.dv, c->G.mark, c->G.act, c->G.n_act, c->C.xp, c->C.nrm,
+                  c->groups_d, c->bodies_d, c->G.mp, c->G.vs, c->G.v, c->G.v2, c->G.vlo, c->G.vlo2, c->G.acc0, c->G.acc1,
+                  c->G.acc2, c->G.dv, c->G.mark, c->G.cflag, c->G.cnodes, c->G.n_cnodes, c->G.pstar2, c->G.act, c->G.n_act, c->C.xp, c->C.nrm,
                   c->C.bias, c->C.id, c->C.vc, c->C.dvc, c->C.gamma, c->C.count, c->red, c->bar,
                   c->status, c->stats, c->impulses, c->sb.keys[0], c->sb.keys[1], c->sb.vals[0],
                   c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage};
@@ -302,16 +302,25 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
   }
   const size_t nn = ctx->n_nodes;
   ok = ok && dalloc(&ctx->G.mp, nn) == cudaSuccess && dalloc(&ctx->G.vs, nn) == cudaSuccess &&
-       dalloc(&ctx->G.v, nn) == cudaSuccess && dalloc(&ctx->G.acc0, nn) == cudaSuccess &&
+       dalloc(&ctx->G.v, nn) == cudaSuccess && dalloc(&ctx->G.v2, nn) == cudaSuccess &&
+       dalloc(&ctx->G.vlo, nn) == cudaSuccess && dalloc(&ctx->G.vlo2, nn) == cudaSuccess &&
+       dalloc(&ctx->G.acc0, nn) == cudaSuccess &&
        dalloc(&ctx->G.acc1, nn) == cudaSuccess && dalloc(&ctx->G.acc2, nn) == cudaSuccess &&
        dalloc(&ctx->G.dv, nn) == cudaSuccess && dalloc(&ctx->G.mark, ctx->n_blocks) == cudaSuccess &&
+       dalloc(&ctx->G.cflag, nn) == cudaSuccess && dalloc(&ctx->G.n_cnodes, 1) == cudaSuccess &&
+       dalloc(&ctx->G.pstar2, 1) == cudaSuccess &&
        dalloc(&ctx->G.act, ctx->n_blocks) == cudaSuccess && dalloc(&ctx->G.n_act, 1) == cudaSuccess;
   ok = ok && dalloc(&ctx->C.xp, ccap) == cudaSuccess && dalloc(&ctx->C.nrm, ccap) == cudaSuccess &&
        dalloc(&ctx->C.bias, ccap) == cudaSuccess && dalloc(&ctx->C.id, ccap) == cudaSuccess &&
        dalloc(&ctx->C.vc, ccap) == cudaSuccess && dalloc(&ctx->C.dvc, ccap) == cudaSuccess &&
        dalloc(&ctx->C.gamma, ccap) == cudaSuccess && dalloc(&ctx->C.count, 1) == cudaSuccess;
   ctx->C.cap = (int)ccap;
-  ok = ok && dalloc(&ctx->red, 32) == cudaSuccess && dalloc(&ctx->bar, 2) == cudaSuccess &&
+  {
+    const size_t cn = (size_t)27 * (size_t)ccap < nn ? (size_t)27 * (size_t)ccap : nn;
+    ctx->G.cnodes_cap = (int)cn;
+    ok = ok && dalloc(&ctx->G.cnodes, cn) == cudaSuccess;
+  }
+  ok = ok && dalloc(&ctx->red, kRedDoubles) == cudaSuccess && dalloc(&ctx->bar, 2) == cudaSuccess &&
        dalloc(&ctx->status, 1) == cudaSuccess && dalloc(&ctx->stats, 1) == cudaSuccess &&
        dalloc(&ctx->impulses, 6 * kMaxBodies) == cudaSuccess &&
        dalloc(&ctx->bodies_d, kMaxBodies) == cudaSuccess;
@@ -333,7 +342,10 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
        cudaMemset(ctx->G.mark, 0, ctx->n_blocks) == cudaSuccess &&
        cudaMemset(ctx->G.n_act, 0, sizeof(int)) == cudaSuccess &&
        cudaMemset(ctx->C.count, 0, sizeof(int)) == cudaSuccess &&
-       cudaMemset(ctx->red, 0, 32 * sizeof(double)) == cudaSuccess &&
+       cudaMemset(ctx->red, 0, kRedDoubles * sizeof(double)) == cudaSuccess &&
+       cudaMemset(ctx->G.cflag, 0, nn * sizeof(int)) == cudaSuccess &&
+       cudaMemset(ctx->G.n_cnodes, 0, sizeof(int)) == cudaSuccess &&
+       cudaMemset(ctx->G.pstar2, 0, sizeof(double)) == cudaSuccess &&
        cudaMemset(ctx->bar, 0, 2 * sizeof(unsigned)) == cudaSuccess &&
        cudaMemset(ctx->status, 0, sizeof(uint32_t)) == cudaSuccess &&
        cudaMemset(ctx->stats, 0, sizeof(DevStats)) == cudaSuccess &&

@@ -73,12 +73,20 @@ struct Particles {
 struct GridArrays {
   float4* mp;      // (m, p): P2G accumulator, all zero outside a substep
   float4* vs;      // (v*, m)
-  float4* v;       // current grid velocity, .w unused
+  float4* v;       // grid velocity (.w flags a Dirichlet node); holds v^{k+1} after the solve
+  float4* v2;      // second buffer of the solve's iterate
+  float4* vlo;     // low parts of the iterate (double-float: v = v + vlo)
+  float4* vlo2;    // low parts of the second buffer
   float4* acc0;    // contact terms of the solve: (g_x, g_y, g_z, H_xx), zero outside use
   float4* acc1;    // (H_yy, H_zz, H_xy, H_xz)
   float* acc2;     // H_yz
   float4* dv;      // search direction
   uint8_t* mark;   // per block: touched by P2G this substep (zero outside)
+  int* cflag;      // per node: in the stencil of a contact this substep (zero outside)
+  int* cnodes;     // contact-node list of the substep's solve
+  int* n_cnodes;   // its length (device)
+  int cnodes_cap;
+  double* pstar2;  // sum over free nodes of m |v*|^2 (grid update), zero outside
   int* act;        // active block list
   int* n_act;      // its length (device)
 };
@@ -108,6 +116,40 @@ __device__ __forceinline__ void red_add_v4(float4* addr, float a, float b, float
 __device__ __forceinline__ void red_add_f32(float* addr, float a) {
   asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(a) : "memory");
 }
+
+// Error-free transformations for double-float (hi + lo) arithmetic in FP32.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += x, renormalised so that |lo| <= ulp(hi) / 2
+__device__ __forceinline__ void dd_add(float& hi, float& lo, float x) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  e += lo;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// compensated accumulator: S + E tracks a sum of FP32 products and terms
+struct CompSum {
+  float S = 0.f, E = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float s, e;
+    two_sum(S, x, s, e);
+    S = s;
+    E += e;
+  }
+  __device__ __forceinline__ void add_prod(float w, float x) {
+    const float p = w * x;
+    const float pe = fmaf(w, x, -p);
+    add(p);
+    E += pe;
+  }
+  __device__ __forceinline__ float value() const { return S + E; }
+};
 
 __device__ __forceinline__ int node_index(const GridDev& g, int i, int j, int k) {
   int b = ((k >> 2) * g.nby + (j >> 2)) * g.nbx + (i >> 2);
@@ -153,101 +195,41 @@ __device__ __forceinline__ bool stencil_inside(const GridDev& g, const Stencil& 
 }
 
 // --------------------------------------------------------------------------
-// 3x3 SVD, F = U diag(S) V^T with U, V proper rotations and S[2] < 0 iff
-// det F < 0. Cyclic Jacobi on the symmetric F^T F gives V; the columns of
-// F V are ordered by length and an orthogonal-triangular factorisation by
-// Givens rotations gives U and the singular values (McAdams et al. 2011,
-// "Computing the singular value decomposition of 3x3 matrices with minimal
-// branching", with exact rather than approximate rotations).
+// 3x3 singular value decomposition for the constitutive models,
+// F = U diag(s) V^T with U, V proper rotations and s[2] < 0 iff det F < 0,
+// computed so that s - 1 stays accurate when F is close to a rotation (the
+// usual state of an elastic body): with D = F - I (exact in FP32 for entries
+// near 1), M = F^T F - I = D + D^T + D^T D is formed without cancellation and
+// diagonalised by cyclic Jacobi rotations (V, eigenvalues l); then
+// s = sqrt(1 + l) and s - 1 = l / (1 + sqrt(1 + l)). U follows from F V by
+// Gram-Schmidt with u2 = u0 x u1. A plain SVD of F in FP32 loses s - 1 (and
+// with it the stress) to roundoff of order 1e-7 near F = I.
+
+struct Polar {
+  float U[9], V[9];
+  float s[3];    // signed singular values, ordered by decreasing magnitude
+  float sm1[3];  // s - 1
+};
 
 __device__ __forceinline__ void jacobi_pair(float& app, float& aqq, float& apq, float& arp,
                                             float& arq, float (&V)[9], int p, int q) {
   if (apq == 0.0f) return;
-  float theta = (aqq - app) / (2.0f * apq);
-  float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
-  float c = rsqrtf(fmaf(t, t, 1.0f));
-  float s = t * c;
+  const float theta = (aqq - app) / (2.0f * apq);
+  const float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+  const float c = rsqrtf(fmaf(t, t, 1.0f));
+  const float s = t * c;
   app = app - t * apq;
   aqq = aqq + t * apq;
   apq = 0.0f;
-  float rp = arp, rq = arq;
+  const float rp = arp, rq = arq;
   arp = c * rp - s * rq;
   arq = s * rp + c * rq;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    float vp = V[3 * r + p], vq = V[3 * r + q];
+    const float vp = V[3 * r + p], vq = V[3 * r + q];
     V[3 * r + p] = c * vp - s * vq;
     V[3 * r + q] = s * vp + c * vq;
   }
-}
-
-__device__ __forceinline__ void givens_rows(float (&B)[9], float (&U)[9], int i, int k, int j) {
-  float a = B[3 * i + j], b = B[3 * k + j];
-  float r2 = a * a + b * b;
-  if (r2 == 0.0f) return;
-  float inv = rsqrtf(r2);
-  float c = a * inv, s = b * inv;
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    float bi = B[3 * i + m], bk = B[3 * k + m];
-    B[3 * i + m] = c * bi + s * bk;
-    B[3 * k + m] = -s * bi + c * bk;
-    float ui = U[3 * m + i], uk = U[3 * m + k];
-    U[3 * m + i] = c * ui + s * uk;
-    U[3 * m + k] = -s * ui + c * uk;
-  }
-}
-
-__device__ __forceinline__ void svd3(const float (&F)[9], float (&U)[9], float (&S)[3],
-                                     float (&V)[9]) {
-  // A = F^T F
-  float a00 = F[0] * F[0] + F[3] * F[3] + F[6] * F[6];
-  float a11 = F[1] * F[1] + F[4] * F[4] + F[7] * F[7];
-  float a22 = F[2] * F[2] + F[5] * F[5] + F[8] * F[8];
-  float a01 = F[0] * F[1] + F[3] * F[4] + F[6] * F[7];
-  float a02 = F[0] * F[2] + F[3] * F[5] + F[6] * F[8];
-  float a12 = F[1] * F[2] + F[4] * F[5] + F[7] * F[8];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.0f : 0.0f;
-#pragma unroll 1
-  for (int sweep = 0; sweep < 6; ++sweep) {
-    jacobi_pair(a00, a11, a01, a02, a12, V, 0, 1);  // r = 2
-    jacobi_pair(a00, a22, a02, a01, a12, V, 0, 2);  // r = 1
-    jacobi_pair(a11, a22, a12, a01, a02, V, 1, 2);  // r = 0
-  }
-  // B = F V
-  float B[9];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      B[3 * r + c] = F[3 * r] * V[c] + F[3 * r + 1] * V[3 + c] + F[3 * r + 2] * V[6 + c];
-  // order columns by decreasing length; each swap negates one column so V
-  // stays a rotation
-  auto col2 = [&](int c) { return B[c] * B[c] + B[3 + c] * B[3 + c] + B[6 + c] * B[6 + c]; };
-  auto swapneg = [&](int c0, int c1) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      float t = B[3 * r + c0];
-      B[3 * r + c0] = -B[3 * r + c1];
-      B[3 * r + c1] = t;
-      t = V[3 * r + c0];
-      V[3 * r + c0] = -V[3 * r + c1];
-      V[3 * r + c1] = t;
-    }
-  };
-  float l0 = col2(0), l1 = col2(1), l2 = col2(2);
-  if (l0 < l1) { swapneg(0, 1); float t = l0; l0 = l1; l1 = t; }
-  if (l0 < l2) { swapneg(0, 2); float t = l0; l0 = l2; l2 = t; }
-  if (l1 < l2) { swapneg(1, 2); }
-#pragma unroll
-  for (int i = 0; i < 9; ++i) U[i] = (i % 4 == 0) ? 1.0f : 0.0f;
-  givens_rows(B, U, 0, 1, 0);
-  givens_rows(B, U, 0, 2, 0);
-  givens_rows(B, U, 1, 2, 1);
-  S[0] = B[0];
-  S[1] = B[4];
-  S[2] = B[8];
 }
 
 __device__ __forceinline__ float det3(const float (&A)[9]) {
@@ -255,73 +237,155 @@ __device__ __forceinline__ float det3(const float (&A)[9]) {
          A[2] * (A[3] * A[7] - A[4] * A[6]);
 }
 
+__device__ __forceinline__ void polar_svd(const float (&F)[9], Polar& P) {
+  float D[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) D[i] = F[i];
+  D[0] -= 1.0f; D[4] -= 1.0f; D[8] -= 1.0f;
+  auto dtd = [&](int a, int b) {
+    return D[a] * D[b] + D[3 + a] * D[3 + b] + D[6 + a] * D[6 + b];
+  };
+  float a00 = 2.0f * D[0] + dtd(0, 0);
+  float a11 = 2.0f * D[4] + dtd(1, 1);
+  float a22 = 2.0f * D[8] + dtd(2, 2);
+  float a01 = D[1] + D[3] + dtd(0, 1);
+  float a02 = D[2] + D[6] + dtd(0, 2);
+  float a12 = D[5] + D[7] + dtd(1, 2);
+  float* V = P.V;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.0f : 0.0f;
+  float (&Vr)[9] = P.V;
+#pragma unroll 1
+  for (int sweep = 0; sweep < 5; ++sweep) {
+    jacobi_pair(a00, a11, a01, a02, a12, Vr, 0, 1);
+    jacobi_pair(a00, a22, a02, a01, a12, Vr, 0, 2);
+    jacobi_pair(a11, a22, a12, a01, a02, Vr, 1, 2);
+  }
+  float l[3] = {a00, a11, a22};
+  // order by decreasing eigenvalue; each swap negates one column so V stays a rotation
+  auto swapneg = [&](int c0, int c1) {
+    float t = l[c0]; l[c0] = l[c1]; l[c1] = t;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      float v = V[3 * r + c0];
+      V[3 * r + c0] = -V[3 * r + c1];
+      V[3 * r + c1] = v;
+    }
+  };
+  if (l[0] < l[1]) swapneg(0, 1);
+  if (l[0] < l[2]) swapneg(0, 2);
+  if (l[1] < l[2]) swapneg(1, 2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float la = fmaxf(l[a], -1.0f);
+    const float sa = sqrtf(1.0f + la);
+    P.s[a] = sa;
+    P.sm1[a] = la / (1.0f + sa);
+  }
+  // U from F V: u0 = Fv0/|Fv0|, u1 = Gram-Schmidt of Fv1, u2 = u0 x u1
+  float b[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      b[c][r] = F[3 * r] * V[c] + F[3 * r + 1] * V[3 + c] + F[3 * r + 2] * V[6 + c];
+  float u0[3], u1[3];
+  float n0 = b[0][0] * b[0][0] + b[0][1] * b[0][1] + b[0][2] * b[0][2];
+  if (n0 > 1e-30f) {
+    const float inv = rsqrtf(n0);
+    u0[0] = b[0][0] * inv; u0[1] = b[0][1] * inv; u0[2] = b[0][2] * inv;
+  } else {
+    u0[0] = 1.0f; u0[1] = 0.0f; u0[2] = 0.0f;
+  }
+  const float pr = u0[0] * b[1][0] + u0[1] * b[1][1] + u0[2] * b[1][2];
+  u1[0] = b[1][0] - pr * u0[0]; u1[1] = b[1][1] - pr * u0[1]; u1[2] = b[1][2] - pr * u0[2];
+  float n1 = u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2];
+  if (!(n1 > 1e-30f)) {  // any unit vector orthogonal to u0
+    const int a = (fabsf(u0[0]) <= fabsf(u0[1]) && fabsf(u0[0]) <= fabsf(u0[2])) ? 0
+                  : (fabsf(u0[1]) <= fabsf(u0[2])) ? 1 : 2;
+    float e[3] = {0.0f, 0.0f, 0.0f};
+    e[a] = 1.0f;
+    u1[0] = u0[1] * e[2] - u0[2] * e[1];
+    u1[1] = u0[2] * e[0] - u0[0] * e[2];
+    u1[2] = u0[0] * e[1] - u0[1] * e[0];
+    n1 = u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2];
+  }
+  const float inv1 = rsqrtf(n1);
+  u1[0] *= inv1; u1[1] *= inv1; u1[2] *= inv1;
+  const float u2[3] = {u0[1] * u1[2] - u0[2] * u1[1], u0[2] * u1[0] - u0[0] * u1[2],
+                       u0[0] * u1[1] - u0[1] * u1[0]};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    P.U[3 * r] = u0[r];
+    P.U[3 * r + 1] = u1[r];
+    P.U[3 * r + 2] = u2[r];
+  }
+  if (det3(F) < 0.0f) {  // reflection carried by the smallest singular value
+    P.s[2] = -P.s[2];
+    P.sm1[2] = P.s[2] - 1.0f;
+  }
+}
+
 constexpr float kHenckySigmaMin = 1e-4f;
 
 // Kirchhoff stress tau = P(F) F^T (symmetric, 6 entries xx yy zz xy xz yz).
 __device__ __forceinline__ void kirchhoff(const DevGroup& gr, const float (&F)[9], float (&t)[6]) {
-  float U[9], S[3], V[9];
-  svd3(F, U, S, V);
+  Polar P;
+  polar_svd(F, P);
+  float d[3];
+  float iso = 0.0f;
   if (gr.model == MPM_DRUCKER_PRAGER) {
-    // Hencky: tau = U diag(2 mu e + lam tr e) U^T, e = log S
+    // Hencky: tau = U diag(2 mu e + lam tr e) U^T, e = log s
     float e[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) e[a] = logf(fmaxf(S[a], kHenckySigmaMin));
-    float tr = e[0] + e[1] + e[2];
-    float d[3];
+    for (int a = 0; a < 3; ++a)
+      e[a] = P.s[a] > kHenckySigmaMin ? log1pf(P.sm1[a]) : logf(kHenckySigmaMin);
+    const float tr = e[0] + e[1] + e[2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) d[a] = 2.0f * gr.mu_l * e[a] + gr.lam * tr;
-    auto ent = [&](int r, int c) {
-      return U[3 * r] * d[0] * U[3 * c] + U[3 * r + 1] * d[1] * U[3 * c + 1] +
-             U[3 * r + 2] * d[2] * U[3 * c + 2];
-    };
-    t[0] = ent(0, 0); t[1] = ent(1, 1); t[2] = ent(2, 2);
-    t[3] = ent(0, 1); t[4] = ent(0, 2); t[5] = ent(1, 2);
   } else {
-    // fixed corotated: tau = 2 mu (F - R) F^T + lam J (J - 1) I, R = U V^T
-    float R[9];
+    // fixed corotated: tau = 2 mu (F - R) F^T + lam J (J - 1) I
+    //                      = U diag(2 mu s (s - 1)) U^T + lam J (J - 1) I
+    const float a = P.sm1[0], b = P.sm1[1], c = P.sm1[2];
+    const float jm1 = a + b + c + a * b + a * c + b * c + a * b * c;  // J - 1
+    iso = gr.lam * (1.0f + jm1) * jm1;
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        R[3 * r + c] = U[3 * r] * V[3 * c] + U[3 * r + 1] * V[3 * c + 1] + U[3 * r + 2] * V[3 * c + 2];
-    float J = det3(F);
-    float D[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) D[i] = F[i] - R[i];
-    auto ent = [&](int r, int c) {
-      return D[3 * r] * F[3 * c] + D[3 * r + 1] * F[3 * c + 1] + D[3 * r + 2] * F[3 * c + 2];
-    };
-    float vol = gr.lam * J * (J - 1.0f);
-    float m2 = 2.0f * gr.mu_l;
-    t[0] = m2 * ent(0, 0) + vol; t[1] = m2 * ent(1, 1) + vol; t[2] = m2 * ent(2, 2) + vol;
-    t[3] = m2 * 0.5f * (ent(0, 1) + ent(1, 0));
-    t[4] = m2 * 0.5f * (ent(0, 2) + ent(2, 0));
-    t[5] = m2 * 0.5f * (ent(1, 2) + ent(2, 1));
+    for (int k = 0; k < 3; ++k) d[k] = 2.0f * gr.mu_l * P.s[k] * P.sm1[k];
   }
+  const float* U = P.U;
+  auto ent = [&](int r, int c) {
+    return U[3 * r] * d[0] * U[3 * c] + U[3 * r + 1] * d[1] * U[3 * c + 1] +
+           U[3 * r + 2] * d[2] * U[3 * c + 2];
+  };
+  t[0] = ent(0, 0) + iso; t[1] = ent(1, 1) + iso; t[2] = ent(2, 2) + iso;
+  t[3] = ent(0, 1); t[4] = ent(0, 2); t[5] = ent(1, 2);
 }
 
 // Drucker-Prager return map in Hencky strain space (sand); F updated in place.
 __device__ __forceinline__ void dp_project(const DevGroup& gr, float (&F)[9]) {
-  float U[9], S[3], V[9];
-  svd3(F, U, S, V);
+  Polar P;
+  polar_svd(F, P);
   bool clamped = false;
   float e[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    float s = S[a];
-    if (s < kHenckySigmaMin) { s = kHenckySigmaMin; clamped = true; }
-    e[a] = logf(s);
+    if (P.s[a] > kHenckySigmaMin) {
+      e[a] = log1pf(P.sm1[a]);
+    } else {
+      e[a] = logf(kHenckySigmaMin);
+      clamped = true;
+    }
   }
-  float tr = e[0] + e[1] + e[2];
-  float eh[3] = {e[0] - tr / 3.0f, e[1] - tr / 3.0f, e[2] - tr / 3.0f};
-  float nh = sqrtf(eh[0] * eh[0] + eh[1] * eh[1] + eh[2] * eh[2]);
+  const float tr = e[0] + e[1] + e[2];
+  const float eh[3] = {e[0] - tr / 3.0f, e[1] - tr / 3.0f, e[2] - tr / 3.0f};
+  const float nh = sqrtf(eh[0] * eh[0] + eh[1] * eh[1] + eh[2] * eh[2]);
   float en[3] = {e[0], e[1], e[2]};
   bool project = false;
   if (tr >= 0.0f) {
     en[0] = en[1] = en[2] = 0.0f;
     project = true;
   } else {
-    float dg = nh + (3.0f * gr.lam + 2.0f * gr.mu_l) / (2.0f * gr.mu_l) * tr * gr.dp_alpha;
+    const float dg = nh + (3.0f * gr.lam + 2.0f * gr.mu_l) / (2.0f * gr.mu_l) * tr * gr.dp_alpha;
     if (dg > 0.0f) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) en[a] = e[a] - dg * eh[a] / nh;
@@ -329,7 +393,9 @@ __device__ __forceinline__ void dp_project(const DevGroup& gr, float (&F)[9]) {
     }
   }
   if (!project && !clamped) return;
-  float s[3] = {expf(en[0]), expf(en[1]), expf(en[2])};
+  const float s[3] = {expf(en[0]), expf(en[1]), expf(en[2])};
+  const float* U = P.U;
+  const float* V = P.V;
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -384,6 +450,36 @@ __device__ __forceinline__ float body_sdf(const DevBody& b, float x, float y, fl
 #pragma unroll
   for (int r = 0; r < 3; ++r) n[r] = b.R[3 * r] * nb[0] + b.R[3 * r + 1] * nb[1] + b.R[3 * r + 2] * nb[2];
   return phi;
+}
+
+// The same signed distance evaluated in FP64 from the FP32 inputs. A
+// penetration of 1e-4 m at 0.05 m from a body origin is only known to ~4e-5
+// relative in FP32, so contact registration and the penetration depth phi0
+// use this value for the (few) particles the FP32 test puts near a surface.
+__device__ __forceinline__ double body_sdf_f64(const DevBody& b, float x, float y, float z) {
+  const double r0 = (double)x - (double)b.p[0], r1 = (double)y - (double)b.p[1],
+               r2 = (double)z - (double)b.p[2];
+  double yb[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    yb[c] = (double)b.R[c] * r0 + (double)b.R[3 + c] * r1 + (double)b.R[6 + c] * r2;
+  if (b.shape == MPM_HALFSPACE) return yb[2];
+  if (b.shape == MPM_SPHERE) return sqrt(yb[0] * yb[0] + yb[1] * yb[1] + yb[2] * yb[2]) - (double)b.prm[0];
+  if (b.shape == MPM_BOX) {
+    double q[3], o2 = 0.0, qm = -1e300;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      q[a] = fabs(yb[a]) - (double)b.prm[a];
+      qm = fmax(qm, q[a]);
+      const double qp = fmax(q[a], 0.0);
+      o2 += qp * qp;
+    }
+    return qm <= 0.0 ? qm : sqrt(o2);
+  }
+  const double L = (double)b.prm[0];
+  const double cz = fmin(fmax(yb[2], -L), L);
+  const double o0 = yb[0], o1 = yb[1], o2 = yb[2] - cz;
+  return sqrt(o0 * o0 + o1 * o1 + o2 * o2) - (double)b.prm[1];
 }
 
 __device__ __forceinline__ void body_velocity(const DevBody& b, float x, float y, float z,

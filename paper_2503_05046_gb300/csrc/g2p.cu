@@ -27,9 +27,11 @@ __global__ void __launch_bounds__(kThreads) k_g2p(G2PArgs a) {
       atomicAdd(&a.stats->substeps, 1);
       *a.C.count = 0;
       *a.G.n_act = 0;
+      *a.G.n_cnodes = 0;
+      *a.G.pstar2 = 0.0;
       a.bar[0] = 0u;
     }
-    if (threadIdx.x < 32) a.red[threadIdx.x] = 0.0;
+    if (threadIdx.x < kRedDoubles) a.red[threadIdx.x] = 0.0;
   }
   const int i = blockIdx.x * kThreads + threadIdx.x;
   if (i >= a.n) return;

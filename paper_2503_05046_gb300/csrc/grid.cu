@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(256) k_grid_update(GridDev g, GridArrays G, fl
     stats->last_active = n_act;
   }
   const long long total = (long long)n_act * kBlockNodes;
+  float p2 = 0.f;  // sum of m |v*|^2 over free nodes (the momentum norm of Alg. 1)
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int blk = G.act[t >> 6];
@@ -55,11 +56,23 @@ __global__ void __launch_bounds__(256) k_grid_update(GridDev g, GridArrays G, fl
       vs.y = wall ? 0.0f : mp.z * inv_m + h * g.gy;
       vs.z = wall ? 0.0f : mp.w * inv_m + h * g.gz;
       vs.w = mp.x;
+      if (!wall) p2 += mp.x * (vs.x * vs.x + vs.y * vs.y + vs.z * vs.z);
     }
     G.mp[node] = make_float4(0.f, 0.f, 0.f, 0.f);
     G.vs[node] = vs;
     // .w flags a Dirichlet node for the contact solve
     G.v[node] = make_float4(vs.x, vs.y, vs.z, wall ? 1.f : 0.f);
+    G.vlo[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __shared__ double s_p2[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+  if ((threadIdx.x & 31) == 0) s_p2[threadIdx.x >> 5] = (double)p2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += s_p2[w];
+    if (sum != 0.0) atomicAdd(G.pstar2, sum);
   }
 }
 

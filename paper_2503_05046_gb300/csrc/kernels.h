@@ -9,6 +9,8 @@
 
 namespace mpmcr {
 
+constexpr int kRedDoubles = 64;  // reduction ring of the contact solve (4 slots of 16)
+
 // Statistics written by the device, read back by mpm_step.
 struct DevStats {
   int iters_total;
@@ -77,7 +79,7 @@ struct SolveArgs {
   int ls_max_iters;
   double eps_r, eps_a;
   int max_iters;
-  double* red;        // reduction ring [4][8]
+  double* red;        // reduction ring [4][16]
   unsigned* bar;      // grid barrier words [2]
   uint32_t* status;
   DevStats* stats;

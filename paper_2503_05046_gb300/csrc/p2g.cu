@@ -187,7 +187,12 @@ __global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
         if (!((cand >> b) & 1u)) continue;
         float nrm[3] = {0.f, 0.f, 1.f};
         float phi = 1.0f;
-        if (valid[it]) phi = body_sdf(s_body[b], xp[0], xp[1], xp[2], nrm);
+        if (valid[it]) {
+          phi = body_sdf(s_body[b], xp[0], xp[1], xp[2], nrm);
+          // near the surface the sign and the depth come from FP64
+          if (phi < 1e-6f + 1e-6f * (fabsf(xp[0]) + fabsf(xp[1]) + fabsf(xp[2])))
+            phi = (float)body_sdf_f64(s_body[b], xp[0], xp[1], xp[2]);
+        }
         const bool hit = valid[it] && phi < 0.0f;
         const unsigned mask = __ballot_sync(0xffffffffu, hit);
         if (mask == 0u) continue;

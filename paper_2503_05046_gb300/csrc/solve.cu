@@ -1,21 +1,29 @@
 // solve.cu -- the contact solve of one substep (Eq. (7)-(8)) by the
 // quasi-Newton iteration of Alg. 1 (Sec. IV-C, V-B), entirely on the device.
 //
-// One cooperative launch runs the whole iteration: all thread blocks are
-// co-resident and step through the phases in lockstep, separated by a grid
-// barrier whose spin has an iteration limit (on expiry the kernel records
-// MPM_ERR_TIMEOUT and every block returns). Per iteration:
-//   G  contacts: v_c += alpha dv_c; gradient (3) and Hessian (3x3) of the
-//      lagged contact potential at v_c, scattered to the nodes with weights
-//      w and w^2 (the 3x3 diagonal blocks of J^T (d2 l_c) J, Eq. (10));
-//      nodes: v += alpha dv.
-//   N  nodes: g = M (v - v*) + J^T dl_c (Eq. (9)), H = M + contact blocks,
-//      stopping norms, dv = -H^-1 g by 3x3 Cholesky; grid sums for the line
-//      search, A = dv^T M dv and B = dv^T M (v - v*).
-//   C  contacts: dv_c = J dv (a G2P gather) and the first line-search
-//      derivatives at alpha = 0 and 1.
-//   L  line search: f'(alpha) = B + alpha A + sum_p dl_c . dv_c and f'' are
-//      contact-only reductions; Newton steps safeguarded by bisection.
+// One cooperative launch runs the whole iteration. The participating thread
+// blocks (as many as the contact count needs, at most one per SM) step
+// through the phases in lockstep, separated by a grid barrier whose spin has
+// an iteration limit (on expiry the kernel records MPM_ERR_TIMEOUT and every
+// block returns). Only the nodes in the stencil of some contact can change
+// (everywhere else the gradient M (v - v*) is zero at v = v*), so the node
+// phases run over a contact-node list built at the start; the momentum norm
+// adds the grid update's sum of m |v*|^2 over the other nodes.
+//
+// Per iteration:
+//   G  contacts: v_c = J v + b (a compensated gather of the double-float
+//      iterate); gradient (3) and Hessian (3x3) of the lagged contact
+//      potential, scattered with weights w and w^2 (the 3x3 diagonal blocks of
+//      J^T (d2 l_c) J, Eq. (10)); contact nodes: v += alpha dv (double-float).
+//   N  contact nodes: g = M (v - v*) + J^T dl_c (Eq. (9)), H = M + contact
+//      blocks, stopping norms, dv = -H^-1 g by 3x3 Cholesky; grid sums of the
+//      line search, A = dv^T M dv and B = dv^T M (v - v*).
+//   C  contacts: dv_c = J dv, and the first line-search pass.
+//   L  exact line search (Alg. 1): f'(alpha) = B + alpha A + sum_p dl_c . dv_c
+//      is monotone (f convex); each pass evaluates it at 8 points in one
+//      contact sweep: first on a doubling grid to bracket the root, then
+//      around the secant estimate inside the bracket, until
+//      |f'| <= ls_rel_tol |f'(0)|.
 // Every block reads the same reduced sums, so all take the same decisions.
 // Scalar sums are accumulated per thread and per warp in FP32, across warps
 // and blocks in FP64.
@@ -29,6 +37,9 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
+constexpr int kContactsPerBlock = 128;
+constexpr int kLsPoints = 8;
+constexpr int kRedWidth = 16;              // doubles per reduction slot
 constexpr unsigned kSpinLimit = 1u << 24;  // ~1 s of polling with the back-off below
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -37,13 +48,9 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-__device__ __forceinline__ double ld_cg(const double* p) {
-  return __ldcg(p);
-}
-
 struct Barrier {
   unsigned* bar;  // [0] arrivals, [1] generation
-  unsigned n;
+  unsigned n;     // participating blocks
   unsigned gen;   // meaningful in thread 0 only
   uint32_t* status;
 };
@@ -68,7 +75,7 @@ __device__ bool grid_sync(Barrier& B) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     B.gen += 1u;
@@ -81,7 +88,7 @@ __device__ bool grid_sync(Barrier& B) {
 }
 
 template <int NV>
-__device__ void block_reduce_add(float (&v)[NV], double* dst, double (*s_red)[8]) {
+__device__ void block_reduce_add(float (&v)[NV], double* dst, double (*s_red)[kRedWidth]) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
@@ -97,7 +104,7 @@ __device__ void block_reduce_add(float (&v)[NV], double* dst, double (*s_red)[8]
       double x = lane < kWarps ? s_red[lane][i] : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) atomicAdd(dst + i, x);
+      if (lane == 0 && x != 0.0) atomicAdd(dst + i, x);
     }
   }
   __syncthreads();
@@ -124,6 +131,38 @@ __device__ __forceinline__ void gather(const GridDev& g, const float4* __restric
     }
 }
 
+// v_c = J v + b + alpha J dv with v = hi + lo, summed with compensation so
+// that the result is accurate to FP32 rounding of v_c itself (a stuck contact's
+// tangential velocity is a small difference of node velocities)
+__device__ __forceinline__ void gather_dd(const GridDev& g, const float4* __restrict__ hi,
+                                          const float4* __restrict__ lo, const float4& xp,
+                                          const float4& b, float al, const float4& dvc,
+                                          float (&out)[3]) {
+  Stencil s;
+  stencil(g, xp.x, xp.y, xp.z, s);
+  CompSum cs[3];
+#pragma unroll
+  for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy) {
+      const float wyz = s.w[1][cy] * s.w[2][cz];
+#pragma unroll
+      for (int cx = 0; cx < 3; ++cx) {
+        const float w = s.w[0][cx] * wyz;
+        const int node = node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz);
+        const float4 h = __ldcg(hi + node);
+        const float4 l = __ldcg(lo + node);
+        cs[0].add_prod(w, h.x); cs[0].E += w * l.x;
+        cs[1].add_prod(w, h.y); cs[1].E += w * l.y;
+        cs[2].add_prod(w, h.z); cs[2].E += w * l.z;
+      }
+    }
+  cs[0].add(b.x); cs[1].add(b.y); cs[2].add(b.z);
+  cs[0].add_prod(al, dvc.x); cs[1].add_prod(al, dvc.y); cs[2].add_prod(al, dvc.z);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[c] = cs[c].value();
+}
+
 __device__ __forceinline__ void load_contact(const Contacts& C, int p, float4& xp, float (&n)[3],
                                              float& n0) {
   xp = C.xp[p];
@@ -132,79 +171,95 @@ __device__ __forceinline__ void load_contact(const Contacts& C, int p, float4& x
   n0 = q.w;
 }
 
-// derivative sums of the line search at alpha for this thread's contacts
-__device__ void ls_eval(const SolveArgs& a, const DevBody* s_body, int nc, float alpha,
-                        float (&acc)[2]) {
-  acc[0] = acc[1] = 0.f;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nc; p += gridDim.x * blockDim.x) {
-    float4 xp; float n[3]; float n0;
-    load_contact(a.C, p, xp, n, n0);
-    const DevBody& bd = s_body[a.C.id[p].y];
-    const float4 vc = a.C.vc[p], dvc = a.C.dvc[p];
-    const float u[3] = {vc.x + alpha * dvc.x, vc.y + alpha * dvc.y, vc.z + alpha * dvc.z};
-    const float e[3] = {dvc.x, dvc.y, dvc.z};
+// contact part of f'(alpha_k), k < kLsPoints, for this thread's contacts
+__device__ __forceinline__ void ls_contact(const SolveArgs& a, const DevBody& bd, const float4& xp,
+                                           const float (&n)[3], float n0, const float4& vc,
+                                           const float (&e)[3], const float (&alphas)[kLsPoints],
+                                           float (&acc)[kLsPoints]) {
+#pragma unroll
+  for (int k = 0; k < kLsPoints; ++k) {
+    const float al = alphas[k];
+    const float u[3] = {vc.x + al * e[0], vc.y + al * e[1], vc.z + al * e[2]};
     ContactLaw L;
     contact_law(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, L);
     float d1, d2;
     contact_dir(L, n, e, d1, d2);
-    acc[0] += d1;
-    acc[1] += d2;
+    acc[k] += d1;
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_solve(SolveArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   __shared__ DevBody s_body[kMaxBodies];
-  __shared__ double s_red[kWarps][8];
+  __shared__ double s_red[kWarps][kRedWidth];
   __shared__ float s_imp[kMaxBodies][6];
   const int tid = threadIdx.x;
+  const int count = *a.C.count;
+  const int nc = count < a.C.cap ? count : a.C.cap;
+  if (nc == 0) return;  // v = v* already (set by the grid update)
+  int nblk = (nc + kContactsPerBlock - 1) / kContactsPerBlock;
+  nblk = nblk < (int)gridDim.x ? nblk : (int)gridDim.x;
+  if ((int)blockIdx.x >= nblk) return;  // not needed for this many contacts
+
   for (int i = tid; i < a.nb * (int)(sizeof(DevBody) / 4); i += kThreads)
     reinterpret_cast<float*>(s_body)[i] = reinterpret_cast<const float*>(a.bodies)[i];
   for (int i = tid; i < kMaxBodies * 6; i += kThreads) (&s_imp[0][0])[i] = 0.f;
-  const int count = *a.C.count;
-  const int nc = count < a.C.cap ? count : a.C.cap;
-  const long long n_nodes = (long long)(*a.G.n_act) * kBlockNodes;
   __syncthreads();
-  if (nc == 0) return;  // v = v* already (set by the grid update)
 
-  Barrier B{a.bar, gridDim.x, 0u, a.status};
+  Barrier B{a.bar, (unsigned)nblk, 0u, a.status};
   if (tid == 0) B.gen = ld_acquire(&a.bar[1]);
   const int gtid = blockIdx.x * kThreads + tid;
-  const int gstride = gridDim.x * kThreads;
+  const int gstride = nblk * kThreads;
   const GridDev& g = a.g;
   int rslot = 0;
   auto next_slot = [&]() -> double* {
-    double* s = a.red + 8 * (rslot & 3);
-    if (blockIdx.x == 0 && tid < 8) a.red[8 * ((rslot + 2) & 3) + tid] = 0.0;
+    double* s = a.red + kRedWidth * (rslot & 3);
+    if (blockIdx.x == 0 && tid < kRedWidth) a.red[kRedWidth * ((rslot + 2) & 3) + tid] = 0.0;
     ++rslot;
     return s;
   };
 
-  // v_c = J v + b at v = v* (Alg. 1 initialisation)
+  // ---- contact-node list: the union of the contacts' stencils
   for (int p = gtid; p < nc; p += gstride) {
-    float u[3];
-    gather(g, a.G.v, a.C.xp[p], u);
-    const float4 b = a.C.bias[p];
-    a.C.vc[p] = make_float4(u[0] + b.x, u[1] + b.y, u[2] + b.z, 0.f);
+    const float4 xp = a.C.xp[p];
+    Stencil s;
+    stencil(g, xp.x, xp.y, xp.z, s);
+#pragma unroll 1
+    for (int c = 0; c < 27; ++c) {
+      const int node = node_index(g, s.base[0] + c % 3, s.base[1] + (c / 3) % 3, s.base[2] + c / 9);
+      if (atomicExch(a.G.cflag + node, 1) == 0) {
+        const int slot = atomicAdd(a.G.n_cnodes, 1);
+        if (slot < a.G.cnodes_cap) a.G.cnodes[slot] = node;
+      }
+    }
   }
   if (!grid_sync(B)) return;
+  int ncn = __ldcg(a.G.n_cnodes);
+  ncn = ncn < a.G.cnodes_cap ? ncn : a.G.cnodes_cap;
+  const double pstar2 = __ldcg(a.G.pstar2);
 
+  // The iterate v = hi + lo is double buffered: in phase G every contact node
+  // writes v_next = v_cur + alpha dv while every contact gathers
+  // v_c = J v_cur + b + alpha J dv from the untouched v_cur. Gathering v_c
+  // afresh keeps it equal to J v (an incrementally updated v_c drifts from
+  // J v over thousands of FP32 updates).
+  float4* vcur = a.G.v;
+  float4* vnxt = a.G.v2;
+  float4* lcur = a.G.vlo;
+  float4* lnxt = a.G.vlo2;
   double alpha = 0.0;
-  int it = 0, ls_evals = 0;
+  int it = 0, ls_passes = 0;
   float resid = 0.f;
   for (;;) {
-    // ---- G: update by the last step, contact gradient / Hessian blocks
+    // ---- G: step by alpha, contact gradient / Hessian blocks
     const float al = (float)alpha;
     for (int p = gtid; p < nc; p += gstride) {
       float4 xp; float n[3]; float n0;
       load_contact(a.C, p, xp, n, n0);
-      float4 vc = a.C.vc[p];
-      if (it > 0) {
-        const float4 dvc = a.C.dvc[p];
-        vc.x += al * dvc.x; vc.y += al * dvc.y; vc.z += al * dvc.z;
-        a.C.vc[p] = vc;
-      }
+      float u[3];
+      const float4 dvc = it > 0 ? a.C.dvc[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+      gather_dd(g, vcur, lcur, xp, a.C.bias[p], al, dvc, u);
+      a.C.vc[p] = make_float4(u[0], u[1], u[2], 0.f);
       const DevBody& bd = s_body[a.C.id[p].y];
-      const float u[3] = {vc.x, vc.y, vc.z};
       ContactLaw L;
       contact_law(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, L);
       float gr[3], H[6];
@@ -228,156 +283,166 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveArgs a) {
         }
     }
     if (it > 0) {
-      for (long long t = gtid; t < n_nodes; t += gstride) {
-        const int node = a.G.act[t >> 6] * kBlockNodes + (int)(t & 63);
-        float4 v = a.G.v[node];
+      for (int t = gtid; t < ncn; t += gstride) {
+        const int node = a.G.cnodes[t];
+        float4 v = vcur[node];
+        float4 l = lcur[node];
         const float4 d = a.G.dv[node];
-        v.x += al * d.x; v.y += al * d.y; v.z += al * d.z;
-        a.G.v[node] = v;
+        dd_add(v.x, l.x, al * d.x);
+        dd_add(v.y, l.y, al * d.y);
+        dd_add(v.z, l.z, al * d.z);
+        vnxt[node] = v;
+        lnxt[node] = l;
       }
+      float4* t = vcur; vcur = vnxt; vnxt = t;
+      t = lcur; lcur = lnxt; lnxt = t;
     }
     if (!grid_sync(B)) return;
 
     // ---- N: gradient, stopping norms, direction, grid line-search sums
+    double* slot = next_slot();
     {
-      double* slot = next_slot();
-      float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // G2, P2, J2, A, B
-      for (long long t = gtid; t < n_nodes; t += gstride) {
-        const int node = a.G.act[t >> 6] * kBlockNodes + (int)(t & 63);
+      float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // G2, P2 - P*2, J2, A, B
+      for (int t = gtid; t < ncn; t += gstride) {
+        const int node = a.G.cnodes[t];
         const float4 vs = a.G.vs[node];
         const float m = vs.w;
         float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (m > 0.f) {
-          const float4 v = a.G.v[node];
-          // written by other blocks' reductions in this launch: read from L2
-          const float4 c0 = __ldcg(a.G.acc0 + node);
-          const float4 c1 = __ldcg(a.G.acc1 + node);
-          const float c2 = __ldcg(a.G.acc2 + node);
-          a.G.acc0[node] = make_float4(0.f, 0.f, 0.f, 0.f);
-          a.G.acc1[node] = make_float4(0.f, 0.f, 0.f, 0.f);
-          a.G.acc2[node] = 0.f;
-          if (v.w == 0.f) {  // free DoF (v.w flags a Dirichlet node)
-            const float r0 = v.x - vs.x, r1 = v.y - vs.y, r2 = v.z - vs.z;
-            const float g0 = m * r0 + c0.x, g1 = m * r1 + c0.y, g2 = m * r2 + c0.z;
-            const float inv_m = 1.0f / m;
-            acc[0] += (g0 * g0 + g1 * g1 + g2 * g2) * inv_m;
-            acc[1] += m * (v.x * v.x + v.y * v.y + v.z * v.z);
-            acc[2] += (c0.x * c0.x + c0.y * c0.y + c0.z * c0.z) * inv_m;
-            // H = m I + contact block; dv = -H^-1 g (Cholesky)
-            const float h00 = m + c0.w, h11 = m + c1.x, h22 = m + c1.y;
-            const float h01 = c1.z, h02 = c1.w, h12 = c2;
-            const float l00 = sqrtf(h00);
-            const float l10 = h01 / l00, l20 = h02 / l00;
-            const float l11 = sqrtf(fmaxf(h11 - l10 * l10, 1e-30f));
-            const float l21 = (h12 - l20 * l10) / l11;
-            const float l22 = sqrtf(fmaxf(h22 - l20 * l20 - l21 * l21, 1e-30f));
-            const float y0 = -g0 / l00;
-            const float y1 = (-g1 - l10 * y0) / l11;
-            const float y2 = (-g2 - l20 * y0 - l21 * y1) / l22;
-            dv.z = y2 / l22;
-            dv.y = (y1 - l21 * dv.z) / l11;
-            dv.x = (y0 - l10 * dv.y - l20 * dv.z) / l00;
-            acc[3] += m * (dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
-            acc[4] += m * (dv.x * r0 + dv.y * r1 + dv.z * r2);
-          }
+        // written by other blocks' reductions in this launch: read from L2
+        const float4 c0 = __ldcg(a.G.acc0 + node);
+        const float4 c1 = __ldcg(a.G.acc1 + node);
+        const float c2 = __ldcg(a.G.acc2 + node);
+        a.G.acc0[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.G.acc1[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.G.acc2[node] = 0.f;
+        const float4 v = vcur[node];
+        if (m > 0.f && v.w == 0.f) {  // free DoF (v.w flags a Dirichlet node)
+          const float4 vl = lcur[node];
+          // v - v* with the low part of the iterate
+          const float r0 = (v.x - vs.x) + vl.x, r1 = (v.y - vs.y) + vl.y, r2 = (v.z - vs.z) + vl.z;
+          const float g0 = m * r0 + c0.x, g1 = m * r1 + c0.y, g2 = m * r2 + c0.z;
+          const float inv_m = 1.0f / m;
+          acc[0] += (g0 * g0 + g1 * g1 + g2 * g2) * inv_m;
+          // m (|v|^2 - |v*|^2) = m r . (2 v* + r)
+          acc[1] += m * (r0 * (2.f * vs.x + r0) + r1 * (2.f * vs.y + r1) + r2 * (2.f * vs.z + r2));
+          acc[2] += (c0.x * c0.x + c0.y * c0.y + c0.z * c0.z) * inv_m;
+          // H = m I + contact block; dv = -H^-1 g (Cholesky)
+          const float h00 = m + c0.w, h11 = m + c1.x, h22 = m + c1.y;
+          const float h01 = c1.z, h02 = c1.w, h12 = c2;
+          const float l00 = sqrtf(h00);
+          const float l10 = h01 / l00, l20 = h02 / l00;
+          const float l11 = sqrtf(fmaxf(h11 - l10 * l10, 1e-30f));
+          const float l21 = (h12 - l20 * l10) / l11;
+          const float l22 = sqrtf(fmaxf(h22 - l20 * l20 - l21 * l21, 1e-30f));
+          const float y0 = -g0 / l00;
+          const float y1 = (-g1 - l10 * y0) / l11;
+          const float y2 = (-g2 - l20 * y0 - l21 * y1) / l22;
+          dv.z = y2 / l22;
+          dv.y = (y1 - l21 * dv.z) / l11;
+          dv.x = (y0 - l10 * dv.y - l20 * dv.z) / l00;
+          acc[3] += m * (dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
+          acc[4] += m * (dv.x * r0 + dv.y * r1 + dv.z * r2);
         }
         a.G.dv[node] = dv;
       }
       block_reduce_add(acc, slot, s_red);
-      if (!grid_sync(B)) return;
-      const double G2 = ld_cg(slot + 0), P2 = ld_cg(slot + 1), J2 = ld_cg(slot + 2);
-      const double A = ld_cg(slot + 3), Bs = ld_cg(slot + 4);
-      const double Gn = sqrt(G2), Pn = sqrt(P2), Jn = sqrt(J2);
-      const double mx = Pn > Jn ? Pn : Jn;
-      resid = mx > 0.0 ? (float)(Gn / mx) : 0.f;
-      if (!(G2 == G2) || !(A == A) || !(Bs == Bs)) {
-        if (gtid == 0) atomicOr(a.status, kStNan);
-        break;
-      }
-      if (Gn < a.eps_a + a.eps_r * mx || G2 == 0.0) break;  // converged
-      if (it >= a.max_iters) {
-        if (gtid == 0) atomicOr(a.status, kStNotConverged);
-        break;
-      }
+    }
+    if (!grid_sync(B)) return;
+    const double G2 = __ldcg(slot + 0), P2 = pstar2 + __ldcg(slot + 1), J2 = __ldcg(slot + 2);
+    const double A = __ldcg(slot + 3), Bs = __ldcg(slot + 4);
+    const double Gn = sqrt(G2), Pn = sqrt(fmax(P2, 0.0)), Jn = sqrt(J2);
+    const double mx = Pn > Jn ? Pn : Jn;
+    resid = mx > 0.0 ? (float)(Gn / mx) : 0.f;
+    if (!(G2 == G2) || !(A == A) || !(Bs == Bs)) {
+      if (gtid == 0) atomicOr(a.status, kStNan);
+      break;
+    }
+    if (Gn < a.eps_a + a.eps_r * mx || G2 == 0.0) break;  // converged
+    if (it >= a.max_iters) {
+      if (gtid == 0) atomicOr(a.status, kStNotConverged);
+      break;
+    }
 
-      // ---- C: dv_c = J dv and the line-search derivatives at 0 and 1
-      double* slot2 = next_slot();
-      float lacc[3] = {0.f, 0.f, 0.f};  // S1(0), S1(1), S2(1)
+    // ---- C + L: dv_c = J dv, then line-search passes of 8 points each
+    double lo = 0.0, hi = -1.0, flo = 0.0, fhi = 0.0, best = 0.0, fbest = 0.0, f0 = 0.0;
+    double pts[kLsPoints];
+    bool failed = false, have_f0 = false;
+    // first pass: 0 and a doubling grid 1/8 .. 8; later passes: see below
+    pts[0] = 0.0;
+    for (int k = 1; k < kLsPoints; ++k) pts[k] = (double)(1 << (k - 1)) * 0.125;
+    for (int pass = 0;; ++pass) {
+      double* sl = next_slot();
+      float alphas[kLsPoints];
+#pragma unroll
+      for (int k = 0; k < kLsPoints; ++k) alphas[k] = (float)pts[k];
+      float acc[kLsPoints];
+#pragma unroll
+      for (int k = 0; k < kLsPoints; ++k) acc[k] = 0.f;
       for (int p = gtid; p < nc; p += gstride) {
         float4 xp; float n[3]; float n0;
         load_contact(a.C, p, xp, n, n0);
         float e[3];
-        gather(g, a.G.dv, xp, e);
-        a.C.dvc[p] = make_float4(e[0], e[1], e[2], 0.f);
-        const float4 vc = a.C.vc[p];
-        const DevBody& bd = s_body[a.C.id[p].y];
-        ContactLaw L;
-        float d1, d2;
-        const float u0[3] = {vc.x, vc.y, vc.z};
-        contact_law(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u0, L);
-        contact_dir(L, n, e, d1, d2);
-        lacc[0] += d1;
-        const float u1[3] = {vc.x + e[0], vc.y + e[1], vc.z + e[2]};
-        contact_law(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u1, L);
-        contact_dir(L, n, e, d1, d2);
-        lacc[1] += d1;
-        lacc[2] += d2;
+        if (pass == 0) {
+          gather(g, a.G.dv, xp, e);
+          a.C.dvc[p] = make_float4(e[0], e[1], e[2], 0.f);
+        } else {
+          const float4 q = a.C.dvc[p];
+          e[0] = q.x; e[1] = q.y; e[2] = q.z;
+        }
+        ls_contact(a, s_body[a.C.id[p].y], xp, n, n0, a.C.vc[p], e, alphas, acc);
       }
-      block_reduce_add(lacc, slot2, s_red);
+      block_reduce_add(acc, sl, s_red);
       if (!grid_sync(B)) return;
-      ls_evals += 2;
-      const double fp0 = Bs + ld_cg(slot2 + 0);
-      double lo = 0.0, hi = 1.0;
-      double d1 = Bs + A + ld_cg(slot2 + 1);
-      double d2 = A + ld_cg(slot2 + 2);
-      if (!(fp0 < 0.0)) {  // no descent left at working precision
-        alpha = 0.0;
-        break;
+      ++ls_passes;
+      // f'(alpha_k) for the evaluated points, merged into the bracket
+      for (int k = 0; k < kLsPoints; ++k) {
+        const double x = pts[k];
+        const double d = Bs + x * A + __ldcg(sl + k);
+        if (!have_f0 && x == 0.0) { f0 = d; have_f0 = true; flo = d; best = 0.0; fbest = d; }
+        if (d < 0.0) {
+          if (x >= lo) { lo = x; flo = d; }
+        } else if (hi < 0.0 || x < hi) {
+          hi = x; fhi = d;
+        }
+        if (fabs(d) < fabs(fbest)) { best = x; fbest = d; }
       }
-      bool failed = false;
-      while (d1 < 0.0) {  // expand the bracket
-        lo = hi;
-        hi *= 2.0;
-        if (hi > 1024.0) { failed = true; break; }
-        double* sl = next_slot();
-        float e2[2];
-        ls_eval(a, s_body, nc, (float)hi, e2);
-        block_reduce_add(e2, sl, s_red);
-        if (!grid_sync(B)) return;
-        ++ls_evals;
-        d1 = Bs + hi * A + ld_cg(sl);
-        d2 = A + ld_cg(sl + 1);
-      }
-      if (failed) {
-        if (gtid == 0) atomicOr(a.status, kStLineSearch);
-        alpha = lo;
-        ++it;
+      if (!(f0 < 0.0)) { best = 0.0; break; }  // no descent left at working precision
+      const double tol = (double)a.ls_rel_tol * fabs(f0);
+      if (fabs(fbest) <= tol) break;
+      if (pass + 1 >= a.ls_max_iters) break;
+      if (hi < 0.0) {  // root beyond the grid: keep doubling
+        if (lo >= 1024.0) { failed = true; break; }
+        for (int k = 0; k < kLsPoints; ++k) pts[k] = lo * (double)(2 << k);
         continue;
       }
-      const double tol = (double)a.ls_rel_tol * fabs(fp0);
-      double x = hi, prev = DBL_MAX;
-      for (int k = 0; k < a.ls_max_iters; ++k) {
-        if (fabs(d1) <= tol) break;
-        if (d1 < 0.0) lo = x; else hi = x;
-        const double xn = x - d1 / d2;
-        const bool newton = d2 > 0.0 && xn > lo && xn < hi && fabs(d1) <= 0.5 * prev;
-        prev = fabs(d1);
-        x = newton ? xn : 0.5 * (lo + hi);
-        double* sl = next_slot();
-        float e2[2];
-        ls_eval(a, s_body, nc, (float)x, e2);
-        block_reduce_add(e2, sl, s_red);
-        if (!grid_sync(B)) return;
-        ++ls_evals;
-        d1 = Bs + x * A + ld_cg(sl);
-        d2 = A + ld_cg(sl + 1);
-        if (hi - lo <= 1e-7 * hi) break;
+      if (hi - lo <= 1e-12 * hi) break;
+      // secant estimate inside [lo, hi] and a cluster of points around it
+      const double w = hi - lo;
+      double sx = lo - flo * w / (fhi - flo);
+      if (!(sx > lo && sx < hi)) sx = 0.5 * (lo + hi);
+      const double off[kLsPoints] = {0.0, -1e-1, 1e-1, -1e-2, 1e-2, -1e-3, 1e-3, 0.0};
+      for (int k = 0; k < kLsPoints; ++k) {
+        double x = sx + off[k] * w;
+        if (k == kLsPoints - 1) x = 0.5 * (lo + hi);  // bisection point
+        if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
+        pts[k] = x;
       }
-      alpha = x;
-      ++it;
     }
+    if (failed) {
+      if (gtid == 0) atomicOr(a.status, kStLineSearch);
+      best = lo;
+    }
+    alpha = best;
+    ++it;
+    if (alpha == 0.0) break;  // no further progress possible at this precision
   }
 
+  // the solution must end in G.v, which G2P reads; release the node flags
+  for (int t = gtid; t < ncn; t += gstride) {
+    const int node = a.G.cnodes[t];
+    if (vcur != a.G.v) a.G.v[node] = vcur[node];
+    a.G.cflag[node] = 0;
+  }
   // ---- impulses at the solution: gamma = -dl_c/dv_c on the particle; the
   // body receives -gamma and its moment about the body origin (Eq. (3))
   for (int p = gtid; p < nc; p += gstride) {
@@ -408,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_solve(SolveArgs a) {
   if (gtid == 0) {
     atomicAdd(&a.stats->iters_total, it);
     atomicMax(&a.stats->iters_max, it);
-    atomicAdd(&a.stats->ls_evals_total, ls_evals);
+    atomicAdd(&a.stats->ls_evals_total, ls_passes);
     atomicMax(reinterpret_cast<int*>(&a.stats->residual_max), __float_as_int(resid));
   }
 }

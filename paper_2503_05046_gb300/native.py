@@ -317,12 +317,17 @@ class Sim:
         self.max_particles = int(max_particles or max(n, 1))
         self.max_contacts = int(max_contacts or max(4 * n, 1024))
         spec = grid_spec(scene["grid"], self.max_particles, self.max_contacts)
+        # the context's work runs on one stream; by default a dedicated torch
+        # stream (kept alive here) so that callers can order torch work and
+        # CUDA events against it
+        self.torch_stream = None
         if stream is None:
             try:
                 import torch
                 if torch.cuda.is_available():
-                    stream = torch.cuda.current_stream().cuda_stream
-            except Exception:  # torch is optional for the binding
+                    self.torch_stream = torch.cuda.Stream()
+                    stream = self.torch_stream.cuda_stream
+            except ImportError:  # torch is optional for the binding
                 stream = None
         self.ctx = mpm_create(spec, stream)
         for g in scene["groups"]:

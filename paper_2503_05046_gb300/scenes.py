@@ -139,18 +139,20 @@ def granular_scoop(n_particles=1_000_000, seed=SEED_BASE + 1, h=5e-5, substeps=1
 
 
 def sand_column(n_side=12, seed=SEED_BASE + 11, dx=0.01, h=1e-4, with_paddle=True):
-    """Small sand block resting on a half-space with a kinematic box pushing
-    into its side: the granular scooping workload at a size the oracle runs in
-    seconds."""
+    """Small sand block resting on a half-space (bottom particle layer on the
+    plane) with a kinematic box paddle moving along +x whose face touches the
+    block's -x side: the granular scooping workload at a size the oracle runs
+    in seconds."""
     rng = np.random.default_rng(seed)
     spacing = dx / 2.0
-    side = n_side * spacing
-    center = (0.0, 0.0, side / 2.0 + 0.2 * spacing)
-    g = cube_group(n_side, spacing, center, (0, 0, 0), dict(SAND), jitter=0.25 * spacing,
+    half = (n_side - 1) * spacing / 2.0
+    jit = 0.1 * spacing
+    g = cube_group(n_side, spacing, (0.0, 0.0, half + jit), (0, 0, 0), dict(SAND), jitter=jit,
                    rng=rng)
     bodies = [body(HALFSPACE, mu=0.4)]
     if with_paddle:
-        bodies.append(body(BOX, (0.01, 0.02, 0.02), p=(-side / 2 - 0.0115, 0, 0.02),
+        # paddle face 0.5 jitter widths inside the outermost lattice column
+        bodies.append(body(BOX, (0.01, 0.02, 0.02), p=(-half - 0.01 + 0.5 * jit, 0, 0.02),
                            v=(0.2, 0, 0), mu=0.4, kinematic=1))
     grid = {"dx": dx, "res": (32, 32, 32), "origin": (-0.16, -0.16, -0.04),
             "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
