@@ -220,6 +220,24 @@ mpm_status mpm_get_rigid_impulses(mpm_ctx* ctx, double* out, int32_t reset);
 mpm_status mpm_get_grid(mpm_ctx* ctx, int64_t cap, int64_t* count, int32_t* node_ids,
                         float* m, float* vstar, float* v);
 
+/* Same readback as mpm_get_grid, but allocating nothing, for callers that
+   cannot call cudaMalloc at this point: code that must not let an allocation
+   synchronise the device or fail mid-run (real-time loops, pools that own all
+   device memory), or that runs where allocation is not allowed. The paper has
+   no counterpart; this is a property of the library only.
+   The compacted grid is staged in one array inside the library, a file-scope
+   __device__ buffer of 262,144 nodes (9.4 MB) that every GPU loading the
+   library holds until the process exits. The last substep may have swept at
+   most 262,144 nodes (4096 blocks of 4^3), else MPM_ERR_CAPACITY (use
+   mpm_get_grid). The first call on a device looks up the buffer's address
+   (with that device current; the context's device must be current), so make
+   that first call before any stream capture. Every call reuses the same
+   buffer: calls that overlap on the GPU (from several threads or contexts of
+   one device) race and must be serialised by the caller. Synchronises the
+   context's stream; host output arrays as in mpm_get_grid. */
+mpm_status mpm_get_grid_noalloc(mpm_ctx* ctx, int64_t cap, int64_t* count, int32_t* node_ids,
+                                float* m, float* vstar, float* v);
+
 /* Contacts of the last substep (one per particle inside a body, Sec. V-B):
    particle id, body index, impulse on the particle (world frame, 3),
    penetration depth and lagged normal impulse. Host arrays, as above. */

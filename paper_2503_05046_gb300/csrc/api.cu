@@ -731,3 +731,99 @@ mpm_status mpm_get_phase_times(mpm_ctx* ctx, double* ms, int64_t* launches, int3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Grid readback that allocates nothing (no counterpart in the paper).
+//
+// mpm_get_grid compacts the last substep's grid into device buffers it
+// allocates per call. Callers that must not allocate device memory use
+// mpm_get_grid_noalloc instead: its compaction output lives in the file-scope
+// array below, of a fixed maximum size, which every GPU that loads this
+// library holds until the process exits.
+
+namespace {
+
+constexpr int kNoAllocMaxNodes = 1 << 18;  // 262,144 grid nodes
+constexpr size_t kNoAllocHeader = 256;     // the node count, padded
+constexpr size_t kNoAllocBytes = kNoAllocHeader + (size_t)kNoAllocMaxNodes * 4 * (1 + 1 + 3 + 3);
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_grid_readback[kNoAllocBytes];
+
+// device address of g_grid_readback, looked up once per device
+void* g_grid_readback_addr[kNoAllocMaxDevices] = {};
+
+__global__ void k_grid_out_static(GridDev g, GridArrays G, int n_act, unsigned char* base) {
+  int* count = reinterpret_cast<int*>(base);
+  int* ids = reinterpret_cast<int*>(base + kNoAllocHeader);
+  float* m = reinterpret_cast<float*>(ids + kNoAllocMaxNodes);
+  float* vs = m + kNoAllocMaxNodes;
+  float* v = vs + 3 * kNoAllocMaxNodes;
+  const long long total = (long long)n_act * kBlockNodes;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int blk = G.act[t >> 6], cell = (int)(t & 63);
+    const int node = blk * kBlockNodes + cell;
+    const float4 a = G.vs[node];
+    if (!(a.w > 0.f)) continue;
+    const float4 b = G.v[node];
+    const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
+    const int i = bx * 4 + (cell & 3), j = by * 4 + ((cell >> 2) & 3), k = bz * 4 + (cell >> 4);
+    const int slot = atomicAdd(count, 1);
+    if (slot >= kNoAllocMaxNodes) continue;
+    ids[slot] = i + g.rx * (j + g.ry * k);
+    m[slot] = a.w;
+    vs[3 * slot] = a.x; vs[3 * slot + 1] = a.y; vs[3 * slot + 2] = a.z;
+    v[3 * slot] = b.x; v[3 * slot + 1] = b.y; v[3 * slot + 2] = b.z;
+  }
+}
+
+}  // namespace
+
+extern "C" mpm_status mpm_get_grid_noalloc(mpm_ctx* ctx, int64_t cap, int64_t* count,
+                                           int32_t* node_ids, float* m, float* vstar, float* v) {
+  if (!ctx || !count || cap < 0) return MPM_ERR_INVALID_ARG;
+  int dev = -1;
+  CU(cudaGetDevice(&dev));
+  if (dev != ctx->device)
+    return fail(ctx, MPM_ERR_INVALID_ARG,
+                "mpm_get_grid_noalloc: make the context's device current before the call");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_get_grid_noalloc: device index out of range");
+  if (!g_grid_readback_addr[dev]) {
+    void* p = nullptr;
+    CU(cudaGetSymbolAddress(&p, g_grid_readback));
+    g_grid_readback_addr[dev] = p;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_grid_readback_addr[dev]);
+  CU(cudaStreamSynchronize(ctx->stream));
+  DevStats ds;
+  CU(cudaMemcpy(&ds, ctx->stats, sizeof(ds), cudaMemcpyDeviceToHost));
+  const int n_act = ds.last_active;
+  if ((long long)n_act * kBlockNodes > kNoAllocMaxNodes)
+    return fail(ctx, MPM_ERR_CAPACITY,
+                "mpm_get_grid_noalloc: the last substep swept more than 262144 grid nodes "
+                "(4096 blocks of 4^3); use mpm_get_grid");
+  // the array keeps the previous call's contents: the node count starts at zero
+  CU(cudaMemsetAsync(base, 0, sizeof(int), ctx->stream));
+  if (n_act > 0)
+    k_grid_out_static<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->g, ctx->G, n_act, base);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(ctx->stream));
+  int got = 0;
+  CU(cudaMemcpy(&got, base, sizeof(int), cudaMemcpyDeviceToHost));
+  got = got < kNoAllocMaxNodes ? got : kNoAllocMaxNodes;
+  *count = got;
+  const size_t k = (size_t)(got < cap ? got : cap);
+  if (k > 0) {
+    const unsigned char* ids = base + kNoAllocHeader;
+    const unsigned char* mm = ids + (size_t)kNoAllocMaxNodes * 4;
+    const unsigned char* vs = mm + (size_t)kNoAllocMaxNodes * 4;
+    const unsigned char* vv = vs + (size_t)kNoAllocMaxNodes * 12;
+    if (node_ids) CU(cudaMemcpy(node_ids, ids, k * 4, cudaMemcpyDeviceToHost));
+    if (m) CU(cudaMemcpy(m, mm, k * 4, cudaMemcpyDeviceToHost));
+    if (vstar) CU(cudaMemcpy(vstar, vs, k * 12, cudaMemcpyDeviceToHost));
+    if (v) CU(cudaMemcpy(v, vv, k * 12, cudaMemcpyDeviceToHost));
+  }
+  return MPM_OK;
+}

@@ -83,6 +83,7 @@ SIGNATURES = {
     "mpm_get_rigid_impulses": [_vp, _dp, C.c_int32],
     "mpm_get_grid": [_vp, C.c_int64, _i64p, _i32p, _fp, _fp, _fp],
     "mpm_get_contacts": [_vp, C.c_int64, _i64p, _i32p, _i32p, _fp, _fp, _fp],
+    "mpm_get_grid_noalloc": [_vp, C.c_int64, _i64p, _i32p, _fp, _fp, _fp],
     "mpm_synchronize": [_vp],
     "mpm_set_option": [_vp, C.c_int32, C.c_int64],
     "mpm_get_phase_times": [_vp, _dp, _i64p, C.c_int32],
