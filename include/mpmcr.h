@@ -154,7 +154,11 @@ typedef struct {
   double residual_max;       /* max over substeps of the final
                                 ||M^-1/2 grad|| / max(||M^1/2 v||, ||M^-1/2 J^T gamma||) */
   int32_t status_bits;       /* OR of (1 << mpm_status) seen on the device */
-  int32_t p2g_global_chunks; /* P2G particle chunks that bypassed the shared tile */
+  int32_t p2g_global_chunks; /* P2G particle chunks too spread for one shared tile */
+  /* device time of the contact solve's phases, summed over substeps [us]:
+     contact-node list, gradient/Hessian scatter (G), node solve (N),
+     line-search passes, impulses */
+  float solve_us[5];
 } mpm_step_stats;
 
 /* Create a context on the current CUDA device. `cuda_stream` is a

@@ -56,6 +56,7 @@ struct mpm_ctx {
 namespace {
 
 const char* kGenericError = "invalid mpm context";
+constexpr int kPlanes = kParticlePlanes;
 
 mpm_status fail(mpm_ctx* c, mpm_status st, const std::string& msg) {
   if (c) c->err = msg;
@@ -77,10 +78,8 @@ cudaError_t dalloc(T** p, size_t count) {
 
 Particles make_particles(float* buf, uint32_t* pid, uint16_t* grp, int64_t cap) {
   Particles P;
-  for (int c = 0; c < 3; ++c) P.x[c] = buf + (size_t)c * cap;
-  for (int c = 0; c < 3; ++c) P.v[c] = buf + (size_t)(3 + c) * cap;
-  for (int c = 0; c < 9; ++c) P.C[c] = buf + (size_t)(6 + c) * cap;
-  for (int c = 0; c < 9; ++c) P.F[c] = buf + (size_t)(15 + c) * cap;
+  P.base = buf;
+  P.stride = cap;
   P.pid = pid;
   P.grp = grp;
   return P;
@@ -92,13 +91,14 @@ __global__ void k_append(Particles P, int64_t offset, int64_t n, const float* __
   if (j >= n) return;
   int64_t i = offset + j;
   for (int c = 0; c < 3; ++c) {
-    P.x[c][i] = x[3 * j + c];
-    P.v[c][i] = v[3 * j + c];
+    P.x(c)[i] = x[3 * j + c];
+    P.v(c)[i] = v[3 * j + c];
   }
   for (int c = 0; c < 9; ++c) {
-    P.C[c][i] = 0.f;
-    P.F[c][i] = (c % 4 == 0) ? 1.f : 0.f;
+    P.C(c)[i] = 0.f;
+    P.F(c)[i] = (c % 4 == 0) ? 1.f : 0.f;
   }
+  for (int c = 0; c < 6; ++c) P.tau(c)[i] = 0.f;  // stress-free at F = I
   P.pid[i] = (uint32_t)i;
   P.grp[i] = grp;
 }
@@ -295,7 +295,7 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
   const int64_t ccap = spec->max_contacts;
   bool ok = true;
   for (int s = 0; s < 2; ++s) {
-    ok = ok && dalloc(&ctx->pbuf[s], (size_t)24 * cap) == cudaSuccess;
+    ok = ok && dalloc(&ctx->pbuf[s], (size_t)kPlanes * cap) == cudaSuccess;
     ok = ok && dalloc(&ctx->pidbuf[s], cap) == cudaSuccess;
     ok = ok && dalloc(&ctx->grpbuf[s], cap) == cudaSuccess;
     if (ok) ctx->P[s] = make_particles(ctx->pbuf[s], ctx->pidbuf[s], ctx->grpbuf[s], cap);
@@ -459,6 +459,7 @@ mpm_status mpm_set_particles(mpm_ctx* ctx, const float* x, const float* v, const
     }
   }
   launch_from_id_order(ctx->P[ctx->cur], (int)n, dptr[0], dptr[1], dptr[2], dptr[3], ctx->stream);
+  if (F) launch_stress_from_F(ctx->P[ctx->cur], (int)n, ctx->groups_d, ctx->stream);
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(ctx->stream));
   return MPM_OK;
@@ -601,6 +602,7 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
   stats->residual_max = ds.residual_max;
   stats->status_bits = (int32_t)bits;
   stats->p2g_global_chunks = ds.p2g_global_chunks;
+  for (int k = 0; k < 5; ++k) stats->solve_us[k] = (float)(ds.solve_ns[k] * 1e-3);
   return st;
 }
 

@@ -59,15 +59,22 @@ struct DevGroup {
   float pad[2];
 };
 
-// Particle state, structure of arrays (one float plane per component).
+// Particle state, structure of arrays: one float plane per component, planes
+// `stride` floats apart: x 0-2, v 3-5, C 6-14, F 15-23 (row-major 3x3), and the
+// Kirchhoff stress P(F) F^T of the current F, 24-29 (xx yy zz xy xz yz).
 struct Particles {
-  float* x[3];
-  float* v[3];
-  float* C[9];
-  float* F[9];
+  float* base;
+  long long stride;
   uint32_t* pid;    // particle id (order of addition)
   uint16_t* grp;    // particle group
+  __host__ __device__ float* plane(int k) const { return base + (long long)k * stride; }
+  __host__ __device__ float* x(int c) const { return plane(c); }
+  __host__ __device__ float* v(int c) const { return plane(3 + c); }
+  __host__ __device__ float* C(int c) const { return plane(6 + c); }
+  __host__ __device__ float* F(int c) const { return plane(15 + c); }
+  __host__ __device__ float* tau(int c) const { return plane(24 + c); }
 };
+constexpr int kParticlePlanes = 30;
 
 // Grid node arrays (dense, block-major).
 struct GridArrays {
@@ -214,8 +221,9 @@ struct Polar {
 __device__ __forceinline__ void jacobi_pair(float& app, float& aqq, float& apq, float& arp,
                                             float& arq, float (&V)[9], int p, int q) {
   if (apq == 0.0f) return;
-  const float theta = (aqq - app) / (2.0f * apq);
-  const float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+  // any rotation angle close to the exact one converges; approximate division
+  const float theta = __fdividef(aqq - app, 2.0f * apq);
+  const float t = __fdividef(copysignf(1.0f, theta), fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
   const float c = rsqrtf(fmaf(t, t, 1.0f));
   const float s = t * c;
   app = app - t * apq;
@@ -328,31 +336,9 @@ __device__ __forceinline__ void polar_svd(const float (&F)[9], Polar& P) {
 
 constexpr float kHenckySigmaMin = 1e-4f;
 
-// Kirchhoff stress tau = P(F) F^T (symmetric, 6 entries xx yy zz xy xz yz).
-__device__ __forceinline__ void kirchhoff(const DevGroup& gr, const float (&F)[9], float (&t)[6]) {
-  Polar P;
-  polar_svd(F, P);
-  float d[3];
-  float iso = 0.0f;
-  if (gr.model == MPM_DRUCKER_PRAGER) {
-    // Hencky: tau = U diag(2 mu e + lam tr e) U^T, e = log s
-    float e[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      e[a] = P.s[a] > kHenckySigmaMin ? log1pf(P.sm1[a]) : logf(kHenckySigmaMin);
-    const float tr = e[0] + e[1] + e[2];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = 2.0f * gr.mu_l * e[a] + gr.lam * tr;
-  } else {
-    // fixed corotated: tau = 2 mu (F - R) F^T + lam J (J - 1) I
-    //                      = U diag(2 mu s (s - 1)) U^T + lam J (J - 1) I
-    const float a = P.sm1[0], b = P.sm1[1], c = P.sm1[2];
-    const float jm1 = a + b + c + a * b + a * c + b * c + a * b * c;  // J - 1
-    iso = gr.lam * (1.0f + jm1) * jm1;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = 2.0f * gr.mu_l * P.s[k] * P.sm1[k];
-  }
-  const float* U = P.U;
+// Kirchhoff stress tau = U diag(d) U^T + iso I as 6 entries (xx yy zz xy xz yz).
+__device__ __forceinline__ void tau_from(const float* U, const float (&d)[3], float iso,
+                                         float (&t)[6]) {
   auto ent = [&](int r, int c) {
     return U[3 * r] * d[0] * U[3 * c] + U[3 * r + 1] * d[1] * U[3 * c + 1] +
            U[3 * r + 2] * d[2] * U[3 * c + 2];
@@ -361,12 +347,9 @@ __device__ __forceinline__ void kirchhoff(const DevGroup& gr, const float (&F)[9
   t[3] = ent(0, 1); t[4] = ent(0, 2); t[5] = ent(1, 2);
 }
 
-// Drucker-Prager return map in Hencky strain space (sand); F updated in place.
-__device__ __forceinline__ void dp_project(const DevGroup& gr, float (&F)[9]) {
-  Polar P;
-  polar_svd(F, P);
+// Hencky log strains of the singular values, clamped below at kHenckySigmaMin
+__device__ __forceinline__ bool hencky_strain(const Polar& P, float (&e)[3]) {
   bool clamped = false;
-  float e[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (P.s[a] > kHenckySigmaMin) {
@@ -376,6 +359,57 @@ __device__ __forceinline__ void dp_project(const DevGroup& gr, float (&F)[9]) {
       clamped = true;
     }
   }
+  return clamped;
+}
+
+// Hencky: tau = U diag(2 mu e + lam tr e) U^T
+__device__ __forceinline__ void tau_hencky(const DevGroup& gr, const float* U, const float (&e)[3],
+                                           float (&t)[6]) {
+  const float tr = e[0] + e[1] + e[2];
+  const float d[3] = {2.0f * gr.mu_l * e[0] + gr.lam * tr, 2.0f * gr.mu_l * e[1] + gr.lam * tr,
+                      2.0f * gr.mu_l * e[2] + gr.lam * tr};
+  tau_from(U, d, 0.0f, t);
+}
+
+// fixed corotated: tau = 2 mu (F - R) F^T + lam J (J - 1) I
+//                      = U diag(2 mu s (s - 1)) U^T + lam J (J - 1) I
+__device__ __forceinline__ void tau_corotated(const DevGroup& gr, const Polar& P, float (&t)[6]) {
+  const float a = P.sm1[0], b = P.sm1[1], c = P.sm1[2];
+  const float jm1 = a + b + c + a * b + a * c + b * c + a * b * c;  // J - 1
+  const float d[3] = {2.0f * gr.mu_l * P.s[0] * a, 2.0f * gr.mu_l * P.s[1] * b,
+                      2.0f * gr.mu_l * P.s[2] * c};
+  tau_from(P.U, d, gr.lam * (1.0f + jm1) * jm1, t);
+}
+
+// Kirchhoff stress of a given F (no plastic projection).
+__device__ __forceinline__ void kirchhoff(const DevGroup& gr, const float (&F)[9], float (&t)[6]) {
+  Polar P;
+  polar_svd(F, P);
+  if (gr.model == MPM_DRUCKER_PRAGER) {
+    float e[3];
+    hencky_strain(P, e);
+    tau_hencky(gr, P.U, e, t);
+  } else {
+    tau_corotated(gr, P, t);
+  }
+}
+
+// Constitutive update at the end of G2P: the Drucker-Prager return map in
+// Hencky strain space for sand (F projected in place), then the Kirchhoff
+// stress of the final F for the next P2G. For an unprojected F one SVD serves
+// both; a projected F = U diag(exp e') V^T is rounded to FP32 when stored, so
+// its stress is taken from the stored value (a second SVD) to keep tau equal
+// to the stress of the state F exactly.
+__device__ __forceinline__ void constitutive_update(const DevGroup& gr, float (&F)[9],
+                                                    float (&t)[6]) {
+  Polar P;
+  polar_svd(F, P);
+  if (gr.model != MPM_DRUCKER_PRAGER) {
+    tau_corotated(gr, P, t);
+    return;
+  }
+  float e[3];
+  const bool clamped = hencky_strain(P, e);
   const float tr = e[0] + e[1] + e[2];
   const float eh[3] = {e[0] - tr / 3.0f, e[1] - tr / 3.0f, e[2] - tr / 3.0f};
   const float nh = sqrtf(eh[0] * eh[0] + eh[1] * eh[1] + eh[2] * eh[2]);
@@ -392,16 +426,20 @@ __device__ __forceinline__ void dp_project(const DevGroup& gr, float (&F)[9]) {
       project = true;
     }
   }
-  if (!project && !clamped) return;
-  const float s[3] = {expf(en[0]), expf(en[1]), expf(en[2])};
+  if (!project && !clamped) {
+    tau_hencky(gr, P.U, en, t);
+    return;
+  }
+  const float sv[3] = {expf(en[0]), expf(en[1]), expf(en[2])};
   const float* U = P.U;
   const float* V = P.V;
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      F[3 * r + c] = U[3 * r] * s[0] * V[3 * c] + U[3 * r + 1] * s[1] * V[3 * c + 1] +
-                     U[3 * r + 2] * s[2] * V[3 * c + 2];
+      F[3 * r + c] = U[3 * r] * sv[0] * V[3 * c] + U[3 * r + 1] * sv[1] * V[3 * c + 1] +
+                     U[3 * r + 2] * sv[2] * V[3 * c + 2];
+  kirchhoff(gr, F, t);
 }
 
 // --------------------------------------------------------------------------

@@ -1,12 +1,14 @@
 // g2p.cu -- grid-to-particle transfer with the constitutive update (Sec. V-A
 // op (3), MLS-MPM): v_p = sum_i w v_i, C_p = (4/dx^2) sum_i w v_i (x_i - x_p)^T,
 // x_p += h v_p, F_p <- (I + h C_p) F_p, then the Drucker-Prager return map for
-// sand. One thread per particle; particle planes are read and written with
+// sand, fused with the stress update: the Kirchhoff stress of the new F is
+// stored for the next P2G, so one SVD per particle and substep serves both
+// the plasticity and the stress. One thread per particle; particle planes are read and written with
 // coalesced loads and stores, grid velocities are gathered from L2.
 //
 // Block 0 also closes the substep: it records the contact / active-block
 // counts for diagnostics and resets the per-substep counters, the solve's
-// barrier word and its reduction ring, so the next substep needs no memset.
+// barrier word, so the next substep needs no memset.
 #include "kernels.h"
 
 namespace mpmcr {
@@ -31,11 +33,10 @@ __global__ void __launch_bounds__(kThreads) k_g2p(G2PArgs a) {
       *a.G.pstar2 = 0.0;
       a.bar[0] = 0u;
     }
-    if (threadIdx.x < kRedDoubles) a.red[threadIdx.x] = 0.0;
   }
   const int i = blockIdx.x * kThreads + threadIdx.x;
   if (i >= a.n) return;
-  const float xp[3] = {a.P.x[0][i], a.P.x[1][i], a.P.x[2][i]};
+  const float xp[3] = {a.P.x(0)[i], a.P.x(1)[i], a.P.x(2)[i]};
   Stencil s;
   stencil(g, xp[0], xp[1], xp[2], s);
   if (!stencil_inside(g, s)) return;  // reported by P2G
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(kThreads) k_g2p(G2PArgs a) {
 #pragma unroll
   for (int c = 0; c < 9; ++c) {
     C[c] = dinv * Bm[c];
-    F[c] = a.P.F[c][i];
+    F[c] = a.P.F(c)[i];
   }
 #pragma unroll
   for (int r = 0; r < 3; ++r)
@@ -74,17 +75,20 @@ __global__ void __launch_bounds__(kThreads) k_g2p(G2PArgs a) {
     for (int c = 0; c < 3; ++c)
       Fn[3 * r + c] = F[3 * r + c] + h * (C[3 * r] * F[c] + C[3 * r + 1] * F[3 + c] + C[3 * r + 2] * F[6 + c]);
   const DevGroup gr = a.groups[a.P.grp[i]];
-  if (gr.model == MPM_DRUCKER_PRAGER) dp_project(gr, Fn);
+  float tau[6];
+  constitutive_update(gr, Fn, tau);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    a.P.v[c][i] = vp[c];
-    a.P.x[c][i] = xp[c] + h * vp[c];
+    a.P.v(c)[i] = vp[c];
+    a.P.x(c)[i] = xp[c] + h * vp[c];
   }
 #pragma unroll
   for (int c = 0; c < 9; ++c) {
-    a.P.C[c][i] = C[c];
-    a.P.F[c][i] = Fn[c];
+    a.P.C(c)[i] = C[c];
+    a.P.F(c)[i] = Fn[c];
   }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) a.P.tau(c)[i] = tau[c];
 }
 
 }  // namespace

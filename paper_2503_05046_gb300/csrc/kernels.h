@@ -9,7 +9,7 @@
 
 namespace mpmcr {
 
-constexpr int kRedDoubles = 64;  // reduction ring of the contact solve (4 slots of 16)
+constexpr int kRedDoubles = 4 * 256 * 16;  // contact-solve partial sums: 4 slots x 256 blocks x 16
 
 // Statistics written by the device, read back by mpm_step.
 struct DevStats {
@@ -25,6 +25,9 @@ struct DevStats {
   int last_contacts;     // contacts of the last substep
   int last_active;       // active blocks of the last substep
   int pad[2];
+  // device time of the contact solve's phases (ns, block 0's view):
+  // contact-node list, G, N, line search, impulses
+  unsigned long long solve_ns[5];
 };
 
 // Scratch of the radix sort.
@@ -45,6 +48,8 @@ void launch_to_id_order(const Particles& P, int n, float* out_x, float* out_v, f
                         float* out_F, cudaStream_t s);
 void launch_from_id_order(const Particles& P, int n, const float* in_x, const float* in_v,
                           const float* in_C, const float* in_F, cudaStream_t s);
+// Kirchhoff stress planes from F (after F was set from outside)
+void launch_stress_from_F(const Particles& P, int n, const DevGroup* groups, cudaStream_t s);
 
 // ---- p2g.cu: particle-to-grid with shared-memory tiles + contact registration ----
 struct P2GArgs {
@@ -79,7 +84,7 @@ struct SolveArgs {
   int ls_max_iters;
   double eps_r, eps_a;
   int max_iters;
-  double* red;        // reduction ring [4][16]
+  double* red;        // per-block partial sums [4][256][16]
   unsigned* bar;      // grid barrier words [2]
   uint32_t* status;
   DevStats* stats;

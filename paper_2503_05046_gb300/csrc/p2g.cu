@@ -8,8 +8,12 @@
 // momentum into a shared-memory tile of that box (shared-memory atomics play
 // the role of the paper's warp-level pre-reduction, Sec. V-A). The tile is
 // then flushed with one 16-byte vector reduction (red.global.add.v4.f32) per
-// touched node. A chunk whose box does not fit the tile falls back to direct
-// vector reductions. Particle planes are read with coalesced 4-byte loads.
+// touched node. When the chunk's box exceeds the tile (the Morton order jumps
+// at a coarse cell boundary, or the chunk straddles the edge of the material)
+// each warp uses its own sub-tile of its own box; only a warp whose box is
+// still too large reduces straight into the grid. The Kirchhoff stress comes
+// precomputed from the previous G2P, so no SVD runs here. Particle planes are
+// read with coalesced 4-byte loads.
 #include "kernels.h"
 
 namespace mpmcr {
@@ -18,15 +22,16 @@ namespace {
 
 constexpr int kTileCap = 2048;  // nodes in the shared tile (32 KB)
 constexpr int kThreads = 256;
+constexpr int kWarpTileCap = kTileCap / (kThreads / 32);  // 256 nodes per warp
 
 template <int ITEMS>
-__global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
   __shared__ float t_m[kTileCap], t_px[kTileCap], t_py[kTileCap], t_pz[kTileCap];
   __shared__ DevBody s_body[kMaxBodies];
   __shared__ int s_min[3], s_max[3];
   __shared__ unsigned s_cand;
   const GridDev& g = a.g;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int first = blockIdx.x * kThreads * ITEMS;
 
   if (tid < 3) { s_min[tid] = 0x7fffffff; s_max[tid] = -0x7fffffff; }
@@ -34,16 +39,16 @@ __global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
     reinterpret_cast<float*>(s_body)[i] = reinterpret_cast<const float*>(a.bodies)[i];
   __syncthreads();
 
-  // stencils of this thread's particles and the chunk's bounding box
+  // stencils of this thread's particles; bounding boxes of the warp and chunk
   Stencil st[ITEMS];
   bool valid[ITEMS];
   int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
-    int i = first + it * kThreads + tid;
+    const int i = first + it * kThreads + tid;
     valid[it] = i < a.n;
     if (valid[it]) {
-      stencil(g, a.P.x[0][i], a.P.x[1][i], a.P.x[2][i], st[it]);
+      stencil(g, a.P.x(0)[i], a.P.x(1)[i], a.P.x(2)[i], st[it]);
       if (!stencil_inside(g, st[it])) {
         valid[it] = false;
         atomicOr(a.status, kStOutOfDomain);
@@ -65,38 +70,50 @@ __global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
       hi[c] = max(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
     }
   }
-  if ((tid & 31) == 0) {
+  if (lane == 0) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) { atomicMin(&s_min[c], lo[c]); atomicMax(&s_max[c], hi[c]); }
   }
   __syncthreads();
-  const int b0 = s_min[0], b1 = s_min[1], b2 = s_min[2];
-  const bool any = s_max[0] >= b0;
-  const int ex = any ? s_max[0] - b0 + 3 : 0, ey = any ? s_max[1] - b1 + 3 : 0,
-            ez = any ? s_max[2] - b2 + 3 : 0;
-  const int tile_n = ex * ey * ez;
-  const bool use_tile = any && tile_n <= kTileCap;
-  if (use_tile) {
+  const bool any = s_max[0] >= s_min[0];
+  const int cx0 = s_min[0], cy0 = s_min[1], cz0 = s_min[2];
+  const int cex = any ? s_max[0] - cx0 + 3 : 0, cey = any ? s_max[1] - cy0 + 3 : 0,
+            cez = any ? s_max[2] - cz0 + 3 : 0;
+  const bool block_tile = any && cex * cey * cez <= kTileCap;
+  // the tile this thread accumulates into: the chunk's, or its warp's
+  const bool wany = hi[0] >= lo[0];
+  const int wex = wany ? hi[0] - lo[0] + 3 : 0, wey = wany ? hi[1] - lo[1] + 3 : 0,
+            wez = wany ? hi[2] - lo[2] + 3 : 0;
+  const bool warp_tile = !block_tile && wany && wex * wey * wez <= kWarpTileCap;
+  const bool use_tile = block_tile || warp_tile;
+  const int b0 = block_tile ? cx0 : lo[0], b1 = block_tile ? cy0 : lo[1], b2 = block_tile ? cz0 : lo[2];
+  const int ex = block_tile ? cex : wex, ey = block_tile ? cey : wey, ez = block_tile ? cez : wez;
+  const int toff = block_tile ? 0 : warp * kWarpTileCap;
+  const int tile_n = use_tile ? ex * ey * ez : 0;
+  if (block_tile) {
     for (int t = tid; t < tile_n; t += kThreads) { t_m[t] = 0.f; t_px[t] = 0.f; t_py[t] = 0.f; t_pz[t] = 0.f; }
-  } else if (any && tid == 0) {
-    atomicAdd(&a.stats->p2g_global_chunks, 1);
+  } else if (warp_tile) {
+    for (int t = lane; t < tile_n; t += 32) {
+      t_m[toff + t] = 0.f; t_px[toff + t] = 0.f; t_py[toff + t] = 0.f; t_pz[toff + t] = 0.f;
+    }
   }
+  if (any && !block_tile && tid == 0) atomicAdd(&a.stats->p2g_global_chunks, 1);
   // bodies that may hold a particle of this chunk: the signed distance is
   // 1-Lipschitz, so a body whose distance at the box centre exceeds the half
   // diagonal cannot contain any point of the box
   if (tid < 32) {
     bool cand = false;
     if (any && tid < a.nb) {
-      float c0 = g.ox + g.dx * (0.5f * (b0 + s_max[0]) + 1.0f);
-      float c1 = g.oy + g.dx * (0.5f * (b1 + s_max[1]) + 1.0f);
-      float c2 = g.oz + g.dx * (0.5f * (b2 + s_max[2]) + 1.0f);
-      float h0 = 0.5f * g.dx * (s_max[0] - b0 + 1), h1 = 0.5f * g.dx * (s_max[1] - b1 + 1),
-            h2 = 0.5f * g.dx * (s_max[2] - b2 + 1);
+      const float c0 = g.ox + g.dx * (0.5f * (cx0 + s_max[0]) + 1.0f);
+      const float c1 = g.oy + g.dx * (0.5f * (cy0 + s_max[1]) + 1.0f);
+      const float c2 = g.oz + g.dx * (0.5f * (cz0 + s_max[2]) + 1.0f);
+      const float h0 = 0.5f * g.dx * (s_max[0] - cx0 + 1), h1 = 0.5f * g.dx * (s_max[1] - cy0 + 1),
+                  h2 = 0.5f * g.dx * (s_max[2] - cz0 + 1);
       float nrm[3];
-      float phi = body_sdf(s_body[tid], c0, c1, c2, nrm);
+      const float phi = body_sdf(s_body[tid], c0, c1, c2, nrm);
       cand = phi <= sqrtf(h0 * h0 + h1 * h1 + h2 * h2) * 1.001f + 1e-6f;
     }
-    unsigned m = __ballot_sync(0xffffffffu, cand);
+    const unsigned m = __ballot_sync(0xffffffffu, cand);
     if (tid == 0) s_cand = m;
   }
   __syncthreads();
@@ -110,16 +127,16 @@ __global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
     if (valid[it]) {
       const Stencil& s = st[it];
       const DevGroup gr = a.groups[a.P.grp[i]];
-      float vp[3] = {a.P.v[0][i], a.P.v[1][i], a.P.v[2][i]};
-      float F[9], A[9];
-#pragma unroll
-      for (int c = 0; c < 9; ++c) F[c] = a.P.F[c][i];
+      const float vp[3] = {a.P.v(0)[i], a.P.v(1)[i], a.P.v(2)[i]};
       float tau[6];
-      kirchhoff(gr, F, tau);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) tau[c] = a.P.tau(c)[i];
+      // affine momentum m C - h (4/dx^2) V tau
       const float sc = h * dinv * gr.vol;
       const float tf[9] = {tau[0], tau[3], tau[4], tau[3], tau[1], tau[5], tau[4], tau[5], tau[2]};
+      float A[9];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) A[c] = gr.mass * a.P.C[c][i] - sc * tf[c];
+      for (int c = 0; c < 9; ++c) A[c] = gr.mass * a.P.C(c)[i] - sc * tf[c];
       const float mvx = gr.mass * vp[0], mvy = gr.mass * vp[1], mvz = gr.mass * vp[2];
       if (use_tile) {
         const int l0 = s.base[0] - b0, l1 = s.base[1] - b1, l2 = s.base[2] - b2;
@@ -130,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
           for (int cy = 0; cy < 3; ++cy) {
             const float dy = (cy - s.fx[1]) * g.dx;
             const float wyz = s.w[1][cy] * s.w[2][cz];
-            const int row = ((l2 + cz) * ey + (l1 + cy)) * ex + l0;
+            const int row = toff + ((l2 + cz) * ey + (l1 + cy)) * ex + l0;
 #pragma unroll
             for (int cx = 0; cx < 3; ++cx) {
               const float dxp = (cx - s.fx[0]) * g.dx;
@@ -169,8 +186,8 @@ __global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
           for (int cy = 0; cy < 2; ++cy)
 #pragma unroll
             for (int cx = 0; cx < 2; ++cx) {
-              int bi = (s.base[0] + 2 * cx) >> 2, bj = (s.base[1] + 2 * cy) >> 2,
-                  bk = (s.base[2] + 2 * cz) >> 2;
+              const int bi = (s.base[0] + 2 * cx) >> 2, bj = (s.base[1] + 2 * cy) >> 2,
+                        bk = (s.base[2] + 2 * cz) >> 2;
               a.G.mark[(bk * g.nby + bj) * g.nbx + bi] = 1;
             }
       }
@@ -181,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
       float xp[3] = {0.f, 0.f, 0.f}, vp[3] = {0.f, 0.f, 0.f};
       if (valid[it]) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) { xp[c] = a.P.x[c][i]; vp[c] = a.P.v[c][i]; }
+        for (int c = 0; c < 3; ++c) { xp[c] = a.P.x(c)[i]; vp[c] = a.P.v(c)[i]; }
       }
       for (int b = 0; b < a.nb; ++b) {
         if (!((cand >> b) & 1u)) continue;
@@ -196,7 +213,6 @@ __global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
         const bool hit = valid[it] && phi < 0.0f;
         const unsigned mask = __ballot_sync(0xffffffffu, hit);
         if (mask == 0u) continue;
-        const int lane = tid & 31;
         const int leader = __ffs(mask) - 1;
         int slot0 = 0;
         if (lane == leader) slot0 = atomicAdd(a.C.count, __popc(mask));
@@ -222,24 +238,25 @@ __global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
     }
   }
   __syncthreads();
-  if (use_tile) {
-    // flush: one vector reduction per touched node
-    for (int t = tid; t < tile_n; t += kThreads) {
-      float m = t_m[t];
-      if (m != 0.0f || t_px[t] != 0.0f || t_py[t] != 0.0f || t_pz[t] != 0.0f) {
-        int lx = t % ex, r = t / ex, ly = r % ey, lz = r / ey;
-        int node = node_index(g, b0 + lx, b1 + ly, b2 + lz);
-        red_add_v4(a.G.mp + node, m, t_px[t], t_py[t], t_pz[t]);
-      }
+  if (!use_tile) return;
+  // flush: one vector reduction per touched node of the (chunk or warp) tile
+  const int fstart = block_tile ? tid : lane, fstride = block_tile ? kThreads : 32;
+  for (int t = fstart; t < tile_n; t += fstride) {
+    const int q = toff + t;
+    const float m = t_m[q];
+    if (m != 0.0f || t_px[q] != 0.0f || t_py[q] != 0.0f || t_pz[q] != 0.0f) {
+      const int lx = t % ex, r = t / ex, ly = r % ey, lz = r / ey;
+      const int node = node_index(g, b0 + lx, b1 + ly, b2 + lz);
+      red_add_v4(a.G.mp + node, m, t_px[q], t_py[q], t_pz[q]);
     }
-    // mark the blocks overlapped by the tile
-    int bx0 = b0 >> 2, by0 = b1 >> 2, bz0 = b2 >> 2;
-    int bnx = ((b0 + ex - 1) >> 2) - bx0 + 1, bny = ((b1 + ey - 1) >> 2) - by0 + 1,
-        bnz = ((b2 + ez - 1) >> 2) - bz0 + 1;
-    for (int t = tid; t < bnx * bny * bnz; t += kThreads) {
-      int qx = t % bnx, r = t / bnx, qy = r % bny, qz = r / bny;
-      a.G.mark[((bz0 + qz) * g.nby + (by0 + qy)) * g.nbx + (bx0 + qx)] = 1;
-    }
+  }
+  // mark the 4^3 blocks the tile overlaps
+  const int bx0 = b0 >> 2, by0 = b1 >> 2, bz0 = b2 >> 2;
+  const int bnx = ((b0 + ex - 1) >> 2) - bx0 + 1, bny = ((b1 + ey - 1) >> 2) - by0 + 1,
+            bnz = ((b2 + ez - 1) >> 2) - bz0 + 1;
+  for (int t = fstart; t < bnx * bny * bnz; t += fstride) {
+    const int qx = t % bnx, r = t / bnx, qy = r % bny, qz = r / bny;
+    a.G.mark[((bz0 + qz) * g.nby + (by0 + qy)) * g.nbx + (bx0 + qx)] = 1;
   }
 }
 
@@ -247,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_p2g(P2GArgs a) {
 
 void launch_p2g(const P2GArgs& a, int chunk, cudaStream_t s) {
   if (a.n <= 0) return;
-  int items = chunk / kThreads;
+  const int items = chunk / kThreads;
   if (items <= 1) {
     k_p2g<1><<<(a.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
   } else if (items == 2) {

@@ -37,10 +37,17 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kContactsPerBlock = 128;
+constexpr int kContactsPerBlock = 64;
 constexpr int kLsPoints = 8;
-constexpr int kRedWidth = 16;              // doubles per reduction slot
+constexpr int kRedWidth = 16;              // doubles per block and reduction
+constexpr int kMaxSolveBlocks = 256;
 constexpr unsigned kSpinLimit = 1u << 24;  // ~1 s of polling with the back-off below
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -55,14 +62,19 @@ struct Barrier {
   uint32_t* status;
 };
 
-// Returns false if any block gave up waiting (the caller then returns).
+// Device-wide barrier of the participating blocks. Thread 0 publishes its
+// block's writes (fence), arrives, and the last arriver releases the next
+// generation; the others spin with an iteration limit and return false on
+// expiry (the caller then returns; the other blocks expire at their next
+// barrier). A single participating block needs only __syncthreads.
 __device__ bool grid_sync(Barrier& B) {
-  __shared__ int s_ok;
   __syncthreads();
+  if (B.n == 1) return true;
+  __shared__ int s_ok;
   if (threadIdx.x == 0) {
     int ok = 1;
     __threadfence();
-    unsigned arrived = atomicAdd(&B.bar[0], 1u);
+    const unsigned arrived = atomicAdd(&B.bar[0], 1u);
     if (arrived == B.n - 1) {
       atomicExch(&B.bar[0], 0u);
       __threadfence();
@@ -75,39 +87,76 @@ __device__ bool grid_sync(Barrier& B) {
           ok = 0;
           break;
         }
-        __nanosleep(32);
+        __nanosleep(20);
       }
+      __threadfence();
     }
     B.gen += 1u;
-    __threadfence();
-    if (*reinterpret_cast<volatile uint32_t*>(B.status) & kStTimeout) ok = 0;
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
 }
 
+// Block sums of NV per-thread values, exchanged through per-block slots and
+// summed by every block in the same fixed order (deterministic). Returns the
+// totals in s_tot (shared) and false if the barrier expired.
 template <int NV>
-__device__ void block_reduce_add(float (&v)[NV], double* dst, double (*s_red)[kRedWidth]) {
+__device__ bool reduce_all(const float (&v)[NV], double* part, Barrier& B, float (*s_red)[kRedWidth],
+                           double* s_tot) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     float x = v[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) s_red[w][i] = (double)x;
+    if (lane == 0) s_red[w][i] = x;
   }
   __syncthreads();
-  if (w == 0) {
+  if (w == 0 && lane < NV) {
+    float x = 0.f;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      double x = lane < kWarps ? s_red[lane][i] : 0.0;
+    for (int k = 0; k < kWarps; ++k) x += s_red[k][lane];
+    if (B.n == 1)
+      s_tot[lane] = (double)x;
+    else
+      part[blockIdx.x * kRedWidth + lane] = (double)x;
+  }
+  if (!grid_sync(B)) return false;
+  if (B.n > 1) {
+    if (w == 0) {
+      if (B.n <= 32) {
+        // lane i sums value i over the blocks, in block order
+        if (lane < NV) {
+          double x = 0.0;
+          for (int b = 0; b < (int)B.n; ++b) x += __ldcg(part + b * kRedWidth + lane);
+          s_tot[lane] = x;
+        }
+      } else {
+        double acc[NV];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0 && x != 0.0) atomicAdd(dst + i, x);
+        for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+        for (int b = lane; b < (int)B.n; b += 32) {
+          const double2* q = reinterpret_cast<const double2*>(part + b * kRedWidth);
+#pragma unroll
+          for (int i = 0; i < NV / 2; ++i) {
+            const double2 d = __ldcg(q + i);
+            acc[2 * i] += d.x;
+            acc[2 * i + 1] += d.y;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+          double x = acc[i];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+          if (lane == 0) s_tot[i] = x;
+        }
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
+  return true;
 }
 
 __device__ __forceinline__ void gather(const GridDev& g, const float4* __restrict__ f,
@@ -163,6 +212,45 @@ __device__ __forceinline__ void gather_dd(const GridDev& g, const float4* __rest
   for (int c = 0; c < 3; ++c) out[c] = cs[c].value();
 }
 
+// Warp-cooperative stencil access: lane l < 27 owns node (l % 3, l / 3 % 3, l / 9)
+// of the contact's 3x3x3 stencil, so the 27 loads or reductions of a contact
+// go out together instead of in register-limited groups.
+struct LaneNode {
+  int node;
+  float w;
+};
+
+__device__ __forceinline__ LaneNode lane_node(const GridDev& g, const float4& xp, int lane) {
+  Stencil s;
+  stencil(g, xp.x, xp.y, xp.z, s);
+  const int l = lane < 27 ? lane : 0;
+  const int cx = l % 3, cy = (l / 3) % 3, cz = l / 9;
+  LaneNode r;
+  r.node = node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz);
+  r.w = lane < 27 ? s.w[0][cx] * s.w[1][cy] * s.w[2][cz] : 0.f;
+  return r;
+}
+
+// compensated warp sum of (S, E) pairs; the total is returned in every lane
+__device__ __forceinline__ float warp_comp_sum(float S, float E) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float S2 = __shfl_xor_sync(0xffffffffu, S, o);
+    const float E2 = __shfl_xor_sync(0xffffffffu, E, o);
+    float s, e;
+    two_sum(S, S2, s, e);
+    S = s;
+    E = E + E2 + e;
+  }
+  return S + E;
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
 __device__ __forceinline__ void load_contact(const Contacts& C, int p, float4& xp, float (&n)[3],
                                              float& n0) {
   xp = C.xp[p];
@@ -171,11 +259,12 @@ __device__ __forceinline__ void load_contact(const Contacts& C, int p, float4& x
   n0 = q.w;
 }
 
-// contact part of f'(alpha_k), k < kLsPoints, for this thread's contacts
+// contact parts of f'(alpha_k) and f''(alpha_k), k < kLsPoints, for this
+// thread's contacts (acc[k] and acc[kLsPoints + k])
 __device__ __forceinline__ void ls_contact(const SolveArgs& a, const DevBody& bd, const float4& xp,
                                            const float (&n)[3], float n0, const float4& vc,
                                            const float (&e)[3], const float (&alphas)[kLsPoints],
-                                           float (&acc)[kLsPoints]) {
+                                           float (&acc)[2 * kLsPoints]) {
 #pragma unroll
   for (int k = 0; k < kLsPoints; ++k) {
     const float al = alphas[k];
@@ -185,19 +274,79 @@ __device__ __forceinline__ void ls_contact(const SolveArgs& a, const DevBody& bd
     float d1, d2;
     contact_dir(L, n, e, d1, d2);
     acc[k] += d1;
+    acc[kLsPoints + k] += d2;
   }
 }
 
+// Exact line search of Alg. 1 on f'(alpha) = B + alpha A + sum_p dl_c . dv_c,
+// which is continuous and non-decreasing (f convex). Each pass has f' and f''
+// at 8 points; the bracket [lo, hi] keeps f'(lo) < 0 <= f'(hi). The first
+// pass is 0 and a doubling grid (extended by further doublings while f' < 0);
+// later passes evaluate the Newton step from the best point, the secant of
+// the bracket and six evenly spaced points (the bracket shrinks at least
+// sevenfold). Stops when |f'(best)| <= rel_tol |f'(0)|. Thread-0 state.
+struct LineSearch {
+  enum { kMore = 0, kDone = 1, kFailed = 2 };
+  float lo, hi, flo, fhi, best, fbest, f2best, f0;
+  bool have_f0;
+  float pts[kLsPoints];
+  __device__ void reset() {
+    lo = 0.f; hi = -1.f; flo = fhi = best = fbest = f2best = f0 = 0.f;
+    have_f0 = false;
+  }
+  // FP64 only to form f' = B + alpha A + S (its terms can cancel); the
+  // bracket logic runs in FP32 (alpha is applied in FP32 anyway)
+  __device__ int update(const double* tot, double A, double B, float rel_tol, bool last) {
+    for (int k = 0; k < kLsPoints; ++k) {
+      const float x = pts[k];
+      const float d = (float)(B + (double)x * A + tot[k]);
+      const float d2 = (float)(A + tot[kLsPoints + k]);
+      if (!have_f0 && x == 0.f) {
+        f0 = d; have_f0 = true; flo = d; best = 0.f; fbest = d; f2best = d2;
+      }
+      if (d < 0.f) {
+        if (x >= lo) { lo = x; flo = d; }
+      } else if (hi < 0.f || x < hi) {
+        hi = x; fhi = d;
+      }
+      if (fabsf(d) < fabsf(fbest)) { best = x; fbest = d; f2best = d2; }
+    }
+    if (!(f0 < 0.f)) { best = 0.f; return kDone; }  // no descent left at working precision
+    if (fabsf(fbest) <= rel_tol * fabsf(f0) || last) return kDone;
+    if (hi < 0.f) {  // root beyond the grid: keep doubling
+      if (lo >= 1024.f) { best = lo; return kFailed; }
+      for (int k = 0; k < kLsPoints; ++k) pts[k] = lo * (float)(2 << k);
+      return kMore;
+    }
+    if (hi - lo <= 1e-7f * hi) return kDone;
+    const float w = hi - lo;
+    float xn = f2best > 0.f ? best - fbest / f2best : 0.5f * (lo + hi);
+    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
+    float xs = lo - flo * w / (fhi - flo);
+    if (!(xs > lo && xs < hi)) xs = 0.5f * (lo + hi);
+    pts[0] = xn;
+    pts[1] = xs;
+    for (int k = 2; k < kLsPoints; ++k) pts[k] = lo + w * (float)(k - 1) / 7.0f;
+    return kMore;
+  }
+};
+
 __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   __shared__ DevBody s_body[kMaxBodies];
-  __shared__ double s_red[kWarps][kRedWidth];
+  __shared__ float s_red[kWarps][kRedWidth];
+  __shared__ double s_tot[kRedWidth];
   __shared__ float s_imp[kMaxBodies][6];
+  __shared__ float s_pts[kLsPoints];
+  __shared__ double s_A, s_B, s_alpha;
+  __shared__ int s_dec;
+  LineSearch ls;  // used by thread 0
   const int tid = threadIdx.x;
   const int count = *a.C.count;
   const int nc = count < a.C.cap ? count : a.C.cap;
   if (nc == 0) return;  // v = v* already (set by the grid update)
   int nblk = (nc + kContactsPerBlock - 1) / kContactsPerBlock;
   nblk = nblk < (int)gridDim.x ? nblk : (int)gridDim.x;
+  nblk = nblk < kMaxSolveBlocks ? nblk : kMaxSolveBlocks;
   if ((int)blockIdx.x >= nblk) return;  // not needed for this many contacts
 
   for (int i = tid; i < a.nb * (int)(sizeof(DevBody) / 4); i += kThreads)
@@ -205,15 +354,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   for (int i = tid; i < kMaxBodies * 6; i += kThreads) (&s_imp[0][0])[i] = 0.f;
   __syncthreads();
 
+  // phase timers (block 0, thread 0): list, G, N, line search, impulses
+  unsigned long long tph[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
+  unsigned long long tmark = global_ns();
+  auto lap = [&](int ph) {
+    if (blockIdx.x == 0 && tid == 0) {
+      const unsigned long long now = global_ns();
+      tph[ph] += now - tmark;
+      tmark = now;
+    }
+  };
   Barrier B{a.bar, (unsigned)nblk, 0u, a.status};
   if (tid == 0) B.gen = ld_acquire(&a.bar[1]);
   const int gtid = blockIdx.x * kThreads + tid;
   const int gstride = nblk * kThreads;
+  const int lane = tid & 31;
+  const int gwarp = gtid >> 5;
+  const int nwarps = gstride >> 5;
   const GridDev& g = a.g;
+  // per-block partial sums, a ring of 4 slots of kMaxSolveBlocks x kRedWidth;
+  // a slot is rewritten two reductions later, after every block has read it
   int rslot = 0;
   auto next_slot = [&]() -> double* {
-    double* s = a.red + kRedWidth * (rslot & 3);
-    if (blockIdx.x == 0 && tid < kRedWidth) a.red[kRedWidth * ((rslot + 2) & 3) + tid] = 0.0;
+    double* s = a.red + (size_t)(rslot & 3) * kMaxSolveBlocks * kRedWidth;
     ++rslot;
     return s;
   };
@@ -223,16 +386,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     const float4 xp = a.C.xp[p];
     Stencil s;
     stencil(g, xp.x, xp.y, xp.z, s);
-#pragma unroll 1
+    int node[27];
+    unsigned won = 0u;  // 27 bits: this thread claimed the node first
+#pragma unroll
     for (int c = 0; c < 27; ++c) {
-      const int node = node_index(g, s.base[0] + c % 3, s.base[1] + (c / 3) % 3, s.base[2] + c / 9);
-      if (atomicExch(a.G.cflag + node, 1) == 0) {
-        const int slot = atomicAdd(a.G.n_cnodes, 1);
-        if (slot < a.G.cnodes_cap) a.G.cnodes[slot] = node;
-      }
+      node[c] = node_index(g, s.base[0] + c % 3, s.base[1] + (c / 3) % 3, s.base[2] + c / 9);
+      if (atomicExch(a.G.cflag + node[c], 1) == 0) won |= 1u << c;
+    }
+    if (won) {
+      int slot = atomicAdd(a.G.n_cnodes, __popc(won));
+#pragma unroll
+      for (int c = 0; c < 27; ++c)
+        if ((won >> c) & 1u) {
+          if (slot < a.G.cnodes_cap) a.G.cnodes[slot] = node[c];
+          ++slot;
+        }
     }
   }
   if (!grid_sync(B)) return;
+  lap(0);
   int ncn = __ldcg(a.G.n_cnodes);
   ncn = ncn < a.G.cnodes_cap ? ncn : a.G.cnodes_cap;
   const double pstar2 = __ldcg(a.G.pstar2);
@@ -250,37 +422,54 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   int it = 0, ls_passes = 0;
   float resid = 0.f;
   for (;;) {
-    // ---- G: step by alpha, contact gradient / Hessian blocks
+    // ---- G: step by alpha, contact gradient / Hessian blocks (warp per contact)
     const float al = (float)alpha;
-    for (int p = gtid; p < nc; p += gstride) {
+    for (int p = gwarp; p < nc; p += nwarps) {
       float4 xp; float n[3]; float n0;
       load_contact(a.C, p, xp, n, n0);
+      const LaneNode ln = lane_node(g, xp, lane);
       float u[3];
-      const float4 dvc = it > 0 ? a.C.dvc[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-      gather_dd(g, vcur, lcur, xp, a.C.bias[p], al, dvc, u);
-      a.C.vc[p] = make_float4(u[0], u[1], u[2], 0.f);
+      {
+        const float4 h = __ldcg(vcur + ln.node);
+        const float4 l = __ldcg(lcur + ln.node);
+        const float hv[3] = {h.x, h.y, h.z}, lv[3] = {l.x, l.y, l.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          // exact product w*hi as (p, pe), plus the low part
+          const float pr = ln.w * hv[c];
+          const float pe = fmaf(ln.w, hv[c], -pr) + ln.w * lv[c];
+          u[c] = warp_comp_sum(pr, pe);
+        }
+      }
+      if (lane == 0) {
+        // + b + alpha J dv, compensated
+        const float4 bb = a.C.bias[p];
+        const float4 dvc = it > 0 ? a.C.dvc[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float bv[3] = {bb.x, bb.y, bb.z}, dv3[3] = {dvc.x, dvc.y, dvc.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          CompSum cs;
+          cs.S = u[c];
+          cs.add(bv[c]);
+          cs.add_prod(al, dv3[c]);
+          u[c] = cs.value();
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u[c] = __shfl_sync(0xffffffffu, u[c], 0);
+      if (lane == 0) a.C.vc[p] = make_float4(u[0], u[1], u[2], 0.f);
       const DevBody& bd = s_body[a.C.id[p].y];
       ContactLaw L;
       contact_law(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, L);
       float gr[3], H[6];
       contact_grad(L, n, gr);
       contact_hess(L, n, H);
-      Stencil s;
-      stencil(g, xp.x, xp.y, xp.z, s);
-#pragma unroll
-      for (int cz = 0; cz < 3; ++cz)
-#pragma unroll
-        for (int cy = 0; cy < 3; ++cy) {
-          const float wyz = s.w[1][cy] * s.w[2][cz];
-#pragma unroll
-          for (int cx = 0; cx < 3; ++cx) {
-            const float w = s.w[0][cx] * wyz, w2 = w * w;
-            const int node = node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz);
-            red_add_v4(a.G.acc0 + node, w * gr[0], w * gr[1], w * gr[2], w2 * H[0]);
-            red_add_v4(a.G.acc1 + node, w2 * H[1], w2 * H[2], w2 * H[3], w2 * H[4]);
-            red_add_f32(a.G.acc2 + node, w2 * H[5]);
-          }
-        }
+      if (lane < 27) {
+        const float w = ln.w, w2 = w * w;
+        red_add_v4(a.G.acc0 + ln.node, w * gr[0], w * gr[1], w * gr[2], w2 * H[0]);
+        red_add_v4(a.G.acc1 + ln.node, w2 * H[1], w2 * H[2], w2 * H[3], w2 * H[4]);
+        red_add_f32(a.G.acc2 + ln.node, w2 * H[5]);
+      }
     }
     if (it > 0) {
       for (int t = gtid; t < ncn; t += gstride) {
@@ -298,6 +487,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
       t = lcur; lcur = lnxt; lnxt = t;
     }
     if (!grid_sync(B)) return;
+    lap(1);
 
     // ---- N: gradient, stopping norms, direction, grid line-search sums
     double* slot = next_slot();
@@ -345,94 +535,84 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
         }
         a.G.dv[node] = dv;
       }
-      block_reduce_add(acc, slot, s_red);
+      float acc6[6] = {acc[0], acc[1], acc[2], acc[3], acc[4], 0.f};
+      if (!reduce_all(acc6, slot, B, s_red, s_tot)) return;
+    }
+    lap(2);
+    // stopping test (Alg. 1). The scalar logic runs in thread 0 of each block
+    // (FP64 is a narrow pipe on GB300) and the decision is broadcast; every
+    // block computes it from the same totals, so all decide alike.
+    if (tid == 0) {
+      const double A = s_tot[3], Bs = s_tot[4];
+      const float G2 = (float)s_tot[0], P2 = (float)(pstar2 + s_tot[1]), J2 = (float)s_tot[2];
+      const float Gn = sqrtf(G2), Pn = sqrtf(fmaxf(P2, 0.f)), Jn = sqrtf(J2);
+      const float mx = fmaxf(Pn, Jn);
+      resid = mx > 0.f ? Gn / mx : 0.f;
+      int dec = 0;
+      if (!(G2 == G2) || !(A == A) || !(Bs == Bs)) {
+        if (blockIdx.x == 0) atomicOr(a.status, kStNan);
+        dec = 1;
+      } else if ((double)Gn < a.eps_a + a.eps_r * (double)mx || G2 == 0.f) {
+        dec = 1;  // converged
+      } else if (it >= a.max_iters) {
+        if (blockIdx.x == 0) atomicOr(a.status, kStNotConverged);
+        dec = 1;
+      }
+      s_dec = dec;
+      s_A = A;
+      s_B = Bs;
+      // line-search state, first pass: 0 and a doubling grid 1/8 .. 8
+      ls.reset();
+      ls.pts[0] = 0.f;
+      s_pts[0] = 0.f;
+      for (int k = 1; k < kLsPoints; ++k) {
+        ls.pts[k] = (float)(1 << (k - 1)) * 0.125f;
+        s_pts[k] = ls.pts[k];
+      }
+    }
+    __syncthreads();
+    if (s_dec) break;
+
+    // ---- C: dv_c = J dv (warp per contact)
+    for (int p = gwarp; p < nc; p += nwarps) {
+      const float4 xp = a.C.xp[p];
+      const LaneNode ln = lane_node(g, xp, lane);
+      const float4 d = __ldcg(a.G.dv + ln.node);
+      const float e0 = warp_sum(ln.w * d.x), e1 = warp_sum(ln.w * d.y), e2 = warp_sum(ln.w * d.z);
+      if (lane == 0) a.C.dvc[p] = make_float4(e0, e1, e2, 0.f);
     }
     if (!grid_sync(B)) return;
-    const double G2 = __ldcg(slot + 0), P2 = pstar2 + __ldcg(slot + 1), J2 = __ldcg(slot + 2);
-    const double A = __ldcg(slot + 3), Bs = __ldcg(slot + 4);
-    const double Gn = sqrt(G2), Pn = sqrt(fmax(P2, 0.0)), Jn = sqrt(J2);
-    const double mx = Pn > Jn ? Pn : Jn;
-    resid = mx > 0.0 ? (float)(Gn / mx) : 0.f;
-    if (!(G2 == G2) || !(A == A) || !(Bs == Bs)) {
-      if (gtid == 0) atomicOr(a.status, kStNan);
-      break;
-    }
-    if (Gn < a.eps_a + a.eps_r * mx || G2 == 0.0) break;  // converged
-    if (it >= a.max_iters) {
-      if (gtid == 0) atomicOr(a.status, kStNotConverged);
-      break;
-    }
-
-    // ---- C + L: dv_c = J dv, then line-search passes of 8 points each
-    double lo = 0.0, hi = -1.0, flo = 0.0, fhi = 0.0, best = 0.0, fbest = 0.0, f0 = 0.0;
-    double pts[kLsPoints];
-    bool failed = false, have_f0 = false;
-    // first pass: 0 and a doubling grid 1/8 .. 8; later passes: see below
-    pts[0] = 0.0;
-    for (int k = 1; k < kLsPoints; ++k) pts[k] = (double)(1 << (k - 1)) * 0.125;
+    // ---- L: line-search passes of 8 points each (thread per contact)
     for (int pass = 0;; ++pass) {
       double* sl = next_slot();
       float alphas[kLsPoints];
 #pragma unroll
-      for (int k = 0; k < kLsPoints; ++k) alphas[k] = (float)pts[k];
-      float acc[kLsPoints];
+      for (int k = 0; k < kLsPoints; ++k) alphas[k] = s_pts[k];
+      float acc[2 * kLsPoints];
 #pragma unroll
-      for (int k = 0; k < kLsPoints; ++k) acc[k] = 0.f;
+      for (int k = 0; k < 2 * kLsPoints; ++k) acc[k] = 0.f;
       for (int p = gtid; p < nc; p += gstride) {
         float4 xp; float n[3]; float n0;
         load_contact(a.C, p, xp, n, n0);
-        float e[3];
-        if (pass == 0) {
-          gather(g, a.G.dv, xp, e);
-          a.C.dvc[p] = make_float4(e[0], e[1], e[2], 0.f);
-        } else {
-          const float4 q = a.C.dvc[p];
-          e[0] = q.x; e[1] = q.y; e[2] = q.z;
-        }
-        ls_contact(a, s_body[a.C.id[p].y], xp, n, n0, a.C.vc[p], e, alphas, acc);
+        const float4 q = __ldcg(a.C.dvc + p);
+        const float e[3] = {q.x, q.y, q.z};
+        // v_c was written by another warp in phase G: read it from L2
+        ls_contact(a, s_body[a.C.id[p].y], xp, n, n0, __ldcg(a.C.vc + p), e, alphas, acc);
       }
-      block_reduce_add(acc, sl, s_red);
-      if (!grid_sync(B)) return;
+      if (!reduce_all(acc, sl, B, s_red, s_tot)) return;
+      lap(3);
       ++ls_passes;
-      // f'(alpha_k) for the evaluated points, merged into the bracket
-      for (int k = 0; k < kLsPoints; ++k) {
-        const double x = pts[k];
-        const double d = Bs + x * A + __ldcg(sl + k);
-        if (!have_f0 && x == 0.0) { f0 = d; have_f0 = true; flo = d; best = 0.0; fbest = d; }
-        if (d < 0.0) {
-          if (x >= lo) { lo = x; flo = d; }
-        } else if (hi < 0.0 || x < hi) {
-          hi = x; fhi = d;
-        }
-        if (fabs(d) < fabs(fbest)) { best = x; fbest = d; }
+      if (tid == 0) {
+        const int st = ls.update(s_tot, s_A, s_B, a.ls_rel_tol, pass + 1 >= a.ls_max_iters);
+        if (st == LineSearch::kFailed && blockIdx.x == 0) atomicOr(a.status, kStLineSearch);
+        s_dec = st != LineSearch::kMore;
+        s_alpha = ls.best;
+        for (int k = 0; k < kLsPoints; ++k) s_pts[k] = ls.pts[k];
       }
-      if (!(f0 < 0.0)) { best = 0.0; break; }  // no descent left at working precision
-      const double tol = (double)a.ls_rel_tol * fabs(f0);
-      if (fabs(fbest) <= tol) break;
-      if (pass + 1 >= a.ls_max_iters) break;
-      if (hi < 0.0) {  // root beyond the grid: keep doubling
-        if (lo >= 1024.0) { failed = true; break; }
-        for (int k = 0; k < kLsPoints; ++k) pts[k] = lo * (double)(2 << k);
-        continue;
-      }
-      if (hi - lo <= 1e-12 * hi) break;
-      // secant estimate inside [lo, hi] and a cluster of points around it
-      const double w = hi - lo;
-      double sx = lo - flo * w / (fhi - flo);
-      if (!(sx > lo && sx < hi)) sx = 0.5 * (lo + hi);
-      const double off[kLsPoints] = {0.0, -1e-1, 1e-1, -1e-2, 1e-2, -1e-3, 1e-3, 0.0};
-      for (int k = 0; k < kLsPoints; ++k) {
-        double x = sx + off[k] * w;
-        if (k == kLsPoints - 1) x = 0.5 * (lo + hi);  // bisection point
-        if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
-        pts[k] = x;
-      }
+      __syncthreads();
+      if (s_dec) break;
     }
-    if (failed) {
-      if (gtid == 0) atomicOr(a.status, kStLineSearch);
-      best = lo;
-    }
-    alpha = best;
+    alpha = s_alpha;
     ++it;
     if (alpha == 0.0) break;  // no further progress possible at this precision
   }
@@ -450,7 +630,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     load_contact(a.C, p, xp, n, n0);
     const int b = a.C.id[p].y;
     const DevBody& bd = s_body[b];
-    const float4 vc = a.C.vc[p];
+    const float4 vc = __ldcg(a.C.vc + p);
     const float u[3] = {vc.x, vc.y, vc.z};
     ContactLaw L;
     contact_law(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, L);
@@ -470,7 +650,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     const float v = (&s_imp[0][0])[i];
     if (v != 0.f) atomicAdd(a.impulses + i, (double)v);
   }
+  lap(4);
   if (gtid == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) atomicAdd(&a.stats->solve_ns[k], tph[k]);
     atomicAdd(&a.stats->iters_total, it);
     atomicMax(&a.stats->iters_max, it);
     atomicAdd(&a.stats->ls_evals_total, ls_passes);

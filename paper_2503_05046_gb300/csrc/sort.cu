@@ -173,14 +173,16 @@ __global__ void k_permute(Particles src, Particles dst, const uint32_t* __restri
   uint32_t j = perm[i];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    dst.x[c][i] = src.x[c][j];
-    dst.v[c][i] = src.v[c][j];
+    dst.x(c)[i] = src.x(c)[j];
+    dst.v(c)[i] = src.v(c)[j];
   }
 #pragma unroll
   for (int c = 0; c < 9; ++c) {
-    dst.C[c][i] = src.C[c][j];
-    dst.F[c][i] = src.F[c][j];
+    dst.C(c)[i] = src.C(c)[j];
+    dst.F(c)[i] = src.F(c)[j];
   }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) dst.tau(c)[i] = src.tau(c)[j];
   dst.pid[i] = src.pid[j];
   dst.grp[i] = src.grp[j];
 }
@@ -191,13 +193,13 @@ __global__ void k_to_id(Particles P, int n, float* __restrict__ ox, float* __res
   if (i >= n) return;
   size_t id = P.pid[i];
   if (ox)
-    for (int c = 0; c < 3; ++c) ox[3 * id + c] = P.x[c][i];
+    for (int c = 0; c < 3; ++c) ox[3 * id + c] = P.x(c)[i];
   if (ov)
-    for (int c = 0; c < 3; ++c) ov[3 * id + c] = P.v[c][i];
+    for (int c = 0; c < 3; ++c) ov[3 * id + c] = P.v(c)[i];
   if (oC)
-    for (int c = 0; c < 9; ++c) oC[9 * id + c] = P.C[c][i];
+    for (int c = 0; c < 9; ++c) oC[9 * id + c] = P.C(c)[i];
   if (oF)
-    for (int c = 0; c < 9; ++c) oF[9 * id + c] = P.F[c][i];
+    for (int c = 0; c < 9; ++c) oF[9 * id + c] = P.F(c)[i];
 }
 
 __global__ void k_from_id(Particles P, int n, const float* __restrict__ ix,
@@ -207,13 +209,24 @@ __global__ void k_from_id(Particles P, int n, const float* __restrict__ ix,
   if (i >= n) return;
   size_t id = P.pid[i];
   if (ix)
-    for (int c = 0; c < 3; ++c) P.x[c][i] = ix[3 * id + c];
+    for (int c = 0; c < 3; ++c) P.x(c)[i] = ix[3 * id + c];
   if (iv)
-    for (int c = 0; c < 3; ++c) P.v[c][i] = iv[3 * id + c];
+    for (int c = 0; c < 3; ++c) P.v(c)[i] = iv[3 * id + c];
   if (iC)
-    for (int c = 0; c < 9; ++c) P.C[c][i] = iC[9 * id + c];
+    for (int c = 0; c < 9; ++c) P.C(c)[i] = iC[9 * id + c];
   if (iF)
-    for (int c = 0; c < 9; ++c) P.F[c][i] = iF[9 * id + c];
+    for (int c = 0; c < 9; ++c) P.F(c)[i] = iF[9 * id + c];
+}
+
+__global__ void k_stress(Particles P, int n, const DevGroup* __restrict__ groups) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float F[9], t[6];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) F[c] = P.F(c)[i];
+  kirchhoff(groups[P.grp[i]], F, t);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) P.tau(c)[i] = t[c];
 }
 
 void exclusive_scan(uint32_t* data, int len, uint32_t* partial, cudaStream_t s) {
@@ -234,7 +247,7 @@ void launch_sort(const GridDev& g, const Particles& src, const Particles& dst, i
                  SortBuffers& sb, cudaStream_t s) {
   if (n <= 0) return;
   int tpb = 256;
-  k_keys<<<(n + tpb - 1) / tpb, tpb, 0, s>>>(g, src.x[0], src.x[1], src.x[2], n, sb.keys[0],
+  k_keys<<<(n + tpb - 1) / tpb, tpb, 0, s>>>(g, src.x(0), src.x(1), src.x(2), n, sb.keys[0],
                                             sb.vals[0]);
   int key_bits = 3 * g.morton_bits;
   int passes = (key_bits + 7) / 8;
@@ -264,4 +277,11 @@ void launch_from_id_order(const Particles& P, int n, const float* ix, const floa
   k_from_id<<<(n + 255) / 256, 256, 0, s>>>(P, n, ix, iv, iC, iF);
 }
 
+}  // namespace mpmcr
+
+namespace mpmcr {
+void launch_stress_from_F(const Particles& P, int n, const DevGroup* groups, cudaStream_t s) {
+  if (n <= 0) return;
+  k_stress<<<(n + 255) / 256, 256, 0, s>>>(P, n, groups);
+}
 }  // namespace mpmcr
