@@ -44,7 +44,7 @@ struct mpm_ctx {
   float* stage = nullptr;  // 24 floats per particle
   bool profile = false;
   int sort_every = 1;
-  int p2g_chunk = 256;
+  int p2g_chunk = 512;
   int64_t step_count = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, cudaEvent_t>> ev_marks;  // (phase starting at this event, event)
@@ -288,6 +288,7 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
   int mb = g.nbx > g.nby ? g.nbx : g.nby;
   mb = mb > g.nbz ? mb : g.nbz;
   g.morton_bits = ceil_log2(mb) > 0 ? ceil_log2(mb) : 1;
+  g.sort_cell_bits = 3 * g.morton_bits + 6 <= 32 ? 1 : 0;
   ctx->cap = spec->max_particles;
   ctx->n_blocks = g.nbx * g.nby * g.nbz;
   ctx->n_nodes = (size_t)ctx->n_blocks * kBlockNodes;

@@ -34,6 +34,7 @@ struct GridDev {
   int nbx, nby, nbz;      // 4^3 blocks per axis
   int bc;                 // Dirichlet layers
   int morton_bits;        // bits per axis of the block sort key
+  int sort_cell_bits;     // 1: the sort key also orders cells within a block
 };
 
 // Rigid body frozen for a time step (Eq. (3)-(4)); 32 words.

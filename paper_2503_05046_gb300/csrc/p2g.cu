@@ -5,8 +5,10 @@
 //
 // GB300 layout: each thread block takes a contiguous chunk of block-sorted
 // particles, finds the bounding box of their stencils and accumulates mass and
-// momentum into a shared-memory tile of that box (shared-memory atomics play
-// the role of the paper's warp-level pre-reduction, Sec. V-A). The tile is
+// momentum into a shared-memory tile of that box. Lanes of a warp whose
+// particles share a base cell first combine their contributions with a
+// segmented shuffle reduction (the warp-level pre-reduction of Sec. V-A), so
+// one shared-memory atomic per node and run is issued. The tile is
 // then flushed with one 16-byte vector reduction (red.global.add.v4.f32) per
 // touched node. When the chunk's box exceeds the tile (the Morton order jumps
 // at a coarse cell boundary, or the chunk straddles the edge of the material)
@@ -40,7 +42,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
   __syncthreads();
 
   // stencils of this thread's particles; bounding boxes of the warp and chunk
-  Stencil st[ITEMS];
+  // (the stencils are recomputed below rather than held in registers)
   bool valid[ITEMS];
   int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
 #pragma unroll
@@ -48,17 +50,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
     const int i = first + it * kThreads + tid;
     valid[it] = i < a.n;
     if (valid[it]) {
-      stencil(g, a.P.x(0)[i], a.P.x(1)[i], a.P.x(2)[i], st[it]);
-      if (!stencil_inside(g, st[it])) {
+      Stencil st;
+      stencil(g, a.P.x(0)[i], a.P.x(1)[i], a.P.x(2)[i], st);
+      if (!stencil_inside(g, st)) {
         valid[it] = false;
         atomicOr(a.status, kStOutOfDomain);
-      }
-    }
-    if (valid[it]) {
+      } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        lo[c] = min(lo[c], st[it].base[c]);
-        hi[c] = max(hi[c], st[it].base[c]);
+        for (int c = 0; c < 3; ++c) {
+          lo[c] = min(lo[c], st.base[c]);
+          hi[c] = max(hi[c], st.base[c]);
+        }
       }
     }
   }
@@ -124,8 +126,85 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
     const int i = first + it * kThreads + tid;
-    if (valid[it]) {
-      const Stencil& s = st[it];
+    Stencil st = Stencil{};
+    if (valid[it]) stencil(g, a.P.x(0)[i], a.P.x(1)[i], a.P.x(2)[i], st);
+    if (use_tile) {
+      // warp-level pre-reduction (Sec. V-A): lanes whose stencils share a
+      // base cell (adjacent after the cell-ordered sort) add their 27 node
+      // contributions with a segmented shuffle reduction, and only the first
+      // lane of each run issues the shared-memory atomics
+      const Stencil& s = st;
+      float mass = 0.f, mvx = 0.f, mvy = 0.f, mvz = 0.f;
+      float A[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) A[c] = 0.f;
+      int l0 = 0, l1 = 0, l2 = 0, key = -1 - lane;
+      if (valid[it]) {
+        const DevGroup gr = a.groups[a.P.grp[i]];
+        float tau[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) tau[c] = a.P.tau(c)[i];
+        // affine momentum m C - h (4/dx^2) V tau
+        const float sc = h * dinv * gr.vol;
+        const float tf[9] = {tau[0], tau[3], tau[4], tau[3], tau[1], tau[5], tau[4], tau[5], tau[2]};
+#pragma unroll
+        for (int c = 0; c < 9; ++c) A[c] = gr.mass * a.P.C(c)[i] - sc * tf[c];
+        mass = gr.mass;
+        mvx = gr.mass * a.P.v(0)[i];
+        mvy = gr.mass * a.P.v(1)[i];
+        mvz = gr.mass * a.P.v(2)[i];
+        l0 = s.base[0] - b0;
+        l1 = s.base[1] - b1;
+        l2 = s.base[2] - b2;
+        key = (l2 * ey + l1) * ex + l0;
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int head = __ffs(peers) - 1, seg_end = 31 - __clz(peers);
+      const unsigned run = (0xffffffffu >> (31 - seg_end)) & (0xffffffffu << head);
+      const bool contiguous = __all_sync(0xffffffffu, peers == run);
+      const int len = contiguous ? seg_end - head + 1 : 1;
+      const int maxlen = __reduce_max_sync(0xffffffffu, (unsigned)len);
+      const int steps = maxlen > 1 ? 32 - __clz(maxlen - 1) : 0;
+      const bool issue = valid[it] && (!contiguous || lane == head);
+#pragma unroll
+      for (int cz = 0; cz < 3; ++cz) {
+        const float dz = (cz - s.fx[2]) * g.dx;
+#pragma unroll
+        for (int cy = 0; cy < 3; ++cy) {
+          const float dy = (cy - s.fx[1]) * g.dx;
+          const float wyz = s.w[1][cy] * s.w[2][cz];
+          const int row = toff + ((l2 + cz) * ey + (l1 + cy)) * ex + l0;
+#pragma unroll
+          for (int cx = 0; cx < 3; ++cx) {
+            const float dxp = (cx - s.fx[0]) * g.dx;
+            const float w = valid[it] ? s.w[0][cx] * wyz : 0.f;
+            float q0 = w * mass;
+            float q1 = w * (mvx + A[0] * dxp + A[1] * dy + A[2] * dz);
+            float q2 = w * (mvy + A[3] * dxp + A[4] * dy + A[5] * dz);
+            float q3 = w * (mvz + A[6] * dxp + A[7] * dy + A[8] * dz);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+              if (k < steps) {
+                const int off = 1 << k;
+                const float r0 = __shfl_down_sync(0xffffffffu, q0, off);
+                const float r1 = __shfl_down_sync(0xffffffffu, q1, off);
+                const float r2 = __shfl_down_sync(0xffffffffu, q2, off);
+                const float r3 = __shfl_down_sync(0xffffffffu, q3, off);
+                if (lane + off <= seg_end) { q0 += r0; q1 += r1; q2 += r2; q3 += r3; }
+              }
+            }
+            if (issue) {
+              const int t = row + cx;
+              atomicAdd(&t_m[t], q0);
+              atomicAdd(&t_px[t], q1);
+              atomicAdd(&t_py[t], q2);
+              atomicAdd(&t_pz[t], q3);
+            }
+          }
+        }
+      }
+    } else if (valid[it]) {
+      const Stencil& s = st;
       const DevGroup gr = a.groups[a.P.grp[i]];
       const float vp[3] = {a.P.v(0)[i], a.P.v(1)[i], a.P.v(2)[i]};
       float tau[6];
@@ -138,59 +217,35 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) A[c] = gr.mass * a.P.C(c)[i] - sc * tf[c];
       const float mvx = gr.mass * vp[0], mvy = gr.mass * vp[1], mvz = gr.mass * vp[2];
-      if (use_tile) {
-        const int l0 = s.base[0] - b0, l1 = s.base[1] - b1, l2 = s.base[2] - b2;
 #pragma unroll
-        for (int cz = 0; cz < 3; ++cz) {
-          const float dz = (cz - s.fx[2]) * g.dx;
+      for (int cz = 0; cz < 3; ++cz) {
+        const float dz = (cz - s.fx[2]) * g.dx;
 #pragma unroll
-          for (int cy = 0; cy < 3; ++cy) {
-            const float dy = (cy - s.fx[1]) * g.dx;
-            const float wyz = s.w[1][cy] * s.w[2][cz];
-            const int row = toff + ((l2 + cz) * ey + (l1 + cy)) * ex + l0;
+        for (int cy = 0; cy < 3; ++cy) {
+          const float dy = (cy - s.fx[1]) * g.dx;
+          const float wyz = s.w[1][cy] * s.w[2][cz];
 #pragma unroll
-            for (int cx = 0; cx < 3; ++cx) {
-              const float dxp = (cx - s.fx[0]) * g.dx;
-              const float w = s.w[0][cx] * wyz;
-              const int t = row + cx;
-              atomicAdd(&t_m[t], w * gr.mass);
-              atomicAdd(&t_px[t], w * (mvx + A[0] * dxp + A[1] * dy + A[2] * dz));
-              atomicAdd(&t_py[t], w * (mvy + A[3] * dxp + A[4] * dy + A[5] * dz));
-              atomicAdd(&t_pz[t], w * (mvz + A[6] * dxp + A[7] * dy + A[8] * dz));
-            }
+          for (int cx = 0; cx < 3; ++cx) {
+            const float dxp = (cx - s.fx[0]) * g.dx;
+            const float w = s.w[0][cx] * wyz;
+            const int node = node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz);
+            red_add_v4(a.G.mp + node, w * gr.mass, w * (mvx + A[0] * dxp + A[1] * dy + A[2] * dz),
+                       w * (mvy + A[3] * dxp + A[4] * dy + A[5] * dz),
+                       w * (mvz + A[6] * dxp + A[7] * dy + A[8] * dz));
           }
         }
-      } else {
-#pragma unroll
-        for (int cz = 0; cz < 3; ++cz) {
-          const float dz = (cz - s.fx[2]) * g.dx;
-#pragma unroll
-          for (int cy = 0; cy < 3; ++cy) {
-            const float dy = (cy - s.fx[1]) * g.dx;
-            const float wyz = s.w[1][cy] * s.w[2][cz];
-#pragma unroll
-            for (int cx = 0; cx < 3; ++cx) {
-              const float dxp = (cx - s.fx[0]) * g.dx;
-              const float w = s.w[0][cx] * wyz;
-              const int node = node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz);
-              red_add_v4(a.G.mp + node, w * gr.mass, w * (mvx + A[0] * dxp + A[1] * dy + A[2] * dz),
-                         w * (mvy + A[3] * dxp + A[4] * dy + A[5] * dz),
-                         w * (mvz + A[6] * dxp + A[7] * dy + A[8] * dz));
-            }
-          }
-        }
-        // mark the (up to 8) blocks of this stencil
-#pragma unroll
-        for (int cz = 0; cz < 2; ++cz)
-#pragma unroll
-          for (int cy = 0; cy < 2; ++cy)
-#pragma unroll
-            for (int cx = 0; cx < 2; ++cx) {
-              const int bi = (s.base[0] + 2 * cx) >> 2, bj = (s.base[1] + 2 * cy) >> 2,
-                        bk = (s.base[2] + 2 * cz) >> 2;
-              a.G.mark[(bk * g.nby + bj) * g.nbx + bi] = 1;
-            }
       }
+      // mark the (up to 8) blocks of this stencil
+#pragma unroll
+      for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+        for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+          for (int cx = 0; cx < 2; ++cx) {
+            const int bi = (s.base[0] + 2 * cx) >> 2, bj = (s.base[1] + 2 * cy) >> 2,
+                      bk = (s.base[2] + 2 * cz) >> 2;
+            a.G.mark[(bk * g.nby + bj) * g.nbx + bi] = 1;
+          }
     }
     // contact registration: warp-aggregated append, one contact per
     // (particle, body) pair with the particle strictly inside

@@ -4,8 +4,11 @@
 //
 // Key: Morton code of the 4^3 block holding the particle's B-spline base
 // node, so that a run of consecutive particles covers a compact box of
-// blocks. Sort: stable LSD radix sort with 8-bit digits, one pass per digit
-// of the key (a 128^3 grid has 15 key bits: two passes). Each pass is a
+// blocks, followed by the base cell within the block (x fastest), so that
+// the lanes of a warp touch consecutive nodes of P2G's shared tile and lanes
+// sharing a cell are adjacent (for the warp-level pre-reduction). Sort:
+// stable LSD radix sort with 8-bit digits, one pass per digit of the key (a
+// 128^3 grid has 15 + 6 key bits: three passes). Each pass is a
 // per-warp-tile histogram, an exclusive scan over (digit, tile), and a
 // stable per-warp scatter whose in-warp ranks come from __match_any_sync.
 // The permutation is then applied to every particle plane at once.
@@ -28,15 +31,20 @@ __global__ void k_keys(GridDev g, const float* __restrict__ x0, const float* __r
   if (i >= n) return;
   float xi[3] = {(x0[i] - g.ox) * g.inv_dx, (x1[i] - g.oy) * g.inv_dx, (x2[i] - g.oz) * g.inv_dx};
   int lim[3] = {g.nbx - 1, g.nby - 1, g.nbz - 1};
-  uint32_t b[3];
+  uint32_t b[3], c[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     int base = (int)floorf(xi[a] - 0.5f);
     int blk = base >> 2;  // arithmetic shift: floor division for negatives
-    blk = blk < 0 ? 0 : (blk > lim[a] ? lim[a] : blk);
+    c[a] = (uint32_t)(base & 3);
+    if (blk < 0) { blk = 0; c[a] = 0; }
+    if (blk > lim[a]) { blk = lim[a]; c[a] = 3; }
     b[a] = (uint32_t)blk;
   }
-  keys[i] = spread_bits3(b[0]) | (spread_bits3(b[1]) << 1) | (spread_bits3(b[2]) << 2);
+  uint32_t key = spread_bits3(b[0]) | (spread_bits3(b[1]) << 1) | (spread_bits3(b[2]) << 2);
+  // cell within the block, x fastest (the order of the P2G tile), when it fits
+  if (g.sort_cell_bits) key = (key << 6) | (c[2] << 4) | (c[1] << 2) | c[0];
+  keys[i] = key;
   vals[i] = (uint32_t)i;
 }
 
@@ -249,7 +257,7 @@ void launch_sort(const GridDev& g, const Particles& src, const Particles& dst, i
   int tpb = 256;
   k_keys<<<(n + tpb - 1) / tpb, tpb, 0, s>>>(g, src.x(0), src.x(1), src.x(2), n, sb.keys[0],
                                             sb.vals[0]);
-  int key_bits = 3 * g.morton_bits;
+  int key_bits = 3 * g.morton_bits + (g.sort_cell_bits ? 6 : 0);
   int passes = (key_bits + 7) / 8;
   int n_tiles = (n + kWarpTile - 1) / kWarpTile;
   int blocks = (n_tiles + kSortWarps - 1) / kSortWarps;
