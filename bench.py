@@ -142,6 +142,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_launches_per_step(res, n_substeps):
+    """Kernels one mpm_step launches: the radix sort (keys, five kernels per
+    8-bit digit pass, permutation) and per substep P2G, block compaction,
+    grid update, solve and G2P."""
+    blocks = max(-(-int(r) // 4) for r in res)
+    morton_bits = max((blocks - 1).bit_length(), 1)
+    key_bits = 3 * morton_bits + (6 if 3 * morton_bits + 6 <= 32 else 0)
+    passes = -(-key_bits // 8)
+    return (1 + 5 * passes + 1) + 5 * n_substeps
+
+
 def make_scene(n=N_PARTICLES):
     from paper_2503_05046_gb300 import scenes
     return scenes.granular_scoop(n_particles=n)
@@ -226,8 +237,7 @@ def run_ours(args):
     roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GBps"], "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": kern[dom]["GBps"] / peak,
             "traffic": profiled_traffic(dom)}
-    sort_passes = (3 * 5 + 7) // 8  # 32^3 blocks -> 5 Morton bits per axis
-    launches_per_step = (1 + 5 * sort_passes + 1) + N * 5
+    launches_per_step = kernel_launches_per_step(sc["grid"]["res"], N)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

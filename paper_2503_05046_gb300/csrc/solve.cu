@@ -18,15 +18,19 @@
 //   N  contact nodes: g = M (v - v*) + J^T dl_c (Eq. (9)), H = M + contact
 //      blocks, stopping norms, dv = -H^-1 g by 3x3 Cholesky; grid sums of the
 //      line search, A = dv^T M dv and B = dv^T M (v - v*).
-//   C  contacts: dv_c = J dv, and the first line-search pass.
+//   C  contacts: dv_c = J dv.
 //   L  exact line search (Alg. 1): f'(alpha) = B + alpha A + sum_p dl_c . dv_c
 //      is monotone (f convex); each pass evaluates it at 8 points in one
 //      contact sweep: first on a doubling grid to bracket the root, then
 //      around the secant estimate inside the bracket, until
-//      |f'| <= ls_rel_tol |f'(0)|.
-// Every block reads the same reduced sums, so all take the same decisions.
-// Scalar sums are accumulated per thread and per warp in FP32, across warps
-// and blocks in FP64.
+//      |f'| <= ls_rel_tol |f'(0)|. Up to kLocalLsMax contacts every block
+//      runs the whole line search by itself over all contacts (their v_c and
+//      dv_c sit in L2), so its passes need no grid barrier; above that the
+//      contacts are split over the blocks and each pass ends in a grid-wide
+//      reduction.
+// Every block reads the same reduced sums (or computes the same ones in the
+// same order), so all take the same decisions. Scalar sums are accumulated
+// per thread and per warp in FP32, across warps and blocks in FP64.
 #include <cfloat>
 
 #include "kernels.h"
@@ -37,7 +41,8 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kContactsPerBlock = 64;
+constexpr int kContactsPerBlock = 16;  // one contact per warp in the gather phases
+constexpr int kLocalLsMax = 4096;      // up to this many contacts each block line-searches alone
 constexpr int kLsPoints = 8;
 constexpr int kRedWidth = 16;              // doubles per block and reduction
 constexpr int kMaxSolveBlocks = 256;
@@ -114,13 +119,13 @@ __device__ bool reduce_all(const float (&v)[NV], double* part, Barrier& B, float
   }
   __syncthreads();
   if (w == 0 && lane < NV) {
-    float x = 0.f;
+    double x = 0.0;
 #pragma unroll
-    for (int k = 0; k < kWarps; ++k) x += s_red[k][lane];
+    for (int k = 0; k < kWarps; ++k) x += (double)s_red[k][lane];
     if (B.n == 1)
-      s_tot[lane] = (double)x;
+      s_tot[lane] = x;
     else
-      part[blockIdx.x * kRedWidth + lane] = (double)x;
+      part[blockIdx.x * kRedWidth + lane] = x;
   }
   if (!grid_sync(B)) return false;
   if (B.n > 1) {
@@ -418,6 +423,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   float4* vnxt = a.G.v2;
   float4* lcur = a.G.vlo;
   float4* lnxt = a.G.vlo2;
+  // line search alone in each block (no grid barrier) or split over blocks
+  const bool local_ls = nc <= kLocalLsMax;
+  const int ls_first = local_ls ? tid : gtid, ls_stride = local_ls ? kThreads : gstride;
+  Barrier Bl{nullptr, 1u, 0u, a.status};
   double alpha = 0.0;
   int it = 0, ls_passes = 0;
   float resid = 0.f;
@@ -427,6 +436,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     for (int p = gwarp; p < nc; p += nwarps) {
       float4 xp; float n[3]; float n0;
       load_contact(a.C, p, xp, n, n0);
+      // issued early: these loads do not depend on the gather
+      const float4 bb = a.C.bias[p];
+      const float4 dvc = it > 0 ? __ldcg(a.C.dvc + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int body = a.C.id[p].y;
       const LaneNode ln = lane_node(g, xp, lane);
       float u[3];
       {
@@ -443,8 +456,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
       }
       if (lane == 0) {
         // + b + alpha J dv, compensated
-        const float4 bb = a.C.bias[p];
-        const float4 dvc = it > 0 ? a.C.dvc[p] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float bv[3] = {bb.x, bb.y, bb.z}, dv3[3] = {dvc.x, dvc.y, dvc.z};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -458,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) u[c] = __shfl_sync(0xffffffffu, u[c], 0);
       if (lane == 0) a.C.vc[p] = make_float4(u[0], u[1], u[2], 0.f);
-      const DevBody& bd = s_body[a.C.id[p].y];
+      const DevBody& bd = s_body[body];
       ContactLaw L;
       contact_law(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, L);
       float gr[3], H[6];
@@ -584,14 +595,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     if (!grid_sync(B)) return;
     // ---- L: line-search passes of 8 points each (thread per contact)
     for (int pass = 0;; ++pass) {
-      double* sl = next_slot();
+      double* sl = local_ls ? nullptr : next_slot();
       float alphas[kLsPoints];
 #pragma unroll
       for (int k = 0; k < kLsPoints; ++k) alphas[k] = s_pts[k];
       float acc[2 * kLsPoints];
 #pragma unroll
       for (int k = 0; k < 2 * kLsPoints; ++k) acc[k] = 0.f;
-      for (int p = gtid; p < nc; p += gstride) {
+      for (int p = ls_first; p < nc; p += ls_stride) {
         float4 xp; float n[3]; float n0;
         load_contact(a.C, p, xp, n, n0);
         const float4 q = __ldcg(a.C.dvc + p);
@@ -599,7 +610,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
         // v_c was written by another warp in phase G: read it from L2
         ls_contact(a, s_body[a.C.id[p].y], xp, n, n0, __ldcg(a.C.vc + p), e, alphas, acc);
       }
-      if (!reduce_all(acc, sl, B, s_red, s_tot)) return;
+      if (!reduce_all(acc, sl, local_ls ? Bl : B, s_red, s_tot)) return;
       lap(3);
       ++ls_passes;
       if (tid == 0) {
