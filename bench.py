@@ -16,9 +16,8 @@ Metric: particle-substeps per second including the contact solve.
 Rank r of a torchrun job runs an independent replica on its own GPU (a single
 scene does not shard); value sums the replicas over the slowest rank's time.
 
-`--impl reference` times the FP64 CPU oracle (oracle/) on the host cores on a
-bounded sample of the same workload (one octant of the sand, one substep per
-bench step).
+`--impl reference` times the FP64 CPU oracle (oracle/) on one host thread, one
+substep of the whole workload per bench step.
 """
 import argparse
 import json
@@ -38,8 +37,8 @@ UNIT = "particle-substeps/s"
 WORKLOAD = "granular_scoop_1M"
 N_PARTICLES = 1_000_000
 # algorithmic bytes per particle per launch (FP32 SoA planes)
-P2G_BYTES_PER_PARTICLE = 12 + 12 + 36 + 36 + 2      # read x, v, C, F, group
-G2P_BYTES_PER_PARTICLE = 12 + 36 + 2 + 12 + 12 + 36 + 36  # read x, F, group; write x, v, C, F
+P2G_BYTES_PER_PARTICLE = 12 + 12 + 36 + 24 + 2      # read x, v, C, tau, group
+G2P_BYTES_PER_PARTICLE = 12 + 36 + 2 + 12 + 12 + 36 + 36 + 24  # read x, F, group; write x, v, C, F, tau
 GRID_NODE_BYTES_P2G = 16                              # one (m, p) write per active node
 GRID_NODE_BYTES_G2P = 16                              # one v read per active node
 
@@ -153,6 +152,15 @@ def kernel_launches_per_step(res, n_substeps):
     return (1 + 5 * passes + 1) + 5 * n_substeps
 
 
+def bench_config(sc, n, ws):
+    """The workload description shared by both arms' JSON lines."""
+    return {"workload": WORKLOAD, "particles": n, "material": "drucker_prager_sand",
+            "bodies": len(sc["bodies"]), "dx": sc["grid"]["dx"], "grid": list(sc["grid"]["res"]),
+            "h": sc["h"], "substeps_per_step": sc["substeps"], "eps_r": 5e-2,
+            "l2": "flushed between timed steps (256 MB write)",
+            "parallelism": "replica per GPU" if ws > 1 else "single GPU"}
+
+
 def make_scene(n=N_PARTICLES):
     from paper_2503_05046_gb300 import scenes
     return scenes.granular_scoop(n_particles=n)
@@ -242,11 +250,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles": n, "material": "drucker_prager_sand",
-                   "bodies": len(sc["bodies"]), "dx": sc["grid"]["dx"], "grid": list(sc["grid"]["res"]),
-                   "h": sc["h"], "substeps_per_step": N, "eps_r": 5e-2,
-                   "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": "replica per GPU" if ws > 1 else "single GPU"},
+        "config": bench_config(sc, n, ws),
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(len(bodies) * C_sizeof_body(native)),
                 "d2h_bytes_per_step": int(12 * n + 48 * len(bodies))},
@@ -277,67 +281,71 @@ def C_sizeof_body(native):
     return ctypes.sizeof(native.RigidBody)
 
 
-def octant_sample(sc, state=None):
-    """One octant of the sand (x < 0, y < 0, z < 0.15) with every body: a
-    bounded sample of the workload for the CPU oracle."""
-    x = np.asarray(state["x"] if state is not None else sc["groups"][0]["x"])
-    sel = (x[:, 0] < 0) & (x[:, 1] < 0) & (x[:, 2] < 0.15)
-    return sel
-
-
-def oracle_time(sc, state, sel, n_substeps=1):
+def oracle_state(sc, state):
+    """Oracle particle state (FP64) of a float32 particle state of the scene."""
     import oracle as O
     g = sc["groups"][0]
-    m = int(sel.sum())
+    m = len(state["x"])
     V = float(np.float32(g["vol"]))
-    st = O.Sim.state({"x": state["x"][sel], "v": state["v"][sel], "C": state["C"][sel],
-                      "F": state["F"][sel], "mass": np.full(m, V * float(np.float32(g["material"]["rho"]))),
-                      "vol": np.full(m, V), "mat": np.zeros(m, np.int32)})
-    _, mats = O.from_scene({"groups": [g]})
+    return O.Sim.state({"x": state["x"], "v": state["v"], "C": state["C"], "F": state["F"],
+                        "mass": np.full(m, V * float(np.float32(g["material"]["rho"]))),
+                        "vol": np.full(m, V), "mat": np.zeros(m, np.int32)})
+
+
+def oracle_runner(sc):
+    """(advance, n): advance(st, k) runs k oracle substeps of the whole scene
+    on state st and returns the seconds taken."""
+    import oracle as O
+    _, mats = O.from_scene({"groups": [sc["groups"][0]]})
     osim = O.Sim(sc["grid"])
     bodies = [O.make_body(b) for b in O.bodies_from_scene(sc)]
     S = O.solver(eps_r=5e-2, max_iters=1000)
-    t0 = time.perf_counter()
-    for _ in range(n_substeps):
-        osim.substep(st, mats, bodies, sc["h"], S)
-    return m, time.perf_counter() - t0
+
+    def advance(st, k):
+        t0 = time.perf_counter()
+        for _ in range(k):
+            osim.substep(st, mats, bodies, sc["h"], S)
+        return time.perf_counter() - t0
+    return advance
 
 
 def cpu_baseline(sc, sim, native):
+    """The FP64 oracle (one host thread) on one whole bench step: all
+    particles, all bodies, the step's N substeps, from the bench's state."""
     state = sim.get_particles()
-    sel = octant_sample(sc, state)
-    m, secs = oracle_time(sc, state, sel, n_substeps=2)
-    return {"value": m * 2 / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "FP64 oracle, 1 thread: 2 substeps of the %d particles in one octant "
-                      "(x<0, y<0, z<0.15 m) of the bench state, all bodies; %.1f s" % (m, secs)}
+    n = len(state["x"])
+    st = oracle_state(sc, state)
+    secs = oracle_runner(sc)(st, sc["substeps"])
+    return {"value": n * sc["substeps"] / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 oracle, 1 thread: one bench step (%d substeps) of all %d particles "
+                      "and %d bodies from the bench state; %.1f s" % (sc["substeps"], n,
+                                                                       len(sc["bodies"]), secs)}
 
 
 def run_reference(args):
+    """Reference arm: the FP64 oracle on the host, one substep of the whole
+    workload (all particles and bodies) per bench step."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     sc = make_scene()
-    state = {"x": sc["groups"][0]["x"], "v": sc["groups"][0]["v"],
-             "C": np.zeros((N_PARTICLES, 3, 3), np.float32),
-             "F": np.tile(np.eye(3, dtype=np.float32), (N_PARTICLES, 1, 1))}
-    sel = octant_sample(sc, state)
-    for _ in range(min(args.warmup, 1)):
-        oracle_time(sc, state, sel, 1)
-    total_units, total_s = 0.0, 0.0
-    for _ in range(args.steps):
-        m, s = oracle_time(sc, state, sel, 1)
-        total_units += m
-        total_s += s
-    value = total_units / total_s
+    g = sc["groups"][0]
+    n = len(g["x"])
+    state = {"x": g["x"], "v": g["v"], "C": np.zeros((n, 3, 3), np.float32),
+             "F": np.tile(np.eye(3, dtype=np.float32), (n, 1, 1))}
+    st = oracle_state(sc, state)
+    advance = oracle_runner(sc)
+    advance(st, args.warmup)
+    total_s = sum(advance(st, 1) for _ in range(args.steps))
+    value = n * args.steps / total_s
+    cfg = bench_config(sc, n, ws)
+    cfg["sample"] = "one substep of the whole workload per bench step, after %d warm-up substeps" % args.warmup
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "particles": N_PARTICLES,
-                       "sample": "one octant (%d particles), one substep per step" % int(sel.sum())},
+            "data": "synthetic", "impl": "reference", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "FP64 oracle on one octant of the initial sand state, "
-                                       "one substep per bench step"},
+                             "sample": cfg["sample"] + ", FP64 oracle on 1 host thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

@@ -598,4 +598,56 @@ __device__ __forceinline__ void contact_dir(const ContactLaw& L, const float (&n
   d2 = L.d2N * en * en + L.cs * (et2 - ute * ute * L.inv_s2);
 }
 
+// The contact potential on the line u(alpha) = v_c + alpha e of the line
+// search (Sec. V-B): the per-contact invariants are formed once, after which
+// f' and f'' contributions at any alpha cost a few FMAs and one rsqrt
+// (u_t(alpha) = (v_c - v_n n) + alpha (e - e_n n)).
+struct ContactLine {
+  float vn0, en, vhat, phi0, hk, h, d, mun0, eps2, et2;
+  float vt[3], et[3];
+};
+
+__device__ __forceinline__ void contact_line(float phi0, float n0, float mu, float k, float d,
+                                             float h, float eps_s, const float (&n)[3],
+                                             const float (&u)[3], const float (&e)[3],
+                                             ContactLine& L) {
+  L.vn0 = n[0] * u[0] + n[1] * u[1] + n[2] * u[2];
+  L.en = n[0] * e[0] + n[1] * e[1] + n[2] * e[2];
+  float vhat = phi0 / h;
+  if (d > 0.0f) vhat = fminf(vhat, 1.0f / d);
+  L.vhat = vhat;
+  L.phi0 = phi0;
+  L.hk = h * k;
+  L.h = h;
+  L.d = d;
+  L.mun0 = mu * n0;
+  L.eps2 = eps_s * eps_s;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    L.vt[r] = u[r] - L.vn0 * n[r];
+    L.et[r] = e[r] - L.en * n[r];
+  }
+  L.et2 = L.et[0] * L.et[0] + L.et[1] * L.et[1] + L.et[2] * L.et[2];
+}
+
+// d/dalpha and d2/dalpha2 of l_c(v_c + alpha e)
+__device__ __forceinline__ void contact_line_eval(const ContactLine& L, float al, float& d1,
+                                                  float& d2) {
+  const float vn = fmaf(al, L.en, L.vn0);
+  float dN = 0.0f, d2N = 0.0f;
+  if (vn < L.vhat) {
+    const float a = L.phi0 - L.h * vn, c = 1.0f - L.d * vn;
+    dN = -L.hk * a * c;
+    d2N = L.hk * (L.h * c + L.d * a);
+  }
+  const float u0 = fmaf(al, L.et[0], L.vt[0]), u1 = fmaf(al, L.et[1], L.vt[1]),
+              u2 = fmaf(al, L.et[2], L.vt[2]);
+  const float s2 = u0 * u0 + u1 * u1 + u2 * u2 + L.eps2;
+  const float inv_s = rsqrtf(s2);
+  const float cs = L.mun0 * inv_s;
+  const float ute = u0 * L.et[0] + u1 * L.et[1] + u2 * L.et[2];
+  d1 = dN * L.en + cs * ute;
+  d2 = d2N * L.en * L.en + cs * (L.et2 - ute * ute * inv_s * inv_s);
+}
+
 }  // namespace mpmcr

@@ -123,7 +123,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
   const float h = a.h;
   const float dinv = 4.0f * g.inv_dx * g.inv_dx;
 
-#pragma unroll
+  // not unrolled: one copy of the large per-particle body keeps the
+  // instruction footprint small
+#pragma unroll 1
   for (int it = 0; it < ITEMS; ++it) {
     const int i = first + it * kThreads + tid;
     Stencil st = Stencil{};

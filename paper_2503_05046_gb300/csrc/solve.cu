@@ -14,8 +14,9 @@
 //   G  contacts: v_c = J v + b (a compensated gather of the double-float
 //      iterate); gradient (3) and Hessian (3x3) of the lagged contact
 //      potential, scattered with weights w and w^2 (the 3x3 diagonal blocks of
-//      J^T (d2 l_c) J, Eq. (10)); contact nodes: v += alpha dv (double-float).
-//   N  contact nodes: g = M (v - v*) + J^T dl_c (Eq. (9)), H = M + contact
+//      J^T (d2 l_c) J, Eq. (10)).
+//   N  contact nodes: v += alpha dv (double-float, into the other buffer of
+//      the iterate), g = M (v - v*) + J^T dl_c (Eq. (9)), H = M + contact
 //      blocks, stopping norms, dv = -H^-1 g by 3x3 Cholesky; grid sums of the
 //      line search, A = dv^T M dv and B = dv^T M (v - v*).
 //   C  contacts: dv_c = J dv.
@@ -30,7 +31,9 @@
 //      reduction.
 // Every block reads the same reduced sums (or computes the same ones in the
 // same order), so all take the same decisions. Scalar sums are accumulated
-// per thread and per warp in FP32, across warps and blocks in FP64.
+// per thread and per warp in FP32, across warps and blocks as double-float
+// (hi, lo) pairs with error-free FP32 transforms: GB300's FP64 pipe is narrow
+// enough that FP64 on these serial paths costs more than the rest of a pass.
 #include <cfloat>
 
 #include "kernels.h"
@@ -44,7 +47,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kContactsPerBlock = 16;  // one contact per warp in the gather phases
 constexpr int kLocalLsMax = 4096;      // up to this many contacts each block line-searches alone
 constexpr int kLsPoints = 8;
-constexpr int kRedWidth = 16;              // doubles per block and reduction
+constexpr int kRedWidth = 16;              // (hi, lo) pairs per block and reduction
 constexpr int kMaxSolveBlocks = 256;
 constexpr unsigned kSpinLimit = 1u << 24;  // ~1 s of polling with the back-off below
 
@@ -61,17 +64,18 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 struct Barrier {
-  unsigned* bar;  // [0] arrivals, [1] generation
+  unsigned* bar;  // [0] arrival counter (zeroed between launches)
   unsigned n;     // participating blocks
-  unsigned gen;   // meaningful in thread 0 only
   uint32_t* status;
 };
 
-// Device-wide barrier of the participating blocks. Thread 0 publishes its
-// block's writes (fence), arrives, and the last arriver releases the next
-// generation; the others spin with an iteration limit and return false on
-// expiry (the caller then returns; the other blocks expire at their next
-// barrier). A single participating block needs only __syncthreads.
+// Device-wide barrier of the participating blocks. The arrival counter only
+// grows: the k-th barrier is complete when it reaches (k + 1) n, which each
+// block reads off its own arrival ticket, so the last arriver has nothing to
+// reset or publish. Thread 0 publishes its block's writes (fence), arrives,
+// and the others spin with an iteration limit and return false on expiry
+// (the caller then returns; the other blocks expire at their next barrier).
+// A single participating block needs only __syncthreads.
 __device__ bool grid_sync(Barrier& B) {
   __syncthreads();
   if (B.n == 1) return true;
@@ -79,14 +83,11 @@ __device__ bool grid_sync(Barrier& B) {
   if (threadIdx.x == 0) {
     int ok = 1;
     __threadfence();
-    const unsigned arrived = atomicAdd(&B.bar[0], 1u);
-    if (arrived == B.n - 1) {
-      atomicExch(&B.bar[0], 0u);
-      __threadfence();
-      atomicExch(&B.bar[1], B.gen + 1u);
-    } else {
+    const unsigned ticket = atomicAdd(&B.bar[0], 1u);
+    const unsigned target = (ticket / B.n + 1u) * B.n;
+    if (ticket + 1u != target) {
       unsigned spins = 0;
-      while (ld_acquire(&B.bar[1]) == B.gen) {
+      while (ld_acquire(&B.bar[0]) < target) {
         if (++spins > kSpinLimit) {
           atomicOr(B.status, kStTimeout);
           ok = 0;
@@ -94,38 +95,78 @@ __device__ bool grid_sync(Barrier& B) {
         }
         __nanosleep(20);
       }
-      __threadfence();
     }
-    B.gen += 1u;
+    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
 }
 
+// double-float value (hi, lo), |lo| <= ulp(hi) / 2
+__device__ __forceinline__ float2 df_norm(float S, float E) {
+  const float hi = S + E;
+  return make_float2(hi, E - (hi - S));
+}
+
+// (S, E) += (hi, lo)
+__device__ __forceinline__ void df_acc(float& S, float& E, float2 x) {
+  float s, e;
+  two_sum(S, x.x, s, e);
+  S = s;
+  E += e + x.y;
+}
+
 // Block sums of NV per-thread values, exchanged through per-block slots and
 // summed by every block in the same fixed order (deterministic). Returns the
-// totals in s_tot (shared) and false if the barrier expired.
+// double-float totals in s_tot (shared) and false if the barrier expired.
 template <int NV>
-__device__ bool reduce_all(const float (&v)[NV], double* part, Barrier& B, float (*s_red)[kRedWidth],
-                           double* s_tot) {
+__device__ bool reduce_all(const float (&v)[NV], float2* part, Barrier& B, float (*s_red)[kRedWidth],
+                           float2* s_tot) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if constexpr (NV == 16) {
+    // reduce-scatter butterfly: after the exchange over lane bit b each lane
+    // keeps half of its values (those whose index bit b equals its lane bit
+    // b), so lane l ends with value l & 15 summed over the warp (16 shuffles
+    // instead of 80)
+    float x[16];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    float x = v[i];
+    for (int i = 0; i < 16; ++i) x[i] = v[i];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) s_red[w][i] = x;
+    for (int b = 0, m = 8; b < 4; ++b, m >>= 1) {
+      const bool hi = (lane >> b) & 1;
+#pragma unroll
+      for (int j = 0; j < m; ++j) {
+        const float keep = hi ? x[2 * j + 1] : x[2 * j];
+        const float send = hi ? x[2 * j] : x[2 * j + 1];
+        x[j] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << b);
+      }
+    }
+    const float t = x[0] + __shfl_xor_sync(0xffffffffu, x[0], 16);
+    if (lane < 16) s_red[w][lane] = t;
+  } else {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      float x = v[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) s_red[w][i] = x;
+    }
   }
   __syncthreads();
   if (w == 0 && lane < NV) {
-    double x = 0.0;
+    float S = 0.f, E = 0.f;
 #pragma unroll
-    for (int k = 0; k < kWarps; ++k) x += (double)s_red[k][lane];
+    for (int k = 0; k < kWarps; ++k) {
+      float t, e;
+      two_sum(S, s_red[k][lane], t, e);
+      S = t;
+      E += e;
+    }
     if (B.n == 1)
-      s_tot[lane] = x;
+      s_tot[lane] = df_norm(S, E);
     else
-      part[blockIdx.x * kRedWidth + lane] = x;
+      part[blockIdx.x * kRedWidth + lane] = df_norm(S, E);
   }
   if (!grid_sync(B)) return false;
   if (B.n > 1) {
@@ -133,29 +174,36 @@ __device__ bool reduce_all(const float (&v)[NV], double* part, Barrier& B, float
       if (B.n <= 32) {
         // lane i sums value i over the blocks, in block order
         if (lane < NV) {
-          double x = 0.0;
-          for (int b = 0; b < (int)B.n; ++b) x += __ldcg(part + b * kRedWidth + lane);
-          s_tot[lane] = x;
+          float S = 0.f, E = 0.f;
+          for (int b = 0; b < (int)B.n; ++b) df_acc(S, E, __ldcg(part + b * kRedWidth + lane));
+          s_tot[lane] = df_norm(S, E);
         }
       } else {
-        double acc[NV];
+        float S[NV], E[NV];
 #pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+        for (int i = 0; i < NV; ++i) { S[i] = 0.f; E[i] = 0.f; }
         for (int b = lane; b < (int)B.n; b += 32) {
-          const double2* q = reinterpret_cast<const double2*>(part + b * kRedWidth);
+          const float4* q = reinterpret_cast<const float4*>(part + b * kRedWidth);
 #pragma unroll
           for (int i = 0; i < NV / 2; ++i) {
-            const double2 d = __ldcg(q + i);
-            acc[2 * i] += d.x;
-            acc[2 * i + 1] += d.y;
+            const float4 d = __ldcg(q + i);
+            df_acc(S[2 * i], E[2 * i], make_float2(d.x, d.y));
+            df_acc(S[2 * i + 1], E[2 * i + 1], make_float2(d.z, d.w));
           }
         }
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-          double x = acc[i];
+          float Si = S[i], Ei = E[i];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-          if (lane == 0) s_tot[i] = x;
+          for (int o = 16; o > 0; o >>= 1) {
+            const float S2 = __shfl_xor_sync(0xffffffffu, Si, o);
+            const float E2 = __shfl_xor_sync(0xffffffffu, Ei, o);
+            float t, e;
+            two_sum(Si, S2, t, e);
+            Si = t;
+            Ei = Ei + E2 + e;
+          }
+          if (lane == 0) s_tot[i] = df_norm(Si, Ei);
         }
       }
     }
@@ -270,14 +318,13 @@ __device__ __forceinline__ void ls_contact(const SolveArgs& a, const DevBody& bd
                                            const float (&n)[3], float n0, const float4& vc,
                                            const float (&e)[3], const float (&alphas)[kLsPoints],
                                            float (&acc)[2 * kLsPoints]) {
+  const float u[3] = {vc.x, vc.y, vc.z};
+  ContactLine L;
+  contact_line(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, e, L);
 #pragma unroll
   for (int k = 0; k < kLsPoints; ++k) {
-    const float al = alphas[k];
-    const float u[3] = {vc.x + al * e[0], vc.y + al * e[1], vc.z + al * e[2]};
-    ContactLaw L;
-    contact_law(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, L);
     float d1, d2;
-    contact_dir(L, n, e, d1, d2);
+    contact_line_eval(L, alphas[k], d1, d2);
     acc[k] += d1;
     acc[kLsPoints + k] += d2;
   }
@@ -299,13 +346,18 @@ struct LineSearch {
     lo = 0.f; hi = -1.f; flo = fhi = best = fbest = f2best = f0 = 0.f;
     have_f0 = false;
   }
-  // FP64 only to form f' = B + alpha A + S (its terms can cancel); the
-  // bracket logic runs in FP32 (alpha is applied in FP32 anyway)
-  __device__ int update(const double* tot, double A, double B, float rel_tol, bool last) {
+  // f' = B + alpha A + S is formed in double-float (its terms can cancel);
+  // the bracket logic runs in FP32 (alpha is applied in FP32 anyway)
+  __device__ int update(const float2* tot, float2 A, float2 B, float rel_tol, bool last) {
     for (int k = 0; k < kLsPoints; ++k) {
       const float x = pts[k];
-      const float d = (float)(B + (double)x * A + tot[k]);
-      const float d2 = (float)(A + tot[kLsPoints + k]);
+      CompSum c;
+      c.S = B.x;
+      c.E = B.y + x * A.y + tot[k].y;
+      c.add_prod(x, A.x);
+      c.add(tot[k].x);
+      const float d = c.value();
+      const float d2 = (A.x + tot[kLsPoints + k].x) + (A.y + tot[kLsPoints + k].y);
       if (!have_f0 && x == 0.f) {
         f0 = d; have_f0 = true; flo = d; best = 0.f; fbest = d; f2best = d2;
       }
@@ -339,10 +391,11 @@ struct LineSearch {
 __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   __shared__ DevBody s_body[kMaxBodies];
   __shared__ float s_red[kWarps][kRedWidth];
-  __shared__ double s_tot[kRedWidth];
+  __shared__ float2 s_tot[kRedWidth];
   __shared__ float s_imp[kMaxBodies][6];
   __shared__ float s_pts[kLsPoints];
-  __shared__ double s_A, s_B, s_alpha;
+  __shared__ float2 s_A, s_B;
+  __shared__ float s_alpha;
   __shared__ int s_dec;
   LineSearch ls;  // used by thread 0
   const int tid = threadIdx.x;
@@ -369,8 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
       tmark = now;
     }
   };
-  Barrier B{a.bar, (unsigned)nblk, 0u, a.status};
-  if (tid == 0) B.gen = ld_acquire(&a.bar[1]);
+  Barrier B{a.bar, (unsigned)nblk, a.status};
   const int gtid = blockIdx.x * kThreads + tid;
   const int gstride = nblk * kThreads;
   const int lane = tid & 31;
@@ -380,8 +432,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   // per-block partial sums, a ring of 4 slots of kMaxSolveBlocks x kRedWidth;
   // a slot is rewritten two reductions later, after every block has read it
   int rslot = 0;
-  auto next_slot = [&]() -> double* {
-    double* s = a.red + (size_t)(rslot & 3) * kMaxSolveBlocks * kRedWidth;
+  auto next_slot = [&]() -> float2* {
+    float2* s = reinterpret_cast<float2*>(a.red) + (size_t)(rslot & 3) * kMaxSolveBlocks * kRedWidth;
     ++rslot;
     return s;
   };
@@ -412,7 +464,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   lap(0);
   int ncn = __ldcg(a.G.n_cnodes);
   ncn = ncn < a.G.cnodes_cap ? ncn : a.G.cnodes_cap;
-  const double pstar2 = __ldcg(a.G.pstar2);
+  // sum of m |v*|^2 over the grid (FP64 from the grid update) as double-float
+  const double pstar2_d = __ldcg(a.G.pstar2);
+  const float pstar2_hi = (float)pstar2_d, pstar2_lo = (float)(pstar2_d - (double)pstar2_hi);
+  const float eps_a = (float)a.eps_a, eps_r = (float)a.eps_r;
 
   // The iterate v = hi + lo is double buffered: in phase G every contact node
   // writes v_next = v_cur + alpha dv while every contact gathers
@@ -426,13 +481,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   // line search alone in each block (no grid barrier) or split over blocks
   const bool local_ls = nc <= kLocalLsMax;
   const int ls_first = local_ls ? tid : gtid, ls_stride = local_ls ? kThreads : gstride;
-  Barrier Bl{nullptr, 1u, 0u, a.status};
-  double alpha = 0.0;
+  Barrier Bl{nullptr, 1u, a.status};
+  float alpha = 0.f;
   int it = 0, ls_passes = 0;
   float resid = 0.f;
   for (;;) {
     // ---- G: step by alpha, contact gradient / Hessian blocks (warp per contact)
-    const float al = (float)alpha;
+    const float al = alpha;
     for (int p = gwarp; p < nc; p += nwarps) {
       float4 xp; float n[3]; float n0;
       load_contact(a.C, p, xp, n, n0);
@@ -482,32 +537,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
         red_add_f32(a.G.acc2 + ln.node, w2 * H[5]);
       }
     }
-    if (it > 0) {
-      for (int t = gtid; t < ncn; t += gstride) {
-        const int node = a.G.cnodes[t];
-        float4 v = vcur[node];
-        float4 l = lcur[node];
-        const float4 d = a.G.dv[node];
-        dd_add(v.x, l.x, al * d.x);
-        dd_add(v.y, l.y, al * d.y);
-        dd_add(v.z, l.z, al * d.z);
-        vnxt[node] = v;
-        lnxt[node] = l;
-      }
-      float4* t = vcur; vcur = vnxt; vnxt = t;
-      t = lcur; lcur = lnxt; lnxt = t;
-    }
     if (!grid_sync(B)) return;
     lap(1);
 
-    // ---- N: gradient, stopping norms, direction, grid line-search sums
-    double* slot = next_slot();
+    // ---- N: step the contact nodes by alpha (v_next = v_cur + alpha dv, in
+    // double-float, into the other buffer), gradient, stopping norms,
+    // direction, grid line-search sums
+    float2* slot = next_slot();
     {
       float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // G2, P2 - P*2, J2, A, B
       for (int t = gtid; t < ncn; t += gstride) {
         const int node = a.G.cnodes[t];
         const float4 vs = a.G.vs[node];
         const float m = vs.w;
+        float4 v = vcur[node];
+        float4 vl = lcur[node];
+        if (it > 0) {
+          const float4 d = a.G.dv[node];
+          dd_add(v.x, vl.x, al * d.x);
+          dd_add(v.y, vl.y, al * d.y);
+          dd_add(v.z, vl.z, al * d.z);
+          vnxt[node] = v;
+          lnxt[node] = vl;
+        }
         float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
         // written by other blocks' reductions in this launch: read from L2
         const float4 c0 = __ldcg(a.G.acc0 + node);
@@ -516,9 +568,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
         a.G.acc0[node] = make_float4(0.f, 0.f, 0.f, 0.f);
         a.G.acc1[node] = make_float4(0.f, 0.f, 0.f, 0.f);
         a.G.acc2[node] = 0.f;
-        const float4 v = vcur[node];
         if (m > 0.f && v.w == 0.f) {  // free DoF (v.w flags a Dirichlet node)
-          const float4 vl = lcur[node];
           // v - v* with the low part of the iterate
           const float r0 = (v.x - vs.x) + vl.x, r1 = (v.y - vs.y) + vl.y, r2 = (v.z - vs.z) + vl.z;
           const float g0 = m * r0 + c0.x, g1 = m * r1 + c0.y, g2 = m * r2 + c0.z;
@@ -546,6 +596,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
         }
         a.G.dv[node] = dv;
       }
+      if (it > 0) {
+        float4* t = vcur; vcur = vnxt; vnxt = t;
+        t = lcur; lcur = lnxt; lnxt = t;
+      }
       float acc6[6] = {acc[0], acc[1], acc[2], acc[3], acc[4], 0.f};
       if (!reduce_all(acc6, slot, B, s_red, s_tot)) return;
     }
@@ -554,16 +608,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     // (FP64 is a narrow pipe on GB300) and the decision is broadcast; every
     // block computes it from the same totals, so all decide alike.
     if (tid == 0) {
-      const double A = s_tot[3], Bs = s_tot[4];
-      const float G2 = (float)s_tot[0], P2 = (float)(pstar2 + s_tot[1]), J2 = (float)s_tot[2];
+      const float2 A = s_tot[3], Bs = s_tot[4];
+      const float G2 = s_tot[0].x + s_tot[0].y, J2 = s_tot[2].x + s_tot[2].y;
+      const float P2 = (pstar2_hi + s_tot[1].x) + (pstar2_lo + s_tot[1].y);
       const float Gn = sqrtf(G2), Pn = sqrtf(fmaxf(P2, 0.f)), Jn = sqrtf(J2);
       const float mx = fmaxf(Pn, Jn);
       resid = mx > 0.f ? Gn / mx : 0.f;
       int dec = 0;
-      if (!(G2 == G2) || !(A == A) || !(Bs == Bs)) {
+      if (!(G2 == G2) || !(A.x == A.x) || !(Bs.x == Bs.x)) {
         if (blockIdx.x == 0) atomicOr(a.status, kStNan);
         dec = 1;
-      } else if ((double)Gn < a.eps_a + a.eps_r * (double)mx || G2 == 0.f) {
+      } else if (Gn < eps_a + eps_r * mx || G2 == 0.f) {
         dec = 1;  // converged
       } else if (it >= a.max_iters) {
         if (blockIdx.x == 0) atomicOr(a.status, kStNotConverged);
@@ -595,7 +650,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     if (!grid_sync(B)) return;
     // ---- L: line-search passes of 8 points each (thread per contact)
     for (int pass = 0;; ++pass) {
-      double* sl = local_ls ? nullptr : next_slot();
+      float2* sl = local_ls ? nullptr : next_slot();
       float alphas[kLsPoints];
 #pragma unroll
       for (int k = 0; k < kLsPoints; ++k) alphas[k] = s_pts[k];
@@ -625,7 +680,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     }
     alpha = s_alpha;
     ++it;
-    if (alpha == 0.0) break;  // no further progress possible at this precision
+    if (alpha == 0.f) break;  // no further progress possible at this precision
   }
 
   // the solution must end in G.v, which G2P reads; release the node flags
