@@ -212,59 +212,6 @@ __device__ bool reduce_all(const float (&v)[NV], float2* part, Barrier& B, float
   return true;
 }
 
-__device__ __forceinline__ void gather(const GridDev& g, const float4* __restrict__ f,
-                                       const float4& xp, float (&out)[3]) {
-  Stencil s;
-  stencil(g, xp.x, xp.y, xp.z, s);
-  out[0] = out[1] = out[2] = 0.f;
-#pragma unroll
-  for (int cz = 0; cz < 3; ++cz)
-#pragma unroll
-    for (int cy = 0; cy < 3; ++cy) {
-      const float wyz = s.w[1][cy] * s.w[2][cz];
-#pragma unroll
-      for (int cx = 0; cx < 3; ++cx) {
-        const float w = s.w[0][cx] * wyz;
-        const float4 q = __ldcg(f + node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz));
-        out[0] += w * q.x;
-        out[1] += w * q.y;
-        out[2] += w * q.z;
-      }
-    }
-}
-
-// v_c = J v + b + alpha J dv with v = hi + lo, summed with compensation so
-// that the result is accurate to FP32 rounding of v_c itself (a stuck contact's
-// tangential velocity is a small difference of node velocities)
-__device__ __forceinline__ void gather_dd(const GridDev& g, const float4* __restrict__ hi,
-                                          const float4* __restrict__ lo, const float4& xp,
-                                          const float4& b, float al, const float4& dvc,
-                                          float (&out)[3]) {
-  Stencil s;
-  stencil(g, xp.x, xp.y, xp.z, s);
-  CompSum cs[3];
-#pragma unroll
-  for (int cz = 0; cz < 3; ++cz)
-#pragma unroll
-    for (int cy = 0; cy < 3; ++cy) {
-      const float wyz = s.w[1][cy] * s.w[2][cz];
-#pragma unroll
-      for (int cx = 0; cx < 3; ++cx) {
-        const float w = s.w[0][cx] * wyz;
-        const int node = node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz);
-        const float4 h = __ldcg(hi + node);
-        const float4 l = __ldcg(lo + node);
-        cs[0].add_prod(w, h.x); cs[0].E += w * l.x;
-        cs[1].add_prod(w, h.y); cs[1].E += w * l.y;
-        cs[2].add_prod(w, h.z); cs[2].E += w * l.z;
-      }
-    }
-  cs[0].add(b.x); cs[1].add(b.y); cs[2].add(b.z);
-  cs[0].add_prod(al, dvc.x); cs[1].add_prod(al, dvc.y); cs[2].add_prod(al, dvc.z);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) out[c] = cs[c].value();
-}
-
 // Warp-cooperative stencil access: lane l < 27 owns node (l % 3, l / 3 % 3, l / 9)
 // of the contact's 3x3x3 stencil, so the 27 loads or reductions of a contact
 // go out together instead of in register-limited groups.
