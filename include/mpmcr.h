@@ -254,7 +254,7 @@ mpm_status mpm_synchronize(mpm_ctx* ctx);
 /* Options. MPM_OPT_PROFILE: nonzero records CUDA events around each phase of
    each substep (read with mpm_get_phase_times). MPM_OPT_SORT_EVERY: sort the
    particles every k-th time step (default 1). MPM_OPT_P2G_CHUNK: particles
-   per P2G thread block (256, 512 or 1024; default 512). */
+   per P2G thread block (256, 512 or 1024; default 256). */
 enum { MPM_OPT_PROFILE = 1, MPM_OPT_SORT_EVERY = 2, MPM_OPT_P2G_CHUNK = 3 };
 mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value);
 

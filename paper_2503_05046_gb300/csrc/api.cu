@@ -44,7 +44,7 @@ struct mpm_ctx {
   float* stage = nullptr;  // 24 floats per particle
   bool profile = false;
   int sort_every = 1;
-  int p2g_chunk = 512;
+  int p2g_chunk = 256;
   int64_t step_count = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, cudaEvent_t>> ev_marks;  // (phase starting at this event, event)
@@ -353,6 +353,7 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
        cudaMemset(ctx->impulses, 0, 6 * kMaxBodies * sizeof(double)) == cudaSuccess &&
        cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) return bail(MPM_ERR_CUDA);
+  if (p2g_prepare() != cudaSuccess) return bail(MPM_ERR_CUDA);
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_kernel_ptr(), solve_block_size(), 0) !=
           cudaSuccess ||

@@ -66,6 +66,7 @@ struct P2GArgs {
   DevStats* stats;
 };
 void launch_p2g(const P2GArgs& a, int chunk, cudaStream_t s);
+cudaError_t p2g_prepare();  // once per device: the kernel's shared-memory attributes
 
 // ---- grid.cu: active-block compaction and grid update ----
 void launch_grid(const GridDev& g, const GridArrays& G, float h, int num_sms, DevStats* stats,

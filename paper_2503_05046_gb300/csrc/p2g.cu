@@ -3,51 +3,54 @@
 // (Sec. V-B: one contact point per particle inside a rigid geometry, at the
 // start of the substep).
 //
-// GB300 layout: each thread block takes a contiguous chunk of block-sorted
-// particles, finds the bounding box of their stencils and accumulates mass and
-// momentum into a shared-memory tile of that box. Lanes of a warp whose
-// particles share a base cell first combine their contributions with a
-// segmented shuffle reduction (the warp-level pre-reduction of Sec. V-A), so
-// one shared-memory atomic per node and run is issued. The tile is
-// then flushed with one 16-byte vector reduction (red.global.add.v4.f32) per
-// touched node. When the chunk's box exceeds the tile (the Morton order jumps
-// at a coarse cell boundary, or the chunk straddles the edge of the material)
-// each warp uses its own sub-tile of its own box; only a warp whose box is
-// still too large reduces straight into the grid. The Kirchhoff stress comes
-// precomputed from the previous G2P, so no SVD runs here. Particle planes are
-// read with coalesced 4-byte loads.
+// GB300 layout: each warp takes a contiguous run of 32 x ITEMS cell-sorted
+// particles and accumulates their mass and momentum into a private
+// shared-memory tile of the bounding box of their stencils (one float4
+// (m, p) per node). Lanes whose particles share a base cell (adjacent after
+// the cell-ordered sort) first combine their 27 node contributions with a
+// segmented shuffle reduction (the warp-level pre-reduction of Sec. V-A);
+// the remaining lanes have distinct base cells, so within one node offset
+// they touch distinct nodes and update the private tile with plain
+// read-modify-write, no atomics. The tile is then flushed with one 16-byte
+// vector reduction (red.global.add.v4.f32) per touched node. A warp whose box
+// exceeds its tile (the Morton order jumps at a coarse cell boundary, or the
+// run straddles the edge of the material) reduces straight into the grid.
+// The Kirchhoff stress comes precomputed from the previous G2P, so no SVD
+// runs here. Particle planes are read with coalesced 4-byte loads.
 #include "kernels.h"
 
 namespace mpmcr {
 
 namespace {
 
-constexpr int kTileCap = 2048;  // nodes in the shared tile (32 KB)
 constexpr int kThreads = 256;
-constexpr int kWarpTileCap = kTileCap / (kThreads / 32);  // 256 nodes per warp
+constexpr int kWarps = kThreads / 32;
+constexpr int kWarpTileCap = 512;  // nodes per warp tile (8 KB)
+
+// dynamic shared memory: kWarps tiles of kWarpTileCap float4
+constexpr size_t kDynSmem = sizeof(float4) * kWarps * kWarpTileCap;
 
 template <int ITEMS>
 __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
-  __shared__ float t_m[kTileCap], t_px[kTileCap], t_py[kTileCap], t_pz[kTileCap];
+  extern __shared__ float4 s_tiles[];
   __shared__ DevBody s_body[kMaxBodies];
-  __shared__ int s_min[3], s_max[3];
-  __shared__ unsigned s_cand;
   const GridDev& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int first = blockIdx.x * kThreads * ITEMS;
+  // this warp's particles: [first, first + 32 * ITEMS), lane-contiguous per item
+  const int first = (blockIdx.x * kWarps + warp) * 32 * ITEMS;
+  float4* tile = s_tiles + warp * kWarpTileCap;
 
-  if (tid < 3) { s_min[tid] = 0x7fffffff; s_max[tid] = -0x7fffffff; }
   for (int i = tid; i < a.nb * (int)(sizeof(DevBody) / 4); i += kThreads)
     reinterpret_cast<float*>(s_body)[i] = reinterpret_cast<const float*>(a.bodies)[i];
   __syncthreads();
+  if (first >= a.n) return;
 
-  // stencils of this thread's particles; bounding boxes of the warp and chunk
-  // (the stencils are recomputed below rather than held in registers)
+  // bounding box of the warp's stencils (base nodes)
   bool valid[ITEMS];
   int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
-    const int i = first + it * kThreads + tid;
+    const int i = first + it * 32 + lane;
     valid[it] = i < a.n;
     if (valid[it]) {
       Stencil st;
@@ -66,60 +69,32 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      lo[c] = min(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
-      hi[c] = max(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
-    }
+    lo[c] = __reduce_min_sync(0xffffffffu, lo[c]);
+    hi[c] = __reduce_max_sync(0xffffffffu, hi[c]);
   }
-  if (lane == 0) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) { atomicMin(&s_min[c], lo[c]); atomicMax(&s_max[c], hi[c]); }
-  }
-  __syncthreads();
-  const bool any = s_max[0] >= s_min[0];
-  const int cx0 = s_min[0], cy0 = s_min[1], cz0 = s_min[2];
-  const int cex = any ? s_max[0] - cx0 + 3 : 0, cey = any ? s_max[1] - cy0 + 3 : 0,
-            cez = any ? s_max[2] - cz0 + 3 : 0;
-  const bool block_tile = any && cex * cey * cez <= kTileCap;
-  // the tile this thread accumulates into: the chunk's, or its warp's
-  const bool wany = hi[0] >= lo[0];
-  const int wex = wany ? hi[0] - lo[0] + 3 : 0, wey = wany ? hi[1] - lo[1] + 3 : 0,
-            wez = wany ? hi[2] - lo[2] + 3 : 0;
-  const bool warp_tile = !block_tile && wany && wex * wey * wez <= kWarpTileCap;
-  const bool use_tile = block_tile || warp_tile;
-  const int b0 = block_tile ? cx0 : lo[0], b1 = block_tile ? cy0 : lo[1], b2 = block_tile ? cz0 : lo[2];
-  const int ex = block_tile ? cex : wex, ey = block_tile ? cey : wey, ez = block_tile ? cez : wez;
-  const int toff = block_tile ? 0 : warp * kWarpTileCap;
+  const bool any = hi[0] >= lo[0];
+  const int ex = any ? hi[0] - lo[0] + 3 : 0, ey = any ? hi[1] - lo[1] + 3 : 0,
+            ez = any ? hi[2] - lo[2] + 3 : 0;
+  const bool use_tile = any && ex * ey * ez <= kWarpTileCap;
   const int tile_n = use_tile ? ex * ey * ez : 0;
-  if (block_tile) {
-    for (int t = tid; t < tile_n; t += kThreads) { t_m[t] = 0.f; t_px[t] = 0.f; t_py[t] = 0.f; t_pz[t] = 0.f; }
-  } else if (warp_tile) {
-    for (int t = lane; t < tile_n; t += 32) {
-      t_m[toff + t] = 0.f; t_px[toff + t] = 0.f; t_py[toff + t] = 0.f; t_pz[toff + t] = 0.f;
-    }
-  }
-  if (any && !block_tile && tid == 0) atomicAdd(&a.stats->p2g_global_chunks, 1);
-  // bodies that may hold a particle of this chunk: the signed distance is
+  for (int t = lane; t < tile_n; t += 32) tile[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (any && !use_tile && lane == 0) atomicAdd(&a.stats->p2g_global_chunks, 1);
+  // bodies that may hold a particle of this warp: the signed distance is
   // 1-Lipschitz, so a body whose distance at the box centre exceeds the half
   // diagonal cannot contain any point of the box
-  if (tid < 32) {
-    bool cand = false;
-    if (any && tid < a.nb) {
-      const float c0 = g.ox + g.dx * (0.5f * (cx0 + s_max[0]) + 1.0f);
-      const float c1 = g.oy + g.dx * (0.5f * (cy0 + s_max[1]) + 1.0f);
-      const float c2 = g.oz + g.dx * (0.5f * (cz0 + s_max[2]) + 1.0f);
-      const float h0 = 0.5f * g.dx * (s_max[0] - cx0 + 1), h1 = 0.5f * g.dx * (s_max[1] - cy0 + 1),
-                  h2 = 0.5f * g.dx * (s_max[2] - cz0 + 1);
-      float nrm[3];
-      const float phi = body_sdf(s_body[tid], c0, c1, c2, nrm);
-      cand = phi <= sqrtf(h0 * h0 + h1 * h1 + h2 * h2) * 1.001f + 1e-6f;
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, cand);
-    if (tid == 0) s_cand = m;
+  bool cand_b = false;
+  if (any && lane < a.nb) {
+    const float c0 = g.ox + g.dx * (0.5f * (lo[0] + hi[0]) + 1.0f);
+    const float c1 = g.oy + g.dx * (0.5f * (lo[1] + hi[1]) + 1.0f);
+    const float c2 = g.oz + g.dx * (0.5f * (lo[2] + hi[2]) + 1.0f);
+    const float h0 = 0.5f * g.dx * (hi[0] - lo[0] + 1), h1 = 0.5f * g.dx * (hi[1] - lo[1] + 1),
+                h2 = 0.5f * g.dx * (hi[2] - lo[2] + 1);
+    float nrm[3];
+    const float phi = body_sdf(s_body[lane], c0, c1, c2, nrm);
+    cand_b = phi <= sqrtf(h0 * h0 + h1 * h1 + h2 * h2) * 1.001f + 1e-6f;
   }
-  __syncthreads();
-  const unsigned cand = s_cand;
+  const unsigned cand = __ballot_sync(0xffffffffu, cand_b);
+  __syncwarp();
   const float h = a.h;
   const float dinv = 4.0f * g.inv_dx * g.inv_dx;
 
@@ -127,20 +102,27 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
   // instruction footprint small
 #pragma unroll 1
   for (int it = 0; it < ITEMS; ++it) {
-    const int i = first + it * kThreads + tid;
+    const int i = first + it * 32 + lane;
     Stencil st = Stencil{};
     if (valid[it]) stencil(g, a.P.x(0)[i], a.P.x(1)[i], a.P.x(2)[i], st);
+    // runs of lanes sharing a base cell (contiguous in cell order); without
+    // that order this item of the warp reduces straight into the grid
+    int key = -1 - lane;
+    if (use_tile && valid[it])
+      key = ((st.base[2] - lo[2]) * ey + (st.base[1] - lo[1])) * ex + (st.base[0] - lo[0]);
+    unsigned peers = 1u << lane;
+    bool tile_item = false;
     if (use_tile) {
-      // warp-level pre-reduction (Sec. V-A): lanes whose stencils share a
-      // base cell (adjacent after the cell-ordered sort) add their 27 node
-      // contributions with a segmented shuffle reduction, and only the first
-      // lane of each run issues the shared-memory atomics
+      peers = __match_any_sync(0xffffffffu, key);
+      const int h0 = __ffs(peers) - 1, h1 = 31 - __clz(peers);
+      tile_item = __all_sync(0xffffffffu, peers == ((0xffffffffu >> (31 - h1)) & (0xffffffffu << h0)));
+    }
+    if (tile_item) {
       const Stencil& s = st;
       float mass = 0.f, mvx = 0.f, mvy = 0.f, mvz = 0.f;
       float A[9];
 #pragma unroll
       for (int c = 0; c < 9; ++c) A[c] = 0.f;
-      int l0 = 0, l1 = 0, l2 = 0, key = -1 - lane;
       if (valid[it]) {
         const DevGroup gr = a.groups[a.P.grp[i]];
         float tau[6];
@@ -155,19 +137,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
         mvx = gr.mass * a.P.v(0)[i];
         mvy = gr.mass * a.P.v(1)[i];
         mvz = gr.mass * a.P.v(2)[i];
-        l0 = s.base[0] - b0;
-        l1 = s.base[1] - b1;
-        l2 = s.base[2] - b2;
-        key = (l2 * ey + l1) * ex + l0;
       }
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
       const int head = __ffs(peers) - 1, seg_end = 31 - __clz(peers);
-      const unsigned run = (0xffffffffu >> (31 - seg_end)) & (0xffffffffu << head);
-      const bool contiguous = __all_sync(0xffffffffu, peers == run);
-      const int len = contiguous ? seg_end - head + 1 : 1;
-      const int maxlen = __reduce_max_sync(0xffffffffu, (unsigned)len);
+      const int maxlen = __reduce_max_sync(0xffffffffu, (unsigned)(seg_end - head + 1));
       const int steps = maxlen > 1 ? 32 - __clz(maxlen - 1) : 0;
-      const bool issue = valid[it] && (!contiguous || lane == head);
+      // the run's first lane updates the tile
+      const bool issue = valid[it] && lane == head;
+      const int kz = key / (ex * ey);  // tile-local base cell (valid lanes)
+      const int base_row = key - kz * ex * ey;
 #pragma unroll
       for (int cz = 0; cz < 3; ++cz) {
         const float dz = (cz - s.fx[2]) * g.dx;
@@ -175,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
         for (int cy = 0; cy < 3; ++cy) {
           const float dy = (cy - s.fx[1]) * g.dx;
           const float wyz = s.w[1][cy] * s.w[2][cz];
-          const int row = toff + ((l2 + cz) * ey + (l1 + cy)) * ex + l0;
+          const int row = (kz + cz) * ex * ey + base_row + cy * ex;
 #pragma unroll
           for (int cx = 0; cx < 3; ++cx) {
             const float dxp = (cx - s.fx[0]) * g.dx;
@@ -196,12 +173,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
               }
             }
             if (issue) {
-              const int t = row + cx;
-              atomicAdd(&t_m[t], q0);
-              atomicAdd(&t_px[t], q1);
-              atomicAdd(&t_py[t], q2);
-              atomicAdd(&t_pz[t], q3);
+              float4* t = tile + row + cx;
+              const float4 o = *t;
+              *t = make_float4(o.x + q0, o.y + q1, o.z + q2, o.w + q3);
             }
+            // the issuing lanes of one node offset hit distinct nodes; order
+            // this offset's updates before the next offset's reads
+            __syncwarp();
           }
         }
       }
@@ -294,41 +272,60 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
       }
     }
   }
-  __syncthreads();
   if (!use_tile) return;
-  // flush: one vector reduction per touched node of the (chunk or warp) tile
-  const int fstart = block_tile ? tid : lane, fstride = block_tile ? kThreads : 32;
-  for (int t = fstart; t < tile_n; t += fstride) {
-    const int q = toff + t;
-    const float m = t_m[q];
-    if (m != 0.0f || t_px[q] != 0.0f || t_py[q] != 0.0f || t_pz[q] != 0.0f) {
+  __syncwarp();
+  // flush: one vector reduction per touched node of the warp tile
+  for (int t = lane; t < tile_n; t += 32) {
+    const float4 q = tile[t];
+    if (q.x != 0.0f || q.y != 0.0f || q.z != 0.0f || q.w != 0.0f) {
       const int lx = t % ex, r = t / ex, ly = r % ey, lz = r / ey;
-      const int node = node_index(g, b0 + lx, b1 + ly, b2 + lz);
-      red_add_v4(a.G.mp + node, m, t_px[q], t_py[q], t_pz[q]);
+      const int node = node_index(g, lo[0] + lx, lo[1] + ly, lo[2] + lz);
+      red_add_v4(a.G.mp + node, q.x, q.y, q.z, q.w);
     }
   }
   // mark the 4^3 blocks the tile overlaps
-  const int bx0 = b0 >> 2, by0 = b1 >> 2, bz0 = b2 >> 2;
-  const int bnx = ((b0 + ex - 1) >> 2) - bx0 + 1, bny = ((b1 + ey - 1) >> 2) - by0 + 1,
-            bnz = ((b2 + ez - 1) >> 2) - bz0 + 1;
-  for (int t = fstart; t < bnx * bny * bnz; t += fstride) {
+  const int bx0 = lo[0] >> 2, by0 = lo[1] >> 2, bz0 = lo[2] >> 2;
+  const int bnx = ((lo[0] + ex - 1) >> 2) - bx0 + 1, bny = ((lo[1] + ey - 1) >> 2) - by0 + 1,
+            bnz = ((lo[2] + ez - 1) >> 2) - bz0 + 1;
+  for (int t = lane; t < bnx * bny * bnz; t += 32) {
     const int qx = t % bnx, r = t / bnx, qy = r % bny, qz = r / bny;
     a.G.mark[((bz0 + qz) * g.nby + (by0 + qy)) * g.nbx + (bx0 + qx)] = 1;
   }
 }
 
+template <int ITEMS>
+void launch_items(const P2GArgs& a, cudaStream_t s) {
+  const int per_block = kThreads * ITEMS;
+  k_p2g<ITEMS><<<(a.n + per_block - 1) / per_block, kThreads, kDynSmem, s>>>(a);
+}
+
+template <int ITEMS>
+cudaError_t prepare_items() {
+  cudaError_t e = cudaFuncSetAttribute(k_p2g<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kDynSmem);
+  if (e != cudaSuccess) return e;
+  // room for three blocks' tiles per SM
+  return cudaFuncSetAttribute(k_p2g<ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
 }  // namespace
+
+cudaError_t p2g_prepare() {
+  cudaError_t e = prepare_items<1>();
+  if (e == cudaSuccess) e = prepare_items<2>();
+  if (e == cudaSuccess) e = prepare_items<4>();
+  return e;
+}
 
 void launch_p2g(const P2GArgs& a, int chunk, cudaStream_t s) {
   if (a.n <= 0) return;
   const int items = chunk / kThreads;
-  if (items <= 1) {
-    k_p2g<1><<<(a.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
-  } else if (items == 2) {
-    k_p2g<2><<<(a.n + 2 * kThreads - 1) / (2 * kThreads), kThreads, 0, s>>>(a);
-  } else {
-    k_p2g<4><<<(a.n + 4 * kThreads - 1) / (4 * kThreads), kThreads, 0, s>>>(a);
-  }
+  if (items <= 1)
+    launch_items<1>(a, s);
+  else if (items == 2)
+    launch_items<2>(a, s);
+  else
+    launch_items<4>(a, s);
 }
 
 }  // namespace mpmcr
