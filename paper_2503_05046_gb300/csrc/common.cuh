@@ -246,7 +246,13 @@ __device__ __forceinline__ float det3(const float (&A)[9]) {
          A[2] * (A[3] * A[7] - A[4] * A[6]);
 }
 
-__device__ __forceinline__ void polar_svd(const float (&F)[9], Polar& P) {
+constexpr int kSvdSweeps = 5;      // most cyclic Jacobi sweeps from the identity
+constexpr int kSvdWarmSweeps = 2;  // most sweeps from a nearly diagonalising V0
+
+// V0 (optional): a rotation that nearly diagonalises F^T F (the V of a nearby
+// F), from which `sweeps` Jacobi sweeps suffice.
+__device__ __forceinline__ void polar_svd(const float (&F)[9], Polar& P, const float* V0 = nullptr,
+                                          int sweeps = kSvdSweeps) {
   float D[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) D[i] = F[i];
@@ -261,11 +267,35 @@ __device__ __forceinline__ void polar_svd(const float (&F)[9], Polar& P) {
   float a02 = D[2] + D[6] + dtd(0, 2);
   float a12 = D[5] + D[7] + dtd(1, 2);
   float* V = P.V;
+  if (V0) {
+    // A <- V0^T A V0 (orthogonal congruence: the absolute accuracy of A near
+    // F = I is kept) and V <- V0
+    const float M[9] = {a00, a01, a02, a01, a11, a12, a02, a12, a22};
+    float W[9];  // M V0
 #pragma unroll
-  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.0f : 0.0f;
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        W[3 * r + c] = M[3 * r] * V0[c] + M[3 * r + 1] * V0[3 + c] + M[3 * r + 2] * V0[6 + c];
+    auto vtw = [&](int r, int c) {
+      return V0[r] * W[c] + V0[3 + r] * W[3 + c] + V0[6 + r] * W[6 + c];
+    };
+    a00 = vtw(0, 0); a11 = vtw(1, 1); a22 = vtw(2, 2);
+    a01 = vtw(0, 1); a02 = vtw(0, 2); a12 = vtw(1, 2);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) V[i] = V0[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.0f : 0.0f;
+  }
   float (&Vr)[9] = P.V;
 #pragma unroll 1
-  for (int sweep = 0; sweep < 5; ++sweep) {
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    // converged once the off-diagonal part is below FP32 resolution of the
+    // diagonal (squared norms; a zero matrix needs no rotation)
+    const float off = a01 * a01 + a02 * a02 + a12 * a12;
+    const float dia = a00 * a00 + a11 * a11 + a22 * a22;
+    if (off <= 1e-15f * dia) break;
     jacobi_pair(a00, a11, a01, a02, a12, Vr, 0, 1);
     jacobi_pair(a00, a22, a02, a01, a12, Vr, 0, 2);
     jacobi_pair(a11, a22, a12, a01, a02, Vr, 1, 2);
@@ -382,10 +412,11 @@ __device__ __forceinline__ void tau_corotated(const DevGroup& gr, const Polar& P
   tau_from(P.U, d, gr.lam * (1.0f + jm1) * jm1, t);
 }
 
-// Kirchhoff stress of a given F (no plastic projection).
-__device__ __forceinline__ void kirchhoff(const DevGroup& gr, const float (&F)[9], float (&t)[6]) {
+// Kirchhoff stress of a given F (no plastic projection); V0 as in polar_svd.
+__device__ __forceinline__ void kirchhoff(const DevGroup& gr, const float (&F)[9], float (&t)[6],
+                                          const float* V0 = nullptr, int sweeps = kSvdSweeps) {
   Polar P;
-  polar_svd(F, P);
+  polar_svd(F, P, V0, sweeps);
   if (gr.model == MPM_DRUCKER_PRAGER) {
     float e[3];
     hencky_strain(P, e);
@@ -399,8 +430,9 @@ __device__ __forceinline__ void kirchhoff(const DevGroup& gr, const float (&F)[9
 // Hencky strain space for sand (F projected in place), then the Kirchhoff
 // stress of the final F for the next P2G. For an unprojected F one SVD serves
 // both; a projected F = U diag(exp e') V^T is rounded to FP32 when stored, so
-// its stress is taken from the stored value (a second SVD) to keep tau equal
-// to the stress of the state F exactly.
+// its stress is taken from the stored value (a second SVD, started from the
+// first one's V, which nearly diagonalises it) to keep tau equal to the
+// stress of the state F exactly.
 __device__ __forceinline__ void constitutive_update(const DevGroup& gr, float (&F)[9],
                                                     float (&t)[6]) {
   Polar P;
@@ -440,7 +472,7 @@ __device__ __forceinline__ void constitutive_update(const DevGroup& gr, float (&
     for (int c = 0; c < 3; ++c)
       F[3 * r + c] = U[3 * r] * sv[0] * V[3 * c] + U[3 * r + 1] * sv[1] * V[3 * c + 1] +
                      U[3 * r + 2] * sv[2] * V[3 * c + 2];
-  kirchhoff(gr, F, t);
+  kirchhoff(gr, F, t, V, kSvdWarmSweeps);
 }
 
 // --------------------------------------------------------------------------
