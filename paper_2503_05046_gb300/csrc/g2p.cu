@@ -17,7 +17,7 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__global__ void __launch_bounds__(kThreads) k_g2p(G2PArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) k_g2p(G2PArgs a) {
   const GridDev& g = a.g;
   if (blockIdx.x == 0) {
     if (threadIdx.x == 0) {

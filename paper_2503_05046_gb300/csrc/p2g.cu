@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
       const int kz = key / (ex * ey);  // tile-local base cell (valid lanes)
       const int base_row = key - kz * ex * ey;
 #pragma unroll
+      // (invalid lanes carry zero mass, momentum and weights)
+      const float dx0[3] = {(0.f - s.fx[0]) * g.dx, (1.f - s.fx[0]) * g.dx, (2.f - s.fx[0]) * g.dx};
       for (int cz = 0; cz < 3; ++cz) {
         const float dz = (cz - s.fx[2]) * g.dx;
 #pragma unroll
@@ -153,14 +155,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
           const float dy = (cy - s.fx[1]) * g.dx;
           const float wyz = s.w[1][cy] * s.w[2][cz];
           const int row = (kz + cz) * ex * ey + base_row + cy * ex;
+          // momentum of the row's nodes up to the x term: m v + A (., dy, dz)
+          const float rx = fmaf(A[2], dz, fmaf(A[1], dy, mvx));
+          const float ry = fmaf(A[5], dz, fmaf(A[4], dy, mvy));
+          const float rz = fmaf(A[8], dz, fmaf(A[7], dy, mvz));
 #pragma unroll
           for (int cx = 0; cx < 3; ++cx) {
-            const float dxp = (cx - s.fx[0]) * g.dx;
-            const float w = valid[it] ? s.w[0][cx] * wyz : 0.f;
+            const float w = s.w[0][cx] * wyz;
             float q0 = w * mass;
-            float q1 = w * (mvx + A[0] * dxp + A[1] * dy + A[2] * dz);
-            float q2 = w * (mvy + A[3] * dxp + A[4] * dy + A[5] * dz);
-            float q3 = w * (mvz + A[6] * dxp + A[7] * dy + A[8] * dz);
+            float q1 = w * fmaf(A[0], dx0[cx], rx);
+            float q2 = w * fmaf(A[3], dx0[cx], ry);
+            float q3 = w * fmaf(A[6], dx0[cx], rz);
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
               if (k < steps) {
@@ -275,10 +280,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
   if (!use_tile) return;
   __syncwarp();
   // flush: one vector reduction per touched node of the warp tile
+  // t / ex and r / ey by float reciprocals: exact, since t < 2^22 and the
+  // fractional parts stay at least 0.5 / ex away from an integer
+  const float inv_ex = 1.0f / ex, inv_ey = 1.0f / ey;
   for (int t = lane; t < tile_n; t += 32) {
     const float4 q = tile[t];
     if (q.x != 0.0f || q.y != 0.0f || q.z != 0.0f || q.w != 0.0f) {
-      const int lx = t % ex, r = t / ex, ly = r % ey, lz = r / ey;
+      const int r = __float2int_rz(((float)t + 0.5f) * inv_ex), lx = t - r * ex;
+      const int lz = __float2int_rz(((float)r + 0.5f) * inv_ey), ly = r - lz * ey;
       const int node = node_index(g, lo[0] + lx, lo[1] + ly, lo[2] + lz);
       red_add_v4(a.G.mp + node, q.x, q.y, q.z, q.w);
     }
