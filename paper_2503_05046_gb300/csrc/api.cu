@@ -355,8 +355,9 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
   if (!ok) return bail(MPM_ERR_CUDA);
   if (p2g_prepare() != cudaSuccess) return bail(MPM_ERR_CUDA);
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_kernel_ptr(), solve_block_size(), 0) !=
-          cudaSuccess ||
+  if (solve_prepare() != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_kernel_ptr(), solve_block_size(),
+                                                    solve_dynamic_smem()) != cudaSuccess ||
       occ < 1)
     return bail(MPM_ERR_CUDA);
   ctx->solve_blocks = ctx->num_sms * (occ < 2 ? occ : 2);

@@ -94,6 +94,8 @@ struct SolveArgs {
 cudaError_t launch_solve(const SolveArgs& a, int grid_blocks, cudaStream_t s);
 int solve_block_size();
 const void* solve_kernel_ptr();
+size_t solve_dynamic_smem();
+cudaError_t solve_prepare();  // once per device, before the occupancy query
 
 // ---- g2p.cu: grid-to-particle with the constitutive update ----
 struct G2PArgs {

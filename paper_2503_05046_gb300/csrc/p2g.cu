@@ -145,9 +145,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
       const bool issue = valid[it] && lane == head;
       const int kz = key / (ex * ey);  // tile-local base cell (valid lanes)
       const int base_row = key - kz * ex * ey;
-#pragma unroll
       // (invalid lanes carry zero mass, momentum and weights)
       const float dx0[3] = {(0.f - s.fx[0]) * g.dx, (1.f - s.fx[0]) * g.dx, (2.f - s.fx[0]) * g.dx};
+#pragma unroll
       for (int cz = 0; cz < 3; ++cz) {
         const float dz = (cz - s.fx[2]) * g.dx;
 #pragma unroll

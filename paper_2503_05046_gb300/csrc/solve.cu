@@ -179,32 +179,20 @@ __device__ bool reduce_all(const float (&v)[NV], float2* part, Barrier& B, float
           s_tot[lane] = df_norm(S, E);
         }
       } else {
-        float S[NV], E[NV];
+        // lane (c, i) = (lane / NV, lane % NV) sums value i over the blocks
+        // b = c (mod chunks); lanes 0..NV-1 then add the other chunks
+        constexpr int kChunks = 32 / NV;
+        const int i = lane % NV, c = lane / NV;
+        float S = 0.f, E = 0.f;
+        if (c < kChunks)
+          for (int b = c; b < (int)B.n; b += kChunks) df_acc(S, E, __ldcg(part + b * kRedWidth + i));
 #pragma unroll
-        for (int i = 0; i < NV; ++i) { S[i] = 0.f; E[i] = 0.f; }
-        for (int b = lane; b < (int)B.n; b += 32) {
-          const float4* q = reinterpret_cast<const float4*>(part + b * kRedWidth);
-#pragma unroll
-          for (int i = 0; i < NV / 2; ++i) {
-            const float4 d = __ldcg(q + i);
-            df_acc(S[2 * i], E[2 * i], make_float2(d.x, d.y));
-            df_acc(S[2 * i + 1], E[2 * i + 1], make_float2(d.z, d.w));
-          }
+        for (int c2 = 1; c2 < kChunks; ++c2) {
+          const float S2 = __shfl_sync(0xffffffffu, S, (lane + c2 * NV) & 31);
+          const float E2 = __shfl_sync(0xffffffffu, E, (lane + c2 * NV) & 31);
+          if (lane < NV) df_acc(S, E, make_float2(S2, E2));
         }
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-          float Si = S[i], Ei = E[i];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const float S2 = __shfl_xor_sync(0xffffffffu, Si, o);
-            const float E2 = __shfl_xor_sync(0xffffffffu, Ei, o);
-            float t, e;
-            two_sum(Si, S2, t, e);
-            Si = t;
-            Ei = Ei + E2 + e;
-          }
-          if (lane == 0) s_tot[i] = df_norm(Si, Ei);
-        }
+        if (lane < NV) s_tot[lane] = df_norm(S, E);
       }
     }
     __syncthreads();
@@ -259,22 +247,31 @@ __device__ __forceinline__ void load_contact(const Contacts& C, int p, float4& x
   n0 = q.w;
 }
 
-// contact parts of f'(alpha_k) and f''(alpha_k), k < kLsPoints, for this
-// thread's contacts (acc[k] and acc[kLsPoints + k])
-__device__ __forceinline__ void ls_contact(const SolveArgs& a, const DevBody& bd, const float4& xp,
-                                           const float (&n)[3], float n0, const float4& vc,
-                                           const float (&e)[3], const float (&alphas)[kLsPoints],
-                                           float (&acc)[2 * kLsPoints]) {
-  const float u[3] = {vc.x, vc.y, vc.z};
-  ContactLine L;
-  contact_line(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, e, L);
-#pragma unroll
-  for (int k = 0; k < kLsPoints; ++k) {
-    float d1, d2;
-    contact_line_eval(L, alphas[k], d1, d2);
-    acc[k] += d1;
-    acc[kLsPoints + k] += d2;
-  }
+// Line-search cache: a thread's k-th contact (k < kLsCacheDepth) keeps its
+// line form in shared-memory slot k * kThreads + tid across the passes of one
+// line search, packed into three float4: (v_n, e_n, vhat, phi0),
+// (mu n0, body, v_t.x, v_t.y), (v_t.z, e_t); k and d come from the body table.
+constexpr int kLsCacheDepth = 4;
+constexpr int kLsCacheSlots = kLsCacheDepth * kThreads;
+
+__device__ __forceinline__ void line_store(float4* cache, int slot, const ContactLine& L, int body) {
+  cache[3 * slot] = make_float4(L.vn0, L.en, L.vhat, L.phi0);
+  cache[3 * slot + 1] = make_float4(L.mun0, __int_as_float(body), L.vt[0], L.vt[1]);
+  cache[3 * slot + 2] = make_float4(L.vt[2], L.et[0], L.et[1], L.et[2]);
+}
+
+__device__ __forceinline__ void line_load(const float4* cache, int slot, const DevBody* bodies,
+                                          float h, float eps2, ContactLine& L) {
+  const float4 q0 = cache[3 * slot], q1 = cache[3 * slot + 1], q2 = cache[3 * slot + 2];
+  const DevBody& bd = bodies[__float_as_int(q1.y)];
+  L.vn0 = q0.x; L.en = q0.y; L.vhat = q0.z; L.phi0 = q0.w;
+  L.mun0 = q1.x; L.vt[0] = q1.z; L.vt[1] = q1.w; L.vt[2] = q2.x;
+  L.et[0] = q2.y; L.et[1] = q2.z; L.et[2] = q2.w;
+  L.hk = h * bd.k;
+  L.h = h;
+  L.d = bd.d;
+  L.eps2 = eps2;
+  L.et2 = L.et[0] * L.et[0] + L.et[1] * L.et[1] + L.et[2] * L.et[2];
 }
 
 // Exact line search of Alg. 1 on f'(alpha) = B + alpha A + sum_p dl_c . dv_c,
@@ -344,6 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   __shared__ float2 s_A, s_B;
   __shared__ float s_alpha;
   __shared__ int s_dec;
+  extern __shared__ float4 s_line[];  // 3 x kLsCacheSlots: the line-search cache
   LineSearch ls;  // used by thread 0
   const int tid = threadIdx.x;
   const int count = *a.C.count;
@@ -429,6 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   const bool local_ls = nc <= kLocalLsMax;
   const int ls_first = local_ls ? tid : gtid, ls_stride = local_ls ? kThreads : gstride;
   Barrier Bl{nullptr, 1u, a.status};
+  const float eps2 = a.eps_s * a.eps_s;
   float alpha = 0.f;
   int it = 0, ls_passes = 0;
   float resid = 0.f;
@@ -604,13 +603,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
       float acc[2 * kLsPoints];
 #pragma unroll
       for (int k = 0; k < 2 * kLsPoints; ++k) acc[k] = 0.f;
-      for (int p = ls_first; p < nc; p += ls_stride) {
-        float4 xp; float n[3]; float n0;
-        load_contact(a.C, p, xp, n, n0);
-        const float4 q = __ldcg(a.C.dvc + p);
-        const float e[3] = {q.x, q.y, q.z};
-        // v_c was written by another warp in phase G: read it from L2
-        ls_contact(a, s_body[a.C.id[p].y], xp, n, n0, __ldcg(a.C.vc + p), e, alphas, acc);
+      int k = 0;
+      for (int p = ls_first; p < nc; p += ls_stride, ++k) {
+        const int slot = k * kThreads + tid;
+        ContactLine L;
+        if (pass > 0 && k < kLsCacheDepth) {
+          line_load(s_line, slot, s_body, a.h, eps2, L);
+        } else {
+          float4 xp; float n[3]; float n0;
+          load_contact(a.C, p, xp, n, n0);
+          const int b = a.C.id[p].y;
+          const DevBody& bd = s_body[b];
+          // written by other blocks in phases G and C: read from L2
+          const float4 vc = __ldcg(a.C.vc + p), q = __ldcg(a.C.dvc + p);
+          const float u[3] = {vc.x, vc.y, vc.z}, e[3] = {q.x, q.y, q.z};
+          contact_line(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, e, L);
+          if (k < kLsCacheDepth) line_store(s_line, slot, L, b);
+        }
+#pragma unroll
+        for (int j = 0; j < kLsPoints; ++j) {
+          float d1, d2;
+          contact_line_eval(L, alphas[j], d1, d2);
+          acc[j] += d1;
+          acc[kLsPoints + j] += d2;
+        }
       }
       if (!reduce_all(acc, sl, local_ls ? Bl : B, s_red, s_tot)) return;
       lap(3);
@@ -678,12 +694,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
 
 int solve_block_size() { return kThreads; }
 const void* solve_kernel_ptr() { return reinterpret_cast<const void*>(&k_solve); }
+size_t solve_dynamic_smem() { return 3 * sizeof(float4) * kLsCacheSlots; }
+cudaError_t solve_prepare() {
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_solve),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_dynamic_smem());
+}
 
 cudaError_t launch_solve(const SolveArgs& a, int grid_blocks, cudaStream_t s) {
   SolveArgs args = a;
   void* params[] = {&args};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_solve), dim3(grid_blocks),
-                                     dim3(kThreads), params, 0, s);
+                                     dim3(kThreads), params, solve_dynamic_smem(), s);
 }
 
 }  // namespace mpmcr
