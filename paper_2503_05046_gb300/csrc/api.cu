@@ -280,7 +280,11 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
   GridDev& g = ctx->g;
   g.dx = (float)spec->dx;
   g.inv_dx = (float)(1.0 / spec->dx);
+  g.inv_dx_lo = (float)(1.0 / spec->dx - (double)g.inv_dx);
   g.ox = (float)spec->origin[0]; g.oy = (float)spec->origin[1]; g.oz = (float)spec->origin[2];
+  g.ox_lo = (float)(spec->origin[0] - (double)g.ox);
+  g.oy_lo = (float)(spec->origin[1] - (double)g.oy);
+  g.oz_lo = (float)(spec->origin[2] - (double)g.oz);
   g.gx = (float)spec->gravity[0]; g.gy = (float)spec->gravity[1]; g.gz = (float)spec->gravity[2];
   g.rx = spec->res[0]; g.ry = spec->res[1]; g.rz = spec->res[2];
   g.nbx = g.rx / 4; g.nby = g.ry / 4; g.nbz = g.rz / 4;

@@ -28,7 +28,9 @@ constexpr uint32_t kStLineSearch = 1u << MPM_ERR_LINE_SEARCH;
 
 struct GridDev {
   float dx, inv_dx;
+  float inv_dx_lo;        // 1/dx = inv_dx + inv_dx_lo (double-float)
   float ox, oy, oz;       // origin
+  float ox_lo, oy_lo, oz_lo;  // origin = o + o_lo (double-float)
   float gx, gy, gz;       // gravity
   int rx, ry, rz;         // nodes per axis
   int nbx, nby, nbz;      // 4^3 blocks per axis
@@ -181,15 +183,39 @@ struct Stencil {
   float w[3][3];
 };
 
+// Base node and fractional offset of coordinate x along one axis: the cell
+// coordinate (x - origin) / dx is formed in double-float (the origin and 1/dx
+// are stored as FP32 pairs), so that f is accurate to FP32 rounding of f
+// itself (~6e-8 of a cell) instead of FP32 rounding of the cell coordinate
+// (~1e-7 of the node index, 1e-5 of a cell on a 128-node axis): the B-spline
+// weights then depend only on the stored position.
+__device__ __forceinline__ void cell_coord(float x, float o, float o_lo, float inv, float inv_lo,
+                                           int& base, float& f) {
+  float dh, dl;
+  two_sum(x, -o, dh, dl);
+  dl -= o_lo;
+  const float p = dh * inv;
+  const float lo = fmaf(dh, inv, -p) + fmaf(dh, inv_lo, dl * inv);
+  const float b = floorf(p - 0.5f);
+  f = (p - b) + lo;  // p - b is exact
+  base = (int)b;
+  if (f < 0.5f) {
+    f += 1.0f;
+    base -= 1;
+  } else if (f >= 1.5f) {
+    f -= 1.0f;
+    base += 1;
+  }
+}
+
 __device__ __forceinline__ void stencil(const GridDev& g, float x, float y, float z,
                                         Stencil& s) {
-  float xi[3] = {(x - g.ox) * g.inv_dx, (y - g.oy) * g.inv_dx, (z - g.oz) * g.inv_dx};
+  cell_coord(x, g.ox, g.ox_lo, g.inv_dx, g.inv_dx_lo, s.base[0], s.fx[0]);
+  cell_coord(y, g.oy, g.oy_lo, g.inv_dx, g.inv_dx_lo, s.base[1], s.fx[1]);
+  cell_coord(z, g.oz, g.oz_lo, g.inv_dx, g.inv_dx_lo, s.base[2], s.fx[2]);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    float b = floorf(xi[a] - 0.5f);
-    s.base[a] = (int)b;
-    float f = xi[a] - b;
-    s.fx[a] = f;
+    const float f = s.fx[a];
     float t0 = 1.5f - f, t1 = f - 1.0f, t2 = f - 0.5f;
     s.w[a][0] = 0.5f * t0 * t0;
     s.w[a][1] = 0.75f - t1 * t1;

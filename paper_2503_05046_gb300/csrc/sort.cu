@@ -29,12 +29,14 @@ __global__ void k_keys(GridDev g, const float* __restrict__ x0, const float* __r
                        uint32_t* __restrict__ vals) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float xi[3] = {(x0[i] - g.ox) * g.inv_dx, (x1[i] - g.oy) * g.inv_dx, (x2[i] - g.oz) * g.inv_dx};
+  // the base node of the particle's stencil, as P2G computes it
+  Stencil st;
+  stencil(g, x0[i], x1[i], x2[i], st);
   int lim[3] = {g.nbx - 1, g.nby - 1, g.nbz - 1};
   uint32_t b[3], c[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    int base = (int)floorf(xi[a] - 0.5f);
+    const int base = st.base[a];
     int blk = base >> 2;  // arithmetic shift: floor division for negatives
     c[a] = (uint32_t)(base & 3);
     if (blk < 0) { blk = 0; c[a] = 0; }

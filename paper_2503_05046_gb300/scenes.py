@@ -160,6 +160,29 @@ def sand_column(n_side=12, seed=SEED_BASE + 11, dx=0.01, h=1e-4, with_paddle=Tru
             "bodies": bodies, "h": h, "substeps": 10}
 
 
+def sand_random(n_particles=8000, ppc=1.0, seed=SEED_BASE + 12, dx=0.01, h=1e-4,
+                penetration=0.0, speed=0.1):
+    """Sand sampled uniformly at random (not on a lattice) at about `ppc`
+    particles per grid cell in a cube over a half-space, with seeded random
+    velocities of up to `speed` per component: the sparse random sampling of
+    the granular scooping workload (about one particle per cell) at a size
+    the oracle runs in seconds. The cube's bottom reaches `penetration` below
+    the plane, so the lowest particles start in contact."""
+    rng = np.random.default_rng(seed)
+    side = (n_particles / ppc) ** (1.0 / 3.0) * dx
+    x = rng.uniform((-side / 2, -side / 2, -penetration),
+                    (side / 2, side / 2, side - penetration), (n_particles, 3))
+    v = rng.uniform(-speed, speed, (n_particles, 3))
+    g = {"x": x.astype(np.float32), "v": v.astype(np.float32),
+         "vol": float(side ** 3 / n_particles), "material": dict(SAND)}
+    bodies = [body(HALFSPACE, mu=0.4)]
+    res = 4 * int(np.ceil((side / dx + 12) / 4))  # grid sizes are multiples of 4
+    grid = {"dx": dx, "res": (res, res, res), "origin": (-res * dx / 2, -res * dx / 2, -0.04),
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    return {"name": "sand_random_%d" % n_particles, "grid": grid, "groups": [g],
+            "bodies": bodies, "h": h, "substeps": 10}
+
+
 def n_particles(scene):
     return int(sum(len(g["x"]) for g in scene["groups"]))
 

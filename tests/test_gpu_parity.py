@@ -92,14 +92,20 @@ def run_parity(native, sc, n_sub=2, warm_steps=0, warm_solver=None, tol_v=TOL_V,
             # has a relative error above 1e-5)
             mid = om >= 1e-3 * mass_p
             assert rel_linf(vs[mid], ovs[mid]) < 1e-5
-            # post-contact velocity: the solve bounds the error in the M-norm,
-            # ||v - v_opt||_M <= ||M^-1/2 grad||, so node i may deviate by
-            # residual / sqrt(m_i); checked in the M-norm over all nodes and
-            # pointwise on nodes holding at least half a particle mass
-            dm = np.sqrt(om)[:, None] * (v - ov)
-            assert np.linalg.norm(dm) <= 1e-5 * np.linalg.norm(np.sqrt(om)[:, None] * ov)
-            heavy = om >= 0.5 * mass_p
-            assert rel_linf(v[heavy], ov[heavy]) < 1e-5
+            # post-contact velocity: the objective is M-strongly convex, so the
+            # stopping test of Alg. 1 bounds the solve's error in the M-norm,
+            # ||v - v_opt||_M <= ||M^-1/2 grad|| <= r * scale with r the
+            # relative residual (1e-6) and scale >= ||M^1/2 v||; node i may
+            # thus deviate by r * scale / sqrt(m_i) (about 2x for the FP32
+            # evaluation of the stopping norms). Checked in the M-norm over all
+            # nodes and pointwise with that bound.
+            sm = np.sqrt(om)[:, None]
+            dm = sm * (v - ov)
+            scale = np.linalg.norm(sm * ov)
+            assert np.linalg.norm(dm) <= 1e-5 * scale
+            vmax_g = np.max(np.abs(ov))
+            bound = 1e-5 * vmax_g + 2.0 * 1e-6 * scale / np.sqrt(om)
+            assert np.all(np.abs(v - ov).max(1) <= bound)
         report.append((k, info.n_contacts, info.iters, stats.iters_total, ev))
     sim.close()
     return report
@@ -168,3 +174,15 @@ def test_sort_only_step_keeps_state_bit_exact(native):
     for key in a:
         assert np.array_equal(a[key], b[key])
     sim.close()
+
+
+@pytest.mark.parametrize("ppc", [1.0, 4.0])
+def test_random_sparse_sand_parity(native, ppc):
+    """Sand sampled at random at about one (and four) particles per cell, as in
+    the granular scooping benchmark, with the lowest particles starting in
+    contact with the ground: P2G's short-run path (lanes updating the warp tile
+    in rounds) and its shuffle pre-reduction path, and G2P's Drucker-Prager
+    update, off the lattice."""
+    sc = scenes.sand_random(n_particles=8000, ppc=ppc, penetration=0.02 * 0.01)
+    rep = run_parity(native, sc, n_sub=3)
+    assert any(r[1] > 0 for r in rep)
