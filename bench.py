@@ -266,6 +266,8 @@ def run_ours(args):
     }
     if clk:
         line["clocks"] = clk
+    if not args.no_small:
+        line["small_scenes"] = small_scene_latency(native)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, sim, native)
     sim.close()
@@ -274,6 +276,49 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def small_scene_latency(native, n_steps=10):
+    """Latency per substep of the 8,000-particle elastic cube (L2-resident and
+    launch-bound, so reported as latency rather than a bandwidth fraction): the
+    cube dropped from 0.2 m (free fall over the measured steps) and the same
+    cube caught at touch-down on the ground (contacts every substep), the
+    latter at the paper's tolerance and at 1e-6, with QN iterations per
+    substep."""
+    import torch
+    from paper_2503_05046_gb300 import scenes
+    out = {}
+    cases = (("cube_drop_8k", scenes.cube_drop(), 5e-2),
+             ("cube_contact_8k", scenes.cube_contact(n_side=20, v0=(0.0, 0.0, -0.05)), 5e-2),
+             ("cube_contact_8k_tight", scenes.cube_contact(n_side=20, v0=(0.0, 0.0, -0.05)), 1e-6))
+    for name, sc, eps in cases:
+        sim = native.Sim(sc)
+        solver = native.solver_params(eps_r=eps, max_iters=200000)
+        N = sc["substeps"]
+        sim.step(solver=solver, check=False)
+        st0 = sim.get_particles()
+        b0 = sim.bodies()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(sim.torch_stream)
+        for _ in range(n_steps):
+            native.mpm_step(sim.ctx, sc["h"], N, solver, want_stats=False)
+        ev1.record(sim.torch_stream)
+        torch.cuda.synchronize()
+        us = 1e3 * ev0.elapsed_time(ev1) / (n_steps * N)
+        # iteration counts from a repeat of the same steps with statistics
+        sim.set_particles(st0["x"], st0["v"], st0["C"], st0["F"])
+        sim.set_bodies(b0)
+        iters, subs, contacts = 0, 0, 0
+        for _ in range(n_steps):
+            st = sim.step(solver=solver, check=False)[1]
+            iters += st.iters_total
+            subs += st.substeps
+            contacts = max(contacts, st.contacts_max)
+        out[name] = {"us_per_substep": us, "eps_r": eps, "iters_per_substep": iters / max(subs, 1),
+                     "contacts_max": contacts, "particles": scenes.n_particles(sc)}
+        sim.close()
+    return out
 
 
 def C_sizeof_body(native):
@@ -358,6 +403,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--max-iters", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-small", action="store_true", help="skip the 8k-particle latency cases")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -25,13 +25,13 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kWarpTileCap = 512;  // nodes per warp tile (8 KB)
+constexpr int kWarpTileCap = 384;  // nodes per warp tile (6 KB)
 
 // dynamic shared memory: kWarps tiles of kWarpTileCap float4
 constexpr size_t kDynSmem = sizeof(float4) * kWarps * kWarpTileCap;
 
 template <int ITEMS>
-__global__ void __launch_bounds__(kThreads, 3) k_p2g(P2GArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) k_p2g(P2GArgs a) {
   extern __shared__ float4 s_tiles[];
   __shared__ DevBody s_body[kMaxBodies];
   const GridDev& g = a.g;
@@ -313,7 +313,7 @@ cudaError_t prepare_items() {
   cudaError_t e = cudaFuncSetAttribute(k_p2g<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kDynSmem);
   if (e != cudaSuccess) return e;
-  // room for three blocks' tiles per SM
+  // room for four blocks' tiles per SM
   return cudaFuncSetAttribute(k_p2g<ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
