@@ -254,8 +254,21 @@ mpm_status mpm_synchronize(mpm_ctx* ctx);
 /* Options. MPM_OPT_PROFILE: nonzero records CUDA events around each phase of
    each substep (read with mpm_get_phase_times). MPM_OPT_SORT_EVERY: sort the
    particles every k-th time step (default 1). MPM_OPT_P2G_CHUNK: particles
-   per P2G thread block (256, 512 or 1024; default 256). */
-enum { MPM_OPT_PROFILE = 1, MPM_OPT_SORT_EVERY = 2, MPM_OPT_P2G_CHUNK = 3 };
+   per P2G thread block (256, 512 or 1024; default 256). MPM_OPT_GRAPHS:
+   nonzero (default) records each step's launch sequence once as a CUDA graph
+   and replays it while the particle count, substep count, h, solver
+   parameters, body count and launch options stay the same (a change
+   re-records; profiling launches directly); zero always launches directly.
+   MPM_OPT_SOLVE_BLOCKS: at most this many thread blocks (one per SM) work on
+   the contact solve (0, the default: as many as the device holds); a small
+   cap lets contexts on other streams run beside a small scene's solve. */
+enum {
+  MPM_OPT_PROFILE = 1,
+  MPM_OPT_SORT_EVERY = 2,
+  MPM_OPT_P2G_CHUNK = 3,
+  MPM_OPT_GRAPHS = 4,
+  MPM_OPT_SOLVE_BLOCKS = 5
+};
 mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value);
 
 /* Phases timed when profiling is on. */

@@ -43,6 +43,18 @@ struct mpm_ctx {
   SortBuffers sb{};
   float* stage = nullptr;  // 24 floats per particle
   bool profile = false;
+  // CUDA graphs of the step's launch sequence, one per particle buffer the
+  // step starts from (the sort ping-pongs between the two), re-captured when
+  // anything baked into the launches changes
+  bool use_graphs = true;
+  struct GraphKey {
+    int64_t n = -1;
+    int n_substeps = 0, nb = 0, chunk = 0, sort_now = 0, solve_blocks = 0;
+    float h = 0.f;
+    mpm_solver_params sp{};
+  } gkey[2];
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int solve_blocks_cap = 0;  // 0: as many as the device holds
   int sort_every = 1;
   int p2g_chunk = 256;
   int64_t step_count = 0;
@@ -232,9 +244,50 @@ void release(mpm_ctx* c) {
                   c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (auto& e : c->gexec)
+    if (e) cudaGraphExecDestroy(e);
   for (auto& e : c->ev_marks) cudaEventDestroy(e.second);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+// The launches of one step: the radix sort from particle buffer `from` into
+// the other (if sort_now), then n_substeps substeps on the sorted buffer.
+cudaError_t enqueue_step(mpm_ctx* ctx, int from, bool sort_now, int n_substeps, float hf,
+                         const mpm_solver_params& sp, int solve_blocks, cudaStream_t s) {
+  const int n = (int)ctx->n;
+  const int nb = (int)ctx->bodies.size();
+  int cur = from;
+  if (sort_now) {
+    mark_phase(ctx, MPM_PHASE_SORT);
+    launch_sort(ctx->g, ctx->P[cur], ctx->P[1 - cur], n, ctx->sb, s);
+    cur = 1 - cur;
+  }
+  for (int k = 0; k < n_substeps; ++k) {
+    P2GArgs pa;
+    pa.g = ctx->g; pa.P = ctx->P[cur]; pa.n = n; pa.groups = ctx->groups_d;
+    pa.bodies = ctx->bodies_d; pa.nb = nb; pa.h = hf; pa.G = ctx->G; pa.C = ctx->C;
+    pa.status = ctx->status; pa.stats = ctx->stats;
+    mark_phase(ctx, MPM_PHASE_P2G);
+    launch_p2g(pa, ctx->p2g_chunk, s);
+    mark_phase(ctx, MPM_PHASE_GRID);
+    launch_grid(ctx->g, ctx->G, hf, ctx->num_sms, ctx->stats, s);
+    SolveArgs sa;
+    sa.g = ctx->g; sa.G = ctx->G; sa.C = ctx->C; sa.bodies = ctx->bodies_d; sa.nb = nb;
+    sa.h = hf; sa.eps_s = sp.eps_s; sa.ls_rel_tol = sp.ls_rel_tol; sa.ls_max_iters = sp.ls_max_iters;
+    sa.eps_r = sp.eps_r; sa.eps_a = sp.eps_a; sa.max_iters = sp.max_iters; sa.red = ctx->red;
+    sa.bar = ctx->bar; sa.status = ctx->status; sa.stats = ctx->stats; sa.impulses = ctx->impulses;
+    mark_phase(ctx, MPM_PHASE_SOLVE);
+    const cudaError_t e = launch_solve(sa, solve_blocks, s);
+    if (e != cudaSuccess) return e;
+    G2PArgs ga;
+    ga.g = ctx->g; ga.P = ctx->P[cur]; ga.n = n; ga.groups = ctx->groups_d; ga.G = ctx->G;
+    ga.C = ctx->C; ga.h = hf; ga.bar = ctx->bar; ga.red = ctx->red; ga.stats = ctx->stats;
+    mark_phase(ctx, MPM_PHASE_G2P);
+    launch_g2p(ga, s);
+    mark_phase(ctx, -1);
+  }
+  return cudaGetLastError();
 }
 
 int ceil_log2(int v) {
@@ -552,35 +605,54 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
   }
   CU(cudaMemsetAsync(ctx->stats, 0, sizeof(DevStats), s));
   const int n = (int)ctx->n;
-  if (n > 0 && ctx->step_count % ctx->sort_every == 0) {
-    mark_phase(ctx, MPM_PHASE_SORT);
-    launch_sort(ctx->g, ctx->P[ctx->cur], ctx->P[1 - ctx->cur], n, ctx->sb, s);
-    ctx->cur = 1 - ctx->cur;
-  }
+  const bool sort_now = n > 0 && ctx->step_count % ctx->sort_every == 0;
   const float hf = (float)h;
-  for (int k = 0; k < n_substeps; ++k) {
-    P2GArgs pa;
-    pa.g = ctx->g; pa.P = ctx->P[ctx->cur]; pa.n = n; pa.groups = ctx->groups_d;
-    pa.bodies = ctx->bodies_d; pa.nb = nb; pa.h = hf; pa.G = ctx->G; pa.C = ctx->C;
-    pa.status = ctx->status; pa.stats = ctx->stats;
-    mark_phase(ctx, MPM_PHASE_P2G);
-    launch_p2g(pa, ctx->p2g_chunk, s);
-    mark_phase(ctx, MPM_PHASE_GRID);
-    launch_grid(ctx->g, ctx->G, hf, ctx->num_sms, ctx->stats, s);
-    SolveArgs sa;
-    sa.g = ctx->g; sa.G = ctx->G; sa.C = ctx->C; sa.bodies = ctx->bodies_d; sa.nb = nb;
-    sa.h = hf; sa.eps_s = sp.eps_s; sa.ls_rel_tol = sp.ls_rel_tol; sa.ls_max_iters = sp.ls_max_iters;
-    sa.eps_r = sp.eps_r; sa.eps_a = sp.eps_a; sa.max_iters = sp.max_iters; sa.red = ctx->red;
-    sa.bar = ctx->bar; sa.status = ctx->status; sa.stats = ctx->stats; sa.impulses = ctx->impulses;
-    mark_phase(ctx, MPM_PHASE_SOLVE);
-    CU(launch_solve(sa, ctx->solve_blocks, s));
-    G2PArgs ga;
-    ga.g = ctx->g; ga.P = ctx->P[ctx->cur]; ga.n = n; ga.groups = ctx->groups_d; ga.G = ctx->G;
-    ga.C = ctx->C; ga.h = hf; ga.bar = ctx->bar; ga.red = ctx->red; ga.stats = ctx->stats;
-    mark_phase(ctx, MPM_PHASE_G2P);
-    launch_g2p(ga, s);
-    mark_phase(ctx, -1);
+  const int solve_blocks = ctx->solve_blocks_cap > 0 && ctx->solve_blocks_cap < ctx->solve_blocks
+                               ? ctx->solve_blocks_cap
+                               : ctx->solve_blocks;
+  const int from = ctx->cur;
+  bool launched = false;
+  if (ctx->use_graphs && !ctx->profile && n_substeps > 0) {
+    mpm_ctx::GraphKey k;
+    k.n = n; k.n_substeps = n_substeps; k.nb = nb; k.chunk = ctx->p2g_chunk;
+    k.sort_now = sort_now ? 1 : 0; k.solve_blocks = solve_blocks; k.h = hf; k.sp = sp;
+    const mpm_ctx::GraphKey& o = ctx->gkey[from];
+    const bool same = ctx->gexec[from] && o.n == k.n && o.n_substeps == k.n_substeps && o.nb == k.nb &&
+                      o.chunk == k.chunk && o.sort_now == k.sort_now &&
+                      o.solve_blocks == k.solve_blocks && o.h == k.h &&
+                      memcmp(&o.sp, &k.sp, sizeof(k.sp)) == 0;
+    if (!same) {
+      if (ctx->gexec[from]) {
+        cudaGraphExecDestroy(ctx->gexec[from]);
+        ctx->gexec[from] = nullptr;
+      }
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const cudaError_t le = enqueue_step(ctx, from, sort_now, n_substeps, hf, sp, solve_blocks, s);
+        e = cudaStreamEndCapture(s, &graph);
+        if (e == cudaSuccess) e = le;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->gexec[from], graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e == cudaSuccess) {
+        ctx->gkey[from] = k;
+      } else {
+        // this device or driver cannot capture the sequence: launch directly
+        // from now on (the same kernels, without the graph)
+        cudaGetLastError();
+        if (ctx->gexec[from]) cudaGraphExecDestroy(ctx->gexec[from]);
+        ctx->gexec[from] = nullptr;
+        ctx->use_graphs = false;
+      }
+    }
+    if (ctx->gexec[from]) {
+      CU(cudaGraphLaunch(ctx->gexec[from], s));
+      launched = true;
+    }
   }
+  if (!launched) CU(enqueue_step(ctx, from, sort_now, n_substeps, hf, sp, solve_blocks, s));
+  if (sort_now) ctx->cur = 1 - from;
   CU(cudaGetLastError());
   // async splitting: kinematic bodies move with their frozen velocity
   const double dt = h * n_substeps;
@@ -718,6 +790,13 @@ mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value) {
       if (value != 256 && value != 512 && value != 1024)
         return fail(ctx, MPM_ERR_INVALID_ARG, "P2G chunk must be 256, 512 or 1024");
       ctx->p2g_chunk = (int)value;
+      return MPM_OK;
+    case MPM_OPT_GRAPHS:
+      ctx->use_graphs = value != 0;
+      return MPM_OK;
+    case MPM_OPT_SOLVE_BLOCKS:
+      if (value < 0) return fail(ctx, MPM_ERR_INVALID_ARG, "solve block cap must be >= 0");
+      ctx->solve_blocks_cap = (int)(value > (1 << 20) ? (1 << 20) : value);
       return MPM_OK;
     default:
       return fail(ctx, MPM_ERR_INVALID_ARG, "unknown option");

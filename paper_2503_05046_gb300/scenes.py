@@ -183,6 +183,39 @@ def sand_random(n_particles=8000, ppc=1.0, seed=SEED_BASE + 12, dx=0.01, h=1e-4,
             "bodies": bodies, "h": h, "substeps": 10}
 
 
+def batch_scene(index, seed=SEED_BASE + 4, n_min=2000, n_max=64000, dx=5e-3, h=1e-4,
+                penetration=1e-4):
+    """Scene `index` of a batch of independent scenes of uneven size: a cube of
+    n ~ U[n_min, n_max] particles at 2 per dx per axis (elastic, E log-uniform in
+    [1e4, 2e5] -- the explicit substep's CFL limit at dx = 5e-3 m and h = 1e-4 s
+    is E < 6e5 for rho = 1000 -- or Drucker-Prager sand, chosen by the seed)
+    caught at touch-down: its bottom layer `penetration` into the ground while
+    falling at 0.05 m/s, and a kinematic box gripper jaw moving along +x at
+    0.05 m/s whose face overlaps the cube's -x side by `penetration`."""
+    rng = np.random.default_rng(seed * 1000 + index)
+    n = int(rng.integers(n_min, n_max + 1))
+    n_side = max(int(round(n ** (1.0 / 3.0))), 2)
+    spacing = dx / 2.0
+    half = (n_side - 1) * spacing / 2.0
+    if rng.random() < 0.5:
+        mat = elastic(E=float(10 ** rng.uniform(4.0, np.log10(2e5))), nu=0.3, rho=1000.0)
+    else:
+        mat = dict(SAND)
+    jit = 1e-4 * dx
+    g = cube_group(n_side, spacing, (0.0, 0.0, half - penetration), (0.0, 0.0, -0.05), mat,
+                   jitter=jit, rng=rng)
+    mu = float(rng.uniform(0.2, 0.8))
+    bodies = [body(HALFSPACE, mu=mu),
+              body(BOX, (0.01, half + dx, half + dx), p=(-half - 0.01 + penetration, 0, half + dx),
+                   v=(0.05, 0, 0), mu=mu, kinematic=1)]
+    side = 2 * half + 0.06
+    res = 4 * int(np.ceil((side / dx + 12) / 4))
+    grid = {"dx": dx, "res": (res, res, res), "origin": (-res * dx / 2, -res * dx / 2, -6 * dx),
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    return {"name": "batch_%d_%d" % (index, len(g["x"])), "grid": grid, "groups": [g],
+            "bodies": bodies, "h": h, "substeps": 10}
+
+
 def n_particles(scene):
     return int(sum(len(g["x"]) for g in scene["groups"]))
 
