@@ -127,6 +127,29 @@ typedef struct {
   int32_t kinematic;
 } mpm_rigid_body;
 
+/* Dynamics of a rigid body that the library integrates itself (Eq. (3),
+   without rigid-rigid contact): after each mpm_step its spatial velocity
+   takes the step's external impulse and the contact impulses accumulated
+   over the step's substeps,
+     m (v+ - v) = dt (force + gravity * m) + sum_k impulse on the body,
+     I (w+ - w) = dt (torque - w x I w) + sum_k moment of those impulses,
+   with I = R diag(inertia) R^T and dt = n_substeps * h (semi-implicit
+   Euler), then components outside dof_mask are zeroed and the pose advances
+   with (v+, w+) as for a kinematic body. mass > 0; inertia: principal
+   moments about the body origin in the body frame (kg m^2, > 0); force and
+   torque: constant external load, world frame (N, N m); dof_mask: free
+   degrees of freedom, bits 0-2 translation along world x, y, z, bits 3-5
+   rotation about world x, y, z; gravity nonzero adds mass times the grid
+   spec's gravity. */
+typedef struct {
+  float mass;
+  float inertia[3];
+  float force[3];
+  float torque[3];
+  int32_t dof_mask;
+  int32_t gravity;
+} mpm_rigid_dynamics;
+
 /* Settings of the contact solve (Alg. 1). The iteration stops when
    ||M^-1/2 grad l_p|| < eps_a + eps_r max(||M^1/2 v||, ||M^-1/2 J^T gamma||);
    the paper's defaults are eps_r = 5e-2 and eps_a = machine epsilon (Sec. VI).
@@ -197,13 +220,22 @@ mpm_status mpm_get_particles(mpm_ctx* ctx, float* x, float* v, float* C, float* 
 /* Replace the rigid bodies (at most 16). They apply from the next mpm_step. */
 mpm_status mpm_set_rigid_bodies(mpm_ctx* ctx, int32_t n, const mpm_rigid_body* bodies);
 
-/* Current rigid bodies (kinematic ones after their pose updates). */
+/* Current rigid bodies (kinematic and dynamic ones after their pose
+   updates). */
 mpm_status mpm_get_rigid_bodies(const mpm_ctx* ctx, int32_t n, mpm_rigid_body* out);
+
+/* Make body `index` (of the current set) dynamic with `dyn`, or, with dyn
+   NULL, stop integrating it (it keeps its current pose and velocity and
+   its kinematic flag applies again). A dynamic body's kinematic flag is
+   ignored. Each mpm_step with a dynamic body synchronises at its end to
+   read the step's impulses. mpm_set_rigid_bodies clears all dynamics. */
+mpm_status mpm_set_rigid_dynamics(mpm_ctx* ctx, int32_t index, const mpm_rigid_dynamics* dyn);
 
 /* One rigid time step: n_substeps MPM substeps of size h with the rigid
    bodies frozen (Eq. (4)). The particle order is refreshed (radix sort) at
    the start of the step and reused by all substeps (Sec. V-A). Kinematic
-   bodies then advance by n_substeps*h. `solver` may be NULL for the paper's
+   bodies then advance by n_substeps*h; dynamic bodies (see
+   mpm_set_rigid_dynamics) are integrated with the step's impulses. `solver` may be NULL for the paper's
    defaults (eps_r = 5e-2, eps_a = DBL_EPSILON, eps_s = 1e-4 m/s). With
    `stats` non-NULL the call synchronises, fills it and returns the first
    device-side failure; with NULL it returns without waiting. */

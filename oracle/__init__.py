@@ -34,6 +34,11 @@ class Body(C.Structure):
                 ("kinematic", C.c_int)]
 
 
+class Dynamics(C.Structure):
+    _fields_ = [("mass", C.c_double), ("inertia", C.c_double * 3), ("force", C.c_double * 3),
+                ("torque", C.c_double * 3), ("dof_mask", C.c_int), ("gravity", C.c_int)]
+
+
 class Material(C.Structure):
     _fields_ = [("model", C.c_int), ("E", C.c_double), ("nu", C.c_double),
                 ("friction_angle_deg", C.c_double)]
@@ -101,6 +106,8 @@ def lib():
         L.orc_last_grid.argtypes = [C.c_void_p, C.c_int, _ip, _dp, _dp, _dp]
         L.orc_last_contacts.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _dp, _dp, _dp]
         L.orc_advance_kinematic.argtypes = [C.c_int, C.POINTER(Body), C.c_double]
+        L.orc_rigid_dynamics_step.argtypes = [C.POINTER(Body), C.POINTER(Dynamics), _dp, _dp,
+                                              C.c_double]
         _lib = L
     return _lib
 
@@ -390,6 +397,33 @@ def advance_kinematic(bodies, dt):
         bs[i] = make_body(b)
     lib().orc_advance_kinematic(nb, bs, float(dt))
     return [body_dict(bs[i]) for i in range(nb)]
+
+
+def make_dynamics(dyn):
+    """dict(mass, inertia[3], force[3], torque[3], dof_mask, gravity) -> Dynamics."""
+    d = Dynamics()
+    d.mass = float(dyn["mass"])
+    for key in ("inertia", "force", "torque"):
+        arr = getattr(d, key)
+        val = np.asarray(dyn.get(key, [0, 0, 0]), np.float64).reshape(3)
+        for i in range(3):
+            arr[i] = float(val[i])
+    d.dof_mask = int(dyn.get("dof_mask", 63))
+    d.gravity = int(dyn.get("gravity", 1))
+    return d
+
+
+def rigid_dynamics_step(body, dyn, gravity, impulse, dt):
+    """Eq. (3) for one dynamic body over a time step dt with the step's impulse
+    on the body and its moment about the body origin (impulse[6], world).
+    Returns the new body dict."""
+    b = make_body(body)
+    d = make_dynamics(dyn)
+    lib().orc_rigid_dynamics_step(C.byref(b), C.byref(d), _d(_f64(gravity, (3,))),
+                                  _d(_f64(impulse, (6,))), float(dt))
+    out = body_dict(b)
+    out["shape"] = int(body["shape"])
+    return out
 
 
 def from_scene(scene):

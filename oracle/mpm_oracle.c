@@ -1175,3 +1175,41 @@ void orc_advance_kinematic(int nb, orc_body* bodies, double dt) {
     mat_mul(Q, bodies[b].R, bodies[b].R);
   }
 }
+
+void orc_rigid_dynamics_step(orc_body* b, const orc_dynamics* d, const double gravity[3],
+                             const double impulse[6], double dt) {
+  /* linear momentum */
+  for (int c = 0; c < 3; ++c) {
+    double f = d->force[c];
+    if (d->gravity) f += d->mass * gravity[c];
+    b->v[c] += (dt * f + impulse[c]) / d->mass;
+  }
+  /* angular momentum: I_w = R diag(I) R^T */
+  double D[9] = {d->inertia[0], 0, 0, 0, d->inertia[1], 0, 0, 0, d->inertia[2]};
+  double RD[9], Iw[9];
+  mat_mul(b->R, D, RD);
+  mat_mul_bt(RD, b->R, Iw);
+  double Lw[3];
+  for (int r = 0; r < 3; ++r)
+    Lw[r] = Iw[3 * r] * b->omega[0] + Iw[3 * r + 1] * b->omega[1] + Iw[3 * r + 2] * b->omega[2];
+  double gyro[3];
+  cross3(b->omega, Lw, gyro);
+  double rhs[3];
+  for (int c = 0; c < 3; ++c) rhs[c] = dt * (d->torque[c] - gyro[c]) + impulse[3 + c];
+  /* dw = I_w^-1 rhs with the adjugate: I_w^-1 = cof(I_w)^T / det (symmetric) */
+  double K[9];
+  mat_cofactor(Iw, K);
+  const double det = mat_det(Iw);
+  for (int r = 0; r < 3; ++r)
+    b->omega[r] += (K[r] * rhs[0] + K[3 + r] * rhs[1] + K[6 + r] * rhs[2]) / det;
+  for (int c = 0; c < 3; ++c) {
+    if (!(d->dof_mask & (1 << c))) b->v[c] = 0.0;
+    if (!(d->dof_mask & (1 << (3 + c)))) b->omega[c] = 0.0;
+  }
+  /* pose with the new velocity */
+  for (int c = 0; c < 3; ++c) b->p[c] += dt * b->v[c];
+  double wdt[3] = {dt * b->omega[0], dt * b->omega[1], dt * b->omega[2]};
+  double Q[9];
+  rotation_from_vector(wdt, Q);
+  mat_mul(Q, b->R, b->R);
+}

@@ -203,6 +203,28 @@ int orc_last_contacts(const orc_sim* s, int cap, int* particle, int* body,
    frozen velocity after the N substeps of a time step. */
 void orc_advance_kinematic(int nb, orc_body* bodies, double dt);
 
+/* A rigid body integrated with the contact impulses of a time step (Eq. (3),
+   without rigid-rigid contact): mass, principal inertia about the body origin
+   (body frame), constant external force and torque (world), free degrees of
+   freedom (bits 0-2 translation along world x, y, z; bits 3-5 rotation about
+   world x, y, z) and whether gravity acts on it. */
+typedef struct {
+  double mass;
+  double inertia[3];
+  double force[3];
+  double torque[3];
+  int dof_mask;
+  int gravity;
+} orc_dynamics;
+
+/* One time step dt of Eq. (3): M (v+ - v) = dt k + J^T sum_k gamma with the
+   step's impulse on the body (impulse[0..2], world) and its moment about the
+   body origin (impulse[3..5]); k holds the external load, gravity and the
+   gyroscopic term -w x (I w) at the start of the step; locked degrees of
+   freedom are set to zero; the pose then advances with the new velocity. */
+void orc_rigid_dynamics_step(orc_body* b, const orc_dynamics* d, const double gravity[3],
+                             const double impulse[6], double dt);
+
 #ifdef __cplusplus
 }
 #endif

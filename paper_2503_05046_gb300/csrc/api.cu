@@ -29,6 +29,11 @@ struct mpm_ctx {
   DevGroup* groups_d = nullptr;
   int groups_cap = 0;
   std::vector<mpm_rigid_body> bodies;
+  // dynamic bodies (Eq. (3)): per body, integrated by the library if set
+  std::vector<int> is_dyn;
+  std::vector<mpm_rigid_dynamics> dyn;
+  std::vector<double> imp_seen;  // impulse accumulator at the end of the last step
+  bool imp_seen_valid = false;
   DevBody* bodies_d = nullptr;
   bool bodies_dirty = true;
   GridArrays G{};
@@ -170,6 +175,49 @@ void advance_kinematic(mpm_rigid_body& b, double dt) {
     for (int cc = 0; cc < 3; ++cc)
       R[3 * r + cc] = Q[3 * r] * b.R[cc] + Q[3 * r + 1] * b.R[3 + cc] + Q[3 * r + 2] * b.R[6 + cc];
   for (int i = 0; i < 9; ++i) b.R[i] = (float)R[i];
+}
+
+// Eq. (3) for one dynamic body over a time step dt with the step's impulse
+// J (on the body, world frame) and its moment L about the body origin:
+// semi-implicit Euler, then the locked degrees of freedom are zeroed.
+void integrate_dynamic(mpm_rigid_body& b, const mpm_rigid_dynamics& d, const double* gravity,
+                       const double* J, const double* L, double dt) {
+  const double m = d.mass;
+  double v[3], w[3];
+  for (int i = 0; i < 3; ++i) {
+    const double f = d.force[i] + (d.gravity ? m * gravity[i] : 0.0);
+    v[i] = b.v[i] + (dt * f + J[i]) / m;
+  }
+  // world inertia I = R diag(Ib) R^T and the gyroscopic term w x I w
+  double R[9], Iw[9];
+  for (int i = 0; i < 9; ++i) R[i] = b.R[i];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += R[3 * r + k] * (double)d.inertia[k] * R[3 * c + k];
+      Iw[3 * r + c] = acc;
+    }
+  const double w0[3] = {b.omega[0], b.omega[1], b.omega[2]};
+  double Iw0[3];
+  for (int r = 0; r < 3; ++r) Iw0[r] = Iw[3 * r] * w0[0] + Iw[3 * r + 1] * w0[1] + Iw[3 * r + 2] * w0[2];
+  const double gyro[3] = {w0[1] * Iw0[2] - w0[2] * Iw0[1], w0[2] * Iw0[0] - w0[0] * Iw0[2],
+                          w0[0] * Iw0[1] - w0[1] * Iw0[0]};
+  double rhs[3];
+  for (int i = 0; i < 3; ++i) rhs[i] = dt * (d.torque[i] - gyro[i]) + L[i];
+  // dw = Iw^-1 rhs (symmetric positive definite 3x3: by cofactors)
+  const double a = Iw[0], bb = Iw[1], c = Iw[2], e = Iw[4], f = Iw[5], i9 = Iw[8];
+  const double A0 = e * i9 - f * f, A1 = c * f - bb * i9, A2 = bb * f - c * e;
+  const double det = a * A0 + bb * A1 + c * A2;
+  const double inv[9] = {A0, A1, A2, A1, a * i9 - c * c, bb * c - a * f, A2, bb * c - a * f, a * e - bb * bb};
+  for (int r = 0; r < 3; ++r)
+    w[r] = w0[r] + (inv[3 * r] * rhs[0] + inv[3 * r + 1] * rhs[1] + inv[3 * r + 2] * rhs[2]) / det;
+  for (int i = 0; i < 3; ++i) {
+    if (!((d.dof_mask >> i) & 1)) v[i] = 0.0;
+    if (!((d.dof_mask >> (3 + i)) & 1)) w[i] = 0.0;
+    b.v[i] = (float)v[i];
+    b.omega[i] = (float)w[i];
+  }
+  advance_kinematic(b, dt);
 }
 
 mpm_status first_error(mpm_ctx* ctx, uint32_t bits) {
@@ -567,6 +615,27 @@ mpm_status mpm_set_rigid_bodies(mpm_ctx* ctx, int32_t n, const mpm_rigid_body* b
   }
   ctx->bodies.assign(bodies, bodies + n);
   ctx->bodies_dirty = true;
+  ctx->is_dyn.assign(n, 0);
+  ctx->dyn.assign(n, mpm_rigid_dynamics{});
+  ctx->imp_seen_valid = false;
+  return MPM_OK;
+}
+
+mpm_status mpm_set_rigid_dynamics(mpm_ctx* ctx, int32_t index, const mpm_rigid_dynamics* dyn) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (index < 0 || index >= (int32_t)ctx->bodies.size())
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_rigid_dynamics: no such body");
+  if (dyn) {
+    if (!(dyn->mass > 0.f) || !(dyn->inertia[0] > 0.f) || !(dyn->inertia[1] > 0.f) ||
+        !(dyn->inertia[2] > 0.f) || dyn->dof_mask < 0 || dyn->dof_mask > 63)
+      return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_rigid_dynamics: bad mass, inertia or mask");
+    for (int i = 0; i < 3; ++i)
+      if (!std::isfinite(dyn->force[i]) || !std::isfinite(dyn->torque[i]))
+        return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_rigid_dynamics: non-finite load");
+    ctx->dyn[index] = *dyn;
+  }
+  ctx->is_dyn[index] = dyn ? 1 : 0;
+  ctx->imp_seen_valid = false;
   return MPM_OK;
 }
 
@@ -602,6 +671,19 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     for (int i = 0; i < nb; ++i) tmp[i] = to_dev(ctx->bodies[i]);
     if (nb) CU(cudaMemcpyAsync(ctx->bodies_d, tmp, nb * sizeof(DevBody), cudaMemcpyHostToDevice, s));
     ctx->bodies_dirty = false;
+  }
+  bool has_dyn = false;
+  for (int d : ctx->is_dyn) has_dyn = has_dyn || d;
+  if (has_dyn && !ctx->imp_seen_valid) {
+    // the impulse accumulator at the start of the step (the caller's resets
+    // and earlier steps included), so that the step's own impulses are known
+    ctx->imp_seen.assign(6 * kMaxBodies, 0.0);
+    if (nb) {
+      CU(cudaMemcpyAsync(ctx->imp_seen.data(), ctx->impulses, 6 * nb * sizeof(double),
+                         cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+    }
+    ctx->imp_seen_valid = true;
   }
   CU(cudaMemsetAsync(ctx->stats, 0, sizeof(DevStats), s));
   const int n = (int)ctx->n;
@@ -654,14 +736,37 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
   if (!launched) CU(enqueue_step(ctx, from, sort_now, n_substeps, hf, sp, solve_blocks, s));
   if (sort_now) ctx->cur = 1 - from;
   CU(cudaGetLastError());
-  // async splitting: kinematic bodies move with their frozen velocity
+  // async splitting (Eq. (3)-(4)): kinematic bodies move with their frozen
+  // velocity; dynamic ones take the step's accumulated contact impulses
   const double dt = h * n_substeps;
-  bool moved = false;
-  for (auto& b : ctx->bodies)
-    if (b.kinematic) {
-      advance_kinematic(b, dt);
+  bool moved = false, any_dyn = false;
+  for (size_t i = 0; i < ctx->bodies.size(); ++i) {
+    if (ctx->is_dyn[i]) {
+      any_dyn = true;
+    } else if (ctx->bodies[i].kinematic) {
+      advance_kinematic(ctx->bodies[i], dt);
       moved = true;
     }
+  }
+  if (any_dyn) {
+    std::vector<double> now(6 * kMaxBodies, 0.0);
+    CU(cudaMemcpyAsync(now.data(), ctx->impulses, 6 * nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < ctx->bodies.size(); ++i) {
+      if (!ctx->is_dyn[i]) continue;
+      double J[3], L[3];
+      for (int c = 0; c < 3; ++c) {
+        J[c] = now[6 * i + c] - ctx->imp_seen[6 * i + c];
+        L[c] = now[6 * i + 3 + c] - ctx->imp_seen[6 * i + 3 + c];
+      }
+      integrate_dynamic(ctx->bodies[i], ctx->dyn[i], ctx->spec.gravity, J, L, dt);
+    }
+    ctx->imp_seen = now;
+    ctx->imp_seen_valid = true;
+    moved = true;
+  } else {
+    ctx->imp_seen_valid = false;  // the accumulator moves on untracked
+  }
   if (moved) ctx->bodies_dirty = true;
   ctx->step_count += 1;
   if (!stats) return MPM_OK;
@@ -690,7 +795,11 @@ mpm_status mpm_get_rigid_impulses(mpm_ctx* ctx, double* out, int32_t reset) {
   CU(cudaStreamSynchronize(ctx->stream));
   const size_t nb = ctx->bodies.size();
   if (nb) CU(cudaMemcpy(out, ctx->impulses, 6 * nb * sizeof(double), cudaMemcpyDeviceToHost));
-  if (reset) CU(cudaMemset(ctx->impulses, 0, 6 * kMaxBodies * sizeof(double)));
+  if (reset) {
+    CU(cudaMemset(ctx->impulses, 0, 6 * kMaxBodies * sizeof(double)));
+    ctx->imp_seen.assign(6 * kMaxBodies, 0.0);
+    ctx->imp_seen_valid = true;
+  }
   return MPM_OK;
 }
 

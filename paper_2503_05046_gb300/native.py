@@ -45,6 +45,11 @@ class RigidBody(C.Structure):
                 ("mu", C.c_float), ("k", C.c_float), ("d", C.c_float), ("kinematic", C.c_int32)]
 
 
+class RigidDynamics(C.Structure):
+    _fields_ = [("mass", C.c_float), ("inertia", C.c_float * 3), ("force", C.c_float * 3),
+                ("torque", C.c_float * 3), ("dof_mask", C.c_int32), ("gravity", C.c_int32)]
+
+
 class SolverParams(C.Structure):
     _fields_ = [("eps_r", C.c_double), ("eps_a", C.c_double), ("max_iters", C.c_int32),
                 ("eps_s", C.c_float), ("ls_rel_tol", C.c_float), ("ls_max_iters", C.c_int32)]
@@ -81,6 +86,7 @@ SIGNATURES = {
     "mpm_get_particles": [_vp, _vp, _vp, _vp, _vp, C.c_int32],
     "mpm_set_rigid_bodies": [_vp, C.c_int32, C.POINTER(RigidBody)],
     "mpm_get_rigid_bodies": [_vp, C.c_int32, C.POINTER(RigidBody)],
+    "mpm_set_rigid_dynamics": [_vp, C.c_int32, C.POINTER(RigidDynamics)],
     "mpm_step": [_vp, C.c_double, C.c_int32, C.POINTER(SolverParams), C.POINTER(StepStats)],
     "mpm_get_rigid_impulses": [_vp, _dp, C.c_int32],
     "mpm_get_grid": [_vp, C.c_int64, _i64p, _i32p, _fp, _fp, _fp],
@@ -191,6 +197,25 @@ def mpm_set_rigid_bodies(ctx, bodies):
     for i, b in enumerate(bodies):
         arr[i] = b if isinstance(b, RigidBody) else make_body(b)
     _check(ctx, lib.mpm_set_rigid_bodies(ctx, len(bodies), arr))
+
+
+def make_dynamics(dyn):
+    """dict(mass, inertia[3], force[3], torque[3], dof_mask, gravity) -> RigidDynamics."""
+    d = RigidDynamics()
+    d.mass = float(dyn["mass"])
+    for key in ("inertia", "force", "torque"):
+        val = np.asarray(dyn.get(key, [0.0, 0.0, 0.0]), np.float64).reshape(3)
+        arr = getattr(d, key)
+        for i in range(3):
+            arr[i] = float(val[i])
+    d.dof_mask = int(dyn.get("dof_mask", 63))
+    d.gravity = int(dyn.get("gravity", 1))
+    return d
+
+
+def mpm_set_rigid_dynamics(ctx, index, dyn):
+    _check(ctx, lib.mpm_set_rigid_dynamics(ctx, int(index),
+                                           C.byref(make_dynamics(dyn)) if dyn is not None else None))
 
 
 def mpm_get_rigid_bodies(ctx, n):
@@ -377,6 +402,10 @@ class Sim:
     def set_bodies(self, bodies):
         self.n_bodies = len(bodies)
         mpm_set_rigid_bodies(self.ctx, bodies)
+
+    def set_dynamics(self, index, dyn):
+        """Make body `index` dynamic (dict as make_dynamics) or, with None, not."""
+        mpm_set_rigid_dynamics(self.ctx, index, dyn)
 
     def bodies(self):
         return [body_dict(b) for b in mpm_get_rigid_bodies(self.ctx, self.n_bodies)]

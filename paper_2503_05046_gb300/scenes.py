@@ -216,6 +216,37 @@ def batch_scene(index, seed=SEED_BASE + 4, n_min=2000, n_max=64000, dx=5e-3, h=1
             "bodies": bodies, "h": h, "substeps": 10}
 
 
+def panel_squeeze(n_side=12, dx=0.01, E=1.0e5, mu=0.5, force=10.0, panel_mass=0.5,
+                  overlap=1e-4, h=1e-4, substeps=1):
+    """The panel squeeze of Sec. VI-A (Fig. 2): an elastic cube (n_side^3
+    particles at 2 per dx, rho = 1000) between two dynamic box panels that
+    may only translate along x and are pushed towards each other with
+    `force` newtons each, holding the cube against gravity by friction; no
+    ground. At steady state each panel carries the normal force `force` and a
+    vertical friction force of half the cube's weight. Returns the scene and
+    the panels' dynamics (indices 0 and 1)."""
+    rng = np.random.default_rng(SEED_BASE + 41)
+    spacing = dx / 2.0
+    half = n_side * spacing / 2.0  # cube faces at +-half (particle cells)
+    g = cube_group(n_side, spacing, (0.0, 0.0, 0.0), (0, 0, 0), elastic(E, 0.3, 1000.0),
+                   jitter=1e-4 * dx, rng=rng)
+    t = 0.005
+    edge = (n_side - 1) * spacing / 2.0  # outermost particle column
+    bodies = [body(BOX, (t, 0.05, 0.05), p=(-edge - t + overlap, 0, 0), mu=mu),
+              body(BOX, (t, 0.05, 0.05), p=(edge + t - overlap, 0, 0), mu=mu)]
+    inertia = [panel_mass * (0.1 ** 2 + 0.1 ** 2) / 12.0, panel_mass * (0.1 ** 2 + (2 * t) ** 2) / 12.0,
+               panel_mass * (0.1 ** 2 + (2 * t) ** 2) / 12.0]
+    dyn = [dict(mass=panel_mass, inertia=inertia, force=[force, 0.0, 0.0], torque=[0, 0, 0],
+                dof_mask=0b000001, gravity=0),
+           dict(mass=panel_mass, inertia=inertia, force=[-force, 0.0, 0.0], torque=[0, 0, 0],
+                dof_mask=0b000001, gravity=0)]
+    grid = {"dx": dx, "res": (32, 32, 32), "origin": (-0.16, -0.16, -0.16),
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    sc = {"name": "panel_squeeze_%d" % len(g["x"]), "grid": grid, "groups": [g],
+          "bodies": bodies, "h": h, "substeps": substeps}
+    return sc, dyn
+
+
 def n_particles(scene):
     return int(sum(len(g["x"]) for g in scene["groups"]))
 
