@@ -22,9 +22,9 @@
 //   C  contacts: dv_c = J dv.
 //   L  exact line search (Alg. 1): f'(alpha) = B + alpha A + sum_p dl_c . dv_c
 //      is monotone (f convex); each pass evaluates it at 8 points in one
-//      contact sweep: first on a doubling grid to bracket the root, then
-//      around the secant estimate inside the bracket, until
-//      |f'| <= ls_rel_tol |f'(0)|. Up to kLocalLsMax contacts every block
+//      contact sweep: first on a geometric grid (0, 4^-5 .. 4) to bracket the
+//      root, then at the Newton and secant estimates and points that split
+//      the bracket, until |f'| <= ls_rel_tol |f'(0)|. Up to kLocalLsMax contacts every block
 //      runs the whole line search by itself over all contacts (their v_c and
 //      dv_c sit in L2), so its passes need no grid barrier; above that the
 //      contacts are split over the blocks and each pass ends in a grid-wide
@@ -277,10 +277,11 @@ __device__ __forceinline__ void line_load(const float4* cache, int slot, const D
 // Exact line search of Alg. 1 on f'(alpha) = B + alpha A + sum_p dl_c . dv_c,
 // which is continuous and non-decreasing (f convex). Each pass has f' and f''
 // at 8 points; the bracket [lo, hi] keeps f'(lo) < 0 <= f'(hi). The first
-// pass is 0 and a doubling grid (extended by further doublings while f' < 0);
-// later passes evaluate the Newton step from the best point, the secant of
-// the bracket and six evenly spaced points (the bracket shrinks at least
-// sevenfold). Stops when |f'(best)| <= rel_tol |f'(0)|. Thread-0 state.
+// pass is 0 and a geometric grid (ratio 4, extended while f' < 0); later
+// passes evaluate the Newton step from the best point, the secant of the
+// bracket and six points that split it (geometrically while it spans more
+// than a factor 4, else its thirds and points around the Newton step).
+// Stops when |f'(best)| <= rel_tol |f'(0)|. Thread-0 state.
 struct LineSearch {
   enum { kMore = 0, kDone = 1, kFailed = 2 };
   float lo, hi, flo, fhi, best, fbest, f2best, f0;
@@ -314,9 +315,9 @@ struct LineSearch {
     }
     if (!(f0 < 0.f)) { best = 0.f; return kDone; }  // no descent left at working precision
     if (fabsf(fbest) <= rel_tol * fabsf(f0) || last) return kDone;
-    if (hi < 0.f) {  // root beyond the grid: keep doubling
+    if (hi < 0.f) {  // root beyond the grid: keep growing by 4x
       if (lo >= 1024.f) { best = lo; return kFailed; }
-      for (int k = 0; k < kLsPoints; ++k) pts[k] = lo * (float)(2 << k);
+      for (int k = 0; k < kLsPoints; ++k) pts[k] = lo * (float)(4 << (2 * k));
       return kMore;
     }
     if (hi - lo <= 1e-7f * hi) return kDone;
@@ -327,7 +328,26 @@ struct LineSearch {
     if (!(xs > lo && xs < hi)) xs = 0.5f * (lo + hi);
     pts[0] = xn;
     pts[1] = xs;
-    for (int k = 2; k < kLsPoints; ++k) pts[k] = lo + w * (float)(k - 1) / 7.0f;
+    // a bracket spanning more than a factor 4 (or reaching down to 0) is
+    // split geometrically; a narrow one by its thirds (the bracket shrinks at
+    // least threefold) and points 1% and 10% of its width either side of
+    // the Newton point (where the root lies once Newton converges)
+    const float lo_g = lo > 0.f ? lo : hi * (1.0f / 4096.0f);
+    if (hi > 4.f * lo_g) {
+      const float r = exp2f(__log2f(hi / lo_g) / 7.0f);
+      float x = lo_g;
+      for (int k = 2; k < kLsPoints; ++k) {
+        x *= r;
+        pts[k] = x;
+      }
+    } else {
+      const float c[6] = {1.f / 3.f, 2.f / 3.f, -0.1f, 0.1f, -0.01f, 0.01f};
+      for (int k = 2; k < kLsPoints; ++k) {
+        float x = k < 4 ? lo + c[k - 2] * w : xn + c[k - 2] * w;
+        if (!(x > lo && x < hi)) x = lo + (float)(k - 1) / 7.0f * w;
+        pts[k] = x;
+      }
+    }
     return kMore;
   }
 };
@@ -573,12 +593,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
       s_dec = dec;
       s_A = A;
       s_B = Bs;
-      // line-search state, first pass: 0 and a doubling grid 1/8 .. 8
+      // line-search state, first pass: 0 and a geometric grid 4^-5 .. 4
+      // (quasi-Newton steps on stiff contacts are often much shorter than 1)
       ls.reset();
       ls.pts[0] = 0.f;
       s_pts[0] = 0.f;
       for (int k = 1; k < kLsPoints; ++k) {
-        ls.pts[k] = (float)(1 << (k - 1)) * 0.125f;
+        ls.pts[k] = exp2f(2.0f * (float)(k - 6));
         s_pts[k] = ls.pts[k];
       }
     }
