@@ -293,13 +293,19 @@ mpm_status mpm_synchronize(mpm_ctx* ctx);
    re-records; profiling launches directly); zero always launches directly.
    MPM_OPT_SOLVE_BLOCKS: at most this many thread blocks (one per SM) work on
    the contact solve (0, the default: as many as the device holds); a small
-   cap lets contexts on other streams run beside a small scene's solve. */
+   cap lets contexts on other streams run beside a small scene's solve.
+   MPM_OPT_TEST_BARRIER_TIMEOUT: for testing failure detection only; nonzero
+   makes each device-wide barrier of the contact solve wait for one arrival
+   more than there are blocks, so that (with two or more participating
+   blocks) it gives up after its 1 s limit, the solve returns and the step
+   reports MPM_ERR_TIMEOUT; the context stays usable. */
 enum {
   MPM_OPT_PROFILE = 1,
   MPM_OPT_SORT_EVERY = 2,
   MPM_OPT_P2G_CHUNK = 3,
   MPM_OPT_GRAPHS = 4,
-  MPM_OPT_SOLVE_BLOCKS = 5
+  MPM_OPT_SOLVE_BLOCKS = 5,
+  MPM_OPT_TEST_BARRIER_TIMEOUT = 6
 };
 mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value);
 

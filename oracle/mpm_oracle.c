@@ -234,10 +234,24 @@ void orc_hencky_P(const double F[9], double mu, double lam, double P[9]) {
   mat_mul_bt(T, V, P);
 }
 
+/* Kirchhoff stress of the Hencky model in principal form,
+   tau = U diag(2 mu e + lam tr e) U^T with e = ln max(sigma, sigma_min): equal
+   to P F^T while no singular value is clamped, and the stress of the clamped
+   strain otherwise (also for an inverted F, whose negative singular value is
+   clamped). */
 void orc_hencky_tau(const double F[9], double mu, double lam, double tau[9]) {
-  double P[9];
-  orc_hencky_P(F, mu, lam, P);
-  mat_mul_bt(P, F, tau);
+  double U[9], S[3], V[9];
+  orc_svd3(F, U, S, V);
+  double e[3], tr = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    e[a] = log(fmax(S[a], ORC_HENCKY_SIGMA_MIN));
+    tr += e[a];
+  }
+  double D[9] = {0};
+  for (int a = 0; a < 3; ++a) D[4 * a] = 2.0 * mu * e[a] + lam * tr;
+  double T[9];
+  mat_mul(U, D, T);
+  mat_mul_bt(T, U, tau);
 }
 
 /* Drucker-Prager plasticity in Hencky strain space (the granular model the

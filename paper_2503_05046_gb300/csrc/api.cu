@@ -42,6 +42,7 @@ struct mpm_ctx {
   Contacts C{};
   double* red = nullptr;
   unsigned* bar = nullptr;
+  int* poison = nullptr;
   uint32_t* status = nullptr;
   DevStats* stats = nullptr;
   double* impulses = nullptr;
@@ -60,6 +61,7 @@ struct mpm_ctx {
   } gkey[2];
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   int solve_blocks_cap = 0;  // 0: as many as the device holds
+  bool wait_test = false;    // MPM_OPT_TEST_BARRIER_TIMEOUT
   int sort_every = 1;
   int p2g_chunk = 256;
   int64_t step_count = 0;
@@ -287,7 +289,7 @@ void release(mpm_ctx* c) {
   void* ptrs[] = {c->pbuf[0], c->pbuf[1], c->pidbuf[0], c->pidbuf[1], c->grpbuf[0], c->grpbuf[1],
                   c->groups_d, c->bodies_d, c->G.mp, c->G.vs, c->G.v, c->G.v2, c->G.vlo, c->G.vlo2, c->G.acc0, c->G.acc1,
                   c->G.acc2, c->G.dv, c->G.mark, c->G.cflag, c->G.cnodes, c->G.n_cnodes, c->G.pstar2, c->G.act, c->G.n_act, c->C.xp, c->C.nrm,
-                  c->C.bias, c->C.id, c->C.vc, c->C.dvc, c->C.gamma, c->C.count, c->red, c->bar,
+                  c->C.bias, c->C.id, c->C.vc, c->C.dvc, c->C.gamma, c->C.count, c->red, c->bar, c->poison,
                   c->status, c->stats, c->impulses, c->sb.keys[0], c->sb.keys[1], c->sb.vals[0],
                   c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage};
   for (void* p : ptrs)
@@ -325,6 +327,8 @@ cudaError_t enqueue_step(mpm_ctx* ctx, int from, bool sort_now, int n_substeps, 
     sa.h = hf; sa.eps_s = sp.eps_s; sa.ls_rel_tol = sp.ls_rel_tol; sa.ls_max_iters = sp.ls_max_iters;
     sa.eps_r = sp.eps_r; sa.eps_a = sp.eps_a; sa.max_iters = sp.max_iters; sa.red = ctx->red;
     sa.bar = ctx->bar; sa.status = ctx->status; sa.stats = ctx->stats; sa.impulses = ctx->impulses;
+    sa.wait_extra = ctx->wait_test ? 1 : 0;
+    sa.poison = ctx->poison;
     mark_phase(ctx, MPM_PHASE_SOLVE);
     const cudaError_t e = launch_solve(sa, solve_blocks, s);
     if (e != cudaSuccess) return e;
@@ -427,6 +431,7 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
     ok = ok && dalloc(&ctx->G.cnodes, cn) == cudaSuccess;
   }
   ok = ok && dalloc(&ctx->red, kRedDoubles) == cudaSuccess && dalloc(&ctx->bar, 2) == cudaSuccess &&
+       dalloc(&ctx->poison, 1) == cudaSuccess &&
        dalloc(&ctx->status, 1) == cudaSuccess && dalloc(&ctx->stats, 1) == cudaSuccess &&
        dalloc(&ctx->impulses, 6 * kMaxBodies) == cudaSuccess &&
        dalloc(&ctx->bodies_d, kMaxBodies) == cudaSuccess;
@@ -453,6 +458,7 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
        cudaMemset(ctx->G.n_cnodes, 0, sizeof(int)) == cudaSuccess &&
        cudaMemset(ctx->G.pstar2, 0, sizeof(double)) == cudaSuccess &&
        cudaMemset(ctx->bar, 0, 2 * sizeof(unsigned)) == cudaSuccess &&
+       cudaMemset(ctx->poison, 0, sizeof(int)) == cudaSuccess &&
        cudaMemset(ctx->status, 0, sizeof(uint32_t)) == cudaSuccess &&
        cudaMemset(ctx->stats, 0, sizeof(DevStats)) == cudaSuccess &&
        cudaMemset(ctx->impulses, 0, 6 * kMaxBodies * sizeof(double)) == cudaSuccess &&
@@ -694,7 +700,7 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
                                : ctx->solve_blocks;
   const int from = ctx->cur;
   bool launched = false;
-  if (ctx->use_graphs && !ctx->profile && n_substeps > 0) {
+  if (ctx->use_graphs && !ctx->profile && !ctx->wait_test && n_substeps > 0) {
     mpm_ctx::GraphKey k;
     k.n = n; k.n_substeps = n_substeps; k.nb = nb; k.chunk = ctx->p2g_chunk;
     k.sort_now = sort_now ? 1 : 0; k.solve_blocks = solve_blocks; k.h = hf; k.sp = sp;
@@ -902,6 +908,9 @@ mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value) {
       return MPM_OK;
     case MPM_OPT_GRAPHS:
       ctx->use_graphs = value != 0;
+      return MPM_OK;
+    case MPM_OPT_TEST_BARRIER_TIMEOUT:
+      ctx->wait_test = value != 0;
       return MPM_OK;
     case MPM_OPT_SOLVE_BLOCKS:
       if (value < 0) return fail(ctx, MPM_ERR_INVALID_ARG, "solve block cap must be >= 0");

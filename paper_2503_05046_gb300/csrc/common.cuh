@@ -354,6 +354,16 @@ __device__ __forceinline__ void polar_svd(const float (&F)[9], Polar& P, const f
 #pragma unroll
     for (int r = 0; r < 3; ++r)
       b[c][r] = F[3 * r] * V[c] + F[3 * r + 1] * V[3 + c] + F[3 * r + 2] * V[6 + c];
+  // a singular value far below 1 is taken as |F v| (relative accuracy
+  // ~eps / s) instead of sqrt(1 + lambda), where 1 + lambda cancels
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (l[a] < -0.5f) {
+      const float sa = sqrtf(b[a][0] * b[a][0] + b[a][1] * b[a][1] + b[a][2] * b[a][2]);
+      P.s[a] = sa;
+      P.sm1[a] = sa - 1.0f;
+    }
+  }
   float u0[3], u1[3];
   float n0 = b[0][0] * b[0][0] + b[0][1] * b[0][1] + b[0][2] * b[0][2];
   if (n0 > 1e-30f) {

@@ -90,6 +90,8 @@ struct SolveArgs {
   uint32_t* status;
   DevStats* stats;
   double* impulses;   // [6 nb]
+  int wait_extra;     // 0; 1 makes every grid barrier wait for one block too many (test)
+  int* poison;        // nonzero after a barrier gave up (set and cleared by the solve)
 };
 cudaError_t launch_solve(const SolveArgs& a, int grid_blocks, cudaStream_t s);
 int solve_block_size();

@@ -49,7 +49,8 @@ constexpr int kLocalLsMax = 4096;      // up to this many contacts each block li
 constexpr int kLsPoints = 8;
 constexpr int kRedWidth = 16;              // (hi, lo) pairs per block and reduction
 constexpr int kMaxSolveBlocks = 256;
-constexpr unsigned kSpinLimit = 1u << 24;  // ~1 s of polling with the back-off below
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a barrier gives up after 1 s
+constexpr unsigned kSpinCap = 1u << 28;  // backstop on the number of polls
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -65,17 +66,19 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 
 struct Barrier {
   unsigned* bar;  // [0] arrival counter (zeroed between launches)
-  unsigned n;     // participating blocks
+  unsigned n;     // arrivals that complete a barrier: the participating blocks
   uint32_t* status;
+  int* poison;    // set on expiry: the next solve first clears the node scratch
 };
 
 // Device-wide barrier of the participating blocks. The arrival counter only
 // grows: the k-th barrier is complete when it reaches (k + 1) n, which each
 // block reads off its own arrival ticket, so the last arriver has nothing to
 // reset or publish. Thread 0 publishes its block's writes (fence), arrives,
-// and the others spin with an iteration limit and return false on expiry
-// (the caller then returns; the other blocks expire at their next barrier).
-// A single participating block needs only __syncthreads.
+// and the others poll with a time limit (1 s of the global timer) and return
+// false on expiry (the caller then returns; the other blocks expire at the
+// same or their next barrier). A single participating block needs only
+// __syncthreads.
 __device__ bool grid_sync(Barrier& B) {
   __syncthreads();
   if (B.n == 1) return true;
@@ -86,10 +89,13 @@ __device__ bool grid_sync(Barrier& B) {
     const unsigned ticket = atomicAdd(&B.bar[0], 1u);
     const unsigned target = (ticket / B.n + 1u) * B.n;
     if (ticket + 1u != target) {
+      const unsigned long long t0 = global_ns();
       unsigned spins = 0;
       while (ld_acquire(&B.bar[0]) < target) {
-        if (++spins > kSpinLimit) {
+        ++spins;
+        if (((spins & 63u) == 0u && global_ns() - t0 > kWaitLimitNs) || spins > kSpinCap) {
           atomicOr(B.status, kStTimeout);
+          if (B.poison) atomicExch(B.poison, 1);
           ok = 0;
           break;
         }
@@ -387,7 +393,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
       tmark = now;
     }
   };
-  Barrier B{a.bar, (unsigned)nblk, a.status};
+  // (wait_extra > 0 only in the test of the barrier's time limit: the
+  // barrier then waits for arrivals that never come)
+  Barrier B{a.bar, (unsigned)(nblk + a.wait_extra), a.status, a.poison};
   const int gtid = blockIdx.x * kThreads + tid;
   const int gstride = nblk * kThreads;
   const int lane = tid & 31;
@@ -402,6 +410,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     ++rslot;
     return s;
   };
+
+  // a solve that gave up at a barrier left node flags and gradient
+  // accumulators behind: clear them over the whole grid first
+  if (__ldcg(a.poison)) {
+    const size_t n_nodes = (size_t)g.nbx * g.nby * g.nbz * kBlockNodes;
+    for (size_t t = gtid; t < n_nodes; t += gstride) {
+      a.G.cflag[t] = 0;
+      a.G.acc0[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a.G.acc1[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a.G.acc2[t] = 0.f;
+    }
+    if (!grid_sync(B)) return;
+    if (gtid == 0) *a.poison = 0;
+  }
 
   // ---- contact-node list: the union of the contacts' stencils
   for (int p = gtid; p < nc; p += gstride) {
@@ -446,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   // line search alone in each block (no grid barrier) or split over blocks
   const bool local_ls = nc <= kLocalLsMax;
   const int ls_first = local_ls ? tid : gtid, ls_stride = local_ls ? kThreads : gstride;
-  Barrier Bl{nullptr, 1u, a.status};
+  Barrier Bl{nullptr, 1u, a.status, nullptr};
   const float eps2 = a.eps_s * a.eps_s;
   float alpha = 0.f;
   int it = 0, ls_passes = 0;

@@ -128,6 +128,25 @@ def test_hencky_P_is_energy_gradient(trial):
     assert np.allclose(P, G, rtol=1e-6, atol=1e-3)
     tau = O.hencky_tau(F, mu, lam)
     assert np.allclose(tau, tau.T, atol=1e-8)
+    # principal form agrees with P F^T while nothing is clamped
+    assert np.allclose(tau, P @ F.T, rtol=1e-9, atol=1e-6)
+
+
+def test_hencky_tau_clamps_the_strain():
+    """Singular values below 1e-4, and the negative one of an inverted F, are
+    clamped before the logarithm: the stress is that of the clamped F with
+    the same rotations."""
+    mu, lam = O.lame(3.5e5, 0.3)
+    rng = np.random.default_rng(11)
+    U, V = _rotation(rng), _rotation(rng)
+    for s3 in (-0.8, 1e-6, 0.0):
+        F = U @ np.diag([1.2, 0.9, s3]) @ V.T
+        Fc = U @ np.diag([1.2, 0.9, 1e-4]) @ V.T
+        assert np.allclose(O.hencky_tau(F, mu, lam), O.hencky_tau(Fc, mu, lam), rtol=1e-9, atol=1e-3)
+    e = np.log([1.2, 0.9, 1e-4])
+    expected = U @ np.diag(2 * mu * e + lam * e.sum()) @ U.T
+    assert np.allclose(O.hencky_tau(U @ np.diag([1.2, 0.9, -0.5]) @ V.T, mu, lam), expected,
+                       rtol=1e-9, atol=1e-3)
 
 
 def _rotation(rng):
