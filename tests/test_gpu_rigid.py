@@ -2,6 +2,8 @@
 of each time step (Eq. (3)): one step against the oracle (its substeps with
 the body frozen, then its rigid step), and the panel squeeze of Sec. VI-A
 (Fig. 2) reaching the analytic steady state."""
+import os
+
 import numpy as np
 import pytest
 
@@ -64,12 +66,25 @@ def test_dynamic_body_step_matches_oracle(native):
     sim.close()
 
 
+def _golden(name):
+    vals = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            key, val = line.split()
+            vals[key] = float(val)
+    return vals
+
+
 def test_panel_squeeze_reaches_the_analytic_steady_state(native):
     """Two panels pushed together with 10 N each hold an elastic cube against
     gravity by friction (Sec. VI-A, Fig. 2): after the transient each panel
     feels the normal force 10 N and a vertical friction force of half the
     cube's weight (dt = 0.1 ms, one substep per step, eps_r = 5e-2)."""
-    sc, dyn = scenes.panel_squeeze()
+    gold = _golden("panel_squeeze_steady_state.txt")
+    f_e = gold["applied_normal_force_N"]
+    sc, dyn = scenes.panel_squeeze(force=f_e)
     sim = native.Sim(sc)
     for i, d in enumerate(dyn):
         sim.set_dynamics(i, d)
@@ -85,10 +100,10 @@ def test_panel_squeeze_reaches_the_analytic_steady_state(native):
         if k >= n_steps - window:
             hist[k - (n_steps - window)] = imp[:, :3] / sc["h"]
     m_box = scenes.n_particles(sc) * float(np.float32(sc["groups"][0]["vol"])) * 1000.0
-    half_weight = 0.5 * m_box * 9.81
+    half_weight = gold["friction_fraction_of_weight_per_panel"] * m_box * 9.81
     f_left, f_right = hist[:, 0].mean(0), hist[:, 1].mean(0)
     # the cube pushes each panel outwards with the applied 10 N
-    assert abs(f_left[0] + 10.0) < 0.2 and abs(f_right[0] - 10.0) < 0.2
+    assert abs(f_left[0] + f_e) < 0.02 * f_e and abs(f_right[0] - f_e) < 0.02 * f_e
     # and drags each down with half its weight; no sideways force
     assert abs(f_left[2] + half_weight) < 0.05 * half_weight
     assert abs(f_right[2] + half_weight) < 0.05 * half_weight
