@@ -273,7 +273,12 @@ __device__ __forceinline__ float det3(const float (&A)[9]) {
 }
 
 constexpr int kSvdSweeps = 5;      // most cyclic Jacobi sweeps from the identity
-constexpr int kSvdWarmSweeps = 2;  // most sweeps from a nearly diagonalising V0
+// From the V of the SVD that the stored (rounded) F was rebuilt from,
+// V^T (F^T F - I) V is diagonal up to that rounding: its diagonal gives the
+// eigenvalues to second order, and keeping V misplaces the singular vectors
+// only within nearly equal singular values, where the stress does not depend
+// on them to first order. No sweep is needed.
+constexpr int kSvdWarmSweeps = 0;
 
 // V0 (optional): a rotation that nearly diagonalises F^T F (the V of a nearby
 // F), from which `sweeps` Jacobi sweeps suffice.
@@ -466,9 +471,9 @@ __device__ __forceinline__ void kirchhoff(const DevGroup& gr, const float (&F)[9
 // Hencky strain space for sand (F projected in place), then the Kirchhoff
 // stress of the final F for the next P2G. For an unprojected F one SVD serves
 // both; a projected F = U diag(exp e') V^T is rounded to FP32 when stored, so
-// its stress is taken from the stored value (a second SVD, started from the
-// first one's V, which nearly diagonalises it) to keep tau equal to the
-// stress of the state F exactly.
+// its stress is taken from the stored value (a second decomposition, in the
+// first one's V, which diagonalises it up to the rounding) to keep tau equal
+// to the stress of the state F.
 __device__ __forceinline__ void constitutive_update(const DevGroup& gr, float (&F)[9],
                                                     float (&t)[6]) {
   Polar P;

@@ -147,7 +147,7 @@ def test_device_tensor_io_matches_host_io(native):
     """Particles added, set and read through CUDA tensors (device pointers,
     MPM_MEM_DEVICE) give the results of the host-array path."""
     import torch
-    sc = scenes.sand_column(n_side=8)
+    sc = scenes.cube_contact(n_side=8, v0=(0.0, 0.0, -0.05))
     g = sc["groups"][0]
     n = len(g["x"])
     sim_h = native.Sim(sc)
