@@ -36,7 +36,7 @@ METRIC = "particle-substeps/sec incl. contact solve"
 UNIT = "particle-substeps/s"
 WORKLOAD = "granular_scoop_1M"
 N_PARTICLES = 1_000_000
-# algorithmic bytes per particle per launch (FP32 SoA planes)
+# algorithmic bytes per particle per launch (FP32 structure-of-arrays planes)
 P2G_BYTES_PER_PARTICLE = 12 + 12 + 36 + 24 + 2      # read x, v, C, tau, group
 G2P_BYTES_PER_PARTICLE = 12 + 36 + 2 + 12 + 12 + 36 + 36 + 24  # read x, F, group; write x, v, C, F, tau
 GRID_NODE_BYTES_P2G = 16                              # one (m, p) write per active node
