@@ -465,6 +465,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   float4* vnxt = a.G.v2;
   float4* lcur = a.G.vlo;
   float4* lnxt = a.G.vlo2;
+  // this warp's first contact, kept in registers across the iterations (with
+  // one contact per warp, whenever nc <= 16 x the blocks, nothing else is
+  // loaded per iteration but the iterate)
+  const bool own = gwarp < nc;
+  float4 own_xp = make_float4(0.f, 0.f, 0.f, 0.f), own_nrm = own_xp, own_bias = own_xp;
+  int own_body = 0;
+  LaneNode own_ln{0, 0.f};
+  if (own) {
+    own_xp = a.C.xp[gwarp];
+    own_nrm = a.C.nrm[gwarp];
+    own_bias = a.C.bias[gwarp];
+    own_body = a.C.id[gwarp].y;
+    own_ln = lane_node(g, own_xp, lane);
+  }
   // line search alone in each block (no grid barrier) or split over blocks
   const bool local_ls = nc <= kLocalLsMax;
   const int ls_first = local_ls ? tid : gtid, ls_stride = local_ls ? kThreads : gstride;
@@ -476,14 +490,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   for (;;) {
     // ---- G: step by alpha, contact gradient / Hessian blocks (warp per contact)
     const float al = alpha;
-    for (int p = gwarp; p < nc; p += nwarps) {
-      float4 xp; float n[3]; float n0;
-      load_contact(a.C, p, xp, n, n0);
-      // issued early: these loads do not depend on the gather
-      const float4 bb = a.C.bias[p];
+    auto phase_g = [&](int p, const float4& xp, const float (&n)[3], float n0, const float4& bb,
+                       int body, const LaneNode& ln) {
       const float4 dvc = it > 0 ? __ldcg(a.C.dvc + p) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const int body = a.C.id[p].y;
-      const LaneNode ln = lane_node(g, xp, lane);
       float u[3];
       {
         const float4 h = __ldcg(vcur + ln.node);
@@ -524,6 +533,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
         red_add_v4(a.G.acc1 + ln.node, w2 * H[1], w2 * H[2], w2 * H[3], w2 * H[4]);
         red_add_f32(a.G.acc2 + ln.node, w2 * H[5]);
       }
+    };
+    if (own) {
+      const float n3[3] = {own_nrm.x, own_nrm.y, own_nrm.z};
+      phase_g(gwarp, own_xp, n3, own_nrm.w, own_bias, own_body, own_ln);
+    }
+    for (int p = gwarp + nwarps; p < nc; p += nwarps) {
+      float4 xp; float n[3]; float n0;
+      load_contact(a.C, p, xp, n, n0);
+      phase_g(p, xp, n, n0, a.C.bias[p], a.C.id[p].y, lane_node(g, xp, lane));
     }
     if (!grid_sync(B)) return;
     lap(1);
@@ -630,8 +648,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
 
     // ---- C: dv_c = J dv (warp per contact)
     for (int p = gwarp; p < nc; p += nwarps) {
-      const float4 xp = a.C.xp[p];
-      const LaneNode ln = lane_node(g, xp, lane);
+      const LaneNode ln = p == gwarp ? own_ln : lane_node(g, a.C.xp[p], lane);
       const float4 d = __ldcg(a.G.dv + ln.node);
       const float e0 = warp_sum(ln.w * d.x), e1 = warp_sum(ln.w * d.y), e2 = warp_sum(ln.w * d.z);
       if (lane == 0) a.C.dvc[p] = make_float4(e0, e1, e2, 0.f);
