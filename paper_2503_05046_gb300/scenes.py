@@ -247,6 +247,82 @@ def panel_squeeze(n_side=12, dx=0.01, E=1.0e5, mu=0.5, force=10.0, panel_mass=0.
     return sc, dyn
 
 
+def ball_group(n_target, spacing, center, material, jitter, rng):
+    """About n_target lattice points (x fastest) inside a sphere, with jitter."""
+    r = (3.0 * n_target / (4.0 * np.pi)) ** (1.0 / 3.0) * spacing
+    k = int(np.ceil(r / spacing)) + 1
+    idx = np.arange(-k, k + 1, dtype=np.float64) * spacing
+    gx, gy, gz = np.meshgrid(idx, idx, idx, indexing="ij")
+    pts = np.stack([gx.transpose(2, 1, 0).ravel(), gy.transpose(2, 1, 0).ravel(),
+                    gz.transpose(2, 1, 0).ravel()], 1)
+    pts = pts[np.sum(pts * pts, 1) <= r * r] + np.asarray(center, np.float64)
+    if jitter > 0:
+        pts = pts + rng.uniform(-jitter, jitter, pts.shape)
+    x = pts.astype(np.float32)
+    return {"x": x, "v": np.zeros_like(x), "vol": float(spacing ** 3), "material": material}, r
+
+
+def mixed_manipulation(n_objects=32, n_per_object=125_000, seed=SEED_BASE + 2, dx=2e-3,
+                       h=2.5e-5, substeps=10):
+    """Mixed-material manipulation: n_objects objects of about n_per_object
+    particles each at 2 per dx per axis, half elastic (E log-uniform in
+    [1e4, 1e6], rho = 1000) and half Drucker-Prager sand, alternately cubes and
+    balls, on a floor in rows of 8 with 7 cm pitch; 12 rigid bodies: the floor,
+    two box jaws of a parallel gripper closing on object 0 at 0.05 m/s (faces
+    0.01 dx inside it), and nine static obstacles (boxes, capsules, spheres)
+    between the objects; mu ~ U[0.2, 0.8] per body. h = 2.5e-5 s keeps the
+    stiffest elastic objects inside the explicit substep's CFL limit."""
+    rng = np.random.default_rng(seed)
+    spacing = dx / 2.0
+    pitch = 0.07
+    cols = min(n_objects, 8)
+    rows = (n_objects + cols - 1) // cols
+    groups, extents = [], []
+    jit = 1e-4 * dx
+    for i in range(n_objects):
+        r_i, c_i = divmod(i, cols)
+        cx = (c_i - (cols - 1) / 2.0) * pitch
+        cy = (r_i - (rows - 1) / 2.0) * pitch
+        if i % 2 == 0:
+            mat = elastic(E=float(10 ** rng.uniform(4.0, 6.0)), nu=0.3, rho=1000.0)
+        else:
+            mat = dict(SAND)
+        if (i // 2) % 2 == 0:
+            n_side = max(int(round(n_per_object ** (1.0 / 3.0))), 2)
+            half = (n_side - 1) * spacing / 2.0
+            g = cube_group(n_side, spacing, (cx, cy, half + jit), (0, 0, 0), mat, jitter=jit, rng=rng)
+            extents.append((cx, cy, half))
+        else:
+            g0, r = ball_group(n_per_object, spacing, (cx, cy, 0.0), mat, jit, rng)
+            g0["x"][:, 2] += np.float32(-g0["x"][:, 2].min() + jit)
+            g = g0
+            extents.append((cx, cy, r))
+        groups.append(g)
+    mus = rng.uniform(0.2, 0.8, 12)
+    bodies = [body(HALFSPACE, mu=float(mus[0]))]
+    cx0, cy0, e0 = extents[0]
+    jaw = (0.01, e0 + dx, e0 + dx)
+    bodies.append(body(BOX, jaw, p=(cx0 - e0 - 0.01 + 0.01 * dx, cy0, e0), v=(0.05, 0, 0),
+                       mu=float(mus[1]), kinematic=1))
+    bodies.append(body(BOX, jaw, p=(cx0 + e0 + 0.01 - 0.01 * dx, cy0, e0), v=(-0.05, 0, 0),
+                       mu=float(mus[2]), kinematic=1))
+    # static obstacles in the gaps between object rows
+    for k in range(9):
+        gx = ((k % cols) - (cols - 1) / 2.0 + 0.5) * pitch
+        gy = ((rows - 1) / 2.0 - 0.5) * pitch if rows > 1 else pitch / 2.0
+        shape = (BOX, CAPSULE, SPHERE)[k % 3]
+        params = {BOX: (0.005, 0.005, 0.01), CAPSULE: (0.008, 0.004), SPHERE: (0.006,)}[shape]
+        bodies.append(body(shape, params, p=(gx, gy, 0.012), mu=float(mus[3 + k])))
+    span_x = cols * pitch + 0.08
+    span_y = rows * pitch + 0.08
+    res = (4 * int(np.ceil(span_x / dx / 4)), 4 * int(np.ceil(span_y / dx / 4)),
+           4 * int(np.ceil((0.1 + 12 * dx) / dx / 4)))
+    origin = (-res[0] * dx / 2.0, -res[1] * dx / 2.0, -6 * dx)
+    grid = {"dx": dx, "res": res, "origin": origin, "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    return {"name": "mixed_manipulation_%d" % sum(len(g["x"]) for g in groups), "grid": grid,
+            "groups": groups, "bodies": bodies, "h": h, "substeps": substeps}
+
+
 def n_particles(scene):
     return int(sum(len(g["x"]) for g in scene["groups"]))
 

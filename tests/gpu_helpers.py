@@ -36,3 +36,29 @@ def oracle_substep(sc, gpu_state, gpu_bodies, solver, h=None):
 def rel_linf(a, b):
     scale = np.max(np.abs(b))
     return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / (scale if scale > 0 else 1.0))
+
+
+def align_grids(gpu, orc, mass_slack):
+    """Grid readbacks (ids, m, v*, v) of the CUDA path and the oracle on the
+    union of their node ids. A particle within rounding of a cell boundary has
+    two valid stencils that differ in a node of weight ~0, so a node may be
+    present on one side only; such nodes must hold at most `mass_slack`.
+    Returns both sides' (m, v*, v) on the union (zeros where absent)."""
+    ids, m, vs, v = gpu
+    oids, om, ovs, ov = orc
+    union = np.union1d(ids, oids)
+    out = []
+    for i_, m_, vs_, v_ in ((ids, m, vs, v), (oids, om, ovs, ov)):
+        k = np.searchsorted(union, i_)
+        M = np.zeros(len(union))
+        VS = np.zeros((len(union), 3))
+        V = np.zeros((len(union), 3))
+        M[k], VS[k], V[k] = m_, vs_, v_
+        out.append((M, VS, V))
+    only = np.setxor1d(ids, oids)
+    if len(only):
+        k = np.searchsorted(union, only)
+        assert np.all(out[0][0][k] <= mass_slack) and np.all(out[1][0][k] <= mass_slack), \
+            "a node present on one side only holds mass"
+    return out[0], out[1]
+

@@ -17,7 +17,7 @@ import pytest
 
 import oracle as O
 from paper_2503_05046_gb300 import scenes
-from gpu_helpers import oracle_substep, rel_linf
+from gpu_helpers import align_grids, oracle_substep, rel_linf
 
 pytestmark = pytest.mark.gpu
 
@@ -81,9 +81,7 @@ def run_parity(native, sc, n_sub=2, warm_steps=0, warm_solver=None, tol_v=TOL_V,
             assert np.max(np.abs(imp[:, :3] - oimp[:, :3])) < 1e-4 * iscale
         # grid
         if check_grid:
-            ids, m, vs, v = sim.grid()
-            oids, om, ovs, ov = osim.last_grid()
-            assert np.array_equal(ids, oids)
+            (m, vs, v), (om, ovs, ov) = align_grids(sim.grid(), osim.last_grid(), 1e-6 * mass_p)
             # FP32 sums of B-spline-weighted masses: 1e-5 relative, plus the
             # absolute FP32 error of small weights (about 1e-7 of a particle mass)
             assert np.all(np.abs(m - om) <= 1e-5 * om + 1e-6 * mass_p)
@@ -104,7 +102,7 @@ def run_parity(native, sc, n_sub=2, warm_steps=0, warm_solver=None, tol_v=TOL_V,
             scale = np.linalg.norm(sm * ov)
             assert np.linalg.norm(dm) <= 1e-5 * scale
             vmax_g = np.max(np.abs(ov))
-            bound = 1e-5 * vmax_g + 2.0 * 1e-6 * scale / np.sqrt(om)
+            bound = 1e-5 * vmax_g + 2.0 * 1e-6 * scale / np.sqrt(np.maximum(om, 1e-300))
             assert np.all(np.abs(v - ov).max(1) <= bound)
         report.append((k, info.n_contacts, info.iters, stats.iters_total, ev))
     sim.close()
