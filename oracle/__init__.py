@@ -106,6 +106,7 @@ def lib():
         L.orc_last_grid.argtypes = [C.c_void_p, C.c_int, _ip, _dp, _dp, _dp]
         L.orc_last_contacts.argtypes = [C.c_void_p, C.c_int, _ip, _ip, _dp, _dp, _dp]
         L.orc_advance_kinematic.argtypes = [C.c_int, C.POINTER(Body), C.c_double]
+        L.orc_contact_adjoint.argtypes = [C.POINTER(Problem), _dp, _dp, _dp, _dp, _dp]
         L.orc_rigid_dynamics_step.argtypes = [C.POINTER(Body), C.POINTER(Dynamics), _dp, _dp,
                                               C.c_double]
         _lib = L
@@ -294,6 +295,16 @@ class ContactProblem:
         if history:
             out = out + (hist[:info.iters + 1],)
         return out
+
+    def adjoint(self, v, vbar):
+        """Adjoint of the solve at the minimiser v for dL/dv = vbar:
+        (dL/dv*[n,3], dL/db[nc,3] contact frame, dL/dmu[nc], status)."""
+        vsb = np.zeros(self.n * 3)
+        bb = np.zeros(max(self.nc, 1) * 3)
+        mb = np.zeros(max(self.nc, 1))
+        st = lib().orc_contact_adjoint(C.byref(self.s), _d(_f64(v, (self.n * 3,))),
+                                       _d(_f64(vbar, (self.n * 3,))), _d(vsb), _d(bb), _d(mb))
+        return vsb.reshape(self.n, 3), bb[:3 * self.nc].reshape(self.nc, 3), mb[:self.nc], st
 
     def solve_dense_newton(self, S, v0=None):
         v = (self.vstar.copy() if v0 is None else _f64(v0, (self.n * 3,)).copy())

@@ -1227,3 +1227,77 @@ void orc_rigid_dynamics_step(orc_body* b, const orc_dynamics* d, const double gr
   rotation_from_vector(wdt, Q);
   mat_mul(Q, b->R, b->R);
 }
+
+int orc_contact_adjoint(const orc_problem* P, const double* v, const double* vbar,
+                        double* vstar_bar, double* b_bar, double* mu_bar) {
+  const int n = P->n_nodes, nc = P->n_contacts, N3 = 3 * n;
+  double* vc = (double*)malloc(sizeof(double) * 3 * (nc + 1));
+  double* G = (double*)malloc(sizeof(double) * 9 * (nc + 1));    /* contact-frame Hessians */
+  double* dg = (double*)malloc(sizeof(double) * 3 * (nc + 1));   /* d(grad l_c)/d mu */
+  double* Hd = (double*)malloc(sizeof(double) * (size_t)N3 * N3 + 8);
+  double* lam = (double*)malloc(sizeof(double) * (N3 + 1));
+  double* jl = (double*)malloc(sizeof(double) * 3 * (nc + 1));
+  contact_velocities(P, v, 1, vc);
+  for (int p = 0; p < nc; ++p) {
+    double gr[3], g1[3], g0[3], Hs[9];
+    contact_l(P, p, vc + 3 * p, gr, G + 9 * p);
+    /* the gradient is affine in mu: its mu-derivative is grad(mu=1) - grad(mu=0) */
+    orc_contact_potential(P->phi0[p], P->n0[p], 1.0, P->k[p], P->d[p], P->h, P->eps_s, vc + 3 * p, g1, Hs);
+    orc_contact_potential(P->phi0[p], P->n0[p], 0.0, P->k[p], P->d[p], P->h, P->eps_s, vc + 3 * p, g0, Hs);
+    for (int c = 0; c < 3; ++c) dg[3 * p + c] = g1[c] - g0[c];
+  }
+  /* full Hessian on the free DoFs (Dirichlet rows and columns -> identity) */
+  memset(Hd, 0, sizeof(double) * (size_t)N3 * N3);
+  for (int i = 0; i < n; ++i)
+    for (int c = 0; c < 3; ++c) Hd[(size_t)(3 * i + c) * N3 + 3 * i + c] = is_fixed(P, i) ? 1.0 : P->m[i];
+  for (int p = 0; p < nc; ++p) {
+    double RG[9], Gw[9];
+    mat_mul(P->R + 9 * p, G + 9 * p, RG);
+    mat_mul_bt(RG, P->R + 9 * p, Gw);
+    for (int s = 0; s < 27; ++s) {
+      int i = P->nodes[27 * p + s];
+      if (i < 0 || is_fixed(P, i)) continue;
+      for (int t = 0; t < 27; ++t) {
+        int j = P->nodes[27 * p + t];
+        if (j < 0 || is_fixed(P, j)) continue;
+        double ww = P->w[27 * p + s] * P->w[27 * p + t];
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c) Hd[(size_t)(3 * i + r) * N3 + 3 * j + c] += ww * Gw[3 * r + c];
+      }
+    }
+  }
+  int status = ORC_OK;
+  if (!dense_cholesky(Hd, N3)) {
+    status = ORC_ERR_NOT_SPD;
+  } else {
+    for (int i = 0; i < n; ++i)
+      for (int c = 0; c < 3; ++c) lam[3 * i + c] = is_fixed(P, i) ? 0.0 : vbar[3 * i + c];
+    dense_cholesky_solve(Hd, N3, lam);
+    for (int i = 0; i < n; ++i)
+      if (is_fixed(P, i)) for (int c = 0; c < 3; ++c) lam[3 * i + c] = 0.0;
+    contact_velocities(P, lam, 0, jl); /* J lambda, contact frame */
+    for (int i = 0; i < n; ++i)
+      for (int c = 0; c < 3; ++c)
+        vstar_bar[3 * i + c] = is_fixed(P, i) ? vbar[3 * i + c] : P->m[i] * lam[3 * i + c];
+    for (int p = 0; p < nc; ++p) {
+      const double* Gp = G + 9 * p;
+      double gl[3];
+      for (int r = 0; r < 3; ++r)
+        gl[r] = Gp[3 * r] * jl[3 * p] + Gp[3 * r + 1] * jl[3 * p + 1] + Gp[3 * r + 2] * jl[3 * p + 2];
+      for (int c = 0; c < 3; ++c) b_bar[3 * p + c] = -gl[c];
+      mu_bar[p] = -(dg[3 * p] * jl[3 * p] + dg[3 * p + 1] * jl[3 * p + 1] + dg[3 * p + 2] * jl[3 * p + 2]);
+      /* Dirichlet nodes in the stencil: - J_x^T (d2 l_c) J lambda */
+      const double* R = P->R + 9 * p;
+      double glw[3];
+      for (int r = 0; r < 3; ++r) glw[r] = R[3 * r] * gl[0] + R[3 * r + 1] * gl[1] + R[3 * r + 2] * gl[2];
+      for (int s2 = 0; s2 < 27; ++s2) {
+        int i = P->nodes[27 * p + s2];
+        if (i < 0 || !is_fixed(P, i)) continue;
+        for (int c = 0; c < 3; ++c) vstar_bar[3 * i + c] -= P->w[27 * p + s2] * glw[c];
+      }
+    }
+  }
+  free(vc); free(G); free(dg); free(Hd); free(lam); free(jl);
+  return status;
+}
+

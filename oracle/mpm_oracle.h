@@ -199,6 +199,19 @@ int orc_last_grid(const orc_sim* s, int cap, int* ids, double* m, double* vstar,
 int orc_last_contacts(const orc_sim* s, int cap, int* particle, int* body,
                       double* gamma_world, double* phi0, double* n0);
 
+/* Adjoint of the contact solve by implicit differentiation of its optimality
+   condition grad l_p(v) = 0 (Eq. (8)-(9)) at a minimiser v: with vbar = dL/dv,
+   lambda solves H_hat lambda = vbar on the free DoFs, H_hat = M + J^T (d2 l_c) J
+   the full Hessian (Eq. (10)); then
+     dL/dv*   = M lambda on free DoFs, and vbar - J_x^T (d2 l_c) J lambda on
+                Dirichlet DoFs (v = v* there, which the contacts see);
+     dL/db_c  = -(d2 l_c) (J lambda)_c, contact frame (b: the bias velocity);
+     dL/dmu_c = -(d/dmu dl_c/dv_c) . (J lambda)_c.
+   vstar_bar [3 n_nodes], b_bar [3 n_contacts], mu_bar [n_contacts]. Dense
+   Cholesky: small problems only. Returns ORC_OK or ORC_ERR_NOT_SPD. */
+int orc_contact_adjoint(const orc_problem* P, const double* v, const double* vbar,
+                        double* vstar_bar, double* b_bar, double* mu_bar);
+
 /* Async time splitting (Eq. (3)-(4)): advance kinematic bodies by dt with their
    frozen velocity after the N substeps of a time step. */
 void orc_advance_kinematic(int nb, orc_body* bodies, double dt);
