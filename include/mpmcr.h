@@ -57,7 +57,7 @@ typedef enum {
   MPM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
   MPM_ERR_OOM = 3,            /* device allocation failed */
   MPM_ERR_CAPACITY = 4,       /* more particles or contacts than the context holds */
-  MPM_ERR_NOT_CONVERGED = 5,  /* a contact solve hit max_iters (Alg. 1) */
+  MPM_ERR_NOT_CONVERGED = 5,  /* a contact solve (Alg. 1) or its adjoint hit max_iters */
   MPM_ERR_OUT_OF_DOMAIN = 6,  /* a particle's stencil left the grid */
   MPM_ERR_NAN = 7,            /* a non-finite value appeared in the solve */
   MPM_ERR_STATE = 8,          /* call not valid in the context's state */
@@ -279,6 +279,64 @@ mpm_status mpm_get_grid_noalloc(mpm_ctx* ctx, int64_t cap, int64_t* count, int32
    penetration depth and lagged normal impulse. Host arrays, as above. */
 mpm_status mpm_get_contacts(mpm_ctx* ctx, int64_t cap, int64_t* count, int32_t* particle,
                             int32_t* body, float* gamma, float* phi0, float* n0);
+
+/* Adjoint of the last substep's contact solve (the contact problem of
+   Eq. (7)-(8) as it stood at the end of the last mpm_step), by implicit
+   differentiation of its optimality condition
+     M (v - v*) + J^T dl_c(J v + b) = 0   on the free grid DoFs,
+   where b = -v_r(x_p) is minus the frozen body velocity at each contact point
+   and l_c is the lagged contact potential of Sec. IV-B. The paper does not
+   differentiate its solver; this is an extension of the library.
+   Given vbar = dL/dv for a loss L of the post-contact grid velocity v, let
+   lambda solve (M + J^T d2l_c J) lambda = vbar on the free DoFs (the exact
+   Hessian: the 3x3 blocks of Eq. (10) and their couplings). Then
+     dL/dv*      = M lambda on free nodes; on Dirichlet or massless nodes
+                   (where v = v*) vbar - (J^T d2l_c J lambda);
+     dL/dv_r(x_p) = d2l_c (J lambda)_c   per contact (world frame);
+     dL/dmu_c    = -(n0 / s) u_t . (J lambda)_c   per contact,
+   with u_t the tangential relative velocity at the solution and
+   s = sqrt(|u_t|^2 + eps_s^2). The lagged depth phi0 and normal impulse n0
+   are held fixed. lambda is found by conjugate gradients preconditioned by
+   the 3x3 diagonal blocks of the Hessian, in one cooperative launch.
+
+   Inputs (mem_kind MPM_MEM_HOST or MPM_MEM_DEVICE for all four node and
+   contact arrays): n grid nodes as linear ids i + res[0]*(j + res[1]*k)
+   (the ids of mpm_get_grid), each in [0, res[0]*res[1]*res[2]), and vbar
+   [n][3]. Nodes not listed have vbar = 0; a node listed twice has its vbar
+   summed and both entries receive the node's result.
+   Outputs: vstar_bar [n][3] = dL/dv* at the listed nodes (vbar itself at a
+   node outside the contacts' stencils, where v = v* + 0); contact_bar
+   [contact_cap][4] (may be NULL with contact_cap 0): per contact, in the
+   order of mpm_get_contacts, dL/dv_r(x_p) (3) and dL/dmu_c, rows beyond the
+   contact count untouched; body_bar [n_bodies][7] doubles (may be NULL): per
+   body of the last step, dL/dv (3) and dL/domega (3) of its spatial velocity
+   (through b only: v_r(x) = v + omega x (x - p)) and dL/dmu.
+   params may be NULL for eps_r = 1e-5 (stop when the residual's P^-1 norm
+   falls below eps_r times vbar's) and max_iters = 1000.
+   Errors: MPM_ERR_STATE before any mpm_step with n_substeps > 0;
+   MPM_ERR_INVALID_ARG for bad arguments or (host ids) an id outside the
+   grid, checked before any work; device ids outside the grid are reported
+   after the call as MPM_ERR_INVALID_ARG and give zeros; MPM_ERR_NOT_CONVERGED
+   if max_iters was reached (outputs hold the last iterate). A device-side
+   failure of an earlier call is returned first, without computing.
+   Synchronises the context's stream; the grid, contacts and particles are
+   left as they were (mpm_get_grid / mpm_get_contacts still read them). */
+typedef struct {
+  double eps_r;
+  int32_t max_iters;
+} mpm_adjoint_params;
+
+typedef struct {
+  int32_t iters;          /* conjugate-gradient iterations */
+  float residual;         /* final |r|_P^-1 / |vbar|_P^-1 on the contact nodes */
+  int32_t contacts;       /* contacts of the differentiated substep */
+  int32_t contact_nodes;  /* grid nodes in their stencils */
+} mpm_adjoint_stats;
+
+mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const int32_t* node_ids,
+                               const float* vbar, float* vstar_bar, int64_t contact_cap,
+                               float* contact_bar, double* body_bar,
+                               const mpm_adjoint_params* params, mpm_adjoint_stats* stats);
 
 /* Wait for the context's stream and report any device-side failure. */
 mpm_status mpm_synchronize(mpm_ctx* ctx);

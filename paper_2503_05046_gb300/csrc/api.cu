@@ -69,6 +69,18 @@ struct mpm_ctx {
   std::vector<std::pair<int, cudaEvent_t>> ev_marks;  // (phase starting at this event, event)
   double phase_ms[MPM_NUM_PHASES] = {0};
   int64_t phase_n[MPM_NUM_PHASES] = {0};
+  // the last substep, for mpm_contact_adjoint
+  bool adj_ready = false;
+  float last_h = 0.f, last_eps_s = 0.f;
+  int last_nb = 0;
+  // the adjoint's device buffers, allocated at its first call
+  float4* adj_vec = nullptr;       // kAdjointVectors x cnodes_cap
+  double* adj_body = nullptr;      // 7 per body
+  float* adj_out = nullptr;        // iterations, residual, contacts, contact nodes
+  int adj_blocks = 0;
+  int32_t* adj_ids = nullptr;      // staging of host inputs and outputs
+  float* adj_io = nullptr;         // vbar (3n), vstar_bar (3n), contact_bar (4 cap)
+  size_t adj_ids_cap = 0, adj_io_cap = 0;
   std::string err;
 };
 
@@ -225,14 +237,15 @@ void integrate_dynamic(mpm_rigid_body& b, const mpm_rigid_dynamics& d, const dou
 mpm_status first_error(mpm_ctx* ctx, uint32_t bits) {
   static const mpm_status order[] = {MPM_ERR_TIMEOUT, MPM_ERR_NAN, MPM_ERR_OUT_OF_DOMAIN,
                                      MPM_ERR_CAPACITY, MPM_ERR_LINE_SEARCH,
-                                     MPM_ERR_NOT_CONVERGED};
+                                     MPM_ERR_NOT_CONVERGED, MPM_ERR_INVALID_ARG};
   static const char* msg[] = {"a device-wide barrier of the contact solve timed out",
                               "a non-finite value appeared in the contact solve",
                               "a particle's B-spline stencil left the grid domain",
                               "more contact points than max_contacts in one substep",
                               "the line-search bracket could not be formed",
-                              "a contact solve reached max_iters before converging"};
-  for (int i = 0; i < 6; ++i)
+                              "a contact solve (or its adjoint) reached max_iters before converging",
+                              "a node id given to the adjoint lies outside the grid"};
+  for (int i = 0; i < 7; ++i)
     if (bits & (1u << order[i])) return fail(ctx, order[i], msg[i]);
   return MPM_OK;
 }
@@ -291,7 +304,8 @@ void release(mpm_ctx* c) {
                   c->G.acc2, c->G.dv, c->G.mark, c->G.cflag, c->G.cnodes, c->G.n_cnodes, c->G.pstar2, c->G.act, c->G.n_act, c->C.xp, c->C.nrm,
                   c->C.bias, c->C.id, c->C.vc, c->C.dvc, c->C.gamma, c->C.count, c->red, c->bar, c->poison,
                   c->status, c->stats, c->impulses, c->sb.keys[0], c->sb.keys[1], c->sb.vals[0],
-                  c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage};
+                  c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage, c->adj_vec, c->adj_body,
+                  c->adj_out, c->adj_ids, c->adj_io};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : c->gexec)
@@ -742,6 +756,10 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
   if (!launched) CU(enqueue_step(ctx, from, sort_now, n_substeps, hf, sp, solve_blocks, s));
   if (sort_now) ctx->cur = 1 - from;
   CU(cudaGetLastError());
+  ctx->adj_ready = n_substeps > 0;
+  ctx->last_h = hf;
+  ctx->last_eps_s = sp.eps_s;
+  ctx->last_nb = nb;
   // async splitting (Eq. (3)-(4)): kinematic bodies move with their frozen
   // velocity; dynamic ones take the step's accumulated contact impulses
   const double dt = h * n_substeps;
@@ -884,6 +902,109 @@ mpm_status mpm_get_contacts(mpm_ctx* ctx, int64_t cap, int64_t* count, int32_t* 
     if (n0) n0[i] = nrm[i].w;
   }
   return MPM_OK;
+}
+
+mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const int32_t* node_ids,
+                               const float* vbar, float* vstar_bar, int64_t contact_cap,
+                               float* contact_bar, double* body_bar,
+                               const mpm_adjoint_params* params, mpm_adjoint_stats* stats) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (mem_kind != MPM_MEM_HOST && mem_kind != MPM_MEM_DEVICE)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_contact_adjoint: bad mem_kind");
+  if (n < 0 || n > (int64_t)(INT32_MAX / 3) || (n > 0 && (!node_ids || !vbar || !vstar_bar)) ||
+      contact_cap < 0 || (contact_cap > 0 && !contact_bar))
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_contact_adjoint: bad node or contact arrays");
+  mpm_adjoint_params ap;
+  ap.eps_r = 1e-5;
+  ap.max_iters = 1000;
+  if (params) ap = *params;
+  if (!(ap.eps_r >= 0.0) || ap.max_iters < 0)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_contact_adjoint: bad parameters");
+  if (!ctx->adj_ready)
+    return fail(ctx, MPM_ERR_STATE, "mpm_contact_adjoint: no substep to differentiate (mpm_step first)");
+  const int64_t n_grid = (int64_t)ctx->g.rx * ctx->g.ry * ctx->g.rz;
+  if (mem_kind == MPM_MEM_HOST)
+    for (int64_t i = 0; i < n; ++i)
+      if (node_ids[i] < 0 || node_ids[i] >= n_grid)
+        return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_contact_adjoint: node id outside the grid");
+  // failures of earlier calls are reported first, not taken for the adjoint's
+  mpm_status st = drain_status(ctx);
+  if (st != MPM_OK) return st;
+  cudaStream_t s = ctx->stream;
+  if (!ctx->adj_vec) {
+    CU(dalloc(&ctx->adj_vec, (size_t)kAdjointVectors * ctx->G.cnodes_cap));
+    CU(dalloc(&ctx->adj_body, 7 * kMaxBodies));
+    CU(dalloc(&ctx->adj_out, 4));
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel_ptr(), solve_block_size(), 0));
+    if (occ < 1) return fail(ctx, MPM_ERR_CUDA, "mpm_contact_adjoint: kernel does not fit an SM");
+    ctx->adj_blocks = ctx->num_sms * (occ < 2 ? occ : 2);
+  }
+  const int64_t ccap = contact_cap < ctx->C.cap ? contact_cap : ctx->C.cap;
+  const int32_t* d_ids = node_ids;
+  const float* d_vbar = vbar;
+  float* d_vsb = vstar_bar;
+  float* d_cbar = contact_bar;
+  if (mem_kind == MPM_MEM_HOST) {
+    const size_t need_io = (size_t)6 * n + (size_t)4 * ccap;
+    if (ctx->adj_ids_cap < (size_t)n || !ctx->adj_ids) {
+      if (ctx->adj_ids) cudaFree(ctx->adj_ids);
+      ctx->adj_ids = nullptr;
+      ctx->adj_ids_cap = 0;
+      CU(dalloc(&ctx->adj_ids, (size_t)n + 1));
+      ctx->adj_ids_cap = (size_t)n + 1;
+    }
+    if (ctx->adj_io_cap < need_io || !ctx->adj_io) {
+      if (ctx->adj_io) cudaFree(ctx->adj_io);
+      ctx->adj_io = nullptr;
+      ctx->adj_io_cap = 0;
+      CU(dalloc(&ctx->adj_io, need_io + 4));
+      ctx->adj_io_cap = need_io + 4;
+    }
+    float* io = ctx->adj_io;
+    d_ids = ctx->adj_ids;
+    d_vbar = io;
+    d_vsb = io + 3 * n;
+    d_cbar = ccap > 0 ? io + 6 * n : nullptr;
+    if (n > 0) {
+      CU(cudaMemcpyAsync(ctx->adj_ids, node_ids, n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      CU(cudaMemcpyAsync(io, vbar, 3 * n * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+  }
+  AdjointArgs a;
+  a.g = ctx->g; a.G = ctx->G; a.C = ctx->C; a.bodies = ctx->bodies_d; a.nb = ctx->last_nb;
+  a.h = ctx->last_h; a.eps_s = ctx->last_eps_s; a.eps_r = ap.eps_r; a.max_iters = ap.max_iters;
+  a.n_in = (int)n; a.ids = d_ids; a.vbar = d_vbar; a.vstar_bar = d_vsb;
+  a.contact_bar = d_cbar; a.contact_cap = (int)ccap; a.body_bar = ctx->adj_body;
+  a.vec = ctx->adj_vec; a.red = ctx->red; a.bar = ctx->bar; a.status = ctx->status;
+  a.poison = ctx->poison; a.stats = ctx->stats; a.out = ctx->adj_out;
+  // the barrier counter and the node-list length are zero between launches
+  CU(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned), s));
+  CU(cudaMemsetAsync(ctx->G.n_cnodes, 0, sizeof(int), s));
+  CU(cudaMemsetAsync(ctx->adj_body, 0, 7 * kMaxBodies * sizeof(double), s));
+  CU(cudaMemsetAsync(ctx->adj_out, 0, 4 * sizeof(float), s));
+  CU(launch_adjoint(a, ctx->adj_blocks, s));
+  CU(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned), s));
+  CU(cudaMemsetAsync(ctx->G.n_cnodes, 0, sizeof(int), s));
+  st = drain_status(ctx);
+  float out[4];
+  CU(cudaMemcpy(out, ctx->adj_out, sizeof(out), cudaMemcpyDeviceToHost));
+  const int64_t nc = (int64_t)out[2];
+  const int64_t k = nc < ccap ? nc : ccap;
+  const cudaMemcpyKind back = mem_kind == MPM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (mem_kind == MPM_MEM_HOST) {
+    if (n > 0) CU(cudaMemcpy(vstar_bar, d_vsb, 3 * n * sizeof(float), cudaMemcpyDeviceToHost));
+    if (k > 0) CU(cudaMemcpy(contact_bar, d_cbar, 4 * k * sizeof(float), cudaMemcpyDeviceToHost));
+  }
+  if (body_bar && ctx->last_nb > 0)
+    CU(cudaMemcpy(body_bar, ctx->adj_body, 7 * ctx->last_nb * sizeof(double), back));
+  if (stats) {
+    stats->iters = (int32_t)out[0];
+    stats->residual = out[1];
+    stats->contacts = (int32_t)out[2];
+    stats->contact_nodes = (int32_t)out[3];
+  }
+  return st;
 }
 
 mpm_status mpm_synchronize(mpm_ctx* ctx) {

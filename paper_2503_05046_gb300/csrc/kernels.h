@@ -99,6 +99,37 @@ const void* solve_kernel_ptr();
 size_t solve_dynamic_smem();
 cudaError_t solve_prepare();  // once per device, before the occupancy query
 
+// ---- solve.cu: adjoint of the contact solve (implicit differentiation of
+// Eq. (8)), conjugate gradients in one cooperative launch
+struct AdjointArgs {
+  GridDev g;
+  GridArrays G;
+  Contacts C;
+  const DevBody* bodies;
+  int nb;
+  float h;            // substep of the differentiated solve
+  float eps_s;        // its friction regularisation
+  double eps_r;       // stop at |r|_P^-1 <= eps_r |vbar|_P^-1
+  int max_iters;
+  int n_in;           // (node id, vbar) pairs
+  const int* ids;     // linear node ids i + rx (j + ry k)
+  const float* vbar;  // [3 n_in]
+  float* vstar_bar;   // [3 n_in]
+  float* contact_bar; // [4 contact_cap]: dL/dv_r(x_p) (3), dL/dmu; may be null
+  int contact_cap;
+  double* body_bar;   // [7 nb]: dL/dv, dL/domega, dL/dmu per body, zeroed by the caller
+  float4* vec;        // kAdjointVectors x cnodes_cap float4
+  double* red;
+  unsigned* bar;
+  uint32_t* status;
+  int* poison;
+  const DevStats* stats;  // last_contacts: the differentiated substep's contact count
+  float* out;         // [4]: iterations, relative residual, contacts, contact nodes
+};
+constexpr int kAdjointVectors = 13;
+cudaError_t launch_adjoint(const AdjointArgs& a, int grid_blocks, cudaStream_t s);
+const void* adjoint_kernel_ptr();
+
 // ---- g2p.cu: grid-to-particle with the constitutive update ----
 struct G2PArgs {
   GridDev g;

@@ -750,6 +750,563 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the contact solve: implicit differentiation of the optimality
+// condition of Eq. (8)-(9) at the last substep's solution v,
+//   grad l_p = M (v - v*) + J^T dl_c(J v + b) = 0   (free DoFs).
+// For a loss L(v) with vbar = dL/dv, lambda solves H^ lambda = vbar on the
+// free DoFs, with H^ = M + J^T (d2 l_c) J the exact Hessian (the blocks of
+// Eq. (10) plus their couplings between nodes), and
+//   dL/dv*    = M lambda on free DoFs; vbar - (J^T d2l_c J lambda) on the
+//               other nodes (Dirichlet or massless: v = v* there),
+//   dL/dv_r   = d2l_c (J lambda)_c   (the contact velocity has b = -v_r(x_p)),
+//   dL/dmu_c  = -(n0 / s) u_t . (J lambda)_c   (d/dmu of dl_c, Sec. IV-B).
+// H^ is symmetric positive definite (M > 0 on free DoFs, d2 l_c positive
+// semidefinite), so lambda comes from conjugate gradients preconditioned by
+// the 3x3 diagonal blocks of H^, the matrix the quasi-Newton iteration
+// inverts (Eq. (10)). Only contact nodes take part: elsewhere H^ = M, so
+// lambda = M^-1 vbar and dL/dv* = vbar.
+//
+// Per CG iteration (one cooperative launch, like the forward solve):
+//   A  contacts: y_c = d2l_c J (z + beta p), scattered as w y_c;
+//   B  contact nodes: p = z + beta p, q = M p + J^T y; sum p.q;
+//   C  contact nodes: x += a p, r -= a q, z = P^-1 r; sum r.z.
+// CG runs in FP32 inside a mixed-precision iterative refinement: lambda is
+// kept as a double-float pair and the residual vbar - H^ lambda that starts
+// each round (and decides convergence) is formed in FP64.
+// The contact-node list is rebuilt here (the forward solve releases its
+// own); its node flags hold list positions + 1 for the duration of the call.
+
+// per-node vectors of the adjoint, each cnodes_cap float4 apart
+// (kVD and the slot after it hold 4 doubles per node)
+enum { kVRhs = 0, kVX, kVR, kVZ, kVP, kVQ, kVAcc, kVL0, kVL1, kVXh, kVXl, kVD, kVD2, kAdjVectors };
+constexpr int kRefineRounds = 3;  // FP32 CG rounds of the iterative refinement
+static_assert(kAdjVectors == kAdjointVectors, "adjoint vector count");
+
+// The contact Hessian at the stored solution velocity, kept in factored form
+// d2l_c = N'' n n^T + (mu n0 / s) (I - n n^T - u_t u_t^T / s^2) and applied
+// as such: the stiff normal term then never rounds into the tangential
+// components, which stay accurate to the (much smaller) friction scale.
+struct AdjHess {
+  float n[3], ut[3];
+  float d2N, cs, inv_s2;
+  float n0_s;  // n0 / s, for dL/dmu
+};
+
+__device__ __forceinline__ void adjoint_contact(const Contacts& C, int p, const DevBody* bodies,
+                                                float h, float eps_s, AdjHess& A, int& body,
+                                                float4& xp) {
+  float n0;
+  load_contact(C, p, xp, A.n, n0);
+  body = C.id[p].y;
+  const DevBody& bd = bodies[body];
+  const float4 vc = C.vc[p];
+  const float u[3] = {vc.x, vc.y, vc.z};
+  ContactLaw L;
+  contact_law(xp.w, n0, bd.mu, bd.k, bd.d, h, eps_s, A.n, u, L);
+  // u_t = u - (u.n) n keeps a normal component of the order of ulp(|u|)
+  // from rounding; near sticking, where |u_t| ~ eps_s << |u|, that component
+  // would mix the large normal part of J lambda into the friction terms, so
+  // project it out once more
+  const float tn = L.ut[0] * A.n[0] + L.ut[1] * A.n[1] + L.ut[2] * A.n[2];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) A.ut[r] = L.ut[r] - tn * A.n[r];
+  A.d2N = L.d2N;
+  A.cs = L.cs;
+  A.inv_s2 = L.inv_s2;
+  A.n0_s = n0 * sqrtf(L.inv_s2);
+}
+
+// y = d2l_c u (FP32)
+__device__ __forceinline__ void hess_apply(const AdjHess& A, const float (&u)[3], float (&y)[3]) {
+  const float un = A.n[0] * u[0] + A.n[1] * u[1] + A.n[2] * u[2];
+  const float tu = (A.ut[0] * u[0] + A.ut[1] * u[1] + A.ut[2] * u[2]) * A.inv_s2;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) y[r] = A.d2N * un * A.n[r] + A.cs * ((u[r] - un * A.n[r]) - tu * A.ut[r]);
+}
+
+// y = d2l_c u (FP64, same factors)
+__device__ __forceinline__ void hess_apply(const AdjHess& A, const double (&u)[3], double (&y)[3]) {
+  const double n[3] = {A.n[0], A.n[1], A.n[2]}, t[3] = {A.ut[0], A.ut[1], A.ut[2]};
+  const double un = n[0] * u[0] + n[1] * u[1] + n[2] * u[2];
+  const double tu = (t[0] * u[0] + t[1] * u[1] + t[2] * u[2]) * (double)A.inv_s2;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    y[r] = (double)A.d2N * un * n[r] + (double)A.cs * ((u[r] - un * n[r]) - tu * t[r]);
+}
+
+// the 3x3 block (xx yy zz xy xz yz), for the preconditioner
+__device__ __forceinline__ void hess_block(const AdjHess& A, float (&H)[6]) {
+  auto e = [&](int r, int c) {
+    const float id = (r == c) ? 1.0f : 0.0f;
+    return A.d2N * A.n[r] * A.n[c] + A.cs * (id - A.n[r] * A.n[c] - A.ut[r] * A.ut[c] * A.inv_s2);
+  };
+  H[0] = e(0, 0); H[1] = e(1, 1); H[2] = e(2, 2);
+  H[3] = e(0, 1); H[4] = e(0, 2); H[5] = e(1, 2);
+}
+
+// z = P^-1 r with P = L L^T stored as (l10, l20, l21, 1/l00), (1/l11, 1/l22, free, m)
+__device__ __forceinline__ float4 chol_apply(const float4 a, const float4 b, const float4 r) {
+  const float y0 = r.x * a.w;
+  const float y1 = (r.y - a.x * y0) * b.x;
+  const float y2 = (r.z - a.y * y0 - a.z * y1) * b.y;
+  const float z2 = y2 * b.y;
+  const float z1 = (y1 - a.z * z2) * b.x;
+  const float z0 = (y0 - a.x * z1 - a.y * z2) * a.w;
+  return make_float4(z0, z1, z2, 0.f);
+}
+
+__device__ __forceinline__ double warp_sum_f64(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// lambda = hi + lo at list position ci (zero off the list)
+__device__ __forceinline__ void lambda_at(const float4* xh, const float4* xl, int ci, double (&x)[3]) {
+  x[0] = x[1] = x[2] = 0.0;
+  if (ci >= 0) {
+    const float4 h = __ldcg(xh + ci), l = __ldcg(xl + ci);
+    x[0] = (double)h.x + (double)l.x;
+    x[1] = (double)h.y + (double)l.y;
+    x[2] = (double)h.z + (double)l.z;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
+  __shared__ DevBody s_body[kMaxBodies];
+  __shared__ float s_red[kWarps][kRedWidth];
+  __shared__ float2 s_tot[kRedWidth];
+  __shared__ float s_bb[kMaxBodies][7];
+  const int tid = threadIdx.x;
+  // the last substep's contact count (G2P has reset the live counter)
+  const int count = a.stats->last_contacts;
+  const int nc = count < a.C.cap ? count : a.C.cap;
+  int nblk = (nc + kContactsPerBlock - 1) / kContactsPerBlock;
+  nblk = nblk < (int)gridDim.x ? nblk : (int)gridDim.x;
+  nblk = nblk < kMaxSolveBlocks ? nblk : kMaxSolveBlocks;
+  nblk = nblk > 1 ? nblk : 1;
+  if ((int)blockIdx.x >= nblk) return;
+  for (int i = tid; i < a.nb * (int)(sizeof(DevBody) / 4); i += kThreads)
+    reinterpret_cast<float*>(s_body)[i] = reinterpret_cast<const float*>(a.bodies)[i];
+  for (int i = tid; i < kMaxBodies * 7; i += kThreads) (&s_bb[0][0])[i] = 0.f;
+  __syncthreads();
+  Barrier B{a.bar, (unsigned)nblk, a.status, a.poison};
+  const int gtid = blockIdx.x * kThreads + tid;
+  const int gstride = nblk * kThreads;
+  const int lane = tid & 31;
+  const int gwarp = gtid >> 5;
+  const int nwarps = gstride >> 5;
+  const GridDev& g = a.g;
+  const size_t cap = (size_t)a.G.cnodes_cap;
+  float4* vRhs = a.vec + kVRhs * cap;
+  float4* vX = a.vec + kVX * cap;
+  float4* vR = a.vec + kVR * cap;
+  float4* vZ = a.vec + kVZ * cap;
+  float4* vP = a.vec + kVP * cap;
+  float4* vQ = a.vec + kVQ * cap;
+  float4* vAcc = a.vec + kVAcc * cap;
+  float4* vL0 = a.vec + kVL0 * cap;
+  float4* vL1 = a.vec + kVL1 * cap;
+  float4* vXh = a.vec + kVXh * cap;
+  float4* vXl = a.vec + kVXl * cap;
+  double* acc64 = reinterpret_cast<double*>(a.vec + kVD * cap);  // 4 doubles per node
+  int rslot = 0;
+  auto next_slot = [&]() -> float2* {
+    float2* s = reinterpret_cast<float2*>(a.red) + (size_t)(rslot & 3) * kMaxSolveBlocks * kRedWidth;
+    ++rslot;
+    return s;
+  };
+  const int n_nodes_total = g.rx * g.ry * g.rz;
+  auto node_of_id = [&](int id) -> int {
+    if (id < 0 || id >= n_nodes_total) return -1;
+    const int i = id % g.rx, j = (id / g.rx) % g.ry, k = id / (g.rx * g.ry);
+    return node_index(g, i, j, k);
+  };
+  auto list_pos = [&](const LaneNode& ln) -> int {
+    return lane < 27 ? __ldcg(a.G.cflag + ln.node) - 1 : -1;
+  };
+
+  // a solve that gave up at a barrier left node flags and accumulators behind
+  if (__ldcg(a.poison)) {
+    const size_t n_nodes = (size_t)g.nbx * g.nby * g.nbz * kBlockNodes;
+    for (size_t t = gtid; t < n_nodes; t += gstride) {
+      a.G.cflag[t] = 0;
+      a.G.acc0[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a.G.acc1[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a.G.acc2[t] = 0.f;
+    }
+    if (!grid_sync(B)) return;
+    if (gtid == 0) *a.poison = 0;
+  }
+
+  // ---- contact-node list; flags hold list position + 1 (-1: claimed, no room)
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int p = gtid; p < nc; p += gstride) {
+    const float4 xp = a.C.xp[p];
+    Stencil s;
+    stencil(g, xp.x, xp.y, xp.z, s);
+    int node[27];
+    unsigned won = 0u;
+#pragma unroll
+    for (int c = 0; c < 27; ++c) {
+      node[c] = node_index(g, s.base[0] + c % 3, s.base[1] + (c / 3) % 3, s.base[2] + c / 9);
+      if (atomicCAS(a.G.cflag + node[c], 0, -1) == 0) won |= 1u << c;
+    }
+    if (won) {
+      int slot = atomicAdd(a.G.n_cnodes, __popc(won));
+#pragma unroll
+      for (int c = 0; c < 27; ++c)
+        if ((won >> c) & 1u) {
+          if (slot < a.G.cnodes_cap) {
+            a.G.cnodes[slot] = node[c];
+            a.G.cflag[node[c]] = slot + 1;
+            vRhs[slot] = zero4;
+            vL0[slot] = zero4;
+            vL1[slot] = zero4;
+            vAcc[slot] = zero4;
+            double* d = acc64 + 4 * (size_t)slot;
+            d[0] = d[1] = d[2] = d[3] = 0.0;
+          } else {  // unreachable (the list holds every grid node): flag and clean up
+            atomicOr(a.status, kStCapacity);
+            atomicExch(a.poison, 1);
+          }
+          ++slot;
+        }
+    }
+  }
+  if (!grid_sync(B)) return;
+  int ncn = __ldcg(a.G.n_cnodes);
+  ncn = ncn < a.G.cnodes_cap ? ncn : a.G.cnodes_cap;
+
+  // ---- vbar onto the contact nodes; diagonal blocks of J^T d2l_c J (w^2 H)
+  for (int i = gtid; i < a.n_in; i += gstride) {
+    const int node = node_of_id(a.ids[i]);
+    if (node < 0) {
+      atomicOr(a.status, 1u << MPM_ERR_INVALID_ARG);
+      continue;
+    }
+    const int ci = __ldcg(a.G.cflag + node) - 1;
+    if (ci >= 0) {
+      float* d = reinterpret_cast<float*>(vRhs + ci);
+      atomicAdd(d, a.vbar[3 * i]);
+      atomicAdd(d + 1, a.vbar[3 * i + 1]);
+      atomicAdd(d + 2, a.vbar[3 * i + 2]);
+    }
+  }
+  for (int p = gwarp; p < nc; p += nwarps) {
+    AdjHess A;
+    int body;
+    float4 xp;
+    adjoint_contact(a.C, p, s_body, a.h, a.eps_s, A, body, xp);
+    const LaneNode ln = lane_node(g, xp, lane);
+    const int ci = list_pos(ln);
+    if (ci >= 0) {
+      float H[6];
+      hess_block(A, H);
+      const float w2 = ln.w * ln.w;
+      red_add_v4(vL0 + ci, w2 * H[0], w2 * H[1], w2 * H[2], w2 * H[3]);
+      red_add_v4(vL1 + ci, w2 * H[4], w2 * H[5], 0.f, 0.f);
+    }
+  }
+  if (!grid_sync(B)) return;
+
+  // ---- preconditioner P = m I + block (Cholesky), r = vbar (free DoFs),
+  // lambda = 0, increment x = 0
+  {
+    float acc[1] = {0.f};  // r.z
+    for (int t = gtid; t < ncn; t += gstride) {
+      const int node = a.G.cnodes[t];
+      const float m = a.G.vs[node].w;
+      const bool fre = m > 0.f && a.G.v[node].w == 0.f;
+      const float4 c0 = __ldcg(vL0 + t), c1 = __ldcg(vL1 + t);
+      float4 L0 = zero4, L1 = make_float4(0.f, 0.f, 0.f, m);
+      float4 r = zero4, z = zero4;
+      if (fre) {
+        const float h00 = m + c0.x, h11 = m + c0.y, h22 = m + c0.z;
+        const float h01 = c0.w, h02 = c1.x, h12 = c1.y;
+        const float l00 = sqrtf(h00);
+        const float l10 = h01 / l00, l20 = h02 / l00;
+        const float l11 = sqrtf(fmaxf(h11 - l10 * l10, 1e-30f));
+        const float l21 = (h12 - l20 * l10) / l11;
+        const float l22 = sqrtf(fmaxf(h22 - l20 * l20 - l21 * l21, 1e-30f));
+        L0 = make_float4(l10, l20, l21, 1.0f / l00);
+        L1 = make_float4(1.0f / l11, 1.0f / l22, 1.f, m);
+        r = __ldcg(vRhs + t);
+        r.w = 0.f;
+        z = chol_apply(L0, L1, r);
+        acc[0] += r.x * z.x + r.y * z.y + r.z * z.z;
+      }
+      vL0[t] = L0;
+      vL1[t] = L1;
+      vR[t] = r;
+      vZ[t] = z;
+      vX[t] = zero4;
+      vP[t] = zero4;
+      vXh[t] = zero4;
+      vXl[t] = zero4;
+    }
+    if (!reduce_all(acc, next_slot(), B, s_red, s_tot)) return;
+  }
+  const float rz_ref = s_tot[0].x + s_tot[0].y;  // |vbar|^2 in the P^-1 norm
+  const float tol2 = (float)(a.eps_r * a.eps_r) * rz_ref;
+  float rz = rz_ref;
+  float rz_true = rz_ref;
+  int it = 0;
+  // the warp's first contact, kept in registers across the iterations
+  const bool own = gwarp < nc;
+  AdjHess own_A{};
+  LaneNode own_ln{0, 0.f};
+  int own_ci = -1;
+  if (own) {
+    int body;
+    float4 xp;
+    adjoint_contact(a.C, gwarp, s_body, a.h, a.eps_s, own_A, body, xp);
+    own_ln = lane_node(g, xp, lane);
+    own_ci = list_pos(own_ln);
+  }
+
+  // J^T d2l_c J lambda in FP64 onto acc64 (lambda = hi + lo)
+  auto hessian_lambda_f64 = [&](const AdjHess& A, const LaneNode& ln, int ci, double (&u)[3],
+                                double (&y)[3]) {
+    double x[3];
+    lambda_at(vXh, vXl, ci, x);
+    const double w = (double)ln.w;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = warp_sum_f64(w * x[c]);
+    hess_apply(A, u, y);
+    if (ci >= 0) {
+      double* d = acc64 + 4 * (size_t)ci;
+      atomicAdd(d, w * y[0]);
+      atomicAdd(d + 1, w * y[1]);
+      atomicAdd(d + 2, w * y[2]);
+    }
+  };
+
+  // Mixed-precision iterative refinement: each round runs FP32 conjugate
+  // gradients on H^ x = r from x = 0, adds x to lambda (double-float), and
+  // forms the true residual r = vbar - H^ lambda in FP64 for the next round.
+  // FP32 CG alone stalls where the stiff normal blocks dominate H^ (its
+  // attainable accuracy is ~1e-7 of |H^| |lambda|, and the tangential parts
+  // of J lambda that dL/dmu reads are much smaller than the normal ones).
+  for (int round = 0;; ++round) {
+    float beta = 0.f;
+    while (rz > tol2 && rz > 0.f && it < a.max_iters) {
+      // ---- A: y_c = d2l_c J (z + beta p), scattered with weights w
+      auto phase_a = [&](const AdjHess& A, const LaneNode& ln, int ci) {
+        float pv[3] = {0.f, 0.f, 0.f};
+        if (ci >= 0) {
+          const float4 z = __ldcg(vZ + ci), pp = __ldcg(vP + ci);
+          pv[0] = fmaf(beta, pp.x, z.x);
+          pv[1] = fmaf(beta, pp.y, z.y);
+          pv[2] = fmaf(beta, pp.z, z.z);
+        }
+        const float u[3] = {warp_sum(ln.w * pv[0]), warp_sum(ln.w * pv[1]), warp_sum(ln.w * pv[2])};
+        float y[3];
+        hess_apply(A, u, y);
+        if (ci >= 0) red_add_v4(vAcc + ci, ln.w * y[0], ln.w * y[1], ln.w * y[2], 0.f);
+      };
+      if (own) phase_a(own_A, own_ln, own_ci);
+      for (int p = gwarp + nwarps; p < nc; p += nwarps) {
+        AdjHess A;
+        int body;
+        float4 xp;
+        adjoint_contact(a.C, p, s_body, a.h, a.eps_s, A, body, xp);
+        const LaneNode ln = lane_node(g, xp, lane);
+        phase_a(A, ln, list_pos(ln));
+      }
+      if (!grid_sync(B)) return;
+      // ---- B: p = z + beta p, q = M p + J^T y
+      {
+        float acc[1] = {0.f};
+        for (int t = gtid; t < ncn; t += gstride) {
+          const float4 L1 = vL1[t];
+          const float4 y = __ldcg(vAcc + t);
+          vAcc[t] = zero4;
+          float4 q = zero4, pp = zero4;
+          if (L1.z != 0.f) {
+            const float4 z = vZ[t], po = vP[t];
+            pp = make_float4(fmaf(beta, po.x, z.x), fmaf(beta, po.y, z.y), fmaf(beta, po.z, z.z), 0.f);
+            q = make_float4(fmaf(L1.w, pp.x, y.x), fmaf(L1.w, pp.y, y.y), fmaf(L1.w, pp.z, y.z), 0.f);
+            acc[0] += pp.x * q.x + pp.y * q.y + pp.z * q.z;
+          }
+          vP[t] = pp;
+          vQ[t] = q;
+        }
+        if (!reduce_all(acc, next_slot(), B, s_red, s_tot)) return;
+      }
+      const float pq = s_tot[0].x + s_tot[0].y;
+      if (!(pq > 0.f)) {  // H^ is positive definite on the free DoFs: only rounding gets here
+        if (blockIdx.x == 0 && tid == 0 && !(pq == pq)) atomicOr(a.status, kStNan);
+        break;
+      }
+      const float alpha = rz / pq;
+      // ---- C: x += alpha p, r -= alpha q, z = P^-1 r
+      {
+        float acc[1] = {0.f};
+        for (int t = gtid; t < ncn; t += gstride) {
+          const float4 L1 = vL1[t];
+          if (L1.z == 0.f) continue;
+          const float4 pp = vP[t], q = vQ[t];
+          float4 x = vX[t], r = vR[t];
+          x.x = fmaf(alpha, pp.x, x.x); x.y = fmaf(alpha, pp.y, x.y); x.z = fmaf(alpha, pp.z, x.z);
+          r.x = fmaf(-alpha, q.x, r.x); r.y = fmaf(-alpha, q.y, r.y); r.z = fmaf(-alpha, q.z, r.z);
+          const float4 z = chol_apply(vL0[t], L1, r);
+          vX[t] = x;
+          vR[t] = r;
+          vZ[t] = z;
+          acc[0] += r.x * z.x + r.y * z.y + r.z * z.z;
+        }
+        if (!reduce_all(acc, next_slot(), B, s_red, s_tot)) return;
+      }
+      const float rz_new = s_tot[0].x + s_tot[0].y;
+      beta = rz > 0.f ? rz_new / rz : 0.f;
+      rz = rz_new;
+      ++it;
+    }
+    // ---- lambda += x (double-float); the next round starts from x = 0
+    for (int t = gtid; t < ncn; t += gstride) {
+      if (vL1[t].z == 0.f) continue;
+      const float4 x = vX[t];
+      float4 h = vXh[t], l = vXl[t];
+      dd_add(h.x, l.x, x.x);
+      dd_add(h.y, l.y, x.y);
+      dd_add(h.z, l.z, x.z);
+      vXh[t] = h;
+      vXl[t] = l;
+      vX[t] = zero4;
+      vP[t] = zero4;
+    }
+    if (!grid_sync(B)) return;
+    // ---- true residual r = vbar - M lambda - J^T d2l_c J lambda (FP64)
+    if (own) {
+      double u[3], y[3];
+      hessian_lambda_f64(own_A, own_ln, own_ci, u, y);
+    }
+    for (int p = gwarp + nwarps; p < nc; p += nwarps) {
+      AdjHess A;
+      int body;
+      float4 xp;
+      adjoint_contact(a.C, p, s_body, a.h, a.eps_s, A, body, xp);
+      const LaneNode ln = lane_node(g, xp, lane);
+      double u[3], y[3];
+      hessian_lambda_f64(A, ln, list_pos(ln), u, y);
+    }
+    if (!grid_sync(B)) return;
+    {
+      float acc[1] = {0.f};
+      for (int t = gtid; t < ncn; t += gstride) {
+        const float4 L1 = vL1[t];
+        double* d = acc64 + 4 * (size_t)t;
+        const double y[3] = {__ldcg(d), __ldcg(d + 1), __ldcg(d + 2)};
+        d[0] = d[1] = d[2] = 0.0;
+        if (L1.z == 0.f) continue;
+        const float4 b = vRhs[t], h = vXh[t], l = vXl[t];
+        const double m = (double)L1.w;
+        float4 r;
+        r.x = (float)((double)b.x - m * ((double)h.x + (double)l.x) - y[0]);
+        r.y = (float)((double)b.y - m * ((double)h.y + (double)l.y) - y[1]);
+        r.z = (float)((double)b.z - m * ((double)h.z + (double)l.z) - y[2]);
+        r.w = 0.f;
+        const float4 z = chol_apply(vL0[t], L1, r);
+        vR[t] = r;
+        vZ[t] = z;
+        acc[0] += r.x * z.x + r.y * z.y + r.z * z.z;
+      }
+      if (!reduce_all(acc, next_slot(), B, s_red, s_tot)) return;
+    }
+    rz_true = s_tot[0].x + s_tot[0].y;
+    rz = rz_true;
+    if (!(rz_true == rz_true)) {
+      if (blockIdx.x == 0 && tid == 0) atomicOr(a.status, kStNan);
+      break;
+    }
+    if (rz_true <= tol2 || round + 1 >= kRefineRounds || it >= a.max_iters) break;
+  }
+  if (rz_true > tol2 && blockIdx.x == 0 && tid == 0) atomicOr(a.status, kStNotConverged);
+
+  // ---- outputs per contact: dL/dv_r(x_p) = d2l_c J lambda, dL/dmu_c (FP64
+  // from lambda = hi + lo); J^T d2l_c J lambda onto the nodes for the
+  // Dirichlet / massless correction
+  for (int p = gwarp; p < nc; p += nwarps) {
+    AdjHess A;
+    int body;
+    float4 xp;
+    adjoint_contact(a.C, p, s_body, a.h, a.eps_s, A, body, xp);
+    const LaneNode ln = lane_node(g, xp, lane);
+    double u[3], yd[3];
+    hessian_lambda_f64(A, ln, list_pos(ln), u, yd);
+    if (lane == 0) {
+      const float y[3] = {(float)yd[0], (float)yd[1], (float)yd[2]};
+      const float mub = (float)(-(double)A.n0_s * ((double)A.ut[0] * u[0] + (double)A.ut[1] * u[1] +
+                                                   (double)A.ut[2] * u[2]));
+      if (a.contact_bar && p < a.contact_cap) {  // caller memory: 4-byte alignment only
+        float* o = a.contact_bar + 4 * (size_t)p;
+        o[0] = y[0]; o[1] = y[1]; o[2] = y[2]; o[3] = mub;
+      }
+      const DevBody& bd = s_body[body];
+      const float r0 = xp.x - bd.p[0], r1 = xp.y - bd.p[1], r2 = xp.z - bd.p[2];
+      atomicAdd(&s_bb[body][0], y[0]);
+      atomicAdd(&s_bb[body][1], y[1]);
+      atomicAdd(&s_bb[body][2], y[2]);
+      atomicAdd(&s_bb[body][3], r1 * y[2] - r2 * y[1]);
+      atomicAdd(&s_bb[body][4], r2 * y[0] - r0 * y[2]);
+      atomicAdd(&s_bb[body][5], r0 * y[1] - r1 * y[0]);
+      atomicAdd(&s_bb[body][6], mub);
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < a.nb * 7; i += kThreads) {
+    const float v = (&s_bb[0][0])[i];
+    if (v != 0.f) atomicAdd(a.body_bar + i, (double)v);
+  }
+  if (!grid_sync(B)) return;
+  // ---- dL/dv* on the contact nodes (into q)
+  for (int t = gtid; t < ncn; t += gstride) {
+    const float4 L1 = vL1[t];
+    double* d = acc64 + 4 * (size_t)t;
+    const double y[3] = {__ldcg(d), __ldcg(d + 1), __ldcg(d + 2)};
+    d[0] = d[1] = d[2] = 0.0;
+    float4 o;
+    if (L1.z != 0.f) {
+      const float4 h = vXh[t], l = vXl[t];
+      const double m = (double)L1.w;
+      o = make_float4((float)(m * ((double)h.x + (double)l.x)), (float)(m * ((double)h.y + (double)l.y)),
+                      (float)(m * ((double)h.z + (double)l.z)), 0.f);
+    } else {
+      const float4 b = vRhs[t];
+      o = make_float4((float)((double)b.x - y[0]), (float)((double)b.y - y[1]),
+                      (float)((double)b.z - y[2]), 0.f);
+    }
+    vQ[t] = o;
+  }
+  if (!grid_sync(B)) return;
+  for (int i = gtid; i < a.n_in; i += gstride) {
+    const int node = node_of_id(a.ids[i]);
+    float o[3] = {0.f, 0.f, 0.f};
+    if (node >= 0) {
+      const int ci = __ldcg(a.G.cflag + node) - 1;
+      if (ci >= 0) {
+        const float4 q = __ldcg(vQ + ci);
+        o[0] = q.x; o[1] = q.y; o[2] = q.z;
+      } else {
+        o[0] = a.vbar[3 * i]; o[1] = a.vbar[3 * i + 1]; o[2] = a.vbar[3 * i + 2];
+      }
+    }
+    a.vstar_bar[3 * i] = o[0];
+    a.vstar_bar[3 * i + 1] = o[1];
+    a.vstar_bar[3 * i + 2] = o[2];
+  }
+  if (!grid_sync(B)) return;
+  // release the node flags
+  for (int t = gtid; t < ncn; t += gstride) a.G.cflag[a.G.cnodes[t]] = 0;
+  if (gtid == 0) {
+    a.out[0] = (float)it;
+    a.out[1] = rz_ref > 0.f ? sqrtf(fmaxf(rz_true, 0.f) / rz_ref) : 0.f;
+    a.out[2] = (float)nc;
+    a.out[3] = (float)ncn;
+  }
+}
 }  // namespace
 
 int solve_block_size() { return kThreads; }
@@ -765,6 +1322,15 @@ cudaError_t launch_solve(const SolveArgs& a, int grid_blocks, cudaStream_t s) {
   void* params[] = {&args};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_solve), dim3(grid_blocks),
                                      dim3(kThreads), params, solve_dynamic_smem(), s);
+}
+
+const void* adjoint_kernel_ptr() { return reinterpret_cast<const void*>(&k_adjoint); }
+
+cudaError_t launch_adjoint(const AdjointArgs& a, int grid_blocks, cudaStream_t s) {
+  AdjointArgs args = a;
+  void* params[] = {&args};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_adjoint), dim3(grid_blocks),
+                                     dim3(kThreads), params, 0, s);
 }
 
 }  // namespace mpmcr

@@ -69,6 +69,18 @@ class StepStats(C.Structure):
         return d
 
 
+MAX_BODIES = 16  # rigid bodies per context
+
+
+class AdjointParams(C.Structure):
+    _fields_ = [("eps_r", C.c_double), ("max_iters", C.c_int32)]
+
+
+class AdjointStats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("residual", C.c_float), ("contacts", C.c_int32),
+                ("contact_nodes", C.c_int32)]
+
+
 _vp = C.c_void_p
 _fp = C.POINTER(C.c_float)
 _dp = C.POINTER(C.c_double)
@@ -93,6 +105,8 @@ SIGNATURES = {
     "mpm_get_grid": [_vp, C.c_int64, _i64p, _i32p, _fp, _fp, _fp],
     "mpm_get_contacts": [_vp, C.c_int64, _i64p, _i32p, _i32p, _fp, _fp, _fp],
     "mpm_get_grid_noalloc": [_vp, C.c_int64, _i64p, _i32p, _fp, _fp, _fp],
+    "mpm_contact_adjoint": [_vp, C.c_int32, C.c_int64, _vp, _vp, _vp, C.c_int64, _vp, _vp,
+                            C.POINTER(AdjointParams), C.POINTER(AdjointStats)],
     "mpm_synchronize": [_vp],
     "mpm_set_option": [_vp, C.c_int32, C.c_int64],
     "mpm_get_phase_times": [_vp, _dp, _i64p, C.c_int32],
@@ -268,6 +282,49 @@ def mpm_get_contacts(ctx):
     return p[:n], b[:n], g[:n], phi[:n], n0[:n]
 
 
+def mpm_contact_adjoint(ctx, node_ids, vbar, n_contacts=None, n_bodies=0, eps_r=1e-5,
+                        max_iters=1000, check=True):
+    """Adjoint of the last substep's contact solve (see include/mpmcr.h).
+
+    node_ids [n] int32 and vbar [n, 3] float32, both numpy (host) or both CUDA
+    tensors (device, outputs then CUDA tensors too). Returns (vstar_bar [n, 3],
+    contact_bar [n_contacts, 4], body_bar [n_bodies, 7] float64, stats, status);
+    n_contacts None reads the contact count first. body_bar rows are the bodies
+    of the last mpm_step."""
+    device = not isinstance(vbar, np.ndarray)
+    if n_contacts is None:
+        count = C.c_int64()
+        _check(ctx, lib.mpm_get_contacts(ctx, 0, C.byref(count), None, None, None, None, None))
+        n_contacts = count.value
+    n = len(node_ids)
+    if device:
+        import torch
+        if node_ids.dtype != torch.int32 or vbar.dtype != torch.float32:
+            raise TypeError("int32 ids and float32 vbar required")
+        ids_t, vb_t = node_ids.contiguous(), vbar.contiguous()
+        vsb = torch.empty((n, 3), dtype=torch.float32, device=vbar.device)
+        cbar = torch.zeros((max(n_contacts, 1), 4), dtype=torch.float32, device=vbar.device)
+        bbar = torch.zeros((MAX_BODIES, 7), dtype=torch.float64, device=vbar.device)
+        ptrs = (ids_t.data_ptr(), vb_t.data_ptr(), vsb.data_ptr(), cbar.data_ptr(), bbar.data_ptr())
+        kind = MEM_DEVICE
+    else:
+        ids_t = np.ascontiguousarray(node_ids, dtype=np.int32)
+        vb_t = np.ascontiguousarray(vbar, dtype=np.float32).reshape(n, 3)
+        vsb = np.zeros((max(n, 1), 3), np.float32)
+        cbar = np.zeros((max(n_contacts, 1), 4), np.float32)
+        bbar = np.zeros((MAX_BODIES, 7), np.float64)
+        ptrs = (ids_t.ctypes.data, vb_t.ctypes.data, vsb.ctypes.data, cbar.ctypes.data,
+                bbar.ctypes.data)
+        kind = MEM_HOST
+    params = AdjointParams(float(eps_r), int(max_iters))
+    st = AdjointStats()
+    code = lib.mpm_contact_adjoint(ctx, kind, n, ptrs[0], ptrs[1], ptrs[2], n_contacts, ptrs[3],
+                                   ptrs[4], C.byref(params), C.byref(st))
+    if check:
+        _check(ctx, code)
+    return vsb[:n], cbar[:n_contacts], bbar[:n_bodies], st, code
+
+
 def mpm_synchronize(ctx):
     return lib.mpm_synchronize(ctx)
 
@@ -419,3 +476,9 @@ class Sim:
 
     def contacts(self):
         return mpm_get_contacts(self.ctx)
+
+    def contact_adjoint(self, node_ids, vbar, eps_r=1e-5, max_iters=1000, check=True):
+        """dL/dv*, per-contact (dL/dv_r, dL/dmu) and per-body gradients of the
+        last substep's contact solve for vbar = dL/dv (mpm_contact_adjoint)."""
+        return mpm_contact_adjoint(self.ctx, node_ids, vbar, n_bodies=self.n_bodies, eps_r=eps_r,
+                                   max_iters=max_iters, check=check)
