@@ -338,6 +338,57 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
                                float* contact_bar, double* body_bar,
                                const mpm_adjoint_params* params, mpm_adjoint_stats* stats);
 
+/* Reverse-mode differentiation of a rollout (mpm_backward). The paper does
+   not differentiate its simulator; this is an extension of the library.
+
+   mpm_tape_begin clears any previous tape and starts recording: every
+   following mpm_step (with n_substeps > 0) stores a checkpoint of the
+   particle state at its start (device memory, 96 bytes per particle) with the
+   step's frozen bodies, h and solver parameters. mpm_tape_end stops
+   recording and keeps the tape. Adding particles while recording is an
+   error at the next mpm_step. */
+mpm_status mpm_tape_begin(mpm_ctx* ctx);
+mpm_status mpm_tape_end(mpm_ctx* ctx);
+
+typedef struct {
+  int32_t steps;          /* recorded steps differentiated */
+  int32_t substeps;       /* substeps differentiated */
+  int32_t last_iters;     /* CG iterations of the last contact adjoint */
+  float last_residual;    /* its relative residual */
+} mpm_backward_stats;
+
+/* Gradient of a loss L of the state after the last recorded step with
+   respect to the state before the first one and to the parameters, by the
+   adjoint of every substep in reverse: G2P with the constitutive update,
+   the contact solve by implicit differentiation of its optimality condition
+   (as in mpm_contact_adjoint, Eq. (8)-(9), plus the dependence of the lagged
+   contact terms phi0, n, n0 and of the contact velocity's bias and stencil
+   on the particle state), the grid update and P2G (with the weights'
+   gradient and the fixed-corotated stress through its polar decomposition).
+   Each recorded step is replayed from its checkpoint once to rebuild its
+   substep states; each substep's grid and contact solve are then recomputed
+   before its adjoint, so memory is one checkpoint per step plus one step's
+   substep states.
+
+   Inputs, in id order and caller layout (x, v [n][3]; C, F [n][3][3]), any
+   may be NULL for zero: dL/dx, dL/dv, dL/dC, dL/dF of the final state.
+   Outputs (NULL to skip): the same four for the state at the start of the
+   first recorded step; material_bar [n_groups][2] doubles = dL/dE, dL/dnu
+   per particle group (in the order the groups were added); mu_bar
+   [n_bodies] doubles = dL/dmu per body index. Rigid bodies are inputs: their
+   recorded poses and velocities are replayed, and only mu is differentiated.
+   The contact solve's adjoint is solved to params->eps_r (NULL: 1e-6, 2000
+   iterations); the implicit gradient is exact at an exact minimiser, so the
+   recorded steps should use a tight solver tolerance.
+   Requires: a tape; the same particles; corotated materials only
+   (MPM_ERR_STATE otherwise) and no dynamic bodies in the recorded steps.
+   Synchronises; afterwards the particle state is the final state again, the
+   impulse accumulators are as before, and the tape is kept. */
+mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, const float* v_bar,
+                        const float* C_bar, const float* F_bar, float* x0_bar, float* v0_bar,
+                        float* C0_bar, float* F0_bar, double* material_bar, double* mu_bar,
+                        const mpm_adjoint_params* params, mpm_backward_stats* stats);
+
 /* Wait for the context's stream and report any device-side failure. */
 mpm_status mpm_synchronize(mpm_ctx* ctx);
 

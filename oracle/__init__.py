@@ -410,6 +410,32 @@ def advance_kinematic(bodies, dt):
     return [body_dict(bs[i]) for i in range(nb)]
 
 
+def rollout(scene, steps, S, materials=None, bodies=None, state=None, substeps=None):
+    """Asynchronous time splitting (Sec. IV-A, Eq. (3)-(4)): `steps` rigid time
+    steps of `substeps` (default scene["substeps"]) MPM substeps each, the
+    rigid bodies frozen within a step and the kinematic ones advanced by
+    substeps*h after it. Oracle state, materials and bodies default to the
+    scene's (from_scene, bodies_from_scene); returns the final FP64 state and
+    the first non-OK substep status (OK if none)."""
+    st0, mats0 = from_scene(scene)
+    st = Sim.state(st0 if state is None else state)
+    mats = mats0 if materials is None else materials
+    bds = bodies_from_scene(scene) if bodies is None else [dict(b) for b in bodies]
+    n_sub = scene["substeps"] if substeps is None else substeps
+    sim = Sim(scene["grid"])
+    code = OK
+    try:
+        for _ in range(steps):
+            for _ in range(n_sub):
+                c, _ = sim.substep(st, mats, bds, scene["h"], S)
+                if code == OK and c != OK:
+                    code = c
+            bds = advance_kinematic(bds, n_sub * scene["h"])
+    finally:
+        sim.close()
+    return st, code
+
+
 def make_dynamics(dyn):
     """dict(mass, inertia[3], force[3], torque[3], dof_mask, gravity) -> Dynamics."""
     d = Dynamics()

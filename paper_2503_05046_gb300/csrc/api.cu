@@ -81,6 +81,29 @@ struct mpm_ctx {
   int32_t* adj_ids = nullptr;      // staging of host inputs and outputs
   float* adj_io = nullptr;         // vbar (3n), vstar_bar (3n), contact_bar (4 cap)
   size_t adj_ids_cap = 0, adj_io_cap = 0;
+  // materials as given, per particle group (for dL/dE, dL/dnu)
+  std::vector<mpm_material> mats;
+  // mpm_backward tape: per recorded mpm_step, the particle state at its start
+  // (id order, x v C F = 24 floats per particle, one device buffer each), its
+  // frozen bodies, substep size and count, and solver parameters
+  struct TapeStep {
+    float* state = nullptr;
+    std::vector<DevBody> bodies;
+    int n_substeps = 0;
+    float h = 0.f;
+    mpm_solver_params sp{};
+    bool dynamic = false;
+  };
+  bool taping = false;
+  int64_t tape_n = 0;
+  std::vector<TapeStep> tape;
+  // mpm_backward scratch, grown on demand
+  float* bw_buf = nullptr;  // bar[2], final state, substep states: 24 floats per particle each
+  size_t bw_buf_cap = 0;
+  float4* bw_gbar = nullptr;
+  int* bw_slot = nullptr;
+  double* bw_mat = nullptr;
+  size_t bw_mat_cap = 0;
   std::string err;
 };
 
@@ -305,7 +328,9 @@ void release(mpm_ctx* c) {
                   c->C.bias, c->C.id, c->C.vc, c->C.dvc, c->C.gamma, c->C.count, c->red, c->bar, c->poison,
                   c->status, c->stats, c->impulses, c->sb.keys[0], c->sb.keys[1], c->sb.vals[0],
                   c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage, c->adj_vec, c->adj_body,
-                  c->adj_out, c->adj_ids, c->adj_io};
+                  c->adj_out, c->adj_ids, c->adj_io, c->bw_buf, c->bw_gbar, c->bw_slot, c->bw_mat};
+  for (auto& t : c->tape)
+    if (t.state) cudaFree(t.state);
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : c->gexec)
@@ -313,6 +338,40 @@ void release(mpm_ctx* c) {
   for (auto& e : c->ev_marks) cudaEventDestroy(e.second);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+// One substep on particle buffer `cur`: P2G, grid update, contact solve and
+// (with_g2p) G2P.
+cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_solver_params& sp,
+                            int solve_blocks, bool with_g2p, cudaStream_t s) {
+  const int n = (int)ctx->n;
+  P2GArgs pa;
+  pa.g = ctx->g; pa.P = ctx->P[cur]; pa.n = n; pa.groups = ctx->groups_d;
+  pa.bodies = ctx->bodies_d; pa.nb = nb; pa.h = hf; pa.G = ctx->G; pa.C = ctx->C;
+  pa.status = ctx->status; pa.stats = ctx->stats;
+  mark_phase(ctx, MPM_PHASE_P2G);
+  launch_p2g(pa, ctx->p2g_chunk, s);
+  mark_phase(ctx, MPM_PHASE_GRID);
+  launch_grid(ctx->g, ctx->G, hf, ctx->num_sms, ctx->stats, s);
+  SolveArgs sa;
+  sa.g = ctx->g; sa.G = ctx->G; sa.C = ctx->C; sa.bodies = ctx->bodies_d; sa.nb = nb;
+  sa.h = hf; sa.eps_s = sp.eps_s; sa.ls_rel_tol = sp.ls_rel_tol; sa.ls_max_iters = sp.ls_max_iters;
+  sa.eps_r = sp.eps_r; sa.eps_a = sp.eps_a; sa.max_iters = sp.max_iters; sa.red = ctx->red;
+  sa.bar = ctx->bar; sa.status = ctx->status; sa.stats = ctx->stats; sa.impulses = ctx->impulses;
+  sa.wait_extra = ctx->wait_test ? 1 : 0;
+  sa.poison = ctx->poison;
+  mark_phase(ctx, MPM_PHASE_SOLVE);
+  const cudaError_t e = launch_solve(sa, solve_blocks, s);
+  if (e != cudaSuccess) return e;
+  if (with_g2p) {
+    G2PArgs ga;
+    ga.g = ctx->g; ga.P = ctx->P[cur]; ga.n = n; ga.groups = ctx->groups_d; ga.G = ctx->G;
+    ga.C = ctx->C; ga.h = hf; ga.bar = ctx->bar; ga.red = ctx->red; ga.stats = ctx->stats;
+    mark_phase(ctx, MPM_PHASE_G2P);
+    launch_g2p(ga, s);
+  }
+  mark_phase(ctx, -1);
+  return cudaGetLastError();
 }
 
 // The launches of one step: the radix sort from particle buffer `from` into
@@ -328,30 +387,8 @@ cudaError_t enqueue_step(mpm_ctx* ctx, int from, bool sort_now, int n_substeps, 
     cur = 1 - cur;
   }
   for (int k = 0; k < n_substeps; ++k) {
-    P2GArgs pa;
-    pa.g = ctx->g; pa.P = ctx->P[cur]; pa.n = n; pa.groups = ctx->groups_d;
-    pa.bodies = ctx->bodies_d; pa.nb = nb; pa.h = hf; pa.G = ctx->G; pa.C = ctx->C;
-    pa.status = ctx->status; pa.stats = ctx->stats;
-    mark_phase(ctx, MPM_PHASE_P2G);
-    launch_p2g(pa, ctx->p2g_chunk, s);
-    mark_phase(ctx, MPM_PHASE_GRID);
-    launch_grid(ctx->g, ctx->G, hf, ctx->num_sms, ctx->stats, s);
-    SolveArgs sa;
-    sa.g = ctx->g; sa.G = ctx->G; sa.C = ctx->C; sa.bodies = ctx->bodies_d; sa.nb = nb;
-    sa.h = hf; sa.eps_s = sp.eps_s; sa.ls_rel_tol = sp.ls_rel_tol; sa.ls_max_iters = sp.ls_max_iters;
-    sa.eps_r = sp.eps_r; sa.eps_a = sp.eps_a; sa.max_iters = sp.max_iters; sa.red = ctx->red;
-    sa.bar = ctx->bar; sa.status = ctx->status; sa.stats = ctx->stats; sa.impulses = ctx->impulses;
-    sa.wait_extra = ctx->wait_test ? 1 : 0;
-    sa.poison = ctx->poison;
-    mark_phase(ctx, MPM_PHASE_SOLVE);
-    const cudaError_t e = launch_solve(sa, solve_blocks, s);
+    const cudaError_t e = enqueue_substep(ctx, cur, nb, hf, sp, solve_blocks, true, s);
     if (e != cudaSuccess) return e;
-    G2PArgs ga;
-    ga.g = ctx->g; ga.P = ctx->P[cur]; ga.n = n; ga.groups = ctx->groups_d; ga.G = ctx->G;
-    ga.C = ctx->C; ga.h = hf; ga.bar = ctx->bar; ga.red = ctx->red; ga.stats = ctx->stats;
-    mark_phase(ctx, MPM_PHASE_G2P);
-    launch_g2p(ga, s);
-    mark_phase(ctx, -1);
   }
   return cudaGetLastError();
 }
@@ -528,6 +565,7 @@ mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const floa
   gr.dp_alpha = (float)(std::sqrt(2.0 / 3.0) * 2.0 * sphi / (3.0 - sphi));
   gr.model = mat->model;
   ctx->groups.push_back(gr);
+  ctx->mats.push_back(*mat);
   if ((int)ctx->groups.size() > ctx->groups_cap) {
     int nc = ctx->groups_cap ? 2 * ctx->groups_cap : 64;
     while (nc < (int)ctx->groups.size()) nc *= 2;
@@ -704,6 +742,21 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
       CU(cudaStreamSynchronize(s));
     }
     ctx->imp_seen_valid = true;
+  }
+  if (ctx->taping && n_substeps > 0) {
+    if (ctx->n != ctx->tape_n)
+      return fail(ctx, MPM_ERR_STATE, "mpm_step: particles were added while a tape is recorded");
+    mpm_ctx::TapeStep t;
+    CU(dalloc(&t.state, (size_t)24 * ctx->n));
+    const size_t nn = (size_t)ctx->n;
+    launch_to_id_order(ctx->P[ctx->cur], (int)nn, t.state, t.state + 3 * nn, t.state + 6 * nn,
+                       t.state + 15 * nn, s);
+    for (int i = 0; i < nb; ++i) t.bodies.push_back(to_dev(ctx->bodies[i]));
+    t.n_substeps = n_substeps;
+    t.h = (float)h;
+    t.sp = sp;
+    for (int d : ctx->is_dyn) t.dynamic = t.dynamic || d;
+    ctx->tape.push_back(std::move(t));
   }
   CU(cudaMemsetAsync(ctx->stats, 0, sizeof(DevStats), s));
   const int n = (int)ctx->n;
@@ -1003,6 +1056,215 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
     stats->residual = out[1];
     stats->contacts = (int32_t)out[2];
     stats->contact_nodes = (int32_t)out[3];
+  }
+  return st;
+}
+
+mpm_status mpm_tape_begin(mpm_ctx* ctx) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  CU(cudaStreamSynchronize(ctx->stream));
+  for (auto& t : ctx->tape)
+    if (t.state) cudaFree(t.state);
+  ctx->tape.clear();
+  ctx->taping = true;
+  ctx->tape_n = ctx->n;
+  return MPM_OK;
+}
+
+mpm_status mpm_tape_end(mpm_ctx* ctx) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  ctx->taping = false;
+  return MPM_OK;
+}
+
+namespace {
+
+// state buffer (24 floats per particle, id order) -> particle buffer `cur`
+void restore_state(mpm_ctx* ctx, const float* st, cudaStream_t s) {
+  const size_t n = (size_t)ctx->n;
+  launch_from_id_order(ctx->P[ctx->cur], (int)n, st, st + 3 * n, st + 6 * n, st + 15 * n, s);
+  launch_stress_from_F(ctx->P[ctx->cur], (int)n, ctx->groups_d, s);
+}
+
+void save_state(mpm_ctx* ctx, float* st, cudaStream_t s) {
+  const size_t n = (size_t)ctx->n;
+  launch_to_id_order(ctx->P[ctx->cur], (int)n, st, st + 3 * n, st + 6 * n, st + 15 * n, s);
+}
+
+mpm_status ensure_adjoint_buffers(mpm_ctx* ctx) {
+  if (ctx->adj_vec) return MPM_OK;
+  CU(dalloc(&ctx->adj_vec, (size_t)kAdjointVectors * ctx->G.cnodes_cap));
+  CU(dalloc(&ctx->adj_body, 7 * kMaxBodies));
+  CU(dalloc(&ctx->adj_out, 4));
+  int occ = 0;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel_ptr(), solve_block_size(), 0));
+  if (occ < 1) return fail(ctx, MPM_ERR_CUDA, "adjoint kernel does not fit an SM");
+  ctx->adj_blocks = ctx->num_sms * (occ < 2 ? occ : 2);
+  return MPM_OK;
+}
+
+}  // namespace
+
+mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, const float* v_bar,
+                        const float* C_bar, const float* F_bar, float* x0_bar, float* v0_bar,
+                        float* C0_bar, float* F0_bar, double* material_bar, double* mu_bar,
+                        const mpm_adjoint_params* params, mpm_backward_stats* stats) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (mem_kind != MPM_MEM_HOST && mem_kind != MPM_MEM_DEVICE)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_backward: bad mem_kind");
+  mpm_adjoint_params ap;
+  ap.eps_r = 1e-6;
+  ap.max_iters = 2000;
+  if (params) ap = *params;
+  if (!(ap.eps_r >= 0.0) || ap.max_iters < 0)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_backward: bad parameters");
+  if (ctx->tape.empty()) return fail(ctx, MPM_ERR_STATE, "mpm_backward: no recorded steps (mpm_tape_begin)");
+  if (ctx->n != ctx->tape_n)
+    return fail(ctx, MPM_ERR_STATE, "mpm_backward: the particle count changed since the tape began");
+  for (const auto& gr : ctx->groups)
+    if (gr.model != MPM_COROTATED)
+      return fail(ctx, MPM_ERR_STATE, "mpm_backward: the adjoint covers corotated materials only");
+  for (const auto& t : ctx->tape)
+    if (t.dynamic) return fail(ctx, MPM_ERR_STATE, "mpm_backward: a recorded step had dynamic bodies");
+  mpm_status st = drain_status(ctx);
+  if (st != MPM_OK) return st;
+  st = ensure_adjoint_buffers(ctx);
+  if (st != MPM_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const size_t n = (size_t)ctx->n;
+  int max_sub = 1;
+  for (const auto& t : ctx->tape) max_sub = t.n_substeps > max_sub ? t.n_substeps : max_sub;
+  // scratch: two adjoint plane sets, the final state, the substep states
+  const size_t per = 24 * n;
+  const size_t need = per * (3 + (size_t)max_sub);
+  if (ctx->bw_buf_cap < need) {
+    if (ctx->bw_buf) cudaFree(ctx->bw_buf);
+    ctx->bw_buf = nullptr;
+    ctx->bw_buf_cap = 0;
+    CU(dalloc(&ctx->bw_buf, need));
+    ctx->bw_buf_cap = need;
+  }
+  if (!ctx->bw_gbar) CU(dalloc(&ctx->bw_gbar, ctx->n_nodes));
+  if (!ctx->bw_slot) CU(dalloc(&ctx->bw_slot, ctx->cap));
+  const size_t ng = ctx->groups.size();
+  if (ctx->bw_mat_cap < 2 * ng + 2) {
+    if (ctx->bw_mat) cudaFree(ctx->bw_mat);
+    ctx->bw_mat = nullptr;
+    ctx->bw_mat_cap = 0;
+    CU(dalloc(&ctx->bw_mat, 2 * ng + 2));
+    ctx->bw_mat_cap = 2 * ng + 2;
+  }
+  float* bar[2] = {ctx->bw_buf, ctx->bw_buf + per};
+  float* final_state = ctx->bw_buf + 2 * per;
+  float* sub_states = ctx->bw_buf + 3 * per;
+  const Particles P = ctx->P[ctx->cur];
+  // the replayed solves add to the impulse accumulators: keep the caller's
+  std::vector<double> imp_saved(6 * kMaxBodies);
+  CU(cudaMemcpyAsync(imp_saved.data(), ctx->impulses, 6 * kMaxBodies * sizeof(double),
+                     cudaMemcpyDeviceToHost, s));
+  // the adjoint of the final state, into planes in the current slot order
+  save_state(ctx, final_state, s);
+  launch_slot_map(P, (int)n, ctx->bw_slot, s);
+  const float* src[4] = {x_bar, v_bar, C_bar, F_bar};
+  const float* dsrc[4] = {x_bar, v_bar, C_bar, F_bar};
+  const int width[4] = {3, 3, 9, 9};
+  if (mem_kind == MPM_MEM_HOST) {
+    size_t off = 0;
+    for (int f = 0; f < 4; ++f) {
+      dsrc[f] = nullptr;
+      if (!src[f]) { off += n * width[f]; continue; }
+      CU(cudaMemcpyAsync(ctx->stage + off, src[f], n * width[f] * sizeof(float), cudaMemcpyHostToDevice, s));
+      dsrc[f] = ctx->stage + off;
+      off += n * width[f];
+    }
+  }
+  launch_bar_in(P, (int)n, dsrc[0], dsrc[1], dsrc[2], dsrc[3], bar[0], s);
+  CU(cudaMemsetAsync(ctx->bw_mat, 0, (2 * ng + 2) * sizeof(double), s));
+  CU(cudaMemsetAsync(ctx->adj_body, 0, 7 * kMaxBodies * sizeof(double), s));
+  int in = 0;
+  int substeps = 0;
+  int nb_max = 0;
+  for (int t = (int)ctx->tape.size() - 1; t >= 0; --t) {
+    const mpm_ctx::TapeStep& T = ctx->tape[t];
+    const int nb = (int)T.bodies.size();
+    nb_max = nb > nb_max ? nb : nb_max;
+    if (nb) CU(cudaMemcpyAsync(ctx->bodies_d, T.bodies.data(), nb * sizeof(DevBody), cudaMemcpyHostToDevice, s));
+    // replay the step from its checkpoint, keeping each substep's start state
+    restore_state(ctx, T.state, s);
+    for (int k = 0; k < T.n_substeps; ++k) {
+      save_state(ctx, sub_states + (size_t)k * per, s);
+      if (k + 1 < T.n_substeps)
+        CU(enqueue_substep(ctx, ctx->cur, nb, T.h, T.sp, ctx->solve_blocks, true, s));
+    }
+    for (int k = T.n_substeps - 1; k >= 0; --k) {
+      restore_state(ctx, sub_states + (size_t)k * per, s);
+      CU(enqueue_substep(ctx, ctx->cur, nb, T.h, T.sp, ctx->solve_blocks, false, s));
+      CU(cudaMemsetAsync(ctx->bw_gbar, 0, ctx->n_nodes * sizeof(float4), s));
+      BackwardArgs ba;
+      ba.g = ctx->g; ba.P = P; ba.n = (int)n; ba.groups = ctx->groups_d; ba.G = ctx->G;
+      ba.h = T.h; ba.gbar = ctx->bw_gbar; ba.bin = bar[in]; ba.bout = bar[1 - in];
+      ba.mat_bar = ctx->bw_mat; ba.status = ctx->status;
+      launch_g2p_adjoint(ba, s);
+      // contact solve (implicit differentiation) with the contact geometry
+      AdjointArgs a;
+      memset(&a, 0, sizeof(a));
+      a.g = ctx->g; a.G = ctx->G; a.C = ctx->C; a.bodies = ctx->bodies_d; a.nb = nb;
+      a.h = T.h; a.eps_s = T.sp.eps_s; a.eps_r = ap.eps_r; a.max_iters = ap.max_iters;
+      a.n_in = 0; a.body_bar = ctx->adj_body; a.vec = ctx->adj_vec; a.red = ctx->red;
+      a.bar = ctx->bar; a.status = ctx->status; a.poison = ctx->poison; a.stats = ctx->stats;
+      a.out = ctx->adj_out; a.gbar = ctx->bw_gbar; a.pbar = bar[1 - in]; a.slot_of = ctx->bw_slot;
+      a.P = P; a.n_particles = (int)n;
+      CU(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned), s));
+      CU(cudaMemsetAsync(ctx->G.n_cnodes, 0, sizeof(int), s));
+      CU(launch_adjoint(a, ctx->adj_blocks, s));
+      launch_grid_adjoint(ba, ctx->num_sms, s);
+      launch_p2g_adjoint(ba, s);
+      launch_reset_counters(ctx->G, ctx->C, ctx->bar, s);
+      CU(cudaGetLastError());
+      in = 1 - in;
+      ++substeps;
+    }
+  }
+  // outputs: the adjoint of the first recorded state, in id order
+  float* dst[4] = {x0_bar, v0_bar, C0_bar, F0_bar};
+  float* ddst[4] = {x0_bar, v0_bar, C0_bar, F0_bar};
+  if (mem_kind == MPM_MEM_HOST) {
+    size_t off = 0;
+    for (int f = 0; f < 4; ++f) {
+      ddst[f] = dst[f] ? ctx->stage + off : nullptr;
+      off += n * width[f];
+    }
+  }
+  launch_bar_out(P, (int)n, bar[in], ddst[0], ddst[1], ddst[2], ddst[3], s);
+  if (mem_kind == MPM_MEM_HOST)
+    for (int f = 0; f < 4; ++f)
+      if (dst[f]) CU(cudaMemcpyAsync(dst[f], ddst[f], n * width[f] * sizeof(float), cudaMemcpyDeviceToHost, s));
+  std::vector<double> lame(2 * ng + 2), body(7 * kMaxBodies);
+  CU(cudaMemcpyAsync(lame.data(), ctx->bw_mat, (2 * ng + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(body.data(), ctx->adj_body, 7 * kMaxBodies * sizeof(double), cudaMemcpyDeviceToHost, s));
+  float out[4];
+  CU(cudaMemcpyAsync(out, ctx->adj_out, sizeof(out), cudaMemcpyDeviceToHost, s));
+  // put the state back as it was after the last step; the bodies upload again
+  restore_state(ctx, final_state, s);
+  ctx->bodies_dirty = true;
+  st = drain_status(ctx);
+  CU(cudaMemcpy(ctx->impulses, imp_saved.data(), 6 * kMaxBodies * sizeof(double), cudaMemcpyHostToDevice));
+  if (material_bar)
+    for (size_t gi = 0; gi < ng; ++gi) {
+      // mu = E / (2 (1 + nu)), lam = E nu / ((1 + nu)(1 - 2 nu))
+      const double E = ctx->mats[gi].E, nu = ctx->mats[gi].nu;
+      const double mub = lame[2 * gi], lamb = lame[2 * gi + 1];
+      const double a = 1.0 + nu, b = 1.0 - 2.0 * nu;
+      material_bar[2 * gi] = mub / (2.0 * a) + lamb * nu / (a * b);
+      material_bar[2 * gi + 1] = -mub * E / (2.0 * a * a) + lamb * E * (1.0 + 2.0 * nu * nu) / (a * a * b * b);
+    }
+  if (mu_bar)
+    for (int b = 0; b < nb_max; ++b) mu_bar[b] = body[7 * b + 6];
+  if (stats) {
+    stats->steps = (int32_t)ctx->tape.size();
+    stats->substeps = substeps;
+    stats->last_iters = (int32_t)out[0];
+    stats->last_residual = out[1];
   }
   return st;
 }

@@ -125,10 +125,43 @@ struct AdjointArgs {
   int* poison;
   const DevStats* stats;  // last_contacts: the differentiated substep's contact count
   float* out;         // [4]: iterations, relative residual, contacts, contact nodes
+  // mpm_backward mode (gbar non-null): vbar comes from the dense grid adjoint
+  // gbar and (v*bar, mbar) go back into it on the contact nodes; the contact
+  // geometry's adjoint is added to the particle adjoint planes `pbar` (slot
+  // order, via slot_of[particle id]); the contact count is the live one
+  float4* gbar;
+  float* pbar;
+  const int* slot_of;
+  Particles P;
+  int n_particles;
 };
 constexpr int kAdjointVectors = 13;
 cudaError_t launch_adjoint(const AdjointArgs& a, int grid_blocks, cudaStream_t s);
 const void* adjoint_kernel_ptr();
+
+// ---- backward.cu: adjoints of G2P, the grid update and P2G (mpm_backward)
+struct BackwardArgs {
+  GridDev g;
+  Particles P;        // the substep's start state (slot order)
+  int n;
+  const DevGroup* groups;
+  GridArrays G;       // the substep's grid after P2G, grid update and solve
+  float h;
+  float4* gbar;       // dense grid adjoint
+  const float* bin;   // adjoint of the substep's end state: 24 planes x n (slot order)
+  float* bout;        // adjoint of its start state
+  double* mat_bar;    // per group: dL/dmu_lame, dL/dlambda_lame
+  uint32_t* status;
+};
+void launch_g2p_adjoint(const BackwardArgs& a, cudaStream_t s);
+void launch_grid_adjoint(const BackwardArgs& a, int num_sms, cudaStream_t s);
+void launch_p2g_adjoint(const BackwardArgs& a, cudaStream_t s);
+void launch_reset_counters(const GridArrays& G, const Contacts& C, unsigned* bar, cudaStream_t s);
+void launch_slot_map(const Particles& P, int n, int* slot_of, cudaStream_t s);
+void launch_bar_in(const Particles& P, int n, const float* x, const float* v, const float* C,
+                   const float* F, float* bar, cudaStream_t s);
+void launch_bar_out(const Particles& P, int n, const float* bar, float* x, float* v, float* C,
+                    float* F, cudaStream_t s);
 
 // ---- g2p.cu: grid-to-particle with the constitutive update ----
 struct G2PArgs {

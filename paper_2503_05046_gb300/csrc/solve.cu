@@ -789,7 +789,8 @@ static_assert(kAdjVectors == kAdjointVectors, "adjoint vector count");
 // components, which stay accurate to the (much smaller) friction scale.
 struct AdjHess {
   float n[3], ut[3];
-  float d2N, cs, inv_s2;
+  float dN, d2N, cs, inv_s2;
+  float n0;
   float n0_s;  // n0 / s, for dL/dmu
 };
 
@@ -811,10 +812,107 @@ __device__ __forceinline__ void adjoint_contact(const Contacts& C, int p, const 
   const float tn = L.ut[0] * A.n[0] + L.ut[1] * A.n[1] + L.ut[2] * A.n[2];
 #pragma unroll
   for (int r = 0; r < 3; ++r) A.ut[r] = L.ut[r] - tn * A.n[r];
+  A.dN = L.dN;
   A.d2N = L.d2N;
   A.cs = L.cs;
   A.inv_s2 = L.inv_s2;
+  A.n0 = n0;
   A.n0_s = n0 * sqrtf(L.inv_s2);
+}
+
+// Gradient of w_ip (physical units) at the lane's stencil node (lane_node's
+// node order; zero for lanes >= 27).
+__device__ __forceinline__ void lane_weight_grad(const GridDev& g, const float4& xp, int lane,
+                                                 float (&gw)[3]) {
+  Stencil s;
+  stencil(g, xp.x, xp.y, xp.z, s);
+  const int l = lane < 27 ? lane : 0;
+  const int c[3] = {l % 3, (l / 3) % 3, l / 9};
+  float dw[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float f = s.fx[a];
+    dw[a] = (c[a] == 0 ? -(1.5f - f) : c[a] == 1 ? -2.0f * (f - 1.0f) : (f - 0.5f)) * g.inv_dx;
+  }
+  const float w0 = s.w[0][c[0]], w1 = s.w[1][c[1]], w2 = s.w[2][c[2]];
+  const float on = lane < 27 ? 1.0f : 0.0f;
+  gw[0] = on * dw[0] * w1 * w2;
+  gw[1] = on * w0 * dw[1] * w2;
+  gw[2] = on * w0 * w1 * dw[2];
+}
+
+// Adjoint of the contact's inputs to the solve, given xi = J lambda and
+// y = d2l_c xi (FP64). With theta_bar = -(d grad l_c / d theta)^T xi
+// (implicit differentiation of Eq. (9)) for the lagged depth phi0, the lagged
+// normal impulse n0, the normal n and the bias b = -v_r(x_p) of Sec. IV-B,
+// V-B, and their dependence on the particle's start-of-substep position and
+// velocity (phi0 = -sdf(x_p), n = grad sdf(x_p), n0 = gamma_n(phi0, n.(v_p -
+// v_r(x_p))), v_r(x) = v + omega x (x - p)): the adjoint of x_p (without the
+// stencil-weight term) and of v_p.
+__device__ void contact_input_adjoint(const AdjHess& A, const DevBody& bd, const float4& xp,
+                                      const float4& vc, const float4& bias, const float (&vp)[3],
+                                      float h, const double (&xi)[3], const double (&y)[3],
+                                      float (&xb)[3], float (&vb)[3]) {
+  const double n[3] = {A.n[0], A.n[1], A.n[2]}, t[3] = {A.ut[0], A.ut[1], A.ut[2]};
+  const double u[3] = {vc.x, vc.y, vc.z};
+  const double un = n[0] * u[0] + n[1] * u[1] + n[2] * u[2];
+  const double nxi = n[0] * xi[0] + n[1] * xi[1] + n[2] * xi[2];
+  const double txi = t[0] * xi[0] + t[1] * xi[1] + t[2] * xi[2];
+  const double hk = (double)h * (double)bd.k, d = bd.d;
+  const double cs = A.cs, inv_s2 = A.inv_s2, inv_s = sqrt(inv_s2);
+  const double bbar[3] = {-y[0], -y[1], -y[2]};
+  const double n0bar = -(double)bd.mu * inv_s * txi;
+  // the normal law is active where N' < 0 (v_n below its cutoff)
+  double phi0bar = A.dN < 0.f ? hk * (1.0 - d * un) * nxi : 0.0;
+  double nbar[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    nbar[r] = -((double)A.d2N * nxi * u[r] + (double)A.dN * xi[r] + cs * un * txi * inv_s2 * t[r] -
+                cs * nxi * u[r] - cs * un * xi[r]);
+  // lagged normal impulse n0 = h k (phi0 - h vn0) (1 - d vn0), vn0 = n . (v_p - v_r)
+  const double rel[3] = {(double)vp[0] + bias.x, (double)vp[1] + bias.y, (double)vp[2] + bias.z};
+  const double vn0 = n[0] * rel[0] + n[1] * rel[1] + n[2] * rel[2];
+  const double a0 = (double)xp.w - h * vn0, c0 = 1.0 - d * vn0;
+  double vn0bar = 0.0;
+  if (a0 > 0.0 && c0 > 0.0) {
+    phi0bar += n0bar * hk * c0;
+    vn0bar = n0bar * hk * (-(double)h * c0 - d * a0);
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    vb[r] = (float)(vn0bar * n[r]);
+    nbar[r] += vn0bar * rel[r];
+  }
+  const double w[3] = {bd.w[0], bd.w[1], bd.w[2]};
+  const double wxb[3] = {w[1] * bbar[2] - w[2] * bbar[1], w[2] * bbar[0] - w[0] * bbar[2],
+                         w[0] * bbar[1] - w[1] * bbar[0]};
+  const double wxn[3] = {w[1] * n[2] - w[2] * n[1], w[2] * n[0] - w[0] * n[2], w[0] * n[1] - w[1] * n[0]};
+  // (d n / d x)^T nbar: sphere (I - n n^T) / dist, capsule side (I - n n^T - a a^T) / dist
+  double dn[3] = {0.0, 0.0, 0.0};
+  if (bd.shape == MPM_SPHERE || bd.shape == MPM_CAPSULE) {
+    const double r[3] = {(double)xp.x - bd.p[0], (double)xp.y - bd.p[1], (double)xp.z - bd.p[2]};
+    double o[3] = {r[0], r[1], r[2]};
+    double ax[3] = {0.0, 0.0, 0.0};
+    if (bd.shape == MPM_CAPSULE) {
+      ax[0] = bd.R[2]; ax[1] = bd.R[5]; ax[2] = bd.R[8];
+      const double z = ax[0] * r[0] + ax[1] * r[1] + ax[2] * r[2];
+      const double L = bd.prm[0];
+      const double cz = z < -L ? -L : (z > L ? L : z);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) o[c] = r[c] - cz * ax[c];
+      if (!(z > -L && z < L)) ax[0] = ax[1] = ax[2] = 0.0;  // a cap: sphere-like
+    }
+    const double dist = sqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]);
+    if (dist > 0.0) {
+      const double nn = n[0] * nbar[0] + n[1] * nbar[1] + n[2] * nbar[2];
+      const double an = ax[0] * nbar[0] + ax[1] * nbar[1] + ax[2] * nbar[2];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dn[c] = (nbar[c] - nn * n[c] - an * ax[c]) / dist;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    xb[c] = (float)(-phi0bar * n[c] + wxb[c] + vn0bar * wxn[c] + dn[c]);
 }
 
 // y = d2l_c u (FP32)
@@ -879,8 +977,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
   __shared__ float2 s_tot[kRedWidth];
   __shared__ float s_bb[kMaxBodies][7];
   const int tid = threadIdx.x;
-  // the last substep's contact count (G2P has reset the live counter)
-  const int count = a.stats->last_contacts;
+  // the last substep's contact count (G2P has reset the live counter), or
+  // in mpm_backward mode the live count of the substep just solved
+  const int count = a.gbar ? *a.C.count : a.stats->last_contacts;
   const int nc = count < a.C.cap ? count : a.C.cap;
   int nblk = (nc + kContactsPerBlock - 1) / kContactsPerBlock;
   nblk = nblk < (int)gridDim.x ? nblk : (int)gridDim.x;
@@ -961,7 +1060,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
           if (slot < a.G.cnodes_cap) {
             a.G.cnodes[slot] = node[c];
             a.G.cflag[node[c]] = slot + 1;
-            vRhs[slot] = zero4;
+            if (a.gbar) {
+              const float4 gb = a.gbar[node[c]];
+              vRhs[slot] = make_float4(gb.x, gb.y, gb.z, 0.f);
+            } else {
+              vRhs[slot] = zero4;
+            }
             vL0[slot] = zero4;
             vL1[slot] = zero4;
             vAcc[slot] = zero4;
@@ -1234,8 +1338,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
     float4 xp;
     adjoint_contact(a.C, p, s_body, a.h, a.eps_s, A, body, xp);
     const LaneNode ln = lane_node(g, xp, lane);
+    const int ci = list_pos(ln);
     double u[3], yd[3];
-    hessian_lambda_f64(A, ln, list_pos(ln), u, yd);
+    hessian_lambda_f64(A, ln, ci, u, yd);
+    float xw[3] = {0.f, 0.f, 0.f};
+    if (a.gbar) {
+      // stencil-weight term of x_p: -sum_i (lambda_i . g_c + v_i . y) grad w_ip
+      float gw[3];
+      lane_weight_grad(g, xp, lane, gw);
+      double lam[3];
+      lambda_at(vXh, vXl, ci, lam);
+      const float4 vi = lane < 27 ? __ldg(a.G.v + ln.node) : zero4;
+      double gc[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) gc[r] = (double)A.dN * A.n[r] + (double)A.cs * A.ut[r];
+      const float term = (float)(lam[0] * gc[0] + lam[1] * gc[1] + lam[2] * gc[2] +
+                                 (double)vi.x * yd[0] + (double)vi.y * yd[1] + (double)vi.z * yd[2]);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) xw[r] = warp_sum(-term * gw[r]);
+    }
+    if (lane == 0 && a.gbar) {
+      const int slot = a.slot_of[a.C.id[p].x];
+      const float vp[3] = {a.P.v(0)[slot], a.P.v(1)[slot], a.P.v(2)[slot]};
+      float xb[3], vb[3];
+      contact_input_adjoint(A, s_body[body], xp, a.C.vc[p], a.C.bias[p], vp, a.h, u, yd, xb, vb);
+      const size_t np = (size_t)a.n_particles;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        atomicAdd(a.pbar + r * np + slot, xb[r] + xw[r]);
+        atomicAdd(a.pbar + (3 + r) * np + slot, vb[r]);
+      }
+    }
     if (lane == 0) {
       const float y[3] = {(float)yd[0], (float)yd[1], (float)yd[2]};
       const float mub = (float)(-(double)A.n0_s * ((double)A.ut[0] * u[0] + (double)A.ut[1] * u[1] +
@@ -1271,14 +1404,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
     if (L1.z != 0.f) {
       const float4 h = vXh[t], l = vXl[t];
       const double m = (double)L1.w;
-      o = make_float4((float)(m * ((double)h.x + (double)l.x)), (float)(m * ((double)h.y + (double)l.y)),
-                      (float)(m * ((double)h.z + (double)l.z)), 0.f);
+      const double lam[3] = {(double)h.x + (double)l.x, (double)h.y + (double)l.y,
+                             (double)h.z + (double)l.z};
+      o = make_float4((float)(m * lam[0]), (float)(m * lam[1]), (float)(m * lam[2]), 0.f);
+      if (a.gbar) {
+        // the mass in M (v - v*) of Eq. (9): mbar = -lambda . (v - v*)
+        const int node = a.G.cnodes[t];
+        const float4 v = a.G.v[node], vs = a.G.vs[node];
+        o.w = (float)(-(lam[0] * (double)(v.x - vs.x) + lam[1] * (double)(v.y - vs.y) +
+                        lam[2] * (double)(v.z - vs.z)));
+      }
     } else {
       const float4 b = vRhs[t];
       o = make_float4((float)((double)b.x - y[0]), (float)((double)b.y - y[1]),
                       (float)((double)b.z - y[2]), 0.f);
     }
     vQ[t] = o;
+    if (a.gbar) a.gbar[a.G.cnodes[t]] = o;
   }
   if (!grid_sync(B)) return;
   for (int i = gtid; i < a.n_in; i += gstride) {

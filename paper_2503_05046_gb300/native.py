@@ -81,6 +81,11 @@ class AdjointStats(C.Structure):
                 ("contact_nodes", C.c_int32)]
 
 
+class BackwardStats(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("substeps", C.c_int32), ("last_iters", C.c_int32),
+                ("last_residual", C.c_float)]
+
+
 _vp = C.c_void_p
 _fp = C.POINTER(C.c_float)
 _dp = C.POINTER(C.c_double)
@@ -107,6 +112,10 @@ SIGNATURES = {
     "mpm_get_grid_noalloc": [_vp, C.c_int64, _i64p, _i32p, _fp, _fp, _fp],
     "mpm_contact_adjoint": [_vp, C.c_int32, C.c_int64, _vp, _vp, _vp, C.c_int64, _vp, _vp,
                             C.POINTER(AdjointParams), C.POINTER(AdjointStats)],
+    "mpm_tape_begin": [_vp],
+    "mpm_tape_end": [_vp],
+    "mpm_backward": [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                     C.POINTER(AdjointParams), C.POINTER(BackwardStats)],
     "mpm_synchronize": [_vp],
     "mpm_set_option": [_vp, C.c_int32, C.c_int64],
     "mpm_get_phase_times": [_vp, _dp, _i64p, C.c_int32],
@@ -325,6 +334,52 @@ def mpm_contact_adjoint(ctx, node_ids, vbar, n_contacts=None, n_bodies=0, eps_r=
     return vsb[:n], cbar[:n_contacts], bbar[:n_bodies], st, code
 
 
+def mpm_tape_begin(ctx):
+    _check(ctx, lib.mpm_tape_begin(ctx))
+
+
+def mpm_tape_end(ctx):
+    _check(ctx, lib.mpm_tape_end(ctx))
+
+
+def mpm_backward(ctx, n, n_groups, n_bodies, x_bar=None, v_bar=None, C_bar=None, F_bar=None,
+                 eps_r=1e-6, max_iters=2000, check=True):
+    """Reverse pass over the recorded steps (see include/mpmcr.h).
+
+    The four cotangents are numpy arrays (host) or CUDA tensors (device, all
+    alike; None for zero). Returns dict(x, v, C, F: adjoints of the first
+    recorded state, E, nu: [n_groups], mu: [n_bodies], stats, status)."""
+    given = [a for a in (x_bar, v_bar, C_bar, F_bar) if a is not None]
+    device = bool(given) and not isinstance(given[0], np.ndarray)
+    shapes = ((n, 3), (n, 3), (n, 3, 3), (n, 3, 3))
+    if device:
+        import torch
+        dev = given[0].device
+        ins = [None if a is None else a.to(torch.float32).contiguous() for a in (x_bar, v_bar, C_bar, F_bar)]
+        outs = [torch.zeros(sh, dtype=torch.float32, device=dev) for sh in shapes]
+        iptr = [None if a is None else a.data_ptr() for a in ins]
+        optr = [o.data_ptr() for o in outs]
+        kind = MEM_DEVICE
+    else:
+        ins = [None if a is None else np.ascontiguousarray(a, np.float32).reshape(sh)
+               for a, sh in zip((x_bar, v_bar, C_bar, F_bar), shapes)]
+        outs = [np.zeros(sh, np.float32) for sh in shapes]
+        iptr = [None if a is None else a.ctypes.data for a in ins]
+        optr = [o.ctypes.data for o in outs]
+        kind = MEM_HOST
+    mat = np.zeros(2 * max(n_groups, 1))
+    mu = np.zeros(max(n_bodies, 1))
+    st = BackwardStats()
+    params = AdjointParams(float(eps_r), int(max_iters))
+    code = lib.mpm_backward(ctx, kind, *iptr, *optr, mat.ctypes.data, mu.ctypes.data,
+                            C.byref(params), C.byref(st))
+    if check:
+        _check(ctx, code)
+    return {"x": outs[0], "v": outs[1], "C": outs[2], "F": outs[3],
+            "E": mat[0:2 * n_groups:2].copy(), "nu": mat[1:2 * n_groups:2].copy(),
+            "mu": mu[:n_bodies].copy(), "stats": st, "status": code}
+
+
 def mpm_synchronize(ctx):
     return lib.mpm_synchronize(ctx)
 
@@ -476,6 +531,21 @@ class Sim:
 
     def contacts(self):
         return mpm_get_contacts(self.ctx)
+
+    def tape_begin(self):
+        """Record a checkpoint at every following step (mpm_tape_begin)."""
+        mpm_tape_begin(self.ctx)
+
+    def tape_end(self):
+        mpm_tape_end(self.ctx)
+
+    def backward(self, x_bar=None, v_bar=None, C_bar=None, F_bar=None, eps_r=1e-6,
+                 max_iters=2000, check=True):
+        """Adjoint of the recorded rollout for the cotangents of its final
+        state (mpm_backward): dL/d(first recorded state), dL/dE, dL/dnu per
+        group, dL/dmu per body."""
+        return mpm_backward(self.ctx, self.n, len(self.scene["groups"]), self.n_bodies,
+                            x_bar, v_bar, C_bar, F_bar, eps_r, max_iters, check)
 
     def contact_adjoint(self, node_ids, vbar, eps_r=1e-5, max_iters=1000, check=True):
         """dL/dv*, per-contact (dL/dv_r, dL/dmu) and per-body gradients of the

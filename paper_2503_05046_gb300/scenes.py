@@ -361,3 +361,46 @@ def cube_contact(n_side=10, seed=SEED_BASE + 31, v0=(0.05, 0.0, -0.05), penetrat
     sc["groups"][0]["material"] = elastic(E, 0.3, 1000.0)
     sc["name"] = "cube_contact_%d" % (n_side ** 3)
     return sc
+
+
+def push_cube(n_particles=65536, side=0.1, seed=SEED_BASE + 3, dx=5e-3, h=1e-4, substeps=25,
+              E=1.0e5, nu=0.3, v0=(0.0, 0.0, 0.0), push_speed=0.1, box_overlap=0.0,
+              mu_ground=0.5, mu_box=0.3, sink=0.0, lattice_side=0):
+    """The differentiation workload: an elastic cube of `n_particles` seeded
+    uniformly at random in a box of edge `side` (65,536 in 0.1 m at dx = 5e-3
+    is ~8.2 per cell), standing on a static half-space z = 0 (its bottom
+    `sink` below the plane) and pushed along +x by a kinematic box whose face
+    starts `box_overlap` inside the cube's -x face. With lattice_side > 0 the
+    particles sit instead on a lattice_side^3 grid at spacing side /
+    lattice_side (cell centres; `sink` and `box_overlap` are then measured
+    from the outer particle layers). Substeps per rigid step = the checkpoint
+    interval of the rollout. Returns the scene and a seeded target point for
+    the centroid loss."""
+    rng = np.random.default_rng(seed)
+    lo = np.array([-side / 2.0, -side / 2.0, -sink])
+    if lattice_side > 0:
+        sp = side / lattice_side
+        i = (np.arange(lattice_side) + 0.5) * sp
+        grid3 = np.stack(np.meshgrid(i, i, i, indexing="ij"), -1).reshape(-1, 3)
+        x = (lo + grid3 - np.array([0.0, 0.0, sp / 2.0])).astype(np.float32)
+        box_overlap = box_overlap + sp / 2.0
+        n_particles = len(x)
+    else:
+        x = (lo + side * rng.random((n_particles, 3))).astype(np.float32)
+    vol = side ** 3 / n_particles
+    g = {"x": x, "v": np.tile(np.asarray(v0, np.float32), (n_particles, 1)), "vol": vol,
+         "material": elastic(E, nu, 1000.0)}
+    half = (0.02, 0.6 * side, 0.4 * side)
+    box_x = -side / 2.0 - half[0] + box_overlap
+    bodies = [body(HALFSPACE, mu=mu_ground),
+              body(BOX, half, p=(box_x, 0.0, half[2] + 0.1 * side), v=(push_speed, 0.0, 0.0),
+                   mu=mu_box, kinematic=1)]
+    # domain: the cube, the box's travel and a margin of Dirichlet layers
+    span = 2.0 * side + 0.1
+    res = int(np.ceil(span / dx / 4.0)) * 4 + 16
+    grid = {"dx": dx, "res": (res, res, res), "origin": (-res * dx / 2.0, -res * dx / 2.0, -8 * dx),
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    target = np.array([side, 0.0, side / 2.0]) + 0.01 * side * rng.standard_normal(3)
+    sc = {"name": "push_cube_%d" % n_particles, "grid": grid, "groups": [g], "bodies": bodies,
+          "h": h, "substeps": substeps}
+    return sc, target

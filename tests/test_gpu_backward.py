@@ -1,0 +1,104 @@
+"""mpm_backward against the FP64 oracle: directional derivatives of a linear
+functional of the final state of a short rollout (the differentiation
+workload in miniature: an elastic lattice cube on the ground, pushed by a
+kinematic box; 2 rigid steps of 5 substeps) with respect to the initial
+state, E, nu and each body's mu, by central differences of the oracle's
+rollout (Eq. (3)-(8), FP64, tightly solved), compared with the inner product
+of the CUDA path's adjoint and the same direction."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_05046_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+SCENE = dict(side=0.04, dx=0.01, lattice_side=8, substeps=5, sink=1e-5, box_overlap=1e-5,
+             v0=(0.02, 0.0, -0.02))
+STEPS = 2
+GPU_SOLVER = dict(eps_r=1e-7, eps_a=0.0, max_iters=100000, ls_rel_tol=1e-6, ls_max_iters=60)
+ORC_SOLVER = dict(eps_r=1e-10, eps_a=0.0, max_iters=50000, ls_rel_tol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def case():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2503_05046_gb300 import native
+    sc, _ = scenes.push_cube(**SCENE)
+    n = scenes.n_particles(sc)
+    rng = np.random.default_rng(11)
+    cot = {"x": rng.normal(size=(n, 3)), "v": rng.normal(size=(n, 3)) * 1e-2,
+           "C": rng.normal(size=(n, 3, 3)) * 1e-4, "F": rng.normal(size=(n, 3, 3)) * 1e-3}
+    sim = native.Sim(sc)
+    sim.tape_begin()
+    for _ in range(STEPS):
+        sim.step(n_substeps=sc["substeps"], solver=native.solver_params(**GPU_SOLVER))
+    sim.tape_end()
+    out = sim.backward(x_bar=cot["x"].astype(np.float32), v_bar=cot["v"].astype(np.float32),
+                       C_bar=cot["C"].astype(np.float32), F_bar=cot["F"].astype(np.float32))
+    final = sim.get_particles()
+    sim.close()
+    return native, sc, cot, out, final
+
+
+def _loss(sc, cot, state=None, materials=None, bodies=None):
+    st, code = O.rollout(sc, STEPS, O.solver(**ORC_SOLVER), materials=materials, bodies=bodies,
+                         state=state)
+    assert code == O.OK
+    return sum(float(np.sum(cot[k] * st[k])) for k in ("x", "v", "C", "F"))
+
+
+def _fd_state(sc, cot, key, delta, eps):
+    st0, _ = O.from_scene(sc)
+    plus, minus = dict(st0), dict(st0)
+    plus[key] = st0[key] + eps * delta
+    minus[key] = st0[key] - eps * delta
+    return (_loss(sc, cot, state=plus) - _loss(sc, cot, state=minus)) / (2 * eps)
+
+
+def _fd_material(sc, cot, key, eps):
+    _, mats = O.from_scene(sc)
+    p, m = [dict(x) for x in mats], [dict(x) for x in mats]
+    p[0][key] += eps
+    m[0][key] -= eps
+    return (_loss(sc, cot, materials=p) - _loss(sc, cot, materials=m)) / (2 * eps)
+
+
+def _fd_mu(sc, cot, b, eps):
+    bp, bm = O.bodies_from_scene(sc), O.bodies_from_scene(sc)
+    bp[b]["mu"] += eps
+    bm[b]["mu"] -= eps
+    return (_loss(sc, cot, bodies=bp) - _loss(sc, cot, bodies=bm)) / (2 * eps)
+
+
+def test_forward_matches_oracle(case):
+    native, sc, cot, out, final = case
+    st, code = O.rollout(sc, STEPS, O.solver(**ORC_SOLVER))
+    assert code == O.OK
+    assert np.max(np.abs(final["x"] - st["x"])) < 1e-6
+
+
+@pytest.mark.parametrize("key,eps", [("v", 1e-6), ("x", 1e-8), ("F", 1e-7), ("C", 1e-5)])
+def test_state_adjoint(case, key, eps):
+    native, sc, cot, out, final = case
+    n = scenes.n_particles(sc)
+    shape = (n, 3) if key in "xv" else (n, 3, 3)
+    delta = np.random.default_rng(hash(key) % 1000).normal(size=shape)
+    fd = _fd_state(sc, cot, key, delta, eps)
+    got = float(np.sum(out[key].astype(np.float64) * delta))
+    print("d/d%s0: fd %.6e adjoint %.6e rel %.2e" % (key, fd, got, abs(got - fd) / abs(fd)))
+    assert abs(got - fd) <= 2e-3 * abs(fd)
+
+
+def test_parameter_adjoint(case):
+    native, sc, cot, out, final = case
+    E = float(np.float32(sc["groups"][0]["material"]["E"]))
+    rows = [("E", _fd_material(sc, cot, "E", 1e-6 * E), out["E"][0]),
+            ("nu", _fd_material(sc, cot, "nu", 1e-6), out["nu"][0])]
+    for b in range(len(sc["bodies"])):
+        rows.append(("mu%d" % b, _fd_mu(sc, cot, b, 1e-6), out["mu"][b]))
+    for name, fd, got in rows:
+        print("d/d%s: fd %.6e adjoint %.6e rel %.2e" % (name, fd, got, abs(got - fd) / max(abs(fd), 1e-300)))
+    for name, fd, got in rows:
+        assert abs(got - fd) <= 2e-3 * abs(fd), name
