@@ -217,6 +217,13 @@ mpm_status mpm_set_particles(mpm_ctx* ctx, const float* x, const float* v, const
 mpm_status mpm_get_particles(mpm_ctx* ctx, float* x, float* v, float* C, float* F,
                              int32_t mem_kind);
 
+/* Change the material of particle group `group` (0-based, in the order of
+   mpm_add_particles calls): model, E, nu, friction angle; the density, and
+   with it the particle mass, must stay the same (MPM_ERR_INVALID_ARG
+   otherwise). The stored stresses are recomputed. Not allowed while a tape
+   is recorded (MPM_ERR_STATE). Synchronises. */
+mpm_status mpm_set_material(mpm_ctx* ctx, int32_t group, const mpm_material* mat);
+
 /* Replace the rigid bodies (at most 16). They apply from the next mpm_step. */
 mpm_status mpm_set_rigid_bodies(mpm_ctx* ctx, int32_t n, const mpm_rigid_body* bodies);
 

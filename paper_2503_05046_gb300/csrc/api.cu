@@ -540,6 +540,50 @@ const char* mpm_last_error(const mpm_ctx* ctx) {
   return ctx->err.c_str();
 }
 
+namespace {
+
+// Per-group constants: Lame parameters from (E, nu), Drucker-Prager slope
+// from the friction angle.
+DevGroup make_group(const mpm_material& mat, float particle_volume) {
+  DevGroup gr;
+  memset(&gr, 0, sizeof(gr));
+  const double E = mat.E, nu = mat.nu;
+  gr.vol = particle_volume;
+  gr.mass = (float)((double)mat.rho * (double)particle_volume);
+  gr.mu_l = (float)(E / (2.0 * (1.0 + nu)));
+  gr.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+  const double sphi = std::sin((double)mat.friction_angle_deg * 3.14159265358979323846 / 180.0);
+  gr.dp_alpha = (float)(std::sqrt(2.0 / 3.0) * 2.0 * sphi / (3.0 - sphi));
+  gr.model = mat.model;
+  return gr;
+}
+
+bool material_ok(const mpm_material* mat) {
+  return mat && (mat->model == MPM_COROTATED || mat->model == MPM_DRUCKER_PRAGER) && mat->E > 0.f &&
+         mat->nu > -1.f && mat->nu < 0.5f && mat->rho > 0.f;
+}
+
+}  // namespace
+
+mpm_status mpm_set_material(mpm_ctx* ctx, int32_t group, const mpm_material* mat) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (group < 0 || group >= (int32_t)ctx->groups.size() || !material_ok(mat))
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_material: bad group or material");
+  if (ctx->taping)
+    return fail(ctx, MPM_ERR_STATE, "mpm_set_material: not while a tape is recorded");
+  if (mat->rho != ctx->mats[group].rho)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_material: the density (particle mass) is fixed");
+  ctx->groups[group] = make_group(*mat, ctx->groups[group].vol);
+  ctx->mats[group] = *mat;
+  CU(cudaMemcpyAsync(ctx->groups_d, ctx->groups.data(), ctx->groups.size() * sizeof(DevGroup),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  // the stored stress follows the new constants
+  if (ctx->n > 0) launch_stress_from_F(ctx->P[ctx->cur], (int)ctx->n, ctx->groups_d, ctx->stream);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(ctx->stream));
+  return MPM_OK;
+}
+
 mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v,
                              float particle_volume, const mpm_material* mat, int32_t mem_kind,
                              int64_t* first_id) {
@@ -554,16 +598,7 @@ mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const floa
   if (ctx->n + n > ctx->cap) return fail(ctx, MPM_ERR_CAPACITY, "mpm_add_particles: max_particles exceeded");
   if (ctx->groups.size() >= 65535) return fail(ctx, MPM_ERR_CAPACITY, "mpm_add_particles: too many groups");
   if (first_id) *first_id = ctx->n;
-  DevGroup gr;
-  memset(&gr, 0, sizeof(gr));
-  double E = mat->E, nu = mat->nu;
-  gr.vol = particle_volume;
-  gr.mass = (float)((double)mat->rho * (double)particle_volume);
-  gr.mu_l = (float)(E / (2.0 * (1.0 + nu)));
-  gr.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
-  double sphi = std::sin((double)mat->friction_angle_deg * 3.14159265358979323846 / 180.0);
-  gr.dp_alpha = (float)(std::sqrt(2.0 / 3.0) * 2.0 * sphi / (3.0 - sphi));
-  gr.model = mat->model;
+  const DevGroup gr = make_group(*mat, particle_volume);
   ctx->groups.push_back(gr);
   ctx->mats.push_back(*mat);
   if ((int)ctx->groups.size() > ctx->groups_cap) {

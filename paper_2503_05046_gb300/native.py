@@ -112,6 +112,7 @@ SIGNATURES = {
     "mpm_get_grid_noalloc": [_vp, C.c_int64, _i64p, _i32p, _fp, _fp, _fp],
     "mpm_contact_adjoint": [_vp, C.c_int32, C.c_int64, _vp, _vp, _vp, C.c_int64, _vp, _vp,
                             C.POINTER(AdjointParams), C.POINTER(AdjointStats)],
+    "mpm_set_material": [_vp, C.c_int32, C.POINTER(Material)],
     "mpm_tape_begin": [_vp],
     "mpm_tape_end": [_vp],
     "mpm_backward": [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -332,6 +333,11 @@ def mpm_contact_adjoint(ctx, node_ids, vbar, n_contacts=None, n_bodies=0, eps_r=
     if check:
         _check(ctx, code)
     return vsb[:n], cbar[:n_contacts], bbar[:n_bodies], st, code
+
+
+def mpm_set_material(ctx, group, material):
+    m = material if isinstance(material, Material) else make_material(material)
+    _check(ctx, lib.mpm_set_material(ctx, int(group), C.byref(m)))
 
 
 def mpm_tape_begin(ctx):

@@ -102,3 +102,64 @@ def test_parameter_adjoint(case):
         print("d/d%s: fd %.6e adjoint %.6e rel %.2e" % (name, fd, got, abs(got - fd) / max(abs(fd), 1e-300)))
     for name, fd, got in rows:
         assert abs(got - fd) <= 2e-3 * abs(fd), name
+
+
+def test_autograd_rollout(case):
+    """The torch.autograd binding: a nonlinear loss (squared centroid
+    distance plus a velocity term) through the rollout; E.grad, nu.grad,
+    mu.grad and a direction of v0.grad against central differences of the
+    oracle's rollout."""
+    import torch
+    from paper_2503_05046_gb300 import autograd
+    native, sc, cot, out, final = case
+    n = scenes.n_particles(sc)
+    target = np.array([0.01, 0.0, 0.02])
+    wv = np.random.default_rng(12).normal(size=(n, 3)) * 1e-2
+
+    def loss_np(st):
+        c = st["x"].mean(0)
+        return float(np.sum((c - target) ** 2) + np.sum(wv * st["v"]))
+
+    mat = sc["groups"][0]["material"]
+    x0 = torch.tensor(sc["groups"][0]["x"], dtype=torch.float32, device="cuda")
+    v0 = torch.tensor(sc["groups"][0]["v"], dtype=torch.float32, device="cuda", requires_grad=True)
+    E = torch.tensor([float(np.float32(mat["E"]))], dtype=torch.float64, requires_grad=True)
+    nu = torch.tensor([float(np.float32(mat["nu"]))], dtype=torch.float64, requires_grad=True)
+    mu = torch.tensor([float(np.float32(b["mu"])) for b in sc["bodies"]], dtype=torch.float64,
+                      requires_grad=True)
+    sim = native.Sim(sc)
+    xf, vf = autograd.rollout(sim, STEPS, x0, v0, E, nu, mu,
+                              solver=native.solver_params(**GPU_SOLVER))
+    L = ((xf.double().mean(0) - torch.tensor(target, device="cuda")) ** 2).sum() + \
+        (vf.double() * torch.tensor(wv, device="cuda")).sum()
+    L.backward()
+    sim.close()
+    S = O.solver(**ORC_SOLVER)
+
+    def orc(materials=None, bodies=None, state=None):
+        st, code = O.rollout(sc, STEPS, S, materials=materials, bodies=bodies, state=state)
+        assert code == O.OK
+        return loss_np(st)
+
+    _, mats = O.from_scene(sc)
+    hE = 1e-6 * mats[0]["E"]
+    p, m = [dict(mats[0], E=mats[0]["E"] + hE)], [dict(mats[0], E=mats[0]["E"] - hE)]
+    assert abs(E.grad.item() - (orc(materials=p) - orc(materials=m)) / (2 * hE)) <= \
+        2e-3 * abs((orc(materials=p) - orc(materials=m)) / (2 * hE))
+    p, m = [dict(mats[0], nu=mats[0]["nu"] + 1e-6)], [dict(mats[0], nu=mats[0]["nu"] - 1e-6)]
+    fd = (orc(materials=p) - orc(materials=m)) / 2e-6
+    assert abs(nu.grad.item() - fd) <= 2e-3 * abs(fd)
+    for b in range(len(sc["bodies"])):
+        bp, bm = O.bodies_from_scene(sc), O.bodies_from_scene(sc)
+        bp[b]["mu"] += 1e-6
+        bm[b]["mu"] -= 1e-6
+        fd = (orc(bodies=bp) - orc(bodies=bm)) / 2e-6
+        assert abs(mu.grad[b].item() - fd) <= 2e-3 * abs(fd), b
+    st0, _ = O.from_scene(sc)
+    dv = np.random.default_rng(13).normal(size=(n, 3))
+    sp, sm = dict(st0), dict(st0)
+    sp["v"] = st0["v"] + 1e-6 * dv
+    sm["v"] = st0["v"] - 1e-6 * dv
+    fd = (orc(state=sp) - orc(state=sm)) / 2e-6
+    got = float(np.sum(v0.grad.double().cpu().numpy() * dv))
+    assert abs(got - fd) <= 2e-3 * abs(fd)
