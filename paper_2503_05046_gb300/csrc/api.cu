@@ -1060,6 +1060,7 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
     }
   }
   AdjointArgs a;
+  memset(&a, 0, sizeof(a));  // gbar = nullptr: the single-solve mode
   a.g = ctx->g; a.G = ctx->G; a.C = ctx->C; a.bodies = ctx->bodies_d; a.nb = ctx->last_nb;
   a.h = ctx->last_h; a.eps_s = ctx->last_eps_s; a.eps_r = ap.eps_r; a.max_iters = ap.max_iters;
   a.n_in = (int)n; a.ids = d_ids; a.vbar = d_vbar; a.vstar_bar = d_vsb;

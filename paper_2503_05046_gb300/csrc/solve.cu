@@ -975,7 +975,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
   __shared__ DevBody s_body[kMaxBodies];
   __shared__ float s_red[kWarps][kRedWidth];
   __shared__ float2 s_tot[kRedWidth];
-  __shared__ float s_bb[kMaxBodies][7];
+  __shared__ double s_bb[kMaxBodies][7];  // FP64: the per-body sums cancel strongly
   const int tid = threadIdx.x;
   // the last substep's contact count (G2P has reset the live counter), or
   // in mpm_backward mode the live count of the substep just solved
@@ -988,7 +988,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
   if ((int)blockIdx.x >= nblk) return;
   for (int i = tid; i < a.nb * (int)(sizeof(DevBody) / 4); i += kThreads)
     reinterpret_cast<float*>(s_body)[i] = reinterpret_cast<const float*>(a.bodies)[i];
-  for (int i = tid; i < kMaxBodies * 7; i += kThreads) (&s_bb[0][0])[i] = 0.f;
+  for (int i = tid; i < kMaxBodies * 7; i += kThreads) (&s_bb[0][0])[i] = 0.0;
   __syncthreads();
   Barrier B{a.bar, (unsigned)nblk, a.status, a.poison};
   const int gtid = blockIdx.x * kThreads + tid;
@@ -1378,20 +1378,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
         o[0] = y[0]; o[1] = y[1]; o[2] = y[2]; o[3] = mub;
       }
       const DevBody& bd = s_body[body];
-      const float r0 = xp.x - bd.p[0], r1 = xp.y - bd.p[1], r2 = xp.z - bd.p[2];
-      atomicAdd(&s_bb[body][0], y[0]);
-      atomicAdd(&s_bb[body][1], y[1]);
-      atomicAdd(&s_bb[body][2], y[2]);
-      atomicAdd(&s_bb[body][3], r1 * y[2] - r2 * y[1]);
-      atomicAdd(&s_bb[body][4], r2 * y[0] - r0 * y[2]);
-      atomicAdd(&s_bb[body][5], r0 * y[1] - r1 * y[0]);
-      atomicAdd(&s_bb[body][6], mub);
+      const double r0 = (double)xp.x - bd.p[0], r1 = (double)xp.y - bd.p[1], r2 = (double)xp.z - bd.p[2];
+      atomicAdd(&s_bb[body][0], yd[0]);
+      atomicAdd(&s_bb[body][1], yd[1]);
+      atomicAdd(&s_bb[body][2], yd[2]);
+      atomicAdd(&s_bb[body][3], r1 * yd[2] - r2 * yd[1]);
+      atomicAdd(&s_bb[body][4], r2 * yd[0] - r0 * yd[2]);
+      atomicAdd(&s_bb[body][5], r0 * yd[1] - r1 * yd[0]);
+      atomicAdd(&s_bb[body][6], (double)mub);
     }
   }
   __syncthreads();
   for (int i = tid; i < a.nb * 7; i += kThreads) {
-    const float v = (&s_bb[0][0])[i];
-    if (v != 0.f) atomicAdd(a.body_bar + i, (double)v);
+    const double v = (&s_bb[0][0])[i];
+    if (v != 0.0) atomicAdd(a.body_bar + i, v);
   }
   if (!grid_sync(B)) return;
   // ---- dL/dv* on the contact nodes (into q)
