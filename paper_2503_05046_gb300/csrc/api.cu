@@ -101,6 +101,8 @@ struct mpm_ctx {
   float* bw_buf = nullptr;  // bar[2], final state, substep states: 24 floats per particle each
   size_t bw_buf_cap = 0;
   float4* bw_gbar = nullptr;
+  float4* bw_vsave = nullptr;  // each substep's solved grid velocity (warm starts)
+  size_t bw_vsave_cap = 0;     // substeps it holds
   int* bw_slot = nullptr;
   double* bw_mat = nullptr;
   size_t bw_mat_cap = 0;
@@ -328,7 +330,8 @@ void release(mpm_ctx* c) {
                   c->C.bias, c->C.id, c->C.vc, c->C.dvc, c->C.gamma, c->C.count, c->red, c->bar, c->poison,
                   c->status, c->stats, c->impulses, c->sb.keys[0], c->sb.keys[1], c->sb.vals[0],
                   c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage, c->adj_vec, c->adj_body,
-                  c->adj_out, c->adj_ids, c->adj_io, c->bw_buf, c->bw_gbar, c->bw_slot, c->bw_mat};
+                  c->adj_out, c->adj_ids, c->adj_io, c->bw_buf, c->bw_gbar, c->bw_slot, c->bw_mat,
+                  c->bw_vsave};
   for (auto& t : c->tape)
     if (t.state) cudaFree(t.state);
   for (void* p : ptrs)
@@ -341,9 +344,12 @@ void release(mpm_ctx* c) {
 }
 
 // One substep on particle buffer `cur`: P2G, grid update, contact solve and
-// (with_g2p) G2P.
+// (with_g2p) G2P. warm_v: a grid velocity field (this substep's solution,
+// saved earlier) that replaces v* as the solve's starting iterate; save_v:
+// receives the grid velocity after the solve.
 cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_solver_params& sp,
-                            int solve_blocks, bool with_g2p, cudaStream_t s) {
+                            int solve_blocks, bool with_g2p, cudaStream_t s,
+                            const float4* warm_v = nullptr, float4* save_v = nullptr) {
   const int n = (int)ctx->n;
   P2GArgs pa;
   pa.g = ctx->g; pa.P = ctx->P[cur]; pa.n = n; pa.groups = ctx->groups_d;
@@ -353,6 +359,11 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
   launch_p2g(pa, ctx->p2g_chunk, s);
   mark_phase(ctx, MPM_PHASE_GRID);
   launch_grid(ctx->g, ctx->G, hf, ctx->num_sms, ctx->stats, s);
+  if (warm_v) {
+    const cudaError_t e = cudaMemcpyAsync(ctx->G.v, warm_v, ctx->n_nodes * sizeof(float4),
+                                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
   SolveArgs sa;
   sa.g = ctx->g; sa.G = ctx->G; sa.C = ctx->C; sa.bodies = ctx->bodies_d; sa.nb = nb;
   sa.h = hf; sa.eps_s = sp.eps_s; sa.ls_rel_tol = sp.ls_rel_tol; sa.ls_max_iters = sp.ls_max_iters;
@@ -363,6 +374,11 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
   mark_phase(ctx, MPM_PHASE_SOLVE);
   const cudaError_t e = launch_solve(sa, solve_blocks, s);
   if (e != cudaSuccess) return e;
+  if (save_v) {
+    const cudaError_t e2 = cudaMemcpyAsync(save_v, ctx->G.v, ctx->n_nodes * sizeof(float4),
+                                           cudaMemcpyDeviceToDevice, s);
+    if (e2 != cudaSuccess) return e2;
+  }
   if (with_g2p) {
     G2PArgs ga;
     ga.g = ctx->g; ga.P = ctx->P[cur]; ga.n = n; ga.groups = ctx->groups_d; ga.G = ctx->G;
@@ -1181,6 +1197,19 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
     ctx->bw_buf_cap = need;
   }
   if (!ctx->bw_gbar) CU(dalloc(&ctx->bw_gbar, ctx->n_nodes));
+  // one grid velocity field per substep of a step, to warm-start each
+  // substep's second solve from its first one's solution (without room for
+  // them the second solve starts from v* as the first did)
+  if (ctx->bw_vsave_cap < (size_t)max_sub) {
+    if (ctx->bw_vsave) cudaFree(ctx->bw_vsave);
+    ctx->bw_vsave = nullptr;
+    ctx->bw_vsave_cap = 0;
+    if (dalloc(&ctx->bw_vsave, ctx->n_nodes * (size_t)max_sub) == cudaSuccess)
+      ctx->bw_vsave_cap = (size_t)max_sub;
+    else
+      cudaGetLastError();
+  }
+  float4* vsave = ctx->bw_vsave_cap >= (size_t)max_sub ? ctx->bw_vsave : nullptr;
   if (!ctx->bw_slot) CU(dalloc(&ctx->bw_slot, ctx->cap));
   const size_t ng = ctx->groups.size();
   if (ctx->bw_mat_cap < 2 * ng + 2) {
@@ -1229,12 +1258,14 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
     restore_state(ctx, T.state, s);
     for (int k = 0; k < T.n_substeps; ++k) {
       save_state(ctx, sub_states + (size_t)k * per, s);
-      if (k + 1 < T.n_substeps)
-        CU(enqueue_substep(ctx, ctx->cur, nb, T.h, T.sp, ctx->solve_blocks, true, s));
+      float4* sv = vsave ? vsave + (size_t)k * ctx->n_nodes : nullptr;
+      if (k + 1 < T.n_substeps || sv)
+        CU(enqueue_substep(ctx, ctx->cur, nb, T.h, T.sp, ctx->solve_blocks, true, s, nullptr, sv));
     }
     for (int k = T.n_substeps - 1; k >= 0; --k) {
       restore_state(ctx, sub_states + (size_t)k * per, s);
-      CU(enqueue_substep(ctx, ctx->cur, nb, T.h, T.sp, ctx->solve_blocks, false, s));
+      const float4* wv = vsave ? vsave + (size_t)k * ctx->n_nodes : nullptr;
+      CU(enqueue_substep(ctx, ctx->cur, nb, T.h, T.sp, ctx->solve_blocks, false, s, wv));
       CU(cudaMemsetAsync(ctx->bw_gbar, 0, ctx->n_nodes * sizeof(float4), s));
       BackwardArgs ba;
       ba.g = ctx->g; ba.P = P; ba.n = (int)n; ba.groups = ctx->groups_d; ba.G = ctx->G;
