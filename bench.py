@@ -341,22 +341,26 @@ def small_scene_latency(native, n_steps=10):
     return out
 
 
-def batched_throughput(native, n_scenes=256, steps=3, warmup=2, solve_cap=4):
+def batched_throughput(native, n_scenes=256, steps=3, warmup=2):
     """Many independent scenes of uneven size (2k-64k particles each, elastic or
     sand, a gripper jaw and the ground), each in its own context and stream,
     their steps enqueued one after another without waiting (CUDA-graph replays,
-    so the scenes run side by side on the GPU; each scene's contact solve is
-    capped at `solve_cap` SMs), against the single-scene path looped (one scene
-    at a time, every step waited for, the solve on as many SMs as it takes)."""
+    so the scenes run side by side on the GPU), with the SM cap of each
+    scene's contact solve and the P2G block size picked by the autotuner
+    (tune.tune_batch, timed steps of the batch per candidate), against the
+    single-scene path looped (one scene at a time, every step waited for, the
+    solve on as many SMs as it takes, default P2G blocks)."""
     import torch
-    from paper_2503_05046_gb300 import scenes
+    from paper_2503_05046_gb300 import scenes, tune
     scs = [scenes.batch_scene(i) for i in range(n_scenes)]
     sims = [native.Sim(sc, max_contacts=2 * scenes.n_particles(sc)) for sc in scs]
     solver = native.solver_params(eps_r=5e-2, max_iters=1000)
+    (solve_cap, chunk), table = tune.tune_batch(sims, scs, solver)
 
-    def run(cap, wait_each):
+    def run(cap, wait_each, p2g_chunk=256):
         for sim in sims:
             native.mpm_set_option(sim.ctx, native.OPT_SOLVE_BLOCKS, cap)
+            native.mpm_set_option(sim.ctx, native.OPT_P2G_CHUNK, p2g_chunk)
         for _ in range(warmup):
             for sim, sc in zip(sims, scs):
                 native.mpm_step(sim.ctx, sc["h"], sc["substeps"], solver, want_stats=False)
@@ -372,7 +376,7 @@ def batched_throughput(native, n_scenes=256, steps=3, warmup=2, solve_cap=4):
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
-    t_batch = run(solve_cap, False)
+    t_batch = run(solve_cap, False, chunk)
     codes = [native.mpm_synchronize(sim.ctx) for sim in sims]
     t_loop = run(0, True)
     n_total = sum(scenes.n_particles(sc) for sc in scs)
@@ -384,6 +388,8 @@ def batched_throughput(native, n_scenes=256, steps=3, warmup=2, solve_cap=4):
             "substeps_per_step": scs[0]["substeps"], "value": v_batch, "unit": "scene-steps/s",
             "loop_value": v_loop, "speedup": v_batch / v_loop,
             "particle_substeps_per_s": n_total * scs[0]["substeps"] * steps / t_batch,
+            "tuned": {"solve_cap": solve_cap, "p2g_chunk": chunk,
+                      "candidates_s_per_2_steps": [[c, k, round(t, 4)] for c, k, t in table]},
             "status_batched": "ok" if all(c == 0 for c in codes) else
                               "%d scenes reported %s" % (sum(c != 0 for c in codes), sorted(set(codes))),
             "timing": "host clock around the enqueue loop, synchronised on both sides"}

@@ -191,7 +191,11 @@ def batch_scene(index, seed=SEED_BASE + 4, n_min=2000, n_max=64000, dx=5e-3, h=1
     is E < 6e5 for rho = 1000 -- or Drucker-Prager sand, chosen by the seed)
     caught at touch-down: its bottom layer `penetration` into the ground while
     falling at 0.05 m/s, and a kinematic box gripper jaw moving along +x at
-    0.05 m/s whose face overlaps the cube's -x side by `penetration`."""
+    0.05 m/s whose face overlaps the cube's -x side by `penetration`. The
+    contact stiffness per contact point is scaled with the particle mass so
+    that h^2 k / m_p = 0.8, the value of the 8,000-particle cube (k = 1e4 N/m,
+    m_p = 1.25e-4 kg, h = 1e-4 s): these particles are 5-8x lighter, and at
+    k = 1e4 the contact solve of a scene would be that much stiffer."""
     rng = np.random.default_rng(seed * 1000 + index)
     n = int(rng.integers(n_min, n_max + 1))
     n_side = max(int(round(n ** (1.0 / 3.0))), 2)
@@ -205,9 +209,10 @@ def batch_scene(index, seed=SEED_BASE + 4, n_min=2000, n_max=64000, dx=5e-3, h=1
     g = cube_group(n_side, spacing, (0.0, 0.0, half - penetration), (0.0, 0.0, -0.05), mat,
                    jitter=jit, rng=rng)
     mu = float(rng.uniform(0.2, 0.8))
-    bodies = [body(HALFSPACE, mu=mu),
+    k = 0.8 * mat["rho"] * spacing ** 3 / h ** 2
+    bodies = [body(HALFSPACE, mu=mu, k=k),
               body(BOX, (0.01, half + dx, half + dx), p=(-half - 0.01 + penetration, 0, half + dx),
-                   v=(0.05, 0, 0), mu=mu, kinematic=1)]
+                   v=(0.05, 0, 0), mu=mu, k=k, kinematic=1)]
     side = 2 * half + 0.06
     res = 4 * int(np.ceil((side / dx + 12) / 4))
     grid = {"dx": dx, "res": (res, res, res), "origin": (-res * dx / 2, -res * dx / 2, -6 * dx),

@@ -91,3 +91,19 @@ def test_batched_contexts_match_one_at_a_time(native):
         out = sim.get_particles()
         assert rel_linf(out["v"], r["v"].astype(np.float64)) < 1e-4
         sim.close()
+
+
+def test_batch_autotuner(native):
+    """tune.tune_batch times each candidate (solve cap, P2G chunk) on the
+    batch, applies the fastest and leaves every context able to step."""
+    from paper_2503_05046_gb300 import tune
+    scs = [scenes.batch_scene(i, n_max=8000) for i in range(3)]
+    sims = [native.Sim(sc) for sc in scs]
+    solver = native.solver_params(eps_r=5e-2, max_iters=1000)
+    (cap, chunk), table = tune.tune_batch(sims, scs, solver, caps=(2, 4), chunks=(256, 512), steps=1)
+    assert len(table) == 4 and all(t > 0 for _, _, t in table)
+    assert (cap, chunk) == min(table, key=lambda r: r[2])[:2]
+    for sim in sims:
+        code, _ = sim.step(solver=solver, check=False)
+        assert code in (native.OK, native.ERR_NOT_CONVERGED)
+        sim.close()
