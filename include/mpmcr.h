@@ -371,7 +371,9 @@ typedef struct {
    (as in mpm_contact_adjoint, Eq. (8)-(9), plus the dependence of the lagged
    contact terms phi0, n, n0 and of the contact velocity's bias and stencil
    on the particle state), the grid update and P2G (with the weights'
-   gradient and the fixed-corotated stress through its polar decomposition).
+   gradient and the stress: fixed-corotated through its polar decomposition,
+   Hencky with the Drucker-Prager return map through the singular value
+   decomposition).
    Each recorded step is replayed from its checkpoint once to rebuild its
    substep states; each substep's grid and contact solve are then recomputed
    before its adjoint, so memory is one checkpoint per step plus one step's
@@ -387,8 +389,11 @@ typedef struct {
    The contact solve's adjoint is solved to params->eps_r (NULL: 1e-6, 2000
    iterations); the implicit gradient is exact at an exact minimiser, so the
    recorded steps should use a tight solver tolerance.
-   Requires: a tape; the same particles; corotated materials only
-   (MPM_ERR_STATE otherwise) and no dynamic bodies in the recorded steps.
+   The return map's branch boundaries (tension, the yield cone) and the
+   Hencky clamp are kinks where the one-sided derivatives differ; sand
+   starting exactly at F = I with a uniform velocity sits on one.
+   Requires: a tape; the same particles; no dynamic bodies in the recorded
+   steps (MPM_ERR_STATE otherwise).
    Synchronises; afterwards the particle state is the final state again, the
    impulse accumulators are as before, and the tape is kept. */
 mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, const float* v_bar,

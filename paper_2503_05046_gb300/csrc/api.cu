@@ -1173,9 +1173,6 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
   if (ctx->tape.empty()) return fail(ctx, MPM_ERR_STATE, "mpm_backward: no recorded steps (mpm_tape_begin)");
   if (ctx->n != ctx->tape_n)
     return fail(ctx, MPM_ERR_STATE, "mpm_backward: the particle count changed since the tape began");
-  for (const auto& gr : ctx->groups)
-    if (gr.model != MPM_COROTATED)
-      return fail(ctx, MPM_ERR_STATE, "mpm_backward: the adjoint covers corotated materials only");
   for (const auto& t : ctx->tape)
     if (t.dynamic) return fail(ctx, MPM_ERR_STATE, "mpm_backward: a recorded step had dynamic bodies");
   mpm_status st = drain_status(ctx);

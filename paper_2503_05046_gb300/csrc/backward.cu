@@ -1,5 +1,6 @@
 // backward.cu -- reverse-mode adjoint of one MPM substep (the free motion of
-// Eq. (6) and G2P with the corotated stress), for mpm_backward. The contact
+// Eq. (6) and G2P with the constitutive update: fixed-corotated stress, or the
+// Hencky stress with the Drucker-Prager return map), for mpm_backward. The contact
 // solve's part (implicit differentiation of Eq. (8)-(9), with the contact
 // geometry's dependence on the particle state) is k_adjoint in solve.cu.
 //
@@ -46,6 +47,244 @@ __device__ __forceinline__ float4 ld_bar3(const float* bar, int plane, size_t n,
   return make_float4(bar[plane * n + i], bar[(plane + 1) * n + i], bar[(plane + 2) * n + i], 0.f);
 }
 
+// ---- adjoints of spectral matrix functions ----------------------------------
+// G(F) = U diag(h(s)) V^T for F = U diag(s) V^T. With M = U^T dF V (ds_i =
+// M_ii; the rotations follow from the off-diagonal M), U^T dG V has diagonal
+// sum_j dh_i/ds_j M_jj and, for i != j, (a + b)/2 M_ij + (a - b)/2 M_ji with
+// a = (h_i - h_j) / (s_i - s_j), b = (h_i + h_j) / (s_i + s_j). The 2x2 map on
+// (M_ij, M_ji) is symmetric, so the adjoint has the same form on A = U^T Gbar V;
+// Fbar = U Mbar V^T. The divided differences a come from the caller: near
+// rest the s_i differ by ~1e-5 and h_i - h_j formed in FP32 would keep only
+// two or three digits, so each caller writes them out in closed form.
+__device__ void spectral_adjoint(const Polar& P, const float (&h)[3], const float (&dh)[3][3],
+                                 const float (&a)[3][3], const float (&Gb)[9], float (&Fb)[9]) {
+  const float* U = P.U;
+  const float* V = P.V;
+  float T[9], A[9], Mb[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) T[3 * r + q] = Gb[3 * r] * V[q] + Gb[3 * r + 1] * V[3 + q] + Gb[3 * r + 2] * V[6 + q];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) A[3 * r + q] = U[r] * T[q] + U[3 + r] * T[3 + q] + U[6 + r] * T[6 + q];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float d = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) d += dh[j][i] * A[4 * j];
+    Mb[4 * i] = d;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (i == j) continue;
+      float ss = P.s[i] + P.s[j];
+      if (fabsf(ss) < 1e-6f) ss = ss < 0.f ? -1e-6f : 1e-6f;
+      const float b = (h[i] + h[j]) / ss;
+      Mb[3 * i + j] = 0.5f * (a[i][j] + b) * A[3 * i + j] + 0.5f * (a[i][j] - b) * A[3 * j + i];
+    }
+  float MV[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) MV[3 * r + q] = Mb[3 * r] * V[3 * q] + Mb[3 * r + 1] * V[3 * q + 1] + Mb[3 * r + 2] * V[3 * q + 2];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) Fb[3 * r + q] = U[3 * r] * MV[q] + U[3 * r + 1] * MV[3 + q] + U[3 * r + 2] * MV[6 + q];
+}
+
+// s_i - s_j from the accurate s - 1, and (log s_i - log s_j) / (s_i - s_j)
+__device__ __forceinline__ float ds_of(const Polar& P, int i, int j) { return P.sm1[i] - P.sm1[j]; }
+__device__ __forceinline__ float dlog_ratio(const Polar& P, int i, int j) {
+  const float ds = ds_of(P, i, j);
+  const float r = ds / P.s[j];
+  return fabsf(r) > 1e-4f ? log1pf(r) / ds : (1.0f - 0.5f * r + r * r / 3.0f) / P.s[j];
+}
+
+// divided differences of an h with h_i = H(s_i, common terms), generic form
+__device__ __forceinline__ float divided(const Polar& P, const float (&h)[3], const float (&dh)[3][3],
+                                         int i, int j) {
+  const float ds = ds_of(P, i, j);
+  return fabsf(ds) > 1e-4f * (fabsf(P.s[i]) + fabsf(P.s[j])) ? (h[i] - h[j]) / ds
+                                                                : dh[i][i] - dh[i][j];
+}
+
+// Hencky log strain of a singular value and its derivative (0 where clamped)
+__device__ __forceinline__ void hencky_eps(const Polar& P, float (&e)[3], float (&de)[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (P.s[a] > kHenckySigmaMin) {
+      e[a] = log1pf(P.sm1[a]);
+      de[a] = 1.0f / P.s[a];
+    } else {
+      e[a] = logf(kHenckySigmaMin);
+      de[a] = 0.0f;
+    }
+  }
+}
+
+// Hencky Kirchhoff stress tau = U diag(g) U^T, g = 2 mu e + lam tr(e) 1, as
+// tau = Pt F^T with Pt = U diag(g / s) V^T: Fbar = (spectral adjoint of Pt
+// at Ptbar = taubar F) + taubar^T Pt; mubar = 2 sum e_a u_a^T taubar u_a,
+// lambar = tr(taubar) tr(e). Divided differences of h = g / s:
+// (h_i - h_j) / (s_i - s_j) = (2 mu (s_j q_ij - e_j) - lam tr e) / (s_i s_j),
+// q_ij = (e_i - e_j) / (s_i - s_j).
+__device__ void hencky_adjoint(const float (&F)[9], const float (&tb)[9], float mu, float lam,
+                               float (&Fb)[9], float& mub, float& lamb) {
+  Polar P;
+  polar_svd(F, P);
+  float e[3], de[3];
+  hencky_eps(P, e, de);
+  const bool clamped = de[0] == 0.f || de[1] == 0.f || de[2] == 0.f;
+  const float tr = e[0] + e[1] + e[2];
+  float g[3], h[3], dh[3][3], a[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    g[i] = 2.0f * mu * e[i] + lam * tr;
+    float s = P.s[i];
+    if (fabsf(s) < 1e-12f) s = s < 0.f ? -1e-12f : 1e-12f;
+    h[i] = g[i] / s;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dh[i][j] = ((i == j ? 2.0f * mu : 0.0f) + lam) * de[j] / s;
+    dh[i][i] -= g[i] / (s * s);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      a[i][j] = (i == j) ? 0.f
+                : clamped ? divided(P, h, dh, i, j)
+                          : (2.0f * mu * (P.s[j] * dlog_ratio(P, i, j) - e[j]) - lam * tr) / (P.s[i] * P.s[j]);
+  float Pb[9], Pt[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      Pb[3 * r + q] = tb[3 * r] * F[q] + tb[3 * r + 1] * F[3 + q] + tb[3 * r + 2] * F[6 + q];
+      Pt[3 * r + q] = P.U[3 * r] * h[0] * P.V[3 * q] + P.U[3 * r + 1] * h[1] * P.V[3 * q + 1] +
+                      P.U[3 * r + 2] * h[2] * P.V[3 * q + 2];
+    }
+  spectral_adjoint(P, h, dh, a, Pb, Fb);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      Fb[3 * r + q] += tb[r] * Pt[q] + tb[3 + r] * Pt[3 + q] + tb[6 + r] * Pt[6 + q];  // taubar^T Pt
+  float m = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float utu = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) utu += P.U[3 * r + k] * tb[3 * r + q] * P.U[3 * q + k];
+    m += e[k] * utu;
+  }
+  mub = 2.0f * m;
+  lamb = (tb[0] + tb[4] + tb[8]) * tr;
+}
+
+// Drucker-Prager return map in Hencky strain (the forward's
+// constitutive_update): F_new = U exp(e') V^T with e = log s (clamped) and
+//   tr e >= 0:            e' = 0
+//   dgamma = |e^| + c tr e > 0 (c = (3 lam + 2 mu) / (2 mu) alpha):
+//                         e' = (tr e / 3) 1 - c tr e n,  n = e^ / |e^|
+//   otherwise:            e' = e (F_new = F_trial).
+// Given Fbar of F_new: Fbar of F_trial (spectral adjoint with h = exp(e'),
+// dh_i/ds_j = exp(e'_i) (de'_i/de_j) de_j/ds_j, and on the plastic branch
+// (h_i - h_j) / (s_i - s_j) = exp(e'_j) expm1(e'_i - e'_j) / (s_i - s_j) with
+// e'_i - e'_j = -c tr (e_i - e_j) / |e^|) and the adjoints of mu and lam
+// through c (de'/dc = -tr e n).
+__device__ void dp_return_adjoint(const DevGroup& gr, const float (&Ft)[9], const float (&Gb)[9],
+                                  float (&Fb)[9], float& mub, float& lamb) {
+  mub = lamb = 0.f;
+  Polar P;
+  polar_svd(Ft, P);
+  float e[3], de[3];
+  hencky_eps(P, e, de);
+  const bool clamped = de[0] == 0.f || de[1] == 0.f || de[2] == 0.f;
+  const float tr = e[0] + e[1] + e[2];
+  const float eh[3] = {e[0] - tr / 3.0f, e[1] - tr / 3.0f, e[2] - tr / 3.0f};
+  const float nh = sqrtf(eh[0] * eh[0] + eh[1] * eh[1] + eh[2] * eh[2]);
+  const float c = (3.0f * gr.lam + 2.0f * gr.mu_l) / (2.0f * gr.mu_l) * gr.dp_alpha;
+  float ep[3] = {e[0], e[1], e[2]};
+  float J[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+  int branch = 0;  // 0 elastic, 1 tensile (e' = 0), 2 plastic
+  float n[3] = {0.f, 0.f, 0.f};
+  if (tr >= 0.0f) {
+    branch = 1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      ep[i] = 0.f;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) J[i][j] = 0.f;
+    }
+  } else if (nh + c * tr > 0.0f) {
+    branch = 2;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      n[i] = eh[i] / nh;
+      ep[i] = tr / 3.0f - c * tr * n[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        J[i][j] = 1.0f / 3.0f - c * n[i] -
+                  c * tr * ((i == j ? 1.0f : 0.0f) - 1.0f / 3.0f - n[i] * n[j]) / nh;
+  } else if (!clamped) {
+    // elastic, no clamp: F_new = F_trial
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Fb[k] = Gb[k];
+    return;
+  }
+  float h[3], dh[3][3], a[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    h[i] = expf(ep[i]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dh[i][j] = h[i] * J[i][j] * de[j];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (i == j) { a[i][j] = 0.f; continue; }
+      if (branch == 1) {
+        a[i][j] = 0.f;  // h = 1
+      } else if (branch == 2 && !clamped) {
+        const float ds = ds_of(P, i, j);
+        const float dq = dlog_ratio(P, i, j);              // (e_i - e_j) / ds
+        const float dep = -c * tr * dq / nh;               // (e'_i - e'_j) / ds
+        const float x = dep * ds;                          // e'_i - e'_j
+        a[i][j] = h[j] * (fabsf(x) > 1e-4f ? expm1f(x) / ds : dep * (1.0f + 0.5f * x));
+      } else {
+        a[i][j] = divided(P, h, dh, i, j);
+      }
+    }
+  spectral_adjoint(P, h, dh, a, Gb, Fb);
+  if (branch == 2) {
+    // cbar = sum_i hbar_i h_i de'_i/dc, hbar_i = (U^T Gbar V)_ii
+    float cb = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float A = 0.f;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) A += P.U[3 * r + i] * Gb[3 * r + q] * P.V[3 * q + i];
+      cb += A * h[i] * (-tr * n[i]);
+    }
+    // c = (3 lam / (2 mu) + 1) alpha
+    lamb = cb * 3.0f * gr.dp_alpha / (2.0f * gr.mu_l);
+    mub = -cb * 3.0f * gr.lam * gr.dp_alpha / (2.0f * gr.mu_l * gr.mu_l);
+  }
+}
+
 // ---- G2P adjoint -----------------------------------------------------------
 // vbar'_tot = vbar' + h xbar'  (x' = x + h v')
 // Cbar'_tot = Cbar' + h Fbar' F^T,  Fbar = (I + h C')^T Fbar'
@@ -90,6 +329,23 @@ __global__ void __launch_bounds__(kThreads) k_g2p_adjoint(BackwardArgs a) {
   }
   const float4 xb = ld_bar3(a.bin, 0, n, i), vb = ld_bar3(a.bin, 3, n, i);
   const float ub[3] = {vb.x + h * xb.x, vb.y + h * xb.y, vb.z + h * xb.z};
+  // sand: the stored F is the return map of F_trial = (I + h C') F; carry
+  // Fbar back through it (the corotated F is F_trial itself)
+  const int grp = a.P.grp[i];
+  const DevGroup gr = a.groups[grp];
+  if (gr.model == MPM_DRUCKER_PRAGER) {
+    float Ft[9], Gt[9], mub, lamb;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        Ft[3 * r + c] = F[3 * r + c] + h * (Cn[3 * r] * F[c] + Cn[3 * r + 1] * F[3 + c] + Cn[3 * r + 2] * F[6 + c]);
+    dp_return_adjoint(gr, Ft, Fb, Gt, mub, lamb);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Fb[c] = Gt[c];
+    if (mub != 0.f) atomicAdd(a.mat_bar + 2 * grp, (double)mub);
+    if (lamb != 0.f) atomicAdd(a.mat_bar + 2 * grp + 1, (double)lamb);
+  }
   float Ch[9], Fo[9];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
@@ -325,19 +581,18 @@ __global__ void __launch_bounds__(kThreads) k_p2g_adjoint(BackwardArgs a) {
       }
 #pragma unroll
       for (int c = 0; c < 9; ++c) a.bout[(6 + c) * n + i] += gr.mass * Ab[c];
-      if (gr.model == MPM_COROTATED) {
-        float F[9], tb[9], Fb[9];
+      float F[9], tb[9], Fb[9];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) {
-          F[c] = a.P.F(c)[i];
-          tb[c] = -sc * Ab[c];
-        }
-        corotated_adjoint(F, tb, gr.mu_l, gr.lam, Fb, mub, lamb);
-#pragma unroll
-        for (int c = 0; c < 9; ++c) a.bout[(15 + c) * n + i] += Fb[c];
-      } else {
-        atomicOr(a.status, kStUnsupported);
+      for (int c = 0; c < 9; ++c) {
+        F[c] = a.P.F(c)[i];
+        tb[c] = -sc * Ab[c];
       }
+      if (gr.model == MPM_COROTATED)
+        corotated_adjoint(F, tb, gr.mu_l, gr.lam, Fb, mub, lamb);
+      else
+        hencky_adjoint(F, tb, gr.mu_l, gr.lam, Fb, mub, lamb);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) a.bout[(15 + c) * n + i] += Fb[c];
     }
   }
   // per-group parameter adjoints: warp sums when the warp shares a group

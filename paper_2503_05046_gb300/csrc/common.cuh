@@ -25,7 +25,6 @@ constexpr uint32_t kStNotConverged = 1u << MPM_ERR_NOT_CONVERGED;
 constexpr uint32_t kStNan = 1u << MPM_ERR_NAN;
 constexpr uint32_t kStTimeout = 1u << MPM_ERR_TIMEOUT;
 constexpr uint32_t kStLineSearch = 1u << MPM_ERR_LINE_SEARCH;
-constexpr uint32_t kStUnsupported = 1u << MPM_ERR_STATE;  // a kernel met a case it does not handle
 
 struct GridDev {
   float dx, inv_dx;

@@ -370,7 +370,8 @@ def cube_contact(n_side=10, seed=SEED_BASE + 31, v0=(0.05, 0.0, -0.05), penetrat
 
 def push_cube(n_particles=65536, side=0.1, seed=SEED_BASE + 3, dx=5e-3, h=1e-4, substeps=25,
               E=1.0e5, nu=0.3, v0=(0.0, 0.0, 0.0), push_speed=0.1, box_overlap=0.0,
-              mu_ground=0.5, mu_box=0.3, sink=0.0, lattice_side=0, k_contact=1.0e3):
+              mu_ground=0.5, mu_box=0.3, sink=0.0, lattice_side=0, k_contact=1.0e3,
+              material=None):
     """The differentiation workload: an elastic cube of `n_particles` seeded
     uniformly at random in a box of edge `side` (65,536 in 0.1 m at dx = 5e-3
     is ~8.2 per cell), standing on a static half-space z = 0 (its bottom
@@ -380,7 +381,8 @@ def push_cube(n_particles=65536, side=0.1, seed=SEED_BASE + 3, dx=5e-3, h=1e-4, 
     lattice_side (cell centres; `sink` and `box_overlap` are then measured
     from the outer particle layers). Substeps per rigid step = the checkpoint
     interval of the rollout. Returns the scene and a seeded target point for
-    the centroid loss. The contact stiffness k_contact (per contact point) is
+    the centroid loss. `material` replaces the elastic (E, nu) material (e.g.
+    SAND). The contact stiffness k_contact (per contact point) is
     lower than the other scenes' 1e4 N/m: these particles are ~8x lighter, and
     a cube resting on 65k of them stays well conditioned for the solve."""
     rng = np.random.default_rng(seed)
@@ -396,7 +398,7 @@ def push_cube(n_particles=65536, side=0.1, seed=SEED_BASE + 3, dx=5e-3, h=1e-4, 
         x = (lo + side * rng.random((n_particles, 3))).astype(np.float32)
     vol = side ** 3 / n_particles
     g = {"x": x, "v": np.tile(np.asarray(v0, np.float32), (n_particles, 1)), "vol": vol,
-         "material": elastic(E, nu, 1000.0)}
+         "material": dict(material) if material is not None else elastic(E, nu, 1000.0)}
     half = (0.02, 0.6 * side, 0.4 * side)
     box_x = -side / 2.0 - half[0] + box_overlap
     bodies = [body(HALFSPACE, mu=mu_ground, k=k_contact),
