@@ -395,7 +395,9 @@ typedef struct {
    Requires: a tape; the same particles; no dynamic bodies in the recorded
    steps (MPM_ERR_STATE otherwise).
    Synchronises; afterwards the particle state is the final state again, the
-   impulse accumulators are as before, and the tape is kept. */
+   impulse accumulators are as before, and the tape is kept; the grid and
+   contacts hold a replayed substep, so mpm_contact_adjoint needs an
+   mpm_step first (MPM_ERR_STATE otherwise). */
 mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, const float* v_bar,
                         const float* C_bar, const float* F_bar, float* x0_bar, float* v0_bar,
                         float* C0_bar, float* F0_bar, double* material_bar, double* mu_bar,

@@ -1311,6 +1311,7 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
   // put the state back as it was after the last step; the bodies upload again
   restore_state(ctx, final_state, s);
   ctx->bodies_dirty = true;
+  ctx->adj_ready = false;  // the grid and contacts now hold a replayed substep
   st = drain_status(ctx);
   CU(cudaMemcpy(ctx->impulses, imp_saved.data(), 6 * kMaxBodies * sizeof(double), cudaMemcpyHostToDevice));
   if (material_bar)

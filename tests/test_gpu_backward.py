@@ -190,3 +190,39 @@ def test_autograd_rollout(case):
     fd = (orc(state=sp) - orc(state=sm)) / 2e-6
     got = float(np.sum(v0.grad.double().cpu().numpy() * dv))
     assert abs(got - fd) <= 2e-3 * abs(fd)
+
+
+def test_backward_error_paths():
+    """mpm_backward refuses what it cannot differentiate, with MPM_ERR_STATE
+    and without touching the state: no tape, a tape with dynamic bodies,
+    particles added after the tape began; mpm_set_material is refused while
+    recording."""
+    from paper_2503_05046_gb300 import native
+    sc, _ = scenes.push_cube(**SCENE)
+    sim = native.Sim(sc, max_particles=2 * scenes.n_particles(sc))
+    with pytest.raises(native.MpmError) as e:
+        sim.backward(x_bar=np.zeros((sim.n, 3), np.float32))
+    assert e.value.code == native.ERR_STATE
+    sim.tape_begin()
+    with pytest.raises(native.MpmError) as e:
+        native.mpm_set_material(sim.ctx, 0, sc["groups"][0]["material"])
+    assert e.value.code == native.ERR_STATE
+    sim.step(n_substeps=2)
+    before = sim.get_particles()
+    sim.set_dynamics(1, {"mass": 1.0, "inertia": [1e-3, 1e-3, 1e-3]})
+    sim.step(n_substeps=2)
+    sim.tape_end()
+    after = sim.get_particles()
+    with pytest.raises(native.MpmError) as e:
+        sim.backward(x_bar=np.zeros((sim.n, 3), np.float32))
+    assert e.value.code == native.ERR_STATE
+    assert np.array_equal(sim.get_particles()["x"], after["x"])
+    sim.set_dynamics(1, None)
+    sim.tape_begin()
+    native.mpm_add_particles(sim.ctx, before["x"][:4] + np.float32([0, 0, 0.05]),
+                             before["v"][:4], sc["groups"][0]["vol"],
+                             native.make_material(sc["groups"][0]["material"]))
+    with pytest.raises(native.MpmError) as e:
+        sim.step(n_substeps=1)
+    assert e.value.code == native.ERR_STATE
+    sim.close()
