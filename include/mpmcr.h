@@ -351,9 +351,11 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
    mpm_tape_begin clears any previous tape and starts recording: every
    following mpm_step (with n_substeps > 0) stores a checkpoint of the
    particle state at its start (device memory, 96 bytes per particle) with the
-   step's frozen bodies, h and solver parameters. mpm_tape_end stops
-   recording and keeps the tape. Adding particles while recording is an
-   error at the next mpm_step. */
+   step's frozen bodies, h and solver parameters, and each substep's solved
+   velocities on its contact nodes (16 bytes per contact node, in a pool of
+   16M entries allocated at the first mpm_tape_begin; substeps beyond it are
+   re-solved by the backward). mpm_tape_end stops recording and keeps the
+   tape. Adding particles while recording is an error at the next mpm_step. */
 mpm_status mpm_tape_begin(mpm_ctx* ctx);
 mpm_status mpm_tape_end(mpm_ctx* ctx);
 
@@ -376,8 +378,8 @@ typedef struct {
    decomposition).
    Each recorded step is replayed from its checkpoint once to rebuild its
    substep states; each substep's grid and contact solve are then recomputed
-   before its adjoint, so memory is one checkpoint per step plus one step's
-   substep states.
+   before its adjoint (the solves start from the recorded solutions), so
+   memory is one checkpoint per step plus one step's substep states.
 
    Inputs, in id order and caller layout (x, v [n][3]; C, F [n][3][3]), any
    may be NULL for zero: dL/dx, dL/dv, dL/dC, dL/dF of the final state.

@@ -55,7 +55,7 @@ struct mpm_ctx {
   bool use_graphs = true;
   struct GraphKey {
     int64_t n = -1;
-    int n_substeps = 0, nb = 0, chunk = 0, sort_now = 0, solve_blocks = 0;
+    int n_substeps = 0, nb = 0, chunk = 0, sort_now = 0, solve_blocks = 0, taping = 0;
     float h = 0.f;
     mpm_solver_params sp{};
   } gkey[2];
@@ -88,6 +88,7 @@ struct mpm_ctx {
   // frozen bodies, substep size and count, and solver parameters
   struct TapeStep {
     float* state = nullptr;
+    int rec_base = 0;  // record index of the step's first substep solution
     std::vector<DevBody> bodies;
     int n_substeps = 0;
     float h = 0.f;
@@ -97,12 +98,16 @@ struct mpm_ctx {
   bool taping = false;
   int64_t tape_n = 0;
   std::vector<TapeStep> tape;
+  // the contact-node solutions of the taped substeps (see launch_tape_save)
+  float4* tape_pool = nullptr;
+  int2* tape_recs = nullptr;
+  int* tape_counters = nullptr;  // [0] pool fill, [1] records written
+  int tape_pool_cap = 0, tape_rec_cap = 0;
+  int tape_substeps = 0;         // substeps recorded so far (host count)
   // mpm_backward scratch, grown on demand
   float* bw_buf = nullptr;  // bar[2], final state, substep states: 24 floats per particle each
   size_t bw_buf_cap = 0;
   float4* bw_gbar = nullptr;
-  float4* bw_vsave = nullptr;  // each substep's solved grid velocity (warm starts)
-  size_t bw_vsave_cap = 0;     // substeps it holds
   int* bw_slot = nullptr;
   double* bw_mat = nullptr;
   size_t bw_mat_cap = 0;
@@ -331,7 +336,7 @@ void release(mpm_ctx* c) {
                   c->status, c->stats, c->impulses, c->sb.keys[0], c->sb.keys[1], c->sb.vals[0],
                   c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage, c->adj_vec, c->adj_body,
                   c->adj_out, c->adj_ids, c->adj_io, c->bw_buf, c->bw_gbar, c->bw_slot, c->bw_mat,
-                  c->bw_vsave};
+                  c->tape_pool, c->tape_recs, c->tape_counters};
   for (auto& t : c->tape)
     if (t.state) cudaFree(t.state);
   for (void* p : ptrs)
@@ -344,12 +349,12 @@ void release(mpm_ctx* c) {
 }
 
 // One substep on particle buffer `cur`: P2G, grid update, contact solve and
-// (with_g2p) G2P. warm_v: a grid velocity field (this substep's solution,
-// saved earlier) that replaces v* as the solve's starting iterate; save_v:
-// receives the grid velocity after the solve.
+// (with_g2p) G2P. save: append the solve's contact-node velocities to the
+// tape's solution pool; warm_rec >= 0: start the solve from the taped
+// solution record warm_rec instead of v*.
 cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_solver_params& sp,
-                            int solve_blocks, bool with_g2p, cudaStream_t s,
-                            const float4* warm_v = nullptr, float4* save_v = nullptr) {
+                            int solve_blocks, bool with_g2p, cudaStream_t s, bool save = false,
+                            int warm_rec = -1) {
   const int n = (int)ctx->n;
   P2GArgs pa;
   pa.g = ctx->g; pa.P = ctx->P[cur]; pa.n = n; pa.groups = ctx->groups_d;
@@ -359,11 +364,8 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
   launch_p2g(pa, ctx->p2g_chunk, s);
   mark_phase(ctx, MPM_PHASE_GRID);
   launch_grid(ctx->g, ctx->G, hf, ctx->num_sms, ctx->stats, s);
-  if (warm_v) {
-    const cudaError_t e = cudaMemcpyAsync(ctx->G.v, warm_v, ctx->n_nodes * sizeof(float4),
-                                          cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
-  }
+  if (warm_rec >= 0 && ctx->tape_pool)
+    launch_tape_warm(ctx->G, ctx->tape_recs, warm_rec, ctx->tape_pool, ctx->num_sms, s);
   SolveArgs sa;
   sa.g = ctx->g; sa.G = ctx->G; sa.C = ctx->C; sa.bodies = ctx->bodies_d; sa.nb = nb;
   sa.h = hf; sa.eps_s = sp.eps_s; sa.ls_rel_tol = sp.ls_rel_tol; sa.ls_max_iters = sp.ls_max_iters;
@@ -374,11 +376,9 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
   mark_phase(ctx, MPM_PHASE_SOLVE);
   const cudaError_t e = launch_solve(sa, solve_blocks, s);
   if (e != cudaSuccess) return e;
-  if (save_v) {
-    const cudaError_t e2 = cudaMemcpyAsync(save_v, ctx->G.v, ctx->n_nodes * sizeof(float4),
-                                           cudaMemcpyDeviceToDevice, s);
-    if (e2 != cudaSuccess) return e2;
-  }
+  if (save && ctx->tape_pool)
+    launch_tape_save(ctx->G, ctx->tape_counters, ctx->tape_recs, ctx->tape_rec_cap, ctx->tape_pool,
+                     ctx->tape_pool_cap, ctx->num_sms, s);
   if (with_g2p) {
     G2PArgs ga;
     ga.g = ctx->g; ga.P = ctx->P[cur]; ga.n = n; ga.groups = ctx->groups_d; ga.G = ctx->G;
@@ -403,7 +403,7 @@ cudaError_t enqueue_step(mpm_ctx* ctx, int from, bool sort_now, int n_substeps, 
     cur = 1 - cur;
   }
   for (int k = 0; k < n_substeps; ++k) {
-    const cudaError_t e = enqueue_substep(ctx, cur, nb, hf, sp, solve_blocks, true, s);
+    const cudaError_t e = enqueue_substep(ctx, cur, nb, hf, sp, solve_blocks, true, s, ctx->taping);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
@@ -804,6 +804,8 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
                        t.state + 15 * nn, s);
     for (int i = 0; i < nb; ++i) t.bodies.push_back(to_dev(ctx->bodies[i]));
     t.n_substeps = n_substeps;
+    t.rec_base = ctx->tape_substeps;
+    ctx->tape_substeps += n_substeps;
     t.h = (float)h;
     t.sp = sp;
     for (int d : ctx->is_dyn) t.dynamic = t.dynamic || d;
@@ -822,10 +824,11 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     mpm_ctx::GraphKey k;
     k.n = n; k.n_substeps = n_substeps; k.nb = nb; k.chunk = ctx->p2g_chunk;
     k.sort_now = sort_now ? 1 : 0; k.solve_blocks = solve_blocks; k.h = hf; k.sp = sp;
+    k.taping = ctx->taping && ctx->tape_pool ? 1 : 0;
     const mpm_ctx::GraphKey& o = ctx->gkey[from];
     const bool same = ctx->gexec[from] && o.n == k.n && o.n_substeps == k.n_substeps && o.nb == k.nb &&
                       o.chunk == k.chunk && o.sort_now == k.sort_now &&
-                      o.solve_blocks == k.solve_blocks && o.h == k.h &&
+                      o.solve_blocks == k.solve_blocks && o.h == k.h && o.taping == k.taping &&
                       memcmp(&o.sp, &k.sp, sizeof(k.sp)) == 0;
     if (!same) {
       if (ctx->gexec[from]) {
@@ -1120,6 +1123,26 @@ mpm_status mpm_tape_begin(mpm_ctx* ctx) {
   ctx->tape.clear();
   ctx->taping = true;
   ctx->tape_n = ctx->n;
+  ctx->tape_substeps = 0;
+  // the solution pool: 16M contact-node velocities (256 MB) and 1M substep
+  // records; without room the backward re-solves from v* instead
+  if (!ctx->tape_pool) {
+    const int pool_cap = 1 << 24, rec_cap = 1 << 20;
+    if (dalloc(&ctx->tape_pool, pool_cap) == cudaSuccess && dalloc(&ctx->tape_recs, rec_cap) == cudaSuccess &&
+        dalloc(&ctx->tape_counters, 2) == cudaSuccess) {
+      ctx->tape_pool_cap = pool_cap;
+      ctx->tape_rec_cap = rec_cap;
+    } else {
+      cudaGetLastError();
+      cudaFree(ctx->tape_pool);
+      cudaFree(ctx->tape_recs);
+      cudaFree(ctx->tape_counters);
+      ctx->tape_pool = nullptr;
+      ctx->tape_recs = nullptr;
+      ctx->tape_counters = nullptr;
+    }
+  }
+  if (ctx->tape_counters) CU(cudaMemset(ctx->tape_counters, 0, 2 * sizeof(int)));
   return MPM_OK;
 }
 
@@ -1194,19 +1217,6 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
     ctx->bw_buf_cap = need;
   }
   if (!ctx->bw_gbar) CU(dalloc(&ctx->bw_gbar, ctx->n_nodes));
-  // one grid velocity field per substep of a step, to warm-start each
-  // substep's second solve from its first one's solution (without room for
-  // them the second solve starts from v* as the first did)
-  if (ctx->bw_vsave_cap < (size_t)max_sub) {
-    if (ctx->bw_vsave) cudaFree(ctx->bw_vsave);
-    ctx->bw_vsave = nullptr;
-    ctx->bw_vsave_cap = 0;
-    if (dalloc(&ctx->bw_vsave, ctx->n_nodes * (size_t)max_sub) == cudaSuccess)
-      ctx->bw_vsave_cap = (size_t)max_sub;
-    else
-      cudaGetLastError();
-  }
-  float4* vsave = ctx->bw_vsave_cap >= (size_t)max_sub ? ctx->bw_vsave : nullptr;
   if (!ctx->bw_slot) CU(dalloc(&ctx->bw_slot, ctx->cap));
   const size_t ng = ctx->groups.size();
   if (ctx->bw_mat_cap < 2 * ng + 2) {
@@ -1253,16 +1263,17 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
     if (nb) CU(cudaMemcpyAsync(ctx->bodies_d, T.bodies.data(), nb * sizeof(DevBody), cudaMemcpyHostToDevice, s));
     // replay the step from its checkpoint, keeping each substep's start state
     restore_state(ctx, T.state, s);
-    for (int k = 0; k < T.n_substeps; ++k) {
+    // (each solve starts from the forward's taped solution of its substep,
+    // when the pool held it, and stops at its first convergence test)
+    auto rec_of = [&](int k) { return T.rec_base + k < ctx->tape_rec_cap ? T.rec_base + k : -1; };
+    for (int k = 0; k + 1 < T.n_substeps; ++k) {
       save_state(ctx, sub_states + (size_t)k * per, s);
-      float4* sv = vsave ? vsave + (size_t)k * ctx->n_nodes : nullptr;
-      if (k + 1 < T.n_substeps || sv)
-        CU(enqueue_substep(ctx, ctx->cur, nb, T.h, T.sp, ctx->solve_blocks, true, s, nullptr, sv));
+      CU(enqueue_substep(ctx, ctx->cur, nb, T.h, T.sp, ctx->solve_blocks, true, s, false, rec_of(k)));
     }
+    save_state(ctx, sub_states + (size_t)(T.n_substeps - 1) * per, s);
     for (int k = T.n_substeps - 1; k >= 0; --k) {
       restore_state(ctx, sub_states + (size_t)k * per, s);
-      const float4* wv = vsave ? vsave + (size_t)k * ctx->n_nodes : nullptr;
-      CU(enqueue_substep(ctx, ctx->cur, nb, T.h, T.sp, ctx->solve_blocks, false, s, wv));
+      CU(enqueue_substep(ctx, ctx->cur, nb, T.h, T.sp, ctx->solve_blocks, false, s, false, rec_of(k)));
       CU(cudaMemsetAsync(ctx->bw_gbar, 0, ctx->n_nodes * sizeof(float4), s));
       BackwardArgs ba;
       ba.g = ctx->g; ba.P = P; ba.n = (int)n; ba.groups = ctx->groups_d; ba.G = ctx->G;

@@ -624,6 +624,46 @@ __global__ void k_reset_counters(GridArrays G, Contacts C, unsigned* bar) {
   bar[0] = 0u;
 }
 
+// ---- solutions of the taped substeps ---------------------------------------
+// After each recorded solve, the velocities of its contact nodes (the only
+// nodes the solve changes) are appended to a pool as (v.x, v.y, v.z, node),
+// one record (offset, count) per substep, in order; count = -1 marks a
+// substep that did not fit. mpm_backward scatters a record back over v* to
+// start that substep's replayed solves at their solution.
+__global__ void k_tape_alloc(GridArrays G, int* __restrict__ counters, int2* __restrict__ recs,
+                             int rec_cap, int pool_cap) {
+  const int n = min(*G.n_cnodes, G.cnodes_cap);
+  const int r = counters[1];
+  const int off = counters[0];
+  const bool fits = off + n <= pool_cap;
+  if (r < rec_cap) recs[r] = make_int2(off, fits ? n : -1);
+  if (fits) counters[0] = off + n;
+  counters[1] = r + 1;
+}
+
+__global__ void k_tape_copy(GridArrays G, const int* __restrict__ counters, const int2* __restrict__ recs,
+                            int rec_cap, float4* __restrict__ pool) {
+  const int r = counters[1] - 1;
+  if (r >= rec_cap) return;
+  const int2 rec = recs[r];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rec.y; t += gridDim.x * blockDim.x) {
+    const int node = G.cnodes[t];
+    const float4 v = G.v[node];
+    pool[rec.x + t] = make_float4(v.x, v.y, v.z, __int_as_float(node));
+  }
+}
+
+__global__ void k_tape_warm(GridArrays G, const int2* __restrict__ recs, int r,
+                            const float4* __restrict__ pool) {
+  const int2 rec = recs[r];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rec.y; t += gridDim.x * blockDim.x) {
+    const float4 q = pool[rec.x + t];
+    float4* v = G.v + __float_as_int(q.w);
+    const float w = v->w;  // the Dirichlet flag of this substep's grid update
+    *v = make_float4(q.x, q.y, q.z, w);
+  }
+}
+
 // slot_of[pid[i]] = i
 __global__ void k_slot_map(const uint32_t* __restrict__ pid, int n, int* __restrict__ slot_of) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -683,6 +723,17 @@ void launch_p2g_adjoint(const BackwardArgs& a, cudaStream_t s) {
 
 void launch_reset_counters(const GridArrays& G, const Contacts& C, unsigned* bar, cudaStream_t s) {
   k_reset_counters<<<1, 1, 0, s>>>(G, C, bar);
+}
+
+void launch_tape_save(const GridArrays& G, int* counters, int2* recs, int rec_cap, float4* pool,
+                      int pool_cap, int num_sms, cudaStream_t s) {
+  k_tape_alloc<<<1, 1, 0, s>>>(G, counters, recs, rec_cap, pool_cap);
+  k_tape_copy<<<num_sms, 256, 0, s>>>(G, counters, recs, rec_cap, pool);
+}
+
+void launch_tape_warm(const GridArrays& G, const int2* recs, int r, const float4* pool, int num_sms,
+                      cudaStream_t s) {
+  k_tape_warm<<<num_sms, 256, 0, s>>>(G, recs, r, pool);
 }
 
 void launch_slot_map(const Particles& P, int n, int* slot_of, cudaStream_t s) {

@@ -158,6 +158,12 @@ void launch_grid_adjoint(const BackwardArgs& a, int num_sms, cudaStream_t s);
 void launch_p2g_adjoint(const BackwardArgs& a, cudaStream_t s);
 void launch_reset_counters(const GridArrays& G, const Contacts& C, unsigned* bar, cudaStream_t s);
 void launch_slot_map(const Particles& P, int n, int* slot_of, cudaStream_t s);
+// taped solutions: append the contact-node velocities after a solve (counters:
+// [0] pool fill, [1] records written); scatter record r over v*
+void launch_tape_save(const GridArrays& G, int* counters, int2* recs, int rec_cap, float4* pool,
+                      int pool_cap, int num_sms, cudaStream_t s);
+void launch_tape_warm(const GridArrays& G, const int2* recs, int r, const float4* pool, int num_sms,
+                      cudaStream_t s);
 void launch_bar_in(const Particles& P, int n, const float* x, const float* v, const float* C,
                    const float* F, float* bar, cudaStream_t s);
 void launch_bar_out(const Particles& P, int n, const float* bar, float* x, float* v, float* C,
