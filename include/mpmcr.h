@@ -423,14 +423,20 @@ mpm_status mpm_synchronize(mpm_ctx* ctx);
    makes each device-wide barrier of the contact solve wait for one arrival
    more than there are blocks, so that (with two or more participating
    blocks) it gives up after its 1 s limit, the solve returns and the step
-   reports MPM_ERR_TIMEOUT; the context stays usable. */
+   reports MPM_ERR_TIMEOUT; the context stays usable.
+   MPM_OPT_TAPE_SOLUTIONS: capacity, in contact nodes, of the pool in which a
+   recorded rollout keeps each substep's contact-node solutions for
+   mpm_backward (default 16,777,216 = 256 MB; 0: keep none, the backward then
+   solves every replayed substep from v*); applies from the next
+   mpm_tape_begin. */
 enum {
   MPM_OPT_PROFILE = 1,
   MPM_OPT_SORT_EVERY = 2,
   MPM_OPT_P2G_CHUNK = 3,
   MPM_OPT_GRAPHS = 4,
   MPM_OPT_SOLVE_BLOCKS = 5,
-  MPM_OPT_TEST_BARRIER_TIMEOUT = 6
+  MPM_OPT_TEST_BARRIER_TIMEOUT = 6,
+  MPM_OPT_TAPE_SOLUTIONS = 7
 };
 mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value);
 

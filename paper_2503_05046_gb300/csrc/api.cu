@@ -56,6 +56,7 @@ struct mpm_ctx {
   struct GraphKey {
     int64_t n = -1;
     int n_substeps = 0, nb = 0, chunk = 0, sort_now = 0, solve_blocks = 0, taping = 0;
+    const void* tape_pool = nullptr;  // baked into the launches when taping
     float h = 0.f;
     mpm_solver_params sp{};
   } gkey[2];
@@ -103,6 +104,7 @@ struct mpm_ctx {
   int2* tape_recs = nullptr;
   int* tape_counters = nullptr;  // [0] pool fill, [1] records written
   int tape_pool_cap = 0, tape_rec_cap = 0;
+  int64_t tape_pool_want = 1 << 24;  // MPM_OPT_TAPE_SOLUTIONS
   int tape_substeps = 0;         // substeps recorded so far (host count)
   // mpm_backward scratch, grown on demand
   float* bw_buf = nullptr;  // bar[2], final state, substep states: 24 floats per particle each
@@ -825,10 +827,12 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     k.n = n; k.n_substeps = n_substeps; k.nb = nb; k.chunk = ctx->p2g_chunk;
     k.sort_now = sort_now ? 1 : 0; k.solve_blocks = solve_blocks; k.h = hf; k.sp = sp;
     k.taping = ctx->taping && ctx->tape_pool ? 1 : 0;
+    k.tape_pool = ctx->tape_pool;
     const mpm_ctx::GraphKey& o = ctx->gkey[from];
     const bool same = ctx->gexec[from] && o.n == k.n && o.n_substeps == k.n_substeps && o.nb == k.nb &&
                       o.chunk == k.chunk && o.sort_now == k.sort_now &&
                       o.solve_blocks == k.solve_blocks && o.h == k.h && o.taping == k.taping &&
+                      o.tape_pool == k.tape_pool &&
                       memcmp(&o.sp, &k.sp, sizeof(k.sp)) == 0;
     if (!same) {
       if (ctx->gexec[from]) {
@@ -1124,10 +1128,20 @@ mpm_status mpm_tape_begin(mpm_ctx* ctx) {
   ctx->taping = true;
   ctx->tape_n = ctx->n;
   ctx->tape_substeps = 0;
-  // the solution pool: 16M contact-node velocities (256 MB) and 1M substep
-  // records; without room the backward re-solves from v* instead
-  if (!ctx->tape_pool) {
-    const int pool_cap = 1 << 24, rec_cap = 1 << 20;
+  // the solution pool (MPM_OPT_TAPE_SOLUTIONS contact-node velocities, 256 MB
+  // by default) and 1M substep records; without room the backward re-solves
+  // from v* instead
+  if (ctx->tape_pool && ctx->tape_pool_cap != ctx->tape_pool_want) {
+    cudaFree(ctx->tape_pool);
+    cudaFree(ctx->tape_recs);
+    cudaFree(ctx->tape_counters);
+    ctx->tape_pool = nullptr;
+    ctx->tape_recs = nullptr;
+    ctx->tape_counters = nullptr;
+    ctx->tape_pool_cap = ctx->tape_rec_cap = 0;
+  }
+  if (!ctx->tape_pool && ctx->tape_pool_want > 0) {
+    const int pool_cap = (int)ctx->tape_pool_want, rec_cap = 1 << 20;
     if (dalloc(&ctx->tape_pool, pool_cap) == cudaSuccess && dalloc(&ctx->tape_recs, rec_cap) == cudaSuccess &&
         dalloc(&ctx->tape_counters, 2) == cudaSuccess) {
       ctx->tape_pool_cap = pool_cap;
@@ -1265,7 +1279,9 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
     restore_state(ctx, T.state, s);
     // (each solve starts from the forward's taped solution of its substep,
     // when the pool held it, and stops at its first convergence test)
-    auto rec_of = [&](int k) { return T.rec_base + k < ctx->tape_rec_cap ? T.rec_base + k : -1; };
+    auto rec_of = [&](int k) {
+      return ctx->tape_pool && T.rec_base + k < ctx->tape_rec_cap ? T.rec_base + k : -1;
+    };
     for (int k = 0; k + 1 < T.n_substeps; ++k) {
       save_state(ctx, sub_states + (size_t)k * per, s);
       CU(enqueue_substep(ctx, ctx->cur, nb, T.h, T.sp, ctx->solve_blocks, true, s, false, rec_of(k)));
@@ -1370,6 +1386,11 @@ mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value) {
       return MPM_OK;
     case MPM_OPT_TEST_BARRIER_TIMEOUT:
       ctx->wait_test = value != 0;
+      return MPM_OK;
+    case MPM_OPT_TAPE_SOLUTIONS:
+      if (value < 0 || value > (1LL << 30))
+        return fail(ctx, MPM_ERR_INVALID_ARG, "tape solution pool must hold 0 .. 2^30 entries");
+      ctx->tape_pool_want = value;
       return MPM_OK;
     case MPM_OPT_SOLVE_BLOCKS:
       if (value < 0) return fail(ctx, MPM_ERR_INVALID_ARG, "solve block cap must be >= 0");

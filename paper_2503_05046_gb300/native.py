@@ -25,6 +25,7 @@ STATUS_NAMES = ["MPM_OK", "MPM_ERR_INVALID_ARG", "MPM_ERR_CUDA", "MPM_ERR_OOM", 
                 "MPM_ERR_TIMEOUT", "MPM_ERR_LINE_SEARCH"]
 MEM_HOST, MEM_DEVICE = 0, 1
 OPT_PROFILE, OPT_SORT_EVERY, OPT_P2G_CHUNK, OPT_GRAPHS, OPT_SOLVE_BLOCKS = 1, 2, 3, 4, 5
+OPT_TAPE_SOLUTIONS = 7
 OPT_TEST_BARRIER_TIMEOUT = 6
 PHASES = ["sort", "p2g", "grid", "solve", "g2p"]
 

@@ -226,3 +226,29 @@ def test_backward_error_paths():
         sim.step(n_substeps=1)
     assert e.value.code == native.ERR_STATE
     sim.close()
+
+
+def test_backward_without_taped_solutions_agrees():
+    """With the solution pool switched off (MPM_OPT_TAPE_SOLUTIONS = 0) every
+    replayed solve starts from v*; the gradients equal those of the default
+    warm-started backward (both solve the same substeps to the same
+    tolerance)."""
+    from paper_2503_05046_gb300 import native
+    sc, _ = scenes.push_cube(**SCENE)
+    n = scenes.n_particles(sc)
+    xbar = np.random.default_rng(31).normal(size=(n, 3)).astype(np.float32)
+    out = []
+    for pool in (1 << 24, 0):
+        sim = native.Sim(sc)
+        native.mpm_set_option(sim.ctx, native.OPT_TAPE_SOLUTIONS, pool)
+        sim.tape_begin()
+        for _ in range(STEPS):
+            sim.step(n_substeps=sc["substeps"], solver=native.solver_params(**GPU_SOLVER))
+        sim.tape_end()
+        out.append(sim.backward(x_bar=xbar))
+        sim.close()
+    for key in ("x", "v", "F"):
+        a, b = out[0][key].astype(np.float64), out[1][key].astype(np.float64)
+        assert np.max(np.abs(a - b)) <= 1e-3 * np.max(np.abs(b)), key
+    for key in ("E", "nu", "mu"):
+        assert np.allclose(out[0][key], out[1][key], rtol=1e-3, atol=0), key
