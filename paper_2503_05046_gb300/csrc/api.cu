@@ -287,7 +287,12 @@ mpm_status drain_status(mpm_ctx* ctx, uint32_t* bits_out = nullptr) {
   CU(cudaStreamSynchronize(ctx->stream));
   uint32_t bits = 0;
   CU(cudaMemcpy(&bits, ctx->status, sizeof(bits), cudaMemcpyDeviceToHost));
-  if (bits) CU(cudaMemset(ctx->status, 0, sizeof(uint32_t)));
+  // (on the context's stream: it is non-blocking, so a legacy-stream memset
+  // would not be ordered before the next launch)
+  if (bits) {
+    CU(cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t), ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
   if (bits_out) *bits_out = bits;
   return first_error(ctx, bits);
 }
@@ -931,7 +936,7 @@ mpm_status mpm_get_rigid_impulses(mpm_ctx* ctx, double* out, int32_t reset) {
   const size_t nb = ctx->bodies.size();
   if (nb) CU(cudaMemcpy(out, ctx->impulses, 6 * nb * sizeof(double), cudaMemcpyDeviceToHost));
   if (reset) {
-    CU(cudaMemset(ctx->impulses, 0, 6 * kMaxBodies * sizeof(double)));
+    CU(cudaMemsetAsync(ctx->impulses, 0, 6 * kMaxBodies * sizeof(double), ctx->stream));
     ctx->imp_seen.assign(6 * kMaxBodies, 0.0);
     ctx->imp_seen_valid = true;
   }
@@ -957,7 +962,7 @@ mpm_status mpm_get_grid(mpm_ctx* ctx, int64_t cap, int64_t* count, int32_t* node
             dalloc(&d_vs, 3 * max_nodes + 3) == cudaSuccess && dalloc(&d_v, 3 * max_nodes + 3) == cudaSuccess;
   int got = 0;
   if (ok) {
-    cudaMemset(d_count, 0, sizeof(int));
+    cudaMemsetAsync(d_count, 0, sizeof(int), ctx->stream);
     if (n_act > 0)
       k_grid_out<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->g, ctx->G, n_act, d_count, d_ids, d_m,
                                                            d_vs, d_v);
@@ -1108,8 +1113,10 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
     if (n > 0) CU(cudaMemcpy(vstar_bar, d_vsb, 3 * n * sizeof(float), cudaMemcpyDeviceToHost));
     if (k > 0) CU(cudaMemcpy(contact_bar, d_cbar, 4 * k * sizeof(float), cudaMemcpyDeviceToHost));
   }
-  if (body_bar && ctx->last_nb > 0)
-    CU(cudaMemcpy(body_bar, ctx->adj_body, 7 * ctx->last_nb * sizeof(double), back));
+  if (body_bar && ctx->last_nb > 0) {
+    CU(cudaMemcpyAsync(body_bar, ctx->adj_body, 7 * ctx->last_nb * sizeof(double), back, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
   if (stats) {
     stats->iters = (int32_t)out[0];
     stats->residual = out[1];
@@ -1156,7 +1163,7 @@ mpm_status mpm_tape_begin(mpm_ctx* ctx) {
       ctx->tape_counters = nullptr;
     }
   }
-  if (ctx->tape_counters) CU(cudaMemset(ctx->tape_counters, 0, 2 * sizeof(int)));
+  if (ctx->tape_counters) CU(cudaMemsetAsync(ctx->tape_counters, 0, 2 * sizeof(int), ctx->stream));
   return MPM_OK;
 }
 
@@ -1340,7 +1347,9 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
   ctx->bodies_dirty = true;
   ctx->adj_ready = false;  // the grid and contacts now hold a replayed substep
   st = drain_status(ctx);
-  CU(cudaMemcpy(ctx->impulses, imp_saved.data(), 6 * kMaxBodies * sizeof(double), cudaMemcpyHostToDevice));
+  CU(cudaMemcpyAsync(ctx->impulses, imp_saved.data(), 6 * kMaxBodies * sizeof(double),
+                     cudaMemcpyHostToDevice, s));
+  CU(cudaStreamSynchronize(s));
   if (material_bar)
     for (size_t gi = 0; gi < ng; ++gi) {
       // mu = E / (2 (1 + nu)), lam = E nu / ((1 + nu)(1 - 2 nu))
