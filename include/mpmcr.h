@@ -385,9 +385,14 @@ typedef struct {
    may be NULL for zero: dL/dx, dL/dv, dL/dC, dL/dF of the final state.
    Outputs (NULL to skip): the same four for the state at the start of the
    first recorded step; material_bar [n_groups][2] doubles = dL/dE, dL/dnu
-   per particle group (in the order the groups were added); mu_bar
-   [n_bodies] doubles = dL/dmu per body index. Rigid bodies are inputs: their
-   recorded poses and velocities are replayed, and only mu is differentiated.
+   per particle group (in the order the groups were added); body_bar
+   [n_bodies][7] doubles per body index = dL/dmu, dL/dv (3) and dL/dp (3),
+   where v is the body's (frozen) linear velocity over the recorded steps and
+   p its position at the first one: v and p enter every contact's bias,
+   lagged normal impulse and geometry (through x - p), and a kinematic
+   body's position advances by n_substeps h v after each step. Rigid bodies
+   are otherwise inputs: their recorded orientations and angular velocities
+   are replayed and not differentiated.
    The contact solve's adjoint is solved to params->eps_r (NULL: 1e-6, 2000
    iterations); the implicit gradient is exact at an exact minimiser, so the
    recorded steps should use a tight solver tolerance.
@@ -402,7 +407,7 @@ typedef struct {
    mpm_step first (MPM_ERR_STATE otherwise). */
 mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, const float* v_bar,
                         const float* C_bar, const float* F_bar, float* x0_bar, float* v0_bar,
-                        float* C0_bar, float* F0_bar, double* material_bar, double* mu_bar,
+                        float* C0_bar, float* F0_bar, double* material_bar, double* body_bar,
                         const mpm_adjoint_params* params, mpm_backward_stats* stats);
 
 /* Wait for the context's stream and report any device-side failure. */

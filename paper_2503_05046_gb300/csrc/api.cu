@@ -76,7 +76,7 @@ struct mpm_ctx {
   int last_nb = 0;
   // the adjoint's device buffers, allocated at its first call
   float4* adj_vec = nullptr;       // kAdjointVectors x cnodes_cap
-  double* adj_body = nullptr;      // 7 per body
+  double* adj_body = nullptr;      // kAdjBodySlots per body
   float* adj_out = nullptr;        // iterations, residual, contacts, contact nodes
   int adj_blocks = 0;
   int32_t* adj_ids = nullptr;      // staging of host inputs and outputs
@@ -91,6 +91,7 @@ struct mpm_ctx {
     float* state = nullptr;
     int rec_base = 0;  // record index of the step's first substep solution
     std::vector<DevBody> bodies;
+    std::vector<int> kinematic;  // per body: its pose advances by n_substeps h v after the step
     int n_substeps = 0;
     float h = 0.f;
     mpm_solver_params sp{};
@@ -113,6 +114,8 @@ struct mpm_ctx {
   int* bw_slot = nullptr;
   double* bw_mat = nullptr;
   size_t bw_mat_cap = 0;
+  double* bw_snap = nullptr;   // per recorded step: the body accumulators after it
+  size_t bw_snap_cap = 0;
   std::string err;
 };
 
@@ -343,7 +346,7 @@ void release(mpm_ctx* c) {
                   c->status, c->stats, c->impulses, c->sb.keys[0], c->sb.keys[1], c->sb.vals[0],
                   c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage, c->adj_vec, c->adj_body,
                   c->adj_out, c->adj_ids, c->adj_io, c->bw_buf, c->bw_gbar, c->bw_slot, c->bw_mat,
-                  c->tape_pool, c->tape_recs, c->tape_counters};
+                  c->tape_pool, c->tape_recs, c->tape_counters, c->bw_snap};
   for (auto& t : c->tape)
     if (t.state) cudaFree(t.state);
   for (void* p : ptrs)
@@ -809,7 +812,10 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     const size_t nn = (size_t)ctx->n;
     launch_to_id_order(ctx->P[ctx->cur], (int)nn, t.state, t.state + 3 * nn, t.state + 6 * nn,
                        t.state + 15 * nn, s);
-    for (int i = 0; i < nb; ++i) t.bodies.push_back(to_dev(ctx->bodies[i]));
+    for (int i = 0; i < nb; ++i) {
+      t.bodies.push_back(to_dev(ctx->bodies[i]));
+      t.kinematic.push_back(ctx->bodies[i].kinematic != 0 && !(i < (int)ctx->is_dyn.size() && ctx->is_dyn[i]));
+    }
     t.n_substeps = n_substeps;
     t.rec_base = ctx->tape_substeps;
     ctx->tape_substeps += n_substeps;
@@ -1049,7 +1055,7 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
   cudaStream_t s = ctx->stream;
   if (!ctx->adj_vec) {
     CU(dalloc(&ctx->adj_vec, (size_t)kAdjointVectors * ctx->G.cnodes_cap));
-    CU(dalloc(&ctx->adj_body, 7 * kMaxBodies));
+    CU(dalloc(&ctx->adj_body, kAdjBodySlots * kMaxBodies));
     CU(dalloc(&ctx->adj_out, 4));
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel_ptr(), solve_block_size(), 0));
@@ -1098,7 +1104,7 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
   // the barrier counter and the node-list length are zero between launches
   CU(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned), s));
   CU(cudaMemsetAsync(ctx->G.n_cnodes, 0, sizeof(int), s));
-  CU(cudaMemsetAsync(ctx->adj_body, 0, 7 * kMaxBodies * sizeof(double), s));
+  CU(cudaMemsetAsync(ctx->adj_body, 0, kAdjBodySlots * kMaxBodies * sizeof(double), s));
   CU(cudaMemsetAsync(ctx->adj_out, 0, 4 * sizeof(float), s));
   CU(launch_adjoint(a, ctx->adj_blocks, s));
   CU(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned), s));
@@ -1114,7 +1120,9 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
     if (k > 0) CU(cudaMemcpy(contact_bar, d_cbar, 4 * k * sizeof(float), cudaMemcpyDeviceToHost));
   }
   if (body_bar && ctx->last_nb > 0) {
-    CU(cudaMemcpyAsync(body_bar, ctx->adj_body, 7 * ctx->last_nb * sizeof(double), back, ctx->stream));
+    // the first 7 of each body's accumulators
+    CU(cudaMemcpy2DAsync(body_bar, 7 * sizeof(double), ctx->adj_body, kAdjBodySlots * sizeof(double),
+                         7 * sizeof(double), ctx->last_nb, back, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
   }
   if (stats) {
@@ -1190,7 +1198,7 @@ void save_state(mpm_ctx* ctx, float* st, cudaStream_t s) {
 mpm_status ensure_adjoint_buffers(mpm_ctx* ctx) {
   if (ctx->adj_vec) return MPM_OK;
   CU(dalloc(&ctx->adj_vec, (size_t)kAdjointVectors * ctx->G.cnodes_cap));
-  CU(dalloc(&ctx->adj_body, 7 * kMaxBodies));
+  CU(dalloc(&ctx->adj_body, kAdjBodySlots * kMaxBodies));
   CU(dalloc(&ctx->adj_out, 4));
   int occ = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel_ptr(), solve_block_size(), 0));
@@ -1203,7 +1211,7 @@ mpm_status ensure_adjoint_buffers(mpm_ctx* ctx) {
 
 mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, const float* v_bar,
                         const float* C_bar, const float* F_bar, float* x0_bar, float* v0_bar,
-                        float* C0_bar, float* F0_bar, double* material_bar, double* mu_bar,
+                        float* C0_bar, float* F0_bar, double* material_bar, double* body_bar,
                         const mpm_adjoint_params* params, mpm_backward_stats* stats) {
   if (!ctx) return MPM_ERR_INVALID_ARG;
   if (mem_kind != MPM_MEM_HOST && mem_kind != MPM_MEM_DEVICE)
@@ -1247,6 +1255,14 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
     CU(dalloc(&ctx->bw_mat, 2 * ng + 2));
     ctx->bw_mat_cap = 2 * ng + 2;
   }
+  const size_t nsnap = ctx->tape.size() * kMaxBodies * kAdjBodySlots;
+  if (ctx->bw_snap_cap < nsnap) {
+    if (ctx->bw_snap) cudaFree(ctx->bw_snap);
+    ctx->bw_snap = nullptr;
+    ctx->bw_snap_cap = 0;
+    CU(dalloc(&ctx->bw_snap, nsnap));
+    ctx->bw_snap_cap = nsnap;
+  }
   float* bar[2] = {ctx->bw_buf, ctx->bw_buf + per};
   float* final_state = ctx->bw_buf + 2 * per;
   float* sub_states = ctx->bw_buf + 3 * per;
@@ -1273,7 +1289,7 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
   }
   launch_bar_in(P, (int)n, dsrc[0], dsrc[1], dsrc[2], dsrc[3], bar[0], s);
   CU(cudaMemsetAsync(ctx->bw_mat, 0, (2 * ng + 2) * sizeof(double), s));
-  CU(cudaMemsetAsync(ctx->adj_body, 0, 7 * kMaxBodies * sizeof(double), s));
+  CU(cudaMemsetAsync(ctx->adj_body, 0, kAdjBodySlots * kMaxBodies * sizeof(double), s));
   int in = 0;
   int substeps = 0;
   int nb_max = 0;
@@ -1322,6 +1338,9 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
       in = 1 - in;
       ++substeps;
     }
+    // the body accumulators so far (steps t .. end), to split them by step
+    CU(cudaMemcpyAsync(ctx->bw_snap + (size_t)t * kMaxBodies * kAdjBodySlots, ctx->adj_body,
+                       kMaxBodies * kAdjBodySlots * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   // outputs: the adjoint of the first recorded state, in id order
   float* dst[4] = {x0_bar, v0_bar, C0_bar, F0_bar};
@@ -1337,9 +1356,9 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
   if (mem_kind == MPM_MEM_HOST)
     for (int f = 0; f < 4; ++f)
       if (dst[f]) CU(cudaMemcpyAsync(dst[f], ddst[f], n * width[f] * sizeof(float), cudaMemcpyDeviceToHost, s));
-  std::vector<double> lame(2 * ng + 2), body(7 * kMaxBodies);
+  std::vector<double> lame(2 * ng + 2), snap(nsnap);
   CU(cudaMemcpyAsync(lame.data(), ctx->bw_mat, (2 * ng + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CU(cudaMemcpyAsync(body.data(), ctx->adj_body, 7 * kMaxBodies * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(snap.data(), ctx->bw_snap, nsnap * sizeof(double), cudaMemcpyDeviceToHost, s));
   float out[4];
   CU(cudaMemcpyAsync(out, ctx->adj_out, sizeof(out), cudaMemcpyDeviceToHost, s));
   // put the state back as it was after the last step; the bodies upload again
@@ -1359,8 +1378,32 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
       material_bar[2 * gi] = mub / (2.0 * a) + lamb * nu / (a * b);
       material_bar[2 * gi + 1] = -mub * E / (2.0 * a * a) + lamb * E * (1.0 + 2.0 * nu * nu) / (a * a * b * b);
     }
-  if (mu_bar)
-    for (int b = 0; b < nb_max; ++b) mu_bar[b] = body[7 * b + 6];
+  if (body_bar) {
+    // per body: dL/dmu; dL/dv = sum over steps of the direct terms (bias,
+    // lagged normal impulse) plus, for a kinematic body, the position
+    // adjoint of each step times the time its pose had advanced by then
+    // (p_t = p_0 + sum_{t' < t} n_substeps h v); dL/dp_0 = sum of the
+    // position adjoints
+    const int T = (int)ctx->tape.size();
+    auto S = [&](int t, int b, int k) {
+      return t >= T ? 0.0 : snap[((size_t)t * kMaxBodies + b) * kAdjBodySlots + k];
+    };
+    for (int b = 0; b < nb_max; ++b) {
+      double* o = body_bar + 7 * b;
+      o[0] = S(0, b, 6);
+      for (int c = 0; c < 3; ++c) {
+        o[1 + c] = S(0, b, c) + S(0, b, 10 + c);
+        o[4 + c] = S(0, b, 7 + c);
+      }
+      double offset = 0.0;
+      for (int t = 0; t < T; ++t) {
+        const auto& tk = ctx->tape[t];
+        if (b >= (int)tk.bodies.size()) break;
+        for (int c = 0; c < 3; ++c) o[1 + c] += offset * (S(t, b, 7 + c) - S(t + 1, b, 7 + c));
+        if (tk.kinematic[b]) offset += (double)tk.n_substeps * (double)tk.h;
+      }
+    }
+  }
   if (stats) {
     stats->steps = (int32_t)ctx->tape.size();
     stats->substeps = substeps;

@@ -117,7 +117,7 @@ struct AdjointArgs {
   float* vstar_bar;   // [3 n_in]
   float* contact_bar; // [4 contact_cap]: dL/dv_r(x_p) (3), dL/dmu; may be null
   int contact_cap;
-  double* body_bar;   // [7 nb]: dL/dv, dL/domega, dL/dmu per body, zeroed by the caller
+  double* body_bar;   // [kAdjBodySlots nb], zeroed by the caller
   float4* vec;        // kAdjointVectors x cnodes_cap float4
   double* red;
   unsigned* bar;
@@ -136,6 +136,11 @@ struct AdjointArgs {
   int n_particles;
 };
 constexpr int kAdjointVectors = 13;
+// per-body adjoint accumulators: dL/dv_r through the bias (3), its moment
+// about the body origin (3), dL/dmu, and in mpm_backward mode dL/dp of the
+// body position through the contact geometry (3) and dL/dv through the
+// lagged normal impulse (3)
+constexpr int kAdjBodySlots = 13;
 cudaError_t launch_adjoint(const AdjointArgs& a, int grid_blocks, cudaStream_t s);
 const void* adjoint_kernel_ptr();
 

@@ -975,7 +975,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
   __shared__ DevBody s_body[kMaxBodies];
   __shared__ float s_red[kWarps][kRedWidth];
   __shared__ float2 s_tot[kRedWidth];
-  __shared__ double s_bb[kMaxBodies][7];  // FP64: the per-body sums cancel strongly
+  __shared__ double s_bb[kMaxBodies][kAdjBodySlots];  // FP64: the per-body sums cancel strongly
   const int tid = threadIdx.x;
   // the last substep's contact count (G2P has reset the live counter), or
   // in mpm_backward mode the live count of the substep just solved
@@ -988,7 +988,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
   if ((int)blockIdx.x >= nblk) return;
   for (int i = tid; i < a.nb * (int)(sizeof(DevBody) / 4); i += kThreads)
     reinterpret_cast<float*>(s_body)[i] = reinterpret_cast<const float*>(a.bodies)[i];
-  for (int i = tid; i < kMaxBodies * 7; i += kThreads) (&s_bb[0][0])[i] = 0.0;
+  for (int i = tid; i < kMaxBodies * kAdjBodySlots; i += kThreads) (&s_bb[0][0])[i] = 0.0;
   __syncthreads();
   Barrier B{a.bar, (unsigned)nblk, a.status, a.poison};
   const int gtid = blockIdx.x * kThreads + tid;
@@ -1367,6 +1367,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
       for (int r = 0; r < 3; ++r) {
         atomicAdd(a.pbar + r * np + slot, xb[r] + xw[r]);
         atomicAdd(a.pbar + (3 + r) * np + slot, vb[r]);
+        // the contact geometry depends on x_p - p_body: dL/dp = -(its part of
+        // dL/dx_p); the body velocity enters n0 through -v: dL/dv gets -vbar
+        atomicAdd(&s_bb[body][7 + r], -(double)xb[r]);
+        atomicAdd(&s_bb[body][10 + r], -(double)vb[r]);
       }
     }
     if (lane == 0) {
@@ -1389,7 +1393,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
     }
   }
   __syncthreads();
-  for (int i = tid; i < a.nb * 7; i += kThreads) {
+  for (int i = tid; i < a.nb * kAdjBodySlots; i += kThreads) {
     const double v = (&s_bb[0][0])[i];
     if (v != 0.0) atomicAdd(a.body_bar + i, v);
   }

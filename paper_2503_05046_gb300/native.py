@@ -355,7 +355,8 @@ def mpm_backward(ctx, n, n_groups, n_bodies, x_bar=None, v_bar=None, C_bar=None,
 
     The four cotangents are numpy arrays (host) or CUDA tensors (device, all
     alike; None for zero). Returns dict(x, v, C, F: adjoints of the first
-    recorded state, E, nu: [n_groups], mu: [n_bodies], stats, status)."""
+    recorded state, E, nu: [n_groups], mu: [n_bodies], body_v, body_p: [n_bodies, 3]
+    (dL/d linear velocity, dL/d initial position), stats, status)."""
     given = [a for a in (x_bar, v_bar, C_bar, F_bar) if a is not None]
     device = bool(given) and not isinstance(given[0], np.ndarray)
     shapes = ((n, 3), (n, 3), (n, 3, 3), (n, 3, 3))
@@ -375,16 +376,17 @@ def mpm_backward(ctx, n, n_groups, n_bodies, x_bar=None, v_bar=None, C_bar=None,
         optr = [o.ctypes.data for o in outs]
         kind = MEM_HOST
     mat = np.zeros(2 * max(n_groups, 1))
-    mu = np.zeros(max(n_bodies, 1))
+    bodyb = np.zeros((max(n_bodies, 1), 7))
     st = BackwardStats()
     params = AdjointParams(float(eps_r), int(max_iters))
-    code = lib.mpm_backward(ctx, kind, *iptr, *optr, mat.ctypes.data, mu.ctypes.data,
+    code = lib.mpm_backward(ctx, kind, *iptr, *optr, mat.ctypes.data, bodyb.ctypes.data,
                             C.byref(params), C.byref(st))
     if check:
         _check(ctx, code)
     return {"x": outs[0], "v": outs[1], "C": outs[2], "F": outs[3],
             "E": mat[0:2 * n_groups:2].copy(), "nu": mat[1:2 * n_groups:2].copy(),
-            "mu": mu[:n_bodies].copy(), "stats": st, "status": code}
+            "mu": bodyb[:n_bodies, 0].copy(), "body_v": bodyb[:n_bodies, 1:4].copy(),
+            "body_p": bodyb[:n_bodies, 4:7].copy(), "stats": st, "status": code}
 
 
 def mpm_synchronize(ctx):

@@ -162,9 +162,14 @@ def test_adjoint_device_buffers_match_host(solved):
     d = sim.contact_adjoint(torch.from_numpy(ids).cuda(), torch.from_numpy(vbar).cuda(), eps_r=1e-6,
                             max_iters=5000)
     assert h[4] == native.OK and d[4] == native.OK
-    for a, b_ in zip(h[:3], d[:3]):
+    for a, b_ in zip(h[:2], d[:2]):
         b_ = b_.cpu().numpy()
         assert np.allclose(a, b_, rtol=1e-4, atol=1e-5 * np.max(np.abs(a)))
+    # the per-body sums cancel strongly (contacts pull both ways) and the
+    # solve's atomic accumulation order varies between runs: bound their
+    # difference by the rounding of the summed magnitudes
+    scale = np.abs(h[1][:, :3]).sum()
+    assert np.all(np.abs(h[2] - d[2].cpu().numpy()) <= 1e-4 * scale)
 
 
 def test_adjoint_errors(solved):

@@ -3,9 +3,9 @@ functional of the final state of a short rollout (the differentiation
 workload in miniature: a lattice cube of elastic material or of
 Drucker-Prager sand on the ground, pushed by a kinematic box; 2 rigid steps
 of 5 substeps) with respect to the initial state, E, nu and each body's mu,
-by central differences of the oracle's rollout (Eq. (3)-(8), FP64, tightly
-solved), compared with the inner product of the CUDA path's adjoint and the
-same direction."""
+and the bodies' linear velocity and position, by central differences of the
+oracle's rollout (Eq. (3)-(8), FP64, tightly solved), compared with the inner
+product of the CUDA path's adjoint and the same direction."""
 import numpy as np
 import pytest
 
@@ -96,6 +96,15 @@ def _fd_mu(sc, cot, b, eps):
     return (_loss(sc, cot, bodies=bp) - _loss(sc, cot, bodies=bm)) / (2 * eps)
 
 
+def _fd_body(sc, cot, b, key, c, eps):
+    bp, bm = O.bodies_from_scene(sc), O.bodies_from_scene(sc)
+    bp[b][key] = np.array(bp[b][key], np.float64)
+    bm[b][key] = np.array(bm[b][key], np.float64)
+    bp[b][key][c] += eps
+    bm[b][key][c] -= eps
+    return (_loss(sc, cot, bodies=bp) - _loss(sc, cot, bodies=bm)) / (2 * eps)
+
+
 def test_forward_matches_oracle(case):
     native, sc, cot, out, final = case
     st, code = O.rollout(sc, STEPS, O.solver(**ORC_SOLVER), state=sc["init"])
@@ -122,6 +131,12 @@ def test_parameter_adjoint(case):
             ("nu", _fd_material(sc, cot, "nu", 1e-6), out["nu"][0])]
     for b in range(len(sc["bodies"])):
         rows.append(("mu%d" % b, _fd_mu(sc, cot, b, 1e-6), out["mu"][b]))
+    # the pushing box (kinematic: its position advances with v) and the
+    # ground's velocity (static: it enters the contacts' bias only)
+    for c in (0, 2):
+        rows.append(("v1_%d" % c, _fd_body(sc, cot, 1, "v", c, 1e-6), out["body_v"][1][c]))
+        rows.append(("p1_%d" % c, _fd_body(sc, cot, 1, "p", c, 1e-8), out["body_p"][1][c]))
+    rows.append(("v0_0", _fd_body(sc, cot, 0, "v", 0, 1e-6), out["body_v"][0][0]))
     for name, fd, got in rows:
         print("d/d%s: fd %.6e adjoint %.6e rel %.2e" % (name, fd, got, abs(got - fd) / max(abs(fd), 1e-300)))
     for name, fd, got in rows:
