@@ -1,10 +1,11 @@
 """torch.autograd binding of a differentiable rollout.
 
-`rollout(sim, n_steps, x0, v0, E, nu, mu, solver)` runs `n_steps` rigid time
-steps of the context held by `sim` (native.Sim) from the particle positions
-x0 and velocities v0 (C = 0, F = I), with Young's modulus E and Poisson ratio
-nu per particle group and friction coefficient mu per rigid body, and returns
-the final positions and velocities. Its backward pass is the library's
+`rollout(sim, n_steps, x0, v0, E, nu, mu, solver, body_v=...)` runs `n_steps`
+rigid time steps of the context held by `sim` (native.Sim) from the particle
+positions x0 and velocities v0 (C = 0, F = I), with Young's modulus E and
+Poisson ratio nu per particle group, friction coefficient mu and linear
+velocity body_v per rigid body, and returns the final positions and
+velocities. Its backward pass is the library's
 hand-written adjoint (mpm_backward: checkpoints per step, the adjoints of
 G2P, the contact solve by implicit differentiation, the grid update and
 P2G); nothing is traced or taped by torch.
@@ -17,7 +18,7 @@ from . import native
 
 class _Rollout(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, sim, n_steps, solver, eps_r, x0, v0, E, nu, mu):
+    def forward(ctx, sim, n_steps, solver, eps_r, x0, v0, E, nu, mu, body_v):
         n = sim.n
         for gi, g in enumerate(sim.scene["groups"]):
             m = dict(g["material"], E=float(E[gi]), nu=float(nu[gi]))
@@ -25,6 +26,8 @@ class _Rollout(torch.autograd.Function):
         bodies = sim.bodies()
         for b, mb in zip(bodies, mu.detach().cpu().numpy()):
             b["mu"] = float(mb)
+        for b, vb in zip(bodies, body_v.detach().cpu().numpy().reshape(-1, 3)):
+            b["v"] = np.asarray(vb, np.float64)
         sim.set_bodies(bodies)
         x = x0.detach().to(torch.float32).cpu().numpy().reshape(n, 3)
         v = v0.detach().to(torch.float32).cpu().numpy().reshape(n, 3)
@@ -38,7 +41,7 @@ class _Rollout(torch.autograd.Function):
         out = sim.get_particles()
         ctx.sim = sim
         ctx.eps_r = eps_r
-        ctx.like = [(a.device, a.dtype) for a in (x0, v0, E, nu, mu)]
+        ctx.like = [(a.device, a.dtype) for a in (x0, v0, E, nu, mu, body_v)]
         xf = torch.from_numpy(out["x"]).to(x0.device)
         vf = torch.from_numpy(out["v"]).to(x0.device)
         return xf, vf
@@ -48,13 +51,16 @@ class _Rollout(torch.autograd.Function):
         sim = ctx.sim
         g = sim.backward(x_bar=None if gx is None else gx.detach().cpu().numpy(),
                          v_bar=None if gv is None else gv.detach().cpu().numpy(), eps_r=ctx.eps_r)
-        grads = [np.asarray(g[k]) for k in ("x", "v", "E", "nu", "mu")]
+        grads = [np.asarray(g[k]) for k in ("x", "v", "E", "nu", "mu", "body_v")]
         out = [torch.as_tensor(a, dtype=dt, device=dev) for a, (dev, dt) in zip(grads, ctx.like)]
         return (None, None, None, None, *out)
 
 
-def rollout(sim, n_steps, x0, v0, E, nu, mu, solver=None, eps_r=1e-6):
+def rollout(sim, n_steps, x0, v0, E, nu, mu, solver=None, eps_r=1e-6, body_v=None):
     """Differentiable rollout (see the module docstring). x0, v0: [n, 3]
-    tensors; E, nu: [n_groups] tensors; mu: [n_bodies] tensor. Returns the
-    final (x, v). The materials must be corotated (the adjoint's scope)."""
-    return _Rollout.apply(sim, n_steps, solver, eps_r, x0, v0, E, nu, mu)
+    tensors; E, nu: [n_groups] tensors; mu: [n_bodies] tensor; body_v:
+    optional [n_bodies, 3] tensor of the bodies' linear velocities (default:
+    as they are). Returns the final (x, v)."""
+    if body_v is None:
+        body_v = torch.tensor(np.array([b["v"] for b in sim.bodies()], np.float64).reshape(-1, 3))
+    return _Rollout.apply(sim, n_steps, solver, eps_r, x0, v0, E, nu, mu, body_v)

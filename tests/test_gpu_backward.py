@@ -146,8 +146,8 @@ def test_parameter_adjoint(case):
 def test_autograd_rollout(case):
     """The torch.autograd binding: a nonlinear loss (squared centroid
     distance plus a velocity term) through the rollout; E.grad, nu.grad,
-    mu.grad and a direction of v0.grad against central differences of the
-    oracle's rollout."""
+    mu.grad, the pushing box's velocity gradient and a direction of v0.grad
+    against central differences of the oracle's rollout."""
     import torch
     from paper_2503_05046_gb300 import autograd
     native, sc, cot, out, final = case
@@ -168,9 +168,11 @@ def test_autograd_rollout(case):
     nu = torch.tensor([float(np.float32(mat["nu"]))], dtype=torch.float64, requires_grad=True)
     mu = torch.tensor([float(np.float32(b["mu"])) for b in sc["bodies"]], dtype=torch.float64,
                       requires_grad=True)
+    bv = torch.tensor(np.array([np.float32(b["v"]) for b in sc["bodies"]], np.float64),
+                      requires_grad=True)
     sim = native.Sim(sc)
     xf, vf = autograd.rollout(sim, STEPS, x0, v0, E, nu, mu,
-                              solver=native.solver_params(**GPU_SOLVER))
+                              solver=native.solver_params(**GPU_SOLVER), body_v=bv)
     L = ((xf.double().mean(0) - torch.tensor(target, device="cuda")) ** 2).sum() + \
         (vf.double() * torch.tensor(wv, device="cuda")).sum()
     L.backward()
@@ -197,6 +199,11 @@ def test_autograd_rollout(case):
         bm[b]["mu"] -= 1e-6
         fd = (orc(bodies=bp) - orc(bodies=bm)) / 2e-6
         assert abs(mu.grad[b].item() - fd) <= 2e-3 * abs(fd), b
+    bp, bm = O.bodies_from_scene(sc), O.bodies_from_scene(sc)
+    bp[1]["v"] = np.array(bp[1]["v"]) + np.array([1e-6, 0.0, 0.0])
+    bm[1]["v"] = np.array(bm[1]["v"]) - np.array([1e-6, 0.0, 0.0])
+    fd = (orc(bodies=bp) - orc(bodies=bm)) / 2e-6
+    assert abs(bv.grad[1, 0].item() - fd) <= 2e-3 * abs(fd)
     st0 = sc["init"]
     dv = np.random.default_rng(13).normal(size=(n, 3))
     sp, sm = dict(st0), dict(st0)
