@@ -386,13 +386,13 @@ typedef struct {
    Outputs (NULL to skip): the same four for the state at the start of the
    first recorded step; material_bar [n_groups][2] doubles = dL/dE, dL/dnu
    per particle group (in the order the groups were added); body_bar
-   [n_bodies][7] doubles per body index = dL/dmu, dL/dv (3) and dL/dp (3),
-   where v is the body's (frozen) linear velocity over the recorded steps and
-   p its position at the first one: v and p enter every contact's bias,
-   lagged normal impulse and geometry (through x - p), and a kinematic
-   body's position advances by n_substeps h v after each step. Rigid bodies
-   are otherwise inputs: their recorded orientations and angular velocities
-   are replayed and not differentiated.
+   [n_bodies][13] doubles per body index = dL/dmu, dL/dv (3), dL/dp (3),
+   dL/domega (3) and dL/dtheta (3), where v and omega are the body's (frozen)
+   linear and angular velocity over the recorded steps, p its position at the
+   first one and theta a rotation of its orientation R there (R -> exp([theta]x) R,
+   world frame): they enter every contact's bias, lagged normal impulse and
+   geometry (through R^T (x - p)), and a kinematic body's pose advances by
+   n_substeps h (v, omega) after each step.
    The contact solve's adjoint is solved to params->eps_r (NULL: 1e-6, 2000
    iterations); the implicit gradient is exact at an exact minimiser, so the
    recorded steps should use a tight solver tolerance.

@@ -1388,18 +1388,58 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
     auto S = [&](int t, int b, int k) {
       return t >= T ? 0.0 : snap[((size_t)t * kMaxBodies + b) * kAdjBodySlots + k];
     };
+    // Orientation: a kinematic body's R_t = exp(T_t [omega]x) R_0 (T_t the
+    // time advanced before step t), so a left rotation dtheta_t = J_l(T_t
+    // omega) T_t domega + exp(T_t [omega]x) dtheta_0, with J_l the left
+    // Jacobian of SO(3): dL/domega adds T_t J_l^T theta_bar_t, dL/dtheta_0 =
+    // sum exp(-T_t [omega]x) theta_bar_t.
+    auto rodrigues = [](const double* ph, const double* x, double sgn, double* out) {
+      // exp(sgn [ph]x) x
+      const double th = std::sqrt(ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
+      const double a = th > 1e-12 ? std::sin(th) / th : 1.0;
+      const double b = th > 1e-6 ? (1.0 - std::cos(th)) / (th * th) : 0.5;
+      const double px[3] = {ph[1] * x[2] - ph[2] * x[1], ph[2] * x[0] - ph[0] * x[2], ph[0] * x[1] - ph[1] * x[0]};
+      const double ppx[3] = {ph[1] * px[2] - ph[2] * px[1], ph[2] * px[0] - ph[0] * px[2], ph[0] * px[1] - ph[1] * px[0]};
+      for (int c = 0; c < 3; ++c) out[c] = x[c] + sgn * a * px[c] + b * ppx[c];
+    };
+    auto jl_transpose = [](const double* ph, const double* x, double* out) {
+      // J_l(ph)^T x = x - ((1 - cos)/th^2) ph x x + ((th - sin)/th^3) ph x (ph x x)
+      const double th = std::sqrt(ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
+      const double b = th > 1e-6 ? (1.0 - std::cos(th)) / (th * th) : 0.5;
+      const double c3 = th > 1e-4 ? (th - std::sin(th)) / (th * th * th) : 1.0 / 6.0;
+      const double px[3] = {ph[1] * x[2] - ph[2] * x[1], ph[2] * x[0] - ph[0] * x[2], ph[0] * x[1] - ph[1] * x[0]};
+      const double ppx[3] = {ph[1] * px[2] - ph[2] * px[1], ph[2] * px[0] - ph[0] * px[2], ph[0] * px[1] - ph[1] * px[0]};
+      for (int c = 0; c < 3; ++c) out[c] = x[c] - b * px[c] + c3 * ppx[c];
+    };
     for (int b = 0; b < nb_max; ++b) {
-      double* o = body_bar + 7 * b;
+      double* o = body_bar + 13 * b;
       o[0] = S(0, b, 6);
       for (int c = 0; c < 3; ++c) {
         o[1 + c] = S(0, b, c) + S(0, b, 10 + c);
         o[4 + c] = S(0, b, 7 + c);
+        o[7 + c] = S(0, b, 3 + c) + S(0, b, 16 + c);
+        o[10 + c] = 0.0;
       }
+      const double w[3] = {ctx->tape[0].bodies[b].w[0], ctx->tape[0].bodies[b].w[1],
+                           ctx->tape[0].bodies[b].w[2]};
       double offset = 0.0;
       for (int t = 0; t < T; ++t) {
         const auto& tk = ctx->tape[t];
         if (b >= (int)tk.bodies.size()) break;
-        for (int c = 0; c < 3; ++c) o[1 + c] += offset * (S(t, b, 7 + c) - S(t + 1, b, 7 + c));
+        double pb[3], rb[3];
+        for (int c = 0; c < 3; ++c) {
+          pb[c] = S(t, b, 7 + c) - S(t + 1, b, 7 + c);
+          rb[c] = S(t, b, 13 + c) - S(t + 1, b, 13 + c);
+          o[1 + c] += offset * pb[c];
+        }
+        const double ph[3] = {offset * w[0], offset * w[1], offset * w[2]};
+        double jt[3], r0[3];
+        jl_transpose(ph, rb, jt);
+        rodrigues(ph, rb, -1.0, r0);
+        for (int c = 0; c < 3; ++c) {
+          o[7 + c] += offset * jt[c];
+          o[10 + c] += r0[c];
+        }
         if (tk.kinematic[b]) offset += (double)tk.n_substeps * (double)tk.h;
       }
     }

@@ -137,10 +137,12 @@ struct AdjointArgs {
 };
 constexpr int kAdjointVectors = 13;
 // per-body adjoint accumulators: dL/dv_r through the bias (3), its moment
-// about the body origin (3), dL/dmu, and in mpm_backward mode dL/dp of the
-// body position through the contact geometry (3) and dL/dv through the
-// lagged normal impulse (3)
-constexpr int kAdjBodySlots = 13;
+// about the body origin (= dL/domega through the bias, 3), dL/dmu, and in
+// mpm_backward mode dL/dp of the body position through the contact geometry
+// (3), dL/dv through the lagged normal impulse (3), the adjoint of a left
+// rotation of the body's orientation (3) and dL/domega through the lagged
+// normal impulse (3)
+constexpr int kAdjBodySlots = 19;
 cudaError_t launch_adjoint(const AdjointArgs& a, int grid_blocks, cudaStream_t s);
 const void* adjoint_kernel_ptr();
 

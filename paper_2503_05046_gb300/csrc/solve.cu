@@ -852,7 +852,8 @@ __device__ __forceinline__ void lane_weight_grad(const GridDev& g, const float4&
 __device__ void contact_input_adjoint(const AdjHess& A, const DevBody& bd, const float4& xp,
                                       const float4& vc, const float4& bias, const float (&vp)[3],
                                       float h, const double (&xi)[3], const double (&y)[3],
-                                      float (&xb)[3], float (&vb)[3]) {
+                                      float (&xb)[3], float (&vb)[3], double (&rot)[3],
+                                      double (&wdir)[3]) {
   const double n[3] = {A.n[0], A.n[1], A.n[2]}, t[3] = {A.ut[0], A.ut[1], A.ut[2]};
   const double u[3] = {vc.x, vc.y, vc.z};
   const double un = n[0] * u[0] + n[1] * u[1] + n[2] * u[2];
@@ -913,6 +914,21 @@ __device__ void contact_input_adjoint(const AdjHess& A, const DevBody& bd, const
 #pragma unroll
   for (int c = 0; c < 3; ++c)
     xb[c] = (float)(-phi0bar * n[c] + wxb[c] + vn0bar * wxn[c] + dn[c]);
+  // The body's orientation (a rotation dtheta about p): the body-frame point
+  // moves as x would by r x dtheta (r = x_p - p), which the depth and the
+  // normal's x-dependence see, and the normal turns with the body
+  // (dn = dtheta x n); the bias does not depend on it. Left-perturbation
+  // adjoint: rot = (-phi0bar n + dn) x r + n x nbar.
+  const double r[3] = {(double)xp.x - bd.p[0], (double)xp.y - bd.p[1], (double)xp.z - bd.p[2]};
+  const double g[3] = {-phi0bar * n[0] + dn[0], -phi0bar * n[1] + dn[1], -phi0bar * n[2] + dn[2]};
+  rot[0] = g[1] * r[2] - g[2] * r[1] + n[1] * nbar[2] - n[2] * nbar[1];
+  rot[1] = g[2] * r[0] - g[0] * r[2] + n[2] * nbar[0] - n[0] * nbar[2];
+  rot[2] = g[0] * r[1] - g[1] * r[0] + n[0] * nbar[1] - n[1] * nbar[0];
+  // the angular velocity through the lagged normal impulse:
+  // vn0 = n . (v_p - v - omega x r) -> -vn0bar (r x n)
+  wdir[0] = -vn0bar * (r[1] * n[2] - r[2] * n[1]);
+  wdir[1] = -vn0bar * (r[2] * n[0] - r[0] * n[2]);
+  wdir[2] = -vn0bar * (r[0] * n[1] - r[1] * n[0]);
 }
 
 // y = d2l_c u (FP32)
@@ -1361,7 +1377,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
       const int slot = a.slot_of[a.C.id[p].x];
       const float vp[3] = {a.P.v(0)[slot], a.P.v(1)[slot], a.P.v(2)[slot]};
       float xb[3], vb[3];
-      contact_input_adjoint(A, s_body[body], xp, a.C.vc[p], a.C.bias[p], vp, a.h, u, yd, xb, vb);
+      double rot[3], wdir[3];
+      contact_input_adjoint(A, s_body[body], xp, a.C.vc[p], a.C.bias[p], vp, a.h, u, yd, xb, vb,
+                            rot, wdir);
       const size_t np = (size_t)a.n_particles;
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
@@ -1371,6 +1389,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
         // dL/dx_p); the body velocity enters n0 through -v: dL/dv gets -vbar
         atomicAdd(&s_bb[body][7 + r], -(double)xb[r]);
         atomicAdd(&s_bb[body][10 + r], -(double)vb[r]);
+        atomicAdd(&s_bb[body][13 + r], rot[r]);
+        atomicAdd(&s_bb[body][16 + r], wdir[r]);
       }
     }
     if (lane == 0) {

@@ -355,8 +355,9 @@ def mpm_backward(ctx, n, n_groups, n_bodies, x_bar=None, v_bar=None, C_bar=None,
 
     The four cotangents are numpy arrays (host) or CUDA tensors (device, all
     alike; None for zero). Returns dict(x, v, C, F: adjoints of the first
-    recorded state, E, nu: [n_groups], mu: [n_bodies], body_v, body_p: [n_bodies, 3]
-    (dL/d linear velocity, dL/d initial position), stats, status)."""
+    recorded state, E, nu: [n_groups], mu: [n_bodies], body_v, body_p, body_w,
+    body_R: [n_bodies, 3] (dL/d linear velocity, initial position, angular
+    velocity, initial orientation as a world-frame rotation), stats, status)."""
     given = [a for a in (x_bar, v_bar, C_bar, F_bar) if a is not None]
     device = bool(given) and not isinstance(given[0], np.ndarray)
     shapes = ((n, 3), (n, 3), (n, 3, 3), (n, 3, 3))
@@ -376,7 +377,7 @@ def mpm_backward(ctx, n, n_groups, n_bodies, x_bar=None, v_bar=None, C_bar=None,
         optr = [o.ctypes.data for o in outs]
         kind = MEM_HOST
     mat = np.zeros(2 * max(n_groups, 1))
-    bodyb = np.zeros((max(n_bodies, 1), 7))
+    bodyb = np.zeros((max(n_bodies, 1), 13))
     st = BackwardStats()
     params = AdjointParams(float(eps_r), int(max_iters))
     code = lib.mpm_backward(ctx, kind, *iptr, *optr, mat.ctypes.data, bodyb.ctypes.data,
@@ -386,7 +387,8 @@ def mpm_backward(ctx, n, n_groups, n_bodies, x_bar=None, v_bar=None, C_bar=None,
     return {"x": outs[0], "v": outs[1], "C": outs[2], "F": outs[3],
             "E": mat[0:2 * n_groups:2].copy(), "nu": mat[1:2 * n_groups:2].copy(),
             "mu": bodyb[:n_bodies, 0].copy(), "body_v": bodyb[:n_bodies, 1:4].copy(),
-            "body_p": bodyb[:n_bodies, 4:7].copy(), "stats": st, "status": code}
+            "body_p": bodyb[:n_bodies, 4:7].copy(), "body_w": bodyb[:n_bodies, 7:10].copy(),
+            "body_R": bodyb[:n_bodies, 10:13].copy(), "stats": st, "status": code}
 
 
 def mpm_synchronize(ctx):

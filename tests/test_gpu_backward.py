@@ -46,6 +46,7 @@ def case(request):
     from paper_2503_05046_gb300 import native
     sand = request.param == "sand"
     sc, _ = scenes.push_cube(**SCENE, material=scenes.SAND if sand else None)
+    sc["bodies"][1]["omega"] = np.array([0.0, 0.0, 0.5])  # the box also turns
     sc["init"] = _initial_state(sc, sand)
     n = scenes.n_particles(sc)
     rng = np.random.default_rng(11)
@@ -98,10 +99,20 @@ def _fd_mu(sc, cot, b, eps):
 
 def _fd_body(sc, cot, b, key, c, eps):
     bp, bm = O.bodies_from_scene(sc), O.bodies_from_scene(sc)
-    bp[b][key] = np.array(bp[b][key], np.float64)
-    bm[b][key] = np.array(bm[b][key], np.float64)
-    bp[b][key][c] += eps
-    bm[b][key][c] -= eps
+    if key == "R":  # a world-frame rotation of the orientation about axis c
+        def turned(R, t):
+            k = np.zeros(3)
+            k[c] = 1.0
+            K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+            Q = np.eye(3) + np.sin(t) * K + (1 - np.cos(t)) * K @ K
+            return Q @ np.asarray(R, np.float64).reshape(3, 3)
+        bp[b]["R"] = turned(bp[b]["R"], eps)
+        bm[b]["R"] = turned(bm[b]["R"], -eps)
+    else:
+        bp[b][key] = np.array(bp[b][key], np.float64)
+        bm[b][key] = np.array(bm[b][key], np.float64)
+        bp[b][key][c] += eps
+        bm[b][key][c] -= eps
     return (_loss(sc, cot, bodies=bp) - _loss(sc, cot, bodies=bm)) / (2 * eps)
 
 
@@ -137,10 +148,17 @@ def test_parameter_adjoint(case):
         rows.append(("v1_%d" % c, _fd_body(sc, cot, 1, "v", c, 1e-6), out["body_v"][1][c]))
         rows.append(("p1_%d" % c, _fd_body(sc, cot, 1, "p", c, 1e-8), out["body_p"][1][c]))
     rows.append(("v0_0", _fd_body(sc, cot, 0, "v", 0, 1e-6), out["body_v"][0][0]))
+    # angular velocity and orientation of the turning box; a tilt of the ground
+    for c in (0, 2):
+        rows.append(("w1_%d" % c, _fd_body(sc, cot, 1, "omega", c, 1e-6), out["body_w"][1][c]))
+        rows.append(("R1_%d" % c, _fd_body(sc, cot, 1, "R", c, 1e-7), out["body_R"][1][c]))
+    rows.append(("R0_0", _fd_body(sc, cot, 0, "R", 0, 1e-7), out["body_R"][0][0]))
     for name, fd, got in rows:
         print("d/d%s: fd %.6e adjoint %.6e rel %.2e" % (name, fd, got, abs(got - fd) / max(abs(fd), 1e-300)))
+    scale = max(abs(fd) for _, fd, _ in rows if _ is not None)
     for name, fd, got in rows:
-        assert abs(got - fd) <= 2e-3 * abs(fd), name
+        # (a derivative that vanishes by symmetry is compared absolutely)
+        assert abs(got - fd) <= 2e-3 * abs(fd) or abs(got - fd) <= 1e-9 * scale, name
 
 
 def test_autograd_rollout(case):
