@@ -382,7 +382,10 @@ typedef struct {
    memory is one checkpoint per step plus one step's substep states.
 
    Inputs, in id order and caller layout (x, v [n][3]; C, F [n][3][3]), any
-   may be NULL for zero: dL/dx, dL/dv, dL/dC, dL/dF of the final state.
+   may be NULL for zero: dL/dx, dL/dv, dL/dC, dL/dF of the final state; and
+   body_state_bar [n_bodies][12] doubles (host memory, NULL for zero): dL/dv,
+   dL/dp, dL/domega, dL/dtheta of each body's state after the last step
+   (theta a world-frame rotation R -> exp([theta]x) R).
    Outputs (NULL to skip): the same four for the state at the start of the
    first recorded step; material_bar [n_groups][2] doubles = dL/dE, dL/dnu
    per particle group (in the order the groups were added); body_bar
@@ -392,23 +395,29 @@ typedef struct {
    first one and theta a rotation of its orientation R there (R -> exp([theta]x) R,
    world frame): they enter every contact's bias, lagged normal impulse and
    geometry (through R^T (x - p)), and a kinematic body's pose advances by
-   n_substeps h (v, omega) after each step.
+   n_substeps h (v, omega) after each step. For a dynamic body
+   (mpm_set_rigid_dynamics) v, omega, p, theta are its state at the first
+   recorded step and the backward runs through each rigid step of Eq. (3):
+   the step's impulse and moment depend on the contact solves (their
+   cotangents enter the implicit differentiation as an extra right-hand side
+   and in the contact terms), and the state's own update is differentiated
+   on the host. A body must keep its kind over the tape.
    The contact solve's adjoint is solved to params->eps_r (NULL: 1e-6, 2000
    iterations); the implicit gradient is exact at an exact minimiser, so the
    recorded steps should use a tight solver tolerance.
    The return map's branch boundaries (tension, the yield cone) and the
    Hencky clamp are kinks where the one-sided derivatives differ; sand
    starting exactly at F = I with a uniform velocity sits on one.
-   Requires: a tape; the same particles; no dynamic bodies in the recorded
-   steps (MPM_ERR_STATE otherwise).
+   Requires: a tape; the same particles (MPM_ERR_STATE otherwise).
    Synchronises; afterwards the particle state is the final state again, the
    impulse accumulators are as before, and the tape is kept; the grid and
    contacts hold a replayed substep, so mpm_contact_adjoint needs an
    mpm_step first (MPM_ERR_STATE otherwise). */
 mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, const float* v_bar,
-                        const float* C_bar, const float* F_bar, float* x0_bar, float* v0_bar,
-                        float* C0_bar, float* F0_bar, double* material_bar, double* body_bar,
-                        const mpm_adjoint_params* params, mpm_backward_stats* stats);
+                        const float* C_bar, const float* F_bar, const double* body_state_bar,
+                        float* x0_bar, float* v0_bar, float* C0_bar, float* F0_bar,
+                        double* material_bar, double* body_bar, const mpm_adjoint_params* params,
+                        mpm_backward_stats* stats);
 
 /* Wait for the context's stream and report any device-side failure. */
 mpm_status mpm_synchronize(mpm_ctx* ctx);

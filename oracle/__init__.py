@@ -410,30 +410,44 @@ def advance_kinematic(bodies, dt):
     return [body_dict(bs[i]) for i in range(nb)]
 
 
-def rollout(scene, steps, S, materials=None, bodies=None, state=None, substeps=None):
+def rollout(scene, steps, S, materials=None, bodies=None, state=None, substeps=None,
+            dynamics=None, with_bodies=False):
     """Asynchronous time splitting (Sec. IV-A, Eq. (3)-(4)): `steps` rigid time
     steps of `substeps` (default scene["substeps"]) MPM substeps each, the
-    rigid bodies frozen within a step and the kinematic ones advanced by
-    substeps*h after it. Oracle state, materials and bodies default to the
-    scene's (from_scene, bodies_from_scene); returns the final FP64 state and
-    the first non-OK substep status (OK if none)."""
+    rigid bodies frozen within a step; after it the kinematic ones advance by
+    substeps*h and the dynamic ones (`dynamics`: body index -> dict as
+    make_dynamics; their kinematic flag is ignored) take the rigid step of
+    Eq. (3) with the step's accumulated impulses. Oracle state, materials and
+    bodies default to the scene's (from_scene, bodies_from_scene); returns
+    the final FP64 state, the first non-OK substep status (OK if none) and,
+    with with_bodies, the final bodies."""
     st0, mats0 = from_scene(scene)
     st = Sim.state(st0 if state is None else state)
     mats = mats0 if materials is None else materials
     bds = bodies_from_scene(scene) if bodies is None else [dict(b) for b in bodies]
     n_sub = scene["substeps"] if substeps is None else substeps
+    dyn = dynamics or {}
+    grav = scene["grid"].get("gravity", (0.0, 0.0, -9.81))
     sim = Sim(scene["grid"])
     code = OK
     try:
         for _ in range(steps):
+            imp = np.zeros(6 * max(len(bds), 1))
             for _ in range(n_sub):
-                c, _ = sim.substep(st, mats, bds, scene["h"], S)
+                c, _ = sim.substep(st, mats, bds, scene["h"], S, imp)
                 if code == OK and c != OK:
                     code = c
-            bds = advance_kinematic(bds, n_sub * scene["h"])
+            nxt = advance_kinematic([dict(b, kinematic=0) if i in dyn else b
+                                     for i, b in enumerate(bds)], n_sub * scene["h"])
+            for i, d in dyn.items():
+                nxt[i] = rigid_dynamics_step(bds[i], d, grav, imp[6 * i:6 * i + 6], n_sub * scene["h"])
+                nxt[i]["kinematic"] = bds[i].get("kinematic", 0)
+            for i in range(len(nxt)):
+                nxt[i]["shape"] = int(bds[i]["shape"])
+            bds = nxt
     finally:
         sim.close()
-    return st, code
+    return (st, code, bds) if with_bodies else (st, code)
 
 
 def make_dynamics(dyn):

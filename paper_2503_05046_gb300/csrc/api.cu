@@ -92,10 +92,12 @@ struct mpm_ctx {
     int rec_base = 0;  // record index of the step's first substep solution
     std::vector<DevBody> bodies;
     std::vector<int> kinematic;  // per body: its pose advances by n_substeps h v after the step
+    std::vector<int> is_dyn;     // per body: integrated by the library after the step (Eq. (3))
+    std::vector<mpm_rigid_dynamics> dyn;
+    std::vector<double> imp;     // per body: the step's impulse and moment (6)
     int n_substeps = 0;
     float h = 0.f;
     mpm_solver_params sp{};
-    bool dynamic = false;
   };
   bool taping = false;
   int64_t tape_n = 0;
@@ -116,6 +118,7 @@ struct mpm_ctx {
   size_t bw_mat_cap = 0;
   double* bw_snap = nullptr;   // per recorded step: the body accumulators after it
   size_t bw_snap_cap = 0;
+  double* bw_gbody = nullptr;  // per body: the impulse and moment cotangents of a step
   std::string err;
 };
 
@@ -208,6 +211,35 @@ DevBody to_dev(const mpm_rigid_body& b) {
   return d;
 }
 
+// small 3-vector helpers for the rigid adjoint
+void cross3d(const double* a, const double* b, double* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// exp(sgn [ph]x) x (Rodrigues)
+void rot_apply(const double* ph, const double* x, double sgn, double* out) {
+  const double th = std::sqrt(ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
+  const double a = th > 1e-12 ? std::sin(th) / th : 1.0;
+  const double b = th > 1e-6 ? (1.0 - std::cos(th)) / (th * th) : 0.5;
+  double px[3], ppx[3];
+  cross3d(ph, x, px);
+  cross3d(ph, px, ppx);
+  for (int c = 0; c < 3; ++c) out[c] = x[c] + sgn * a * px[c] + b * ppx[c];
+}
+
+// J_l(ph)^T x, J_l the left Jacobian of SO(3)
+void jl_transpose(const double* ph, const double* x, double* out) {
+  const double th = std::sqrt(ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
+  const double b = th > 1e-6 ? (1.0 - std::cos(th)) / (th * th) : 0.5;
+  const double c3 = th > 1e-4 ? (th - std::sin(th)) / (th * th * th) : 1.0 / 6.0;
+  double px[3], ppx[3];
+  cross3d(ph, x, px);
+  cross3d(ph, px, ppx);
+  for (int c = 0; c < 3; ++c) out[c] = x[c] - b * px[c] + c3 * ppx[c];
+}
+
 // R <- exp(dt [omega]x) R, p <- p + dt v (kinematic bodies between time steps)
 void advance_kinematic(mpm_rigid_body& b, double dt) {
   for (int i = 0; i < 3; ++i) b.p[i] = (float)((double)b.p[i] + dt * b.v[i]);
@@ -224,6 +256,91 @@ void advance_kinematic(mpm_rigid_body& b, double dt) {
     for (int cc = 0; cc < 3; ++cc)
       R[3 * r + cc] = Q[3 * r] * b.R[cc] + Q[3 * r + 1] * b.R[3 + cc] + Q[3 * r + 2] * b.R[6 + cc];
   for (int i = 0; i < 9; ++i) b.R[i] = (float)R[i];
+}
+
+// Adjoint of integrate_dynamic. The state is (v, omega, p, theta) with theta
+// a left rotation of R (R -> exp([theta]x) R); sb[12] holds the adjoint of the
+// state after the step on entry and of the state before it on exit; jl[6]
+// receives the adjoints of the step's impulse J and moment L. With
+// v' = v + (dt f + J) / m, q = dt (tau - w x I_w w) + L, a = I_w^-1 q,
+// w' = w + a (masked), p' = p + dt v', R' = exp(dt [w']x) R:
+//   pbar = p'bar, thetabar = exp(-dt [w']x) theta'bar + (terms of I_w below),
+//   v'acc = v'bar + dt p'bar, w'acc = w'bar + dt J_l(dt w')^T theta'bar (masked),
+//   vbar = v'acc, Jbar = v'acc / m, z = I_w^-1 w'acc, Lbar = z,
+//   wbar = w'acc + dt (I_w (w x z) - (I_w w) x z),
+//   thetabar -= (I_w a) x z + (I_w z) x a + dt ((I_w w) x (z x w) + (I_w (z x w)) x w).
+void integrate_dynamic_adjoint(const DevBody& b, const mpm_rigid_dynamics& d, const double* gravity,
+                               const double* J, const double* L, double dt, double* sb, double* jl) {
+  const double m = d.mass;
+  double v2[3], w[3], R[9], Iw[9];
+  for (int i = 0; i < 3; ++i) {
+    const double f = d.force[i] + (d.gravity ? m * gravity[i] : 0.0);
+    v2[i] = b.v[i] + (dt * f + J[i]) / m;
+    w[i] = b.w[i];
+  }
+  for (int i = 0; i < 9; ++i) R[i] = b.R[i];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += R[3 * r + k] * (double)d.inertia[k] * R[3 * c + k];
+      Iw[3 * r + c] = acc;
+    }
+  auto mul = [&](const double* x, double* o) {
+    for (int r = 0; r < 3; ++r) o[r] = Iw[3 * r] * x[0] + Iw[3 * r + 1] * x[1] + Iw[3 * r + 2] * x[2];
+  };
+  const double A0 = Iw[4] * Iw[8] - Iw[5] * Iw[5], A1 = Iw[2] * Iw[5] - Iw[1] * Iw[8],
+               A2 = Iw[1] * Iw[5] - Iw[2] * Iw[4];
+  const double det = Iw[0] * A0 + Iw[1] * A1 + Iw[2] * A2;
+  const double inv[9] = {A0, A1, A2, A1, Iw[0] * Iw[8] - Iw[2] * Iw[2], Iw[1] * Iw[2] - Iw[0] * Iw[5],
+                         A2, Iw[1] * Iw[2] - Iw[0] * Iw[5], Iw[0] * Iw[4] - Iw[1] * Iw[1]};
+  auto solve = [&](const double* x, double* o) {
+    for (int r = 0; r < 3; ++r) o[r] = (inv[3 * r] * x[0] + inv[3 * r + 1] * x[1] + inv[3 * r + 2] * x[2]) / det;
+  };
+  double Iww[3], gyro[3], q[3], a[3], w2[3];
+  mul(w, Iww);
+  cross3d(w, Iww, gyro);
+  for (int i = 0; i < 3; ++i) q[i] = dt * (d.torque[i] - gyro[i]) + L[i];
+  solve(q, a);
+  for (int i = 0; i < 3; ++i) {
+    w2[i] = ((d.dof_mask >> (3 + i)) & 1) ? w[i] + a[i] : 0.0;
+    if (!((d.dof_mask >> i) & 1)) v2[i] = 0.0;
+  }
+  (void)v2;
+  const double* vb2 = sb;
+  const double* pb2 = sb + 3;
+  const double* wb2 = sb + 6;
+  const double* tb2 = sb + 9;
+  double ph[3] = {dt * w2[0], dt * w2[1], dt * w2[2]};
+  double tb[3], jt[3], vacc[3], wacc[3];
+  rot_apply(ph, tb2, -1.0, tb);
+  jl_transpose(ph, tb2, jt);
+  for (int i = 0; i < 3; ++i) {
+    vacc[i] = ((d.dof_mask >> i) & 1) ? vb2[i] + dt * pb2[i] : 0.0;
+    wacc[i] = ((d.dof_mask >> (3 + i)) & 1) ? wb2[i] + dt * jt[i] : 0.0;
+  }
+  double z[3], wz[3], Iwz_[3], Iw_wz[3], Iwwz[3], zw[3], Izw[3], t1[3], t2[3], t3[3], t4[3], Ia[3], Iz[3];
+  solve(wacc, z);
+  cross3d(w, z, wz);
+  mul(wz, Iwz_);
+  cross3d(Iww, z, Iw_wz);
+  cross3d(z, w, zw);
+  mul(zw, Izw);
+  mul(a, Ia);
+  mul(z, Iz);
+  cross3d(Ia, z, t1);
+  cross3d(Iz, a, t2);
+  cross3d(Iww, zw, t3);
+  cross3d(Izw, w, t4);
+  (void)Iwwz;
+  const double pb[3] = {pb2[0], pb2[1], pb2[2]};
+  for (int i = 0; i < 3; ++i) {
+    jl[i] = vacc[i] / m;
+    jl[3 + i] = z[i];
+    sb[i] = vacc[i];                                  // vbar
+    sb[3 + i] = pb[i];                                // pbar
+    sb[6 + i] = wacc[i] + dt * (Iwz_[i] - Iw_wz[i]);  // wbar
+    sb[9 + i] = tb[i] - (t1[i] + t2[i]) - dt * (t3[i] + t4[i]);  // thetabar
+  }
 }
 
 // Eq. (3) for one dynamic body over a time step dt with the step's impulse
@@ -346,7 +463,7 @@ void release(mpm_ctx* c) {
                   c->status, c->stats, c->impulses, c->sb.keys[0], c->sb.keys[1], c->sb.vals[0],
                   c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage, c->adj_vec, c->adj_body,
                   c->adj_out, c->adj_ids, c->adj_io, c->bw_buf, c->bw_gbar, c->bw_slot, c->bw_mat,
-                  c->tape_pool, c->tape_recs, c->tape_counters, c->bw_snap};
+                  c->tape_pool, c->tape_recs, c->tape_counters, c->bw_snap, c->bw_gbody};
   for (auto& t : c->tape)
     if (t.state) cudaFree(t.state);
   for (void* p : ptrs)
@@ -813,15 +930,18 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     launch_to_id_order(ctx->P[ctx->cur], (int)nn, t.state, t.state + 3 * nn, t.state + 6 * nn,
                        t.state + 15 * nn, s);
     for (int i = 0; i < nb; ++i) {
+      const bool d = i < (int)ctx->is_dyn.size() && ctx->is_dyn[i];
       t.bodies.push_back(to_dev(ctx->bodies[i]));
-      t.kinematic.push_back(ctx->bodies[i].kinematic != 0 && !(i < (int)ctx->is_dyn.size() && ctx->is_dyn[i]));
+      t.kinematic.push_back(ctx->bodies[i].kinematic != 0 && !d);
+      t.is_dyn.push_back(d ? 1 : 0);
+      t.dyn.push_back(d ? ctx->dyn[i] : mpm_rigid_dynamics{});
     }
+    t.imp.assign(6 * nb, 0.0);
     t.n_substeps = n_substeps;
     t.rec_base = ctx->tape_substeps;
     ctx->tape_substeps += n_substeps;
     t.h = (float)h;
     t.sp = sp;
-    for (int d : ctx->is_dyn) t.dynamic = t.dynamic || d;
     ctx->tape.push_back(std::move(t));
   }
   CU(cudaMemsetAsync(ctx->stats, 0, sizeof(DevStats), s));
@@ -905,6 +1025,11 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
         J[c] = now[6 * i + c] - ctx->imp_seen[6 * i + c];
         L[c] = now[6 * i + 3 + c] - ctx->imp_seen[6 * i + 3 + c];
       }
+      if (ctx->taping && n_substeps > 0 && !ctx->tape.empty())
+        for (int c = 0; c < 3; ++c) {
+          ctx->tape.back().imp[6 * i + c] = J[c];
+          ctx->tape.back().imp[6 * i + 3 + c] = L[c];
+        }
       integrate_dynamic(ctx->bodies[i], ctx->dyn[i], ctx->spec.gravity, J, L, dt);
     }
     ctx->imp_seen = now;
@@ -1210,9 +1335,10 @@ mpm_status ensure_adjoint_buffers(mpm_ctx* ctx) {
 }  // namespace
 
 mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, const float* v_bar,
-                        const float* C_bar, const float* F_bar, float* x0_bar, float* v0_bar,
-                        float* C0_bar, float* F0_bar, double* material_bar, double* body_bar,
-                        const mpm_adjoint_params* params, mpm_backward_stats* stats) {
+                        const float* C_bar, const float* F_bar, const double* body_state_bar,
+                        float* x0_bar, float* v0_bar, float* C0_bar, float* F0_bar,
+                        double* material_bar, double* body_bar, const mpm_adjoint_params* params,
+                        mpm_backward_stats* stats) {
   if (!ctx) return MPM_ERR_INVALID_ARG;
   if (mem_kind != MPM_MEM_HOST && mem_kind != MPM_MEM_DEVICE)
     return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_backward: bad mem_kind");
@@ -1225,8 +1351,14 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
   if (ctx->tape.empty()) return fail(ctx, MPM_ERR_STATE, "mpm_backward: no recorded steps (mpm_tape_begin)");
   if (ctx->n != ctx->tape_n)
     return fail(ctx, MPM_ERR_STATE, "mpm_backward: the particle count changed since the tape began");
+  // every body keeps its kind (dynamic, kinematic, static) over the tape
   for (const auto& t : ctx->tape)
-    if (t.dynamic) return fail(ctx, MPM_ERR_STATE, "mpm_backward: a recorded step had dynamic bodies");
+    for (size_t b = 0; b < t.bodies.size() && b < ctx->tape[0].bodies.size(); ++b)
+      if (t.is_dyn[b] != ctx->tape[0].is_dyn[b] || t.kinematic[b] != ctx->tape[0].kinematic[b])
+        return fail(ctx, MPM_ERR_STATE, "mpm_backward: a body changed kind within the tape");
+  bool any_dyn = false;
+  for (const auto& t : ctx->tape)
+    for (int d : t.is_dyn) any_dyn = any_dyn || d;
   mpm_status st = drain_status(ctx);
   if (st != MPM_OK) return st;
   st = ensure_adjoint_buffers(ctx);
@@ -1255,6 +1387,7 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
     CU(dalloc(&ctx->bw_mat, 2 * ng + 2));
     ctx->bw_mat_cap = 2 * ng + 2;
   }
+  if (any_dyn && !ctx->bw_gbody) CU(dalloc(&ctx->bw_gbody, 6 * kMaxBodies));
   const size_t nsnap = ctx->tape.size() * kMaxBodies * kAdjBodySlots;
   if (ctx->bw_snap_cap < nsnap) {
     if (ctx->bw_snap) cudaFree(ctx->bw_snap);
@@ -1293,11 +1426,29 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
   int in = 0;
   int substeps = 0;
   int nb_max = 0;
+  // dynamic bodies: the adjoint of their state (v, p, omega, theta) after the
+  // step being processed, carried back through each rigid step (Eq. (3))
+  const int nb_final = (int)ctx->tape.back().bodies.size();
+  std::vector<double> sbody(12 * kMaxBodies, 0.0), prev_snap(kMaxBodies * kAdjBodySlots, 0.0);
+  if (body_state_bar)
+    for (int i = 0; i < 12 * nb_final; ++i) sbody[i] = body_state_bar[i];
   for (int t = (int)ctx->tape.size() - 1; t >= 0; --t) {
     const mpm_ctx::TapeStep& T = ctx->tape[t];
     const int nb = (int)T.bodies.size();
     nb_max = nb > nb_max ? nb : nb_max;
     if (nb) CU(cudaMemcpyAsync(ctx->bodies_d, T.bodies.data(), nb * sizeof(DevBody), cudaMemcpyHostToDevice, s));
+    bool step_dyn = false;
+    for (int d : T.is_dyn) step_dyn = step_dyn || d;
+    if (step_dyn) {
+      std::vector<double> gb(6 * kMaxBodies, 0.0);
+      const double dt = (double)T.n_substeps * (double)T.h;
+      for (int b = 0; b < nb; ++b)
+        if (T.is_dyn[b])
+          integrate_dynamic_adjoint(T.bodies[b], T.dyn[b], ctx->spec.gravity, &T.imp[6 * b],
+                                    &T.imp[6 * b + 3], dt, &sbody[12 * b], &gb[6 * b]);
+      CU(cudaMemcpyAsync(ctx->bw_gbody, gb.data(), 6 * kMaxBodies * sizeof(double), cudaMemcpyHostToDevice, s));
+      CU(cudaStreamSynchronize(s));
+    }
     // replay the step from its checkpoint, keeping each substep's start state
     restore_state(ctx, T.state, s);
     // (each solve starts from the forward's taped solution of its substep,
@@ -1328,6 +1479,7 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
       a.bar = ctx->bar; a.status = ctx->status; a.poison = ctx->poison; a.stats = ctx->stats;
       a.out = ctx->adj_out; a.gbar = ctx->bw_gbar; a.pbar = bar[1 - in]; a.slot_of = ctx->bw_slot;
       a.P = P; a.n_particles = (int)n;
+      a.body_gbar = step_dyn ? ctx->bw_gbody : nullptr;
       CU(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned), s));
       CU(cudaMemsetAsync(ctx->G.n_cnodes, 0, sizeof(int), s));
       CU(launch_adjoint(a, ctx->adj_blocks, s));
@@ -1341,6 +1493,24 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
     // the body accumulators so far (steps t .. end), to split them by step
     CU(cudaMemcpyAsync(ctx->bw_snap + (size_t)t * kMaxBodies * kAdjBodySlots, ctx->adj_body,
                        kMaxBodies * kAdjBodySlots * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (any_dyn) {
+      // this step's contact terms complete the adjoint of the dynamic bodies'
+      // state at its start: v (bias, lagged impulse), p, omega, theta
+      std::vector<double> cur(kMaxBodies * kAdjBodySlots);
+      CU(cudaMemcpyAsync(cur.data(), ctx->adj_body, cur.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      for (int b = 0; b < nb; ++b) {
+        if (!T.is_dyn[b]) continue;
+        auto D = [&](int k) { return cur[b * kAdjBodySlots + k] - prev_snap[b * kAdjBodySlots + k]; };
+        for (int c = 0; c < 3; ++c) {
+          sbody[12 * b + c] += D(c) + D(10 + c);
+          sbody[12 * b + 3 + c] += D(7 + c);
+          sbody[12 * b + 6 + c] += D(3 + c) + D(16 + c);
+          sbody[12 * b + 9 + c] += D(13 + c);
+        }
+      }
+      prev_snap = cur;
+    }
   }
   // outputs: the adjoint of the first recorded state, in id order
   float* dst[4] = {x0_bar, v0_bar, C0_bar, F0_bar};
@@ -1393,26 +1563,20 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
     // omega) T_t domega + exp(T_t [omega]x) dtheta_0, with J_l the left
     // Jacobian of SO(3): dL/domega adds T_t J_l^T theta_bar_t, dL/dtheta_0 =
     // sum exp(-T_t [omega]x) theta_bar_t.
-    auto rodrigues = [](const double* ph, const double* x, double sgn, double* out) {
-      // exp(sgn [ph]x) x
-      const double th = std::sqrt(ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
-      const double a = th > 1e-12 ? std::sin(th) / th : 1.0;
-      const double b = th > 1e-6 ? (1.0 - std::cos(th)) / (th * th) : 0.5;
-      const double px[3] = {ph[1] * x[2] - ph[2] * x[1], ph[2] * x[0] - ph[0] * x[2], ph[0] * x[1] - ph[1] * x[0]};
-      const double ppx[3] = {ph[1] * px[2] - ph[2] * px[1], ph[2] * px[0] - ph[0] * px[2], ph[0] * px[1] - ph[1] * px[0]};
-      for (int c = 0; c < 3; ++c) out[c] = x[c] + sgn * a * px[c] + b * ppx[c];
-    };
-    auto jl_transpose = [](const double* ph, const double* x, double* out) {
-      // J_l(ph)^T x = x - ((1 - cos)/th^2) ph x x + ((th - sin)/th^3) ph x (ph x x)
-      const double th = std::sqrt(ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2]);
-      const double b = th > 1e-6 ? (1.0 - std::cos(th)) / (th * th) : 0.5;
-      const double c3 = th > 1e-4 ? (th - std::sin(th)) / (th * th * th) : 1.0 / 6.0;
-      const double px[3] = {ph[1] * x[2] - ph[2] * x[1], ph[2] * x[0] - ph[0] * x[2], ph[0] * x[1] - ph[1] * x[0]};
-      const double ppx[3] = {ph[1] * px[2] - ph[2] * px[1], ph[2] * px[0] - ph[0] * px[2], ph[0] * px[1] - ph[1] * px[0]};
-      for (int c = 0; c < 3; ++c) out[c] = x[c] - b * px[c] + c3 * ppx[c];
-    };
     for (int b = 0; b < nb_max; ++b) {
       double* o = body_bar + 13 * b;
+      if (ctx->tape[0].is_dyn[b]) {
+        // the recursion through the rigid steps gives the adjoint of the
+        // first state directly
+        o[0] = S(0, b, 6);
+        for (int c = 0; c < 3; ++c) {
+          o[1 + c] = sbody[12 * b + c];
+          o[4 + c] = sbody[12 * b + 3 + c];
+          o[7 + c] = sbody[12 * b + 6 + c];
+          o[10 + c] = sbody[12 * b + 9 + c];
+        }
+        continue;
+      }
       o[0] = S(0, b, 6);
       for (int c = 0; c < 3; ++c) {
         o[1 + c] = S(0, b, c) + S(0, b, 10 + c);
@@ -1435,12 +1599,27 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
         const double ph[3] = {offset * w[0], offset * w[1], offset * w[2]};
         double jt[3], r0[3];
         jl_transpose(ph, rb, jt);
-        rodrigues(ph, rb, -1.0, r0);
+        rot_apply(ph, rb, -1.0, r0);
         for (int c = 0; c < 3; ++c) {
           o[7 + c] += offset * jt[c];
           o[10 + c] += r0[c];
         }
         if (tk.kinematic[b]) offset += (double)tk.n_substeps * (double)tk.h;
+      }
+      if (body_state_bar && b < nb_final) {
+        // the final state: p_T = p_0 + T v, R_T = exp(T [omega]x) R_0 (T the
+        // time a kinematic body advanced; 0 for a static one)
+        const double* f = body_state_bar + 12 * b;
+        const double ph[3] = {offset * w[0], offset * w[1], offset * w[2]};
+        double jt[3], r0[3];
+        jl_transpose(ph, f + 9, jt);
+        rot_apply(ph, f + 9, -1.0, r0);
+        for (int c = 0; c < 3; ++c) {
+          o[1 + c] += f[c] + offset * f[3 + c];
+          o[4 + c] += f[3 + c];
+          o[7 + c] += f[6 + c] + offset * jt[c];
+          o[10 + c] += r0[c];
+        }
       }
     }
   }

@@ -134,6 +134,9 @@ struct AdjointArgs {
   const int* slot_of;
   Particles P;
   int n_particles;
+  // per body (6): the cotangent of the impulse and of its moment that the
+  // substep's contacts give the body (dynamic bodies, Eq. (3)); null: none
+  const double* body_gbar;
 };
 constexpr int kAdjointVectors = 13;
 // per-body adjoint accumulators: dL/dv_r through the bias (3), its moment

@@ -931,6 +931,17 @@ __device__ void contact_input_adjoint(const AdjHess& A, const DevBody& bd, const
   wdir[2] = -vn0bar * (r[0] * n[1] - r[1] * n[0]);
 }
 
+// The cotangent of the contact's gradient dl_c (the impulse the body
+// receives, minus the particle's) from the body's impulse and moment
+// cotangents: ghat = Jbar + Lbar x r, r = x_p - p (Eq. (3)).
+__device__ __forceinline__ void impulse_cotangent(const double* bg, const DevBody& bd,
+                                                  const float4& xp, double (&gh)[3]) {
+  const double r[3] = {(double)xp.x - bd.p[0], (double)xp.y - bd.p[1], (double)xp.z - bd.p[2]};
+  gh[0] = bg[0] + bg[4] * r[2] - bg[5] * r[1];
+  gh[1] = bg[1] + bg[5] * r[0] - bg[3] * r[2];
+  gh[2] = bg[2] + bg[3] * r[1] - bg[4] * r[0];
+}
+
 // y = d2l_c u (FP32)
 __device__ __forceinline__ void hess_apply(const AdjHess& A, const float (&u)[3], float (&y)[3]) {
   const float un = A.n[0] * u[0] + A.n[1] * u[1] + A.n[2] * u[2];
@@ -1127,6 +1138,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
       const float w2 = ln.w * ln.w;
       red_add_v4(vL0 + ci, w2 * H[0], w2 * H[1], w2 * H[2], w2 * H[3]);
       red_add_v4(vL1 + ci, w2 * H[4], w2 * H[5], 0.f, 0.f);
+      if (a.body_gbar) {
+        // the body's impulse depends on the solution through dl_c(J v + b):
+        // vbar += J^T d2l_c ghat
+        double gh[3], y[3];
+        impulse_cotangent(a.body_gbar + 6 * body, s_body[body], xp, gh);
+        hess_apply(A, gh, y);
+        float* d = reinterpret_cast<float*>(vRhs + ci);
+        atomicAdd(d, (float)(ln.w * y[0]));
+        atomicAdd(d + 1, (float)(ln.w * y[1]));
+        atomicAdd(d + 2, (float)(ln.w * y[2]));
+      }
     }
   }
   if (!grid_sync(B)) return;
@@ -1357,6 +1379,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
     const int ci = list_pos(ln);
     double u[3], yd[3];
     hessian_lambda_f64(A, ln, ci, u, yd);
+    // with a body impulse cotangent ghat the contact's inputs see
+    // xi - ghat in place of xi = J lambda (their adjoint is
+    // -(d dl_c / d theta)^T (xi - ghat), the bias's -d2l_c (xi - ghat))
+    double gh[3] = {0.0, 0.0, 0.0};
+    if (a.body_gbar) {
+      impulse_cotangent(a.body_gbar + 6 * body, s_body[body], xp, gh);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) u[r] -= gh[r];
+      hess_apply(A, u, yd);
+    }
     float xw[3] = {0.f, 0.f, 0.f};
     if (a.gbar) {
       // stencil-weight term of x_p: -sum_i (lambda_i . g_c + v_i . y) grad w_ip
@@ -1381,9 +1413,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
       contact_input_adjoint(A, s_body[body], xp, a.C.vc[p], a.C.bias[p], vp, a.h, u, yd, xb, vb,
                             rot, wdir);
       const size_t np = (size_t)a.n_particles;
+      // the moment arm of the body's moment: L = sum r x dl_c, r = x_p - p
+      float arm[3] = {0.f, 0.f, 0.f};
+      if (a.body_gbar) {
+        const double* lb = a.body_gbar + 6 * body + 3;
+        const double gc[3] = {(double)A.dN * A.n[0] + (double)A.cs * A.ut[0],
+                              (double)A.dN * A.n[1] + (double)A.cs * A.ut[1],
+                              (double)A.dN * A.n[2] + (double)A.cs * A.ut[2]};
+        arm[0] = (float)(gc[1] * lb[2] - gc[2] * lb[1]);
+        arm[1] = (float)(gc[2] * lb[0] - gc[0] * lb[2]);
+        arm[2] = (float)(gc[0] * lb[1] - gc[1] * lb[0]);
+      }
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        atomicAdd(a.pbar + r * np + slot, xb[r] + xw[r]);
+        atomicAdd(a.pbar + r * np + slot, xb[r] + xw[r] + arm[r]);
+        atomicAdd(&s_bb[body][7 + r], -(double)arm[r]);
         atomicAdd(a.pbar + (3 + r) * np + slot, vb[r]);
         // the contact geometry depends on x_p - p_body: dL/dp = -(its part of
         // dL/dx_p); the body velocity enters n0 through -v: dL/dv gets -vbar

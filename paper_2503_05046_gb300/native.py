@@ -116,7 +116,7 @@ SIGNATURES = {
     "mpm_set_material": [_vp, C.c_int32, C.POINTER(Material)],
     "mpm_tape_begin": [_vp],
     "mpm_tape_end": [_vp],
-    "mpm_backward": [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+    "mpm_backward": [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                      C.POINTER(AdjointParams), C.POINTER(BackwardStats)],
     "mpm_synchronize": [_vp],
     "mpm_set_option": [_vp, C.c_int32, C.c_int64],
@@ -350,8 +350,11 @@ def mpm_tape_end(ctx):
 
 
 def mpm_backward(ctx, n, n_groups, n_bodies, x_bar=None, v_bar=None, C_bar=None, F_bar=None,
-                 eps_r=1e-6, max_iters=2000, check=True):
+                 eps_r=1e-6, max_iters=2000, check=True, body_state_bar=None):
     """Reverse pass over the recorded steps (see include/mpmcr.h).
+
+    body_state_bar: optional [n_bodies, 12] cotangent of the bodies' final
+    state (dL/dv, dL/dp, dL/domega, dL/dtheta).
 
     The four cotangents are numpy arrays (host) or CUDA tensors (device, all
     alike; None for zero). Returns dict(x, v, C, F: adjoints of the first
@@ -380,8 +383,11 @@ def mpm_backward(ctx, n, n_groups, n_bodies, x_bar=None, v_bar=None, C_bar=None,
     bodyb = np.zeros((max(n_bodies, 1), 13))
     st = BackwardStats()
     params = AdjointParams(float(eps_r), int(max_iters))
-    code = lib.mpm_backward(ctx, kind, *iptr, *optr, mat.ctypes.data, bodyb.ctypes.data,
-                            C.byref(params), C.byref(st))
+    sbar = None
+    if body_state_bar is not None:
+        sbar = np.ascontiguousarray(body_state_bar, np.float64).reshape(n_bodies, 12)
+    code = lib.mpm_backward(ctx, kind, *iptr, sbar.ctypes.data if sbar is not None else None, *optr,
+                            mat.ctypes.data, bodyb.ctypes.data, C.byref(params), C.byref(st))
     if check:
         _check(ctx, code)
     return {"x": outs[0], "v": outs[1], "C": outs[2], "F": outs[3],
@@ -551,12 +557,13 @@ class Sim:
         mpm_tape_end(self.ctx)
 
     def backward(self, x_bar=None, v_bar=None, C_bar=None, F_bar=None, eps_r=1e-6,
-                 max_iters=2000, check=True):
+                 max_iters=2000, check=True, body_state_bar=None):
         """Adjoint of the recorded rollout for the cotangents of its final
         state (mpm_backward): dL/d(first recorded state), dL/dE, dL/dnu per
-        group, dL/dmu per body."""
+        group, and per body dL/dmu and the gradients of its velocities and
+        pose."""
         return mpm_backward(self.ctx, self.n, len(self.scene["groups"]), self.n_bodies,
-                            x_bar, v_bar, C_bar, F_bar, eps_r, max_iters, check)
+                            x_bar, v_bar, C_bar, F_bar, eps_r, max_iters, check, body_state_bar)
 
     def contact_adjoint(self, node_ids, vbar, eps_r=1e-5, max_iters=1000, check=True):
         """dL/dv*, per-contact (dL/dv_r, dL/dmu) and per-body gradients of the

@@ -234,9 +234,9 @@ def test_autograd_rollout(case):
 
 def test_backward_error_paths():
     """mpm_backward refuses what it cannot differentiate, with MPM_ERR_STATE
-    and without touching the state: no tape, a tape with dynamic bodies,
-    particles added after the tape began; mpm_set_material is refused while
-    recording."""
+    and without touching the state: no tape, a body that changed kind
+    (kinematic, then dynamic) within the tape, particles added after the
+    tape began; mpm_set_material is refused while recording."""
     from paper_2503_05046_gb300 import native
     sc, _ = scenes.push_cube(**SCENE)
     sim = native.Sim(sc, max_particles=2 * scenes.n_particles(sc))
@@ -292,3 +292,100 @@ def test_backward_without_taped_solutions_agrees():
         assert np.max(np.abs(a - b)) <= 1e-3 * np.max(np.abs(b)), key
     for key in ("E", "nu", "mu"):
         assert np.allclose(out[0][key], out[1][key], rtol=1e-3, atol=0), key
+
+
+DYN = {"mass": 0.05, "inertia": [2e-5, 3e-5, 4e-5], "force": [0.0, 0.0, 0.0],
+       "torque": [0.0, 0.0, 0.0], "dof_mask": 63, "gravity": 0}
+
+
+def _vee_log(Rn, Rref):
+    M = np.asarray(Rn).reshape(3, 3) @ np.asarray(Rref).reshape(3, 3).T
+    S = 0.5 * (M - M.T)
+    return np.array([S[2, 1], S[0, 2], S[1, 0]])
+
+
+def test_backward_through_a_dynamic_body():
+    """The pushing box is a free rigid body (Eq. (3); no gravity, turning at
+    0.5 rad/s): the loss reads the particles and the box's final state; the
+    gradients in E, mu, the box's initial velocity, angular velocity,
+    position and orientation and the particles' initial velocity against
+    central differences of the oracle's rollout with the same rigid steps."""
+    from paper_2503_05046_gb300 import native
+    sc, _ = scenes.push_cube(**SCENE)
+    sc["bodies"][1]["omega"] = np.array([0.0, 0.0, 0.5])
+    sc["init"] = _initial_state(sc, False)
+    n = scenes.n_particles(sc)
+    rng = np.random.default_rng(41)
+    cot = {"x": rng.normal(size=(n, 3)), "v": rng.normal(size=(n, 3)) * 1e-2,
+           "C": np.zeros((n, 3, 3)), "F": np.zeros((n, 3, 3))}
+    sbar = np.zeros((2, 12))
+    sbar[1] = rng.normal(size=12) * np.repeat([1.0, 30.0, 0.1, 1.0], 3)
+    sim = native.Sim(sc)
+    sim.set_dynamics(1, DYN)
+    sim.tape_begin()
+    for _ in range(STEPS):
+        sim.step(n_substeps=sc["substeps"], solver=native.solver_params(**GPU_SOLVER))
+    sim.tape_end()
+    out = sim.backward(x_bar=cot["x"].astype(np.float32), v_bar=cot["v"].astype(np.float32),
+                       body_state_bar=sbar)
+    final_bodies = sim.bodies()
+    sim.close()
+    S = O.solver(**ORC_SOLVER)
+    st_ref, code, b_ref = O.rollout(sc, STEPS, S, state=sc["init"], dynamics={1: DYN},
+                                    with_bodies=True)
+    assert code == O.OK
+    assert np.allclose(np.float32(b_ref[1]["v"]), final_bodies[1]["v"], rtol=1e-4, atol=1e-6)
+    R_ref = b_ref[1]["R"]
+
+    def loss(state=None, materials=None, bodies=None):
+        st, c, bds = O.rollout(sc, STEPS, S, materials=materials, bodies=bodies,
+                               state=sc["init"] if state is None else state,
+                               dynamics={1: DYN}, with_bodies=True)
+        assert c == O.OK
+        b = bds[1]
+        return (float(np.sum(cot["x"] * st["x"]) + np.sum(cot["v"] * st["v"])) +
+                float(sbar[1, 0:3] @ b["v"] + sbar[1, 3:6] @ b["p"] + sbar[1, 6:9] @ b["omega"] +
+                      sbar[1, 9:12] @ _vee_log(b["R"], R_ref)))
+
+    rows = []
+    _, mats = O.from_scene(sc)
+    hE = 1e-6 * mats[0]["E"]
+    rows.append(("E", (loss(materials=[dict(mats[0], E=mats[0]["E"] + hE)]) -
+                       loss(materials=[dict(mats[0], E=mats[0]["E"] - hE)])) / (2 * hE), out["E"][0]))
+
+    def body_fd(key, c, eps):
+        bp, bm = O.bodies_from_scene(sc), O.bodies_from_scene(sc)
+        if key == "R":
+            k = np.zeros(3)
+            k[c] = 1.0
+            K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+            Q = lambda t: np.eye(3) + np.sin(t) * K + (1 - np.cos(t)) * K @ K
+            bp[1]["R"] = Q(eps) @ np.asarray(bp[1]["R"]).reshape(3, 3)
+            bm[1]["R"] = Q(-eps) @ np.asarray(bm[1]["R"]).reshape(3, 3)
+        elif key == "mu":
+            bp[1]["mu"] += eps
+            bm[1]["mu"] -= eps
+        else:
+            bp[1][key] = np.array(bp[1][key], np.float64)
+            bm[1][key] = np.array(bm[1][key], np.float64)
+            bp[1][key][c] += eps
+            bm[1][key][c] -= eps
+        return (loss(bodies=bp) - loss(bodies=bm)) / (2 * eps)
+
+    rows.append(("mu1", body_fd("mu", 0, 1e-6), out["mu"][1]))
+    for c in (0, 2):
+        rows.append(("v1_%d" % c, body_fd("v", c, 1e-6), out["body_v"][1][c]))
+        rows.append(("p1_%d" % c, body_fd("p", c, 1e-8), out["body_p"][1][c]))
+        rows.append(("w1_%d" % c, body_fd("omega", c, 1e-6), out["body_w"][1][c]))
+        rows.append(("R1_%d" % c, body_fd("R", c, 1e-7), out["body_R"][1][c]))
+    dv = rng.normal(size=(n, 3))
+    sp, sm = dict(sc["init"]), dict(sc["init"])
+    sp["v"] = sc["init"]["v"] + 1e-6 * dv
+    sm["v"] = sc["init"]["v"] - 1e-6 * dv
+    rows.append(("v0", (loss(state=sp) - loss(state=sm)) / 2e-6,
+                 float(np.sum(out["v"].astype(np.float64) * dv))))
+    scale = max(abs(fd) for _, fd, _ in rows)
+    for name, fd, got in rows:
+        print("d/d%s: fd %.6e adjoint %.6e rel %.2e" % (name, fd, got, abs(got - fd) / max(abs(fd), 1e-300)))
+    for name, fd, got in rows:
+        assert abs(got - fd) <= 2e-3 * abs(fd) or abs(got - fd) <= 1e-9 * scale, name
