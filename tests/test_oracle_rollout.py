@@ -60,3 +60,26 @@ def test_kinematic_bodies_advance_between_steps():
     assert np.array_equal(st_a["x"], st_b["x"])
     b = O.advance_kinematic(O.bodies_from_scene(sc), 3 * sc["h"])
     assert np.allclose(b[0]["p"], np.float32([0.2, 0.2, 0.2]) + np.array([0.1, 0, 0]) * 3 * sc["h"])
+
+
+def test_dynamic_body_free_motion():
+    """A dynamic body far from the material, without gravity, force or
+    torque, spinning about a principal axis: the rigid steps of Eq. (3) keep
+    v and omega, p advances by T v and R by exp(T [omega]x) (no gyroscopic
+    torque about a principal axis)."""
+    sc = _free_scene()
+    w = np.array([0.0, 0.0, 1.5])
+    sc["bodies"] = [scenes.body(scenes.BOX, (0.01, 0.02, 0.03), p=(0.2, 0.2, 0.2),
+                                v=(0.1, -0.05, 0.02), omega=w)]
+    dyn = {0: {"mass": 0.3, "inertia": [1e-3, 2e-3, 3e-3], "gravity": 0, "dof_mask": 63}}
+    st, code, bds = O.rollout(sc, 3, O.solver(), dynamics=dyn, with_bodies=True)
+    assert code == O.OK
+    b0 = O.bodies_from_scene(sc)[0]
+    T = 3 * sc["substeps"] * sc["h"]
+    assert np.allclose(bds[0]["v"], b0["v"], rtol=0, atol=1e-15)
+    assert np.allclose(bds[0]["omega"], b0["omega"], rtol=0, atol=1e-12)
+    assert np.allclose(bds[0]["p"], b0["p"] + T * np.asarray(b0["v"]), rtol=0, atol=1e-14)
+    th = T * float(np.float32(1.5))
+    Rz = np.array([[np.cos(th), -np.sin(th), 0.0], [np.sin(th), np.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    assert np.allclose(np.asarray(bds[0]["R"]).reshape(3, 3), Rz @ np.asarray(b0["R"]).reshape(3, 3),
+                       rtol=0, atol=1e-12)
