@@ -272,12 +272,9 @@ void advance_kinematic(mpm_rigid_body& b, double dt) {
 void integrate_dynamic_adjoint(const DevBody& b, const mpm_rigid_dynamics& d, const double* gravity,
                                const double* J, const double* L, double dt, double* sb, double* jl) {
   const double m = d.mass;
-  double v2[3], w[3], R[9], Iw[9];
-  for (int i = 0; i < 3; ++i) {
-    const double f = d.force[i] + (d.gravity ? m * gravity[i] : 0.0);
-    v2[i] = b.v[i] + (dt * f + J[i]) / m;
-    w[i] = b.w[i];
-  }
+  double w[3], R[9], Iw[9];
+  (void)gravity;  // the force and gravity enter v' additively: no adjoint term
+  for (int i = 0; i < 3; ++i) w[i] = b.w[i];
   for (int i = 0; i < 9; ++i) R[i] = b.R[i];
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) {
@@ -301,11 +298,7 @@ void integrate_dynamic_adjoint(const DevBody& b, const mpm_rigid_dynamics& d, co
   cross3d(w, Iww, gyro);
   for (int i = 0; i < 3; ++i) q[i] = dt * (d.torque[i] - gyro[i]) + L[i];
   solve(q, a);
-  for (int i = 0; i < 3; ++i) {
-    w2[i] = ((d.dof_mask >> (3 + i)) & 1) ? w[i] + a[i] : 0.0;
-    if (!((d.dof_mask >> i) & 1)) v2[i] = 0.0;
-  }
-  (void)v2;
+  for (int i = 0; i < 3; ++i) w2[i] = ((d.dof_mask >> (3 + i)) & 1) ? w[i] + a[i] : 0.0;
   const double* vb2 = sb;
   const double* pb2 = sb + 3;
   const double* wb2 = sb + 6;
@@ -318,7 +311,7 @@ void integrate_dynamic_adjoint(const DevBody& b, const mpm_rigid_dynamics& d, co
     vacc[i] = ((d.dof_mask >> i) & 1) ? vb2[i] + dt * pb2[i] : 0.0;
     wacc[i] = ((d.dof_mask >> (3 + i)) & 1) ? wb2[i] + dt * jt[i] : 0.0;
   }
-  double z[3], wz[3], Iwz_[3], Iw_wz[3], Iwwz[3], zw[3], Izw[3], t1[3], t2[3], t3[3], t4[3], Ia[3], Iz[3];
+  double z[3], wz[3], Iwz_[3], Iw_wz[3], zw[3], Izw[3], t1[3], t2[3], t3[3], t4[3], Ia[3], Iz[3];
   solve(wacc, z);
   cross3d(w, z, wz);
   mul(wz, Iwz_);
@@ -331,7 +324,6 @@ void integrate_dynamic_adjoint(const DevBody& b, const mpm_rigid_dynamics& d, co
   cross3d(Iz, a, t2);
   cross3d(Iww, zw, t3);
   cross3d(Izw, w, t4);
-  (void)Iwwz;
   const double pb[3] = {pb2[0], pb2[1], pb2[2]};
   for (int i = 0; i < 3; ++i) {
     jl[i] = vacc[i] / m;
