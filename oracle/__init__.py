@@ -413,7 +413,8 @@ def advance_kinematic(bodies, dt):
 def rollout(scene, steps, S, materials=None, bodies=None, state=None, substeps=None,
             dynamics=None, with_bodies=False):
     """Asynchronous time splitting (Sec. IV-A, Eq. (3)-(4)): `steps` rigid time
-    steps of `substeps` (default scene["substeps"]) MPM substeps each, the
+    steps of `substeps` (default scene["substeps"]; a sequence gives each
+    step its own count) MPM substeps each, the
     rigid bodies frozen within a step; after it the kinematic ones advance by
     substeps*h and the dynamic ones (`dynamics`: body index -> dict as
     make_dynamics; their kinematic flag is ignored) take the rigid step of
@@ -426,12 +427,13 @@ def rollout(scene, steps, S, materials=None, bodies=None, state=None, substeps=N
     mats = mats0 if materials is None else materials
     bds = bodies_from_scene(scene) if bodies is None else [dict(b) for b in bodies]
     n_sub = scene["substeps"] if substeps is None else substeps
+    per_step = list(n_sub) if hasattr(n_sub, "__len__") else [n_sub] * steps
     dyn = dynamics or {}
     grav = scene["grid"].get("gravity", (0.0, 0.0, -9.81))
     sim = Sim(scene["grid"])
     code = OK
     try:
-        for _ in range(steps):
+        for n_sub in per_step[:steps]:
             imp = np.zeros(6 * max(len(bds), 1))
             for _ in range(n_sub):
                 c, _ = sim.substep(st, mats, bds, scene["h"], S, imp)

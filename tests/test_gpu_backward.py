@@ -389,3 +389,63 @@ def test_backward_through_a_dynamic_body():
         print("d/d%s: fd %.6e adjoint %.6e rel %.2e" % (name, fd, got, abs(got - fd) / max(abs(fd), 1e-300)))
     for name, fd, got in rows:
         assert abs(got - fd) <= 2e-3 * abs(fd) or abs(got - fd) <= 1e-9 * scale, name
+
+
+def test_backward_two_materials_uneven_steps():
+    """Two particle groups (the elastic lattice cube and a sand copy beside
+    it, started compressed and sheared) and recorded steps of 3 and 5
+    substeps: dL/dE and dL/dnu of each group and a direction of v0 against
+    central differences of the oracle's rollout."""
+    from paper_2503_05046_gb300 import native
+    sc, _ = scenes.push_cube(**SCENE)
+    g0 = sc["groups"][0]
+    g1 = dict(g0, x=(g0["x"] + np.float32([0.045, 0.0, 0.0])).astype(np.float32),
+              material=dict(scenes.SAND))
+    sc["groups"] = [g0, g1]
+    st0, _ = O.from_scene(sc)
+    st = {k: np.array(v) for k, v in st0.items()}
+    n0, n = len(g0["x"]), len(st["x"])
+    rng = np.random.default_rng(51)
+    F = np.tile(np.eye(3), (n, 1, 1))
+    F[n0:] = np.eye(3) * (1.0 - 2e-3) + 5e-4 * rng.normal(size=(n - n0, 3, 3))
+    st["F"] = F.astype(np.float32).astype(np.float64)
+    st["v"] = (st["v"] + 5e-3 * rng.normal(size=(n, 3))).astype(np.float32).astype(np.float64)
+    steps = [3, 5]
+    cot_x = rng.normal(size=(n, 3))
+    sim = native.Sim(sc)
+    sim.set_particles(st["x"].astype(np.float32), st["v"].astype(np.float32),
+                      st["C"].astype(np.float32), st["F"].astype(np.float32))
+    sim.tape_begin()
+    for k in steps:
+        sim.step(n_substeps=k, solver=native.solver_params(**GPU_SOLVER))
+    sim.tape_end()
+    out = sim.backward(x_bar=cot_x.astype(np.float32))
+    sim.close()
+    S = O.solver(**ORC_SOLVER)
+
+    def loss(materials=None, state=None):
+        fin, c = O.rollout(sc, len(steps), S, materials=materials,
+                           state=st if state is None else state, substeps=steps)
+        assert c == O.OK
+        return float(np.sum(cot_x * fin["x"]))
+
+    _, mats = O.from_scene(sc)
+    rows = []
+    for gi in (0, 1):
+        for key, rel in (("E", 1e-6), ("nu", None)):
+            h = rel * mats[gi][key] if rel else 1e-6
+            p, m = [dict(x) for x in mats], [dict(x) for x in mats]
+            p[gi][key] += h
+            m[gi][key] -= h
+            rows.append(("%s%d" % (key, gi), (loss(materials=p) - loss(materials=m)) / (2 * h),
+                         out[key][gi]))
+    dv = rng.normal(size=(n, 3))
+    sp, sm = dict(st), dict(st)
+    sp["v"] = st["v"] + 1e-6 * dv
+    sm["v"] = st["v"] - 1e-6 * dv
+    rows.append(("v0", (loss(state=sp) - loss(state=sm)) / 2e-6,
+                 float(np.sum(out["v"].astype(np.float64) * dv))))
+    for name, fd, got in rows:
+        print("d/d%s: fd %.6e adjoint %.6e rel %.2e" % (name, fd, got, abs(got - fd) / abs(fd)))
+    for name, fd, got in rows:
+        assert abs(got - fd) <= 2e-3 * abs(fd), name
