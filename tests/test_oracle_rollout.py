@@ -83,3 +83,22 @@ def test_dynamic_body_free_motion():
     Rz = np.array([[np.cos(th), -np.sin(th), 0.0], [np.sin(th), np.cos(th), 0.0], [0.0, 0.0, 1.0]])
     assert np.allclose(np.asarray(bds[0]["R"]).reshape(3, 3), Rz @ np.asarray(b0["R"]).reshape(3, 3),
                        rtol=0, atol=1e-12)
+
+
+def test_per_step_substep_counts():
+    """Steps of 2 and 5 substeps: free fall reaches the closed form at n = 7
+    (not 2 x 3, the scene's default), and a kinematic body far away has
+    advanced by 7 h v."""
+    sc = _free_scene()
+    sc["bodies"] = [scenes.body(scenes.SPHERE, (0.01,), p=(0.2, 0.2, 0.2), v=(0.1, 0.0, 0.0),
+                                kinematic=1)]
+    st0, _ = O.from_scene(sc)
+    st, code, bds = O.rollout(sc, 2, O.solver(), substeps=[2, 5], with_bodies=True)
+    assert code == O.OK
+    n, h = 7, sc["h"]
+    g = np.asarray(sc["grid"]["gravity"])
+    want = st0["x"] + n * h * st0["v"] + h * h * g * n * (n + 1) / 2.0
+    assert np.allclose(st["x"], want, rtol=0, atol=1e-12)
+    b0 = O.bodies_from_scene(sc)[0]
+    assert np.allclose(bds[0]["p"], np.asarray(b0["p"]) + n * h * np.asarray(b0["v"]),
+                       rtol=0, atol=1e-15)
