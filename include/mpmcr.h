@@ -355,7 +355,12 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
    velocities on its contact nodes (16 bytes per contact node, in a pool of
    16M entries allocated at the first mpm_tape_begin; substeps beyond it are
    re-solved by the backward). mpm_tape_end stops recording and keeps the
-   tape. Adding particles while recording is an error at the next mpm_step. */
+   tape. Adding particles while recording is an error at the next mpm_step;
+   setting the particles (mpm_set_particles) or the bodies
+   (mpm_set_rigid_bodies) between two recorded steps breaks the chain from
+   one step's end state to the next one's start, and mpm_backward then
+   refuses the tape (setting them after mpm_tape_begin, before the first
+   recorded step, is fine). */
 mpm_status mpm_tape_begin(mpm_ctx* ctx);
 mpm_status mpm_tape_end(mpm_ctx* ctx);
 
@@ -408,7 +413,8 @@ typedef struct {
    The return map's branch boundaries (tension, the yield cone) and the
    Hencky clamp are kinks where the one-sided derivatives differ; sand
    starting exactly at F = I with a uniform velocity sits on one.
-   Requires: a tape; the same particles (MPM_ERR_STATE otherwise).
+   Requires: a tape whose steps each start where the previous one ended;
+   the same particles (MPM_ERR_STATE otherwise).
    Synchronises; afterwards the particle state is the final state again, the
    impulse accumulators are as before, and the tape is kept; the grid and
    contacts hold a replayed substep, so mpm_contact_adjoint needs an

@@ -100,6 +100,7 @@ struct mpm_ctx {
     mpm_solver_params sp{};
   };
   bool taping = false;
+  bool tape_reset = false;  // particles or bodies set between two recorded steps
   int64_t tape_n = 0;
   std::vector<TapeStep> tape;
   // the contact-node solutions of the taped substeps (see launch_tape_save)
@@ -779,6 +780,7 @@ mpm_status mpm_set_particles(mpm_ctx* ctx, const float* x, const float* v, const
     return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_particles: bad mem_kind");
   const int64_t n = ctx->n;
   if (n == 0) return MPM_OK;
+  if (ctx->taping && !ctx->tape.empty()) ctx->tape_reset = true;
   const float* src[4] = {x, v, C, F};
   const int width[4] = {3, 3, 9, 9};
   const float* dptr[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -841,6 +843,7 @@ mpm_status mpm_set_rigid_bodies(mpm_ctx* ctx, int32_t n, const mpm_rigid_body* b
         !(b.d >= 0.f))
       return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_rigid_bodies: bad body");
   }
+  if (ctx->taping && !ctx->tape.empty()) ctx->tape_reset = true;
   ctx->bodies.assign(bodies, bodies + n);
   ctx->bodies_dirty = true;
   ctx->is_dyn.assign(n, 0);
@@ -1258,6 +1261,7 @@ mpm_status mpm_tape_begin(mpm_ctx* ctx) {
     if (t.state) cudaFree(t.state);
   ctx->tape.clear();
   ctx->taping = true;
+  ctx->tape_reset = false;
   ctx->tape_n = ctx->n;
   ctx->tape_substeps = 0;
   // the solution pool (MPM_OPT_TAPE_SOLUTIONS contact-node velocities, 256 MB
@@ -1343,6 +1347,9 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
   if (ctx->tape.empty()) return fail(ctx, MPM_ERR_STATE, "mpm_backward: no recorded steps (mpm_tape_begin)");
   if (ctx->n != ctx->tape_n)
     return fail(ctx, MPM_ERR_STATE, "mpm_backward: the particle count changed since the tape began");
+  // each recorded step must start from the state the previous one ended in
+  if (ctx->tape_reset)
+    return fail(ctx, MPM_ERR_STATE, "mpm_backward: particles or bodies were set between recorded steps");
   // every body keeps its kind (dynamic, kinematic, static) over the tape
   for (const auto& t : ctx->tape)
     for (size_t b = 0; b < t.bodies.size() && b < ctx->tape[0].bodies.size(); ++b)

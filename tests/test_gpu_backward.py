@@ -236,7 +236,9 @@ def test_backward_error_paths():
     """mpm_backward refuses what it cannot differentiate, with MPM_ERR_STATE
     and without touching the state: no tape, a body that changed kind
     (kinematic, then dynamic) within the tape, particles added after the
-    tape began; mpm_set_material is refused while recording."""
+    tape began, particles or bodies set between two recorded steps;
+    mpm_set_material is refused while recording. Setting them after the tape
+    begins and before its first step is allowed."""
     from paper_2503_05046_gb300 import native
     sc, _ = scenes.push_cube(**SCENE)
     sim = native.Sim(sc, max_particles=2 * scenes.n_particles(sc))
@@ -265,6 +267,26 @@ def test_backward_error_paths():
     with pytest.raises(native.MpmError) as e:
         sim.step(n_substeps=1)
     assert e.value.code == native.ERR_STATE
+    sim.close()
+    sim = native.Sim(sc)
+    start, bodies = sim.get_particles(), sim.bodies()
+    for reset in ("particles", "bodies", None):
+        sim.tape_begin()
+        sim.set_particles(start["x"], start["v"], start["C"], start["F"])
+        sim.set_bodies(bodies)
+        sim.step(n_substeps=1)
+        if reset == "particles":
+            sim.set_particles(start["x"], start["v"], start["C"], start["F"])
+        elif reset == "bodies":
+            sim.set_bodies(bodies)
+        sim.step(n_substeps=1)
+        sim.tape_end()
+        if reset is None:
+            sim.backward(x_bar=np.ones((sim.n, 3), np.float32))
+            continue
+        with pytest.raises(native.MpmError) as e:
+            sim.backward(x_bar=np.ones((sim.n, 3), np.float32))
+        assert e.value.code == native.ERR_STATE
     sim.close()
 
 
