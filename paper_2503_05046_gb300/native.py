@@ -493,6 +493,8 @@ class Sim:
                               g["vol"], make_material(g["material"]))
         self.n_bodies = len(scene["bodies"])
         mpm_set_rigid_bodies(self.ctx, scene["bodies"])
+        # the dynamics set on the current bodies (mpm_set_rigid_bodies clears them)
+        self.dynamics = {}
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -530,12 +532,19 @@ class Sim:
         mpm_set_particles(self.ctx, x, v, Cm, F)
 
     def set_bodies(self, bodies):
-        self.n_bodies = len(bodies)
+        """Replace the bodies; like mpm_set_rigid_bodies this clears every
+        body's dynamics."""
         mpm_set_rigid_bodies(self.ctx, bodies)
+        self.n_bodies = len(bodies)
+        self.dynamics = {}
 
     def set_dynamics(self, index, dyn):
         """Make body `index` dynamic (dict as make_dynamics) or, with None, not."""
         mpm_set_rigid_dynamics(self.ctx, index, dyn)
+        if dyn is None:
+            self.dynamics.pop(int(index), None)
+        else:
+            self.dynamics[int(index)] = dict(dyn)
 
     def bodies(self):
         return [body_dict(b) for b in mpm_get_rigid_bodies(self.ctx, self.n_bodies)]

@@ -87,3 +87,77 @@ def test_bench_config_names_the_workload():
     assert cfg["particles"] == 10_000
     assert cfg["substeps_per_step"] == sc["substeps"]
     assert "model" not in cfg
+
+
+class _FakeSim:
+    """Stands in for native.Sim: records the calls the autograd binding makes
+    and keeps native.Sim's rule that replacing the bodies clears their
+    dynamics."""
+
+    def __init__(self, n, bodies):
+        self.n, self.ctx, self.calls = n, None, []
+        self.scene = {"groups": [{"material": {"model": 0, "E": 1e4, "nu": 0.3, "rho": 1e3}}]}
+        self._bodies = [dict(b) for b in bodies]
+        self.dynamics = {}
+
+    def bodies(self):
+        return [dict(b) for b in self._bodies]
+
+    def set_bodies(self, bodies):
+        self.calls.append(("set_bodies", [dict(b) for b in bodies]))
+        self._bodies = [dict(b) for b in bodies]
+        self.dynamics = {}
+
+    def set_dynamics(self, i, d):
+        self.calls.append(("set_dynamics", i))
+        self.dynamics[i] = d
+
+    def set_particles(self, *a):
+        pass
+
+    def tape_begin(self):
+        self.calls.append(("tape_begin", dict(self.dynamics)))
+
+    def step(self, solver=None):
+        for b in self._bodies:  # bodies move over a step
+            b["p"] = np.asarray(b["p"]) + 1.0
+
+    def tape_end(self):
+        pass
+
+    def get_particles(self):
+        return {"x": np.zeros((self.n, 3), np.float32), "v": np.zeros((self.n, 3), np.float32)}
+
+    def backward(self, x_bar=None, v_bar=None, eps_r=None):
+        return {"x": np.ones((self.n, 3)), "v": np.ones((self.n, 3)), "E": [2.0], "nu": [3.0],
+                "mu": [4.0], "body_v": [[5.0, 6.0, 7.0]]}
+
+
+def test_autograd_rollout_keeps_dynamics_and_start_bodies(monkeypatch):
+    """The rollout replaces the bodies (to apply mu and body_v), which clears
+    dynamics; it sets them again before recording. An explicit `bodies`
+    repeats a rollout from the same start; the gradients come back in the
+    inputs' dtypes."""
+    import torch
+    from paper_2503_05046_gb300 import autograd, native
+    monkeypatch.setattr(native, "mpm_set_material", lambda ctx, gi, m: None)
+    b0 = {"p": np.zeros(3), "v": np.array([0.1, 0.0, 0.0]), "mu": 0.5}
+    sim = _FakeSim(4, [b0])
+    sim.set_dynamics(0, {"mass": 1.0, "inertia": [1.0, 1.0, 1.0]})
+    x0 = torch.zeros(4, 3)
+    v0 = torch.zeros(4, 3, requires_grad=True)
+    E = torch.tensor([1e4], dtype=torch.float64, requires_grad=True)
+    nu = torch.tensor([0.3], dtype=torch.float64)
+    mu = torch.tensor([0.7], dtype=torch.float64, requires_grad=True)
+    for start, p_start in ((None, 0.0), (None, 2.0), ([b0], 0.0)):
+        sim.calls.clear()
+        xf, vf = autograd.rollout(sim, 2, x0, v0, E, nu, mu, bodies=start)
+        kinds = [c[0] for c in sim.calls]
+        assert kinds.index("set_dynamics") > kinds.index("set_bodies")
+        assert sim.calls[kinds.index("tape_begin")][1] == {0: {"mass": 1.0, "inertia": [1.0, 1.0, 1.0]}}
+        set_to = sim.calls[kinds.index("set_bodies")][1][0]
+        assert set_to["mu"] == 0.7 and np.allclose(set_to["v"], [0.1, 0.0, 0.0])
+        assert np.allclose(set_to["p"], p_start)  # the default follows the moved bodies
+    (xf.sum() + vf.sum()).backward()
+    assert v0.grad.dtype == torch.float32 and torch.all(v0.grad == 1.0)
+    assert E.grad.item() == 2.0 and mu.grad.item() == 4.0
