@@ -194,3 +194,35 @@ def test_iteration_cap_reports_not_converged():
     P = random_problem(401, n_nodes=15, n_contacts=8)
     v, gam, info, st = P.solve_qn(O.solver(eps_r=1e-14, eps_a=0.0, max_iters=1))
     assert st == O.ERR_NOT_CONVERGED and info.iters == 1 and not info.converged
+
+
+@pytest.mark.parametrize("seed,fixed_frac", [(0, 0.0), (4, 0.3)])
+def test_gradient_is_the_objectives_derivative(seed, fixed_frac):
+    """Eq. (9) against the objective of Eq. (8): central differences of l_p
+    along each free DoF at a random velocity equal the gradient (fixed DoFs
+    read zero); without contacts the gradient is M (v - v*); at the dense
+    Newton minimiser it vanishes on the free DoFs."""
+    P = random_problem(seed, fixed_frac=fixed_frac)
+    rng = np.random.default_rng(100 + seed)
+    v = rng.normal(scale=0.5, size=(P.n, 3))
+    g = P.gradient(v)
+    free = P.fixed == 0
+    assert np.all(g[~free] == 0.0)
+    eps = 1e-6
+    fd = np.zeros_like(g)
+    for i in np.flatnonzero(free):
+        for c in range(3):
+            d = np.zeros_like(v)
+            d[i, c] = eps
+            fd[i, c] = (P.objective(v + d) - P.objective(v - d)) / (2 * eps)
+    scale = np.max(np.abs(g))
+    assert np.max(np.abs(fd[free] - g[free])) <= 1e-6 * scale
+    P0 = O.ContactProblem(P.m, P.vstar, np.zeros((0, 27)), np.zeros((0, 27)), np.zeros((0, 3, 3)),
+                          np.zeros((0, 3)), [], [], [], [], [], H, 1e-4, P.fixed)
+    g0 = P0.gradient(v)
+    want = P.m[:, None] * (v - P.vstar.reshape(-1, 3))
+    assert np.allclose(g0[free], want[free], rtol=1e-14, atol=0)
+    vs, _, _, st = P.solve_dense_newton(O.solver(eps_r=1e-12, eps_a=0.0, max_iters=200))
+    assert st == O.OK
+    gs = P.gradient(vs)
+    assert np.max(np.abs(gs[free])) <= 1e-9 * scale
