@@ -27,7 +27,9 @@ def lib():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("mpm_create", "mpm_add_particles", "mpm_set_rigid_bodies", "mpm_step",
-                     "mpm_get_particles", "mpm_get_rigid_impulses", "mpm_destroy"):
+                     "mpm_get_particles", "mpm_get_rigid_impulses", "mpm_destroy",
+                     "mpm_tape_begin", "mpm_tape_end", "mpm_backward", "mpm_contact_adjoint",
+                     "mpm_set_rigid_dynamics", "mpm_set_material"):
         assert required in names
 
 
