@@ -64,6 +64,11 @@ def test_argument_validation_without_device(lib):
     assert native.lib.mpm_set_option(None, native.OPT_GRAPHS, 1) == native.ERR_INVALID_ARG
     assert native.lib.mpm_contact_adjoint(None, native.MEM_HOST, 0, None, None, None, 0, None,
                                           None, None, None) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_tape_begin(None) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_tape_end(None) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_backward(None, native.MEM_HOST, None, None, None, None, None, None,
+                                   None, None, None, None, None, None, None) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_set_material(None, 0, None) == native.ERR_INVALID_ARG
     assert native.lib.mpm_destroy(None) == native.OK
     assert native.lib.mpm_last_error(None) == b"invalid mpm context"
 
