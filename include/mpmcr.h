@@ -182,6 +182,10 @@ typedef struct {
      contact-node list, gradient/Hessian scatter (G), node solve (N),
      line-search passes, impulses */
   float solve_us[5];
+  /* substeps whose line-search passes were split over the solve's thread
+     blocks, each pass ending in a device-wide reduction (more contacts than
+     one block line-searches alone) */
+  int32_t ls_split_substeps;
 } mpm_step_stats;
 
 /* Create a context on the current CUDA device. `cuda_stream` is a
@@ -269,7 +273,7 @@ mpm_status mpm_get_grid(mpm_ctx* ctx, int64_t cap, int64_t* count, int32_t* node
    device memory), or that runs where allocation is not allowed. The paper has
    no counterpart; this is a property of the library only.
    The compacted grid is staged in one array inside the library, a file-scope
-   __device__ buffer of 262,144 nodes (9.4 MB) that every GPU loading the
+   __device__ buffer of 262,144 nodes (8,388,864 bytes, 8.4 MB) that every GPU loading the
    library holds until the process exits. The last substep may have swept at
    most 262,144 nodes (4096 blocks of 4^3), else MPM_ERR_CAPACITY (use
    mpm_get_grid). The first call on a device looks up the buffer's address

@@ -1052,6 +1052,7 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
   stats->residual_max = ds.residual_max;
   stats->status_bits = (int32_t)bits;
   stats->p2g_global_chunks = ds.p2g_global_chunks;
+  stats->ls_split_substeps = ds.ls_split;
   for (int k = 0; k < 5; ++k) stats->solve_us[k] = (float)(ds.solve_ns[k] * 1e-3);
   return st;
 }

@@ -24,7 +24,8 @@ struct DevStats {
   int p2g_global_chunks;
   int last_contacts;     // contacts of the last substep
   int last_active;       // active blocks of the last substep
-  int pad[2];
+  int ls_split;          // substeps whose line search was split over the solve's blocks
+  int pad;
   // device time of the contact solve's phases (ns, block 0's view):
   // contact-node list, G, N, line search, impulses
   unsigned long long solve_ns[5];

@@ -746,6 +746,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     atomicAdd(&a.stats->iters_total, it);
     atomicMax(&a.stats->iters_max, it);
     atomicAdd(&a.stats->ls_evals_total, ls_passes);
+    if (!local_ls) atomicAdd(&a.stats->ls_split, 1);
     atomicMax(reinterpret_cast<int*>(&a.stats->residual_max), __float_as_int(resid));
   }
 }

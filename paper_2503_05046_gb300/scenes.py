@@ -183,6 +183,57 @@ def sand_random(n_particles=8000, ppc=1.0, seed=SEED_BASE + 12, dx=0.01, h=1e-4,
             "bodies": bodies, "h": h, "substeps": 10}
 
 
+def sand_slab(n_x=72, n_y=72, n_z=2, seed=SEED_BASE + 13, dx=0.01, h=1e-4, sink=1.2e-5,
+              paddle_overlap=3e-6, v0=(0.02, 0.01, -0.02)):
+    """A thin sand slab (n_x x n_y x n_z lattice at 2 particles per dx per
+    axis, seeded jitter) whose bottom particle layer sits `sink` below the
+    plane z = 0, moving with v0, with a kinematic box paddle along +x whose
+    face overlaps the slab's -x particle column by `paddle_overlap`: a
+    contact-rich case (every particle of the bottom layer, about n_x n_y
+    contacts) small enough for the oracle."""
+    rng = np.random.default_rng(seed)
+    spacing = dx / 2.0
+    jit = 1e-3 * spacing
+    idx = [np.arange(k, dtype=np.float64) for k in (n_x, n_y, n_z)]
+    gz, gy, gx = np.meshgrid(idx[2], idx[1], idx[0], indexing="ij")
+    pts = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], 1) * spacing
+    pts[:, 0] -= (n_x - 1) * spacing / 2.0
+    pts[:, 1] -= (n_y - 1) * spacing / 2.0
+    pts += rng.uniform(-jit, jit, pts.shape)
+    pts[:, 2] += jit - sink  # the lowest particles end up inside the plane
+    x = pts.astype(np.float32)
+    g = {"x": x, "v": np.tile(np.asarray(v0, np.float32), (len(x), 1)), "vol": spacing ** 3,
+         "material": dict(SAND)}
+    edge = (n_x - 1) * spacing / 2.0 + jit
+    height = n_z * spacing
+    bodies = [body(HALFSPACE, mu=0.4),
+              body(BOX, (0.01, n_y * spacing / 2.0 + dx, height + dx),
+                   p=(-edge - 0.01 + paddle_overlap, 0.0, height), v=(0.05, 0, 0), mu=0.4,
+                   kinematic=1)]
+    res_xy = 4 * int(np.ceil((max(n_x, n_y) * spacing / dx + 14) / 4))
+    res_z = 4 * int(np.ceil((n_z * spacing / dx + 16) / 4))
+    grid = {"dx": dx, "res": (res_xy, res_xy, res_z),
+            "origin": (-res_xy * dx / 2, -res_xy * dx / 2, -8 * dx),
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    return {"name": "sand_slab_%d" % len(x), "grid": grid, "groups": [g], "bodies": bodies,
+            "h": h, "substeps": 10}
+
+
+def filled_box(res=12, bc=3, per_axis=20, dx=0.01):
+    """Elastic particles at rest filling a res^3 grid (origin 0) so that every
+    node has mass: per_axis^3 lattice points whose cell coordinates run from
+    0.75 to res - 1.75, so that their stencils cover nodes 0 .. res - 1 and
+    never leave the grid. No bodies. Used to count the Dirichlet layers."""
+    t = np.linspace(0.75, res - 1.75, per_axis) * dx
+    gx, gy, gz = np.meshgrid(t, t, t, indexing="ij")
+    x = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], 1).astype(np.float32)
+    g = {"x": x, "v": np.zeros_like(x), "vol": (dx / 2) ** 3, "material": elastic(1e5, 0.3, 1000.0)}
+    grid = {"dx": dx, "res": (res, res, res), "origin": (0.0, 0.0, 0.0),
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": bc}
+    return {"name": "filled_box_%d" % len(x), "grid": grid, "groups": [g], "bodies": [],
+            "h": 1e-4, "substeps": 1}
+
+
 def batch_scene(index, seed=SEED_BASE + 4, n_min=2000, n_max=64000, dx=5e-3, h=1e-4,
                 penetration=1e-4):
     """Scene `index` of a batch of independent scenes of uneven size: a cube of

@@ -175,3 +175,22 @@ def test_device_tensor_io_matches_host_io(native):
         assert np.array_equal(back[k], out_d[k])
     sim_h.close()
     sim_d.close()
+
+
+@pytest.mark.parametrize("bc", [0, 1, 3])
+def test_dirichlet_layers_counted_by_hand(native, bc):
+    """Domain walls: on a 12^3 grid whose every node has mass, particles at
+    rest under gravity leave exactly (12 - 2 bc)^3 nodes with a nonzero v*
+    (1728, 1000, 216), the nodes with bc <= i, j, k < 12 - bc, each at h g."""
+    sc = scenes.filled_box(bc=bc)
+    sim = native.Sim(sc)
+    sim.step(n_substeps=1)
+    ids, m, vs, v = sim.grid()
+    sim.close()
+    assert len(ids) == 12 ** 3 and np.all(m > 0)
+    moving = np.any(vs != 0.0, axis=1)
+    assert int(moving.sum()) == (12 - 2 * bc) ** 3
+    i, j, k = ids % 12, (ids // 12) % 12, ids // 144
+    inner = (i >= bc) & (i < 12 - bc) & (j >= bc) & (j < 12 - bc) & (k >= bc) & (k < 12 - bc)
+    assert np.array_equal(moving, inner)
+    assert np.allclose(vs[inner], [0.0, 0.0, -9.81e-4], rtol=1e-6, atol=1e-9)

@@ -104,7 +104,8 @@ def run_parity(native, sc, n_sub=2, warm_steps=0, warm_solver=None, tol_v=TOL_V,
             vmax_g = np.max(np.abs(ov))
             bound = 1e-5 * vmax_g + 2.0 * 1e-6 * scale / np.sqrt(np.maximum(om, 1e-300))
             assert np.all(np.abs(v - ov).max(1) <= bound)
-        report.append((k, info.n_contacts, info.iters, stats.iters_total, ev))
+        report.append((k, info.n_contacts, info.iters, stats.iters_total, ev,
+                       stats.ls_split_substeps))
     sim.close()
     return report
 
@@ -184,3 +185,17 @@ def test_random_sparse_sand_parity(native, ppc):
     sc = scenes.sand_random(n_particles=8000, ppc=ppc, penetration=0.02 * 0.01)
     rep = run_parity(native, sc, n_sub=3)
     assert any(r[1] > 0 for r in rep)
+
+
+def test_split_line_search_parity(native):
+    """More contacts than one thread block line-searches alone (4,096): the
+    solve splits each line-search pass over its blocks and ends it in a
+    device-wide reduction (Alg. 1's exact line search, Sec. V-B). A sand slab
+    whose whole bottom layer (72 x 72 particles) is inside the ground, with a
+    paddle on one side: particle and grid velocities, contacts, impulses and
+    the residual against the oracle, substep by substep, and the statistics
+    must show that the split path ran."""
+    sc = scenes.sand_slab()
+    rep = run_parity(native, sc, n_sub=2)
+    assert all(r[1] > 4096 for r in rep), [r[1] for r in rep]
+    assert all(r[5] == 1 for r in rep), "the split line search did not run: %s" % rep

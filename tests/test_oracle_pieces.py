@@ -132,21 +132,58 @@ def test_hencky_P_is_energy_gradient(trial):
     assert np.allclose(tau, P @ F.T, rtol=1e-9, atol=1e-6)
 
 
+def _hencky_grad_hp(F, mu, lam):
+    """Gradient of the Hencky energy density mu sum ln(s_i)^2 + lam/2
+    (sum ln s_i)^2 by central differences in 40-digit arithmetic (mpmath's
+    SVD): at a singular value of 1e-4, double-precision singular values limit
+    a double-precision difference quotient to ~1e-4 relative."""
+    mpmath = pytest.importorskip("mpmath")
+    mp = mpmath.mp
+    mp.dps = 40
+
+    def psi(A):
+        e = [mpmath.log(x) for x in mp.svd_r(mpmath.matrix(A), compute_uv=False)]
+        return mu * sum(x * x for x in e) + lam / 2 * sum(e) ** 2
+
+    Fm = [[mpmath.mpf(float(F[i, j])) for j in range(3)] for i in range(3)]
+    h = mpmath.mpf("1e-20")
+    G = np.zeros((3, 3))
+    for i in range(3):
+        for j in range(3):
+            A = [r[:] for r in Fm]
+            B = [r[:] for r in Fm]
+            A[i][j] += h
+            B[i][j] -= h
+            G[i, j] = float((psi(A) - psi(B)) / (2 * h))
+    return G
+
+
 def test_hencky_tau_clamps_the_strain():
     """Singular values below 1e-4, and the negative one of an inverted F, are
-    clamped before the logarithm: the stress is that of the clamped F with
-    the same rotations."""
+    clamped to 1e-4 before the logarithm: the stress is the Kirchhoff stress
+    of the clamped F_c = U diag(max(s, 1e-4)) V^T (same rotations), pinned
+    here as dpsi/dF (F_c) F_c^T with the gradient of the Hencky energy density
+    taken by central differences at F_c (F_c has no singular value below the
+    clamp, so nothing is clamped there)."""
     mu, lam = O.lame(3.5e5, 0.3)
     rng = np.random.default_rng(11)
+    for trial in range(3):
+        U, V = _rotation(rng), _rotation(rng)
+        s12 = rng.uniform(0.6, 1.4, 2)
+        Fc = U @ np.diag([s12[0], s12[1], 1e-4]) @ V.T
+        expected = _hencky_grad_hp(Fc, mu, lam) @ Fc.T
+        scale = np.max(np.abs(expected))
+        # (an inverted F carries its reflection on the smallest singular value)
+        for s3 in (-0.5, -1e-3, 0.0, 1e-6, 9e-5):
+            F = U @ np.diag([s12[0], s12[1], s3]) @ V.T
+            got = O.hencky_tau(F, mu, lam)
+            assert np.allclose(got, expected, rtol=0, atol=1e-9 * scale), (trial, s3)
+    # a singular value just above the clamp is not clamped: the stress is P F^T
     U, V = _rotation(rng), _rotation(rng)
-    for s3 in (-0.8, 1e-6, 0.0):
-        F = U @ np.diag([1.2, 0.9, s3]) @ V.T
-        Fc = U @ np.diag([1.2, 0.9, 1e-4]) @ V.T
-        assert np.allclose(O.hencky_tau(F, mu, lam), O.hencky_tau(Fc, mu, lam), rtol=1e-9, atol=1e-3)
-    e = np.log([1.2, 0.9, 1e-4])
-    expected = U @ np.diag(2 * mu * e + lam * e.sum()) @ U.T
-    assert np.allclose(O.hencky_tau(U @ np.diag([1.2, 0.9, -0.5]) @ V.T, mu, lam), expected,
-                       rtol=1e-9, atol=1e-3)
+    F = U @ np.diag([1.1, 0.95, 2e-4]) @ V.T
+    expected = _hencky_grad_hp(F, mu, lam) @ F.T
+    assert np.allclose(O.hencky_tau(F, mu, lam), expected, rtol=0,
+                       atol=1e-9 * np.max(np.abs(expected)))
 
 
 def _rotation(rng):

@@ -192,3 +192,23 @@ def test_incline_stick_and_slide(theta, mu, slides):
         assert abs(a - a_exact) < 0.01 * a_exact
     else:
         assert np.max(np.abs(vel[k0:])) < 5 * 1e-4
+
+
+@pytest.mark.parametrize("bc", [0, 1, 3])
+def test_dirichlet_layers_counted_by_hand(bc):
+    """Domain walls (the reading taken where the paper is silent): the nodes
+    within bc_layers of a face are held at v* = 0. On a 12^3 grid whose every
+    node has mass, particles at rest under gravity leave exactly
+    (12 - 2 bc)^3 nodes moving: 1728, 1000 and 6^3 = 216 for 0, 1 and 3
+    layers, and those are the nodes with bc <= i, j, k < 12 - bc."""
+    sc = scenes.filled_box(bc=bc)
+    sim, st, imp, infos = _run(sc, 1)
+    ids, m, vs, v = sim.last_grid()
+    assert len(ids) == 12 ** 3 and np.all(m > 0)
+    moving = np.any(vs != 0.0, axis=1)
+    assert int(moving.sum()) == (12 - 2 * bc) ** 3
+    i, j, k = ids % 12, (ids // 12) % 12, ids // 144
+    inner = (i >= bc) & (i < 12 - bc) & (j >= bc) & (j < 12 - bc) & (k >= bc) & (k < 12 - bc)
+    assert np.array_equal(moving, inner)
+    # free nodes fall with gravity (the particles are at rest and stress-free)
+    assert np.allclose(vs[inner], [0.0, 0.0, -9.81e-4], rtol=0, atol=1e-12)
