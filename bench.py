@@ -1,27 +1,41 @@
 """Throughput of the coupled MPM / rigid-body convex-contact substep on GB300.
 
-Workload (the paper's granular manipulation shape): 1M Drucker-Prager sand
-particles in a 0.3 m box inside a static five-box bin, two kinematic box
-paddles moving through the sand, dx = 3e-3 m on a block-sparse 128^3 grid,
-h = 5e-5 s, N = 10 substeps per rigid time step, solver at the paper's default
-tolerance (eps_r = 5e-2). One bench step is one rigid time step (radix sort +
-10 substeps, each P2G + grid update + quasi-Newton contact solve + G2P).
+Headline workload (the paper's mixed manipulation shape, the largest
+single-GPU configuration): 4M particles in 32 objects (16 corotated elastic
+with E log-uniform in [1e4, 1e6], 16 Drucker-Prager sand), 12 rigid bodies
+(floor, a two-jaw parallel gripper closing on one object, nine static boxes,
+capsules and spheres), dx = 2e-3 m on a block-sparse 320 x 184 x 64 grid,
+h = 2.5e-5 s, N = 10 substeps per rigid time step, the solver at the paper's
+default tolerance (eps_r = 5e-2). One bench step is one rigid time step
+(radix sort + 10 substeps, each P2G + grid update + quasi-Newton contact
+solve + G2P). The 1M-particle granular scooping workload is measured the same
+way and reported under "workloads".
 
 Metric: particle-substeps per second including the contact solve.
   value  device-resident: state in HBM, CUDA events around each mpm_step on the
-         library's stream, L2 flushed (256 MB write) between timed steps.
-  e2e    through the C ABI with host buffers: every step uploads the rigid
-         bodies from host memory, runs mpm_step and reads back the particle
-         positions and the body impulses to host memory.
+         library's stream (CUDA-graph replay), L2 flushed (256 MB write)
+         between timed steps.
+  e2e    the same steps through the C ABI with host buffers: every step uploads
+         the current rigid bodies from host memory, runs mpm_step and reads
+         back the particle positions (pinned host memory) and the body
+         impulses; L2 flushed between steps as above. It replays the first of
+         the timed steps from the same start state.
+  kernels / roofline  per-kernel CUDA-event times of a replay of the same
+         steps with the library's phase events on (direct launches), against
+         algorithmic bytes: P2G 96 B per
+         particle (x, v, C, F) + 16 B per active grid node, G2P 144 B per
+         particle (read x, F; write x, v, C, F).
 Rank r of a torchrun job runs an independent replica on its own GPU (a single
 scene does not shard); value sums the replicas over the slowest rank's time.
 
-`--impl reference` times the FP64 CPU oracle (oracle/) on one host thread, one
-substep of the whole workload per bench step.
+`--impl reference` times the FP64 CPU oracle (oracle/) on the machine's host
+cores (its OpenMP build where it exists), one substep of the whole headline
+workload per bench step.
 """
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import time
@@ -34,13 +48,13 @@ import numpy as np  # noqa: E402
 
 METRIC = "particle-substeps/sec incl. contact solve"
 UNIT = "particle-substeps/s"
-WORKLOAD = "granular_scoop_1M"
-N_PARTICLES = 1_000_000
-# algorithmic bytes per particle per launch (FP32 structure-of-arrays planes)
-P2G_BYTES_PER_PARTICLE = 12 + 12 + 36 + 24 + 2      # read x, v, C, tau, group
-G2P_BYTES_PER_PARTICLE = 12 + 36 + 2 + 12 + 12 + 36 + 36 + 24  # read x, F, group; write x, v, C, F, tau
-GRID_NODE_BYTES_P2G = 16                              # one (m, p) write per active node
-GRID_NODE_BYTES_G2P = 16                              # one v read per active node
+WORKLOAD = "mixed_manipulation_4M"
+SECONDARY = "granular_scoop_1M"
+# algorithmic bytes (FP32 structure-of-arrays planes)
+P2G_BYTES_PER_PARTICLE = 96        # read x, v, C, F
+P2G_BYTES_PER_NODE = 16            # one (m, p) reduction per active node
+G2P_BYTES_PER_PARTICLE = 144       # read x, F; write x, v, C, F
+L2_FLUSH_BYTES = 256 * 1024 * 1024
 
 
 def dist_env():
@@ -76,17 +90,18 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if one exists for
-    the current kernel build (line 'traffic_bytes_per_launch <kernel> <bytes> <n>'
-    with n the particle count of the capture); scaled to the bench's size."""
+def profiled_traffic(kernel, workload, n):
+    """DRAM bytes per launch from the committed ncu summary of the current
+    kernel build, if one exists (line 'traffic_bytes_per_launch <kernel>
+    <workload> <bytes> <particles>'), scaled to n particles."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         parts = line.split()
-        if len(parts) == 4 and parts[0] == "traffic_bytes_per_launch" and parts[1] == kernel:
-            return float(parts[2]) * N_PARTICLES / float(parts[3])
+        if len(parts) == 5 and parts[0] == "traffic_bytes_per_launch" and parts[1] == kernel \
+                and parts[2] == workload:
+            return float(parts[3]) * n / float(parts[4])
     return None
 
 
@@ -144,26 +159,179 @@ class ClockSampler:
 def kernel_launches_per_step(res, n_substeps):
     """Kernels one mpm_step launches: the radix sort (keys, five kernels per
     8-bit digit pass, permutation) and per substep P2G, block compaction,
-    grid update, solve and G2P."""
+    grid update, the two solve kernels (the cluster one and the cooperative
+    one, of which the contact count picks one to work) and G2P."""
     blocks = max(-(-int(r) // 4) for r in res)
     morton_bits = max((blocks - 1).bit_length(), 1)
     key_bits = 3 * morton_bits + (6 if 3 * morton_bits + 6 <= 32 else 0)
     passes = -(-key_bits // 8)
-    return (1 + 5 * passes + 1) + 5 * n_substeps
+    return (1 + 5 * passes + 1) + 6 * n_substeps
+
+
+def workload_name(sc):
+    n = sum(len(g["x"]) for g in sc["groups"])
+    kind = sc["name"].rsplit("_", 1)[0]
+    return "%s_%dM" % (kind, round(n / 1e6)) if n >= 1_000_000 else sc["name"]
 
 
 def bench_config(sc, n, ws):
     """The workload description shared by both arms' JSON lines."""
-    return {"workload": WORKLOAD, "particles": n, "material": "drucker_prager_sand",
-            "bodies": len(sc["bodies"]), "dx": sc["grid"]["dx"], "grid": list(sc["grid"]["res"]),
-            "h": sc["h"], "substeps_per_step": sc["substeps"], "eps_r": 5e-2,
-            "l2": "flushed between timed steps (256 MB write)",
+    models = sorted({int(g["material"]["model"]) for g in sc["groups"]})
+    return {"workload": workload_name(sc), "particles": n,
+            "materials": ["corotated_elastic" if m == 0 else "drucker_prager_sand" for m in models],
+            "objects": len(sc["groups"]), "bodies": len(sc["bodies"]), "dx": sc["grid"]["dx"],
+            "grid": list(sc["grid"]["res"]), "h": sc["h"], "substeps_per_step": sc["substeps"],
+            "eps_r": 5e-2,
+            "l2": "flushed between timed steps (256 MB write); particle state %d MB" %
+                  round(126 * n / 1e6),
             "parallelism": "replica per GPU" if ws > 1 else "single GPU"}
 
 
-def make_scene(n=N_PARTICLES):
+def make_scene(name=WORKLOAD):
     from paper_2503_05046_gb300 import scenes
-    return scenes.granular_scoop(n_particles=n)
+    if name == SECONDARY:
+        return scenes.granular_scoop(n_particles=1_000_000)
+    return scenes.mixed_manipulation()
+
+
+def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
+    """Device-resident throughput, kernel split, end-to-end throughput through
+    the C ABI and a tightly solved step of one workload."""
+    import torch
+    n = sum(len(g["x"]) for g in sc["groups"])
+    N = sc["substeps"]
+    sim = native.Sim(sc, max_contacts=2 * n)
+    stream = sim.torch_stream  # the library's stream: events and the L2 flush go here
+    solver = native.solver_params(eps_r=5e-2, max_iters=args.max_iters)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        sim.step(solver=solver, stats=False, check=False)
+    sim.step(n_substeps=0, solver=solver, check=False)  # drain warm-up status
+
+    def timed_steps(k):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        torch.cuda.synchronize()
+        for i in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            starts[i].record(stream)
+            native.mpm_step(sim.ctx, sc["h"], N, solver, want_stats=False)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+    # every leg starts from the same state: the steps they time are the same
+    st0, b0 = sim.get_particles(), sim.bodies()
+
+    def restore():
+        sim.set_particles(st0["x"], st0["v"], st0["C"], st0["F"])
+        sim.set_bodies(b0)
+
+    # --- headline: graph replay, CUDA events around each step
+    if ws > 1:
+        torch.distributed.barrier()
+    step_ms = timed_steps(args.steps)
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = sum(step_ms)
+    code_timed, _ = sim.step(n_substeps=0, solver=solver, check=False)
+    seconds = max_over_ranks(ms / 1e3, ws)
+    value = whole_job_value(float(n) * N * args.steps, ws, seconds)
+
+    # --- e2e through the C ABI with host buffers (current bodies up, x and
+    # impulses down every step) over the first of the same steps, with the
+    # same L2 policy and graph replay
+    restore()
+    nb = len(sc["bodies"])
+    x_host = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
+    imp_host = np.zeros(6 * max(nb, 1))
+    arr = (native.RigidBody * max(nb, 1))()
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        native.lib.mpm_get_rigid_bodies(sim.ctx, nb, arr)   # host copy of the current bodies
+        native.lib.mpm_set_rigid_bodies(sim.ctx, nb, arr)   # uploaded with the step
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        native.mpm_step(sim.ctx, sc["h"], N, solver, want_stats=False)
+        native.mpm_get_particles(sim.ctx, x_host, None, None, None)
+        native.lib.mpm_get_rigid_impulses(sim.ctx, imp_host.ctypes.data_as(native._dp), 1)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e_value = whole_job_value(float(n) * N * e2e_steps, ws, e2e_s)
+    same_steps_ms = sum(step_ms[:e2e_steps]) if e2e_steps <= len(step_ms) else None
+
+    # --- kernel split: the same steps again with the phase events on
+    restore()
+    native.mpm_set_option(sim.ctx, native.OPT_PROFILE, 1)
+    native.mpm_get_phase_times(sim.ctx, reset=True)
+    ms_prof = sum(timed_steps(args.steps))
+    phase_ms, phase_n = native.mpm_get_phase_times(sim.ctx, reset=True)
+    native.mpm_set_option(sim.ctx, native.OPT_PROFILE, 0)
+    code_stats, st = sim.step(solver=solver, check=False)  # statistics (not timed)
+    act_nodes = st.active_blocks_max * 64
+
+    out = {"value": value, "ms_per_step": ms / args.steps, "steps": args.steps,
+           "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+                   "h2d_bytes_per_step": int(nb * C_sizeof_body(native)),
+                   "d2h_bytes_per_step": int(12 * n + 48 * nb),
+                   "device_ms_same_steps": same_steps_ms, "host_ms": 1e3 * e2e_s},
+           "ms_per_step_profiled": ms_prof / args.steps,
+           "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
+           "solver": {"iters_per_substep": st.iters_total / max(st.substeps, 1),
+                      "ls_passes_per_iter": st.ls_evals_total / max(st.iters_total, 1),
+                      "contacts_max": st.contacts_max, "residual_max": st.residual_max,
+                      "active_blocks_max": st.active_blocks_max, "status_bits": st.status_bits,
+                      "p2g_global_chunks": st.p2g_global_chunks,
+                      "status_timed": native.STATUS_NAMES[code_timed],
+                      "solve_us_per_substep": [u / max(st.substeps, 1) for u in st.solve_us]},
+           "launches_per_step": kernel_launches_per_step(sc["grid"]["res"], N)}
+
+    peak, peak_kind = measured_peak_hbm()
+    kern = {}
+    for name, per_p, per_node in (("p2g", P2G_BYTES_PER_PARTICLE, P2G_BYTES_PER_NODE),
+                                  ("g2p", G2P_BYTES_PER_PARTICLE, 0)):
+        launches = max(int(phase_n[name]), 1)
+        avg_s = phase_ms[name] / launches / 1e3
+        bytes_launch = per_p * n + per_node * act_nodes
+        gbps = bytes_launch / avg_s / 1e9 if avg_s > 0 else 0.0
+        kern[name] = {"avg_us": avg_s * 1e6, "launches": int(phase_n[name]),
+                      "bytes_per_launch": bytes_launch, "GBps": gbps, "frac": gbps / peak}
+    solve_launches = max(int(phase_n["solve"]), 1)
+    kern["solve"] = {"avg_us": phase_ms["solve"] / solve_launches * 1e3,
+                     "launches": int(phase_n["solve"]),
+                     "us_per_qn_iter": (phase_ms["solve"] * 1e3 / max(
+                         out["solver"]["iters_per_substep"] * solve_launches, 1e-9))}
+    out["kernels"] = kern
+    dom = max(("p2g", "g2p"), key=lambda k: phase_ms[k])
+    wl = workload_name(sc)
+    out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GBps"], "peak": peak,
+                       "peak_kind": peak_kind, "unit": "GB/s", "frac": kern[dom]["GBps"] / peak,
+                       "traffic": profiled_traffic(dom, wl, n)}
+
+    # --- the same workload solved to the contact residual 1e-6 (one step)
+    if tight:
+        tsolver = native.solver_params(eps_r=1e-6, eps_a=0.0, max_iters=200000)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        code_t, st_t = native.mpm_step(sim.ctx, sc["h"], N, tsolver, want_stats=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_ms = ev0.elapsed_time(ev1)
+        iters = st_t.iters_total / max(st_t.substeps, 1)
+        out["tight_solve"] = {
+            "eps_r": 1e-6, "value": float(n) * N / (t_ms / 1e3), "unit": UNIT, "ms_per_step": t_ms,
+            "iters_per_substep": iters, "contacts_max": st_t.contacts_max,
+            "ls_passes_per_iter": st_t.ls_evals_total / max(st_t.iters_total, 1),
+            "solve_us_per_qn_iter": sum(st_t.solve_us[1:4]) / max(st_t.iters_total, 1),
+            "residual_max": st_t.residual_max, "status": native.STATUS_NAMES[code_t], "steps": 1}
+    out["state"] = sim.get_particles()
+    out["bodies"] = sim.bodies()
+    sim.close()
+    return out
 
 
 def run_ours(args):
@@ -174,123 +342,38 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     from paper_2503_05046_gb300 import native
-    sc = make_scene()
+    sc = make_scene(WORKLOAD)
     n = sum(len(g["x"]) for g in sc["groups"])
-    N = sc["substeps"]
-    sim = native.Sim(sc, max_contacts=2 * n)
-    stream = sim.torch_stream  # the library's stream: events and the L2 flush go here
-    solver = native.solver_params(eps_r=5e-2, max_iters=args.max_iters)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        sim.step(solver=solver, stats=False, check=False)
-    sim.step(n_substeps=0, solver=solver, check=False)  # drain warm-up status
-    native.mpm_set_option(sim.ctx, native.OPT_PROFILE, 1)
-    native.mpm_get_phase_times(sim.ctx, reset=True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        starts[k].record(stream)
-        code, stt = native.mpm_step(sim.ctx, sc["h"], N, solver, want_stats=False)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    head = measure_workload(native, sc, args, ws, tight=not args.no_small)
     clk = clocks.stop()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    phase_ms, phase_n = native.mpm_get_phase_times(sim.ctx, reset=True)
-    native.mpm_set_option(sim.ctx, native.OPT_PROFILE, 0)
-    code_timed, _ = sim.step(n_substeps=0, solver=solver, check=False)
-    seconds = max_over_ranks(ms / 1e3, ws)
-    units = float(n) * N * args.steps
-    value = whole_job_value(units, ws, seconds)
-    # one more step with statistics (not timed) for the report
-    code_stats, st = sim.step(solver=solver, check=False)
-    act_nodes = st.active_blocks_max * 64
-
-    # --- e2e through the C ABI with host buffers
-    bodies = [native.make_body(b) for b in sc["bodies"]]
-    arr = (native.RigidBody * len(bodies))(*bodies)
-    x_host = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
-    imp_host = np.zeros(6 * len(bodies))
-    e2e_steps = max(3, min(args.steps, 10))
-    for k in range(e2e_steps + 1):
-        if k == 1:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-        native.lib.mpm_set_rigid_bodies(sim.ctx, len(bodies), arr)
-        native.mpm_step(sim.ctx, sc["h"], N, solver, want_stats=False)
-        native.mpm_get_particles(sim.ctx, x_host, None, None, None)
-        native.lib.mpm_get_rigid_impulses(sim.ctx, imp_host.ctypes.data_as(native._dp), 1)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
-    e2e_value = whole_job_value(float(n) * N * e2e_steps, ws, e2e_s)
-
-    # --- the same workload solved to the contact residual 1e-6 (one step)
-    tight = None
-    if not args.no_small:
-        tsolver = native.solver_params(eps_r=1e-6, eps_a=0.0, max_iters=200000)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        code_t, st_t = native.mpm_step(sim.ctx, sc["h"], N, tsolver, want_stats=True)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        t_ms = ev0.elapsed_time(ev1)
-        tight = {"eps_r": 1e-6, "value": float(n) * N / (t_ms / 1e3), "unit": UNIT,
-                 "ms_per_step": t_ms, "iters_per_substep": st_t.iters_total / max(st_t.substeps, 1),
-                 "residual_max": st_t.residual_max, "status": native.STATUS_NAMES[code_t],
-                 "steps": 1}
-
-    peak, peak_kind = measured_peak_hbm()
-    kern = {}
-    for name, per_p, per_node in (("p2g", P2G_BYTES_PER_PARTICLE, GRID_NODE_BYTES_P2G),
-                                  ("g2p", G2P_BYTES_PER_PARTICLE, GRID_NODE_BYTES_G2P)):
-        launches = max(int(phase_n[name]), 1)
-        avg_s = phase_ms[name] / launches / 1e3
-        bytes_launch = per_p * n + per_node * act_nodes
-        kern[name] = {"avg_us": avg_s * 1e6, "launches": int(phase_n[name]),
-                      "bytes_per_launch": bytes_launch,
-                      "GBps": bytes_launch / avg_s / 1e9 if avg_s > 0 else 0.0}
-    dom = max(("p2g", "g2p"), key=lambda k: phase_ms[k])
-    roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GBps"], "peak": peak,
-            "peak_kind": peak_kind, "unit": "GB/s", "frac": kern[dom]["GBps"] / peak,
-            "traffic": profiled_traffic(dom)}
-    launches_per_step = kernel_launches_per_step(sc["grid"]["res"], N)
+    sc2 = make_scene(SECONDARY)
+    second = measure_workload(native, sc2, args, ws, tight=not args.no_small)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": bench_config(sc, n, ws),
-        "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": int(len(bodies) * C_sizeof_body(native)),
-                "d2h_bytes_per_step": int(12 * n + 48 * len(bodies))},
-        "gpu_launches": launches_per_step * args.steps,
-        "roofline": roof,
-        "kernels": kern,
-        "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
-        "solver": {"iters_per_substep": st.iters_total / max(st.substeps, 1),
-                   "contacts_max": st.contacts_max, "residual_max": st.residual_max,
-                   "active_blocks_max": st.active_blocks_max, "status_bits": st.status_bits,
-                   "p2g_global_chunks": st.p2g_global_chunks,
-                   "status_timed": native.STATUS_NAMES[code_timed]},
+        "e2e": head["e2e"],
+        "gpu_launches": head["launches_per_step"] * args.steps,
+        "roofline": head["roofline"],
     }
+    for key in ("kernels", "phase_ms_per_step", "ms_per_step_profiled", "solver", "tight_solve"):
+        if key in head:
+            line[key] = head[key]
     if clk:
         line["clocks"] = clk
-    if tight is not None:
-        line["tight_solve"] = tight
+    n2 = sum(len(g["x"]) for g in sc2["groups"])
+    line["workloads"] = {SECONDARY: dict(
+        {k: v for k, v in second.items() if k not in ("state", "bodies", "launches_per_step")},
+        config=bench_config(sc2, n2, ws))}
     if not args.no_small:
         line["small_scenes"] = small_scene_latency(native)
         line["batched"] = batched_throughput(native)
         line["differentiation"] = differentiation(native)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc, sim, native)
-    sim.close()
+        line["cpu_baseline"] = cpu_baseline({WORKLOAD: (sc, head), SECONDARY: (sc2, second)})
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -503,68 +586,131 @@ def C_sizeof_body(native):
 def oracle_state(sc, state):
     """Oracle particle state (FP64) of a float32 particle state of the scene."""
     import oracle as O
-    g = sc["groups"][0]
-    m = len(state["x"])
-    V = float(np.float32(g["vol"]))
+    mass, vol, mat = [], [], []
+    for gi, g in enumerate(sc["groups"]):
+        k = len(g["x"])
+        V = float(np.float32(g["vol"]))
+        mass.append(np.full(k, V * float(np.float32(g["material"]["rho"]))))
+        vol.append(np.full(k, V))
+        mat.append(np.full(k, gi, np.int32))
     return O.Sim.state({"x": state["x"], "v": state["v"], "C": state["C"], "F": state["F"],
-                        "mass": np.full(m, V * float(np.float32(g["material"]["rho"]))),
-                        "vol": np.full(m, V), "mat": np.zeros(m, np.int32)})
+                        "mass": np.concatenate(mass), "vol": np.concatenate(vol),
+                        "mat": np.concatenate(mat)})
 
 
-def oracle_runner(sc):
-    """(advance, n): advance(st, k) runs k oracle substeps of the whole scene
-    on state st and returns the seconds taken."""
+def oracle_runner(sc, bodies=None, openmp=False, eps_r=5e-2):
+    """advance(st, k): k oracle substeps of the whole scene on state st (the
+    bodies frozen, as within one rigid step); returns the seconds taken."""
     import oracle as O
-    _, mats = O.from_scene({"groups": [sc["groups"][0]]})
-    osim = O.Sim(sc["grid"])
-    bodies = [O.make_body(b) for b in O.bodies_from_scene(sc)]
-    S = O.solver(eps_r=5e-2, max_iters=1000)
+    _, mats = O.from_scene(sc)
+    osim = O.Sim(sc["grid"], openmp=openmp)
+    bds = [O.make_body(b) for b in O.bodies_from_scene({"bodies": bodies if bodies is not None
+                                                         else sc["bodies"]})]
+    S = O.solver(eps_r=eps_r, max_iters=1000)
 
     def advance(st, k):
         t0 = time.perf_counter()
         for _ in range(k):
-            osim.substep(st, mats, bodies, sc["h"], S)
+            osim.substep(st, mats, bds, sc["h"], S)
         return time.perf_counter() - t0
     return advance
 
 
-def cpu_baseline(sc, sim, native):
-    """The FP64 oracle (one host thread) on one whole bench step: all
-    particles, all bodies, the step's N substeps, from the bench's state."""
-    state = sim.get_particles()
-    n = len(state["x"])
-    st = oracle_state(sc, state)
-    secs = oracle_runner(sc)(st, sc["substeps"])
-    return {"value": n * sc["substeps"] / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "FP64 oracle, 1 thread: one bench step (%d substeps) of all %d particles "
-                      "and %d bodies from the bench state; %.1f s" % (sc["substeps"], n,
-                                                                       len(sc["bodies"]), secs)}
+def host_info():
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            low = line.lower()
+            if low.startswith("model name") or low.startswith("cpu part"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"host_cores": os.cpu_count(), "cpu": model, "machine": platform.machine()}
+
+
+def oracle_available(openmp):
+    try:
+        import oracle as O
+        O.lib(openmp)
+        return True
+    except Exception:
+        return False
+
+
+def cpu_baseline(measured):
+    """The FP64 oracle on the machine's host cores, on bounded samples of each
+    workload from the state the GPU run left (one substep of the 4M and 1M
+    workloads), the 8k cube of SURVEY's first configuration whole (200
+    substeps) and one checkpoint interval (25 substeps) of the 65,536-particle
+    differentiation workload: single-threaded (the oracle as written) and its
+    OpenMP build over all host cores."""
+    from paper_2503_05046_gb300 import scenes
+    import oracle as O
+    omp = oracle_available(True)
+    builds = [(False, 1)] + ([(True, O.threads(True))] if omp else [])
+    samples = []
+    for name, (sc, res) in measured.items():
+        samples.append((name, sc, res["state"], res["bodies"], 1))
+    c1 = scenes.cube_drop()
+    samples.append(("cube_drop_8k", c1, None, None, 200))
+    c4, _ = scenes.push_cube()
+    samples.append(("push_cube_65536", c4, None, None, 25))
+    per = {}
+    for name, sc, state, bodies, k in samples:
+        n = sum(len(g["x"]) for g in sc["groups"])
+        row = {"particles": n, "substeps": k}
+        for openmp, threads in builds:
+            if state is None:
+                st, _ = O.from_scene(sc)
+            else:
+                st = oracle_state(sc, state)
+            secs = oracle_runner(sc, bodies, openmp)(st, k)
+            row["all_cores" if openmp else "single_thread"] = {
+                "value": n * k / secs, "seconds": secs, "threads": threads}
+        per[name] = row
+    head = per[WORKLOAD]
+    best = head.get("all_cores", head["single_thread"])
+    out = {"value": best["value"], "unit": UNIT, "cores": best["threads"], "kind": "oracle",
+           "sample": "FP64 oracle (%s) on one substep of all %d particles and %d bodies of %s "
+                     "from the bench's state; %.1f s" % (
+                         "OpenMP build, %d threads" % best["threads"] if "all_cores" in head
+                         else "1 thread", head["particles"], len(measured[WORKLOAD][0]["bodies"]),
+                         WORKLOAD, best["seconds"]),
+           "single_thread": {"value": head["single_thread"]["value"], "cores": 1},
+           "workloads": per}
+    out.update(host_info())
+    if not omp:
+        out["all_cores"] = "unavailable: the OpenMP build of the oracle did not compile"
+    return out
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle on the host, one substep of the whole
-    workload (all particles and bodies) per bench step."""
+    """Reference arm: the FP64 oracle on the host cores (its OpenMP build where
+    it exists), one substep of the whole headline workload (all particles and
+    bodies) per bench step."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     sc = make_scene()
-    g = sc["groups"][0]
-    n = len(g["x"])
-    state = {"x": g["x"], "v": g["v"], "C": np.zeros((n, 3, 3), np.float32),
-             "F": np.tile(np.eye(3, dtype=np.float32), (n, 1, 1))}
-    st = oracle_state(sc, state)
-    advance = oracle_runner(sc)
+    import oracle as O
+    omp = oracle_available(True)
+    st, _ = O.from_scene(sc)
+    n = len(st["x"])
+    advance = oracle_runner(sc, openmp=omp)
     advance(st, args.warmup)
     total_s = sum(advance(st, 1) for _ in range(args.steps))
     value = n * args.steps / total_s
+    threads = O.threads(True) if omp else 1
     cfg = bench_config(sc, n, ws)
     cfg["sample"] = "one substep of the whole workload per bench step, after %d warm-up substeps" % args.warmup
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": cfg["sample"] + ", FP64 oracle on 1 host thread"},
+            "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                  "sample": cfg["sample"] + ", FP64 oracle on %d host thread%s" % (
+                                      threads, "s" if threads > 1 else "")}, **host_info()),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -577,7 +723,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--max-iters", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-small", action="store_true", help="skip the 8k-particle latency cases")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the small-scene, batched, differentiation and tight-solve legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -67,15 +67,17 @@ class SubstepInfo(C.Structure):
                 ("P", C.c_double), ("J", C.c_double)]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    """Load (building first if needed) the oracle shared library."""
-    global _lib
-    if _lib is None:
-        path = _build.build()
+def lib(openmp=False):
+    """Load (building first if needed) the oracle shared library: the serial
+    checker, or with openmp=True its all-core build (CPU baseline only)."""
+    key = bool(openmp)
+    if key not in _libs:
+        path = _build.build(openmp=key)
         L = C.CDLL(path)
+        L.orc_threads.restype = C.c_int
         L.orc_bspline.argtypes = [C.c_double, _dp, _dp, _ip, _dp, _dp]
         L.orc_svd3.argtypes = [_dp, _dp, _dp, _dp]
         L.orc_lame.argtypes = [C.c_double, C.c_double, _dp, _dp]
@@ -109,8 +111,13 @@ def lib():
         L.orc_contact_adjoint.argtypes = [C.POINTER(Problem), _dp, _dp, _dp, _dp, _dp]
         L.orc_rigid_dynamics_step.argtypes = [C.POINTER(Body), C.POINTER(Dynamics), _dp, _dp,
                                               C.c_double]
-        _lib = L
-    return _lib
+        _libs[key] = L
+    return _libs[key]
+
+
+def threads(openmp=False):
+    """Threads one substep of that build uses (1 for the serial checker)."""
+    return int(lib(openmp).orc_threads())
 
 
 def _d(a):
@@ -325,7 +332,8 @@ class Sim:
     friction_angle_deg}. grid: dict {dx, res, origin, gravity, bc_layers}.
     """
 
-    def __init__(self, grid):
+    def __init__(self, grid, openmp=False):
+        self.L = lib(openmp)
         g = Grid()
         g.dx = float(grid["dx"])
         for i in range(3):
@@ -334,11 +342,11 @@ class Sim:
             g.gravity[i] = float(grid.get("gravity", (0.0, 0.0, -9.81))[i])
         g.bc_layers = int(grid.get("bc_layers", 3))
         self.grid = g
-        self.h = lib().orc_create(C.byref(g))
+        self.h = self.L.orc_create(C.byref(g))
 
     def close(self):
         if self.h:
-            lib().orc_destroy(self.h)
+            self.L.orc_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -374,28 +382,28 @@ class Sim:
             bs[i] = b if isinstance(b, Body) else make_body(b)
         imp = impulses if impulses is not None else np.zeros(6 * max(nb, 1))
         info = SubstepInfo()
-        st_code = lib().orc_substep(self.h, n, _d(st["x"]), _d(st["v"]), _d(st["C"]), _d(st["F"]),
+        st_code = self.L.orc_substep(self.h, n, _d(st["x"]), _d(st["v"]), _d(st["C"]), _d(st["F"]),
                                     _d(st["mass"]), _d(st["vol"]), _i(st["mat"]), len(materials),
                                     mats, nb, bs, float(h), C.byref(S), _d(imp), C.byref(info))
         return st_code, info
 
     def last_grid(self):
-        n = lib().orc_last_grid(self.h, 0, None, None, None, None)
+        n = self.L.orc_last_grid(self.h, 0, None, None, None, None)
         ids = np.zeros(n, np.int32)
         m = np.zeros(n)
         vs = np.zeros(3 * n)
         v = np.zeros(3 * n)
-        lib().orc_last_grid(self.h, n, _i(ids), _d(m), _d(vs), _d(v))
+        self.L.orc_last_grid(self.h, n, _i(ids), _d(m), _d(vs), _d(v))
         return ids, m, vs.reshape(n, 3), v.reshape(n, 3)
 
     def last_contacts(self):
-        n = lib().orc_last_contacts(self.h, 0, None, None, None, None, None)
+        n = self.L.orc_last_contacts(self.h, 0, None, None, None, None, None)
         p = np.zeros(n, np.int32)
         b = np.zeros(n, np.int32)
         g = np.zeros(3 * n)
         phi = np.zeros(n)
         n0 = np.zeros(n)
-        lib().orc_last_contacts(self.h, n, _i(p), _i(b), _d(g), _d(phi), _d(n0))
+        self.L.orc_last_contacts(self.h, n, _i(p), _i(b), _d(g), _d(phi), _d(n0))
         return p, b, g.reshape(n, 3), phi, n0
 
 

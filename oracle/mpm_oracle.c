@@ -14,6 +14,17 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------- */
 /* small 3x3 helpers                                                          */
@@ -892,12 +903,177 @@ static void kirchhoff_stress(const orc_material* mt, const double F[9], double t
     orc_corotated_tau(F, mu, lam, tau);
 }
 
+/* P2G of particle q (MLS-MPM, Eq. (6)): its mass and its momentum with the
+   affine and stress terms, scattered to the 27 nodes of its stencil. */
+static void p2g_particle(orc_sim* s, int q, const double* x, const double* v, const double* C,
+                         const double* F, const double* mass, const double* vol, const int* mat,
+                         const orc_material* mats, double h) {
+  const orc_grid* g = &s->g;
+  const double dx = g->dx, Dinv = 4.0 / (dx * dx);
+  int base[3];
+  double fx[3], w[9], tau[9], aff[9];
+  orc_bspline(dx, g->origin, x + 3 * q, base, fx, w);
+  kirchhoff_stress(&mats[mat[q]], F + 9 * q, tau);
+  for (int e = 0; e < 9; ++e) aff[e] = mass[q] * C[9 * q + e] - h * Dinv * vol[q] * tau[e];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) {
+        double wt = w[a] * w[3 + b] * w[6 + c];
+        double dpos[3] = {(a - fx[0]) * dx, (b - fx[1]) * dx, (c - fx[2]) * dx};
+        size_t i = node_id(g, base[0] + a, base[1] + b, base[2] + c);
+        s->m[i] += wt * mass[q];
+        for (int r = 0; r < 3; ++r)
+          s->p[3 * i + r] += wt * (mass[q] * v[3 * q + r] + aff[3 * r] * dpos[0] +
+                                   aff[3 * r + 1] * dpos[1] + aff[3 * r + 2] * dpos[2]);
+      }
+}
+
+/* G2P of particle q with the constitutive update (Sec. V-A op (3)): velocity,
+   affine matrix, position, deformation gradient, and for sand the
+   Drucker-Prager return map. */
+static void g2p_particle(const orc_sim* s, int q, double* x, double* v, double* C, double* F,
+                         const int* mat, const orc_material* mats, double h) {
+  const orc_grid* g = &s->g;
+  const double dx = g->dx, Dinv = 4.0 / (dx * dx);
+  int base[3];
+  double fx[3], w[9];
+  orc_bspline(dx, g->origin, x + 3 * q, base, fx, w);
+  double vp[3] = {0, 0, 0}, Bm[9] = {0};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) {
+        double wt = w[a] * w[3 + b] * w[6 + c];
+        double dpos[3] = {(a - fx[0]) * dx, (b - fx[1]) * dx, (c - fx[2]) * dx};
+        size_t i = node_id(g, base[0] + a, base[1] + b, base[2] + c);
+        for (int r = 0; r < 3; ++r) {
+          vp[r] += wt * s->v[3 * i + r];
+          for (int cc = 0; cc < 3; ++cc) Bm[3 * r + cc] += wt * s->v[3 * i + r] * dpos[cc];
+        }
+      }
+  for (int r = 0; r < 3; ++r) {
+    v[3 * q + r] = vp[r];
+    x[3 * q + r] += h * vp[r];
+  }
+  for (int e = 0; e < 9; ++e) C[9 * q + e] = Dinv * Bm[e];
+  double Fu[9];
+  for (int e = 0; e < 9; ++e) Fu[e] = h * C[9 * q + e];
+  Fu[0] += 1.0; Fu[4] += 1.0; Fu[8] += 1.0;
+  mat_mul(Fu, F + 9 * q, F + 9 * q);
+  const orc_material* mt = &mats[mat[q]];
+  if (mt->model == ORC_DRUCKER_PRAGER) {
+    double mu, lam;
+    orc_lame(mt->E, mt->nu, &mu, &lam);
+    orc_dp_project(F + 9 * q, mu, lam, mt->friction_angle_deg, F + 9 * q);
+  }
+}
+
+#ifdef _OPENMP
+/* Multi-threaded build (a CPU baseline over all host cores, not the checker):
+   P2G over slabs of 4 nodes along the longest grid axis. A particle's stencil
+   spans its base node and the next two, so particles of slabs two apart never
+   touch the same node: the even slabs run in parallel, then the odd ones,
+   each slab's particles in id order. Only the order in which a node sums its
+   contributions differs from the serial build. */
+static void p2g_slabs(orc_sim* s, int n, const double* x, const double* v, const double* C,
+                      const double* F, const double* mass, const double* vol, const int* mat,
+                      const orc_material* mats, double h) {
+  const orc_grid* g = &s->g;
+  int ax = 0;
+  for (int a = 1; a < 3; ++a)
+    if (g->res[a] > g->res[ax]) ax = a;
+  const int n_slabs = (g->res[ax] + 3) / 4;
+  int* slab = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  int* start = (int*)calloc((size_t)n_slabs + 1, sizeof(int));
+  int* order = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
+  for (int q = 0; q < n; ++q) {
+    int base[3];
+    double fx[3], w[9];
+    orc_bspline(g->dx, g->origin, x + 3 * q, base, fx, w);
+    slab[q] = base[ax] / 4;
+  }
+  for (int q = 0; q < n; ++q) start[slab[q] + 1] += 1;
+  for (int k = 0; k < n_slabs; ++k) start[k + 1] += start[k];
+  int* fill = (int*)malloc(sizeof(int) * ((size_t)n_slabs + 1));
+  memcpy(fill, start, sizeof(int) * ((size_t)n_slabs + 1));
+  for (int q = 0; q < n; ++q) order[fill[slab[q]]++] = q;
+  for (int parity = 0; parity < 2; ++parity) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = parity; k < n_slabs; k += 2)
+      for (int t = start[k]; t < start[k + 1]; ++t)
+        p2g_particle(s, order[t], x, v, C, F, mass, vol, mat, mats, h);
+  }
+  free(slab); free(start); free(order); free(fill);
+}
+#endif
+
+/* Contact records of one substep (Sec. V-B), grown by contacts_alloc. */
+typedef struct {
+  int cap;
+  int *p, *b, *nodes;
+  double *w, *R, *bias, *phi0, *n0, *mu, *k, *d;
+} orc_contacts;
+
+/* (Re)allocate the records for `cap` contacts, keeping the existing ones
+   (K starts zeroed). */
+static void contacts_alloc(orc_contacts* K, int cap) {
+  K->cap = cap;
+  K->p = (int*)realloc(K->p, sizeof(int) * cap);
+  K->b = (int*)realloc(K->b, sizeof(int) * cap);
+  K->nodes = (int*)realloc(K->nodes, sizeof(int) * 27 * cap);
+  K->w = (double*)realloc(K->w, sizeof(double) * 27 * cap);
+  K->R = (double*)realloc(K->R, sizeof(double) * 9 * cap);
+  K->bias = (double*)realloc(K->bias, sizeof(double) * 3 * cap);
+  K->phi0 = (double*)realloc(K->phi0, sizeof(double) * cap);
+  K->n0 = (double*)realloc(K->n0, sizeof(double) * cap);
+  K->mu = (double*)realloc(K->mu, sizeof(double) * cap);
+  K->k = (double*)realloc(K->k, sizeof(double) * cap);
+  K->d = (double*)realloc(K->d, sizeof(double) * cap);
+}
+
+/* Contact record slot of particle q inside body bd (phi < 0, outward normal
+   nrm): stencil DoFs and weights, contact frame (z = n), bias
+   b = -R^T v_rigid(x_p) so that v_c = R^T (v_particle - v_rigid), depth
+   phi0 = -phi and the lagged normal impulse from the particle's
+   start-of-substep relative normal velocity. */
+static void register_contact(const orc_sim* s, orc_contacts* K, int slot, int q, int bi,
+                             const orc_body* bd, double phi, const double nrm[3], const double* x,
+                             const double* v, double h) {
+  const orc_grid* g = &s->g;
+  int base[3];
+  double fx[3], w[9];
+  orc_bspline(g->dx, g->origin, x + 3 * q, base, fx, w);
+  int sidx = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c, ++sidx) {
+        size_t i = node_id(g, base[0] + a, base[1] + b, base[2] + c);
+        K->nodes[27 * slot + sidx] = s->dof[i];
+        K->w[27 * slot + sidx] = w[a] * w[3 + b] * w[6 + c];
+      }
+  double* R = K->R + 9 * slot;
+  orc_contact_frame(nrm, 0.0, R);
+  double vr[3];
+  orc_body_velocity(bd, x + 3 * q, vr);
+  for (int c = 0; c < 3; ++c)
+    K->bias[3 * slot + c] = -(R[c] * vr[0] + R[3 + c] * vr[1] + R[6 + c] * vr[2]);
+  K->phi0[slot] = -phi;
+  double vrel[3] = {v[3 * q] - vr[0], v[3 * q + 1] - vr[1], v[3 * q + 2] - vr[2]};
+  double vn0 = dot3(nrm, vrel);
+  K->n0[slot] = orc_normal_impulse(-phi, bd->k, bd->d, h, vn0);
+  K->mu[slot] = bd->mu;
+  K->k[slot] = bd->k;
+  K->d[slot] = bd->d;
+  K->p[slot] = q;
+  K->b[slot] = bi;
+}
+
 int orc_substep(orc_sim* s, int n, double* x, double* v, double* C, double* F,
                 const double* mass, const double* vol, const int* mat, int n_mat,
                 const orc_material* mats, int nb, const orc_body* bodies, double h,
                 const orc_solver* S, double* impulses, orc_substep_info* info) {
   const orc_grid* g = &s->g;
-  const double dx = g->dx, Dinv = 4.0 / (dx * dx);
+  const double dx = g->dx;
   orc_substep_info inf = {0};
   /* every stencil must lie inside the domain */
   for (int q = 0; q < n; ++q) {
@@ -920,24 +1096,11 @@ int orc_substep(orc_sim* s, int n, double* x, double* v, double* C, double* F,
   memset(s->p, 0, 3 * s->nn * sizeof(double));
 
   /* P2G (MLS-MPM): mass and momentum with the stress term, Eq. (6) */
-  for (int q = 0; q < n; ++q) {
-    int base[3];
-    double fx[3], w[9], tau[9], aff[9];
-    orc_bspline(dx, g->origin, x + 3 * q, base, fx, w);
-    kirchhoff_stress(&mats[mat[q]], F + 9 * q, tau);
-    for (int e = 0; e < 9; ++e) aff[e] = mass[q] * C[9 * q + e] - h * Dinv * vol[q] * tau[e];
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b)
-        for (int c = 0; c < 3; ++c) {
-          double wt = w[a] * w[3 + b] * w[6 + c];
-          double dpos[3] = {(a - fx[0]) * dx, (b - fx[1]) * dx, (c - fx[2]) * dx};
-          size_t i = node_id(g, base[0] + a, base[1] + b, base[2] + c);
-          s->m[i] += wt * mass[q];
-          for (int r = 0; r < 3; ++r)
-            s->p[3 * i + r] += wt * (mass[q] * v[3 * q + r] + aff[3 * r] * dpos[0] +
-                                     aff[3 * r + 1] * dpos[1] + aff[3 * r + 2] * dpos[2]);
-        }
-  }
+#ifdef _OPENMP
+  p2g_slabs(s, n, x, v, C, F, mass, vol, mat, mats, h);
+#else
+  for (int q = 0; q < n; ++q) p2g_particle(s, q, x, v, C, F, mass, vol, mat, mats, h);
+#endif
 
   /* grid update: v* = p/m + h g; Dirichlet walls (reading: sticky, v = 0) */
   s->n_dof = 0;
@@ -971,68 +1134,50 @@ int orc_substep(orc_sim* s, int n, double* x, double* v, double* C, double* F,
 
   /* contact registration at the start of the substep (Sec. V-B): one contact
      per (particle, body) pair with the particle inside the body */
-  int cap = 16, nc = 0;
-  int* cp = (int*)malloc(sizeof(int) * cap);
-  int* cb = (int*)malloc(sizeof(int) * cap);
-  int* cn = (int*)malloc(sizeof(int) * 27 * cap);
-  double* cw = (double*)malloc(sizeof(double) * 27 * cap);
-  double* cR = (double*)malloc(sizeof(double) * 9 * cap);
-  double* cbias = (double*)malloc(sizeof(double) * 3 * cap);
-  double* cphi = (double*)malloc(sizeof(double) * cap);
-  double* cn0 = (double*)malloc(sizeof(double) * cap);
-  double* cmu = (double*)malloc(sizeof(double) * cap);
-  double* ck = (double*)malloc(sizeof(double) * cap);
-  double* cd = (double*)malloc(sizeof(double) * cap);
+  orc_contacts K = {0};
+  int nc = 0;
+#ifdef _OPENMP
+  /* count per particle, then fill in the serial order (particle-major, body
+     order) at each particle's offset */
+  int* first = (int*)calloc((size_t)n + 1, sizeof(int));
+#pragma omp parallel for schedule(static)
+  for (int q = 0; q < n; ++q) {
+    int k = 0;
+    for (int bi = 0; bi < nb; ++bi) {
+      double nrm[3];
+      if (orc_sdf(&bodies[bi], x + 3 * q, nrm) < 0.0) ++k;
+    }
+    first[q + 1] = k;
+  }
+  for (int q = 0; q < n; ++q) first[q + 1] += first[q];
+  nc = first[n];
+  contacts_alloc(&K, nc > 16 ? nc : 16);
+#pragma omp parallel for schedule(static)
+  for (int q = 0; q < n; ++q) {
+    int k = first[q];
+    for (int bi = 0; bi < nb; ++bi) {
+      double nrm[3];
+      double phi = orc_sdf(&bodies[bi], x + 3 * q, nrm);
+      if (phi < 0.0) register_contact(s, &K, k++, q, bi, &bodies[bi], phi, nrm, x, v, h);
+    }
+  }
+  free(first);
+#else
+  contacts_alloc(&K, 16);
   for (int q = 0; q < n; ++q) {
     for (int bi = 0; bi < nb; ++bi) {
       double nrm[3];
       double phi = orc_sdf(&bodies[bi], x + 3 * q, nrm);
       if (!(phi < 0.0)) continue;
-      if (nc == cap) {
-        cap *= 2;
-        cp = (int*)realloc(cp, sizeof(int) * cap);
-        cb = (int*)realloc(cb, sizeof(int) * cap);
-        cn = (int*)realloc(cn, sizeof(int) * 27 * cap);
-        cw = (double*)realloc(cw, sizeof(double) * 27 * cap);
-        cR = (double*)realloc(cR, sizeof(double) * 9 * cap);
-        cbias = (double*)realloc(cbias, sizeof(double) * 3 * cap);
-        cphi = (double*)realloc(cphi, sizeof(double) * cap);
-        cn0 = (double*)realloc(cn0, sizeof(double) * cap);
-        cmu = (double*)realloc(cmu, sizeof(double) * cap);
-        ck = (double*)realloc(ck, sizeof(double) * cap);
-        cd = (double*)realloc(cd, sizeof(double) * cap);
-      }
-      int base[3];
-      double fx[3], w[9];
-      orc_bspline(dx, g->origin, x + 3 * q, base, fx, w);
-      int sidx = 0;
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-          for (int c = 0; c < 3; ++c, ++sidx) {
-            size_t i = node_id(g, base[0] + a, base[1] + b, base[2] + c);
-            cn[27 * nc + sidx] = s->dof[i];
-            cw[27 * nc + sidx] = w[a] * w[3 + b] * w[6 + c];
-          }
-      orc_contact_frame(nrm, 0.0, cR + 9 * nc);
-      double vr[3];
-      orc_body_velocity(&bodies[bi], x + 3 * q, vr);
-      /* bias b = -R^T v_rigid(x_p): v_c = R^T (v_particle - v_rigid) */
-      for (int c = 0; c < 3; ++c)
-        cbias[3 * nc + c] = -(cR[9 * nc + c] * vr[0] + cR[9 * nc + 3 + c] * vr[1] + cR[9 * nc + 6 + c] * vr[2]);
-      cphi[nc] = -phi;
-      /* lagged normal impulse from the start-of-substep relative normal
-         velocity of the particle */
-      double vrel[3] = {v[3 * q] - vr[0], v[3 * q + 1] - vr[1], v[3 * q + 2] - vr[2]};
-      double vn0 = dot3(nrm, vrel);
-      cn0[nc] = orc_normal_impulse(-phi, bodies[bi].k, bodies[bi].d, h, vn0);
-      cmu[nc] = bodies[bi].mu;
-      ck[nc] = bodies[bi].k;
-      cd[nc] = bodies[bi].d;
-      cp[nc] = q;
-      cb[nc] = bi;
+      if (nc == K.cap) contacts_alloc(&K, 2 * K.cap);
+      register_contact(s, &K, nc, q, bi, &bodies[bi], phi, nrm, x, v, h);
       ++nc;
     }
   }
+#endif
+  int *cp = K.p, *cb = K.b, *cn = K.nodes;
+  double *cw = K.w, *cR = K.R, *cbias = K.bias, *cphi = K.phi0, *cn0 = K.n0, *cmu = K.mu,
+         *ck = K.k, *cd = K.d;
   inf.n_contacts = nc;
 
   /* contact solve, Eq. (7)-(8) by Alg. 1, from v = v* */
@@ -1093,38 +1238,10 @@ int orc_substep(orc_sim* s, int n, double* x, double* v, double* C, double* F,
     for (int r = 0; r < 3; ++r) s->v[3 * (size_t)s->dof_node[e] + r] = vsol[3 * e + r];
 
   /* G2P with the constitutive update (Sec. V-A op (3)) */
-  for (int q = 0; q < n; ++q) {
-    int base[3];
-    double fx[3], w[9];
-    orc_bspline(dx, g->origin, x + 3 * q, base, fx, w);
-    double vp[3] = {0, 0, 0}, Bm[9] = {0};
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b)
-        for (int c = 0; c < 3; ++c) {
-          double wt = w[a] * w[3 + b] * w[6 + c];
-          double dpos[3] = {(a - fx[0]) * dx, (b - fx[1]) * dx, (c - fx[2]) * dx};
-          size_t i = node_id(g, base[0] + a, base[1] + b, base[2] + c);
-          for (int r = 0; r < 3; ++r) {
-            vp[r] += wt * s->v[3 * i + r];
-            for (int cc = 0; cc < 3; ++cc) Bm[3 * r + cc] += wt * s->v[3 * i + r] * dpos[cc];
-          }
-        }
-    for (int r = 0; r < 3; ++r) {
-      v[3 * q + r] = vp[r];
-      x[3 * q + r] += h * vp[r];
-    }
-    for (int e = 0; e < 9; ++e) C[9 * q + e] = Dinv * Bm[e];
-    double Fu[9];
-    for (int e = 0; e < 9; ++e) Fu[e] = h * C[9 * q + e];
-    Fu[0] += 1.0; Fu[4] += 1.0; Fu[8] += 1.0;
-    mat_mul(Fu, F + 9 * q, F + 9 * q);
-    const orc_material* mt = &mats[mat[q]];
-    if (mt->model == ORC_DRUCKER_PRAGER) {
-      double mu, lam;
-      orc_lame(mt->E, mt->nu, &mu, &lam);
-      orc_dp_project(F + 9 * q, mu, lam, mt->friction_angle_deg, F + 9 * q);
-    }
-  }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+  for (int q = 0; q < n; ++q) g2p_particle(s, q, x, v, C, F, mat, mats, h);
 
   free(dm); free(dvs); free(dfix); free(vsol); free(gam);
   free(cp); free(cb); free(cn); free(cw); free(cR); free(cbias); free(cphi); free(cn0);

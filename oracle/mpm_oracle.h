@@ -9,7 +9,9 @@
  * CPU-baseline leg of the benchmark may load it. It shares no code, header,
  * table or helper with the CUDA library, and the CUDA library never calls it.
  *
- * Everything is FP64 and serial. Conventions:
+ * Everything is FP64 and serial (a separate -fopenmp build of the same source,
+ * used only as the all-core CPU baseline, threads the per-particle loops).
+ * Conventions:
  *   - matrices are 3x3 row-major: M[3*r + c];
  *   - the grid is dense, node (ix,iy,iz) has linear id ix + rx*(iy + ry*iz) and
  *     position origin + dx*(ix,iy,iz);
@@ -180,6 +182,11 @@ typedef struct {
 
 orc_sim* orc_create(const orc_grid* grid);
 void orc_destroy(orc_sim* s);
+
+/* Threads orc_substep uses: 1 in the serial build (the checker); the
+   OpenMP build (-fopenmp, a CPU baseline over all host cores only) runs P2G
+   over alternating grid slabs, contact registration and G2P in parallel. */
+int orc_threads(void);
 
 /* One substep (Eq. (5)): free motion (Eq. (6)), contact registration, contact
    solve (Eq. (7)-(8), Alg. 1), G2P with the constitutive update. Particle

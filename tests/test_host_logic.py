@@ -47,9 +47,9 @@ def test_single_rank_helpers_are_identities():
 
 
 @pytest.mark.parametrize("res,n_sub,expected", [
-    ((128, 128, 128), 10, 1 + 5 * 3 + 1 + 50),  # 32 blocks per axis: 15 + 6 key bits, 3 passes
-    ((40, 16, 24), 1, 1 + 5 * 3 + 1 + 5),       # 10 blocks: 12 + 6 key bits, 3 passes
-    ((8, 8, 8), 2, 1 + 5 * 2 + 1 + 10),         # 2 blocks: 3 + 6 key bits, 2 passes
+    ((128, 128, 128), 10, 1 + 5 * 3 + 1 + 60),  # 32 blocks per axis: 15 + 6 key bits, 3 passes
+    ((40, 16, 24), 1, 1 + 5 * 3 + 1 + 6),       # 10 blocks: 12 + 6 key bits, 3 passes
+    ((8, 8, 8), 2, 1 + 5 * 2 + 1 + 12),         # 2 blocks: 3 + 6 key bits, 2 passes
 ])
 def test_kernel_launch_count(res, n_sub, expected):
     assert bench.kernel_launches_per_step(res, n_sub) == expected
@@ -83,10 +83,17 @@ def test_scene_generators_are_seeded():
 def test_bench_config_names_the_workload():
     sc = scenes.granular_scoop(n_particles=10_000)
     cfg = bench.bench_config(sc, 10_000, 1)
-    assert cfg["workload"] == bench.WORKLOAD
+    assert cfg["workload"] == "granular_scoop_10000"
     assert cfg["particles"] == 10_000
     assert cfg["substeps_per_step"] == sc["substeps"]
     assert "model" not in cfg
+    big = bench.make_scene(bench.SECONDARY)
+    assert bench.workload_name(big) == bench.SECONDARY == "granular_scoop_1M"
+    head = bench.make_scene(bench.WORKLOAD)
+    assert bench.workload_name(head) == bench.WORKLOAD == "mixed_manipulation_4M"
+    cfg = bench.bench_config(head, scenes.n_particles(head), 1)
+    assert cfg["objects"] == 32 and cfg["bodies"] == 12
+    assert cfg["materials"] == ["corotated_elastic", "drucker_prager_sand"]
 
 
 class _FakeSim:
