@@ -20,6 +20,8 @@ struct mpm_ctx {
   GridDev g{};
   int64_t cap = 0, n = 0;
   int num_sms = 0, solve_blocks = 0;
+  int cluster_blocks = 0;     // blocks of the cluster solve (0: the device runs none)
+  int cluster_max = 4096;     // MPM_OPT_CLUSTER_CONTACTS
   float* pbuf[2] = {nullptr, nullptr};
   uint32_t* pidbuf[2] = {nullptr, nullptr};
   uint16_t* grpbuf[2] = {nullptr, nullptr};
@@ -56,6 +58,7 @@ struct mpm_ctx {
   struct GraphKey {
     int64_t n = -1;
     int n_substeps = 0, nb = 0, chunk = 0, sort_now = 0, solve_blocks = 0, taping = 0;
+    int cluster_max = 0;
     const void* tape_pool = nullptr;  // baked into the launches when taping
     float h = 0.f;
     mpm_solver_params sp{};
@@ -468,6 +471,12 @@ void release(mpm_ctx* c) {
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
+// Contact counts up to which one thread-block cluster solves (the barrier
+// time-limit test needs the cooperative kernel's device-wide barriers).
+int cluster_contacts(const mpm_ctx* ctx) {
+  return ctx->wait_test || ctx->cluster_blocks == 0 ? 0 : ctx->cluster_max;
+}
+
 // One substep on particle buffer `cur`: P2G, grid update, contact solve and
 // (with_g2p) G2P. save: append the solve's contact-node velocities to the
 // tape's solution pool; warm_rec >= 0: start the solve from the taped
@@ -493,8 +502,9 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
   sa.bar = ctx->bar; sa.status = ctx->status; sa.stats = ctx->stats; sa.impulses = ctx->impulses;
   sa.wait_extra = ctx->wait_test ? 1 : 0;
   sa.poison = ctx->poison;
+  sa.cluster_max = cluster_contacts(ctx);
   mark_phase(ctx, MPM_PHASE_SOLVE);
-  const cudaError_t e = launch_solve(sa, solve_blocks, s);
+  const cudaError_t e = launch_solve(sa, solve_blocks, ctx->cluster_blocks, s);
   if (e != cudaSuccess) return e;
   if (save && ctx->tape_pool)
     launch_tape_save(ctx->G, ctx->tape_counters, ctx->tape_recs, ctx->tape_rec_cap, ctx->tape_pool,
@@ -617,7 +627,7 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
     ctx->G.cnodes_cap = (int)cn;
     ok = ok && dalloc(&ctx->G.cnodes, cn) == cudaSuccess;
   }
-  ok = ok && dalloc(&ctx->red, kRedDoubles) == cudaSuccess && dalloc(&ctx->bar, 2) == cudaSuccess &&
+  ok = ok && dalloc(&ctx->red, kRedDoubles) == cudaSuccess && dalloc(&ctx->bar, kBarWords) == cudaSuccess &&
        dalloc(&ctx->poison, 1) == cudaSuccess &&
        dalloc(&ctx->status, 1) == cudaSuccess && dalloc(&ctx->stats, 1) == cudaSuccess &&
        dalloc(&ctx->impulses, 6 * kMaxBodies) == cudaSuccess &&
@@ -644,7 +654,7 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
        cudaMemset(ctx->G.cflag, 0, nn * sizeof(int)) == cudaSuccess &&
        cudaMemset(ctx->G.n_cnodes, 0, sizeof(int)) == cudaSuccess &&
        cudaMemset(ctx->G.pstar2, 0, sizeof(double)) == cudaSuccess &&
-       cudaMemset(ctx->bar, 0, 2 * sizeof(unsigned)) == cudaSuccess &&
+       cudaMemset(ctx->bar, 0, kBarWords * sizeof(unsigned)) == cudaSuccess &&
        cudaMemset(ctx->poison, 0, sizeof(int)) == cudaSuccess &&
        cudaMemset(ctx->status, 0, sizeof(uint32_t)) == cudaSuccess &&
        cudaMemset(ctx->stats, 0, sizeof(DevStats)) == cudaSuccess &&
@@ -659,6 +669,7 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
       occ < 1)
     return bail(MPM_ERR_CUDA);
   ctx->solve_blocks = ctx->num_sms * (occ < 2 ? occ : 2);
+  ctx->cluster_blocks = solve_cluster_blocks();
   *out = ctx;
   return MPM_OK;
 }
@@ -889,7 +900,7 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     sp.eps_a = DBL_EPSILON;
     sp.max_iters = 1000;
     sp.eps_s = 1e-4f;
-    sp.ls_rel_tol = 1e-5f;
+    sp.ls_rel_tol = 1e-3f;
     sp.ls_max_iters = 50;
   }
   if (!(sp.eps_r >= 0.0) || !(sp.eps_a >= 0.0) || sp.max_iters < 0 || !(sp.eps_s > 0.f) ||
@@ -952,12 +963,14 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     mpm_ctx::GraphKey k;
     k.n = n; k.n_substeps = n_substeps; k.nb = nb; k.chunk = ctx->p2g_chunk;
     k.sort_now = sort_now ? 1 : 0; k.solve_blocks = solve_blocks; k.h = hf; k.sp = sp;
+    k.cluster_max = cluster_contacts(ctx);
     k.taping = ctx->taping && ctx->tape_pool ? 1 : 0;
     k.tape_pool = ctx->tape_pool;
     const mpm_ctx::GraphKey& o = ctx->gkey[from];
     const bool same = ctx->gexec[from] && o.n == k.n && o.n_substeps == k.n_substeps && o.nb == k.nb &&
                       o.chunk == k.chunk && o.sort_now == k.sort_now &&
                       o.solve_blocks == k.solve_blocks && o.h == k.h && o.taping == k.taping &&
+                      o.cluster_max == k.cluster_max &&
                       o.tape_pool == k.tape_pool &&
                       memcmp(&o.sp, &k.sp, sizeof(k.sp)) == 0;
     if (!same) {
@@ -1053,6 +1066,7 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
   stats->status_bits = (int32_t)bits;
   stats->p2g_global_chunks = ds.p2g_global_chunks;
   stats->ls_split_substeps = ds.ls_split;
+  stats->cluster_substeps = ds.cluster;
   for (int k = 0; k < 5; ++k) stats->solve_us[k] = (float)(ds.solve_ns[k] * 1e-3);
   return st;
 }
@@ -1223,12 +1237,12 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
   a.vec = ctx->adj_vec; a.red = ctx->red; a.bar = ctx->bar; a.status = ctx->status;
   a.poison = ctx->poison; a.stats = ctx->stats; a.out = ctx->adj_out;
   // the barrier counter and the node-list length are zero between launches
-  CU(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned), s));
+  CU(cudaMemsetAsync(ctx->bar, 0, kBarWords * sizeof(unsigned), s));
   CU(cudaMemsetAsync(ctx->G.n_cnodes, 0, sizeof(int), s));
   CU(cudaMemsetAsync(ctx->adj_body, 0, kAdjBodySlots * kMaxBodies * sizeof(double), s));
   CU(cudaMemsetAsync(ctx->adj_out, 0, 4 * sizeof(float), s));
   CU(launch_adjoint(a, ctx->adj_blocks, s));
-  CU(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned), s));
+  CU(cudaMemsetAsync(ctx->bar, 0, kBarWords * sizeof(unsigned), s));
   CU(cudaMemsetAsync(ctx->G.n_cnodes, 0, sizeof(int), s));
   st = drain_status(ctx);
   float out[4];
@@ -1480,7 +1494,7 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
       a.out = ctx->adj_out; a.gbar = ctx->bw_gbar; a.pbar = bar[1 - in]; a.slot_of = ctx->bw_slot;
       a.P = P; a.n_particles = (int)n;
       a.body_gbar = step_dyn ? ctx->bw_gbody : nullptr;
-      CU(cudaMemsetAsync(ctx->bar, 0, 2 * sizeof(unsigned), s));
+      CU(cudaMemsetAsync(ctx->bar, 0, kBarWords * sizeof(unsigned), s));
       CU(cudaMemsetAsync(ctx->G.n_cnodes, 0, sizeof(int), s));
       CU(launch_adjoint(a, ctx->adj_blocks, s));
       launch_grid_adjoint(ba, ctx->num_sms, s);
@@ -1662,6 +1676,11 @@ mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value) {
       if (value < 0 || value > (1LL << 30))
         return fail(ctx, MPM_ERR_INVALID_ARG, "tape solution pool must hold 0 .. 2^30 entries");
       ctx->tape_pool_want = value;
+      return MPM_OK;
+    case MPM_OPT_CLUSTER_CONTACTS:
+      if (value < 0 || value > (1 << 24))
+        return fail(ctx, MPM_ERR_INVALID_ARG, "cluster contact limit must be 0 .. 2^24");
+      ctx->cluster_max = (int)value;
       return MPM_OK;
     case MPM_OPT_SOLVE_BLOCKS:
       if (value < 0) return fail(ctx, MPM_ERR_INVALID_ARG, "solve block cap must be >= 0");

@@ -621,7 +621,7 @@ __global__ void k_reset_counters(GridArrays G, Contacts C, unsigned* bar) {
   *G.n_act = 0;
   *G.n_cnodes = 0;
   *G.pstar2 = 0.0;
-  bar[0] = 0u;
+  for (int g = 0; g <= 256 / kBarGroup; ++g) bar[kBarStride * g] = 0u;
 }
 
 // ---- solutions of the taped substeps ---------------------------------------

@@ -31,8 +31,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_g2p(G2PArgs a) {
       *a.G.n_act = 0;
       *a.G.n_cnodes = 0;
       *a.G.pstar2 = 0.0;
-      a.bar[0] = 0u;
     }
+    if (threadIdx.x <= 256 / kBarGroup) a.bar[kBarStride * threadIdx.x] = 0u;
   }
   const int i = blockIdx.x * kThreads + threadIdx.x;
   if (i >= a.n) return;

@@ -10,6 +10,11 @@
 namespace mpmcr {
 
 constexpr int kRedDoubles = 4 * 256 * 16;  // contact-solve partial sums: 4 slots x 256 blocks x 16
+// device-wide barrier counters of the cooperative solves: the top counter,
+// then one per group of kBarGroup blocks, kBarStride words apart
+constexpr int kBarGroup = 16;
+constexpr int kBarStride = 32;
+constexpr int kBarWords = kBarStride * (1 + 256 / kBarGroup);
 
 // Statistics written by the device, read back by mpm_step.
 struct DevStats {
@@ -25,7 +30,7 @@ struct DevStats {
   int last_contacts;     // contacts of the last substep
   int last_active;       // active blocks of the last substep
   int ls_split;          // substeps whose line search was split over the solve's blocks
-  int pad;
+  int cluster;           // substeps solved by one thread-block cluster
   // device time of the contact solve's phases (ns, block 0's view):
   // contact-node list, G, N, line search, impulses
   unsigned long long solve_ns[5];
@@ -87,14 +92,18 @@ struct SolveArgs {
   double eps_r, eps_a;
   int max_iters;
   double* red;        // per-block partial sums [4][256][16]
-  unsigned* bar;      // grid barrier words [2]
+  unsigned* bar;      // grid barrier counters [kBarWords]
   uint32_t* status;
   DevStats* stats;
   double* impulses;   // [6 nb]
   int wait_extra;     // 0; 1 makes every grid barrier wait for one block too many (test)
   int* poison;        // nonzero after a barrier gave up (set and cleared by the solve)
+  int cluster_max;    // up to this many contacts one thread-block cluster solves (0: never)
 };
-cudaError_t launch_solve(const SolveArgs& a, int grid_blocks, cudaStream_t s);
+// the cluster kernel (cluster_blocks > 0 and a.cluster_max > 0), then the
+// cooperative one; each returns at once when the contact count is the other's
+cudaError_t launch_solve(const SolveArgs& a, int grid_blocks, int cluster_blocks, cudaStream_t s);
+int solve_cluster_blocks();  // largest cluster (16, 8 or 4 blocks) the device holds; 0: none
 int solve_block_size();
 const void* solve_kernel_ptr();
 size_t solve_dynamic_smem();

@@ -11,8 +11,8 @@
 // adds the grid update's sum of m |v*|^2 over the other nodes.
 //
 // Per iteration:
-//   G  contacts: v_c = J v + b (a compensated gather of the double-float
-//      iterate); gradient (3) and Hessian (3x3) of the lagged contact
+//   G  contacts: v_c = J v + b + alpha J dv (a compensated gather of the
+//      double-float iterate); gradient (3) and Hessian (3x3) of the lagged contact
 //      potential, scattered with weights w and w^2 (the 3x3 diagonal blocks of
 //      J^T (d2 l_c) J, Eq. (10)).
 //   N  contact nodes: v += alpha dv (double-float, into the other buffer of
@@ -44,7 +44,8 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kContactsPerBlock = 16;  // one contact per warp in the gather phases
+constexpr int kContactsPerBlock = 128;  // forward solve: 8 contacts per warp in the gather phases
+constexpr int kAdjContactsPerBlock = 16;  // adjoint: one contact per warp
 constexpr int kLocalLsMax = 4096;      // up to this many contacts each block line-searches alone
 constexpr int kLsPoints = 8;
 constexpr int kRedWidth = 16;              // (hi, lo) pairs per block and reduction
@@ -65,42 +66,75 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 struct Barrier {
-  unsigned* bar;  // [0] arrival counter (zeroed between launches)
-  unsigned n;     // arrivals that complete a barrier: the participating blocks
+  unsigned* bar;  // arrival counters (kBarWords, zeroed between launches)
+  unsigned n;     // the participating blocks
   uint32_t* status;
   int* poison;    // set on expiry: the next solve first clears the node scratch
+  int cluster;    // nonzero: the blocks are one thread-block cluster
+  unsigned extra; // arrivals awaited that never come (barrier time-limit test only)
 };
 
-// Device-wide barrier of the participating blocks. The arrival counter only
-// grows: the k-th barrier is complete when it reaches (k + 1) n, which each
-// block reads off its own arrival ticket, so the last arriver has nothing to
-// reset or publish. Thread 0 publishes its block's writes (fence), arrives,
-// and the others poll with a time limit (1 s of the global timer) and return
-// false on expiry (the caller then returns; the other blocks expire at the
-// same or their next barrier). A single participating block needs only
-// __syncthreads.
+// Barrier of all threads of the thread-block cluster (hardware barrier; the
+// arrive releases and the wait acquires every thread's earlier memory
+// operations at cluster scope, global reductions included).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// (hi, lo) pair at the same shared-memory offset in block `rank` of the cluster
+__device__ __forceinline__ float2 ld_cluster_f2(const float2* p, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(ra)
+               : "memory");
+  return v;
+}
+
+// Device-wide barrier of the participating blocks, in two levels so that no
+// counter takes more than kBarGroup arrivals per barrier: block b arrives on
+// the counter of its group of kBarGroup blocks, and each group's last
+// arrival arrives on the top counter. Counters only grow: the k-th barrier
+// is complete when the top counter reaches (k + 1) x groups, which each block
+// reads off its own group ticket, so nothing is reset or published by the
+// last arriver. Thread 0 publishes its block's writes (fence), arrives, and
+// polls with a time limit (1 s of the global timer); on expiry it returns
+// false (the caller then returns; the other blocks expire at the same or
+// their next barrier). A single participating block needs only
+// __syncthreads; the blocks of one cluster use the cluster barrier.
 __device__ bool grid_sync(Barrier& B) {
+  if (B.cluster) {
+    cluster_sync_all();
+    return true;
+  }
   __syncthreads();
-  if (B.n == 1) return true;
+  if (B.n == 1 && B.extra == 0) return true;
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     int ok = 1;
+    const unsigned g = blockIdx.x / kBarGroup;
+    const unsigned gsize = min((unsigned)kBarGroup, B.n - g * kBarGroup);
+    const unsigned top_n = (B.n + kBarGroup - 1) / kBarGroup + B.extra;
     __threadfence();
-    const unsigned ticket = atomicAdd(&B.bar[0], 1u);
-    const unsigned target = (ticket / B.n + 1u) * B.n;
-    if (ticket + 1u != target) {
-      const unsigned long long t0 = global_ns();
-      unsigned spins = 0;
-      while (ld_acquire(&B.bar[0]) < target) {
-        ++spins;
-        if (((spins & 63u) == 0u && global_ns() - t0 > kWaitLimitNs) || spins > kSpinCap) {
-          atomicOr(B.status, kStTimeout);
-          if (B.poison) atomicExch(B.poison, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(20);
+    const unsigned ticket = atomicAdd(&B.bar[kBarStride * (1 + g)], 1u);
+    const unsigned k = ticket / gsize;
+    if (ticket % gsize == gsize - 1) {  // the group's last arrival carries it upwards
+      __threadfence();
+      atomicAdd(&B.bar[0], 1u);
+    }
+    const unsigned target = (k + 1u) * top_n;
+    const unsigned long long t0 = global_ns();
+    unsigned spins = 0;
+    while (ld_acquire(&B.bar[0]) < target) {
+      ++spins;
+      if (((spins & 63u) == 0u && global_ns() - t0 > kWaitLimitNs) || spins > kSpinCap) {
+        atomicOr(B.status, kStTimeout);
+        if (B.poison) atomicExch(B.poison, 1);
+        ok = 0;
+        break;
       }
+      __nanosleep(20);
     }
     __threadfence();
     s_ok = ok;
@@ -126,9 +160,13 @@ __device__ __forceinline__ void df_acc(float& S, float& E, float2 x) {
 // Block sums of NV per-thread values, exchanged through per-block slots and
 // summed by every block in the same fixed order (deterministic). Returns the
 // double-float totals in s_tot (shared) and false if the barrier expired.
+// `part`: the global slot of a device-wide reduction; in a cluster the block
+// sums go to the shared-memory slot `cpart` instead and every block reads the
+// others' through distributed shared memory.
 template <int NV>
 __device__ bool reduce_all(const float (&v)[NV], float2* part, Barrier& B, float (*s_red)[kRedWidth],
-                           float2* s_tot) {
+                           float2* s_tot, float2* cpart = nullptr) {
+  static_assert(NV <= kWarps && NV <= kRedWidth, "one warp per reduced value");
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if constexpr (NV == 16) {
     // reduce-scatter butterfly: after the exchange over lane bit b each lane
@@ -160,46 +198,63 @@ __device__ bool reduce_all(const float (&v)[NV], float2* part, Barrier& B, float
     }
   }
   __syncthreads();
-  if (w == 0 && lane < NV) {
-    float S = 0.f, E = 0.f;
+  // block sum of value w: lane l < kWarps holds warp l's, a butterfly over
+  // those lanes (compensated)
+  if (w < NV) {
+    float S = lane < kWarps ? s_red[lane][w] : 0.f, E = 0.f;
 #pragma unroll
-    for (int k = 0; k < kWarps; ++k) {
-      float t, e;
-      two_sum(S, s_red[k][lane], t, e);
-      S = t;
-      E += e;
+    for (int o = kWarps / 2; o > 0; o >>= 1) {
+      const float S2 = __shfl_xor_sync(0xffffffffu, S, o);
+      const float E2 = __shfl_xor_sync(0xffffffffu, E, o);
+      float s2, e;
+      two_sum(S, S2, s2, e);
+      S = s2;
+      E = E + E2 + e;
     }
-    if (B.n == 1)
-      s_tot[lane] = df_norm(S, E);
-    else
-      part[blockIdx.x * kRedWidth + lane] = df_norm(S, E);
+    if (lane == 0) {
+      if (B.cluster)
+        cpart[w] = df_norm(S, E);
+      else if (B.n == 1)
+        s_tot[w] = df_norm(S, E);
+      else
+        part[w * kMaxSolveBlocks + blockIdx.x] = df_norm(S, E);
+    }
   }
   if (!grid_sync(B)) return false;
-  if (B.n > 1) {
-    if (w == 0) {
-      if (B.n <= 32) {
-        // lane i sums value i over the blocks, in block order
-        if (lane < NV) {
-          float S = 0.f, E = 0.f;
-          for (int b = 0; b < (int)B.n; ++b) df_acc(S, E, __ldcg(part + b * kRedWidth + lane));
-          s_tot[lane] = df_norm(S, E);
+  if (B.cluster || B.n > 1) {
+    // warp i sums value i over the blocks: lane l takes blocks l, l + 32, ...
+    // (their loads in flight together), then a butterfly over the warp's
+    // double-float pairs; the same fixed order in every block
+    if (w < NV) {
+      float S = 0.f, E = 0.f;
+      if (B.cluster) {
+        if (lane < (int)B.n) {
+          const float2 t = ld_cluster_f2(cpart + w, (unsigned)lane);
+          S = t.x;
+          E = t.y;
         }
       } else {
-        // lane (c, i) = (lane / NV, lane % NV) sums value i over the blocks
-        // b = c (mod chunks); lanes 0..NV-1 then add the other chunks
-        constexpr int kChunks = 32 / NV;
-        const int i = lane % NV, c = lane / NV;
-        float S = 0.f, E = 0.f;
-        if (c < kChunks)
-          for (int b = c; b < (int)B.n; b += kChunks) df_acc(S, E, __ldcg(part + b * kRedWidth + i));
+        for (int b0 = 0; b0 < (int)B.n; b0 += 8 * 32) {
+          float2 t[8];
 #pragma unroll
-        for (int c2 = 1; c2 < kChunks; ++c2) {
-          const float S2 = __shfl_sync(0xffffffffu, S, (lane + c2 * NV) & 31);
-          const float E2 = __shfl_sync(0xffffffffu, E, (lane + c2 * NV) & 31);
-          if (lane < NV) df_acc(S, E, make_float2(S2, E2));
+          for (int u = 0; u < 8; ++u) {
+            const int b = b0 + 32 * u + lane;
+            t[u] = b < (int)B.n ? __ldcg(part + w * kMaxSolveBlocks + b) : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) df_acc(S, E, t[u]);
         }
-        if (lane < NV) s_tot[lane] = df_norm(S, E);
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float S2 = __shfl_xor_sync(0xffffffffu, S, o);
+        const float E2 = __shfl_xor_sync(0xffffffffu, E, o);
+        float s2, e;
+        two_sum(S, S2, s2, e);
+        S = s2;
+        E = E + E2 + e;
+      }
+      if (lane == 0) s_tot[w] = df_norm(S, E);
     }
     __syncthreads();
   }
@@ -234,6 +289,46 @@ __device__ __forceinline__ float warp_comp_sum(float S, float E) {
     float s, e;
     two_sum(S, S2, s, e);
     S = s;
+    E = E + E2 + e;
+  }
+  return S + E;
+}
+
+// Contact groups of the forward solve's gather / scatter phases: kGrp lanes
+// per contact, lane sub of a group owning stencil nodes sub, sub + kGrp, ...
+constexpr int kGrp = 4;
+constexpr int kGrpPerWarp = 32 / kGrp;
+constexpr int kGrpNodes = (27 + kGrp - 1) / kGrp;
+
+struct GroupNodes {
+  int node[kGrpNodes];
+  float w[kGrpNodes];
+};
+
+__device__ __forceinline__ void group_nodes(const GridDev& g, const float4& xp, int sub,
+                                            GroupNodes& r) {
+  Stencil s;
+  stencil(g, xp.x, xp.y, xp.z, s);
+#pragma unroll
+  for (int j = 0; j < kGrpNodes; ++j) {
+    const int c = sub + kGrp * j;
+    const int cc = c < 27 ? c : 26;
+    const int cx = cc % 3, cy = (cc / 3) % 3, cz = cc / 9;
+    r.node[j] = node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz);
+    r.w[j] = c < 27 ? s.w[0][cx] * s.w[1][cy] * s.w[2][cz] : 0.f;
+  }
+}
+
+// compensated sum of (S, E) pairs over the lanes of a group, bitwise the same
+// in each of them (TwoSum's error term is exact whichever operand comes first)
+__device__ __forceinline__ float group_comp_sum(float S, float E) {
+#pragma unroll
+  for (int o = 1; o < kGrp; o <<= 1) {
+    const float S2 = __shfl_xor_sync(0xffffffffu, S, o);
+    const float E2 = __shfl_xor_sync(0xffffffffu, E, o);
+    float s2, e;
+    two_sum(S, S2, s2, e);
+    S = s2;
     E = E + E2 + e;
   }
   return S + E;
@@ -287,43 +382,76 @@ __device__ __forceinline__ void line_load(const float4* cache, int slot, const D
 // passes evaluate the Newton step from the best point, the secant of the
 // bracket and six points that split it (geometrically while it spans more
 // than a factor 4, else its thirds and points around the Newton step).
-// Stops when |f'(best)| <= rel_tol |f'(0)|. Thread-0 state.
+// Stops when |f'(best)| <= rel_tol |f'(0)|. Run by the 32 lanes of warp 0:
+// lane l owns point l & 7; the bracket and the best point (kept alike in
+// every lane) are updated by butterfly reductions over the 8 points.
 struct LineSearch {
   enum { kMore = 0, kDone = 1, kFailed = 2 };
   float lo, hi, flo, fhi, best, fbest, f2best, f0;
   bool have_f0;
-  float pts[kLsPoints];
+  float pt;  // this lane's point
   __device__ void reset() {
+    const int k = threadIdx.x & (kLsPoints - 1);
     lo = 0.f; hi = -1.f; flo = fhi = best = fbest = f2best = f0 = 0.f;
     have_f0 = false;
+    // first pass: 0 and a geometric grid 4^-5 .. 4 (quasi-Newton steps on
+    // stiff contacts are often much shorter than 1)
+    pt = k == 0 ? 0.f : exp2f(2.0f * (float)(k - 6));
   }
   // f' = B + alpha A + S is formed in double-float (its terms can cancel);
   // the bracket logic runs in FP32 (alpha is applied in FP32 anyway)
   __device__ int update(const float2* tot, float2 A, float2 B, float rel_tol, bool last) {
-    for (int k = 0; k < kLsPoints; ++k) {
-      const float x = pts[k];
-      CompSum c;
-      c.S = B.x;
-      c.E = B.y + x * A.y + tot[k].y;
-      c.add_prod(x, A.x);
-      c.add(tot[k].x);
-      const float d = c.value();
-      const float d2 = (A.x + tot[kLsPoints + k].x) + (A.y + tot[kLsPoints + k].y);
-      if (!have_f0 && x == 0.f) {
-        f0 = d; have_f0 = true; flo = d; best = 0.f; fbest = d; f2best = d2;
-      }
-      if (d < 0.f) {
-        if (x >= lo) { lo = x; flo = d; }
-      } else if (hi < 0.f || x < hi) {
-        hi = x; fhi = d;
-      }
-      if (fabsf(d) < fabsf(fbest)) { best = x; fbest = d; f2best = d2; }
+    const int k = threadIdx.x & (kLsPoints - 1);
+    const float x = pt;
+    CompSum c;
+    c.S = B.x;
+    c.E = B.y + x * A.y + tot[k].y;
+    c.add_prod(x, A.x);
+    c.add(tot[k].x);
+    const float d = c.value();
+    const float d2 = (A.x + tot[kLsPoints + k].x) + (A.y + tot[kLsPoints + k].y);
+    if (!have_f0) {  // the first pass's point 0 is alpha = 0
+      f0 = __shfl_sync(0xffffffffu, d, 0);
+      flo = f0;
+      best = 0.f;
+      fbest = f0;
+      f2best = __shfl_sync(0xffffffffu, d2, 0);
+      have_f0 = true;
     }
+    // candidates of this pass: the largest point with f' < 0 (ties: the later
+    // point), the smallest with f' >= 0 (ties: the earlier), the smallest
+    // |f'| (ties: the earlier)
+    float clo = d < 0.f ? x : -1.f, cflo = d;
+    int klo = k;
+    float chi = d < 0.f ? INFINITY : x, cfhi = d;
+    int khi = k;
+    float cb = fabsf(d), cbx = x, cbd = d, cbd2 = d2;
+    int kb = k;
+#pragma unroll
+    for (int o = 1; o < kLsPoints; o <<= 1) {
+      const float olo = __shfl_xor_sync(0xffffffffu, clo, o);
+      const float oflo = __shfl_xor_sync(0xffffffffu, cflo, o);
+      const int oklo = __shfl_xor_sync(0xffffffffu, klo, o);
+      if (olo > clo || (olo == clo && oklo > klo)) { clo = olo; cflo = oflo; klo = oklo; }
+      const float ohi = __shfl_xor_sync(0xffffffffu, chi, o);
+      const float ofhi = __shfl_xor_sync(0xffffffffu, cfhi, o);
+      const int okhi = __shfl_xor_sync(0xffffffffu, khi, o);
+      if (ohi < chi || (ohi == chi && okhi < khi)) { chi = ohi; cfhi = ofhi; khi = okhi; }
+      const float ob = __shfl_xor_sync(0xffffffffu, cb, o);
+      const float obx = __shfl_xor_sync(0xffffffffu, cbx, o);
+      const float obd = __shfl_xor_sync(0xffffffffu, cbd, o);
+      const float obd2 = __shfl_xor_sync(0xffffffffu, cbd2, o);
+      const int okb = __shfl_xor_sync(0xffffffffu, kb, o);
+      if (ob < cb || (ob == cb && okb < kb)) { cb = ob; cbx = obx; cbd = obd; cbd2 = obd2; kb = okb; }
+    }
+    if (clo >= lo) { lo = clo; flo = cflo; }
+    if (chi != INFINITY && (hi < 0.f || chi < hi)) { hi = chi; fhi = cfhi; }
+    if (cb < fabsf(fbest)) { best = cbx; fbest = cbd; f2best = cbd2; }
     if (!(f0 < 0.f)) { best = 0.f; return kDone; }  // no descent left at working precision
     if (fabsf(fbest) <= rel_tol * fabsf(f0) || last) return kDone;
     if (hi < 0.f) {  // root beyond the grid: keep growing by 4x
       if (lo >= 1024.f) { best = lo; return kFailed; }
-      for (int k = 0; k < kLsPoints; ++k) pts[k] = lo * (float)(4 << (2 * k));
+      pt = lo * (float)(4 << (2 * k));
       return kMore;
     }
     if (hi - lo <= 1e-7f * hi) return kDone;
@@ -332,34 +460,41 @@ struct LineSearch {
     if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
     float xs = lo - flo * w / (fhi - flo);
     if (!(xs > lo && xs < hi)) xs = 0.5f * (lo + hi);
-    pts[0] = xn;
-    pts[1] = xs;
     // a bracket spanning more than a factor 4 (or reaching down to 0) is
     // split geometrically; a narrow one by its thirds (the bracket shrinks at
     // least threefold) and points 1% and 10% of its width either side of
     // the Newton point (where the root lies once Newton converges)
-    const float lo_g = lo > 0.f ? lo : hi * (1.0f / 4096.0f);
-    if (hi > 4.f * lo_g) {
-      const float r = exp2f(__log2f(hi / lo_g) / 7.0f);
-      float x = lo_g;
-      for (int k = 2; k < kLsPoints; ++k) {
-        x *= r;
-        pts[k] = x;
-      }
+    if (k == 0) {
+      pt = xn;
+    } else if (k == 1) {
+      pt = xs;
     } else {
-      const float c[6] = {1.f / 3.f, 2.f / 3.f, -0.1f, 0.1f, -0.01f, 0.01f};
-      for (int k = 2; k < kLsPoints; ++k) {
-        float x = k < 4 ? lo + c[k - 2] * w : xn + c[k - 2] * w;
-        if (!(x > lo && x < hi)) x = lo + (float)(k - 1) / 7.0f * w;
-        pts[k] = x;
+      const float lo_g = lo > 0.f ? lo : hi * (1.0f / 4096.0f);
+      if (hi > 4.f * lo_g) {
+        const float r = exp2f(__log2f(hi / lo_g) / 7.0f);
+        float xg = lo_g;
+        for (int j = 2; j <= k; ++j) xg *= r;
+        pt = xg;
+      } else {
+        const float cw = k == 2 ? 1.f / 3.f : k == 3 ? 2.f / 3.f : k == 4 ? -0.1f
+                         : k == 5 ? 0.1f : k == 6 ? -0.01f : 0.01f;
+        float xc = k < 4 ? lo + cw * w : xn + cw * w;
+        if (!(xc > lo && xc < hi)) xc = lo + (float)(k - 1) / 7.0f * w;
+        pt = xc;
       }
     }
     return kMore;
   }
 };
 
+// kCluster: the solve of up to a.cluster_max contacts by the blocks of one
+// thread-block cluster (hardware cluster barriers, block sums exchanged
+// through distributed shared memory); otherwise the cooperative launch over
+// as many blocks as the contacts need, for more contacts than that.
+template <bool kCluster>
 __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   __shared__ DevBody s_body[kMaxBodies];
+  __shared__ float2 s_cpart[4][kRedWidth];  // cluster: block sums, a ring of four reductions
   __shared__ float s_red[kWarps][kRedWidth];
   __shared__ float2 s_tot[kRedWidth];
   __shared__ float s_imp[kMaxBodies][6];
@@ -367,16 +502,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   __shared__ float2 s_A, s_B;
   __shared__ float s_alpha;
   __shared__ int s_dec;
-  extern __shared__ float4 s_line[];  // 3 x kLsCacheSlots: the line-search cache
-  LineSearch ls;  // used by thread 0
+  extern __shared__ float4 s_line[];  // 3 x kLsCacheSlots: the line-search cache (+ stencils)
+  LineSearch ls;  // used by warp 0
   const int tid = threadIdx.x;
   const int count = *a.C.count;
   const int nc = count < a.C.cap ? count : a.C.cap;
   if (nc == 0) return;  // v = v* already (set by the grid update)
-  int nblk = (nc + kContactsPerBlock - 1) / kContactsPerBlock;
-  nblk = nblk < (int)gridDim.x ? nblk : (int)gridDim.x;
-  nblk = nblk < kMaxSolveBlocks ? nblk : kMaxSolveBlocks;
-  if ((int)blockIdx.x >= nblk) return;  // not needed for this many contacts
+  // (every block of a launch reads the same count: the choice is uniform)
+  if (kCluster ? nc > a.cluster_max : nc <= a.cluster_max) return;  // the other kernel's
+  int nblk = (int)gridDim.x;  // a cluster: all of its blocks
+  if (!kCluster) {
+    nblk = (nc + kContactsPerBlock - 1) / kContactsPerBlock;
+    nblk = nblk < (int)gridDim.x ? nblk : (int)gridDim.x;
+    nblk = nblk < kMaxSolveBlocks ? nblk : kMaxSolveBlocks;
+    if ((int)blockIdx.x >= nblk) return;  // not needed for this many contacts
+  }
 
   for (int i = tid; i < a.nb * (int)(sizeof(DevBody) / 4); i += kThreads)
     reinterpret_cast<float*>(s_body)[i] = reinterpret_cast<const float*>(a.bodies)[i];
@@ -395,7 +535,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   };
   // (wait_extra > 0 only in the test of the barrier's time limit: the
   // barrier then waits for arrivals that never come)
-  Barrier B{a.bar, (unsigned)(nblk + a.wait_extra), a.status, a.poison};
+  Barrier B{a.bar, (unsigned)nblk, a.status, a.poison, kCluster ? 1 : 0,
+            kCluster ? 0u : (unsigned)a.wait_extra};
   const int gtid = blockIdx.x * kThreads + tid;
   const int gstride = nblk * kThreads;
   const int lane = tid & 31;
@@ -410,6 +551,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     ++rslot;
     return s;
   };
+  // in a cluster the block sums go to a ring of shared-memory slots instead
+  // (rewritten four reductions later, after every block has read it)
+  int cslot = 0;
+  auto next_cpart = [&]() -> float2* { return kCluster ? s_cpart[(cslot++) & 3] : nullptr; };
 
   // a solve that gave up at a barrier left node flags and gradient
   // accumulators behind: clear them over the whole grid first
@@ -425,20 +570,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     if (gtid == 0) *a.poison = 0;
   }
 
-  // ---- contact-node list: the union of the contacts' stencils
-  for (int p = gtid; p < nc; p += gstride) {
-    const float4 xp = a.C.xp[p];
-    Stencil s;
-    stencil(g, xp.x, xp.y, xp.z, s);
+  // ---- contact-node list: the union of the contacts' stencils (a thread
+  // per contact; the warp takes its list slots with one atomic)
+  for (int p0 = gtid & ~31; p0 < nc; p0 += gstride) {
+    const int p = p0 + lane;
     int node[27];
     unsigned won = 0u;  // 27 bits: this thread claimed the node first
+    if (p < nc) {
+      const float4 xp = a.C.xp[p];
+      Stencil s;
+      stencil(g, xp.x, xp.y, xp.z, s);
 #pragma unroll
-    for (int c = 0; c < 27; ++c) {
-      node[c] = node_index(g, s.base[0] + c % 3, s.base[1] + (c / 3) % 3, s.base[2] + c / 9);
-      if (atomicExch(a.G.cflag + node[c], 1) == 0) won |= 1u << c;
+      for (int c = 0; c < 27; ++c) {
+        node[c] = node_index(g, s.base[0] + c % 3, s.base[1] + (c / 3) % 3, s.base[2] + c / 9);
+        if (atomicExch(a.G.cflag + node[c], 1) == 0) won |= 1u << c;
+      }
     }
+    const int cnt = __popc(won);
+    int incl = cnt;  // inclusive prefix sum over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int slot0 = 0;
+    if (lane == 31 && incl > 0) slot0 = atomicAdd(a.G.n_cnodes, incl);
+    int slot = __shfl_sync(0xffffffffu, slot0, 31) + incl - cnt;
     if (won) {
-      int slot = atomicAdd(a.G.n_cnodes, __popc(won));
 #pragma unroll
       for (int c = 0; c < 27; ++c)
         if ((won >> c) & 1u) {
@@ -465,49 +623,90 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   float4* vnxt = a.G.v2;
   float4* lcur = a.G.vlo;
   float4* lnxt = a.G.vlo2;
-  // this warp's first contact, kept in registers across the iterations (with
-  // one contact per warp, whenever nc <= 16 x the blocks, nothing else is
-  // loaded per iteration but the iterate)
-  const bool own = gwarp < nc;
-  float4 own_xp = make_float4(0.f, 0.f, 0.f, 0.f), own_nrm = own_xp, own_bias = own_xp;
-  int own_body = 0;
-  LaneNode own_ln{0, 0.f};
-  if (own) {
-    own_xp = a.C.xp[gwarp];
-    own_nrm = a.C.nrm[gwarp];
-    own_bias = a.C.bias[gwarp];
-    own_body = a.C.id[gwarp].y;
-    own_ln = lane_node(g, own_xp, lane);
+  // Gather / scatter phases: kGrp lanes per contact (lane group grp of the
+  // warp, lane sub of the group owns stencil nodes sub, sub + kGrp, ...), so
+  // a warp works on kGrpPerWarp contacts at once. The contacts of a warp's
+  // first round stay in registers across the iterations.
+  const int grp = lane / kGrp, sub = lane % kGrp;
+  const int wfirst = gwarp * kGrpPerWarp;
+  const int rstride = nwarps * kGrpPerWarp;
+  const int own_p = wfirst + grp;
+  const bool own = own_p < nc;
+  // (the stencil of that contact in shared memory, beside the line-search
+  // cache: registers are kept for the gathers in flight)
+  int* s_own_node = reinterpret_cast<int*>(s_line + 3 * kLsCacheSlots) + tid * kGrpNodes;
+  float* s_own_w = reinterpret_cast<float*>(s_line + 3 * kLsCacheSlots) + kThreads * kGrpNodes +
+                   tid * kGrpNodes;
+  {
+    GroupNodes gn;
+    group_nodes(g, own ? a.C.xp[own_p] : make_float4(0.f, 0.f, 0.f, 0.f), sub, gn);
+#pragma unroll
+    for (int j = 0; j < kGrpNodes; ++j) {
+      s_own_node[j] = gn.node[j];
+      s_own_w[j] = gn.w[j];
+    }
   }
+  auto own_nodes = [&](GroupNodes& gn) {
+#pragma unroll
+    for (int j = 0; j < kGrpNodes; ++j) {
+      gn.node[j] = s_own_node[j];
+      gn.w[j] = s_own_w[j];
+    }
+  };
+  // this thread's first contact node (the list is fixed for the solve)
+  const int my_node = gtid < ncn ? a.G.cnodes[gtid] : -1;
   // line search alone in each block (no grid barrier) or split over blocks
-  const bool local_ls = nc <= kLocalLsMax;
+  const bool local_ls = kCluster ? nc <= kThreads : nc <= kLocalLsMax;
   const int ls_first = local_ls ? tid : gtid, ls_stride = local_ls ? kThreads : gstride;
-  Barrier Bl{nullptr, 1u, a.status, nullptr};
+  Barrier Bl{nullptr, 1u, a.status, nullptr, 0, 0u};
   const float eps2 = a.eps_s * a.eps_s;
   float alpha = 0.f;
   int it = 0, ls_passes = 0;
   float resid = 0.f;
   for (;;) {
-    // ---- G: step by alpha, contact gradient / Hessian blocks (warp per contact)
+    // ---- G: step by alpha, contact gradient / Hessian blocks (kGrp lanes per
+    // contact)
     const float al = alpha;
-    auto phase_g = [&](int p, const float4& xp, const float (&n)[3], float n0, const float4& bb,
-                       int body, const LaneNode& ln) {
-      const float4 dvc = it > 0 ? __ldcg(a.C.dvc + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+    auto phase_g = [&](int p, bool valid, const float4& xp, const float (&n)[3], float n0,
+                       const float4& bb, int body, const GroupNodes& gn) {
+      const float4 dvc = valid && it > 0 ? __ldcg(a.C.dvc + p) : make_float4(0.f, 0.f, 0.f, 0.f);
       float u[3];
       {
-        const float4 h = __ldcg(vcur + ln.node);
-        const float4 l = __ldcg(lcur + ln.node);
-        const float hv[3] = {h.x, h.y, h.z}, lv[3] = {l.x, l.y, l.z};
+        // compensated v_c = J v over the group's nodes: exact products w*hi
+        // as (p, pe), plus w*lo
+        float S[3] = {0.f, 0.f, 0.f}, E[3] = {0.f, 0.f, 0.f};
+        if (valid) {
+          // all of the group's loads first, so that they are in flight together
+          float4 hq[kGrpNodes], lq[kGrpNodes];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          // exact product w*hi as (p, pe), plus the low part
-          const float pr = ln.w * hv[c];
-          const float pe = fmaf(ln.w, hv[c], -pr) + ln.w * lv[c];
-          u[c] = warp_comp_sum(pr, pe);
+          for (int j = 0; j < kGrpNodes; ++j) {
+            if (sub + kGrp * j >= 27) continue;
+            hq[j] = __ldcg(vcur + gn.node[j]);
+            lq[j] = __ldcg(lcur + gn.node[j]);
+          }
+#pragma unroll
+          for (int j = 0; j < kGrpNodes; ++j) {
+            if (sub + kGrp * j >= 27) continue;
+            const float4 h = hq[j], l = lq[j];
+            const float w = gn.w[j];
+            const float hv[3] = {h.x, h.y, h.z}, lv[3] = {l.x, l.y, l.z};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float pr = w * hv[c];
+              const float pe = fmaf(w, hv[c], -pr) + w * lv[c];
+              float t, e;
+              two_sum(S[c], pr, t, e);
+              S[c] = t;
+              E[c] += e + pe;
+            }
+          }
         }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[c] = group_comp_sum(S[c], E[c]);
       }
-      if (lane == 0) {
-        // + b + alpha J dv, compensated
+      if (!valid) return;
+      {
+        // + b + alpha J dv, compensated (the same in every lane of the group)
         const float bv[3] = {bb.x, bb.y, bb.z}, dv3[3] = {dvc.x, dvc.y, dvc.z};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -518,30 +717,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
           u[c] = cs.value();
         }
       }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) u[c] = __shfl_sync(0xffffffffu, u[c], 0);
-      if (lane == 0) a.C.vc[p] = make_float4(u[0], u[1], u[2], 0.f);
+      if (sub == 0) a.C.vc[p] = make_float4(u[0], u[1], u[2], 0.f);
       const DevBody& bd = s_body[body];
       ContactLaw L;
       contact_law(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, L);
       float gr[3], H[6];
       contact_grad(L, n, gr);
       contact_hess(L, n, H);
-      if (lane < 27) {
-        const float w = ln.w, w2 = w * w;
-        red_add_v4(a.G.acc0 + ln.node, w * gr[0], w * gr[1], w * gr[2], w2 * H[0]);
-        red_add_v4(a.G.acc1 + ln.node, w2 * H[1], w2 * H[2], w2 * H[3], w2 * H[4]);
-        red_add_f32(a.G.acc2 + ln.node, w2 * H[5]);
+#pragma unroll
+      for (int j = 0; j < kGrpNodes; ++j) {
+        if (sub + kGrp * j >= 27) continue;
+        const float w = gn.w[j], w2 = w * w;
+        red_add_v4(a.G.acc0 + gn.node[j], w * gr[0], w * gr[1], w * gr[2], w2 * H[0]);
+        red_add_v4(a.G.acc1 + gn.node[j], w2 * H[1], w2 * H[2], w2 * H[3], w2 * H[4]);
+        red_add_f32(a.G.acc2 + gn.node[j], w2 * H[5]);
       }
     };
-    if (own) {
-      const float n3[3] = {own_nrm.x, own_nrm.y, own_nrm.z};
-      phase_g(gwarp, own_xp, n3, own_nrm.w, own_bias, own_body, own_ln);
-    }
-    for (int p = gwarp + nwarps; p < nc; p += nwarps) {
-      float4 xp; float n[3]; float n0;
-      load_contact(a.C, p, xp, n, n0);
-      phase_g(p, xp, n, n0, a.C.bias[p], a.C.id[p].y, lane_node(g, xp, lane));
+    for (int base = wfirst; base < nc; base += rstride) {
+      const int p = base + grp;
+      const bool valid = p < nc;
+      float4 xp = make_float4(0.f, 0.f, 0.f, 0.f), q = xp, bb = xp;
+      int body = 0;
+      if (valid) {
+        xp = a.C.xp[p];
+        q = a.C.nrm[p];
+        bb = a.C.bias[p];
+        body = a.C.id[p].y;
+      }
+      GroupNodes gn;
+      if (base == wfirst)
+        own_nodes(gn);
+      else
+        group_nodes(g, xp, sub, gn);
+      const float n3[3] = {q.x, q.y, q.z};
+      phase_g(p, valid, xp, n3, q.w, bb, body, gn);
     }
     if (!grid_sync(B)) return;
     lap(1);
@@ -553,7 +762,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     {
       float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // G2, P2 - P*2, J2, A, B
       for (int t = gtid; t < ncn; t += gstride) {
-        const int node = a.G.cnodes[t];
+        const int node = t == gtid ? my_node : a.G.cnodes[t];
         const float4 vs = a.G.vs[node];
         const float m = vs.w;
         float4 v = vcur[node];
@@ -607,7 +816,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
         t = lcur; lcur = lnxt; lnxt = t;
       }
       float acc6[6] = {acc[0], acc[1], acc[2], acc[3], acc[4], 0.f};
-      if (!reduce_all(acc6, slot, B, s_red, s_tot)) return;
+      if (!reduce_all(acc6, slot, B, s_red, s_tot, next_cpart())) return;
     }
     lap(2);
     // stopping test (Alg. 1). The scalar logic runs in thread 0 of each block
@@ -633,25 +842,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
       s_dec = dec;
       s_A = A;
       s_B = Bs;
-      // line-search state, first pass: 0 and a geometric grid 4^-5 .. 4
-      // (quasi-Newton steps on stiff contacts are often much shorter than 1)
+    }
+    if (tid < 32) {
       ls.reset();
-      ls.pts[0] = 0.f;
-      s_pts[0] = 0.f;
-      for (int k = 1; k < kLsPoints; ++k) {
-        ls.pts[k] = exp2f(2.0f * (float)(k - 6));
-        s_pts[k] = ls.pts[k];
-      }
+      if (tid < kLsPoints) s_pts[tid] = ls.pt;
     }
     __syncthreads();
     if (s_dec) break;
 
-    // ---- C: dv_c = J dv (warp per contact)
-    for (int p = gwarp; p < nc; p += nwarps) {
-      const LaneNode ln = p == gwarp ? own_ln : lane_node(g, a.C.xp[p], lane);
-      const float4 d = __ldcg(a.G.dv + ln.node);
-      const float e0 = warp_sum(ln.w * d.x), e1 = warp_sum(ln.w * d.y), e2 = warp_sum(ln.w * d.z);
-      if (lane == 0) a.C.dvc[p] = make_float4(e0, e1, e2, 0.f);
+    // ---- C: dv_c = J dv (kGrp lanes per contact)
+    for (int base = wfirst; base < nc; base += rstride) {
+      const int p = base + grp;
+      const bool valid = p < nc;
+      GroupNodes gn;
+      if (base == wfirst)
+        own_nodes(gn);
+      else
+        group_nodes(g, valid ? a.C.xp[p] : make_float4(0.f, 0.f, 0.f, 0.f), sub, gn);
+      float e[3] = {0.f, 0.f, 0.f};
+      if (valid) {
+        float4 dq[kGrpNodes];
+#pragma unroll
+        for (int j = 0; j < kGrpNodes; ++j)
+          if (sub + kGrp * j < 27) dq[j] = __ldcg(a.G.dv + gn.node[j]);
+#pragma unroll
+        for (int j = 0; j < kGrpNodes; ++j) {
+          if (sub + kGrp * j >= 27) continue;
+          e[0] = fmaf(gn.w[j], dq[j].x, e[0]);
+          e[1] = fmaf(gn.w[j], dq[j].y, e[1]);
+          e[2] = fmaf(gn.w[j], dq[j].z, e[2]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int o = 1; o < kGrp; o <<= 1) e[c] += __shfl_xor_sync(0xffffffffu, e[c], o);
+      if (valid && sub == 0) a.C.dvc[p] = make_float4(e[0], e[1], e[2], 0.f);
     }
     if (!grid_sync(B)) return;
     // ---- L: line-search passes of 8 points each (thread per contact)
@@ -676,7 +902,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
           const DevBody& bd = s_body[b];
           // written by other blocks in phases G and C: read from L2
           const float4 vc = __ldcg(a.C.vc + p), q = __ldcg(a.C.dvc + p);
-          const float u[3] = {vc.x, vc.y, vc.z}, e[3] = {q.x, q.y, q.z};
+          const float e[3] = {q.x, q.y, q.z};
+          const float u[3] = {vc.x, vc.y, vc.z};
           contact_line(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, e, L);
           if (k < kLsCacheDepth) line_store(s_line, slot, L, b);
         }
@@ -688,51 +915,77 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
           acc[kLsPoints + j] += d2;
         }
       }
-      if (!reduce_all(acc, sl, local_ls ? Bl : B, s_red, s_tot)) return;
-      lap(3);
+      if (!reduce_all(acc, sl, local_ls ? Bl : B, s_red, s_tot, local_ls ? nullptr : next_cpart()))
+        return;
       ++ls_passes;
-      if (tid == 0) {
+      if (tid < 32) {
         const int st = ls.update(s_tot, s_A, s_B, a.ls_rel_tol, pass + 1 >= a.ls_max_iters);
-        if (st == LineSearch::kFailed && blockIdx.x == 0) atomicOr(a.status, kStLineSearch);
-        s_dec = st != LineSearch::kMore;
-        s_alpha = ls.best;
-        for (int k = 0; k < kLsPoints; ++k) s_pts[k] = ls.pts[k];
+        if (tid == 0) {
+          if (st == LineSearch::kFailed && blockIdx.x == 0) atomicOr(a.status, kStLineSearch);
+          s_dec = st != LineSearch::kMore;
+          s_alpha = ls.best;
+        }
+        if (tid < kLsPoints) s_pts[tid] = ls.pt;
       }
       __syncthreads();
       if (s_dec) break;
     }
+    lap(3);
     alpha = s_alpha;
     ++it;
     if (alpha == 0.f) break;  // no further progress possible at this precision
   }
+  // no block of a cluster leaves while another may still read its shared memory
+  if (kCluster) cluster_sync_all();
 
   // the solution must end in G.v, which G2P reads; release the node flags
   for (int t = gtid; t < ncn; t += gstride) {
-    const int node = a.G.cnodes[t];
+    const int node = t == gtid ? my_node : a.G.cnodes[t];
     if (vcur != a.G.v) a.G.v[node] = vcur[node];
     a.G.cflag[node] = 0;
   }
   // ---- impulses at the solution: gamma = -dl_c/dv_c on the particle; the
-  // body receives -gamma and its moment about the body origin (Eq. (3))
-  for (int p = gtid; p < nc; p += gstride) {
-    float4 xp; float n[3]; float n0;
-    load_contact(a.C, p, xp, n, n0);
-    const int b = a.C.id[p].y;
-    const DevBody& bd = s_body[b];
-    const float4 vc = __ldcg(a.C.vc + p);
-    const float u[3] = {vc.x, vc.y, vc.z};
-    ContactLaw L;
-    contact_law(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, L);
-    float gr[3];
-    contact_grad(L, n, gr);
-    a.C.gamma[p] = make_float4(-gr[0], -gr[1], -gr[2], 0.f);
-    const float r0 = xp.x - bd.p[0], r1 = xp.y - bd.p[1], r2 = xp.z - bd.p[2];
-    atomicAdd(&s_imp[b][0], gr[0]);
-    atomicAdd(&s_imp[b][1], gr[1]);
-    atomicAdd(&s_imp[b][2], gr[2]);
-    atomicAdd(&s_imp[b][3], r1 * gr[2] - r2 * gr[1]);
-    atomicAdd(&s_imp[b][4], r2 * gr[0] - r0 * gr[2]);
-    atomicAdd(&s_imp[b][5], r0 * gr[1] - r1 * gr[0]);
+  // body receives -gamma and its moment about the body origin (Eq. (3));
+  // each warp sums its contacts body by body before the block's shared sums
+  for (int p0 = gtid & ~31; p0 < nc; p0 += gstride) {
+    const int p = p0 + lane;
+    int b = -1;
+    float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (p < nc) {
+      float4 xp; float n[3]; float n0;
+      load_contact(a.C, p, xp, n, n0);
+      b = a.C.id[p].y;
+      const DevBody& bd = s_body[b];
+      const float4 vc = __ldcg(a.C.vc + p);
+      const float u[3] = {vc.x, vc.y, vc.z};
+      ContactLaw L;
+      contact_law(xp.w, n0, bd.mu, bd.k, bd.d, a.h, a.eps_s, n, u, L);
+      float gr[3];
+      contact_grad(L, n, gr);
+      a.C.gamma[p] = make_float4(-gr[0], -gr[1], -gr[2], 0.f);
+      const float r0 = xp.x - bd.p[0], r1 = xp.y - bd.p[1], r2 = xp.z - bd.p[2];
+      q[0] = gr[0]; q[1] = gr[1]; q[2] = gr[2];
+      q[3] = r1 * gr[2] - r2 * gr[1];
+      q[4] = r2 * gr[0] - r0 * gr[2];
+      q[5] = r0 * gr[1] - r1 * gr[0];
+    }
+    unsigned left = __ballot_sync(0xffffffffu, b >= 0);
+    while (left) {  // one body of the warp at a time (mostly a single one)
+      const int bb = __shfl_sync(0xffffffffu, b, __ffs(left) - 1);
+      const bool mine = b == bb;
+      float t[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        t[c] = mine ? q[c] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t[c] += __shfl_xor_sync(0xffffffffu, t[c], o);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) atomicAdd(&s_imp[bb][c], t[c]);
+      }
+      left &= ~__ballot_sync(0xffffffffu, mine);
+    }
   }
   __syncthreads();
   for (int i = tid; i < a.nb * 6; i += kThreads) {
@@ -747,6 +1000,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     atomicMax(&a.stats->iters_max, it);
     atomicAdd(&a.stats->ls_evals_total, ls_passes);
     if (!local_ls) atomicAdd(&a.stats->ls_split, 1);
+    if (kCluster) atomicAdd(&a.stats->cluster, 1);
     atomicMax(reinterpret_cast<int*>(&a.stats->residual_max), __float_as_int(resid));
   }
 }
@@ -1009,7 +1263,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
   // in mpm_backward mode the live count of the substep just solved
   const int count = a.gbar ? *a.C.count : a.stats->last_contacts;
   const int nc = count < a.C.cap ? count : a.C.cap;
-  int nblk = (nc + kContactsPerBlock - 1) / kContactsPerBlock;
+  int nblk = (nc + kAdjContactsPerBlock - 1) / kAdjContactsPerBlock;
   nblk = nblk < (int)gridDim.x ? nblk : (int)gridDim.x;
   nblk = nblk < kMaxSolveBlocks ? nblk : kMaxSolveBlocks;
   nblk = nblk > 1 ? nblk : 1;
@@ -1018,7 +1272,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
     reinterpret_cast<float*>(s_body)[i] = reinterpret_cast<const float*>(a.bodies)[i];
   for (int i = tid; i < kMaxBodies * kAdjBodySlots; i += kThreads) (&s_bb[0][0])[i] = 0.0;
   __syncthreads();
-  Barrier B{a.bar, (unsigned)nblk, a.status, a.poison};
+  Barrier B{a.bar, (unsigned)nblk, a.status, a.poison, 0, 0u};
   const int gtid = blockIdx.x * kThreads + tid;
   const int gstride = nblk * kThreads;
   const int lane = tid & 31;
@@ -1521,18 +1775,69 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
 }  // namespace
 
 int solve_block_size() { return kThreads; }
-const void* solve_kernel_ptr() { return reinterpret_cast<const void*>(&k_solve); }
-size_t solve_dynamic_smem() { return 3 * sizeof(float4) * kLsCacheSlots; }
+const void* solve_kernel_ptr() { return reinterpret_cast<const void*>(&k_solve<false>); }
+// the line-search cache, then each thread's first contact stencil (node, weight)
+size_t solve_dynamic_smem() {
+  return 3 * sizeof(float4) * kLsCacheSlots + (size_t)kThreads * kGrpNodes * (sizeof(int) + sizeof(float));
+}
 cudaError_t solve_prepare() {
-  return cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_solve),
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_dynamic_smem());
+  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_solve<false>),
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)solve_dynamic_smem());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_solve<true>),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_dynamic_smem());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_solve<true>),
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
 }
 
-cudaError_t launch_solve(const SolveArgs& a, int grid_blocks, cudaStream_t s) {
+namespace {
+cudaLaunchConfig_t cluster_config(int blocks, cudaLaunchAttribute* attr, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = solve_dynamic_smem();
+  cfg.stream = s;
+  attr->id = cudaLaunchAttributeClusterDimension;
+  attr->val.clusterDim.x = blocks;
+  attr->val.clusterDim.y = 1;
+  attr->val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+}  // namespace
+
+int solve_cluster_blocks() {
+  for (int blocks : {16, 8, 4}) {
+    cudaLaunchAttribute attr;
+    const cudaLaunchConfig_t cfg = cluster_config(blocks, &attr, nullptr);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, reinterpret_cast<const void*>(&k_solve<true>),
+                                       &cfg) == cudaSuccess &&
+        clusters >= 1)
+      return blocks;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+cudaError_t launch_solve(const SolveArgs& a, int grid_blocks, int cluster_blocks, cudaStream_t s) {
   SolveArgs args = a;
+  if (cluster_blocks > 0 && args.cluster_max > 0) {
+    cudaLaunchAttribute attr;
+    const cudaLaunchConfig_t cfg = cluster_config(cluster_blocks, &attr, s);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_solve<true>, args);
+    if (e != cudaSuccess) return e;
+  } else {
+    args.cluster_max = 0;
+  }
   void* params[] = {&args};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_solve), dim3(grid_blocks),
-                                     dim3(kThreads), params, solve_dynamic_smem(), s);
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_solve<false>),
+                                     dim3(grid_blocks), dim3(kThreads), params,
+                                     solve_dynamic_smem(), s);
 }
 
 const void* adjoint_kernel_ptr() { return reinterpret_cast<const void*>(&k_adjoint); }

@@ -26,6 +26,7 @@ STATUS_NAMES = ["MPM_OK", "MPM_ERR_INVALID_ARG", "MPM_ERR_CUDA", "MPM_ERR_OOM", 
 MEM_HOST, MEM_DEVICE = 0, 1
 OPT_PROFILE, OPT_SORT_EVERY, OPT_P2G_CHUNK, OPT_GRAPHS, OPT_SOLVE_BLOCKS = 1, 2, 3, 4, 5
 OPT_TAPE_SOLUTIONS = 7
+OPT_CLUSTER_CONTACTS = 8
 OPT_TEST_BARRIER_TIMEOUT = 6
 PHASES = ["sort", "p2g", "grid", "solve", "g2p"]
 
@@ -63,7 +64,7 @@ class StepStats(C.Structure):
                 ("active_blocks_max", C.c_int32), ("contacts_total", C.c_int64),
                 ("residual_max", C.c_double), ("status_bits", C.c_int32),
                 ("p2g_global_chunks", C.c_int32), ("solve_us", C.c_float * 5),
-                ("ls_split_substeps", C.c_int32)]
+                ("ls_split_substeps", C.c_int32), ("cluster_substeps", C.c_int32)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -463,7 +464,7 @@ def body_dict(r):
 
 
 def solver_params(eps_r=5e-2, eps_a=np.finfo(np.float64).eps, max_iters=1000, eps_s=scenes.EPS_S,
-                  ls_rel_tol=1e-5, ls_max_iters=50):
+                  ls_rel_tol=1e-3, ls_max_iters=50):
     return SolverParams(eps_r, eps_a, max_iters, eps_s, ls_rel_tol, ls_max_iters)
 
 

@@ -34,8 +34,11 @@ def native():
     return N
 
 
-def run_parity(native, sc, n_sub=2, warm_steps=0, warm_solver=None, tol_v=TOL_V, check_grid=True):
+def run_parity(native, sc, n_sub=2, warm_steps=0, warm_solver=None, tol_v=TOL_V, check_grid=True,
+               options=()):
     sim = native.Sim(sc)
+    for opt, val in options:
+        native.mpm_set_option(sim.ctx, opt, val)
     if warm_steps:
         for _ in range(warm_steps):
             sim.step(solver=warm_solver or native.solver_params(eps_r=1e-4, max_iters=20000),
@@ -105,7 +108,7 @@ def run_parity(native, sc, n_sub=2, warm_steps=0, warm_solver=None, tol_v=TOL_V,
             bound = 1e-5 * vmax_g + 2.0 * 1e-6 * scale / np.sqrt(np.maximum(om, 1e-300))
             assert np.all(np.abs(v - ov).max(1) <= bound)
         report.append((k, info.n_contacts, info.iters, stats.iters_total, ev,
-                       stats.ls_split_substeps))
+                       stats.ls_split_substeps, stats.cluster_substeps))
     sim.close()
     return report
 
@@ -129,6 +132,16 @@ def test_free_fall_matches_closed_form_and_oracle(native):
 def test_normal_contact_parity(native):
     rep = run_parity(native, scenes.cube_contact(n_side=10, v0=(0.0, 0.0, -0.05)), n_sub=3)
     assert all(r[1] > 0 for r in rep)
+    # a few hundred contacts: one thread-block cluster, each block line-searching alone
+    assert all(r[6] == 1 and r[5] == 0 for r in rep), rep
+
+
+def test_normal_contact_parity_cooperative_launch(native):
+    """The same substeps through the cooperative kernel (device-wide barriers)
+    instead of the cluster."""
+    rep = run_parity(native, scenes.cube_contact(n_side=10, v0=(0.0, 0.0, -0.05)), n_sub=2,
+                     options=((native.OPT_CLUSTER_CONTACTS, 0),))
+    assert all(r[1] > 0 and r[6] == 0 for r in rep), rep
 
 
 def test_sliding_contact_parity(native):
@@ -196,6 +209,16 @@ def test_split_line_search_parity(native):
     the residual against the oracle, substep by substep, and the statistics
     must show that the split path ran."""
     sc = scenes.sand_slab()
-    rep = run_parity(native, sc, n_sub=2)
+    rep = run_parity(native, sc, n_sub=2, options=((native.OPT_CLUSTER_CONTACTS, 4096),))
     assert all(r[1] > 4096 for r in rep), [r[1] for r in rep]
-    assert all(r[5] == 1 for r in rep), "the split line search did not run: %s" % rep
+    assert all(r[5] == 1 and r[6] == 0 for r in rep), "the split line search did not run: %s" % rep
+
+
+def test_cluster_split_line_search_parity(native):
+    """The same slab (5,000+ contacts) solved by one thread-block cluster: the
+    line-search passes split over the cluster's blocks and reduced through
+    distributed shared memory, against the oracle."""
+    sc = scenes.sand_slab()
+    rep = run_parity(native, sc, n_sub=2, options=((native.OPT_CLUSTER_CONTACTS, 1 << 16),))
+    assert all(r[1] > 4096 for r in rep), [r[1] for r in rep]
+    assert all(r[5] == 1 and r[6] == 1 for r in rep), "the cluster solve did not run: %s" % rep
