@@ -238,14 +238,17 @@ mpm_status mpm_set_material(mpm_ctx* ctx, int32_t group, const mpm_material* mat
 mpm_status mpm_set_rigid_bodies(mpm_ctx* ctx, int32_t n, const mpm_rigid_body* bodies);
 
 /* Current rigid bodies (kinematic and dynamic ones after their pose
-   updates). */
+   updates; synchronises the context's stream when the device moved them). */
 mpm_status mpm_get_rigid_bodies(const mpm_ctx* ctx, int32_t n, mpm_rigid_body* out);
 
 /* Make body `index` (of the current set) dynamic with `dyn`, or, with dyn
    NULL, stop integrating it (it keeps its current pose and velocity and
    its kinematic flag applies again). A dynamic body's kinematic flag is
-   ignored. Each mpm_step with a dynamic body synchronises at its end to
-   read the step's impulses. mpm_set_rigid_bodies clears all dynamics. */
+   ignored. The bodies' update after each step (this one, and the kinematic
+   advance) runs on the device, one warp per body, inside the step's launch
+   sequence, so mpm_step does not wait for it; while a tape records
+   (mpm_tape_begin) the host integrates the bodies instead, synchronising at
+   the end of each step. mpm_set_rigid_bodies clears all dynamics. */
 mpm_status mpm_set_rigid_dynamics(mpm_ctx* ctx, int32_t index, const mpm_rigid_dynamics* dyn);
 
 /* One rigid time step: n_substeps MPM substeps of size h with the rigid

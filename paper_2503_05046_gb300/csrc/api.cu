@@ -38,6 +38,14 @@ struct mpm_ctx {
   bool imp_seen_valid = false;
   DevBody* bodies_d = nullptr;
   bool bodies_dirty = true;
+  // the bodies' motion on the device between steps (rigid.cu): each body's
+  // kind and dynamics, and the impulse accumulator at the step's start
+  DevDyn* dyn_d = nullptr;
+  double* imp0_d = nullptr;
+  DevBody* bodies_step_d = nullptr;  // the last step's frozen bodies (device update)
+  bool last_dev_rigid = false;
+  bool dyn_dirty = true;
+  bool bodies_stale = false;  // the device moved the bodies since the host copy
   GridArrays G{};
   size_t n_nodes = 0;
   int n_blocks = 0;
@@ -59,6 +67,7 @@ struct mpm_ctx {
     int64_t n = -1;
     int n_substeps = 0, nb = 0, chunk = 0, sort_now = 0, solve_blocks = 0, taping = 0;
     int cluster_max = 0;
+    int rigid = 0;
     const void* tape_pool = nullptr;  // baked into the launches when taping
     float h = 0.f;
     mpm_solver_params sp{};
@@ -459,7 +468,8 @@ void release(mpm_ctx* c) {
                   c->status, c->stats, c->impulses, c->sb.keys[0], c->sb.keys[1], c->sb.vals[0],
                   c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage, c->adj_vec, c->adj_body,
                   c->adj_out, c->adj_ids, c->adj_io, c->bw_buf, c->bw_gbar, c->bw_slot, c->bw_mat,
-                  c->tape_pool, c->tape_recs, c->tape_counters, c->bw_snap, c->bw_gbody};
+                  c->tape_pool, c->tape_recs, c->tape_counters, c->bw_snap, c->bw_gbody, c->dyn_d,
+                  c->imp0_d, c->bodies_step_d};
   for (auto& t : c->tape)
     if (t.state) cudaFree(t.state);
   for (void* p : ptrs)
@@ -522,11 +532,19 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
 
 // The launches of one step: the radix sort from particle buffer `from` into
 // the other (if sort_now), then n_substeps substeps on the sorted buffer.
+// With `rigid`, the bodies then move on the device (kinematic ones by their
+// velocity, dynamic ones by Eq. (3) with the step's impulses, rigid.cu).
 cudaError_t enqueue_step(mpm_ctx* ctx, int from, bool sort_now, int n_substeps, float hf,
-                         const mpm_solver_params& sp, int solve_blocks, cudaStream_t s) {
+                         const mpm_solver_params& sp, int solve_blocks, cudaStream_t s,
+                         bool rigid = false) {
   const int n = (int)ctx->n;
   const int nb = (int)ctx->bodies.size();
   int cur = from;
+  if (rigid && nb > 0) {
+    const cudaError_t e = cudaMemcpyAsync(ctx->imp0_d, ctx->impulses, 6 * nb * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
   if (sort_now) {
     mark_phase(ctx, MPM_PHASE_SORT);
     launch_sort(ctx->g, ctx->P[cur], ctx->P[1 - cur], n, ctx->sb, s);
@@ -536,7 +554,65 @@ cudaError_t enqueue_step(mpm_ctx* ctx, int from, bool sort_now, int n_substeps, 
     const cudaError_t e = enqueue_substep(ctx, cur, nb, hf, sp, solve_blocks, true, s, ctx->taping);
     if (e != cudaSuccess) return e;
   }
+  if (rigid && nb > 0) {
+    // the frozen bodies stay readable for the last substep's contact adjoint
+    const cudaError_t e = cudaMemcpyAsync(ctx->bodies_step_d, ctx->bodies_d, nb * sizeof(DevBody),
+                                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    launch_rigid_update(ctx->bodies_d, ctx->dyn_d, nb, ctx->impulses, ctx->imp0_d,
+                        (double)hf * n_substeps, ctx->spec.gravity, s);
+  }
   return cudaGetLastError();
+}
+
+// The host copy of the bodies, after the device moved them (synchronises).
+cudaError_t sync_host_bodies(mpm_ctx* ctx) {
+  if (!ctx->bodies_stale) return cudaSuccess;
+  const int nb = (int)ctx->bodies.size();
+  DevBody tmp[kMaxBodies];
+  cudaError_t e = cudaSuccess;
+  if (nb) e = cudaMemcpyAsync(tmp, ctx->bodies_d, nb * sizeof(DevBody), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < nb; ++i) {
+    mpm_rigid_body& b = ctx->bodies[i];
+    for (int k = 0; k < 9; ++k) b.R[k] = tmp[i].R[k];
+    for (int k = 0; k < 3; ++k) {
+      b.p[k] = tmp[i].p[k];
+      b.v[k] = tmp[i].v[k];
+      b.omega[k] = tmp[i].w[k];
+    }
+  }
+  ctx->bodies_stale = false;
+  return cudaSuccess;
+}
+
+// Each body's kind and dynamics for the device update.
+cudaError_t upload_dynamics(mpm_ctx* ctx) {
+  const int nb = (int)ctx->bodies.size();
+  DevDyn tmp[kMaxBodies];
+  memset(tmp, 0, sizeof(tmp));
+  for (int i = 0; i < nb; ++i) {
+    DevDyn& d = tmp[i];
+    if (ctx->is_dyn[i]) {
+      const mpm_rigid_dynamics& m = ctx->dyn[i];
+      d.kind = kRigidDynamic;
+      d.dof_mask = m.dof_mask;
+      d.gravity = m.gravity;
+      d.mass = m.mass;
+      for (int k = 0; k < 3; ++k) {
+        d.inertia[k] = m.inertia[k];
+        d.force[k] = m.force[k];
+        d.torque[k] = m.torque[k];
+      }
+    } else {
+      d.kind = ctx->bodies[i].kinematic ? kRigidKinematic : kRigidStatic;
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (nb) e = cudaMemcpyAsync(ctx->dyn_d, tmp, nb * sizeof(DevDyn), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) ctx->dyn_dirty = false;
+  return e;
 }
 
 int ceil_log2(int v) {
@@ -631,7 +707,10 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
        dalloc(&ctx->poison, 1) == cudaSuccess &&
        dalloc(&ctx->status, 1) == cudaSuccess && dalloc(&ctx->stats, 1) == cudaSuccess &&
        dalloc(&ctx->impulses, 6 * kMaxBodies) == cudaSuccess &&
-       dalloc(&ctx->bodies_d, kMaxBodies) == cudaSuccess;
+       dalloc(&ctx->bodies_d, kMaxBodies) == cudaSuccess &&
+       dalloc(&ctx->dyn_d, kMaxBodies) == cudaSuccess &&
+       dalloc(&ctx->imp0_d, 6 * kMaxBodies) == cudaSuccess &&
+       dalloc(&ctx->bodies_step_d, kMaxBodies) == cudaSuccess;
   const int hist_len = sort_hist_len((int)cap);
   ok = ok && dalloc(&ctx->sb.keys[0], cap) == cudaSuccess && dalloc(&ctx->sb.keys[1], cap) == cudaSuccess &&
        dalloc(&ctx->sb.vals[0], cap) == cudaSuccess && dalloc(&ctx->sb.vals[1], cap) == cudaSuccess &&
@@ -857,6 +936,8 @@ mpm_status mpm_set_rigid_bodies(mpm_ctx* ctx, int32_t n, const mpm_rigid_body* b
   if (ctx->taping && !ctx->tape.empty()) ctx->tape_reset = true;
   ctx->bodies.assign(bodies, bodies + n);
   ctx->bodies_dirty = true;
+  ctx->bodies_stale = false;
+  ctx->dyn_dirty = true;
   ctx->is_dyn.assign(n, 0);
   ctx->dyn.assign(n, mpm_rigid_dynamics{});
   ctx->imp_seen_valid = false;
@@ -878,11 +959,15 @@ mpm_status mpm_set_rigid_dynamics(mpm_ctx* ctx, int32_t index, const mpm_rigid_d
   }
   ctx->is_dyn[index] = dyn ? 1 : 0;
   ctx->imp_seen_valid = false;
+  ctx->dyn_dirty = true;
   return MPM_OK;
 }
 
-mpm_status mpm_get_rigid_bodies(const mpm_ctx* ctx, int32_t n, mpm_rigid_body* out) {
-  if (!ctx || !out || n < 0 || n > (int32_t)ctx->bodies.size()) return MPM_ERR_INVALID_ARG;
+mpm_status mpm_get_rigid_bodies(const mpm_ctx* cctx, int32_t n, mpm_rigid_body* out) {
+  if (!cctx || !out || n < 0 || n > (int32_t)cctx->bodies.size()) return MPM_ERR_INVALID_ARG;
+  // (the context's host copy of the bodies is refreshed, nothing else)
+  mpm_ctx* ctx = const_cast<mpm_ctx*>(cctx);
+  CU(sync_host_bodies(ctx));
   for (int i = 0; i < n; ++i) out[i] = ctx->bodies[i];
   return MPM_OK;
 }
@@ -908,15 +993,20 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_step: bad solver parameters");
   cudaStream_t s = ctx->stream;
   const int nb = (int)ctx->bodies.size();
+  // the bodies move on the device after the step unless a tape records the
+  // steps (the tape keeps each step's bodies and impulses on the host)
+  const bool dev_rigid = !ctx->taping;
+  if (!dev_rigid) CU(sync_host_bodies(ctx));
   if (ctx->bodies_dirty) {
     DevBody tmp[kMaxBodies];
     for (int i = 0; i < nb; ++i) tmp[i] = to_dev(ctx->bodies[i]);
     if (nb) CU(cudaMemcpyAsync(ctx->bodies_d, tmp, nb * sizeof(DevBody), cudaMemcpyHostToDevice, s));
     ctx->bodies_dirty = false;
   }
+  if (dev_rigid && ctx->dyn_dirty) CU(upload_dynamics(ctx));
   bool has_dyn = false;
   for (int d : ctx->is_dyn) has_dyn = has_dyn || d;
-  if (has_dyn && !ctx->imp_seen_valid) {
+  if (!dev_rigid && has_dyn && !ctx->imp_seen_valid) {
     // the impulse accumulator at the start of the step (the caller's resets
     // and earlier steps included), so that the step's own impulses are known
     ctx->imp_seen.assign(6 * kMaxBodies, 0.0);
@@ -964,13 +1054,14 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     k.n = n; k.n_substeps = n_substeps; k.nb = nb; k.chunk = ctx->p2g_chunk;
     k.sort_now = sort_now ? 1 : 0; k.solve_blocks = solve_blocks; k.h = hf; k.sp = sp;
     k.cluster_max = cluster_contacts(ctx);
+    k.rigid = dev_rigid ? 1 : 0;
     k.taping = ctx->taping && ctx->tape_pool ? 1 : 0;
     k.tape_pool = ctx->tape_pool;
     const mpm_ctx::GraphKey& o = ctx->gkey[from];
     const bool same = ctx->gexec[from] && o.n == k.n && o.n_substeps == k.n_substeps && o.nb == k.nb &&
                       o.chunk == k.chunk && o.sort_now == k.sort_now &&
                       o.solve_blocks == k.solve_blocks && o.h == k.h && o.taping == k.taping &&
-                      o.cluster_max == k.cluster_max &&
+                      o.cluster_max == k.cluster_max && o.rigid == k.rigid &&
                       o.tape_pool == k.tape_pool &&
                       memcmp(&o.sp, &k.sp, sizeof(k.sp)) == 0;
     if (!same) {
@@ -981,7 +1072,8 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        const cudaError_t le = enqueue_step(ctx, from, sort_now, n_substeps, hf, sp, solve_blocks, s);
+        const cudaError_t le =
+            enqueue_step(ctx, from, sort_now, n_substeps, hf, sp, solve_blocks, s, dev_rigid);
         e = cudaStreamEndCapture(s, &graph);
         if (e == cudaSuccess) e = le;
       }
@@ -1003,18 +1095,24 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
       launched = true;
     }
   }
-  if (!launched) CU(enqueue_step(ctx, from, sort_now, n_substeps, hf, sp, solve_blocks, s));
+  if (!launched) CU(enqueue_step(ctx, from, sort_now, n_substeps, hf, sp, solve_blocks, s, dev_rigid));
   if (sort_now) ctx->cur = 1 - from;
   CU(cudaGetLastError());
   ctx->adj_ready = n_substeps > 0;
+  ctx->last_dev_rigid = dev_rigid;
   ctx->last_h = hf;
   ctx->last_eps_s = sp.eps_s;
   ctx->last_nb = nb;
   // async splitting (Eq. (3)-(4)): kinematic bodies move with their frozen
-  // velocity; dynamic ones take the step's accumulated contact impulses
+  // velocity; dynamic ones take the step's accumulated contact impulses (on
+  // the device, launched above; on the host while a tape records)
   const double dt = h * n_substeps;
   bool moved = false, any_dyn = false;
-  for (size_t i = 0; i < ctx->bodies.size(); ++i) {
+  if (dev_rigid) {
+    if (nb > 0 && n_substeps > 0) ctx->bodies_stale = true;
+    ctx->imp_seen_valid = false;
+  }
+  for (size_t i = 0; i < ctx->bodies.size() && !dev_rigid; ++i) {
     if (ctx->is_dyn[i]) {
       any_dyn = true;
     } else if (ctx->bodies[i].kinematic) {
@@ -1022,7 +1120,7 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
       moved = true;
     }
   }
-  if (any_dyn) {
+  if (any_dyn && !dev_rigid) {
     std::vector<double> now(6 * kMaxBodies, 0.0);
     CU(cudaMemcpyAsync(now.data(), ctx->impulses, 6 * nb * sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -1043,7 +1141,7 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     ctx->imp_seen = now;
     ctx->imp_seen_valid = true;
     moved = true;
-  } else {
+  } else if (!dev_rigid) {
     ctx->imp_seen_valid = false;  // the accumulator moves on untracked
   }
   if (moved) ctx->bodies_dirty = true;
@@ -1230,7 +1328,8 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
   }
   AdjointArgs a;
   memset(&a, 0, sizeof(a));  // gbar = nullptr: the single-solve mode
-  a.g = ctx->g; a.G = ctx->G; a.C = ctx->C; a.bodies = ctx->bodies_d; a.nb = ctx->last_nb;
+  a.g = ctx->g; a.G = ctx->G; a.C = ctx->C; a.nb = ctx->last_nb;
+  a.bodies = ctx->last_dev_rigid ? ctx->bodies_step_d : ctx->bodies_d;
   a.h = ctx->last_h; a.eps_s = ctx->last_eps_s; a.eps_r = ap.eps_r; a.max_iters = ap.max_iters;
   a.n_in = (int)n; a.ids = d_ids; a.vbar = d_vbar; a.vstar_bar = d_vsb;
   a.contact_bar = d_cbar; a.contact_cap = (int)ccap; a.body_bar = ctx->adj_body;
@@ -1353,6 +1452,8 @@ mpm_status mpm_backward(mpm_ctx* ctx, int32_t mem_kind, const float* x_bar, cons
   if (!ctx) return MPM_ERR_INVALID_ARG;
   if (mem_kind != MPM_MEM_HOST && mem_kind != MPM_MEM_DEVICE)
     return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_backward: bad mem_kind");
+  // the replays overwrite the device's body table: keep the current bodies
+  CU(sync_host_bodies(ctx));
   mpm_adjoint_params ap;
   ap.eps_r = 1e-6;
   ap.max_iters = 2000;

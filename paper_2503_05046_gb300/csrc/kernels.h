@@ -189,6 +189,22 @@ void launch_bar_in(const Particles& P, int n, const float* x, const float* v, co
 void launch_bar_out(const Particles& P, int n, const float* bar, float* x, float* v, float* C,
                     float* F, cudaStream_t s);
 
+// ---- rigid.cu: the bodies' update after a time step (Eq. (3)-(4)) ----
+enum { kRigidStatic = 0, kRigidKinematic = 1, kRigidDynamic = 2 };
+struct DevDyn {
+  int kind;      // kRigid*
+  int dof_mask;  // free DoFs of a dynamic body (bits 0-2 translation, 3-5 rotation)
+  int gravity;   // nonzero: the body's weight is part of its load
+  int pad;
+  float mass;
+  float inertia[3];  // principal moments, body frame
+  float force[3];    // constant load, world frame
+  float torque[3];
+};
+// one warp per body; imp - imp0 is the step's impulse and moment on each body
+void launch_rigid_update(DevBody* bodies, const DevDyn* dyn, int nb, const double* imp,
+                         const double* imp0, double dt, const double* gravity, cudaStream_t s);
+
 // ---- g2p.cu: grid-to-particle with the constitutive update ----
 struct G2PArgs {
   GridDev g;
