@@ -10,7 +10,9 @@ ones, which a previous rollout has moved) and keep the dynamics set on `sim`
 (Sim.set_dynamics). Its backward pass is the library's
 hand-written adjoint (mpm_backward: checkpoints per step, the adjoints of
 G2P, the contact solve by implicit differentiation, the grid update and
-P2G); nothing is traced or taped by torch.
+P2G); nothing is traced or taped by torch. Particle states and their
+adjoints move between torch and the library in device memory
+(MPM_MEM_DEVICE).
 """
 import numpy as np
 import torch
@@ -34,30 +36,40 @@ class _Rollout(torch.autograd.Function):
         sim.set_bodies(bodies)  # clears the dynamics: set them again
         for i, d in sorted(dynamics.items()):
             sim.set_dynamics(i, d)
-        x = x0.detach().to(torch.float32).cpu().numpy().reshape(n, 3)
-        v = v0.detach().to(torch.float32).cpu().numpy().reshape(n, 3)
-        Cm = np.zeros((n, 3, 3), np.float32)
-        F = np.tile(np.eye(3, dtype=np.float32), (n, 1, 1))
+        # the state goes to and comes from the context's device memory
+        # directly (no host round trip)
+        dev = sim.device
+        x = x0.detach().to(device=dev, dtype=torch.float32).reshape(n, 3).contiguous()
+        v = v0.detach().to(device=dev, dtype=torch.float32).reshape(n, 3).contiguous()
+        Cm = torch.zeros((n, 3, 3), dtype=torch.float32, device=dev)
+        F = torch.eye(3, dtype=torch.float32, device=dev).expand(n, 3, 3).contiguous()
         sim.set_particles(x, v, Cm, F)
         sim.tape_begin()
         for _ in range(int(n_steps)):
             sim.step(solver=solver)
         sim.tape_end()
-        out = sim.get_particles()
+        xf = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        vf = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        sim.read_particles(x=xf, v=vf)
         ctx.sim = sim
         ctx.eps_r = eps_r
+        ctx.dev = dev
         ctx.like = [(a.device, a.dtype) for a in (x0, v0, E, nu, mu, body_v)]
-        xf = torch.from_numpy(out["x"]).to(x0.device)
-        vf = torch.from_numpy(out["v"]).to(x0.device)
-        return xf, vf
+        return xf.to(x0.device), vf.to(x0.device)
 
     @staticmethod
     def backward(ctx, gx, gv):
         sim = ctx.sim
-        g = sim.backward(x_bar=None if gx is None else gx.detach().cpu().numpy(),
-                         v_bar=None if gv is None else gv.detach().cpu().numpy(), eps_r=ctx.eps_r)
-        grads = [np.asarray(g[k]) for k in ("x", "v", "E", "nu", "mu", "body_v")]
-        out = [torch.as_tensor(a, dtype=dt, device=dev) for a, (dev, dt) in zip(grads, ctx.like)]
+
+        def on_dev(t):
+            return None if t is None else t.detach().to(device=ctx.dev, dtype=torch.float32).contiguous()
+
+        g = sim.backward(x_bar=on_dev(gx), v_bar=on_dev(gv), eps_r=ctx.eps_r)
+        out = []
+        for k, (dev, dt) in zip(("x", "v", "E", "nu", "mu", "body_v"), ctx.like):
+            a = g[k]
+            out.append(a.to(device=dev, dtype=dt) if torch.is_tensor(a)
+                       else torch.as_tensor(np.asarray(a), dtype=dt, device=dev))
         return (None, None, None, None, None, *out)
 
 

@@ -132,11 +132,19 @@ class _FakeSim:
     def tape_end(self):
         pass
 
+    device = None  # torch.device("cpu") once torch is imported (see below)
+
     def get_particles(self):
         return {"x": np.zeros((self.n, 3), np.float32), "v": np.zeros((self.n, 3), np.float32)}
 
+    def read_particles(self, x=None, v=None, Cm=None, F=None):
+        for a in (x, v, Cm, F):
+            if a is not None:
+                a.zero_()
+
     def backward(self, x_bar=None, v_bar=None, eps_r=None):
-        return {"x": np.ones((self.n, 3)), "v": np.ones((self.n, 3)), "E": [2.0], "nu": [3.0],
+        import torch
+        return {"x": torch.ones((self.n, 3)), "v": torch.ones((self.n, 3)), "E": [2.0], "nu": [3.0],
                 "mu": [4.0], "body_v": [[5.0, 6.0, 7.0]]}
 
 
@@ -150,6 +158,7 @@ def test_autograd_rollout_keeps_dynamics_and_start_bodies(monkeypatch):
     monkeypatch.setattr(native, "mpm_set_material", lambda ctx, gi, m: None)
     b0 = {"p": np.zeros(3), "v": np.array([0.1, 0.0, 0.0]), "mu": 0.5}
     sim = _FakeSim(4, [b0])
+    sim.device = torch.device("cpu")
     sim.set_dynamics(0, {"mass": 1.0, "inertia": [1.0, 1.0, 1.0]})
     x0 = torch.zeros(4, 3)
     v0 = torch.zeros(4, 3, requires_grad=True)
