@@ -426,18 +426,42 @@ def small_scene_latency(native, n_steps=10):
 
 def batched_throughput(native, n_scenes=256, steps=3, warmup=2):
     """Many independent scenes of uneven size (2k-64k particles each, elastic or
-    sand, a gripper jaw and the ground), each in its own context and stream,
-    their steps enqueued one after another without waiting (CUDA-graph replays,
-    so the scenes run side by side on the GPU), with the SM cap of each
-    scene's contact solve and the P2G block size picked by the autotuner
-    (tune.tune_batch, timed steps of the batch per candidate), against the
-    single-scene path looped (one scene at a time, every step waited for, the
-    solve on as many SMs as it takes, default P2G blocks)."""
+    sand, a gripper jaw and the ground) advanced three ways, each timed by the
+    host clock around `steps` steps of every scene, synchronised on both sides:
+    - `value`: one batch (mpm_batch_*): a substep of all scenes is one P2G, one
+      compaction, one grid-update, one contact-solve and one G2P launch over
+      (scene, block) work items, the time step one CUDA graph; launch options
+      picked by tune.tune_batch_launch;
+    - `concurrent_value`: one context per scene, each on its own stream
+      replaying its own step graph, enqueued one after another without
+      waiting, SM cap of the solve and P2G block size by tune.tune_batch;
+    - `loop_value`: the single-scene path looped (one scene at a time, every
+      step waited for, default options)."""
     import torch
     from paper_2503_05046_gb300 import scenes, tune
     scs = [scenes.batch_scene(i) for i in range(n_scenes)]
-    sims = [native.Sim(sc, max_contacts=2 * scenes.n_particles(sc)) for sc in scs]
+    h, N = scs[0]["h"], scs[0]["substeps"]
     solver = native.solver_params(eps_r=5e-2, max_iters=1000)
+    n_total = sum(scenes.n_particles(sc) for sc in scs)
+
+    # (1) one batch
+    batch = native.Batch(scs, max_contacts=lambda sc: 2 * scenes.n_particles(sc))
+    best, table_b = tune.tune_batch_launch(batch, h, N, solver)
+    for _ in range(warmup):
+        batch.step(h, N, solver)
+    batch.synchronize(stats=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        batch.step(h, N, solver)
+    torch.cuda.synchronize()
+    t_persist = time.perf_counter() - t0
+    code_b, codes_b, stats_b = batch.synchronize()
+    contacts_b = [s["contacts_max"] for s in stats_b]
+    batch.close()
+
+    # (2) contexts side by side, (3) the loop
+    sims = [native.Sim(sc, max_contacts=2 * scenes.n_particles(sc)) for sc in scs]
     (solve_cap, chunk), table = tune.tune_batch(sims, scs, solver)
 
     def run(cap, wait_each, p2g_chunk=256):
@@ -459,22 +483,34 @@ def batched_throughput(native, n_scenes=256, steps=3, warmup=2):
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
-    t_batch = run(solve_cap, False, chunk)
+    t_conc = run(solve_cap, False, chunk)
     codes = [native.mpm_synchronize(sim.ctx) for sim in sims]
     t_loop = run(0, True)
-    n_total = sum(scenes.n_particles(sc) for sc in scs)
     for sim in sims:
         sim.close()
-    v_batch = n_scenes * steps / t_batch
+    v_persist = n_scenes * steps / t_persist
+    v_conc = n_scenes * steps / t_conc
     v_loop = n_scenes * steps / t_loop
-    return {"scenes": n_scenes, "particles": n_total, "steps": steps,
-            "substeps_per_step": scs[0]["substeps"], "value": v_batch, "unit": "scene-steps/s",
-            "loop_value": v_loop, "speedup": v_batch / v_loop,
-            "particle_substeps_per_s": n_total * scs[0]["substeps"] * steps / t_batch,
-            "tuned": {"solve_cap": solve_cap, "p2g_chunk": chunk,
-                      "candidates_s_per_2_steps": [[c, k, round(t, 4)] for c, k, t in table]},
-            "status_batched": "ok" if all(c == 0 for c in codes) else
-                              "%d scenes reported %s" % (sum(c != 0 for c in codes), sorted(set(codes))),
+    names = {native.BATCH_OPT_P2G_CHUNK: "p2g_chunk", native.BATCH_OPT_G2P_THREADS: "g2p_threads",
+             native.BATCH_OPT_GRID_PARTICLES: "grid_particles_per_block"}
+    return {"scenes": n_scenes, "particles": n_total, "steps": steps, "substeps_per_step": N,
+            "value": v_persist, "unit": "scene-steps/s",
+            "particle_substeps_per_s": n_total * N * steps / t_persist,
+            "ms_per_step": 1e3 * t_persist / steps,
+            "launches_per_step": 2 + 5 * N,
+            "concurrent_value": v_conc, "loop_value": v_loop,
+            "speedup_vs_concurrent": v_persist / v_conc, "speedup_vs_loop": v_persist / v_loop,
+            "tuned": {names[k]: v for k, v in best.items()},
+            "tuning_s_per_2_steps": [[{names[k]: v for k, v in c.items()}, round(t, 4)]
+                                     for c, t in table_b],
+            "contacts_per_scene": [int(min(contacts_b)), int(max(contacts_b))],
+            "status": "ok" if code_b == 0 else
+                      "%d scenes reported %s" % (int(np.sum(codes_b != 0)), sorted(set(codes_b.tolist()))),
+            "concurrent_tuned": {"solve_cap": solve_cap, "p2g_chunk": chunk,
+                                 "candidates_s_per_2_steps": [[c, k, round(t, 4)]
+                                                              for c, k, t in table]},
+            "status_concurrent": "ok" if all(c == 0 for c in codes) else
+                                 "%d scenes reported %s" % (sum(c != 0 for c in codes), sorted(set(codes))),
             "timing": "host clock around the enqueue loop, synchronised on both sides"}
 
 

@@ -494,6 +494,75 @@ enum {
    (arrays of MPM_NUM_PHASES; either may be NULL). Synchronises. */
 mpm_status mpm_get_phase_times(mpm_ctx* ctx, double* ms, int64_t* launches, int32_t reset);
 
+/* ---- Batches: many small scenes advanced by the launches of one ---------
+   Launch overhead dominates small scenes (Sec. V-A: the per-substep kernel
+   launches and host-device synchronisations). A batch advances n
+   independent contexts together so that one substep of ALL of them costs
+   five launches: P2G (with contact registration), block compaction, grid
+   update, contact solve (Alg. 1) and G2P, each over a work list of
+   (scene, thread block) items that covers every scene, plus one launch at
+   the start and one at the end of the time step (the latter moves every
+   scene's bodies on the device as mpm_step does, Eq. (3)-(4)). The time
+   step replays as one CUDA graph. Each scene's contact solve runs in one
+   thread block of its own (its reductions need no device-wide barrier).
+
+   Members are contexts created on the same device with the SAME
+   cuda_stream (the batch's stream), none recording a tape; the caller keeps
+   ownership and destroys them after the batch. Each member keeps its own
+   particles, grid, bodies, dynamics, impulse accumulators and status, and
+   every per-context entry point stays valid on a member between batch steps
+   (the shared stream orders it). The batch sorts each member's particles
+   once when it is created and again on mpm_batch_sort; its steps do not
+   sort. After a batch step a member's contact adjoint is not available
+   (mpm_contact_adjoint returns MPM_ERR_STATE until its next mpm_step).
+   Particle counts may differ between members (uneven scenes). Any contact
+   count is solved, each scene's in its one block: the batch suits scenes of
+   up to a few thousand contacts, larger ones belong in their own context. */
+typedef struct mpm_batch mpm_batch;
+
+/* Create a batch of n >= 1 members. MPM_ERR_INVALID_ARG if a member is NULL,
+   repeated, on another device or stream, or recording a tape. */
+mpm_status mpm_batch_create(mpm_ctx* const* ctxs, int32_t n, mpm_batch** out);
+
+/* One rigid time step of every member: n_substeps substeps of size h with
+   the solver parameters (NULL: the defaults of mpm_step), then the bodies'
+   update. Asynchronous; failures are reported by mpm_batch_synchronize. */
+mpm_status mpm_batch_step(mpm_batch* batch, double h, int32_t n_substeps,
+                          const mpm_solver_params* solver);
+
+/* Re-sort every member's particles by grid block (per-member launches, not
+   part of the step's graph). Asynchronous. */
+mpm_status mpm_batch_sort(mpm_batch* batch);
+
+/* Wait for the batch's stream. status [n] (may be NULL): each member's
+   status (MPM_OK or its first device-side failure, which is then cleared);
+   stats [n] (may be NULL): each member's statistics of the last batch step,
+   as mpm_step reports them (status_bits: the member's status word at the
+   step's end). Returns the first member failure in member order, or MPM_OK. */
+mpm_status mpm_batch_synchronize(mpm_batch* batch, int32_t* status, mpm_step_stats* stats);
+
+/* Launch options of the batch (autotuned by the Python binding):
+   MPM_BATCH_OPT_GRAPHS: nonzero (default) replays the step as a CUDA graph;
+   MPM_BATCH_OPT_P2G_CHUNK: particles per P2G thread block, 256, 512 or 1024
+     (32, 64 or 128 per warp tile; default 256);
+   MPM_BATCH_OPT_G2P_THREADS: threads (= particles) per G2P block, 64 to 512
+     in multiples of 32 (default 256);
+   MPM_BATCH_OPT_GRID_PARTICLES: a scene gets one grid-phase block per this
+     many particles (at least one; default 2048). */
+enum {
+  MPM_BATCH_OPT_GRAPHS = 1,
+  MPM_BATCH_OPT_P2G_CHUNK = 2,
+  MPM_BATCH_OPT_G2P_THREADS = 3,
+  MPM_BATCH_OPT_GRID_PARTICLES = 4
+};
+mpm_status mpm_batch_set_option(mpm_batch* batch, int32_t option, int64_t value);
+
+/* Message of the batch's last failure (never NULL). */
+const char* mpm_batch_last_error(const mpm_batch* batch);
+
+/* Free the batch's own memory (not the members). Synchronises. */
+void mpm_batch_destroy(mpm_batch* batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -723,4 +723,13 @@ __device__ __forceinline__ void contact_line_eval(const ContactLine& L, float al
   d2 = d2N * L.en * L.en + cs * (L.et2 - ute * ute * inv_s * inv_s);
 }
 
+// A batched launch's per-scene argument record, copied from global into
+// shared memory by all threads of the block (the caller then syncs).
+template <class T>
+__device__ __forceinline__ void load_args(const T* __restrict__ src, T& dst) {
+  static_assert(sizeof(T) % 4 == 0, "argument records are whole words");
+  for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x)
+    reinterpret_cast<int*>(&dst)[i] = reinterpret_cast<const int*>(src)[i];
+}
+
 }  // namespace mpmcr

@@ -17,9 +17,11 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__global__ void __launch_bounds__(kThreads, 4) k_g2p(G2PArgs a) {
+// Block `block` of G2P over one scene's particles, blockDim.x particles (a
+// thread block of the single-scene launch, or a work item of the batched one).
+__device__ __forceinline__ void g2p_block(const G2PArgs& a, int block) {
   const GridDev& g = a.g;
-  if (blockIdx.x == 0) {
+  if (block == 0) {
     if (threadIdx.x == 0) {
       const int count = *a.C.count;
       const int nc = count < a.C.cap ? count : a.C.cap;
@@ -34,7 +36,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_g2p(G2PArgs a) {
     }
     if (threadIdx.x <= 256 / kBarGroup) a.bar[kBarStride * threadIdx.x] = 0u;
   }
-  const int i = blockIdx.x * kThreads + threadIdx.x;
+  const int i = block * (int)blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const float xp[3] = {a.P.x(0)[i], a.P.x(1)[i], a.P.x(2)[i]};
   Stencil s;
@@ -91,11 +93,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_g2p(G2PArgs a) {
   for (int c = 0; c < 6; ++c) a.P.tau(c)[i] = tau[c];
 }
 
+__global__ void __launch_bounds__(kThreads, 4) k_g2p(G2PArgs a) { g2p_block(a, blockIdx.x); }
+
+// Batched: thread block b is block work[b].y of scene work[b].x
+__global__ void __launch_bounds__(512, 2) k_g2p_batch(const G2PArgs* __restrict__ args,
+                                                      const int2* __restrict__ work) {
+  __shared__ G2PArgs s_a;
+  const int2 wk = work[blockIdx.x];
+  load_args(args + wk.x, s_a);
+  __syncthreads();
+  g2p_block(s_a, wk.y);
+}
+
 }  // namespace
 
 void launch_g2p(const G2PArgs& a, cudaStream_t s) {
   const int blocks = a.n > 0 ? (a.n + kThreads - 1) / kThreads : 1;
   k_g2p<<<blocks, kThreads, 0, s>>>(a);
+}
+
+void launch_g2p_batch(const G2PArgs* args, const int2* work, int n_work, int threads,
+                      cudaStream_t s) {
+  if (n_work > 0) k_g2p_batch<<<n_work, threads, 0, s>>>(args, work);
 }
 
 }  // namespace mpmcr

@@ -11,14 +11,16 @@ namespace mpmcr {
 
 namespace {
 
-__global__ void k_compact(uint8_t* __restrict__ mark, int n_blocks, int* __restrict__ act,
-                          int* __restrict__ n_act) {
-  int lane = threadIdx.x & 31;
-  for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < n_blocks;
-       base += gridDim.x * blockDim.x) {
-    int b = base + lane;
-    bool on = b < n_blocks && mark[b] != 0;
-    unsigned m = __ballot_sync(0xffffffffu, on);
+// Compaction of one scene's block marks into its active-block list, the
+// threads striding by `stride` from `start` (taken warp-aligned).
+__device__ __forceinline__ void compact_range(uint8_t* __restrict__ mark, int start, int stride,
+                                              int n_blocks, int* __restrict__ act,
+                                              int* __restrict__ n_act) {
+  const int lane = threadIdx.x & 31;
+  for (int base = start & ~31; base < n_blocks; base += stride) {
+    const int b = base + lane;
+    const bool on = b < n_blocks && mark[b] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, on);
     if (m == 0u) continue;
     int slot0 = 0;
     if (lane == 0) slot0 = atomicAdd(n_act, __popc(m));
@@ -30,17 +32,25 @@ __global__ void k_compact(uint8_t* __restrict__ mark, int n_blocks, int* __restr
   }
 }
 
-__global__ void __launch_bounds__(256) k_grid_update(GridDev g, GridArrays G, float h,
-                                                     DevStats* stats) {
+__global__ void k_compact(uint8_t* __restrict__ mark, int n_blocks, int* __restrict__ act,
+                          int* __restrict__ n_act) {
+  compact_range(mark, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, n_blocks,
+                act, n_act);
+}
+
+// The grid update of nodes t = start, start + stride, ... of the active
+// blocks' nodes; `first`: the thread that records the active-block count.
+__device__ __forceinline__ void grid_update_range(const GridDev& g, const GridArrays& G, float h,
+                                                  DevStats* stats, long long start,
+                                                  long long stride, bool first) {
   const int n_act = *G.n_act;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (first) {
     atomicMax(&stats->active_blocks_max, n_act);
     stats->last_active = n_act;
   }
   const long long total = (long long)n_act * kBlockNodes;
   float p2 = 0.f;  // sum of m |v*|^2 over free nodes (the momentum norm of Alg. 1)
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = start; t < total; t += stride) {
     const int blk = G.act[t >> 6];
     const int cell = (int)(t & 63);
     const int node = blk * kBlockNodes + cell;
@@ -64,7 +74,7 @@ __global__ void __launch_bounds__(256) k_grid_update(GridDev g, GridArrays G, fl
     G.v[node] = make_float4(vs.x, vs.y, vs.z, wall ? 1.f : 0.f);
     G.vlo[node] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  __shared__ double s_p2[8];
+  __shared__ double s_p2[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) p2 += __shfl_xor_sync(0xffffffffu, p2, o);
   if ((threadIdx.x & 31) == 0) s_p2[threadIdx.x >> 5] = (double)p2;
@@ -76,6 +86,33 @@ __global__ void __launch_bounds__(256) k_grid_update(GridDev g, GridArrays G, fl
   }
 }
 
+__global__ void __launch_bounds__(256) k_grid_update(GridDev g, GridArrays G, float h,
+                                                     DevStats* stats) {
+  grid_update_range(g, G, h, stats, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                    (long long)gridDim.x * blockDim.x, blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+// Batched: thread block b is slice work[b].y of work[b].x's scene; a scene's
+// n_slices blocks stride together over its marks (compaction) or its active
+// nodes (update)
+__global__ void __launch_bounds__(256) k_compact_batch(const GridBatchArgs* __restrict__ args,
+                                                       const int2* __restrict__ work) {
+  const int2 wk = work[blockIdx.x];
+  const GridBatchArgs& a = args[wk.x];
+  compact_range(a.G.mark, wk.y * blockDim.x + threadIdx.x, a.n_slices * blockDim.x,
+                a.g.nbx * a.g.nby * a.g.nbz, a.G.act, a.G.n_act);
+}
+
+__global__ void __launch_bounds__(256) k_grid_update_batch(const GridBatchArgs* __restrict__ args,
+                                                           const int2* __restrict__ work) {
+  __shared__ GridBatchArgs s_a;
+  const int2 wk = work[blockIdx.x];
+  load_args(args + wk.x, s_a);
+  __syncthreads();
+  grid_update_range(s_a.g, s_a.G, s_a.h, s_a.stats, (long long)wk.y * blockDim.x + threadIdx.x,
+                    (long long)s_a.n_slices * blockDim.x, wk.y == 0 && threadIdx.x == 0);
+}
+
 }  // namespace
 
 void launch_grid(const GridDev& g, const GridArrays& G, float h, int num_sms, DevStats* stats,
@@ -85,6 +122,12 @@ void launch_grid(const GridDev& g, const GridArrays& G, float h, int num_sms, De
   cb = cb > num_sms * 8 ? num_sms * 8 : cb;
   k_compact<<<cb, 256, 0, s>>>(G.mark, n_blocks, G.act, G.n_act);
   k_grid_update<<<num_sms * 8, 256, 0, s>>>(g, G, h, stats);
+}
+
+void launch_grid_batch(const GridBatchArgs* args, const int2* work, int n_work, cudaStream_t s) {
+  if (n_work <= 0) return;
+  k_compact_batch<<<n_work, 256, 0, s>>>(args, work);
+  k_grid_update_batch<<<n_work, 256, 0, s>>>(args, work);
 }
 
 }  // namespace mpmcr

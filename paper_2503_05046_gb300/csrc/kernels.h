@@ -205,6 +205,24 @@ struct DevDyn {
 void launch_rigid_update(DevBody* bodies, const DevDyn* dyn, int nb, const double* imp,
                          const double* imp0, double dt, const double* gravity, cudaStream_t s);
 
+// batched: one block per scene, at the start of a batch step (statistics
+// cleared, imp0 = imp) and at its end (status and statistics gathered into
+// status_out and stats_out, then, if `rigid`, the bodies moved as above)
+struct RigidBatchArgs {
+  DevBody* bodies;
+  const DevDyn* dyn;
+  int nb;
+  int rigid;
+  const double* imp;
+  double* imp0;
+  DevStats* stats;
+  const uint32_t* status;
+  double gravity[3];
+};
+void launch_batch_begin(const RigidBatchArgs* args, int n_scenes, cudaStream_t s);
+void launch_batch_end(const RigidBatchArgs* args, int n_scenes, double dt, uint32_t* status_out,
+                      DevStats* stats_out, cudaStream_t s);
+
 // ---- g2p.cu: grid-to-particle with the constitutive update ----
 struct G2PArgs {
   GridDev g;
@@ -219,5 +237,24 @@ struct G2PArgs {
   DevStats* stats;
 };
 void launch_g2p(const G2PArgs& a, cudaStream_t s);
+
+// ---- batched launches: one per phase over many scenes' work items ----
+// work[b] = (scene, block index within the scene); args: per scene, device
+// memory. P2G blocks hold p2g_block_particles(chunk) particles, G2P blocks
+// `threads` (<= 512); the grid phases give each scene n_slices blocks.
+struct GridBatchArgs {
+  GridDev g;
+  GridArrays G;
+  float h;
+  int n_slices;
+  DevStats* stats;
+};
+int p2g_block_particles(int chunk);
+void launch_p2g_batch(const P2GArgs* args, const int2* work, int n_work, int chunk, cudaStream_t s);
+void launch_grid_batch(const GridBatchArgs* args, const int2* work, int n_work, cudaStream_t s);
+// one block per scene (its whole contact solve; SolveArgs.cluster_max = 0)
+void launch_solve_batch(const SolveArgs* args, int n_scenes, cudaStream_t s);
+void launch_g2p_batch(const G2PArgs* args, const int2* work, int n_work, int threads,
+                      cudaStream_t s);
 
 }  // namespace mpmcr

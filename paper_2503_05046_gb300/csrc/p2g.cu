@@ -30,14 +30,16 @@ constexpr int kWarpTileCap = 384;  // nodes per warp tile (6 KB)
 // dynamic shared memory: kWarps tiles of kWarpTileCap float4
 constexpr size_t kDynSmem = sizeof(float4) * kWarps * kWarpTileCap;
 
+// Block `block` of P2G over one scene's particles (a thread block of the
+// single-scene launch, or a work item of the batched one).
 template <int ITEMS>
-__global__ void __launch_bounds__(kThreads, 4) k_p2g(P2GArgs a) {
+__device__ __forceinline__ void p2g_block(const P2GArgs& a, int block) {
   extern __shared__ float4 s_tiles[];
   __shared__ DevBody s_body[kMaxBodies];
   const GridDev& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // this warp's particles: [first, first + 32 * ITEMS), lane-contiguous per item
-  const int first = (blockIdx.x * kWarps + warp) * 32 * ITEMS;
+  const int first = (block * kWarps + warp) * 32 * ITEMS;
   float4* tile = s_tiles + warp * kWarpTileCap;
 
   for (int i = tid; i < a.nb * (int)(sizeof(DevBody) / 4); i += kThreads)
@@ -303,6 +305,22 @@ __global__ void __launch_bounds__(kThreads, 4) k_p2g(P2GArgs a) {
 }
 
 template <int ITEMS>
+__global__ void __launch_bounds__(kThreads, 4) k_p2g(P2GArgs a) {
+  p2g_block<ITEMS>(a, blockIdx.x);
+}
+
+// Batched: thread block b is block work[b].y of scene work[b].x
+template <int ITEMS>
+__global__ void __launch_bounds__(kThreads, 4) k_p2g_batch(const P2GArgs* __restrict__ args,
+                                                           const int2* __restrict__ work) {
+  __shared__ P2GArgs s_a;
+  const int2 wk = work[blockIdx.x];
+  load_args(args + wk.x, s_a);
+  __syncthreads();
+  p2g_block<ITEMS>(s_a, wk.y);
+}
+
+template <int ITEMS>
 void launch_items(const P2GArgs& a, cudaStream_t s) {
   const int per_block = kThreads * ITEMS;
   k_p2g<ITEMS><<<(a.n + per_block - 1) / per_block, kThreads, kDynSmem, s>>>(a);
@@ -312,9 +330,14 @@ template <int ITEMS>
 cudaError_t prepare_items() {
   cudaError_t e = cudaFuncSetAttribute(k_p2g<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kDynSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_p2g_batch<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kDynSmem);
   if (e != cudaSuccess) return e;
   // room for four blocks' tiles per SM
-  return cudaFuncSetAttribute(k_p2g<ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute(k_p2g<ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_p2g_batch<ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 }  // namespace
@@ -324,6 +347,24 @@ cudaError_t p2g_prepare() {
   if (e == cudaSuccess) e = prepare_items<2>();
   if (e == cudaSuccess) e = prepare_items<4>();
   return e;
+}
+
+namespace {
+int items_of(int chunk) {
+  const int items = chunk / kThreads;
+  return items <= 1 ? 1 : items == 2 ? 2 : 4;
+}
+}  // namespace
+
+int p2g_block_particles(int chunk) { return items_of(chunk) * kThreads; }
+
+void launch_p2g_batch(const P2GArgs* args, const int2* work, int n_work, int chunk, cudaStream_t s) {
+  if (n_work <= 0) return;
+  switch (items_of(chunk)) {
+    case 1: k_p2g_batch<1><<<n_work, kThreads, kDynSmem, s>>>(args, work); break;
+    case 2: k_p2g_batch<2><<<n_work, kThreads, kDynSmem, s>>>(args, work); break;
+    default: k_p2g_batch<4><<<n_work, kThreads, kDynSmem, s>>>(args, work); break;
+  }
 }
 
 void launch_p2g(const P2GArgs& a, int chunk, cudaStream_t s) {

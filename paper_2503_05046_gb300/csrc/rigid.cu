@@ -13,6 +13,9 @@
 // (v+, w+). The 3x3 block is dense: lanes 0-8 form the world inertia's
 // entries, lanes 0-2 its cofactor rows, and the solve is shared through the
 // warp.
+//
+// A batch of scenes runs the update for all of them in one launch (one block
+// per scene, one warp per body), with the step's bookkeeping around it.
 #include "kernels.h"
 
 namespace mpmcr {
@@ -42,11 +45,10 @@ __device__ void rotate_left(const double (&ph)[3], double (&R)[9]) {
   for (int i = 0; i < 9; ++i) R[i] = O[i];
 }
 
-__global__ void k_rigid_update(DevBody* bodies, const DevDyn* dyn, int nb, const double* imp,
-                               const double* imp0, double dt, double gx, double gy, double gz) {
+// Body b's update by one warp.
+__device__ void rigid_update_warp(DevBody* bodies, const DevDyn* dyn, int b, const double* imp,
+                                  const double* imp0, double dt, double gx, double gy, double gz) {
   const int lane = threadIdx.x & 31;
-  const int b = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (b >= nb) return;
   const DevDyn d = dyn[b];
   if (d.kind == kRigidStatic) return;
   DevBody& B = bodies[b];
@@ -127,7 +129,46 @@ __global__ void k_rigid_update(DevBody* bodies, const DevDyn* dyn, int nb, const
   }
 }
 
+__global__ void k_rigid_update(DevBody* bodies, const DevDyn* dyn, int nb, const double* imp,
+                               const double* imp0, double dt, double gx, double gy, double gz) {
+  const int b = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (b < nb) rigid_update_warp(bodies, dyn, b, imp, imp0, dt, gx, gy, gz);
+}
+
+// Batched, block s for scene s: the step's start (its statistics cleared,
+// the impulse accumulator noted) ...
+__global__ void k_batch_begin(const RigidBatchArgs* __restrict__ args) {
+  const RigidBatchArgs& a = args[blockIdx.x];
+  for (int i = threadIdx.x; i < (int)(sizeof(DevStats) / 4); i += blockDim.x)
+    reinterpret_cast<int*>(a.stats)[i] = 0;
+  for (int i = threadIdx.x; i < 6 * a.nb; i += blockDim.x) a.imp0[i] = a.imp[i];
+}
+
+// ... and its end: one warp per body moves the bodies, and the scene's
+// status word and statistics are gathered into the batch's arrays
+__global__ void k_batch_end(const RigidBatchArgs* __restrict__ args, double dt,
+                            uint32_t* __restrict__ status_out, DevStats* __restrict__ stats_out) {
+  const RigidBatchArgs& a = args[blockIdx.x];
+  if (threadIdx.x == 0) status_out[blockIdx.x] = *a.status;
+  for (int i = threadIdx.x; i < (int)(sizeof(DevStats) / 4); i += blockDim.x)
+    reinterpret_cast<int*>(stats_out + blockIdx.x)[i] = reinterpret_cast<const int*>(a.stats)[i];
+  const int b = (int)(threadIdx.x >> 5);
+  if (a.rigid && b < a.nb)
+    rigid_update_warp(a.bodies, a.dyn, b, a.imp, a.imp0, dt, a.gravity[0], a.gravity[1],
+                      a.gravity[2]);
+}
+
 }  // namespace
+
+void launch_batch_begin(const RigidBatchArgs* args, int n_scenes, cudaStream_t s) {
+  if (n_scenes > 0) k_batch_begin<<<n_scenes, 128, 0, s>>>(args);
+}
+
+void launch_batch_end(const RigidBatchArgs* args, int n_scenes, double dt, uint32_t* status_out,
+                      DevStats* stats_out, cudaStream_t s) {
+  if (n_scenes > 0)
+    k_batch_end<<<n_scenes, 32 * kMaxBodies, 0, s>>>(args, dt, status_out, stats_out);
+}
 
 void launch_rigid_update(DevBody* bodies, const DevDyn* dyn, int nb, const double* imp,
                          const double* imp0, double dt, const double* gravity, cudaStream_t s) {

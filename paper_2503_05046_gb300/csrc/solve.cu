@@ -72,6 +72,7 @@ struct Barrier {
   int* poison;    // set on expiry: the next solve first clears the node scratch
   int cluster;    // nonzero: the blocks are one thread-block cluster
   unsigned extra; // arrivals awaited that never come (barrier time-limit test only)
+  unsigned blk;   // this block's index among the participating blocks
 };
 
 // Barrier of all threads of the thread-block cluster (hardware barrier; the
@@ -113,7 +114,7 @@ __device__ bool grid_sync(Barrier& B) {
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned g = blockIdx.x / kBarGroup;
+    const unsigned g = B.blk / kBarGroup;
     const unsigned gsize = min((unsigned)kBarGroup, B.n - g * kBarGroup);
     const unsigned top_n = (B.n + kBarGroup - 1) / kBarGroup + B.extra;
     __threadfence();
@@ -217,7 +218,7 @@ __device__ bool reduce_all(const float (&v)[NV], float2* part, Barrier& B, float
       else if (B.n == 1)
         s_tot[w] = df_norm(S, E);
       else
-        part[w * kMaxSolveBlocks + blockIdx.x] = df_norm(S, E);
+        part[w * kMaxSolveBlocks + B.blk] = df_norm(S, E);
     }
   }
   if (!grid_sync(B)) return false;
@@ -490,9 +491,11 @@ struct LineSearch {
 // kCluster: the solve of up to a.cluster_max contacts by the blocks of one
 // thread-block cluster (hardware cluster barriers, block sums exchanged
 // through distributed shared memory); otherwise the cooperative launch over
-// as many blocks as the contacts need, for more contacts than that.
+// as many blocks as the contacts need, for more contacts than that. `block`
+// is this block's index among the `grid_blocks` blocks of the solve (a
+// batched launch gives every scene one block of its own).
 template <bool kCluster>
-__global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
+__device__ __forceinline__ void solve_body(const SolveArgs& a, int block, int grid_blocks) {
   __shared__ DevBody s_body[kMaxBodies];
   __shared__ float2 s_cpart[4][kRedWidth];  // cluster: block sums, a ring of four reductions
   __shared__ float s_red[kWarps][kRedWidth];
@@ -510,12 +513,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   if (nc == 0) return;  // v = v* already (set by the grid update)
   // (every block of a launch reads the same count: the choice is uniform)
   if (kCluster ? nc > a.cluster_max : nc <= a.cluster_max) return;  // the other kernel's
-  int nblk = (int)gridDim.x;  // a cluster: all of its blocks
+  int nblk = grid_blocks;  // a cluster: all of its blocks
   if (!kCluster) {
     nblk = (nc + kContactsPerBlock - 1) / kContactsPerBlock;
-    nblk = nblk < (int)gridDim.x ? nblk : (int)gridDim.x;
+    nblk = nblk < grid_blocks ? nblk : grid_blocks;
     nblk = nblk < kMaxSolveBlocks ? nblk : kMaxSolveBlocks;
-    if ((int)blockIdx.x >= nblk) return;  // not needed for this many contacts
+    if (block >= nblk) return;  // not needed for this many contacts
   }
 
   for (int i = tid; i < a.nb * (int)(sizeof(DevBody) / 4); i += kThreads)
@@ -527,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   unsigned long long tph[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
   unsigned long long tmark = global_ns();
   auto lap = [&](int ph) {
-    if (blockIdx.x == 0 && tid == 0) {
+    if (block == 0 && tid == 0) {
       const unsigned long long now = global_ns();
       tph[ph] += now - tmark;
       tmark = now;
@@ -536,8 +539,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   // (wait_extra > 0 only in the test of the barrier's time limit: the
   // barrier then waits for arrivals that never come)
   Barrier B{a.bar, (unsigned)nblk, a.status, a.poison, kCluster ? 1 : 0,
-            kCluster ? 0u : (unsigned)a.wait_extra};
-  const int gtid = blockIdx.x * kThreads + tid;
+            kCluster ? 0u : (unsigned)a.wait_extra, (unsigned)block};
+  const int gtid = block * kThreads + tid;
   const int gstride = nblk * kThreads;
   const int lane = tid & 31;
   const int gwarp = gtid >> 5;
@@ -658,7 +661,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   // line search alone in each block (no grid barrier) or split over blocks
   const bool local_ls = kCluster ? nc <= kThreads : nc <= kLocalLsMax;
   const int ls_first = local_ls ? tid : gtid, ls_stride = local_ls ? kThreads : gstride;
-  Barrier Bl{nullptr, 1u, a.status, nullptr, 0, 0u};
+  Barrier Bl{nullptr, 1u, a.status, nullptr, 0, 0u, 0u};
   const float eps2 = a.eps_s * a.eps_s;
   float alpha = 0.f;
   int it = 0, ls_passes = 0;
@@ -831,12 +834,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
       resid = mx > 0.f ? Gn / mx : 0.f;
       int dec = 0;
       if (!(G2 == G2) || !(A.x == A.x) || !(Bs.x == Bs.x)) {
-        if (blockIdx.x == 0) atomicOr(a.status, kStNan);
+        if (block == 0) atomicOr(a.status, kStNan);
         dec = 1;
       } else if (Gn < eps_a + eps_r * mx || G2 == 0.f) {
         dec = 1;  // converged
       } else if (it >= a.max_iters) {
-        if (blockIdx.x == 0) atomicOr(a.status, kStNotConverged);
+        if (block == 0) atomicOr(a.status, kStNotConverged);
         dec = 1;
       }
       s_dec = dec;
@@ -921,7 +924,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
       if (tid < 32) {
         const int st = ls.update(s_tot, s_A, s_B, a.ls_rel_tol, pass + 1 >= a.ls_max_iters);
         if (tid == 0) {
-          if (st == LineSearch::kFailed && blockIdx.x == 0) atomicOr(a.status, kStLineSearch);
+          if (st == LineSearch::kFailed && block == 0) atomicOr(a.status, kStLineSearch);
           s_dec = st != LineSearch::kMore;
           s_alpha = ls.best;
         }
@@ -1003,6 +1006,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
     if (kCluster) atomicAdd(&a.stats->cluster, 1);
     atomicMax(reinterpret_cast<int*>(&a.stats->residual_max), __float_as_int(resid));
   }
+}
+
+template <bool kCluster>
+__global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
+  solve_body<kCluster>(a, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// Batched: block b solves scene b on its own (the scenes of a batch are
+// small: one block holds a scene's contacts, and its reductions need no
+// barrier beyond __syncthreads)
+__global__ void __launch_bounds__(kThreads, 1) k_solve_batch(const SolveArgs* __restrict__ args) {
+  __shared__ SolveArgs s_a;
+  load_args(args + blockIdx.x, s_a);
+  __syncthreads();
+  solve_body<false>(s_a, 0, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1272,7 +1290,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
     reinterpret_cast<float*>(s_body)[i] = reinterpret_cast<const float*>(a.bodies)[i];
   for (int i = tid; i < kMaxBodies * kAdjBodySlots; i += kThreads) (&s_bb[0][0])[i] = 0.0;
   __syncthreads();
-  Barrier B{a.bar, (unsigned)nblk, a.status, a.poison, 0, 0u};
+  Barrier B{a.bar, (unsigned)nblk, a.status, a.poison, 0, 0u, (unsigned)blockIdx.x};
   const int gtid = blockIdx.x * kThreads + tid;
   const int gstride = nblk * kThreads;
   const int lane = tid & 31;
@@ -1790,6 +1808,9 @@ cudaError_t solve_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_solve<true>),
                              cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_solve_batch),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_dynamic_smem());
   return e;
 }
 
@@ -1838,6 +1859,10 @@ cudaError_t launch_solve(const SolveArgs& a, int grid_blocks, int cluster_blocks
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_solve<false>),
                                      dim3(grid_blocks), dim3(kThreads), params,
                                      solve_dynamic_smem(), s);
+}
+
+void launch_solve_batch(const SolveArgs* args, int n_scenes, cudaStream_t s) {
+  if (n_scenes > 0) k_solve_batch<<<n_scenes, kThreads, solve_dynamic_smem(), s>>>(args);
 }
 
 const void* adjoint_kernel_ptr() { return reinterpret_cast<const void*>(&k_adjoint); }

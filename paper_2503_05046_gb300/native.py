@@ -28,6 +28,7 @@ OPT_PROFILE, OPT_SORT_EVERY, OPT_P2G_CHUNK, OPT_GRAPHS, OPT_SOLVE_BLOCKS = 1, 2,
 OPT_TAPE_SOLUTIONS = 7
 OPT_CLUSTER_CONTACTS = 8
 OPT_TEST_BARRIER_TIMEOUT = 6
+BATCH_OPT_GRAPHS, BATCH_OPT_P2G_CHUNK, BATCH_OPT_G2P_THREADS, BATCH_OPT_GRID_PARTICLES = 1, 2, 3, 4
 PHASES = ["sort", "p2g", "grid", "solve", "g2p"]
 
 
@@ -123,7 +124,16 @@ SIGNATURES = {
     "mpm_synchronize": [_vp],
     "mpm_set_option": [_vp, C.c_int32, C.c_int64],
     "mpm_get_phase_times": [_vp, _dp, _i64p, C.c_int32],
+    "mpm_batch_create": [C.POINTER(_vp), C.c_int32, C.POINTER(_vp)],
+    "mpm_batch_step": [_vp, C.c_double, C.c_int32, C.POINTER(SolverParams)],
+    "mpm_batch_sort": [_vp],
+    "mpm_batch_synchronize": [_vp, _i32p, C.POINTER(StepStats)],
+    "mpm_batch_set_option": [_vp, C.c_int32, C.c_int64],
+    "mpm_batch_last_error": [_vp],
+    "mpm_batch_destroy": [_vp],
 }
+_RESTYPES = {"mpm_last_error": C.c_char_p, "mpm_batch_last_error": C.c_char_p,
+             "mpm_batch_destroy": None}
 
 
 def load(path=LIB_PATH):
@@ -135,7 +145,7 @@ def load(path=LIB_PATH):
     for name, args in SIGNATURES.items():
         f = getattr(L, name)
         f.argtypes = args
-        f.restype = C.c_char_p if name == "mpm_last_error" else C.c_int
+        f.restype = _RESTYPES.get(name, C.c_int)
     return L
 
 
@@ -490,6 +500,11 @@ class Sim:
             except ImportError:  # torch is optional for the binding
                 stream = None
         self.ctx = mpm_create(spec, stream)
+        try:
+            import torch
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        except (ImportError, RuntimeError, AssertionError):
+            self.device = None
         for g in scene["groups"]:
             mpm_add_particles(self.ctx, np.asarray(g["x"], np.float32), np.asarray(g["v"], np.float32),
                               g["vol"], make_material(g["material"]))
@@ -532,6 +547,13 @@ class Sim:
 
     def set_particles(self, x=None, v=None, Cm=None, F=None):
         mpm_set_particles(self.ctx, x, v, Cm, F)
+
+    def read_particles(self, x=None, v=None, Cm=None, F=None):
+        """Fill the given arrays (numpy: host; CUDA tensors: device, all
+        alike) with the particle state in id order."""
+        given = [a for a in (x, v, Cm, F) if a is not None]
+        kind = MEM_HOST if not given or isinstance(given[0], np.ndarray) else MEM_DEVICE
+        mpm_get_particles(self.ctx, x, v, Cm, F, mem_kind=kind)
 
     def set_bodies(self, bodies):
         """Replace the bodies; like mpm_set_rigid_bodies this clears every
@@ -581,3 +603,93 @@ class Sim:
         last substep's contact solve for vbar = dL/dv (mpm_contact_adjoint)."""
         return mpm_contact_adjoint(self.ctx, node_ids, vbar, n_bodies=self.n_bodies, eps_r=eps_r,
                                    max_iters=max_iters, check=check)
+
+
+# ---------------------------------------------------------------- batches
+
+def _bcheck(batch, code):
+    if code != OK:
+        msg = lib.mpm_batch_last_error(batch)
+        raise MpmError(code, msg.decode() if msg else "")
+    return code
+
+
+def mpm_batch_create(ctxs):
+    arr = (_vp * len(ctxs))(*[c.value if isinstance(c, _vp) else c for c in ctxs])
+    out = _vp()
+    _check(None, lib.mpm_batch_create(arr, len(ctxs), C.byref(out)))
+    return out
+
+
+def mpm_batch_step(batch, h, n_substeps, solver=None):
+    return lib.mpm_batch_step(batch, float(h), int(n_substeps),
+                              C.byref(solver) if solver is not None else None)
+
+
+def mpm_batch_sort(batch):
+    return lib.mpm_batch_sort(batch)
+
+
+def mpm_batch_synchronize(batch, n, want_stats=True):
+    """(first failure code, per-member codes [n], per-member StepStats or None)."""
+    codes = np.zeros(max(n, 1), np.int32)
+    stats = (StepStats * max(n, 1))() if want_stats else None
+    code = lib.mpm_batch_synchronize(batch, codes.ctypes.data_as(_i32p), stats)
+    return code, codes[:n], ([stats[i] for i in range(n)] if want_stats else None)
+
+
+def mpm_batch_set_option(batch, option, value):
+    _bcheck(batch, lib.mpm_batch_set_option(batch, int(option), int(value)))
+
+
+def mpm_batch_destroy(batch):
+    lib.mpm_batch_destroy(batch)
+
+
+class Batch:
+    """Many scenes advanced together by mpm_batch_* (one launch per phase per
+    substep over all of them). The member contexts share one stream: the
+    batch creates its Sims itself on a stream of its own. Scenes must share h
+    and the substep count of a step."""
+
+    def __init__(self, scenes_, max_contacts=None):
+        import torch
+        self.torch_stream = torch.cuda.Stream()
+        stream = self.torch_stream.cuda_stream
+        self.sims = [Sim(sc, max_contacts=(max_contacts(sc) if callable(max_contacts)
+                                           else max_contacts), stream=stream)
+                     for sc in scenes_]
+        for sim in self.sims:
+            sim.torch_stream = self.torch_stream
+        self.batch = mpm_batch_create([sim.ctx for sim in self.sims])
+
+    def __len__(self):
+        return len(self.sims)
+
+    def step(self, h, n_substeps, solver=None):
+        _bcheck(self.batch, mpm_batch_step(self.batch, h, n_substeps, solver))
+
+    def sort(self):
+        _bcheck(self.batch, mpm_batch_sort(self.batch))
+
+    def synchronize(self, stats=True):
+        """(first failure code, per-member codes, per-member stats dicts)."""
+        code, codes, st = mpm_batch_synchronize(self.batch, len(self.sims), stats)
+        return code, codes, ([s.as_dict() for s in st] if st is not None else None)
+
+    def set_option(self, option, value):
+        mpm_batch_set_option(self.batch, option, value)
+
+    def close(self):
+        if getattr(self, "batch", None):
+            mpm_batch_destroy(self.batch)
+            self.batch = None
+        for sim in getattr(self, "sims", []):
+            sim.close()
+        self.sims = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,12 +1,18 @@
-"""Measured choice of launch options for many contexts stepped side by side.
+"""Measured choice of launch options for many scenes.
 
-Independent scenes advance concurrently, each on its own stream replaying its
-step's CUDA graph (mpm_step with graphs on). How well they share the GPU
-depends on two launch options: the cap on the SMs one context's cooperative
-contact solve occupies (MPM_OPT_SOLVE_BLOCKS) and the particles per P2G thread
-block (MPM_OPT_P2G_CHUNK). `tune_batch` times a few steps of the whole batch
-under each candidate pair and applies the fastest; the scenes advance while
-it measures (the timed steps are ordinary steps of the simulation).
+Two ways to advance many independent scenes, each tuned by timing a few
+steps of the whole set per candidate (the scenes advance while it measures:
+the timed steps are ordinary steps of the simulation):
+
+- a batch (native.Batch, mpm_batch_*): one launch per phase per substep over
+  all scenes' (scene, block) work items. `tune_batch_launch` picks the
+  particles per P2G warp tile (MPM_BATCH_OPT_P2G_CHUNK / 8 warps), the
+  threads per G2P block and the particles per grid-phase block, by
+  coordinate descent;
+- contexts side by side, each on its own stream replaying its step's CUDA
+  graph (mpm_step with graphs on). `tune_batch` picks the cap on the SMs one
+  context's cooperative contact solve occupies (MPM_OPT_SOLVE_BLOCKS) and the
+  particles per P2G thread block (MPM_OPT_P2G_CHUNK).
 """
 import time
 
@@ -45,3 +51,43 @@ def tune_batch(sims, scenes_, solver, caps=(2, 4, 8, 16), chunks=(256, 512), ste
     cap, chunk, _ = min(table, key=lambda r: r[2])
     apply(sims, cap, chunk)
     return (cap, chunk), table
+
+
+def _time_batch(batch, h, n_substeps, solver, steps):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        batch.step(h, n_substeps, solver)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
+def tune_batch_launch(batch, h, n_substeps, solver, steps=2, p2g_chunks=(256, 512, 1024),
+                      g2p_threads=(128, 256, 512), grid_particles=(512, 2048, 8192)):
+    """Coordinate descent over the batch's launch options: for each knob in
+    turn (P2G chunk, G2P threads, grid particles per block), time `steps`
+    steps per value after one untimed step (which records the step's graph
+    for the new work lists), keep the fastest. Applies and returns the best
+    options (dict option -> value) and the table of (options, seconds)."""
+    best = {native.BATCH_OPT_P2G_CHUNK: 256, native.BATCH_OPT_G2P_THREADS: 256,
+            native.BATCH_OPT_GRID_PARTICLES: 2048}
+    table = []
+    for knob, values in ((native.BATCH_OPT_P2G_CHUNK, p2g_chunks),
+                         (native.BATCH_OPT_G2P_THREADS, g2p_threads),
+                         (native.BATCH_OPT_GRID_PARTICLES, grid_particles)):
+        timed = []
+        for v in values:
+            cand = dict(best)
+            cand[knob] = int(v)
+            for opt, val in cand.items():
+                batch.set_option(opt, val)
+            _time_batch(batch, h, n_substeps, solver, 1)
+            t = _time_batch(batch, h, n_substeps, solver, steps)
+            timed.append((t, cand))
+            table.append((dict(cand), t))
+        best = min(timed, key=lambda r: r[0])[1]
+    for opt, val in best.items():
+        batch.set_option(opt, val)
+    batch.synchronize(stats=False)  # status of the tuning steps is not the measurement's
+    return best, table

@@ -71,6 +71,17 @@ def test_argument_validation_without_device(lib):
     assert native.lib.mpm_set_material(None, 0, None) == native.ERR_INVALID_ARG
     assert native.lib.mpm_destroy(None) == native.OK
     assert native.lib.mpm_last_error(None) == b"invalid mpm context"
+    # batches: bad handles and member lists are refused before any device work
+    assert native.lib.mpm_batch_create(None, 1, C.byref(out)) == native.ERR_INVALID_ARG
+    members = (C.c_void_p * 2)(None, None)
+    assert native.lib.mpm_batch_create(members, 2, C.byref(out)) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_batch_create(members, 0, C.byref(out)) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_batch_step(None, 1e-4, 1, None) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_batch_sort(None) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_batch_synchronize(None, None, None) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_batch_set_option(None, native.BATCH_OPT_GRAPHS, 1) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_batch_last_error(None) == b"invalid mpm batch"
+    native.lib.mpm_batch_destroy(None)
 
 
 def test_oracle_is_separate_from_the_cuda_library():
