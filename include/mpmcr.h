@@ -192,6 +192,9 @@ typedef struct {
   /* substeps whose contact solve ran in one thread-block cluster (at most
      MPM_OPT_CLUSTER_CONTACTS contacts) */
   int32_t cluster_substeps;
+  /* grid nodes in the stencil of at least one contact (the solve's DoFs), in
+     one substep */
+  int32_t contact_nodes_max;
 } mpm_step_stats;
 
 /* Create a context on the current CUDA device. `cuda_stream` is a

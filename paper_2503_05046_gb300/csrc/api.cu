@@ -1048,6 +1048,7 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
   stats->p2g_global_chunks = ds.p2g_global_chunks;
   stats->ls_split_substeps = ds.ls_split;
   stats->cluster_substeps = ds.cluster;
+  stats->contact_nodes_max = ds.cnodes_max;
   for (int k = 0; k < 5; ++k) stats->solve_us[k] = (float)(ds.solve_ns[k] * 1e-3);
   return st;
 }

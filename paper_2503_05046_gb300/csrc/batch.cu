@@ -420,6 +420,7 @@ mpm_status mpm_batch_synchronize(mpm_batch* batch, int32_t* status, mpm_step_sta
       o.p2g_global_chunks = d.p2g_global_chunks;
       o.ls_split_substeps = d.ls_split;
       o.cluster_substeps = d.cluster;
+      o.contact_nodes_max = d.cnodes_max;
       for (int k = 0; k < 5; ++k) o.solve_us[k] = (float)(d.solve_ns[k] * 1e-3);
     }
   }

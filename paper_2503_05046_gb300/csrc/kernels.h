@@ -31,6 +31,7 @@ struct DevStats {
   int last_active;       // active blocks of the last substep
   int ls_split;          // substeps whose line search was split over the solve's blocks
   int cluster;           // substeps solved by one thread-block cluster
+  int cnodes_max;        // contact nodes (the union of the contacts' stencils) in one substep
   // device time of the contact solve's phases (ns, block 0's view):
   // contact-node list, G, N, line search, impulses
   unsigned long long solve_ns[5];

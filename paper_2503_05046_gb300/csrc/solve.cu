@@ -1004,6 +1004,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, int block, int gr
     atomicAdd(&a.stats->ls_evals_total, ls_passes);
     if (!local_ls) atomicAdd(&a.stats->ls_split, 1);
     if (kCluster) atomicAdd(&a.stats->cluster, 1);
+    atomicMax(&a.stats->cnodes_max, ncn);
     atomicMax(reinterpret_cast<int*>(&a.stats->residual_max), __float_as_int(resid));
   }
 }

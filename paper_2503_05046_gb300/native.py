@@ -65,7 +65,8 @@ class StepStats(C.Structure):
                 ("active_blocks_max", C.c_int32), ("contacts_total", C.c_int64),
                 ("residual_max", C.c_double), ("status_bits", C.c_int32),
                 ("p2g_global_chunks", C.c_int32), ("solve_us", C.c_float * 5),
-                ("ls_split_substeps", C.c_int32), ("cluster_substeps", C.c_int32)]
+                ("ls_split_substeps", C.c_int32), ("cluster_substeps", C.c_int32),
+                ("contact_nodes_max", C.c_int32)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
