@@ -158,16 +158,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_launches_per_step(res, n_substeps):
+def kernel_launches_per_step(res, n_substeps, n_bodies=0):
     """Kernels one mpm_step launches: the radix sort (keys, five kernels per
-    8-bit digit pass, permutation) and per substep P2G, block compaction,
-    grid update, the two solve kernels (the cluster one and the cooperative
-    one, of which the contact count picks one to work) and G2P."""
+    8-bit digit pass, permutation), per substep P2G, block compaction, grid
+    update, the two solve kernels (the cluster one and the cooperative one,
+    of which the contact count picks one to work) and G2P, and with bodies
+    the rigid update after the substeps."""
     blocks = max(-(-int(r) // 4) for r in res)
     morton_bits = max((blocks - 1).bit_length(), 1)
     key_bits = 3 * morton_bits + (6 if 3 * morton_bits + 6 <= 32 else 0)
     passes = -(-key_bits // 8)
-    return (1 + 5 * passes + 1) + 6 * n_substeps
+    return (1 + 5 * passes + 1) + 6 * n_substeps + (1 if n_bodies > 0 else 0)
 
 
 def workload_name(sc):
@@ -289,7 +290,7 @@ def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
                       "p2g_global_chunks": st.p2g_global_chunks,
                       "status_timed": native.STATUS_NAMES[code_timed],
                       "solve_us_per_substep": [u / max(st.substeps, 1) for u in st.solve_us]},
-           "launches_per_step": kernel_launches_per_step(sc["grid"]["res"], N)}
+           "launches_per_step": kernel_launches_per_step(sc["grid"]["res"], N, len(sc["bodies"]))}
 
     peak, peak_kind = measured_peak_hbm()
     kern = {}
@@ -607,7 +608,14 @@ def differentiation(native, steps=20, eps_r=1e-4, fd=True):
         s2.close()
         return out
 
-    tight = differentiation_tight(native, sc, target) if fd else None
+    tight = None
+    if fd:
+        # the workload itself, and its lattice variant at the same size (40^3
+        # particles at 8 per cell, the outer layers 1e-5 m inside the ground
+        # and the box): no particle sits near a contact threshold there
+        sc_l, target_l = scenes.push_cube(lattice_side=40, sink=1e-5, box_overlap=1e-5)
+        tight = {"random": differentiation_tight(native, sc, target),
+                 "lattice": differentiation_tight(native, sc_l, target_l)}
     nan = float("nan")
     dE_fd = (loss_with(E_rel=1e-2) - loss_with(E_rel=-1e-2)) / (2e-2 * E) if fd else nan
     dv_fd = (loss_with(dvx=1e-3) - loss_with(dvx=-1e-3)) / 2e-3 if fd else nan
@@ -637,16 +645,29 @@ def differentiation_tight(native, sc, target, steps=2, eps_r=1e-6):
     substeps) with the contact solve at eps_r = 1e-6 and the adjoint's CG at
     1e-8: dL/dE and dL/dv0_x from mpm_backward against central differences
     of the CUDA forward at two step sizes each (their agreement with each
-    other bounds the truncation and noise of the differences). The scene keeps
-    its k = 1e3 N/m per contact: its particles are ~8x lighter than the 8k
-    cube's, and at 1e4 N/m the block-diagonal quasi-Newton iteration needs
-    ~3,000 iterations per substep for 1e-6."""
+    other bounds the truncation and noise of the differences). Two losses:
+    the workload's own (squared distance of the centroid to the target) and
+    the mean squared distance of each particle to its start position moved by
+    1 cm along +x, which sees the cube's deformation: the centroid barely
+    depends on E (a 1% change of E moves the centroid loss by ~2e-6 of itself,
+    the size of the FP32 forward's run-to-run differences), the per-particle
+    loss does. The scene keeps its k = 1e3 N/m per contact: its particles are
+    ~8x lighter than the 8k cube's, and at 1e4 N/m the block-diagonal
+    quasi-Newton iteration needs ~3,000 iterations per substep for 1e-6."""
     import torch
     from paper_2503_05046_gb300 import scenes
     n = scenes.n_particles(sc)
     N = sc["substeps"]
     solver = native.solver_params(eps_r=eps_r, eps_a=0.0, max_iters=200000)
     E = float(sc["groups"][0]["material"]["E"])
+
+    x_goal = (np.asarray(sc["groups"][0]["x"], np.float64) +
+              np.array([0.01, 0.0, 0.0]))  # per-particle loss target (id order)
+
+    def losses(x):
+        c = x.mean(0)
+        return (float(np.sum((c - target) ** 2)),
+                float(np.mean(np.sum((x - x_goal) ** 2, axis=1))), c)
 
     def rollout(scene, tape=False):
         s = native.Sim(scene)
@@ -660,40 +681,50 @@ def differentiation_tight(native, sc, target, steps=2, eps_r=1e-6):
             s.tape_end()
         code = native.mpm_synchronize(s.ctx)
         x = s.get_particles()["x"].astype(np.float64)
-        c = x.mean(0)
-        return s, float(np.sum((c - target) ** 2)), c, code, iters
+        return s, x, code, iters
 
-    def loss_with(E_rel=0.0, dvx=0.0):
+    def losses_with(E_rel=0.0, dvx=0.0):
         sc2 = dict(sc)
         g2 = dict(sc["groups"][0])
         g2["material"] = dict(g2["material"], E=E * (1.0 + E_rel))
         g2["v"] = g2["v"] + np.float32([dvx, 0.0, 0.0])
         sc2["groups"] = [g2]
-        s2, L2, _, _, _ = rollout(sc2)
+        s2, x2, _, _ = rollout(sc2)
         s2.close()
-        return L2
+        return losses(x2)[:2]
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim, L, c, code, iters = rollout(sc, tape=True)
-    xbar = np.tile((2.0 * (c - target) / n).astype(np.float32), (n, 1))
-    g = sim.backward(x_bar=xbar, eps_r=1e-8, max_iters=20000, check=False)
+    sim, x, code, iters = rollout(sc, tape=True)
+    L_c, L_p, c = losses(x)
+    bars = {"centroid": np.tile((2.0 * (c - target) / n).astype(np.float32), (n, 1)),
+            "per_particle": (2.0 * (x - x_goal) / n).astype(np.float32)}
+    adj = {}
+    status_bwd = []
+    for name, xbar in bars.items():
+        g = sim.backward(x_bar=xbar, eps_r=1e-8, max_iters=20000, check=False)
+        adj[name] = {"E": float(g["E"][0]), "v0_x": float(g["v"].astype(np.float64)[:, 0].sum())}
+        status_bwd.append(native.STATUS_NAMES[g["status"]])
     sim.close()
-    dE_adj = float(g["E"][0])
-    dv_adj = float(g["v"].astype(np.float64)[:, 0].sum())
-    out = {"workload": "push_cube_65536 shortened to %d steps x %d substeps" % (steps, N),
+    out = {"workload": "%s shortened to %d steps x %d substeps" % (sc["name"], steps, N),
            "eps_r": eps_r, "adjoint_cg_eps_r": 1e-8, "contact_k": sc["bodies"][0]["k"],
-           "qn_iters_per_substep": iters / float(steps * N), "loss": L,
-           "status_fwd": native.STATUS_NAMES[code], "status_bwd": native.STATUS_NAMES[g["status"]]}
-    for key, adj, steps_h, fn in (("E", dE_adj, (1e-2, 5e-3), lambda h: loss_with(E_rel=h)),
-                                  ("v0_x", dv_adj, (1e-3, 5e-4), lambda h: loss_with(dvx=h))):
-        rows = []
+           "qn_iters_per_substep": iters / float(steps * N),
+           "loss": {"centroid": L_c, "per_particle": L_p},
+           "status_fwd": native.STATUS_NAMES[code], "status_bwd": status_bwd}
+    for key, steps_h in (("E", (1e-2, 5e-3)), ("v0_x", (1e-3, 5e-4))):
+        scale = E if key == "E" else 1.0
+        rows = {"centroid": [], "per_particle": []}
         for h in steps_h:
-            scale = E if key == "E" else 1.0
-            fd_val = (fn(h) - fn(-h)) / (2.0 * h * scale)
-            rows.append({"h": h, "fd": fd_val,
-                         "rel_diff": abs(adj - fd_val) / max(abs(fd_val), 1e-300)})
-        out[key] = {"adjoint": adj, "central_differences": rows}
+            args_p = {"E_rel": h} if key == "E" else {"dvx": h}
+            args_m = {"E_rel": -h} if key == "E" else {"dvx": -h}
+            lp, lm = losses_with(**args_p), losses_with(**args_m)
+            for i, name in enumerate(("centroid", "per_particle")):
+                fd_val = (lp[i] - lm[i]) / (2.0 * h * scale)
+                a = adj[name][key]
+                rows[name].append({"h": h, "fd": fd_val,
+                                   "rel_diff": abs(a - fd_val) / max(abs(fd_val), 1e-300)})
+        out[key] = {name: {"adjoint": adj[name][key], "central_differences": rows[name]}
+                    for name in rows}
     torch.cuda.synchronize()
     out["seconds"] = time.perf_counter() - t0
     return out

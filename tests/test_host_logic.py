@@ -46,13 +46,14 @@ def test_single_rank_helpers_are_identities():
     assert bench.whole_job_value(10.0, 1, 2.0) == 5.0
 
 
-@pytest.mark.parametrize("res,n_sub,expected", [
-    ((128, 128, 128), 10, 1 + 5 * 3 + 1 + 60),  # 32 blocks per axis: 15 + 6 key bits, 3 passes
-    ((40, 16, 24), 1, 1 + 5 * 3 + 1 + 6),       # 10 blocks: 12 + 6 key bits, 3 passes
-    ((8, 8, 8), 2, 1 + 5 * 2 + 1 + 12),         # 2 blocks: 3 + 6 key bits, 2 passes
+@pytest.mark.parametrize("res,n_sub,nb,expected", [
+    ((128, 128, 128), 10, 7, 1 + 5 * 3 + 1 + 60 + 1),  # 32 blocks per axis: 15 + 6 key bits, 3 passes
+    ((320, 184, 64), 10, 12, 1 + 5 * 4 + 1 + 60 + 1),  # 80 blocks: 21 + 6 key bits, 4 passes
+    ((40, 16, 24), 1, 0, 1 + 5 * 3 + 1 + 6),           # 10 blocks: 12 + 6 key bits, 3 passes; no bodies
+    ((8, 8, 8), 2, 1, 1 + 5 * 2 + 1 + 12 + 1),         # 2 blocks: 3 + 6 key bits, 2 passes
 ])
-def test_kernel_launch_count(res, n_sub, expected):
-    assert bench.kernel_launches_per_step(res, n_sub) == expected
+def test_kernel_launch_count(res, n_sub, nb, expected):
+    assert bench.kernel_launches_per_step(res, n_sub, nb) == expected
 
 
 def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
