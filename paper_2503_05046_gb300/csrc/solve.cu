@@ -281,20 +281,6 @@ __device__ __forceinline__ LaneNode lane_node(const GridDev& g, const float4& xp
   return r;
 }
 
-// compensated warp sum of (S, E) pairs; the total is returned in every lane
-__device__ __forceinline__ float warp_comp_sum(float S, float E) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float S2 = __shfl_xor_sync(0xffffffffu, S, o);
-    const float E2 = __shfl_xor_sync(0xffffffffu, E, o);
-    float s, e;
-    two_sum(S, S2, s, e);
-    S = s;
-    E = E + E2 + e;
-  }
-  return S + E;
-}
-
 // Contact groups of the forward solve's gather / scatter phases: kGrp lanes
 // per contact, lane sub of a group owning stencil nodes sub, sub + kGrp, ...
 constexpr int kGrp = 4;
