@@ -80,10 +80,18 @@ enum { MPM_HALFSPACE = 0, MPM_SPHERE = 1, MPM_BOX = 2, MPM_CAPSULE = 3 };
 
 /* Eulerian grid (Sec. V-A). Node (i,j,k) sits at origin + dx*(i,j,k). The
    grid is block-sparse in time (only 4^3 blocks touched by particles are
-   swept) over a dense address space of res[0]*res[1]*res[2] nodes; each
+   swept) over an address space of res[0]*res[1]*res[2] < 2^31 nodes; each
    res[a] must be a positive multiple of 4. Nodes within bc_layers of a domain
    face are Dirichlet nodes held at zero velocity (the paper is silent on
-   domain walls; this is the reading taken). */
+   domain walls; this is the reading taken).
+   Storage: with max_blocks = 0 (or at least the domain's 4^3 blocks) every
+   block has its nodes (about 150 B per node). With 0 < max_blocks < blocks
+   the storage is block-sparse: only the blocks a substep's particle stencils
+   touch get nodes, from a pool of max_blocks blocks (plus 9 B per block of
+   the domain for the block table), so memory follows the active blocks, not
+   the domain. A substep that touches more blocks than the pool reports
+   MPM_ERR_CAPACITY (its results are then not valid). Batches take dense
+   contexts only. */
 typedef struct {
   double dx;
   int32_t res[3];
@@ -92,6 +100,7 @@ typedef struct {
   int32_t bc_layers;
   int64_t max_particles;  /* capacity of the context */
   int64_t max_contacts;   /* contact points per substep (Sec. V-B) */
+  int64_t max_blocks;     /* block-sparse pool (0: dense storage) */
 } mpm_grid_spec;
 
 /* Per particle group material. Lame parameters come from (E, nu);
@@ -524,7 +533,8 @@ mpm_status mpm_get_phase_times(mpm_ctx* ctx, double* ms, int64_t* launches, int3
 typedef struct mpm_batch mpm_batch;
 
 /* Create a batch of n >= 1 members. MPM_ERR_INVALID_ARG if a member is NULL,
-   repeated, on another device or stream, or recording a tape. */
+   repeated, on another device or stream, recording a tape, or block-sparse
+   (max_blocks). */
 mpm_status mpm_batch_create(mpm_ctx* const* ctxs, int32_t n, mpm_batch** out);
 
 /* One rigid time step of every member: n_substeps substeps of size h with

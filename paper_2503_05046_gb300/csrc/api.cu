@@ -65,11 +65,11 @@ __global__ void k_append(Particles P, int64_t offset, int64_t n, const float* __
 __global__ void k_grid_out(GridDev g, GridArrays G, int n_act, int* __restrict__ count,
                            int* __restrict__ ids, float* __restrict__ m, float* __restrict__ vs,
                            float* __restrict__ v) {
-  long long total = (long long)n_act * kBlockNodes;
+  long long total = (long long)active_with_storage(g, n_act) * kBlockNodes;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     int blk = G.act[t >> 6], cell = (int)(t & 63);
-    int node = blk * kBlockNodes + cell;
+    int node = active_storage_block(g, G.act, (int)(t >> 6)) * kBlockNodes + cell;
     float4 a = G.vs[node];
     if (!(a.w > 0.f)) continue;
     float4 b = G.v[node];
@@ -346,7 +346,7 @@ void release(mpm_ctx* c) {
                   c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage, c->adj_vec, c->adj_body,
                   c->adj_out, c->adj_ids, c->adj_io, c->bw_buf, c->bw_gbar, c->bw_slot, c->bw_mat,
                   c->tape_pool, c->tape_recs, c->tape_counters, c->bw_snap, c->bw_gbody, c->dyn_d,
-                  c->imp0_d, c->bodies_step_d};
+                  c->imp0_d, c->bodies_step_d, c->G.n_mapped, c->slot_d};
   for (auto& t : c->tape)
     if (t.state) cudaFree(t.state);
   for (void* p : ptrs)
@@ -376,12 +376,17 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
   pa.g = ctx->g; pa.P = ctx->P[cur]; pa.n = n; pa.groups = ctx->groups_d;
   pa.bodies = ctx->bodies_d; pa.nb = nb; pa.h = hf; pa.G = ctx->G; pa.C = ctx->C;
   pa.status = ctx->status; pa.stats = ctx->stats;
+  if (ctx->g.slot) {
+    // a block-sparse grid gives the substep's blocks storage before P2G
+    mark_phase(ctx, MPM_PHASE_GRID);
+    launch_sparse_map(ctx->g, ctx->G, ctx->P[cur], n, ctx->slot_d, ctx->status, ctx->num_sms, s);
+  }
   mark_phase(ctx, MPM_PHASE_P2G);
   launch_p2g(pa, ctx->p2g_chunk, s);
   mark_phase(ctx, MPM_PHASE_GRID);
   launch_grid(ctx->g, ctx->G, hf, ctx->num_sms, ctx->stats, s);
   if (warm_rec >= 0 && ctx->tape_pool)
-    launch_tape_warm(ctx->G, ctx->tape_recs, warm_rec, ctx->tape_pool, ctx->num_sms, s);
+    launch_tape_warm(ctx->g, ctx->G, ctx->tape_recs, warm_rec, ctx->tape_pool, ctx->num_sms, s);
   SolveArgs sa;
   sa.g = ctx->g; sa.G = ctx->G; sa.C = ctx->C; sa.bodies = ctx->bodies_d; sa.nb = nb;
   sa.h = hf; sa.eps_s = sp.eps_s; sa.ls_rel_tol = sp.ls_rel_tol; sa.ls_max_iters = sp.ls_max_iters;
@@ -394,7 +399,7 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
   const cudaError_t e = launch_solve(sa, solve_blocks, ctx->cluster_blocks, s);
   if (e != cudaSuccess) return e;
   if (save && ctx->tape_pool)
-    launch_tape_save(ctx->G, ctx->tape_counters, ctx->tape_recs, ctx->tape_rec_cap, ctx->tape_pool,
+    launch_tape_save(ctx->g, ctx->G, ctx->tape_counters, ctx->tape_recs, ctx->tape_rec_cap, ctx->tape_pool,
                      ctx->tape_pool_cap, ctx->num_sms, s);
   if (with_g2p) {
     G2PArgs ga;
@@ -517,6 +522,9 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
     return MPM_ERR_INVALID_ARG;
   for (int a = 0; a < 3; ++a)
     if (spec->res[a] <= 0 || spec->res[a] % 4 != 0 || spec->res[a] > 4096) return MPM_ERR_INVALID_ARG;
+  // node ids i + rx (j + ry k) are 32-bit
+  if ((int64_t)spec->res[0] * spec->res[1] * spec->res[2] >= (1LL << 31) || spec->max_blocks < 0)
+    return MPM_ERR_INVALID_ARG;
   ctx = new mpm_ctx();
   ctx->spec = *spec;
   cudaError_t e = cudaGetDevice(&ctx->device);
@@ -556,7 +564,12 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
   g.sort_cell_bits = 3 * g.morton_bits + 6 <= 32 ? 1 : 0;
   ctx->cap = spec->max_particles;
   ctx->n_blocks = g.nbx * g.nby * g.nbz;
-  ctx->n_nodes = (size_t)ctx->n_blocks * kBlockNodes;
+  // block-sparse storage for max_blocks active blocks (plus a spare one) when
+  // that is fewer than the domain's blocks; dense otherwise
+  const bool sparse = spec->max_blocks > 0 && spec->max_blocks < ctx->n_blocks;
+  g.slot = nullptr;
+  g.pool_blocks = sparse ? (int)spec->max_blocks : 0;
+  ctx->n_nodes = (size_t)(sparse ? g.pool_blocks + 1 : ctx->n_blocks) * kBlockNodes;
   const int64_t cap = ctx->cap;
   const int64_t ccap = spec->max_contacts;
   bool ok = true;
@@ -575,7 +588,13 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
        dalloc(&ctx->G.dv, nn) == cudaSuccess && dalloc(&ctx->G.mark, ctx->n_blocks) == cudaSuccess &&
        dalloc(&ctx->G.cflag, nn) == cudaSuccess && dalloc(&ctx->G.n_cnodes, 1) == cudaSuccess &&
        dalloc(&ctx->G.pstar2, 1) == cudaSuccess &&
-       dalloc(&ctx->G.act, ctx->n_blocks) == cudaSuccess && dalloc(&ctx->G.n_act, 1) == cudaSuccess;
+       dalloc(&ctx->G.act, ctx->n_blocks) == cudaSuccess && dalloc(&ctx->G.n_act, 1) == cudaSuccess &&
+       dalloc(&ctx->G.n_mapped, 1) == cudaSuccess;
+  if (ok && sparse) {
+    ok = dalloc(&ctx->slot_d, ctx->n_blocks) == cudaSuccess &&
+         cudaMemset(ctx->slot_d, 0xff, (size_t)ctx->n_blocks * sizeof(int)) == cudaSuccess;  // -1
+    g.slot = ctx->slot_d;
+  }
   ok = ok && dalloc(&ctx->C.xp, ccap) == cudaSuccess && dalloc(&ctx->C.nrm, ccap) == cudaSuccess &&
        dalloc(&ctx->C.bias, ccap) == cudaSuccess && dalloc(&ctx->C.id, ccap) == cudaSuccess &&
        dalloc(&ctx->C.vc, ccap) == cudaSuccess && dalloc(&ctx->C.dvc, ccap) == cudaSuccess &&
@@ -611,6 +630,7 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
        cudaMemset(ctx->G.v, 0, nn * sizeof(float4)) == cudaSuccess &&
        cudaMemset(ctx->G.mark, 0, ctx->n_blocks) == cudaSuccess &&
        cudaMemset(ctx->G.n_act, 0, sizeof(int)) == cudaSuccess &&
+       cudaMemset(ctx->G.n_mapped, 0, sizeof(int)) == cudaSuccess &&
        cudaMemset(ctx->C.count, 0, sizeof(int)) == cudaSuccess &&
        cudaMemset(ctx->red, 0, kRedDoubles * sizeof(double)) == cudaSuccess &&
        cudaMemset(ctx->G.cflag, 0, nn * sizeof(int)) == cudaSuccess &&
@@ -1720,11 +1740,11 @@ __global__ void k_grid_out_static(GridDev g, GridArrays G, int n_act, unsigned c
   float* m = reinterpret_cast<float*>(ids + kNoAllocMaxNodes);
   float* vs = m + kNoAllocMaxNodes;
   float* v = vs + 3 * kNoAllocMaxNodes;
-  const long long total = (long long)n_act * kBlockNodes;
+  const long long total = (long long)active_with_storage(g, n_act) * kBlockNodes;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int blk = G.act[t >> 6], cell = (int)(t & 63);
-    const int node = blk * kBlockNodes + cell;
+    const int node = active_storage_block(g, G.act, (int)(t >> 6)) * kBlockNodes + cell;
     const float4 a = G.vs[node];
     if (!(a.w > 0.f)) continue;
     const float4 b = G.v[node];

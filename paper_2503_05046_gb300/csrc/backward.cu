@@ -400,12 +400,12 @@ __global__ void __launch_bounds__(kThreads) k_g2p_adjoint(BackwardArgs a) {
 __global__ void __launch_bounds__(kThreads) k_grid_adjoint(BackwardArgs a) {
   const GridDev& g = a.g;
   const int n_act = *a.G.n_act;
-  const long long total = (long long)n_act * kBlockNodes;
+  const long long total = (long long)active_with_storage(g, n_act) * kBlockNodes;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int blk = a.G.act[t >> 6];
     const int cell = (int)(t & 63);
-    const int node = blk * kBlockNodes + cell;
+    const int node = active_storage_block(g, a.G.act, (int)(t >> 6)) * kBlockNodes + cell;
     const float4 vs = a.G.vs[node];
     const float4 gb = a.gbar[node];
     const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
@@ -641,24 +641,30 @@ __global__ void k_tape_alloc(GridArrays G, int* __restrict__ counters, int2* __r
   counters[1] = r + 1;
 }
 
-__global__ void k_tape_copy(GridArrays G, const int* __restrict__ counters, const int2* __restrict__ recs,
-                            int rec_cap, float4* __restrict__ pool) {
+// Records name nodes by grid block * 64 + cell, which a replayed substep of
+// a sparse grid maps to its own storage (the same blocks are active there).
+__global__ void k_tape_copy(GridDev g, GridArrays G, const int* __restrict__ counters,
+                            const int2* __restrict__ recs, int rec_cap, float4* __restrict__ pool) {
   const int r = counters[1] - 1;
   if (r >= rec_cap) return;
   const int2 rec = recs[r];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rec.y; t += gridDim.x * blockDim.x) {
     const int node = G.cnodes[t];
     const float4 v = G.v[node];
-    pool[rec.x + t] = make_float4(v.x, v.y, v.z, __int_as_float(node));
+    const int id = g.slot ? G.act[node >> 6] * kBlockNodes + (node & 63) : node;
+    pool[rec.x + t] = make_float4(v.x, v.y, v.z, __int_as_float(id));
   }
 }
 
-__global__ void k_tape_warm(GridArrays G, const int2* __restrict__ recs, int r,
+__global__ void k_tape_warm(GridDev g, GridArrays G, const int2* __restrict__ recs, int r,
                             const float4* __restrict__ pool) {
   const int2 rec = recs[r];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rec.y; t += gridDim.x * blockDim.x) {
     const float4 q = pool[rec.x + t];
-    float4* v = G.v + __float_as_int(q.w);
+    const int id = __float_as_int(q.w);
+    const int sb = g.slot ? g.slot[id >> 6] : id >> 6;
+    if (sb < 0) continue;  // (a block no longer active: not warm-started)
+    float4* v = G.v + sb * kBlockNodes + (id & 63);
     const float w = v->w;  // the Dirichlet flag of this substep's grid update
     *v = make_float4(q.x, q.y, q.z, w);
   }
@@ -725,15 +731,15 @@ void launch_reset_counters(const GridArrays& G, const Contacts& C, unsigned* bar
   k_reset_counters<<<1, 1, 0, s>>>(G, C, bar);
 }
 
-void launch_tape_save(const GridArrays& G, int* counters, int2* recs, int rec_cap, float4* pool,
+void launch_tape_save(const GridDev& g, const GridArrays& G, int* counters, int2* recs, int rec_cap, float4* pool,
                       int pool_cap, int num_sms, cudaStream_t s) {
   k_tape_alloc<<<1, 1, 0, s>>>(G, counters, recs, rec_cap, pool_cap);
-  k_tape_copy<<<num_sms, 256, 0, s>>>(G, counters, recs, rec_cap, pool);
+  k_tape_copy<<<num_sms, 256, 0, s>>>(g, G, counters, recs, rec_cap, pool);
 }
 
-void launch_tape_warm(const GridArrays& G, const int2* recs, int r, const float4* pool, int num_sms,
+void launch_tape_warm(const GridDev& g, const GridArrays& G, const int2* recs, int r, const float4* pool, int num_sms,
                       cudaStream_t s) {
-  k_tape_warm<<<num_sms, 256, 0, s>>>(G, recs, r, pool);
+  k_tape_warm<<<num_sms, 256, 0, s>>>(g, G, recs, r, pool);
 }
 
 void launch_slot_map(const Particles& P, int n, int* slot_of, cudaStream_t s) {

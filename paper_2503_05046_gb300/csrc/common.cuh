@@ -37,6 +37,12 @@ struct GridDev {
   int bc;                 // Dirichlet layers
   int morton_bits;        // bits per axis of the block sort key
   int sort_cell_bits;     // 1: the sort key also orders cells within a block
+  // Block-sparse storage (null: dense, every 4^3 block has its nodes at
+  // block * 64): slot[b] is the storage block of grid block b during a
+  // substep (-1: none), out of pool_blocks storage blocks plus one spare
+  // that takes the blocks beyond the pool (reported as a capacity error).
+  const int* slot;
+  int pool_blocks;
 };
 
 // Rigid body frozen for a time step (Eq. (3)-(4)); 32 words.
@@ -79,7 +85,7 @@ struct Particles {
 };
 constexpr int kParticlePlanes = 30;
 
-// Grid node arrays (dense, block-major).
+// Grid node arrays (block-major storage; see GridDev for the sparse pool).
 struct GridArrays {
   float4* mp;      // (m, p): P2G accumulator, all zero outside a substep
   float4* vs;      // (v*, m)
@@ -99,6 +105,7 @@ struct GridArrays {
   double* pstar2;  // sum over free nodes of m |v*|^2 (grid update), zero outside
   int* act;        // active block list
   int* n_act;      // its length (device)
+  int* n_mapped;   // sparse: the length of the list the slot table holds
 };
 
 // Contact points (Sec. V-B), structure of arrays.
@@ -161,9 +168,31 @@ struct CompSum {
   __device__ __forceinline__ float value() const { return S + E; }
 };
 
+// Storage index of node (i, j, k): its block's storage block (the block
+// itself when dense) times 64 plus the cell in the block. kDense: the caller
+// knows the grid is dense (no table lookup).
+template <bool kDense = false>
 __device__ __forceinline__ int node_index(const GridDev& g, int i, int j, int k) {
   int b = ((k >> 2) * g.nby + (j >> 2)) * g.nbx + (i >> 2);
+  if (!kDense && g.slot) b = g.slot[b];
   return b * kBlockNodes + ((k & 3) << 4) + ((j & 3) << 2) + (i & 3);
+}
+
+// Storage block of entry t of the active-block list: the list's order when
+// sparse (slot[act[t]] = t), the block itself when dense.
+__device__ __forceinline__ int active_storage_block(const GridDev& g, const int* act, int t) {
+  return g.slot ? t : act[t];
+}
+
+// Nodes of storage (all blocks when dense; the pool and its spare block when
+// sparse).
+__device__ __forceinline__ long long storage_nodes(const GridDev& g) {
+  return (long long)(g.slot ? g.pool_blocks + 1 : g.nbx * g.nby * g.nbz) * kBlockNodes;
+}
+
+// Active blocks that have storage (the pool caps a sparse grid's list).
+__device__ __forceinline__ int active_with_storage(const GridDev& g, int n_act) {
+  return g.slot && n_act > g.pool_blocks ? g.pool_blocks : n_act;
 }
 
 __device__ __forceinline__ uint32_t spread_bits3(uint32_t v) {

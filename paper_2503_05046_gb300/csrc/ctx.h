@@ -45,8 +45,9 @@ struct mpm_ctx {
   bool dyn_dirty = true;
   bool bodies_stale = false;  // the device moved the bodies since the host copy
   GridArrays G{};
-  size_t n_nodes = 0;
-  int n_blocks = 0;
+  size_t n_nodes = 0;   // nodes of storage
+  int n_blocks = 0;     // 4^3 blocks of the domain
+  int* slot_d = nullptr;  // block-sparse grids: block -> storage block (g.slot)
   Contacts C{};
   double* red = nullptr;
   unsigned* bar = nullptr;

@@ -19,6 +19,7 @@ constexpr int kThreads = 256;
 
 // Block `block` of G2P over one scene's particles, blockDim.x particles (a
 // thread block of the single-scene launch, or a work item of the batched one).
+template <bool kDense>
 __device__ __forceinline__ void g2p_block(const G2PArgs& a, int block) {
   const GridDev& g = a.g;
   if (block == 0) {
@@ -54,7 +55,8 @@ __device__ __forceinline__ void g2p_block(const G2PArgs& a, int block) {
       for (int cx = 0; cx < 3; ++cx) {
         const float dxp = (cx - s.fx[0]) * g.dx;
         const float w = s.w[0][cx] * wyz;
-        const float4 v = __ldg(a.G.v + node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz));
+        const float4 v =
+            __ldg(a.G.v + node_index<kDense>(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz));
         const float wx = w * v.x, wy = w * v.y, wz = w * v.z;
         vp[0] += wx; vp[1] += wy; vp[2] += wz;
         Bm[0] += wx * dxp; Bm[1] += wx * dy; Bm[2] += wx * dz;
@@ -93,7 +95,11 @@ __device__ __forceinline__ void g2p_block(const G2PArgs& a, int block) {
   for (int c = 0; c < 6; ++c) a.P.tau(c)[i] = tau[c];
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_g2p(G2PArgs a) { g2p_block(a, blockIdx.x); }
+// kDense: a dense grid's node addresses (no block-table lookup)
+template <bool kDense>
+__global__ void __launch_bounds__(kThreads, 4) k_g2p(G2PArgs a) {
+  g2p_block<kDense>(a, blockIdx.x);
+}
 
 // Batched: thread block b is block work[b].y of scene work[b].x
 __global__ void __launch_bounds__(512, 2) k_g2p_batch(const G2PArgs* __restrict__ args,
@@ -102,14 +108,17 @@ __global__ void __launch_bounds__(512, 2) k_g2p_batch(const G2PArgs* __restrict_
   const int2 wk = work[blockIdx.x];
   load_args(args + wk.x, s_a);
   __syncthreads();
-  g2p_block(s_a, wk.y);
+  g2p_block<true>(s_a, wk.y);  // (batches take dense grids)
 }
 
 }  // namespace
 
 void launch_g2p(const G2PArgs& a, cudaStream_t s) {
   const int blocks = a.n > 0 ? (a.n + kThreads - 1) / kThreads : 1;
-  k_g2p<<<blocks, kThreads, 0, s>>>(a);
+  if (a.g.slot)
+    k_g2p<false><<<blocks, kThreads, 0, s>>>(a);
+  else
+    k_g2p<true><<<blocks, kThreads, 0, s>>>(a);
 }
 
 void launch_g2p_batch(const G2PArgs* args, const int2* work, int n_work, int threads,

@@ -5,6 +5,13 @@
 // Only 4^3 blocks marked by P2G are swept. The update also clears the P2G
 // accumulator it consumed, so the accumulator is all zero between substeps
 // and no separate clearing pass is needed.
+//
+// A block-sparse grid (GridDev::slot) stores only the substep's active
+// blocks: before P2G the blocks of the particles' stencils are marked and
+// compacted, and entry t of the active list gets storage block t (the slot
+// table maps the grid block to it; the previous substep's entries are unmapped
+// first, so unmapped blocks read -1). Blocks beyond the pool share its spare
+// block and the substep reports a capacity error.
 #include "kernels.h"
 
 namespace mpmcr {
@@ -15,7 +22,9 @@ namespace {
 // threads striding by `stride` from `start` (taken warp-aligned).
 __device__ __forceinline__ void compact_range(uint8_t* __restrict__ mark, int start, int stride,
                                               int n_blocks, int* __restrict__ act,
-                                              int* __restrict__ n_act) {
+                                              int* __restrict__ n_act,
+                                              int* __restrict__ slot_tab = nullptr, int pool = 0,
+                                              uint32_t* __restrict__ status = nullptr) {
   const int lane = threadIdx.x & 31;
   for (int base = start & ~31; base < n_blocks; base += stride) {
     const int b = base + lane;
@@ -26,10 +35,44 @@ __device__ __forceinline__ void compact_range(uint8_t* __restrict__ mark, int st
     if (lane == 0) slot0 = atomicAdd(n_act, __popc(m));
     slot0 = __shfl_sync(0xffffffffu, slot0, 0);
     if (on) {
-      act[slot0 + __popc(m & ((1u << lane) - 1u))] = b;
+      const int t = slot0 + __popc(m & ((1u << lane) - 1u));
+      act[t] = b;
       mark[b] = 0;
+      if (slot_tab) {
+        slot_tab[b] = t < pool ? t : pool;  // beyond the pool: the spare block
+        if (t >= pool) atomicOr(status, kStCapacity);
+      }
     }
   }
+}
+
+// Sparse grids, before P2G: unmap the previous substep's blocks, then mark
+// the blocks of every particle's stencil (the nodes P2G, the solve and G2P
+// of this substep touch).
+__global__ void k_mark_sparse(GridDev g, Particles P, int n, uint8_t* __restrict__ mark,
+                              const int* __restrict__ act, const int* __restrict__ n_mapped,
+                              int* __restrict__ slot_tab) {
+  const int stride = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nm = *n_mapped;
+  for (int t = tid; t < nm; t += stride) slot_tab[act[t]] = -1;
+  for (int i = tid; i < n; i += stride) {
+    Stencil st;
+    stencil(g, P.x(0)[i], P.x(1)[i], P.x(2)[i], st);
+    if (!stencil_inside(g, st)) continue;  // reported by P2G
+    const int bx0 = st.base[0] >> 2, by0 = st.base[1] >> 2, bz0 = st.base[2] >> 2;
+    const int bx1 = (st.base[0] + 2) >> 2, by1 = (st.base[1] + 2) >> 2, bz1 = (st.base[2] + 2) >> 2;
+    for (int bz = bz0; bz <= bz1; ++bz)
+      for (int by = by0; by <= by1; ++by)
+        for (int bx = bx0; bx <= bx1; ++bx) mark[(bz * g.nby + by) * g.nbx + bx] = 1;
+  }
+}
+
+__global__ void k_compact_sparse(uint8_t* __restrict__ mark, int n_blocks, int* __restrict__ act,
+                                 int* __restrict__ n_act, int* __restrict__ slot_tab, int pool,
+                                 uint32_t* __restrict__ status) {
+  compact_range(mark, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, n_blocks,
+                act, n_act, slot_tab, pool, status);
 }
 
 __global__ void k_compact(uint8_t* __restrict__ mark, int n_blocks, int* __restrict__ act,
@@ -47,13 +90,14 @@ __device__ __forceinline__ void grid_update_range(const GridDev& g, const GridAr
   if (first) {
     atomicMax(&stats->active_blocks_max, n_act);
     stats->last_active = n_act;
+    if (g.slot) *G.n_mapped = n_act;  // the list the slot table now holds
   }
-  const long long total = (long long)n_act * kBlockNodes;
+  const long long total = (long long)active_with_storage(g, n_act) * kBlockNodes;
   float p2 = 0.f;  // sum of m |v*|^2 over free nodes (the momentum norm of Alg. 1)
   for (long long t = start; t < total; t += stride) {
     const int blk = G.act[t >> 6];
     const int cell = (int)(t & 63);
-    const int node = blk * kBlockNodes + cell;
+    const int node = active_storage_block(g, G.act, (int)(t >> 6)) * kBlockNodes + cell;
     const float4 mp = G.mp[node];
     float4 vs = make_float4(0.f, 0.f, 0.f, 0.f);
     const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
@@ -120,8 +164,21 @@ void launch_grid(const GridDev& g, const GridArrays& G, float h, int num_sms, De
   int n_blocks = g.nbx * g.nby * g.nbz;
   int cb = (n_blocks + 255) / 256;
   cb = cb > num_sms * 8 ? num_sms * 8 : cb;
-  k_compact<<<cb, 256, 0, s>>>(G.mark, n_blocks, G.act, G.n_act);
+  // (a sparse grid compacted its marks before P2G)
+  if (!g.slot) k_compact<<<cb, 256, 0, s>>>(G.mark, n_blocks, G.act, G.n_act);
   k_grid_update<<<num_sms * 8, 256, 0, s>>>(g, G, h, stats);
+}
+
+void launch_sparse_map(const GridDev& g, const GridArrays& G, const Particles& P, int n,
+                       int* slot_tab, uint32_t* status, int num_sms, cudaStream_t s) {
+  const int n_blocks = g.nbx * g.nby * g.nbz;
+  const int pb = (n + 255) / 256;
+  k_mark_sparse<<<pb < num_sms * 8 ? (pb > 0 ? pb : 1) : num_sms * 8, 256, 0, s>>>(
+      g, P, n, G.mark, G.act, G.n_mapped, slot_tab);
+  int cb = (n_blocks + 255) / 256;
+  cb = cb > num_sms * 8 ? num_sms * 8 : cb;
+  k_compact_sparse<<<cb, 256, 0, s>>>(G.mark, n_blocks, G.act, G.n_act, slot_tab, g.pool_blocks,
+                                      status);
 }
 
 void launch_grid_batch(const GridBatchArgs* args, const int2* work, int n_work, cudaStream_t s) {

@@ -78,6 +78,10 @@ cudaError_t p2g_prepare();  // once per device: the kernel's shared-memory attri
 // ---- grid.cu: active-block compaction and grid update ----
 void launch_grid(const GridDev& g, const GridArrays& G, float h, int num_sms, DevStats* stats,
                  cudaStream_t s);
+// block-sparse grids, before P2G: the substep's blocks marked from the
+// particles' stencils, compacted and given storage (slot_tab = g.slot)
+void launch_sparse_map(const GridDev& g, const GridArrays& G, const Particles& P, int n,
+                       int* slot_tab, uint32_t* status, int num_sms, cudaStream_t s);
 
 // ---- solve.cu: quasi-Newton contact solve (Alg. 1) in one cooperative launch ----
 struct SolveArgs {
@@ -181,9 +185,9 @@ void launch_reset_counters(const GridArrays& G, const Contacts& C, unsigned* bar
 void launch_slot_map(const Particles& P, int n, int* slot_of, cudaStream_t s);
 // taped solutions: append the contact-node velocities after a solve (counters:
 // [0] pool fill, [1] records written); scatter record r over v*
-void launch_tape_save(const GridArrays& G, int* counters, int2* recs, int rec_cap, float4* pool,
+void launch_tape_save(const GridDev& g, const GridArrays& G, int* counters, int2* recs, int rec_cap, float4* pool,
                       int pool_cap, int num_sms, cudaStream_t s);
-void launch_tape_warm(const GridArrays& G, const int2* recs, int r, const float4* pool, int num_sms,
+void launch_tape_warm(const GridDev& g, const GridArrays& G, const int2* recs, int r, const float4* pool, int num_sms,
                       cudaStream_t s);
 void launch_bar_in(const Particles& P, int n, const float* x, const float* v, const float* C,
                    const float* F, float* bar, cudaStream_t s);

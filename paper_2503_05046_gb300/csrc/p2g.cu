@@ -222,17 +222,20 @@ __device__ __forceinline__ void p2g_block(const P2GArgs& a, int block) {
           }
         }
       }
-      // mark the (up to 8) blocks of this stencil
+      // mark the (up to 8) blocks of this stencil (a sparse grid marked them
+      // before P2G)
+      if (!g.slot) {
 #pragma unroll
-      for (int cz = 0; cz < 2; ++cz)
+        for (int cz = 0; cz < 2; ++cz)
 #pragma unroll
-        for (int cy = 0; cy < 2; ++cy)
+          for (int cy = 0; cy < 2; ++cy)
 #pragma unroll
-          for (int cx = 0; cx < 2; ++cx) {
-            const int bi = (s.base[0] + 2 * cx) >> 2, bj = (s.base[1] + 2 * cy) >> 2,
-                      bk = (s.base[2] + 2 * cz) >> 2;
-            a.G.mark[(bk * g.nby + bj) * g.nbx + bi] = 1;
-          }
+            for (int cx = 0; cx < 2; ++cx) {
+              const int bi = (s.base[0] + 2 * cx) >> 2, bj = (s.base[1] + 2 * cy) >> 2,
+                        bk = (s.base[2] + 2 * cz) >> 2;
+              a.G.mark[(bk * g.nby + bj) * g.nbx + bi] = 1;
+            }
+      }
     }
     // contact registration: warp-aggregated append, one contact per
     // (particle, body) pair with the particle strictly inside
@@ -294,7 +297,9 @@ __device__ __forceinline__ void p2g_block(const P2GArgs& a, int block) {
       red_add_v4(a.G.mp + node, q.x, q.y, q.z, q.w);
     }
   }
-  // mark the 4^3 blocks the tile overlaps
+  // mark the 4^3 blocks the tile overlaps (a sparse grid marked its blocks
+  // before P2G)
+  if (g.slot) return;
   const int bx0 = lo[0] >> 2, by0 = lo[1] >> 2, bz0 = lo[2] >> 2;
   const int bnx = ((lo[0] + ex - 1) >> 2) - bx0 + 1, bny = ((lo[1] + ey - 1) >> 2) - by0 + 1,
             bnz = ((lo[2] + ez - 1) >> 2) - bz0 + 1;

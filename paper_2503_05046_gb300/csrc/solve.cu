@@ -548,7 +548,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, int block, int gr
   // a solve that gave up at a barrier left node flags and gradient
   // accumulators behind: clear them over the whole grid first
   if (__ldcg(a.poison)) {
-    const size_t n_nodes = (size_t)g.nbx * g.nby * g.nbz * kBlockNodes;
+    const size_t n_nodes = (size_t)storage_nodes(g);
     for (size_t t = gtid; t < n_nodes; t += gstride) {
       a.G.cflag[t] = 0;
       a.G.acc0[t] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1307,7 +1307,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
   auto node_of_id = [&](int id) -> int {
     if (id < 0 || id >= n_nodes_total) return -1;
     const int i = id % g.rx, j = (id / g.rx) % g.ry, k = id / (g.rx * g.ry);
-    return node_index(g, i, j, k);
+    const int node = node_index(g, i, j, k);  // negative: a sparse grid's unmapped block
+    return node < 0 ? -1 : node;
   };
   auto list_pos = [&](const LaneNode& ln) -> int {
     return lane < 27 ? __ldcg(a.G.cflag + ln.node) - 1 : -1;
@@ -1315,7 +1316,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_adjoint(AdjointArgs a) {
 
   // a solve that gave up at a barrier left node flags and accumulators behind
   if (__ldcg(a.poison)) {
-    const size_t n_nodes = (size_t)g.nbx * g.nby * g.nbz * kBlockNodes;
+    const size_t n_nodes = (size_t)storage_nodes(g);
     for (size_t t = gtid; t < n_nodes; t += gstride) {
       a.G.cflag[t] = 0;
       a.G.acc0[t] = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -35,7 +35,8 @@ PHASES = ["sort", "p2g", "grid", "solve", "g2p"]
 class GridSpec(C.Structure):
     _fields_ = [("dx", C.c_double), ("res", C.c_int32 * 3), ("origin", C.c_double * 3),
                 ("gravity", C.c_double * 3), ("bc_layers", C.c_int32),
-                ("max_particles", C.c_int64), ("max_contacts", C.c_int64)]
+                ("max_particles", C.c_int64), ("max_contacts", C.c_int64),
+                ("max_blocks", C.c_int64)]
 
 
 class Material(C.Structure):
@@ -438,6 +439,7 @@ def grid_spec(grid, max_particles, max_contacts):
     s.bc_layers = int(grid.get("bc_layers", 3))
     s.max_particles = int(max_particles)
     s.max_contacts = int(max_contacts)
+    s.max_blocks = int(grid.get("max_blocks", 0))  # block-sparse pool (0: dense)
     return s
 
 

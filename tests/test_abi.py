@@ -58,6 +58,12 @@ def test_argument_validation_without_device(lib):
     spec.dx = -1.0
     assert native.lib.mpm_create(C.byref(spec), None, C.byref(out)) == native.ERR_INVALID_ARG
     assert native.lib.mpm_create(None, None, C.byref(out)) == native.ERR_INVALID_ARG
+    spec.dx = 0.01
+    spec.max_blocks = -1  # block-sparse pool
+    assert native.lib.mpm_create(C.byref(spec), None, C.byref(out)) == native.ERR_INVALID_ARG
+    spec.max_blocks = 0
+    spec.res[0], spec.res[1], spec.res[2] = 2048, 2048, 1024  # 2^32 nodes: ids overflow 32 bits
+    assert native.lib.mpm_create(C.byref(spec), None, C.byref(out)) == native.ERR_INVALID_ARG
     assert native.lib.mpm_num_particles(None, None) == native.ERR_INVALID_ARG
     assert native.lib.mpm_step(None, 1e-4, 1, None, None) == native.ERR_INVALID_ARG
     assert native.lib.mpm_set_rigid_dynamics(None, 0, None) == native.ERR_INVALID_ARG

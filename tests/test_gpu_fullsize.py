@@ -2,7 +2,8 @@
 every step, default P2G chunk): the benchmark workload (granular scooping, 1M
 sand particles, 128^3 grid) and the mixed-material manipulation workload (4M
 particles in 32 elastic and sand objects, 12 rigid bodies, 320 x 184 x 64
-grid), each from a state a few rigid steps into the scene:
+grid), each with dense and with block-sparse grid storage, from a state a few
+rigid steps into the scene:
 
 1. one substep of P2G + grid update + G2P for every particle and node, against
    the FP64 oracle from the same float32 state (rigid bodies removed, so no
@@ -27,9 +28,19 @@ BENCH_SOLVER = dict(eps_r=5e-2, max_iters=1000)
 TIGHT_SOLVER = dict(eps_r=1e-6, eps_a=0.0, max_iters=200000, ls_rel_tol=1e-5, ls_max_iters=50)
 
 
+def _sparse(sc, max_blocks):
+    sc["grid"] = dict(sc["grid"], max_blocks=max_blocks)
+    return sc
+
+
+# the sparse variants store only the active blocks (~17,600 of 32,768 and
+# ~15,000 of 58,880) in a pool of 20,000
 WORKLOADS = {
     "granular_scoop_1M": (lambda: scenes.granular_scoop(n_particles=N_FULL), 2),
     "mixed_manipulation_4M": (lambda: scenes.mixed_manipulation(), 1),
+    "granular_scoop_1M_sparse":
+        (lambda: _sparse(scenes.granular_scoop(n_particles=N_FULL), 20000), 2),
+    "mixed_manipulation_4M_sparse": (lambda: _sparse(scenes.mixed_manipulation(), 20000), 1),
 }
 
 
