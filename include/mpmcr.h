@@ -479,7 +479,10 @@ mpm_status mpm_synchronize(mpm_ctx* ctx);
    solved by one thread-block cluster (up to 16 SMs exchanging their sums
    through distributed shared memory, hardware cluster barriers); more
    contacts go to the cooperative launch over as many SMs as they need, with
-   device-wide barriers (default 4096; 0: always the cooperative launch). */
+   device-wide barriers (default 4096; 0: always the cooperative launch).
+   MPM_OPT_CLUSTER_BLOCKS: thread blocks (SMs) in that cluster, a power of two
+   up to the largest the device schedules (0, the default: the largest, 16 on
+   GB300). */
 enum {
   MPM_OPT_PROFILE = 1,
   MPM_OPT_SORT_EVERY = 2,
@@ -488,7 +491,8 @@ enum {
   MPM_OPT_SOLVE_BLOCKS = 5,
   MPM_OPT_TEST_BARRIER_TIMEOUT = 6,
   MPM_OPT_TAPE_SOLUTIONS = 7,
-  MPM_OPT_CLUSTER_CONTACTS = 8
+  MPM_OPT_CLUSTER_CONTACTS = 8,
+  MPM_OPT_CLUSTER_BLOCKS = 9
 };
 mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value);
 

@@ -652,6 +652,7 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
     return bail(MPM_ERR_CUDA);
   ctx->solve_blocks = ctx->num_sms * (occ < 2 ? occ : 2);
   ctx->cluster_blocks = solve_cluster_blocks();
+  ctx->cluster_blocks_max = ctx->cluster_blocks;
   *out = ctx;
   return MPM_OK;
 }
@@ -957,6 +958,7 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     k.n = n; k.n_substeps = n_substeps; k.nb = nb; k.chunk = ctx->p2g_chunk;
     k.sort_now = sort_now ? 1 : 0; k.solve_blocks = solve_blocks; k.h = hf; k.sp = sp;
     k.cluster_max = cluster_contacts(ctx);
+    k.cluster_blocks = ctx->cluster_blocks;
     k.rigid = dev_rigid ? 1 : 0;
     k.taping = ctx->taping && ctx->tape_pool ? 1 : 0;
     k.tape_pool = ctx->tape_pool;
@@ -964,7 +966,8 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     const bool same = ctx->gexec[from] && o.n == k.n && o.n_substeps == k.n_substeps && o.nb == k.nb &&
                       o.chunk == k.chunk && o.sort_now == k.sort_now &&
                       o.solve_blocks == k.solve_blocks && o.h == k.h && o.taping == k.taping &&
-                      o.cluster_max == k.cluster_max && o.rigid == k.rigid &&
+                      o.cluster_max == k.cluster_max && o.cluster_blocks == k.cluster_blocks &&
+                      o.rigid == k.rigid &&
                       o.tape_pool == k.tape_pool &&
                       memcmp(&o.sp, &k.sp, sizeof(k.sp)) == 0;
     if (!same) {
@@ -1686,6 +1689,12 @@ mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value) {
       if (value < 0 || value > (1 << 24))
         return fail(ctx, MPM_ERR_INVALID_ARG, "cluster contact limit must be 0 .. 2^24");
       ctx->cluster_max = (int)value;
+      return MPM_OK;
+    case MPM_OPT_CLUSTER_BLOCKS:
+      if (value < 0 || value > ctx->cluster_blocks_max || (value & (value - 1)) != 0)
+        return fail(ctx, MPM_ERR_INVALID_ARG,
+                    "cluster blocks must be 0 or a power of two up to the device's largest cluster");
+      ctx->cluster_blocks = value == 0 ? ctx->cluster_blocks_max : (int)value;
       return MPM_OK;
     case MPM_OPT_SOLVE_BLOCKS:
       if (value < 0) return fail(ctx, MPM_ERR_INVALID_ARG, "solve block cap must be >= 0");

@@ -19,6 +19,7 @@ struct mpm_ctx {
   int64_t cap = 0, n = 0;
   int num_sms = 0, solve_blocks = 0;
   int cluster_blocks = 0;     // blocks of the cluster solve (0: the device runs none)
+  int cluster_blocks_max = 0; // the largest cluster the device schedules
   int cluster_max = 4096;     // MPM_OPT_CLUSTER_CONTACTS
   float* pbuf[2] = {nullptr, nullptr};
   uint32_t* pidbuf[2] = {nullptr, nullptr};
@@ -66,6 +67,7 @@ struct mpm_ctx {
     int64_t n = -1;
     int n_substeps = 0, nb = 0, chunk = 0, sort_now = 0, solve_blocks = 0, taping = 0;
     int cluster_max = 0;
+    int cluster_blocks = 0;
     int rigid = 0;
     const void* tape_pool = nullptr;  // baked into the launches when taping
     float h = 0.f;
