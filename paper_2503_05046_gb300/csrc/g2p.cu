@@ -43,7 +43,18 @@ __device__ __forceinline__ void g2p_block(const G2PArgs& a, int block) {
   Stencil s;
   stencil(g, xp[0], xp[1], xp[2], s);
   if (!stencil_inside(g, s)) return;  // reported by P2G
+  // dense node address = ax[cx] + ay[cy] + az[cz] (block-major: each axis
+  // contributes its block and its cell within the block)
+  int ax[3], ay[3], az[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int ix = s.base[0] + c, iy = s.base[1] + c, iz = s.base[2] + c;
+    ax[c] = (ix >> 2) * kBlockNodes + (ix & 3);
+    ay[c] = (iy >> 2) * (g.nbx * kBlockNodes) + ((iy & 3) << 2);
+    az[c] = (iz >> 2) * (g.nbx * g.nby * kBlockNodes) + ((iz & 3) << 4);
+  }
   float vp[3] = {0.f, 0.f, 0.f}, Bm[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const float dx0[3] = {(0.f - s.fx[0]) * g.dx, (1.f - s.fx[0]) * g.dx, (2.f - s.fx[0]) * g.dx};
 #pragma unroll
   for (int cz = 0; cz < 3; ++cz) {
     const float dz = (cz - s.fx[2]) * g.dx;
@@ -51,17 +62,27 @@ __device__ __forceinline__ void g2p_block(const G2PArgs& a, int block) {
     for (int cy = 0; cy < 3; ++cy) {
       const float dy = (cy - s.fx[1]) * g.dx;
       const float wyz = s.w[1][cy] * s.w[2][cz];
+      // the row's sums of w v and of w v (x_i - x_p), then its dy, dz terms
+      float S[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
 #pragma unroll
       for (int cx = 0; cx < 3; ++cx) {
-        const float dxp = (cx - s.fx[0]) * g.dx;
         const float w = s.w[0][cx] * wyz;
-        const float4 v =
-            __ldg(a.G.v + node_index<kDense>(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz));
-        const float wx = w * v.x, wy = w * v.y, wz = w * v.z;
-        vp[0] += wx; vp[1] += wy; vp[2] += wz;
-        Bm[0] += wx * dxp; Bm[1] += wx * dy; Bm[2] += wx * dz;
-        Bm[3] += wy * dxp; Bm[4] += wy * dy; Bm[5] += wy * dz;
-        Bm[6] += wz * dxp; Bm[7] += wz * dy; Bm[8] += wz * dz;
+        const int node = kDense ? az[cz] + ay[cy] + ax[cx]
+                                : node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz);
+        const float4 v = __ldg(a.G.v + node);
+        const float wv[3] = {w * v.x, w * v.y, w * v.z};
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          S[r] += wv[r];
+          T[r] = fmaf(wv[r], dx0[cx], T[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        vp[r] += S[r];
+        Bm[3 * r] += T[r];
+        Bm[3 * r + 1] = fmaf(S[r], dy, Bm[3 * r + 1]);
+        Bm[3 * r + 2] = fmaf(S[r], dz, Bm[3 * r + 2]);
       }
     }
   }
