@@ -509,7 +509,8 @@ def batched_throughput(native, n_scenes=256, steps=3, warmup=2):
     v_conc = n_scenes * steps / t_conc
     v_loop = n_scenes * steps / t_loop
     names = {native.BATCH_OPT_P2G_CHUNK: "p2g_chunk", native.BATCH_OPT_G2P_THREADS: "g2p_threads",
-             native.BATCH_OPT_GRID_PARTICLES: "grid_particles_per_block"}
+             native.BATCH_OPT_GRID_PARTICLES: "grid_particles_per_block",
+             native.BATCH_OPT_SOLVE_BLOCKS: "solve_blocks_per_scene"}
     return {"scenes": n_scenes, "particles": n_total, "steps": steps, "substeps_per_step": N,
             "value": v_persist, "unit": "scene-steps/s",
             "particle_substeps_per_s": n_total * N * steps / t_persist,

@@ -520,7 +520,8 @@ mpm_status mpm_get_phase_times(mpm_ctx* ctx, double* ms, int64_t* launches, int3
    the start and one at the end of the time step (the latter moves every
    scene's bodies on the device as mpm_step does, Eq. (3)-(4)). The time
    step replays as one CUDA graph. Each scene's contact solve runs in one
-   thread block of its own (its reductions need no device-wide barrier).
+   thread block (or one thread-block cluster) of its own: its reductions need
+   no device-wide barrier.
 
    Members are contexts created on the same device with the SAME
    cuda_stream (the batch's stream), none recording a tape; the caller keeps
@@ -565,12 +566,16 @@ mpm_status mpm_batch_synchronize(mpm_batch* batch, int32_t* status, mpm_step_sta
    MPM_BATCH_OPT_G2P_THREADS: threads (= particles) per G2P block, 64 to 512
      in multiples of 32 (default 256);
    MPM_BATCH_OPT_GRID_PARTICLES: a scene gets one grid-phase block per this
-     many particles (at least one; default 2048). */
+     many particles (at least one; default 2048);
+   MPM_BATCH_OPT_SOLVE_BLOCKS: thread blocks per scene's contact solve, 1, 2, 4
+     or 8 (default 1; more than one form a thread-block cluster per scene). The
+     solves start largest scene (by particle count) first. */
 enum {
   MPM_BATCH_OPT_GRAPHS = 1,
   MPM_BATCH_OPT_P2G_CHUNK = 2,
   MPM_BATCH_OPT_G2P_THREADS = 3,
-  MPM_BATCH_OPT_GRID_PARTICLES = 4
+  MPM_BATCH_OPT_GRID_PARTICLES = 4,
+  MPM_BATCH_OPT_SOLVE_BLOCKS = 5
 };
 mpm_status mpm_batch_set_option(mpm_batch* batch, int32_t option, int64_t value);
 

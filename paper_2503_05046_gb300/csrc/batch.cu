@@ -7,7 +7,8 @@
 // over a work list of (scene, block) items that the host builds from the
 // scenes' particle counts and the launch options, with one argument record
 // per scene in device memory (a block copies its scene's record into shared
-// memory first). The contact solve gives each scene one block. A time step
+// memory first). The contact solve gives each scene one block, or one
+// cluster of 2-8 blocks, largest scenes first. A time step
 // adds one launch before the substeps (statistics cleared, the impulse
 // accumulators noted) and one after them (the bodies' update of
 // Eq. (3)-(4), status and statistics gathered), and replays as one CUDA
@@ -15,6 +16,7 @@
 // scenes' particle counts and the substep count only; the argument records
 // (h, solver parameters, the particle buffer each scene is in) are
 // re-uploaded when they change, under the same graph.
+#include <algorithm>
 #include <cfloat>
 #include <cstring>
 #include <string>
@@ -31,6 +33,7 @@ struct mpm_batch {
   int p2g_chunk = 256;
   int g2p_threads = 256;
   int grid_particles = 2048;
+  int solve_blocks = 1;  // blocks (one cluster) per scene's contact solve
   // per-scene argument records (device) and their host images
   P2GArgs* p2g_d = nullptr;
   GridBatchArgs* grid_d = nullptr;
@@ -51,7 +54,9 @@ struct mpm_batch {
   float rec_h = 0.f;
   mpm_solver_params rec_sp{};
   bool records_valid = false;
-  // work lists: P2G items, then grid items, then G2P items
+  // work lists: P2G items, then grid items, then G2P items; the scenes'
+  // order for the contact solve (largest first)
+  int* order_d = nullptr;
   int2* work_d = nullptr;
   size_t work_cap = 0;
   int n_p2g = 0, n_grid = 0, n_g2p = 0;
@@ -97,6 +102,7 @@ void release(mpm_batch* b) {
   cudaFree(b->g2p_d);
   cudaFree(b->rig_d);
   cudaFree(b->work_d);
+  cudaFree(b->order_d);
   cudaFree(b->status_d);
   cudaFree(b->stats_d);
 }
@@ -179,17 +185,19 @@ std::vector<int2> build_work(mpm_batch* b) {
   return w;
 }
 
-void enqueue(mpm_batch* b, int n_substeps, double dt) {
+cudaError_t enqueue(mpm_batch* b, int n_substeps, double dt) {
   const cudaStream_t s = b->stream;
   const int ns = (int)b->ctx.size();
   launch_batch_begin(b->rig_d, ns, s);
   for (int k = 0; k < n_substeps; ++k) {
     launch_p2g_batch(b->p2g_d, b->work_d, b->n_p2g, b->p2g_chunk, s);
     launch_grid_batch(b->grid_d, b->work_d + b->n_p2g, b->n_grid, s);
-    launch_solve_batch(b->solve_d, ns, s);
+    const cudaError_t e = launch_solve_batch(b->solve_d, b->order_d, ns, b->solve_blocks, s);
+    if (e != cudaSuccess) return e;
     launch_g2p_batch(b->g2p_d, b->work_d + b->n_p2g + b->n_grid, b->n_g2p, b->g2p_threads, s);
   }
   launch_batch_end(b->rig_d, ns, dt, b->status_d, b->stats_d, s);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -312,6 +320,14 @@ mpm_status mpm_batch_step(mpm_batch* batch, double h, int32_t n_substeps,
     }
     // (pageable source: the copy has read it when the call returns)
     BCU(cudaMemcpyAsync(batch->work_d, w.data(), w.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    // the contact solves largest scene first (particle count as the proxy)
+    std::vector<int> order(ns);
+    for (int i = 0; i < ns; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return batch->ctx[x]->n > batch->ctx[y]->n;
+    });
+    if (!batch->order_d) BCU(balloc(&batch->order_d, ns));
+    BCU(cudaMemcpyAsync(batch->order_d, order.data(), ns * sizeof(int), cudaMemcpyHostToDevice, s));
     batch->work_valid = true;
     batch->layout += 1;
   }
@@ -339,8 +355,7 @@ mpm_status mpm_batch_step(mpm_batch* batch, double h, int32_t n_substeps,
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        enqueue(batch, n_substeps, dt);
-        const cudaError_t le = cudaGetLastError();
+        const cudaError_t le = enqueue(batch, n_substeps, dt);
         e = cudaStreamEndCapture(s, &graph);
         if (e == cudaSuccess) e = le;
       }
@@ -363,7 +378,7 @@ mpm_status mpm_batch_step(mpm_batch* batch, double h, int32_t n_substeps,
       launched = true;
     }
   }
-  if (!launched) enqueue(batch, n_substeps, dt);
+  if (!launched) BCU(enqueue(batch, n_substeps, dt));
   BCU(cudaGetLastError());
   // the members' host bookkeeping, as after a device-side mpm_step
   for (mpm_ctx* c : batch->ctx) {
@@ -446,6 +461,12 @@ mpm_status mpm_batch_set_option(mpm_batch* batch, int32_t option, int64_t value)
         return bfail(batch, MPM_ERR_INVALID_ARG, "G2P threads must be 64..512, a multiple of 32");
       if (batch->g2p_threads != (int)value) batch->work_valid = false;
       batch->g2p_threads = (int)value;
+      return MPM_OK;
+    case MPM_BATCH_OPT_SOLVE_BLOCKS:
+      if (value != 1 && value != 2 && value != 4 && value != 8)
+        return bfail(batch, MPM_ERR_INVALID_ARG, "solve blocks per scene must be 1, 2, 4 or 8");
+      if (batch->solve_blocks != (int)value) batch->work_valid = false;  // a new graph
+      batch->solve_blocks = (int)value;
       return MPM_OK;
     case MPM_BATCH_OPT_GRID_PARTICLES:
       if (value < 1 || value > (int64_t)1 << 30)

@@ -257,8 +257,10 @@ struct GridBatchArgs {
 int p2g_block_particles(int chunk);
 void launch_p2g_batch(const P2GArgs* args, const int2* work, int n_work, int chunk, cudaStream_t s);
 void launch_grid_batch(const GridBatchArgs* args, const int2* work, int n_work, cudaStream_t s);
-// one block per scene (its whole contact solve; SolveArgs.cluster_max = 0)
-void launch_solve_batch(const SolveArgs* args, int n_scenes, cudaStream_t s);
+// each scene's contact solve by one block or one cluster of 2, 4 or 8 blocks,
+// scenes in `order` (device, n_scenes entries)
+cudaError_t launch_solve_batch(const SolveArgs* args, const int* order, int n_scenes,
+                               int blocks_per_scene, cudaStream_t s);
 void launch_g2p_batch(const G2PArgs* args, const int2* work, int n_work, int threads,
                       cudaStream_t s);
 

@@ -1000,14 +1000,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveArgs a) {
   solve_body<kCluster>(a, (int)blockIdx.x, (int)gridDim.x);
 }
 
-// Batched: block b solves scene b on its own (the scenes of a batch are
-// small: one block holds a scene's contacts, and its reductions need no
-// barrier beyond __syncthreads)
-__global__ void __launch_bounds__(kThreads, 1) k_solve_batch(const SolveArgs* __restrict__ args) {
+// Batched: scene order[b / kBlocks] is solved by blocks b of one cluster of
+// kBlocks (one block: its reductions need no barrier beyond __syncthreads;
+// more: a thread-block cluster per scene, as the single-scene cluster solve).
+// `order` lists the scenes largest first, so that the long solves start in the
+// first wave of blocks.
+template <int kBlocks>
+__global__ void __launch_bounds__(kThreads, 1) k_solve_batch(const SolveArgs* __restrict__ args,
+                                                             const int* __restrict__ order) {
   __shared__ SolveArgs s_a;
-  load_args(args + blockIdx.x, s_a);
+  load_args(args + order[blockIdx.x / kBlocks], s_a);
   __syncthreads();
-  solve_body<false>(s_a, 0, 1);
+  if (threadIdx.x == 0) s_a.cluster_max = kBlocks > 1 ? 0x7fffffff : 0;  // this launch's kind
+  __syncthreads();
+  if constexpr (kBlocks == 1)
+    solve_body<false>(s_a, 0, 1);
+  else
+    solve_body<true>(s_a, (int)(blockIdx.x % kBlocks), kBlocks);
 }
 
 // ---------------------------------------------------------------------------
@@ -1796,9 +1805,12 @@ cudaError_t solve_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_solve<true>),
                              cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_solve_batch),
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_dynamic_smem());
+  for (const void* f : {reinterpret_cast<const void*>(&k_solve_batch<1>),
+                        reinterpret_cast<const void*>(&k_solve_batch<2>),
+                        reinterpret_cast<const void*>(&k_solve_batch<4>),
+                        reinterpret_cast<const void*>(&k_solve_batch<8>)})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_dynamic_smem());
   return e;
 }
 
@@ -1849,8 +1861,32 @@ cudaError_t launch_solve(const SolveArgs& a, int grid_blocks, int cluster_blocks
                                      solve_dynamic_smem(), s);
 }
 
-void launch_solve_batch(const SolveArgs* args, int n_scenes, cudaStream_t s) {
-  if (n_scenes > 0) k_solve_batch<<<n_scenes, kThreads, solve_dynamic_smem(), s>>>(args);
+namespace {
+template <int kBlocks>
+cudaError_t launch_solve_batch_k(const SolveArgs* args, const int* order, int n_scenes,
+                                 cudaStream_t s) {
+  if (kBlocks == 1) {
+    k_solve_batch<1><<<n_scenes, kThreads, solve_dynamic_smem(), s>>>(args, order);
+    return cudaGetLastError();
+  }
+  cudaLaunchAttribute attr;
+  const cudaLaunchConfig_t cfg0 = cluster_config(kBlocks, &attr, s);
+  cudaLaunchConfig_t cfg = cfg0;
+  cfg.gridDim = dim3(n_scenes * kBlocks);
+  cfg.attrs = &attr;
+  return cudaLaunchKernelEx(&cfg, k_solve_batch<kBlocks>, args, order);
+}
+}  // namespace
+
+cudaError_t launch_solve_batch(const SolveArgs* args, const int* order, int n_scenes,
+                               int blocks_per_scene, cudaStream_t s) {
+  if (n_scenes <= 0) return cudaSuccess;
+  switch (blocks_per_scene) {
+    case 2: return launch_solve_batch_k<2>(args, order, n_scenes, s);
+    case 4: return launch_solve_batch_k<4>(args, order, n_scenes, s);
+    case 8: return launch_solve_batch_k<8>(args, order, n_scenes, s);
+    default: return launch_solve_batch_k<1>(args, order, n_scenes, s);
+  }
 }
 
 const void* adjoint_kernel_ptr() { return reinterpret_cast<const void*>(&k_adjoint); }

@@ -30,6 +30,7 @@ OPT_CLUSTER_CONTACTS = 8
 OPT_CLUSTER_BLOCKS = 9
 OPT_TEST_BARRIER_TIMEOUT = 6
 BATCH_OPT_GRAPHS, BATCH_OPT_P2G_CHUNK, BATCH_OPT_G2P_THREADS, BATCH_OPT_GRID_PARTICLES = 1, 2, 3, 4
+BATCH_OPT_SOLVE_BLOCKS = 5
 PHASES = ["sort", "p2g", "grid", "solve", "g2p"]
 
 

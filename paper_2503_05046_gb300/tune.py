@@ -7,8 +7,8 @@ the timed steps are ordinary steps of the simulation):
 - a batch (native.Batch, mpm_batch_*): one launch per phase per substep over
   all scenes' (scene, block) work items. `tune_batch_launch` picks the
   particles per P2G warp tile (MPM_BATCH_OPT_P2G_CHUNK / 8 warps), the
-  threads per G2P block and the particles per grid-phase block, by
-  coordinate descent;
+  threads per G2P block, the particles per grid-phase block and the blocks
+  per scene's contact solve, by coordinate descent;
 - contexts side by side, each on its own stream replaying its step's CUDA
   graph (mpm_step with graphs on). `tune_batch` picks the cap on the SMs one
   context's cooperative contact solve occupies (MPM_OPT_SOLVE_BLOCKS) and the
@@ -64,18 +64,21 @@ def _time_batch(batch, h, n_substeps, solver, steps):
 
 
 def tune_batch_launch(batch, h, n_substeps, solver, steps=2, p2g_chunks=(256, 512, 1024),
-                      g2p_threads=(128, 256, 512), grid_particles=(512, 2048, 8192)):
+                      g2p_threads=(128, 256, 512), grid_particles=(512, 2048, 8192),
+                      solve_blocks=(1, 2, 4)):
     """Coordinate descent over the batch's launch options: for each knob in
-    turn (P2G chunk, G2P threads, grid particles per block), time `steps`
-    steps per value after one untimed step (which records the step's graph
-    for the new work lists), keep the fastest. Applies and returns the best
-    options (dict option -> value) and the table of (options, seconds)."""
+    turn (P2G chunk, G2P threads, grid particles per block, blocks per
+    scene's contact solve), time `steps` steps per value after one untimed
+    step (which records the step's graph for the new work lists), keep the
+    fastest. Applies and returns the best options (dict option -> value) and
+    the table of (options, seconds)."""
     best = {native.BATCH_OPT_P2G_CHUNK: 256, native.BATCH_OPT_G2P_THREADS: 256,
-            native.BATCH_OPT_GRID_PARTICLES: 2048}
+            native.BATCH_OPT_GRID_PARTICLES: 2048, native.BATCH_OPT_SOLVE_BLOCKS: 1}
     table = []
     for knob, values in ((native.BATCH_OPT_P2G_CHUNK, p2g_chunks),
                          (native.BATCH_OPT_G2P_THREADS, g2p_threads),
-                         (native.BATCH_OPT_GRID_PARTICLES, grid_particles)):
+                         (native.BATCH_OPT_GRID_PARTICLES, grid_particles),
+                         (native.BATCH_OPT_SOLVE_BLOCKS, solve_blocks)):
         timed = []
         for v in values:
             cand = dict(best)

@@ -92,14 +92,16 @@ def test_batched_scenes_match_the_oracle(native):
 
 def test_batched_launch_options_keep_parity(native):
     """Other work lists (64 and 128 particles per P2G warp tile, 128- and
-    512-thread G2P blocks, several grid blocks per scene) re-record the
-    step's graph and give the same results as the oracle."""
+    512-thread G2P blocks, several grid blocks per scene) and each scene's
+    contact solve in a cluster of 4, then 2 blocks re-record the step's graph
+    and give the same results as the oracle."""
     scs = small_scenes()
     batch = native.Batch(scs)
     opts = {0: [(native.BATCH_OPT_P2G_CHUNK, 512), (native.BATCH_OPT_G2P_THREADS, 128),
-                (native.BATCH_OPT_GRID_PARTICLES, 256)],
+                (native.BATCH_OPT_GRID_PARTICLES, 256), (native.BATCH_OPT_SOLVE_BLOCKS, 4)],
             1: [(native.BATCH_OPT_P2G_CHUNK, 1024), (native.BATCH_OPT_G2P_THREADS, 512),
-                (native.BATCH_OPT_GRID_PARTICLES, 100000), (native.BATCH_OPT_GRAPHS, 0)]}
+                (native.BATCH_OPT_GRID_PARTICLES, 100000), (native.BATCH_OPT_SOLVE_BLOCKS, 2),
+                (native.BATCH_OPT_GRAPHS, 0)]}
     run_batch_parity(native, batch, scs, steps=2, options=opts)
     batch.close()
 
