@@ -18,7 +18,7 @@ _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
 
 HALFSPACE, SPHERE, BOX, CAPSULE = 0, 1, 2, 3
-COROTATED, DRUCKER_PRAGER = 0, 1
+COROTATED, DRUCKER_PRAGER, CLOTH = 0, 1, 2
 OK, ERR_OUT_OF_DOMAIN, ERR_NOT_CONVERGED, ERR_LINE_SEARCH, ERR_ARG, ERR_NOT_SPD = range(6)
 
 
@@ -111,6 +111,11 @@ def lib(openmp=False):
         L.orc_contact_adjoint.argtypes = [C.POINTER(Problem), _dp, _dp, _dp, _dp, _dp]
         L.orc_rigid_dynamics_step.argtypes = [C.POINTER(Body), C.POINTER(Dynamics), _dp, _dp,
                                               C.c_double]
+        L.orc_cloth_rest.argtypes = [_dp, _dp, _dp, _dp, _dp]
+        L.orc_cloth_triangle.argtypes = [_dp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_double,
+                                         _dp]
+        L.orc_cloth_triangle.restype = C.c_double
+        L.orc_set_cloth.argtypes = [C.c_void_p, C.c_int, _ip, _dp, _dp, _ip]
         _libs[key] = L
     return _libs[key]
 
@@ -387,6 +392,16 @@ class Sim:
                                     mats, nb, bs, float(h), C.byref(S), _d(imp), C.byref(info))
         return st_code, info
 
+    def set_cloth(self, cloth):
+        """The cloth meshes (dict from cloth_from_scene) for the following substeps."""
+        tris = np.ascontiguousarray(cloth["tris"], np.int32).reshape(-1)
+        dmi = _f64(cloth["Dm_inv"]).reshape(-1).copy()
+        area = _f64(cloth["area"]).reshape(-1).copy()
+        mat = np.ascontiguousarray(cloth["mat"], np.int32).reshape(-1)
+        code = self.L.orc_set_cloth(self.h, len(area), _i(tris), _d(dmi), _d(area), _i(mat))
+        assert code == OK
+        self._cloth = (tris, dmi, area, mat)
+
     def last_grid(self):
         n = self.L.orc_last_grid(self.h, 0, None, None, None, None)
         ids = np.zeros(n, np.int32)
@@ -405,6 +420,45 @@ class Sim:
         n0 = np.zeros(n)
         self.L.orc_last_contacts(self.h, n, _i(p), _i(b), _d(g), _d(phi), _d(n0))
         return p, b, g.reshape(n, 3), phi, n0
+
+
+def cloth_rest(X0, X1, X2):
+    """Rest shape of a cloth triangle: (Dm_inv [2, 2], area)."""
+    dmi = np.zeros(4)
+    area = np.zeros(1)
+    lib().orc_cloth_rest(_d(_f64(X0, (3,))), _d(_f64(X1, (3,))), _d(_f64(X2, (3,))), _d(dmi),
+                         _d(area))
+    return dmi.reshape(2, 2), float(area[0])
+
+
+def cloth_triangle(x0, x1, x2, Dm_inv, area, mu, lam):
+    """Membrane energy of a cloth triangle and the forces on its vertices [3, 3]."""
+    f = np.zeros(9)
+    e = lib().orc_cloth_triangle(_d(_f64(x0, (3,))), _d(_f64(x1, (3,))), _d(_f64(x2, (3,))),
+                                 _d(_f64(Dm_inv, (4,))), float(area), float(mu), float(lam), _d(f))
+    return e, f.reshape(3, 3)
+
+
+def cloth_from_scene(scene):
+    """The cloth meshes of a scene's groups (those with "tris"), in global
+    particle ids, with rest shapes from the groups' float32 rest positions."""
+    tris, dmi, area, mat = [], [], [], []
+    offset = 0
+    for gi, g in enumerate(scene["groups"]):
+        x = np.asarray(g["x"], np.float32).astype(np.float64)
+        if "tris" in g:
+            rest = np.asarray(g.get("rest", g["x"]), np.float32).astype(np.float64)
+            for t in np.asarray(g["tris"], np.int64).reshape(-1, 3):
+                d, a = cloth_rest(rest[t[0]], rest[t[1]], rest[t[2]])
+                tris.append(t + offset)
+                dmi.append(d.reshape(4))
+                area.append(a)
+                mat.append(gi)
+        offset += len(x)
+    if not tris:
+        return None
+    return {"tris": np.array(tris, np.int32), "Dm_inv": np.array(dmi), "area": np.array(area),
+            "mat": np.array(mat, np.int32)}
 
 
 def advance_kinematic(bodies, dt):
@@ -439,6 +493,9 @@ def rollout(scene, steps, S, materials=None, bodies=None, state=None, substeps=N
     dyn = dynamics or {}
     grav = scene["grid"].get("gravity", (0.0, 0.0, -9.81))
     sim = Sim(scene["grid"])
+    cloth = cloth_from_scene(scene)
+    if cloth is not None:
+        sim.set_cloth(cloth)
     code = OK
     try:
         for n_sub in per_step[:steps]:

@@ -319,6 +319,80 @@ void orc_dp_project(const double F[9], double mu, double lam, double friction_an
 /* Rigid geometry (Sec. V-B: one contact per particle inside a geometry)       */
 /* ------------------------------------------------------------------------- */
 
+/* ---- cloth: corotated membrane energy of a triangle ----------------------- */
+
+void orc_cloth_rest(const double X0[3], const double X1[3], const double X2[3],
+                    double Dm_inv[4], double* area) {
+  double e1[3], e2[3], nrm[3], t1[3], t2[3];
+  for (int a = 0; a < 3; ++a) {
+    e1[a] = X1[a] - X0[a];
+    e2[a] = X2[a] - X0[a];
+  }
+  cross3(e1, e2, nrm);
+  const double nn = sqrt(dot3(nrm, nrm)), l1 = sqrt(dot3(e1, e1));
+  *area = 0.5 * nn;
+  for (int a = 0; a < 3; ++a) {
+    t1[a] = e1[a] / l1;
+    nrm[a] /= nn;
+  }
+  cross3(nrm, t1, t2);
+  /* the rest edges in the triangle's frame (t1, t2): Dm = [[|e1|, e2.t1], [0, e2.t2]] */
+  const double a00 = l1, a01 = dot3(e2, t1), a11 = dot3(e2, t2);
+  Dm_inv[0] = 1.0 / a00;
+  Dm_inv[1] = -a01 / (a00 * a11);
+  Dm_inv[2] = 0.0;
+  Dm_inv[3] = 1.0 / a11;
+}
+
+double orc_cloth_triangle(const double x0[3], const double x1[3], const double x2[3],
+                          const double Dm_inv[4], double area, double mu, double lam,
+                          double f[9]) {
+  /* F = Ds Dm^-1, 3x2 row-major: F[2r + c] */
+  double Ds[6], F[6];
+  for (int r = 0; r < 3; ++r) {
+    Ds[2 * r] = x1[r] - x0[r];
+    Ds[2 * r + 1] = x2[r] - x0[r];
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 2; ++c)
+      F[2 * r + c] = Ds[2 * r] * Dm_inv[c] + Ds[2 * r + 1] * Dm_inv[2 + c];
+  /* C = F^T F (2x2), S = sqrt(C) = (C + sqrt(det C) I) / sqrt(tr C + 2 sqrt(det C)) */
+  double Cm[4] = {0, 0, 0, 0};
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      for (int r = 0; r < 3; ++r) Cm[2 * a + b] += F[2 * r + a] * F[2 * r + b];
+  const double detC = Cm[0] * Cm[3] - Cm[1] * Cm[2];
+  const double J = sqrt(detC > 0.0 ? detC : 0.0);
+  const double tnorm = sqrt(Cm[0] + Cm[3] + 2.0 * J);
+  const double S[4] = {(Cm[0] + J) / tnorm, Cm[1] / tnorm, Cm[2] / tnorm, (Cm[3] + J) / tnorm};
+  /* R = F S^-1 (det S = J) */
+  const double Si[4] = {S[3] / J, -S[1] / J, -S[2] / J, S[0] / J};
+  double R[6];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 2; ++c) R[2 * r + c] = F[2 * r] * Si[c] + F[2 * r + 1] * Si[2 + c];
+  double fr2 = 0.0;
+  for (int e = 0; e < 6; ++e) fr2 += (F[e] - R[e]) * (F[e] - R[e]);
+  const double psi = mu * fr2 + 0.5 * lam * (J - 1.0) * (J - 1.0);
+  if (f) {
+    /* P = 2 mu (F - R) + lam (J - 1) J F C^-1 */
+    const double Ci[4] = {Cm[3] / detC, -Cm[1] / detC, -Cm[2] / detC, Cm[0] / detC};
+    double P[6];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 2; ++c)
+        P[2 * r + c] = 2.0 * mu * (F[2 * r + c] - R[2 * r + c]) +
+                       lam * (J - 1.0) * J * (F[2 * r] * Ci[c] + F[2 * r + 1] * Ci[2 + c]);
+    /* dE/dDs = area P Dm^-T; f1, f2 its columns negated, f0 = -(f1 + f2) */
+    for (int r = 0; r < 3; ++r) {
+      const double g1 = area * (P[2 * r] * Dm_inv[0] + P[2 * r + 1] * Dm_inv[1]);
+      const double g2 = area * (P[2 * r] * Dm_inv[2] + P[2 * r + 1] * Dm_inv[3]);
+      f[3 + r] = -g1;
+      f[6 + r] = -g2;
+      f[r] = g1 + g2;
+    }
+  }
+  return area * psi;
+}
+
 double orc_sdf(const orc_body* b, const double x[3], double n[3]) {
   /* body-frame point y = R^T (x - p) */
   double r[3] = {x[0] - b->p[0], x[1] - b->p[1], x[2] - b->p[2]};
@@ -862,6 +936,14 @@ struct orc_sim {
   double* con_gamma;
   double* con_phi0;
   double* con_n0;
+  /* cloth meshes (orc_set_cloth) and the forces of the current substep */
+  int n_tris;
+  int* tris;
+  double* tri_Dm_inv;
+  double* tri_area;
+  int* tri_mat;
+  double* fext;
+  int fext_cap;
 };
 
 orc_sim* orc_create(const orc_grid* grid) {
@@ -877,8 +959,29 @@ orc_sim* orc_create(const orc_grid* grid) {
   return s;
 }
 
+int orc_set_cloth(orc_sim* s, int n_tris, const int* tris, const double* Dm_inv,
+                  const double* area, const int* mat_of_tri) {
+  if (!s || n_tris < 0 || (n_tris > 0 && (!tris || !Dm_inv || !area || !mat_of_tri)))
+    return ORC_ERR_ARG;
+  free(s->tris); free(s->tri_Dm_inv); free(s->tri_area); free(s->tri_mat);
+  s->n_tris = n_tris;
+  const size_t nt = (size_t)(n_tris > 0 ? n_tris : 1);
+  s->tris = (int*)malloc(sizeof(int) * 3 * nt);
+  s->tri_Dm_inv = (double*)malloc(sizeof(double) * 4 * nt);
+  s->tri_area = (double*)malloc(sizeof(double) * nt);
+  s->tri_mat = (int*)malloc(sizeof(int) * nt);
+  if (n_tris > 0) {
+    memcpy(s->tris, tris, sizeof(int) * 3 * (size_t)n_tris);
+    memcpy(s->tri_Dm_inv, Dm_inv, sizeof(double) * 4 * (size_t)n_tris);
+    memcpy(s->tri_area, area, sizeof(double) * (size_t)n_tris);
+    memcpy(s->tri_mat, mat_of_tri, sizeof(int) * (size_t)n_tris);
+  }
+  return ORC_OK;
+}
+
 void orc_destroy(orc_sim* s) {
   if (!s) return;
+  free(s->tris); free(s->tri_Dm_inv); free(s->tri_area); free(s->tri_mat); free(s->fext);
   free(s->m); free(s->p); free(s->v); free(s->dof); free(s->dof_node);
   free(s->con_p); free(s->con_b); free(s->con_gamma); free(s->con_phi0); free(s->con_n0);
   free(s);
@@ -897,17 +1000,20 @@ static int is_bc_node(const orc_grid* g, int ix, int iy, int iz) {
 static void kirchhoff_stress(const orc_material* mt, const double F[9], double tau[9]) {
   double mu, lam;
   orc_lame(mt->E, mt->nu, &mu, &lam);
-  if (mt->model == ORC_DRUCKER_PRAGER)
+  if (mt->model == ORC_CLOTH) {  /* the mesh carries the cloth's elasticity */
+    for (int e = 0; e < 9; ++e) tau[e] = 0.0;
+  } else if (mt->model == ORC_DRUCKER_PRAGER)
     orc_hencky_tau(F, mu, lam, tau);
   else
     orc_corotated_tau(F, mu, lam, tau);
 }
 
 /* P2G of particle q (MLS-MPM, Eq. (6)): its mass and its momentum with the
-   affine and stress terms, scattered to the 27 nodes of its stencil. */
+   affine and stress terms (and h times its mesh force, for cloth), scattered
+   to the 27 nodes of its stencil. */
 static void p2g_particle(orc_sim* s, int q, const double* x, const double* v, const double* C,
                          const double* F, const double* mass, const double* vol, const int* mat,
-                         const orc_material* mats, double h) {
+                         const orc_material* mats, double h, const double* fext) {
   const orc_grid* g = &s->g;
   const double dx = g->dx, Dinv = 4.0 / (dx * dx);
   int base[3];
@@ -924,7 +1030,8 @@ static void p2g_particle(orc_sim* s, int q, const double* x, const double* v, co
         s->m[i] += wt * mass[q];
         for (int r = 0; r < 3; ++r)
           s->p[3 * i + r] += wt * (mass[q] * v[3 * q + r] + aff[3 * r] * dpos[0] +
-                                   aff[3 * r + 1] * dpos[1] + aff[3 * r + 2] * dpos[2]);
+                                   aff[3 * r + 1] * dpos[1] + aff[3 * r + 2] * dpos[2] +
+                                   (fext ? h * fext[3 * q + r] : 0.0));
       }
 }
 
@@ -955,6 +1062,7 @@ static void g2p_particle(const orc_sim* s, int q, double* x, double* v, double* 
     x[3 * q + r] += h * vp[r];
   }
   for (int e = 0; e < 9; ++e) C[9 * q + e] = Dinv * Bm[e];
+  if (mats[mat[q]].model == ORC_CLOTH) return;  /* F stays I: no stress */
   double Fu[9];
   for (int e = 0; e < 9; ++e) Fu[e] = h * C[9 * q + e];
   Fu[0] += 1.0; Fu[4] += 1.0; Fu[8] += 1.0;
@@ -976,7 +1084,7 @@ static void g2p_particle(const orc_sim* s, int q, double* x, double* v, double* 
    contributions differs from the serial build. */
 static void p2g_slabs(orc_sim* s, int n, const double* x, const double* v, const double* C,
                       const double* F, const double* mass, const double* vol, const int* mat,
-                      const orc_material* mats, double h) {
+                      const orc_material* mats, double h, const double* fext) {
   const orc_grid* g = &s->g;
   int ax = 0;
   for (int a = 1; a < 3; ++a)
@@ -1001,7 +1109,7 @@ static void p2g_slabs(orc_sim* s, int n, const double* x, const double* v, const
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = parity; k < n_slabs; k += 2)
       for (int t = start[k]; t < start[k + 1]; ++t)
-        p2g_particle(s, order[t], x, v, C, F, mass, vol, mat, mats, h);
+        p2g_particle(s, order[t], x, v, C, F, mass, vol, mat, mats, h, fext);
   }
   free(slab); free(start); free(order); free(fill);
 }
@@ -1095,11 +1203,38 @@ int orc_substep(orc_sim* s, int n, double* x, double* v, double* C, double* F,
   memset(s->m, 0, s->nn * sizeof(double));
   memset(s->p, 0, 3 * s->nn * sizeof(double));
 
+  /* cloth: the mesh forces at the substep's start positions */
+  const double* fext = NULL;
+  if (s->n_tris > 0) {
+    if (s->fext_cap < n) {
+      free(s->fext);
+      s->fext = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+      s->fext_cap = n;
+    }
+    memset(s->fext, 0, sizeof(double) * 3 * (size_t)n);
+    for (int t = 0; t < s->n_tris; ++t) {
+      const int* v3 = s->tris + 3 * t;
+      if (v3[0] < 0 || v3[0] >= n || v3[1] < 0 || v3[1] >= n || v3[2] < 0 || v3[2] >= n ||
+          s->tri_mat[t] < 0 || s->tri_mat[t] >= n_mat) {
+        inf.status = ORC_ERR_ARG;
+        if (info) *info = inf;
+        return inf.status;
+      }
+      double mu, lam, ft[9];
+      orc_lame(mats[s->tri_mat[t]].E, mats[s->tri_mat[t]].nu, &mu, &lam);
+      orc_cloth_triangle(x + 3 * v3[0], x + 3 * v3[1], x + 3 * v3[2], s->tri_Dm_inv + 4 * t,
+                         s->tri_area[t], mu, lam, ft);
+      for (int k = 0; k < 3; ++k)
+        for (int r = 0; r < 3; ++r) s->fext[3 * v3[k] + r] += ft[3 * k + r];
+    }
+    fext = s->fext;
+  }
+
   /* P2G (MLS-MPM): mass and momentum with the stress term, Eq. (6) */
 #ifdef _OPENMP
-  p2g_slabs(s, n, x, v, C, F, mass, vol, mat, mats, h);
+  p2g_slabs(s, n, x, v, C, F, mass, vol, mat, mats, h, fext);
 #else
-  for (int q = 0; q < n; ++q) p2g_particle(s, q, x, v, C, F, mass, vol, mat, mats, h);
+  for (int q = 0; q < n; ++q) p2g_particle(s, q, x, v, C, F, mass, vol, mat, mats, h, fext);
 #endif
 
   /* grid update: v* = p/m + h g; Dirichlet walls (reading: sticky, v = 0) */

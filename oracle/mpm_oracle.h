@@ -40,7 +40,7 @@ enum {
 };
 
 enum { ORC_HALFSPACE = 0, ORC_SPHERE = 1, ORC_BOX = 2, ORC_CAPSULE = 3 };
-enum { ORC_COROTATED = 0, ORC_DRUCKER_PRAGER = 1 };
+enum { ORC_COROTATED = 0, ORC_DRUCKER_PRAGER = 1, ORC_CLOTH = 2 };
 
 typedef struct {
   double dx;
@@ -133,6 +133,26 @@ void orc_hencky_tau(const double F[9], double mu, double lam, double tau[9]);
 void orc_dp_project(const double F[9], double mu, double lam, double friction_angle_deg,
                     double Fout[9]);
 
+/* Cloth (the paper's cloth results, Sec. VI): a triangle mesh whose vertices
+   are MPM particles of an ORC_CLOTH material. Reading taken: the cloth's
+   in-plane elasticity is a Lagrangian force of the mesh, the corotated
+   membrane energy per triangle
+     psi(F) = mu |F - R|^2 + lam/2 (J - 1)^2,   F = Ds Dm^-1 (3x2),
+   R the 3x2 polar factor of F (F = R S, S = sqrt(F^T F)), J = det S, times
+   the triangle's rest area; Ds = [x1 - x0, x2 - x0], Dm the rest edges in
+   the triangle's own plane. The particles carry no stress (F stays I); their
+   P2G momentum gains h f_p with f_p = -dE/dx_p. Collision and self-collision
+   go through the grid and the contact solve like any particle's. */
+
+/* Rest shape of triangle (X0, X1, X2): Dm^-1 (2x2 row-major) and area. */
+void orc_cloth_rest(const double X0[3], const double X1[3], const double X2[3],
+                    double Dm_inv[4], double* area);
+/* Energy of one triangle and, if f is not NULL, the forces -dE/dx on its
+   three vertices (f[9]). */
+double orc_cloth_triangle(const double x0[3], const double x1[3], const double x2[3],
+                          const double Dm_inv[4], double area, double mu, double lam,
+                          double f[9]);
+
 /* Signed distance of a body at world point x and its outward unit normal. */
 double orc_sdf(const orc_body* b, const double x[3], double n[3]);
 
@@ -182,6 +202,12 @@ typedef struct {
 
 orc_sim* orc_create(const orc_grid* grid);
 void orc_destroy(orc_sim* s);
+
+/* The cloth meshes of the sim's particles: triangle t joins particles
+   tris[3t..3t+2], with rest shape Dm_inv[4t..4t+3], rest area area[t] and
+   the Lame parameters of material mat_of_tri[t] (copied). */
+int orc_set_cloth(orc_sim* s, int n_tris, const int* tris, const double* Dm_inv,
+                  const double* area, const int* mat_of_tri);
 
 /* Threads orc_substep uses: 1 in the serial build (the checker); the
    OpenMP build (-fopenmp, a CPU baseline over all host cores only) runs P2G

@@ -26,6 +26,9 @@ def oracle_substep(sc, gpu_state, gpu_bodies, solver, h=None):
     st = O.Sim.state({"x": gpu_state["x"], "v": gpu_state["v"], "C": gpu_state["C"],
                       "F": gpu_state["F"], "mass": mass, "vol": vol, "mat": mat})
     osim = O.Sim(sc["grid"])
+    cloth = O.cloth_from_scene(sc)
+    if cloth is not None:
+        osim.set_cloth(cloth)
     bodies = O.bodies_from_scene({"bodies": gpu_bodies})
     imp = np.zeros(6 * max(len(bodies), 1))
     code, info = osim.substep(st, mats, [O.make_body(b) for b in bodies],
