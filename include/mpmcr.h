@@ -67,9 +67,10 @@ typedef enum {
 
 enum { MPM_MEM_HOST = 0, MPM_MEM_DEVICE = 1 };
 
-/* Material models: fixed corotated elasticity, and Drucker-Prager sand
-   (Hencky strain, the granular model the paper cites, Sec. II-A). */
-enum { MPM_COROTATED = 0, MPM_DRUCKER_PRAGER = 1 };
+/* Material models: fixed corotated elasticity, Drucker-Prager sand (Hencky
+   strain, the granular model the paper cites, Sec. II-A), and cloth (the
+   vertices of a triangle mesh, mpm_add_cloth; Sec. VI cloth results). */
+enum { MPM_COROTATED = 0, MPM_DRUCKER_PRAGER = 1, MPM_CLOTH = 2 };
 
 /* Rigid geometry (analytic signed distance functions, body frame):
    HALFSPACE  the plane z = 0, outward normal +z (no parameters);
@@ -227,6 +228,26 @@ mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const floa
                              int32_t mem_kind, int64_t* first_id);
 
 /* Number of particles in the context. */
+/* Add a piece of cloth (the paper's cloth results, Sec. VI): a triangle mesh
+   whose n_vertices vertices become particles of a new group with material
+   `material` (model MPM_CLOTH; E, nu of the membrane, rho its density),
+   x, v [n_vertices][3] in mem_kind memory. triangles [n_triangles][3] holds
+   vertex indices 0 .. n_vertices - 1 of this call (host memory). The rest
+   shape of each triangle is taken from x. Reading taken: the cloth's in-plane
+   elasticity is a Lagrangian force of the mesh, the corotated membrane energy
+   per triangle, rest area * thickness times mu |F - R|^2 + lam/2 (J - 1)^2 with
+   F = Ds Dm^-1 (3x2), R its polar factor, J = det(sqrt(F^T F)); every substep
+   the forces on the vertices are recomputed from their positions and P2G adds
+   h f to their momentum. The vertices carry no stress; they collide with
+   bodies, with the cloth itself and with other material through the grid and
+   the contact solve. No bending. Each vertex has mass rho * thickness * (mesh
+   area) / n_vertices. *first_id receives the first vertex's particle id.
+   Contexts with cloth cannot record a tape or join a batch (MPM_ERR_STATE /
+   MPM_ERR_INVALID_ARG there). */
+mpm_status mpm_add_cloth(mpm_ctx* ctx, int64_t n_vertices, const float* x, const float* v,
+                         int64_t n_triangles, const int32_t* triangles, float thickness,
+                         const mpm_material* material, int32_t mem_kind, int64_t* first_id);
+
 mpm_status mpm_num_particles(const mpm_ctx* ctx, int64_t* n);
 
 /* Overwrite the state of all particles, in id order. Any of x, v, C, F may be
@@ -538,8 +559,8 @@ mpm_status mpm_get_phase_times(mpm_ctx* ctx, double* ms, int64_t* launches, int3
 typedef struct mpm_batch mpm_batch;
 
 /* Create a batch of n >= 1 members. MPM_ERR_INVALID_ARG if a member is NULL,
-   repeated, on another device or stream, recording a tape, or block-sparse
-   (max_blocks). */
+   repeated, on another device or stream, recording a tape, block-sparse
+   (max_blocks), or holds cloth. */
 mpm_status mpm_batch_create(mpm_ctx* const* ctxs, int32_t n, mpm_batch** out);
 
 /* One rigid time step of every member: n_substeps substeps of size h with

@@ -431,17 +431,19 @@ def cloth_rest(X0, X1, X2):
     return dmi.reshape(2, 2), float(area[0])
 
 
-def cloth_triangle(x0, x1, x2, Dm_inv, area, mu, lam):
-    """Membrane energy of a cloth triangle and the forces on its vertices [3, 3]."""
+def cloth_triangle(x0, x1, x2, Dm_inv, vol, mu, lam):
+    """Membrane energy of a cloth triangle of rest volume vol and the forces on
+    its vertices [3, 3]."""
     f = np.zeros(9)
     e = lib().orc_cloth_triangle(_d(_f64(x0, (3,))), _d(_f64(x1, (3,))), _d(_f64(x2, (3,))),
-                                 _d(_f64(Dm_inv, (4,))), float(area), float(mu), float(lam), _d(f))
+                                 _d(_f64(Dm_inv, (4,))), float(vol), float(mu), float(lam), _d(f))
     return e, f.reshape(3, 3)
 
 
 def cloth_from_scene(scene):
     """The cloth meshes of a scene's groups (those with "tris"), in global
-    particle ids, with rest shapes from the groups' float32 rest positions."""
+    particle ids, with rest shapes from the groups' float32 rest positions and
+    rest volumes = rest area * the group's thickness."""
     tris, dmi, area, mat = [], [], [], []
     offset = 0
     for gi, g in enumerate(scene["groups"]):
@@ -452,7 +454,7 @@ def cloth_from_scene(scene):
                 d, a = cloth_rest(rest[t[0]], rest[t[1]], rest[t[2]])
                 tris.append(t + offset)
                 dmi.append(d.reshape(4))
-                area.append(a)
+                area.append(a * float(np.float32(g["thickness"])))
                 mat.append(gi)
         offset += len(x)
     if not tris:

@@ -345,7 +345,7 @@ void orc_cloth_rest(const double X0[3], const double X1[3], const double X2[3],
 }
 
 double orc_cloth_triangle(const double x0[3], const double x1[3], const double x2[3],
-                          const double Dm_inv[4], double area, double mu, double lam,
+                          const double Dm_inv[4], double vol, double mu, double lam,
                           double f[9]) {
   /* F = Ds Dm^-1, 3x2 row-major: F[2r + c] */
   double Ds[6], F[6];
@@ -381,16 +381,16 @@ double orc_cloth_triangle(const double x0[3], const double x1[3], const double x
       for (int c = 0; c < 2; ++c)
         P[2 * r + c] = 2.0 * mu * (F[2 * r + c] - R[2 * r + c]) +
                        lam * (J - 1.0) * J * (F[2 * r] * Ci[c] + F[2 * r + 1] * Ci[2 + c]);
-    /* dE/dDs = area P Dm^-T; f1, f2 its columns negated, f0 = -(f1 + f2) */
+    /* dE/dDs = vol P Dm^-T; f1, f2 its columns negated, f0 = -(f1 + f2) */
     for (int r = 0; r < 3; ++r) {
-      const double g1 = area * (P[2 * r] * Dm_inv[0] + P[2 * r + 1] * Dm_inv[1]);
-      const double g2 = area * (P[2 * r] * Dm_inv[2] + P[2 * r + 1] * Dm_inv[3]);
+      const double g1 = vol * (P[2 * r] * Dm_inv[0] + P[2 * r + 1] * Dm_inv[1]);
+      const double g2 = vol * (P[2 * r] * Dm_inv[2] + P[2 * r + 1] * Dm_inv[3]);
       f[3 + r] = -g1;
       f[6 + r] = -g2;
       f[r] = g1 + g2;
     }
   }
-  return area * psi;
+  return vol * psi;
 }
 
 double orc_sdf(const orc_body* b, const double x[3], double n[3]) {
@@ -960,8 +960,8 @@ orc_sim* orc_create(const orc_grid* grid) {
 }
 
 int orc_set_cloth(orc_sim* s, int n_tris, const int* tris, const double* Dm_inv,
-                  const double* area, const int* mat_of_tri) {
-  if (!s || n_tris < 0 || (n_tris > 0 && (!tris || !Dm_inv || !area || !mat_of_tri)))
+                  const double* vol, const int* mat_of_tri) {
+  if (!s || n_tris < 0 || (n_tris > 0 && (!tris || !Dm_inv || !vol || !mat_of_tri)))
     return ORC_ERR_ARG;
   free(s->tris); free(s->tri_Dm_inv); free(s->tri_area); free(s->tri_mat);
   s->n_tris = n_tris;
@@ -973,7 +973,7 @@ int orc_set_cloth(orc_sim* s, int n_tris, const int* tris, const double* Dm_inv,
   if (n_tris > 0) {
     memcpy(s->tris, tris, sizeof(int) * 3 * (size_t)n_tris);
     memcpy(s->tri_Dm_inv, Dm_inv, sizeof(double) * 4 * (size_t)n_tris);
-    memcpy(s->tri_area, area, sizeof(double) * (size_t)n_tris);
+    memcpy(s->tri_area, vol, sizeof(double) * (size_t)n_tris);
     memcpy(s->tri_mat, mat_of_tri, sizeof(int) * (size_t)n_tris);
   }
   return ORC_OK;

@@ -142,15 +142,16 @@ void orc_dp_project(const double F[9], double mu, double lam, double friction_an
    the triangle's rest area; Ds = [x1 - x0, x2 - x0], Dm the rest edges in
    the triangle's own plane. The particles carry no stress (F stays I); their
    P2G momentum gains h f_p with f_p = -dE/dx_p. Collision and self-collision
-   go through the grid and the contact solve like any particle's. */
+   go through the grid and the contact solve like any particle's. The energy
+   of a triangle is psi times its rest volume (rest area times thickness). */
 
 /* Rest shape of triangle (X0, X1, X2): Dm^-1 (2x2 row-major) and area. */
 void orc_cloth_rest(const double X0[3], const double X1[3], const double X2[3],
                     double Dm_inv[4], double* area);
-/* Energy of one triangle and, if f is not NULL, the forces -dE/dx on its
-   three vertices (f[9]). */
+/* Energy of one triangle of rest volume vol and, if f is not NULL, the forces
+   -dE/dx on its three vertices (f[9]). */
 double orc_cloth_triangle(const double x0[3], const double x1[3], const double x2[3],
-                          const double Dm_inv[4], double area, double mu, double lam,
+                          const double Dm_inv[4], double vol, double mu, double lam,
                           double f[9]);
 
 /* Signed distance of a body at world point x and its outward unit normal. */
@@ -204,10 +205,10 @@ orc_sim* orc_create(const orc_grid* grid);
 void orc_destroy(orc_sim* s);
 
 /* The cloth meshes of the sim's particles: triangle t joins particles
-   tris[3t..3t+2], with rest shape Dm_inv[4t..4t+3], rest area area[t] and
+   tris[3t..3t+2], with rest shape Dm_inv[4t..4t+3], rest volume vol[t] and
    the Lame parameters of material mat_of_tri[t] (copied). */
 int orc_set_cloth(orc_sim* s, int n_tris, const int* tris, const double* Dm_inv,
-                  const double* area, const int* mat_of_tri);
+                  const double* vol, const int* mat_of_tri);
 
 /* Threads orc_substep uses: 1 in the serial build (the checker); the
    OpenMP build (-fopenmp, a CPU baseline over all host cores only) runs P2G

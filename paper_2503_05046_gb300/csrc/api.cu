@@ -346,7 +346,8 @@ void release(mpm_ctx* c) {
                   c->sb.vals[1], c->sb.hist, c->sb.partial, c->stage, c->adj_vec, c->adj_body,
                   c->adj_out, c->adj_ids, c->adj_io, c->bw_buf, c->bw_gbar, c->bw_slot, c->bw_mat,
                   c->tape_pool, c->tape_recs, c->tape_counters, c->bw_snap, c->bw_gbody, c->dyn_d,
-                  c->imp0_d, c->bodies_step_d, c->G.n_mapped, c->slot_d};
+                  c->imp0_d, c->bodies_step_d, c->G.n_mapped, c->slot_d, c->cloth_tris_d,
+                  c->cloth_rest_d, c->cloth_f_d, c->cloth_slot_d};
   for (auto& t : c->tape)
     if (t.state) cudaFree(t.state);
   for (void* p : ptrs)
@@ -376,6 +377,15 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
   pa.g = ctx->g; pa.P = ctx->P[cur]; pa.n = n; pa.groups = ctx->groups_d;
   pa.bodies = ctx->bodies_d; pa.nb = nb; pa.h = hf; pa.G = ctx->G; pa.C = ctx->C;
   pa.status = ctx->status; pa.stats = ctx->stats;
+  pa.fext = nullptr;
+  pa.fext_stride = ctx->cap;
+  if (!ctx->cloth_tris.empty()) {
+    // cloth: the mesh forces at the substep's start positions
+    mark_phase(ctx, MPM_PHASE_P2G);
+    launch_cloth_forces(ctx->P[cur], n, ctx->cloth_slot_d, ctx->cloth_tris_d, ctx->cloth_rest_d,
+                        (int)ctx->cloth_tris.size(), ctx->groups_d, ctx->cloth_f_d, ctx->cap, s);
+    pa.fext = ctx->cloth_f_d;
+  }
   if (ctx->g.slot) {
     // a block-sparse grid gives the substep's blocks storage before P2G
     mark_phase(ctx, MPM_PHASE_GRID);
@@ -432,6 +442,9 @@ cudaError_t enqueue_step(mpm_ctx* ctx, int from, bool sort_now, int n_substeps, 
     launch_sort(ctx->g, ctx->P[cur], ctx->P[1 - cur], n, ctx->sb, s);
     cur = 1 - cur;
   }
+  // cloth triangles find their vertices through the id -> slot map of the
+  // buffer the substeps run on
+  if (!ctx->cloth_tris.empty()) launch_slot_map(ctx->P[cur], n, ctx->cloth_slot_d, s);
   for (int k = 0; k < n_substeps; ++k) {
     const cudaError_t e = enqueue_substep(ctx, cur, nb, hf, sp, solve_blocks, true, s, ctx->taping);
     if (e != cudaSuccess) return e;
@@ -689,8 +702,9 @@ DevGroup make_group(const mpm_material& mat, float particle_volume) {
 }
 
 bool material_ok(const mpm_material* mat) {
-  return mat && (mat->model == MPM_COROTATED || mat->model == MPM_DRUCKER_PRAGER) && mat->E > 0.f &&
-         mat->nu > -1.f && mat->nu < 0.5f && mat->rho > 0.f;
+  return mat &&
+         (mat->model == MPM_COROTATED || mat->model == MPM_DRUCKER_PRAGER || mat->model == MPM_CLOTH) &&
+         mat->E > 0.f && mat->nu > -1.f && mat->nu < 0.5f && mat->rho > 0.f;
 }
 
 }  // namespace
@@ -703,6 +717,8 @@ mpm_status mpm_set_material(mpm_ctx* ctx, int32_t group, const mpm_material* mat
     return fail(ctx, MPM_ERR_STATE, "mpm_set_material: not while a tape is recorded");
   if (mat->rho != ctx->mats[group].rho)
     return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_material: the density (particle mass) is fixed");
+  if ((mat->model == MPM_CLOTH) != (ctx->mats[group].model == MPM_CLOTH))
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_material: cloth stays cloth");
   ctx->groups[group] = make_group(*mat, ctx->groups[group].vol);
   ctx->mats[group] = *mat;
   CU(cudaMemcpyAsync(ctx->groups_d, ctx->groups.data(), ctx->groups.size() * sizeof(DevGroup),
@@ -714,15 +730,95 @@ mpm_status mpm_set_material(mpm_ctx* ctx, int32_t group, const mpm_material* mat
   return MPM_OK;
 }
 
+namespace {
+mpm_status add_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v,
+                         float particle_volume, const mpm_material* mat, int32_t mem_kind,
+                         int64_t* first_id);
+}  // namespace
+
 mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v,
                              float particle_volume, const mpm_material* mat, int32_t mem_kind,
                              int64_t* first_id) {
   if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (mat && mat->model != MPM_COROTATED && mat->model != MPM_DRUCKER_PRAGER)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_add_particles: unknown material model");
+  return add_particles(ctx, n, x, v, particle_volume, mat, mem_kind, first_id);
+}
+
+mpm_status mpm_add_cloth(mpm_ctx* ctx, int64_t n_vertices, const float* x, const float* v,
+                         int64_t n_triangles, const int32_t* triangles, float thickness,
+                         const mpm_material* material, int32_t mem_kind, int64_t* first_id) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (n_vertices <= 0 || n_triangles <= 0 || !x || !v || !triangles || !material ||
+      material->model != MPM_CLOTH || !(thickness > 0.f) ||
+      (mem_kind != MPM_MEM_HOST && mem_kind != MPM_MEM_DEVICE))
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_add_cloth: bad argument");
+  if (ctx->taping) return fail(ctx, MPM_ERR_STATE, "mpm_add_cloth: a tape is recording");
+  if (n_triangles >= (1LL << 30)) return fail(ctx, MPM_ERR_CAPACITY, "mpm_add_cloth: too many triangles");
+  // rest positions on the host
+  std::vector<float> xh((size_t)3 * n_vertices);
+  if (mem_kind == MPM_MEM_DEVICE)
+    CU(cudaMemcpy(xh.data(), x, xh.size() * sizeof(float), cudaMemcpyDeviceToHost));
+  else
+    memcpy(xh.data(), x, xh.size() * sizeof(float));
+  std::vector<double> rest((size_t)5 * n_triangles);
+  double total_area = 0.0;
+  for (int64_t t = 0; t < n_triangles; ++t) {
+    double X[3][3];
+    for (int k = 0; k < 3; ++k) {
+      const int32_t vi = triangles[3 * t + k];
+      if (vi < 0 || vi >= n_vertices)
+        return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_add_cloth: vertex index out of range");
+      for (int c = 0; c < 3; ++c) X[k][c] = (double)xh[3 * (size_t)vi + c];
+    }
+    cloth_rest_shape(X[0], X[1], X[2], &rest[5 * (size_t)t]);
+    const double a = rest[5 * (size_t)t + 4];
+    if (!(a > 0.0) || !std::isfinite(rest[5 * (size_t)t]) || !std::isfinite(rest[5 * (size_t)t + 3]))
+      return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_add_cloth: a degenerate triangle");
+    total_area += a;
+    rest[5 * (size_t)t + 4] = a * (double)thickness;  // the energy weight: rest volume
+  }
+  const float vol = (float)(thickness * total_area / (double)n_vertices);
+  int64_t first = 0;
+  const mpm_status st = add_particles(ctx, n_vertices, x, v, vol, material, mem_kind, &first);
+  if (st != MPM_OK) return st;
+  const int grp = (int)ctx->groups.size() - 1;
+  for (int64_t t = 0; t < n_triangles; ++t)
+    ctx->cloth_tris.push_back(make_int4((int)(first + triangles[3 * t]),
+                                        (int)(first + triangles[3 * t + 1]),
+                                        (int)(first + triangles[3 * t + 2]), grp));
+  ctx->cloth_rest.insert(ctx->cloth_rest.end(), rest.begin(), rest.end());
+  // device copies (reallocated: cloth is added at setup, not per step)
+  cudaFree(ctx->cloth_tris_d);
+  cudaFree(ctx->cloth_rest_d);
+  ctx->cloth_tris_d = nullptr;
+  ctx->cloth_rest_d = nullptr;
+  CU(dalloc(&ctx->cloth_tris_d, ctx->cloth_tris.size()));
+  CU(dalloc(&ctx->cloth_rest_d, ctx->cloth_rest.size()));
+  CU(cudaMemcpy(ctx->cloth_tris_d, ctx->cloth_tris.data(), ctx->cloth_tris.size() * sizeof(int4),
+                cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(ctx->cloth_rest_d, ctx->cloth_rest.data(), ctx->cloth_rest.size() * sizeof(double),
+                cudaMemcpyHostToDevice));
+  if (!ctx->cloth_f_d) CU(dalloc(&ctx->cloth_f_d, (size_t)3 * ctx->cap));
+  if (!ctx->cloth_slot_d) CU(dalloc(&ctx->cloth_slot_d, (size_t)ctx->cap));
+  // (graphs recorded before had no cloth pass)
+  for (auto& e : ctx->gexec)
+    if (e) {
+      cudaGraphExecDestroy(e);
+      e = nullptr;
+    }
+  if (first_id) *first_id = first;
+  return MPM_OK;
+}
+
+namespace {
+mpm_status add_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v,
+                         float particle_volume, const mpm_material* mat, int32_t mem_kind,
+                         int64_t* first_id) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
   if (n < 0 || (n > 0 && (!x || !v)) || !mat || !(particle_volume > 0.f) ||
       (mem_kind != MPM_MEM_HOST && mem_kind != MPM_MEM_DEVICE))
     return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_add_particles: bad argument");
-  if (mat->model != MPM_COROTATED && mat->model != MPM_DRUCKER_PRAGER)
-    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_add_particles: unknown material model");
   if (!(mat->E > 0.f) || !(mat->nu > -1.f && mat->nu < 0.5f) || !(mat->rho > 0.f))
     return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_add_particles: bad material constants");
   if (ctx->n + n > ctx->cap) return fail(ctx, MPM_ERR_CAPACITY, "mpm_add_particles: max_particles exceeded");
@@ -760,6 +856,7 @@ mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const floa
   CU(cudaStreamSynchronize(ctx->stream));
   return MPM_OK;
 }
+}  // namespace
 
 mpm_status mpm_num_particles(const mpm_ctx* ctx, int64_t* n) {
   if (!ctx || !n) return MPM_ERR_INVALID_ARG;
@@ -1277,6 +1374,8 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
 
 mpm_status mpm_tape_begin(mpm_ctx* ctx) {
   if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (!ctx->cloth_tris.empty())
+    return fail(ctx, MPM_ERR_STATE, "mpm_tape_begin: the adjoints do not cover cloth");
   CU(cudaStreamSynchronize(ctx->stream));
   for (auto& t : ctx->tape)
     if (t.state) cudaFree(t.state);

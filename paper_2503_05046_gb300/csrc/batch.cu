@@ -209,7 +209,7 @@ mpm_status mpm_batch_create(mpm_ctx* const* ctxs, int32_t n, mpm_batch** out) {
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     const mpm_ctx* c = ctxs[i];
-    if (!c || c->taping || c->g.slot || c->device != ctxs[0]->device ||
+    if (!c || c->taping || c->g.slot || !c->cloth_tris.empty() || c->device != ctxs[0]->device ||
         c->stream != ctxs[0]->stream)
       return MPM_ERR_INVALID_ARG;
     for (int j = 0; j < i; ++j)

@@ -1,0 +1,117 @@
+// cloth.cu -- cloth as a triangle mesh of MPM particles (the paper's cloth
+// results, Sec. VI): the mesh's in-plane elasticity is a Lagrangian force on
+// the vertex particles, the corotated membrane energy per triangle
+//   psi(F) = mu |F - R|^2 + lam/2 (J - 1)^2,  F = Ds Dm^-1 (3x2),
+// R the polar factor of F (F = R S, S = sqrt(F^T F)), J = det S, times the
+// triangle's rest volume (rest area times the cloth's thickness). The forces
+// f = -dE/dx are recomputed at the start of every substep and P2G adds h f
+// to the vertices' momentum; the vertices
+// carry no stress of their own and collide (with bodies, with the cloth
+// itself, with other material) through the grid and the contact solve.
+//
+// One thread per triangle in FP64 (a few hundred operations: near rest
+// F - R is a small difference of O(1) terms, which FP32 would leave with a
+// relative error of 1e-4; GB300's FP64 rate is ample for a mesh), its three
+// forces added to the vertices' force planes with FP32 atomics.
+#include <cmath>
+
+#include "kernels.h"
+
+namespace mpmcr {
+
+namespace {
+
+__global__ void k_cloth_forces(Particles P, const int* __restrict__ slot_of,
+                               const int4* __restrict__ tris, const double* __restrict__ rest,
+                               int n_tris, const DevGroup* __restrict__ groups,
+                               float* __restrict__ f, long long stride) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tris) return;
+  const int4 tv = tris[t];
+  const int sl[3] = {slot_of[tv.x], slot_of[tv.y], slot_of[tv.z]};
+  double x[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[k][c] = (double)P.x(c)[sl[k]];
+  const double* r = rest + 5 * (size_t)t;  // Dm^-1 (2x2 row-major), rest volume
+  const double dmi[4] = {r[0], r[1], r[2], r[3]};
+  const double vol = r[4];
+  const DevGroup gr = groups[tv.w];
+  const double mu = (double)gr.mu_l, lam = (double)gr.lam;
+  double F[3][2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double d1 = x[1][c] - x[0][c], d2 = x[2][c] - x[0][c];
+    F[c][0] = d1 * dmi[0] + d2 * dmi[2];
+    F[c][1] = d1 * dmi[1] + d2 * dmi[3];
+  }
+  // C = F^T F; S = sqrt(C) = (C + sqrt(det C) I) / sqrt(tr C + 2 sqrt(det C))
+  const double c00 = F[0][0] * F[0][0] + F[1][0] * F[1][0] + F[2][0] * F[2][0];
+  const double c01 = F[0][0] * F[0][1] + F[1][0] * F[1][1] + F[2][0] * F[2][1];
+  const double c11 = F[0][1] * F[0][1] + F[1][1] * F[1][1] + F[2][1] * F[2][1];
+  const double detC = c00 * c11 - c01 * c01;
+  if (!(detC > 1e-30)) return;  // a collapsed triangle exerts no force
+  const double J = sqrt(detC);
+  const double tn = sqrt(c00 + c11 + 2.0 * J);
+  const double s00 = (c00 + J) / tn, s01 = c01 / tn, s11 = (c11 + J) / tn;
+  // R = F S^-1 (det S = J); P = 2 mu (F - R) + lam (J - 1) J F C^-1
+  const double si00 = s11 / J, si01 = -s01 / J, si11 = s00 / J;
+  const double ci00 = c11 / detC, ci01 = -c01 / detC, ci11 = c00 / detC;
+  const double kl = lam * (J - 1.0) * J;
+  double g[3][2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double r0 = F[c][0] * si00 + F[c][1] * si01, r1 = F[c][0] * si01 + F[c][1] * si11;
+    const double p0 = 2.0 * mu * (F[c][0] - r0) + kl * (F[c][0] * ci00 + F[c][1] * ci01);
+    const double p1 = 2.0 * mu * (F[c][1] - r1) + kl * (F[c][0] * ci01 + F[c][1] * ci11);
+    // dE/dDs = vol P Dm^-T
+    g[c][0] = vol * (p0 * dmi[0] + p1 * dmi[1]);
+    g[c][1] = vol * (p0 * dmi[2] + p1 * dmi[3]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float* fc = f + (size_t)c * stride;
+    atomicAdd(fc + sl[0], (float)(g[c][0] + g[c][1]));
+    atomicAdd(fc + sl[1], (float)(-g[c][0]));
+    atomicAdd(fc + sl[2], (float)(-g[c][1]));
+  }
+}
+
+}  // namespace
+
+void cloth_rest_shape(const double X0[3], const double X1[3], const double X2[3], double out[5]) {
+  // the rest edges in the triangle's own frame (t1 along the first edge, t2
+  // in its plane): Dm = [[|e1|, e2.t1], [0, e2.t2]], inverted; then the area
+  double e1[3], e2[3];
+  for (int a = 0; a < 3; ++a) {
+    e1[a] = X1[a] - X0[a];
+    e2[a] = X2[a] - X0[a];
+  }
+  const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                       e1[0] * e2[1] - e1[1] * e2[0]};
+  const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  const double l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  const double t1[3] = {e1[0] / l1, e1[1] / l1, e1[2] / l1};
+  const double u[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+  const double t2[3] = {u[1] * t1[2] - u[2] * t1[1], u[2] * t1[0] - u[0] * t1[2],
+                        u[0] * t1[1] - u[1] * t1[0]};
+  const double a00 = l1, a01 = e2[0] * t1[0] + e2[1] * t1[1] + e2[2] * t1[2];
+  const double a11 = e2[0] * t2[0] + e2[1] * t2[1] + e2[2] * t2[2];
+  out[0] = 1.0 / a00;
+  out[1] = -a01 / (a00 * a11);
+  out[2] = 0.0;
+  out[3] = 1.0 / a11;
+  out[4] = 0.5 * nn;
+}
+
+void launch_cloth_forces(const Particles& P, int n, const int* slot_of, const int4* tris,
+                         const double* rest, int n_tris, const DevGroup* groups, float* f,
+                         long long stride, cudaStream_t s) {
+  if (n > 0) cudaMemsetAsync(f, 0, 3 * (size_t)stride * sizeof(float), s);
+  if (n_tris > 0)
+    k_cloth_forces<<<(n_tris + 127) / 128, 128, 0, s>>>(P, slot_of, tris, rest, n_tris, groups, f,
+                                                         stride);
+}
+
+}  // namespace mpmcr

@@ -485,6 +485,11 @@ __device__ __forceinline__ void tau_corotated(const DevGroup& gr, const Polar& P
 // Kirchhoff stress of a given F (no plastic projection); V0 as in polar_svd.
 __device__ __forceinline__ void kirchhoff(const DevGroup& gr, const float (&F)[9], float (&t)[6],
                                           const float* V0 = nullptr, int sweeps = kSvdSweeps) {
+  if (gr.model == MPM_CLOTH) {  // stress-free particles (the mesh carries the elasticity)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) t[c] = 0.f;
+    return;
+  }
   Polar P;
   polar_svd(F, P, V0, sweeps);
   if (gr.model == MPM_DRUCKER_PRAGER) {

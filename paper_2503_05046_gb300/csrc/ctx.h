@@ -49,6 +49,15 @@ struct mpm_ctx {
   size_t n_nodes = 0;   // nodes of storage
   int n_blocks = 0;     // 4^3 blocks of the domain
   int* slot_d = nullptr;  // block-sparse grids: block -> storage block (g.slot)
+  // cloth meshes (mpm_add_cloth): triangles (particle ids, group), rest shapes
+  // (Dm^-1, area), the vertices' forces (3 planes of cap) and the particle
+  // id -> slot map they are found through
+  std::vector<int4> cloth_tris;
+  std::vector<double> cloth_rest;
+  int4* cloth_tris_d = nullptr;
+  double* cloth_rest_d = nullptr;
+  float* cloth_f_d = nullptr;
+  int* cloth_slot_d = nullptr;
   Contacts C{};
   double* red = nullptr;
   unsigned* bar = nullptr;

@@ -94,14 +94,23 @@ __device__ __forceinline__ void g2p_block(const G2PArgs& a, int block) {
     C[c] = dinv * Bm[c];
     F[c] = a.P.F(c)[i];
   }
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      Fn[3 * r + c] = F[3 * r + c] + h * (C[3 * r] * F[c] + C[3 * r + 1] * F[3 + c] + C[3 * r + 2] * F[6 + c]);
   const DevGroup gr = a.groups[a.P.grp[i]];
   float tau[6];
-  constitutive_update(gr, Fn, tau);
+  if (gr.model == MPM_CLOTH) {
+    // the mesh carries the cloth's elasticity: F stays, no stress
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Fn[c] = F[c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tau[c] = 0.f;
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        Fn[3 * r + c] =
+            F[3 * r + c] + h * (C[3 * r] * F[c] + C[3 * r + 1] * F[3 + c] + C[3 * r + 2] * F[6 + c]);
+    constitutive_update(gr, Fn, tau);
+  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     a.P.v(c)[i] = vp[c];

@@ -71,6 +71,8 @@ struct P2GArgs {
   Contacts C;
   uint32_t* status;
   DevStats* stats;
+  const float* fext;   // cloth: per-particle mesh forces, 3 planes of fext_stride (null: none)
+  long long fext_stride;
 };
 void launch_p2g(const P2GArgs& a, int chunk, cudaStream_t s);
 cudaError_t p2g_prepare();  // once per device: the kernel's shared-memory attributes
@@ -193,6 +195,16 @@ void launch_bar_in(const Particles& P, int n, const float* x, const float* v, co
                    const float* F, float* bar, cudaStream_t s);
 void launch_bar_out(const Particles& P, int n, const float* bar, float* x, float* v, float* C,
                     float* F, cudaStream_t s);
+
+// ---- cloth.cu: triangle-mesh membrane forces on cloth vertices ----
+// rest shape of a triangle from its rest vertices: Dm^-1 (2x2 row-major), area
+// (mpm_add_cloth replaces the area by the rest volume, area * thickness)
+void cloth_rest_shape(const double X0[3], const double X1[3], const double X2[3], double out[5]);
+// f (3 planes of `stride` floats, slot order) = the mesh forces at the current
+// positions; tris: (particle ids, group); rest: Dm^-1 and rest volume per triangle
+void launch_cloth_forces(const Particles& P, int n, const int* slot_of, const int4* tris,
+                         const double* rest, int n_tris, const DevGroup* groups, float* f,
+                         long long stride, cudaStream_t s);
 
 // ---- rigid.cu: the bodies' update after a time step (Eq. (3)-(4)) ----
 enum { kRigidStatic = 0, kRigidKinematic = 1, kRigidDynamic = 2 };

@@ -139,6 +139,11 @@ __device__ __forceinline__ void p2g_block(const P2GArgs& a, int block) {
         mvx = gr.mass * a.P.v(0)[i];
         mvy = gr.mass * a.P.v(1)[i];
         mvz = gr.mass * a.P.v(2)[i];
+        if (a.fext) {  // cloth: + h f
+          mvx = fmaf(h, a.fext[i], mvx);
+          mvy = fmaf(h, a.fext[a.fext_stride + i], mvy);
+          mvz = fmaf(h, a.fext[2 * a.fext_stride + i], mvz);
+        }
       }
       const int head = __ffs(peers) - 1, seg_end = 31 - __clz(peers);
       const int maxlen = __reduce_max_sync(0xffffffffu, (unsigned)(seg_end - head + 1));
@@ -203,7 +208,12 @@ __device__ __forceinline__ void p2g_block(const P2GArgs& a, int block) {
       float A[9];
 #pragma unroll
       for (int c = 0; c < 9; ++c) A[c] = gr.mass * a.P.C(c)[i] - sc * tf[c];
-      const float mvx = gr.mass * vp[0], mvy = gr.mass * vp[1], mvz = gr.mass * vp[2];
+      float mvx = gr.mass * vp[0], mvy = gr.mass * vp[1], mvz = gr.mass * vp[2];
+      if (a.fext) {  // cloth: + h f
+        mvx = fmaf(h, a.fext[i], mvx);
+        mvy = fmaf(h, a.fext[a.fext_stride + i], mvy);
+        mvz = fmaf(h, a.fext[2 * a.fext_stride + i], mvz);
+      }
 #pragma unroll
       for (int cz = 0; cz < 3; ++cz) {
         const float dz = (cz - s.fx[2]) * g.dx;

@@ -108,6 +108,8 @@ SIGNATURES = {
     "mpm_add_particles": [_vp, C.c_int64, _vp, _vp, C.c_float, C.POINTER(Material), C.c_int32,
                           _i64p],
     "mpm_num_particles": [_vp, _i64p],
+    "mpm_add_cloth": [_vp, C.c_int64, _vp, _vp, C.c_int64, _i32p, C.c_float, C.POINTER(Material),
+                      C.c_int32, _i64p],
     "mpm_set_particles": [_vp, _vp, _vp, _vp, _vp, C.c_int32],
     "mpm_get_particles": [_vp, _vp, _vp, _vp, _vp, C.c_int32],
     "mpm_set_rigid_bodies": [_vp, C.c_int32, C.POINTER(RigidBody)],
@@ -210,6 +212,22 @@ def mpm_add_particles(ctx, x, v, volume, material):
     first = C.c_int64()
     _check(ctx, lib.mpm_add_particles(ctx, n, px, pv, float(volume), C.byref(material), kx,
                                       C.byref(first)))
+    return first.value
+
+
+def mpm_add_cloth(ctx, x, v, tris, thickness, material):
+    """A triangle mesh of cloth: vertex positions / velocities [n, 3] (numpy or
+    CUDA tensors), triangles [m, 3] int (host), thickness [m]; returns the first
+    vertex's particle id."""
+    n = len(x)
+    px, kx, kx_keep = _ptr(x)
+    pv, kv, kv_keep = _ptr(v)
+    if kx != kv:
+        raise ValueError("x and v must live in the same memory")
+    t = np.ascontiguousarray(np.asarray(tris, np.int32).reshape(-1, 3))
+    first = C.c_int64()
+    _check(ctx, lib.mpm_add_cloth(ctx, n, px, pv, len(t), t.ctypes.data_as(_i32p), float(thickness),
+                                  C.byref(material), kx, C.byref(first)))
     return first.value
 
 
@@ -511,8 +529,14 @@ class Sim:
         except (ImportError, RuntimeError, AssertionError):
             self.device = None
         for g in scene["groups"]:
-            mpm_add_particles(self.ctx, np.asarray(g["x"], np.float32), np.asarray(g["v"], np.float32),
-                              g["vol"], make_material(g["material"]))
+            if "tris" in g:  # a cloth mesh
+                mpm_add_cloth(self.ctx, np.asarray(g["x"], np.float32),
+                              np.asarray(g["v"], np.float32), g["tris"], g["thickness"],
+                              make_material(g["material"]))
+            else:
+                mpm_add_particles(self.ctx, np.asarray(g["x"], np.float32),
+                                  np.asarray(g["v"], np.float32), g["vol"],
+                                  make_material(g["material"]))
         self.n_bodies = len(scene["bodies"])
         mpm_set_rigid_bodies(self.ctx, scene["bodies"])
         # the dynamics set on the current bodies (mpm_set_rigid_bodies clears them)

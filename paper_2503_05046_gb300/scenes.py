@@ -464,3 +464,64 @@ def push_cube(n_particles=65536, side=0.1, seed=SEED_BASE + 3, dx=5e-3, h=1e-4, 
     sc = {"name": "push_cube_%d" % n_particles, "grid": grid, "groups": [g], "bodies": bodies,
           "h": h, "substeps": substeps}
     return sc, target
+
+
+CLOTH = 2  # material model of cloth vertices (include/mpmcr.h MPM_CLOTH)
+
+
+def cloth_material(E=3.2e6, nu=0.4, rho=1.5e3):
+    """Cloth membrane with the E, nu and rho of the paper's cloth experiment
+    (Sec. VI); the paper gives no thickness: the sheets take 0.5 mm, which at
+    this density is 0.75 kg/m^2."""
+    return {"model": CLOTH, "E": float(E), "nu": float(nu), "rho": float(rho),
+            "friction_angle_deg": 0.0}
+
+
+def cloth_sheet(n_side, spacing, center, v0=(0.0, 0.0, 0.0), material=None, thickness=5e-4):
+    """A square sheet of n_side^2 vertices at `spacing` in the plane z =
+    center[2], two triangles per quad (diagonals alternating), as a cloth
+    particle group: its mass per vertex is rho * thickness * area / n."""
+    i, j = np.meshgrid(np.arange(n_side), np.arange(n_side), indexing="ij")
+    half = (n_side - 1) * spacing / 2.0
+    x = np.stack([center[0] - half + i.ravel() * spacing, center[1] - half + j.ravel() * spacing,
+                  np.full(n_side * n_side, center[2])], 1).astype(np.float32)
+    tris = []
+    for a in range(n_side - 1):
+        for b in range(n_side - 1):
+            v00, v10, v01, v11 = a * n_side + b, (a + 1) * n_side + b, a * n_side + b + 1, \
+                (a + 1) * n_side + b + 1
+            if (a + b) % 2 == 0:
+                tris += [(v00, v10, v11), (v00, v11, v01)]
+            else:
+                tris += [(v00, v10, v01), (v10, v11, v01)]
+    tris = np.array(tris, np.int32)
+    xd = x.astype(np.float64)
+    area = 0.5 * np.linalg.norm(np.cross(xd[tris[:, 1]] - xd[tris[:, 0]],
+                                         xd[tris[:, 2]] - xd[tris[:, 0]]), axis=1).sum()
+    n = len(x)
+    vol = float(np.float32(np.float32(thickness) * area / n))
+    return {"x": x, "v": np.tile(np.asarray(v0, np.float32), (n, 1)), "tris": tris,
+            "thickness": float(thickness), "vol": vol,
+            "material": dict(material) if material is not None else cloth_material()}
+
+
+def cloth_drape(n_side=12, spacing=4e-3, radius=0.02, sink=2e-5, h=2e-5, substeps=10,
+                mu=0.4, v0=(0.0, 0.0, -0.05)):
+    """The paper's cloth-on-rigid setting in miniature: a square sheet
+    (E = 3.2e6 Pa, nu = 0.4) caught on top of a static sphere (its centre
+    vertices `sink` inside it) above the ground, falling at 0.05 m/s; grid
+    dx = 2 spacing. The contact stiffness per contact point is scaled with the
+    vertex mass as in the batch scenes (h^2 k / m = 0.8)."""
+    dx = 2.0 * spacing
+    g = cloth_sheet(n_side, spacing, (0.0, 0.0, 2.0 * radius - sink), v0)
+    m_p = g["material"]["rho"] * g["vol"]
+    k = 0.8 * m_p / h ** 2
+    bodies = [body(HALFSPACE, mu=mu, k=k),
+              body(SPHERE, (radius, 0, 0, 0), p=(0.0, 0.0, radius), mu=mu, k=k)]
+    side = (n_side - 1) * spacing + 12 * dx
+    res = 4 * int(np.ceil((side / dx + 8) / 4))
+    rz = 4 * int(np.ceil((2.0 * radius / dx + 16) / 4))
+    grid = {"dx": dx, "res": (res, res, rz), "origin": (-res * dx / 2, -res * dx / 2, -6 * dx),
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    return {"name": "cloth_drape_%d" % len(g["x"]), "grid": grid, "groups": [g],
+            "bodies": bodies, "h": h, "substeps": substeps}

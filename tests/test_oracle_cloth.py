@@ -1,6 +1,7 @@
 """Pins of the oracle's cloth (the paper's cloth results, Sec. VI; reading: a
 corotated membrane energy per mesh triangle, psi = mu |F - R|^2 +
-lam/2 (J - 1)^2 with F = Ds Dm^-1, its forces on the vertex particles added
+lam/2 (J - 1)^2 with F = Ds Dm^-1, times the rest volume, its forces on the
+vertex particles added
 to their P2G momentum): checked against what mechanics fixes, not against its
 own formula: a rest shape has no energy or force, forces are minus the
 gradient of the energy (central differences), rigid motions change neither
@@ -31,7 +32,7 @@ def test_rest_shape_has_no_energy_or_force():
     X = _tri(1)
     dmi, area = O.cloth_rest(*X)
     assert area == pytest.approx(0.5 * np.linalg.norm(np.cross(X[1] - X[0], X[2] - X[0])))
-    e, f = O.cloth_triangle(*X, dmi, area, 1e3, 2e3)
+    e, f = O.cloth_triangle(*X, dmi, area * 1e-3, 1e3, 2e3)
     assert abs(e) < 1e-20 and np.max(np.abs(f)) < 1e-12
 
 
@@ -102,7 +103,7 @@ def test_substep_conserves_momentum_and_keeps_cloth_unstressed():
     grid = {"dx": 0.004, "res": (24, 24, 40), "origin": (-0.048, -0.048, 0.0),
             "gravity": (0.0, 0.0, 0.0), "bc_layers": 3}
     mats = [{"model": O.CLOTH, "E": 1e5, "nu": 0.3, "friction_angle_deg": 0.0}]
-    scene = {"groups": [{"x": x0, "tris": tris}]}
+    scene = {"groups": [{"x": x0, "tris": tris, "thickness": 1e-3}]}
     cloth = O.cloth_from_scene(scene)
     # stretch the sheet and give it a random velocity field
     x = x0 * np.array([1.15, 0.9, 1.0])
