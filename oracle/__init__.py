@@ -116,6 +116,7 @@ def lib(openmp=False):
                                          _dp]
         L.orc_cloth_triangle.restype = C.c_double
         L.orc_set_cloth.argtypes = [C.c_void_p, C.c_int, _ip, _dp, _dp, _ip]
+        L.orc_set_pins.argtypes = [C.c_void_p, C.c_int, _ip, _dp]
         _libs[key] = L
     return _libs[key]
 
@@ -402,6 +403,17 @@ class Sim:
         assert code == OK
         self._cloth = (tris, dmi, area, mat)
 
+    def set_pins(self, ids, v):
+        """Pinned particles (orc_set_pins): ids [k] with prescribed velocities
+        [k, 3] for the following substeps; empty ids release every pin."""
+        ids = np.ascontiguousarray(ids, np.int32).reshape(-1)
+        v = _f64(v).reshape(-1).copy()
+        assert len(v) == 3 * len(ids)
+        code = self.L.orc_set_pins(self.h, len(ids), _i(ids), _d(v))
+        if code != OK:
+            raise ValueError("orc_set_pins: bad pin set")
+        self._pins = (ids, v)
+
     def last_grid(self):
         n = self.L.orc_last_grid(self.h, 0, None, None, None, None)
         ids = np.zeros(n, np.int32)
@@ -463,6 +475,22 @@ def cloth_from_scene(scene):
             "mat": np.array(mat, np.int32)}
 
 
+def pins_from_scene(scene):
+    """The pinned particles of a scene's groups (a group's "pins": {"ids":
+    local indices, "v": [k, 3] prescribed velocities}) in global particle ids,
+    or None."""
+    ids, vel = [], []
+    offset = 0
+    for g in scene["groups"]:
+        if "pins" in g:
+            ids.append(np.asarray(g["pins"]["ids"], np.int64).reshape(-1) + offset)
+            vel.append(np.asarray(g["pins"]["v"], np.float64).reshape(-1, 3))
+        offset += len(g["x"])
+    if not ids:
+        return None
+    return np.concatenate(ids).astype(np.int32), np.concatenate(vel)
+
+
 def advance_kinematic(bodies, dt):
     """Async splitting: kinematic bodies move with their frozen velocity after a
     time step (Eq. (3)-(4)). Returns new body dicts."""
@@ -498,6 +526,9 @@ def rollout(scene, steps, S, materials=None, bodies=None, state=None, substeps=N
     cloth = cloth_from_scene(scene)
     if cloth is not None:
         sim.set_cloth(cloth)
+    pins = pins_from_scene(scene)
+    if pins is not None:
+        sim.set_pins(*pins)
     code = OK
     try:
         for n_sub in per_step[:steps]:

@@ -944,6 +944,12 @@ struct orc_sim {
   int* tri_mat;
   double* fext;
   int fext_cap;
+  /* pinned particles (orc_set_pins): ids, prescribed velocities, and their
+     positions at the start of the current substep */
+  int n_pins;
+  int* pin_ids;
+  double* pin_v;
+  double* pin_x0;
 };
 
 orc_sim* orc_create(const orc_grid* grid) {
@@ -979,8 +985,29 @@ int orc_set_cloth(orc_sim* s, int n_tris, const int* tris, const double* Dm_inv,
   return ORC_OK;
 }
 
+int orc_set_pins(orc_sim* s, int n_pins, const int* ids, const double* v) {
+  if (!s || n_pins < 0 || (n_pins > 0 && (!ids || !v))) return ORC_ERR_ARG;
+  for (int j = 0; j < n_pins; ++j) {
+    if (ids[j] < 0) return ORC_ERR_ARG;
+    for (int k = 0; k < j; ++k)
+      if (ids[k] == ids[j]) return ORC_ERR_ARG;
+  }
+  free(s->pin_ids); free(s->pin_v); free(s->pin_x0);
+  const size_t np = (size_t)(n_pins > 0 ? n_pins : 1);
+  s->n_pins = n_pins;
+  s->pin_ids = (int*)malloc(sizeof(int) * np);
+  s->pin_v = (double*)malloc(sizeof(double) * 3 * np);
+  s->pin_x0 = (double*)malloc(sizeof(double) * 3 * np);
+  if (n_pins > 0) {
+    memcpy(s->pin_ids, ids, sizeof(int) * (size_t)n_pins);
+    memcpy(s->pin_v, v, sizeof(double) * 3 * (size_t)n_pins);
+  }
+  return ORC_OK;
+}
+
 void orc_destroy(orc_sim* s) {
   if (!s) return;
+  free(s->pin_ids); free(s->pin_v); free(s->pin_x0);
   free(s->tris); free(s->tri_Dm_inv); free(s->tri_area); free(s->tri_mat); free(s->fext);
   free(s->m); free(s->p); free(s->v); free(s->dof); free(s->dof_node);
   free(s->con_p); free(s->con_b); free(s->con_gamma); free(s->con_phi0); free(s->con_n0);
@@ -1200,6 +1227,20 @@ int orc_substep(orc_sim* s, int n, double* x, double* v, double* C, double* F,
       return inf.status;
     }
   }
+  /* pinned particles enter the substep on their prescribed motion */
+  for (int j = 0; j < s->n_pins; ++j) {
+    const int q = s->pin_ids[j];
+    if (q >= n) {
+      inf.status = ORC_ERR_ARG;
+      if (info) *info = inf;
+      return inf.status;
+    }
+    for (int r = 0; r < 3; ++r) {
+      s->pin_x0[3 * j + r] = x[3 * q + r];
+      v[3 * q + r] = s->pin_v[3 * j + r];
+    }
+    for (int r = 0; r < 9; ++r) C[9 * q + r] = 0.0;
+  }
   memset(s->m, 0, s->nn * sizeof(double));
   memset(s->p, 0, 3 * s->nn * sizeof(double));
 
@@ -1227,6 +1268,9 @@ int orc_substep(orc_sim* s, int n, double* x, double* v, double* C, double* F,
       for (int k = 0; k < 3; ++k)
         for (int r = 0; r < 3; ++r) s->fext[3 * v3[k] + r] += ft[3 * k + r];
     }
+    /* a pinned vertex is held: the mesh does not push it */
+    for (int j = 0; j < s->n_pins; ++j)
+      for (int r = 0; r < 3; ++r) s->fext[3 * s->pin_ids[j] + r] = 0.0;
     fext = s->fext;
   }
 
@@ -1377,6 +1421,16 @@ int orc_substep(orc_sim* s, int n, double* x, double* v, double* C, double* F,
 #pragma omp parallel for schedule(static)
 #endif
   for (int q = 0; q < n; ++q) g2p_particle(s, q, x, v, C, F, mat, mats, h);
+
+  /* pinned particles back on their prescribed path */
+  for (int j = 0; j < s->n_pins; ++j) {
+    const int q = s->pin_ids[j];
+    for (int r = 0; r < 3; ++r) {
+      x[3 * q + r] = s->pin_x0[3 * j + r] + h * s->pin_v[3 * j + r];
+      v[3 * q + r] = s->pin_v[3 * j + r];
+    }
+    for (int r = 0; r < 9; ++r) C[9 * q + r] = 0.0;
+  }
 
   free(dm); free(dvs); free(dfix); free(vsol); free(gam);
   free(cp); free(cb); free(cn); free(cw); free(cR); free(cbias); free(cphi); free(cn0);

@@ -139,7 +139,7 @@ void orc_dp_project(const double F[9], double mu, double lam, double friction_an
    membrane energy per triangle
      psi(F) = mu |F - R|^2 + lam/2 (J - 1)^2,   F = Ds Dm^-1 (3x2),
    R the 3x2 polar factor of F (F = R S, S = sqrt(F^T F)), J = det S, times
-   the triangle's rest area; Ds = [x1 - x0, x2 - x0], Dm the rest edges in
+   the triangle's rest volume; Ds = [x1 - x0, x2 - x0], Dm the rest edges in
    the triangle's own plane. The particles carry no stress (F stays I); their
    P2G momentum gains h f_p with f_p = -dE/dx_p. Collision and self-collision
    go through the grid and the contact solve like any particle's. The energy
@@ -209,6 +209,17 @@ void orc_destroy(orc_sim* s);
    the Lame parameters of material mat_of_tri[t] (copied). */
 int orc_set_cloth(orc_sim* s, int n_tris, const int* tris, const double* Dm_inv,
                   const double* vol, const int* mat_of_tri);
+
+/* Pinned particles (the held cloth corners of the paper's cloth experiment,
+   Sec. VI: fixed by boundary conditions, moved inward, released). Reading
+   taken: a Dirichlet condition on the particle itself. A pinned particle is
+   kinematic: every substep it enters P2G with v = v_pin and C = 0 (it still
+   lends the grid its mass and momentum, and its stress if it has one), mesh
+   forces on it are dropped, and after G2P it is put back on its prescribed
+   path, x = x_start + h v_pin, v = v_pin, C = 0 (F follows G2P). Replaces the
+   pin set: particle ids[j] gets velocity v[3j..3j+2]; n_pins = 0 releases
+   every pin. Ids must be distinct. */
+int orc_set_pins(orc_sim* s, int n_pins, const int* ids, const double* v);
 
 /* Threads orc_substep uses: 1 in the serial build (the checker); the
    OpenMP build (-fopenmp, a CPU baseline over all host cores only) runs P2G

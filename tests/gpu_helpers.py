@@ -29,6 +29,9 @@ def oracle_substep(sc, gpu_state, gpu_bodies, solver, h=None):
     cloth = O.cloth_from_scene(sc)
     if cloth is not None:
         osim.set_cloth(cloth)
+    pins = O.pins_from_scene(sc)
+    if pins is not None:
+        osim.set_pins(*pins)
     bodies = O.bodies_from_scene({"bodies": gpu_bodies})
     imp = np.zeros(6 * max(len(bodies), 1))
     code, info = osim.substep(st, mats, [O.make_body(b) for b in bodies],
