@@ -227,7 +227,6 @@ mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const floa
                              float particle_volume, const mpm_material* material,
                              int32_t mem_kind, int64_t* first_id);
 
-/* Number of particles in the context. */
 /* Add a piece of cloth (the paper's cloth results, Sec. VI): a triangle mesh
    whose n_vertices vertices become particles of a new group with material
    `material` (model MPM_CLOTH; E, nu of the membrane, rho its density),
@@ -248,6 +247,22 @@ mpm_status mpm_add_cloth(mpm_ctx* ctx, int64_t n_vertices, const float* x, const
                          int64_t n_triangles, const int32_t* triangles, float thickness,
                          const mpm_material* material, int32_t mem_kind, int64_t* first_id);
 
+/* Pinned particles: Dirichlet conditions on particles (the paper's cloth
+   experiment, Sec. VI, holds the cloth's corners by boundary conditions,
+   moves them inward and releases two). Replaces the context's pin set:
+   particle ids[j] (host memory, distinct, 0 <= id < number of particles)
+   gets the prescribed velocity v[3j .. 3j+2] (m/s, host memory, finite);
+   n_pins = 0 releases every pin (ids and v may then be NULL). From the next
+   substep on, a pinned particle is kinematic: it enters each substep with
+   v = v_pin and C = 0 (lending the grid its mass and momentum, and its
+   stress if it has any), mesh forces on it are dropped, and after G2P it is
+   put back on its path, x = (x at the substep's start) + h v_pin, v = v_pin,
+   C = 0; F follows G2P. MPM_ERR_INVALID_ARG for a bad set, MPM_ERR_STATE
+   while a tape is recording; contexts with pins cannot record a tape or
+   step in a batch. Synchronises. */
+mpm_status mpm_set_pins(mpm_ctx* ctx, int64_t n_pins, const int64_t* ids, const float* v);
+
+/* Number of particles in the context. */
 mpm_status mpm_num_particles(const mpm_ctx* ctx, int64_t* n);
 
 /* Overwrite the state of all particles, in id order. Any of x, v, C, F may be
@@ -407,7 +422,8 @@ mpm_status mpm_contact_adjoint(mpm_ctx* ctx, int32_t mem_kind, int64_t n, const 
    (mpm_set_rigid_bodies) between two recorded steps breaks the chain from
    one step's end state to the next one's start, and mpm_backward then
    refuses the tape (setting them after mpm_tape_begin, before the first
-   recorded step, is fine). */
+   recorded step, is fine). The adjoints cover neither cloth nor pinned
+   particles: mpm_tape_begin returns MPM_ERR_STATE for a context with either. */
 mpm_status mpm_tape_begin(mpm_ctx* ctx);
 mpm_status mpm_tape_end(mpm_ctx* ctx);
 
@@ -560,7 +576,8 @@ typedef struct mpm_batch mpm_batch;
 
 /* Create a batch of n >= 1 members. MPM_ERR_INVALID_ARG if a member is NULL,
    repeated, on another device or stream, recording a tape, block-sparse
-   (max_blocks), or holds cloth. */
+   (max_blocks), or holds cloth or pinned particles (a batch step returns
+   MPM_ERR_STATE for a member that gained them since). */
 mpm_status mpm_batch_create(mpm_ctx* const* ctxs, int32_t n, mpm_batch** out);
 
 /* One rigid time step of every member: n_substeps substeps of size h with

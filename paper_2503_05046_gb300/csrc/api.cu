@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/mpmcr.h: context and device memory, the
 // substep schedule of one rigid time step (Eq. (3)-(4)), state I/O in particle
 // id order, diagnostics and phase timing.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
@@ -347,7 +348,7 @@ void release(mpm_ctx* c) {
                   c->adj_out, c->adj_ids, c->adj_io, c->bw_buf, c->bw_gbar, c->bw_slot, c->bw_mat,
                   c->tape_pool, c->tape_recs, c->tape_counters, c->bw_snap, c->bw_gbody, c->dyn_d,
                   c->imp0_d, c->bodies_step_d, c->G.n_mapped, c->slot_d, c->cloth_tris_d,
-                  c->cloth_rest_d, c->cloth_f_d, c->cloth_slot_d};
+                  c->cloth_rest_d, c->cloth_f_d, c->slot_of_d, c->pin_ids_d, c->pin_v_d, c->pin_x_d};
   for (auto& t : c->tape)
     if (t.state) cudaFree(t.state);
   for (void* p : ptrs)
@@ -379,11 +380,18 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
   pa.status = ctx->status; pa.stats = ctx->stats;
   pa.fext = nullptr;
   pa.fext_stride = ctx->cap;
+  if (ctx->n_pins > 0) {
+    // pinned particles enter the substep on their prescribed motion
+    mark_phase(ctx, MPM_PHASE_P2G);
+    launch_pin_init(ctx->P[cur], ctx->slot_of_d, ctx->pin_ids_d, ctx->pin_v_d, ctx->pin_x_d,
+                    ctx->n_pins, ctx->pins_cap, s);
+  }
   if (!ctx->cloth_tris.empty()) {
     // cloth: the mesh forces at the substep's start positions
     mark_phase(ctx, MPM_PHASE_P2G);
-    launch_cloth_forces(ctx->P[cur], n, ctx->cloth_slot_d, ctx->cloth_tris_d, ctx->cloth_rest_d,
+    launch_cloth_forces(ctx->P[cur], n, ctx->slot_of_d, ctx->cloth_tris_d, ctx->cloth_rest_d,
                         (int)ctx->cloth_tris.size(), ctx->groups_d, ctx->cloth_f_d, ctx->cap, s);
+    launch_pin_forces(ctx->slot_of_d, ctx->pin_ids_d, ctx->n_pins, ctx->cloth_f_d, ctx->cap, s);
     pa.fext = ctx->cloth_f_d;
   }
   if (ctx->g.slot) {
@@ -417,6 +425,8 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
     ga.C = ctx->C; ga.h = hf; ga.bar = ctx->bar; ga.red = ctx->red; ga.stats = ctx->stats;
     mark_phase(ctx, MPM_PHASE_G2P);
     launch_g2p(ga, s);
+    launch_pins(ctx->P[cur], ctx->slot_of_d, ctx->pin_ids_d, ctx->pin_v_d, ctx->pin_x_d, ctx->n_pins,
+                ctx->pins_cap, hf, s);
   }
   mark_phase(ctx, -1);
   return cudaGetLastError();
@@ -442,9 +452,9 @@ cudaError_t enqueue_step(mpm_ctx* ctx, int from, bool sort_now, int n_substeps, 
     launch_sort(ctx->g, ctx->P[cur], ctx->P[1 - cur], n, ctx->sb, s);
     cur = 1 - cur;
   }
-  // cloth triangles find their vertices through the id -> slot map of the
-  // buffer the substeps run on
-  if (!ctx->cloth_tris.empty()) launch_slot_map(ctx->P[cur], n, ctx->cloth_slot_d, s);
+  // cloth triangles and pins find their particles through the id -> slot
+  // map of the buffer the substeps run on
+  if (!ctx->cloth_tris.empty() || ctx->n_pins > 0) launch_slot_map(ctx->P[cur], n, ctx->slot_of_d, s);
   for (int k = 0; k < n_substeps; ++k) {
     const cudaError_t e = enqueue_substep(ctx, cur, nb, hf, sp, solve_blocks, true, s, ctx->taping);
     if (e != cudaSuccess) return e;
@@ -800,7 +810,7 @@ mpm_status mpm_add_cloth(mpm_ctx* ctx, int64_t n_vertices, const float* x, const
   CU(cudaMemcpy(ctx->cloth_rest_d, ctx->cloth_rest.data(), ctx->cloth_rest.size() * sizeof(double),
                 cudaMemcpyHostToDevice));
   if (!ctx->cloth_f_d) CU(dalloc(&ctx->cloth_f_d, (size_t)3 * ctx->cap));
-  if (!ctx->cloth_slot_d) CU(dalloc(&ctx->cloth_slot_d, (size_t)ctx->cap));
+  if (!ctx->slot_of_d) CU(dalloc(&ctx->slot_of_d, (size_t)ctx->cap));
   // (graphs recorded before had no cloth pass)
   for (auto& e : ctx->gexec)
     if (e) {
@@ -808,6 +818,58 @@ mpm_status mpm_add_cloth(mpm_ctx* ctx, int64_t n_vertices, const float* x, const
       e = nullptr;
     }
   if (first_id) *first_id = first;
+  return MPM_OK;
+}
+
+mpm_status mpm_set_pins(mpm_ctx* ctx, int64_t n_pins, const int64_t* ids, const float* v) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (n_pins < 0 || (n_pins > 0 && (!ids || !v)))
+    return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_pins: bad argument");
+  if (ctx->taping) return fail(ctx, MPM_ERR_STATE, "mpm_set_pins: a tape is recording");
+  std::vector<int64_t> sorted(ids, ids + n_pins);
+  std::sort(sorted.begin(), sorted.end());
+  for (int64_t j = 0; j < n_pins; ++j) {
+    if (sorted[j] < 0 || sorted[j] >= ctx->n || (j > 0 && sorted[j] == sorted[j - 1]))
+      return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_pins: ids must be distinct particle ids");
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(v[3 * j + c]))
+        return fail(ctx, MPM_ERR_INVALID_ARG, "mpm_set_pins: a velocity is not finite");
+  }
+  // the pin arrays may be in use by work in flight
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (n_pins > ctx->pins_cap) {
+    cudaFree(ctx->pin_ids_d);
+    cudaFree(ctx->pin_v_d);
+    cudaFree(ctx->pin_x_d);
+    ctx->pin_ids_d = nullptr;
+    ctx->pin_v_d = ctx->pin_x_d = nullptr;
+    ctx->pins_cap = 0;
+    CU(dalloc(&ctx->pin_ids_d, (size_t)n_pins));
+    CU(dalloc(&ctx->pin_v_d, 3 * (size_t)n_pins));
+    CU(dalloc(&ctx->pin_x_d, 3 * (size_t)n_pins));
+    ctx->pins_cap = (int)n_pins;
+  }
+  if (n_pins > 0) {
+    if (!ctx->slot_of_d) CU(dalloc(&ctx->slot_of_d, (size_t)ctx->cap));
+    std::vector<int> id32((size_t)n_pins);
+    std::vector<float> vp(3 * (size_t)ctx->pins_cap, 0.f);
+    for (int64_t j = 0; j < n_pins; ++j) {
+      id32[j] = (int)ids[j];
+      for (int c = 0; c < 3; ++c) vp[j + (size_t)c * ctx->pins_cap] = v[3 * j + c];
+    }
+    CU(cudaMemcpyAsync(ctx->pin_ids_d, id32.data(), id32.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaMemcpyAsync(ctx->pin_v_d, vp.data(), vp.size() * sizeof(float), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  ctx->n_pins = (int)n_pins;
+  // (graphs recorded before hold the old pin launches)
+  for (auto& e : ctx->gexec)
+    if (e) {
+      cudaGraphExecDestroy(e);
+      e = nullptr;
+    }
   return MPM_OK;
 }
 
@@ -1376,6 +1438,8 @@ mpm_status mpm_tape_begin(mpm_ctx* ctx) {
   if (!ctx) return MPM_ERR_INVALID_ARG;
   if (!ctx->cloth_tris.empty())
     return fail(ctx, MPM_ERR_STATE, "mpm_tape_begin: the adjoints do not cover cloth");
+  if (ctx->n_pins > 0)
+    return fail(ctx, MPM_ERR_STATE, "mpm_tape_begin: the adjoints do not cover pinned particles");
   CU(cudaStreamSynchronize(ctx->stream));
   for (auto& t : ctx->tape)
     if (t.state) cudaFree(t.state);

@@ -209,7 +209,8 @@ mpm_status mpm_batch_create(mpm_ctx* const* ctxs, int32_t n, mpm_batch** out) {
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     const mpm_ctx* c = ctxs[i];
-    if (!c || c->taping || c->g.slot || !c->cloth_tris.empty() || c->device != ctxs[0]->device ||
+    if (!c || c->taping || c->g.slot || !c->cloth_tris.empty() || c->n_pins > 0 ||
+        c->device != ctxs[0]->device ||
         c->stream != ctxs[0]->stream)
       return MPM_ERR_INVALID_ARG;
     for (int j = 0; j < i; ++j)
@@ -291,6 +292,8 @@ mpm_status mpm_batch_step(mpm_batch* batch, double h, int32_t n_substeps,
     mpm_ctx* c = batch->ctx[i];
     if (c->taping)
       return bfail(batch, MPM_ERR_STATE, "mpm_batch_step: a member is recording a tape");
+    if (!c->cloth_tris.empty() || c->n_pins > 0)
+      return bfail(batch, MPM_ERR_STATE, "mpm_batch_step: a member has cloth or pinned particles");
     const int nb = (int)c->bodies.size();
     if (c->bodies_dirty) {
       DevBody tmp[kMaxBodies];

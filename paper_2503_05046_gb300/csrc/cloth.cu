@@ -13,6 +13,13 @@
 // F - R is a small difference of O(1) terms, which FP32 would leave with a
 // relative error of 1e-4; GB300's FP64 rate is ample for a mesh), its three
 // forces added to the vertices' force planes with FP32 atomics.
+//
+// Pinned particles (the held cloth corners of the same experiment): a
+// Dirichlet condition on the particle. A pinned particle enters every
+// substep with its prescribed velocity and C = 0 (its start position kept),
+// the mesh forces on it are dropped, and after G2P it is put back on its
+// path, x = x_start + h v_pin (F follows G2P). One thread per pin, through
+// the id -> slot map.
 #include <cmath>
 
 #include "kernels.h"
@@ -78,6 +85,46 @@ __global__ void k_cloth_forces(Particles P, const int* __restrict__ slot_of,
   }
 }
 
+__global__ void k_pin_init(Particles P, const int* __restrict__ slot_of, const int* __restrict__ ids,
+                           const float* __restrict__ v_pin, float* __restrict__ x_pin, int n_pins,
+                           int cap) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_pins) return;
+  const int sl = slot_of[ids[j]];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    x_pin[j + c * cap] = P.x(c)[sl];
+    P.v(c)[sl] = v_pin[j + c * cap];
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) P.C(c)[sl] = 0.f;
+}
+
+__global__ void k_pin_forces(const int* __restrict__ slot_of, const int* __restrict__ ids, int n_pins,
+                             float* __restrict__ f, long long stride) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_pins) return;
+  const int sl = slot_of[ids[j]];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) f[(size_t)c * stride + sl] = 0.f;
+}
+
+__global__ void k_pins(Particles P, const int* __restrict__ slot_of, const int* __restrict__ ids,
+                       const float* __restrict__ v_pin, const float* __restrict__ x_pin, int n_pins,
+                       int cap, float h) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_pins) return;
+  const int sl = slot_of[ids[j]];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float vp = v_pin[j + c * cap];
+    P.x(c)[sl] = fmaf(h, vp, x_pin[j + c * cap]);
+    P.v(c)[sl] = vp;
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) P.C(c)[sl] = 0.f;
+}
+
 }  // namespace
 
 void cloth_rest_shape(const double X0[3], const double X1[3], const double X2[3], double out[5]) {
@@ -112,6 +159,23 @@ void launch_cloth_forces(const Particles& P, int n, const int* slot_of, const in
   if (n_tris > 0)
     k_cloth_forces<<<(n_tris + 127) / 128, 128, 0, s>>>(P, slot_of, tris, rest, n_tris, groups, f,
                                                          stride);
+}
+
+void launch_pin_init(const Particles& P, const int* slot_of, const int* ids, const float* v_pin,
+                     float* x_pin, int n_pins, int cap, cudaStream_t s) {
+  if (n_pins > 0)
+    k_pin_init<<<(n_pins + 127) / 128, 128, 0, s>>>(P, slot_of, ids, v_pin, x_pin, n_pins, cap);
+}
+
+void launch_pin_forces(const int* slot_of, const int* ids, int n_pins, float* f, long long stride,
+                       cudaStream_t s) {
+  if (n_pins > 0) k_pin_forces<<<(n_pins + 127) / 128, 128, 0, s>>>(slot_of, ids, n_pins, f, stride);
+}
+
+void launch_pins(const Particles& P, const int* slot_of, const int* ids, const float* v_pin,
+                 const float* x_pin, int n_pins, int cap, float h, cudaStream_t s) {
+  if (n_pins > 0)
+    k_pins<<<(n_pins + 127) / 128, 128, 0, s>>>(P, slot_of, ids, v_pin, x_pin, n_pins, cap, h);
 }
 
 }  // namespace mpmcr

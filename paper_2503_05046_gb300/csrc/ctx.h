@@ -50,14 +50,21 @@ struct mpm_ctx {
   int n_blocks = 0;     // 4^3 blocks of the domain
   int* slot_d = nullptr;  // block-sparse grids: block -> storage block (g.slot)
   // cloth meshes (mpm_add_cloth): triangles (particle ids, group), rest shapes
-  // (Dm^-1, area), the vertices' forces (3 planes of cap) and the particle
-  // id -> slot map they are found through
+  // (Dm^-1, rest volume) and the vertices' forces (3 planes of cap)
   std::vector<int4> cloth_tris;
   std::vector<double> cloth_rest;
   int4* cloth_tris_d = nullptr;
   double* cloth_rest_d = nullptr;
   float* cloth_f_d = nullptr;
-  int* cloth_slot_d = nullptr;
+  // pinned particles (mpm_set_pins): ids, prescribed velocities (3 planes of
+  // pins_cap) and positions on their paths (3 planes of pins_cap)
+  int n_pins = 0;
+  int pins_cap = 0;
+  int* pin_ids_d = nullptr;
+  float* pin_v_d = nullptr;
+  float* pin_x_d = nullptr;
+  // particle id -> slot map of the buffer the substeps run on (cloth, pins)
+  int* slot_of_d = nullptr;
   Contacts C{};
   double* red = nullptr;
   unsigned* bar = nullptr;

@@ -205,6 +205,17 @@ void cloth_rest_shape(const double X0[3], const double X1[3], const double X2[3]
 void launch_cloth_forces(const Particles& P, int n, const int* slot_of, const int4* tris,
                          const double* rest, int n_tris, const DevGroup* groups, float* f,
                          long long stride, cudaStream_t s);
+// pinned particles: ids[j] (found through slot_of) with prescribed velocity
+// (v_pin[j + c * cap]) and the substep's start position (x_pin[j + c * cap]).
+// init, at the substep's start: x_pin = the particle's x; its v = v_pin, C = 0
+void launch_pin_init(const Particles& P, const int* slot_of, const int* ids, const float* v_pin,
+                     float* x_pin, int n_pins, int cap, cudaStream_t s);
+// the mesh forces on pinned vertices dropped (f: 3 planes of stride)
+void launch_pin_forces(const int* slot_of, const int* ids, int n_pins, float* f, long long stride,
+                       cudaStream_t s);
+// after G2P: the particle's x = x_pin + h v_pin, v = v_pin, C = 0
+void launch_pins(const Particles& P, const int* slot_of, const int* ids, const float* v_pin,
+                 const float* x_pin, int n_pins, int cap, float h, cudaStream_t s);
 
 // ---- rigid.cu: the bodies' update after a time step (Eq. (3)-(4)) ----
 enum { kRigidStatic = 0, kRigidKinematic = 1, kRigidDynamic = 2 };

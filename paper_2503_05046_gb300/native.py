@@ -110,6 +110,7 @@ SIGNATURES = {
     "mpm_num_particles": [_vp, _i64p],
     "mpm_add_cloth": [_vp, C.c_int64, _vp, _vp, C.c_int64, _i32p, C.c_float, C.POINTER(Material),
                       C.c_int32, _i64p],
+    "mpm_set_pins": [_vp, C.c_int64, _i64p, _fp],
     "mpm_set_particles": [_vp, _vp, _vp, _vp, _vp, C.c_int32],
     "mpm_get_particles": [_vp, _vp, _vp, _vp, _vp, C.c_int32],
     "mpm_set_rigid_bodies": [_vp, C.c_int32, C.POINTER(RigidBody)],
@@ -229,6 +230,20 @@ def mpm_add_cloth(ctx, x, v, tris, thickness, material):
     _check(ctx, lib.mpm_add_cloth(ctx, n, px, pv, len(t), t.ctypes.data_as(_i32p), float(thickness),
                                   C.byref(material), kx, C.byref(first)))
     return first.value
+
+
+def mpm_set_pins(ctx, ids, v):
+    """Pinned particles: ids [k] (host) with prescribed velocities [k, 3]; an
+    empty set releases every pin."""
+    ids = np.ascontiguousarray(np.asarray(ids, np.int64).reshape(-1))
+    v = np.ascontiguousarray(np.asarray(v, np.float32).reshape(-1, 3))
+    if len(v) != len(ids):
+        raise ValueError("one velocity per pinned particle")
+    if len(ids) == 0:
+        _check(ctx, lib.mpm_set_pins(ctx, 0, None, None))
+        return
+    _check(ctx, lib.mpm_set_pins(ctx, len(ids), ids.ctypes.data_as(_i64p),
+                                 v.ctypes.data_as(_fp)))
 
 
 def mpm_num_particles(ctx):
@@ -537,6 +552,14 @@ class Sim:
                 mpm_add_particles(self.ctx, np.asarray(g["x"], np.float32),
                                   np.asarray(g["v"], np.float32), g["vol"],
                                   make_material(g["material"]))
+        pins, offset = ([], []), 0
+        for g in scene["groups"]:
+            if "pins" in g:  # pinned particles of the group (local ids)
+                pins[0].append(np.asarray(g["pins"]["ids"], np.int64).reshape(-1) + offset)
+                pins[1].append(np.asarray(g["pins"]["v"], np.float32).reshape(-1, 3))
+            offset += len(g["x"])
+        if pins[0]:
+            mpm_set_pins(self.ctx, np.concatenate(pins[0]), np.concatenate(pins[1]))
         self.n_bodies = len(scene["bodies"])
         mpm_set_rigid_bodies(self.ctx, scene["bodies"])
         # the dynamics set on the current bodies (mpm_set_rigid_bodies clears them)
@@ -583,6 +606,9 @@ class Sim:
         given = [a for a in (x, v, Cm, F) if a is not None]
         kind = MEM_HOST if not given or isinstance(given[0], np.ndarray) else MEM_DEVICE
         mpm_get_particles(self.ctx, x, v, Cm, F, mem_kind=kind)
+
+    def set_pins(self, ids, v):
+        mpm_set_pins(self.ctx, ids, v)
 
     def set_bodies(self, bodies):
         """Replace the bodies; like mpm_set_rigid_bodies this clears every

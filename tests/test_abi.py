@@ -77,6 +77,7 @@ def test_argument_validation_without_device(lib):
     assert native.lib.mpm_set_material(None, 0, None) == native.ERR_INVALID_ARG
     assert native.lib.mpm_add_cloth(None, 3, None, None, 1, None, 1e-3, None, native.MEM_HOST,
                                     None) == native.ERR_INVALID_ARG
+    assert native.lib.mpm_set_pins(None, 0, None, None) == native.ERR_INVALID_ARG
     assert native.lib.mpm_destroy(None) == native.OK
     assert native.lib.mpm_last_error(None) == b"invalid mpm context"
     # batches: bad handles and member lists are refused before any device work

@@ -78,6 +78,45 @@ def test_cloth_substeps_match_the_oracle(native):
     sim.close()
 
 
+def _pinned_drape(n_side=13):
+    # the cradle of the paper's cloth experiment in miniature: the drape
+    # sheet held at its four corners, one of them moving inward
+    sc = scenes.cloth_drape(n_side=n_side, v0=(0.0, 0.0, 0.0))
+    n = n_side
+    corners = [0, n - 1, n * (n - 1), n * n - 1]
+    v = np.zeros((4, 3), np.float32)
+    v[3] = (-0.05, -0.05, 0.02)
+    sc["groups"][0]["pins"] = {"ids": corners, "v": v}
+    return sc, np.array(corners), v
+
+
+def test_pinned_cloth_substeps_match_the_oracle(native):
+    sc, corners, vp = _pinned_drape()
+    sim = native.Sim(sc)
+    sgpu = native.solver_params(**SOLVER_GPU)
+    h = sc["h"]
+    x_c = sim.get_particles()["x"][corners].astype(np.float64)
+    for k in range(4):
+        st = sim.get_particles()
+        ost, info, osim, oimp, code = oracle_substep(sc, st, sim.bodies(), SOLVER_ORC)
+        assert code == O.OK
+        stats = sim.step(n_substeps=1, solver=sgpu)
+        out = sim.get_particles()
+        assert stats.contacts_max == info.n_contacts > 0
+        assert rel_linf(out["v"], ost["v"]) < 1e-5
+        assert np.max(np.abs(out["x"] - ost["x"])) < 1e-7
+        # the pins: on their prescribed paths, C = 0
+        x_c = x_c + h * vp
+        assert np.max(np.abs(out["x"][corners] - x_c)) < 1e-8
+        assert np.array_equal(out["v"][corners], vp)
+        assert not np.any(out["C"][corners])
+    # released: the corners fall with the rest of the sheet
+    sim.set_pins([], np.zeros((0, 3)))
+    sim.step(n_substeps=20, solver=native.solver_params(eps_r=1e-4, max_iters=2000))
+    assert np.all(sim.get_particles()["v"][corners[:3], 2] < -1e-3)
+    sim.close()
+
+
 def test_cloth_drape_is_stable(native):
     sc = scenes.cloth_drape(n_side=24, spacing=4e-3, v0=(0.0, 0.0, -0.2))
     sim = native.Sim(sc)
@@ -111,8 +150,23 @@ def test_cloth_refusals(native):
         sim.tape_begin()  # the adjoints do not cover cloth
     with pytest.raises(native.MpmError):
         native.mpm_batch_create([sim.ctx])
+    with pytest.raises(native.MpmError):
+        sim.set_pins([1, 1], np.zeros((2, 3)))
+    with pytest.raises(native.MpmError):
+        sim.set_pins([sim.n], np.zeros((1, 3)))
     g = sc["groups"][0]
     bad = np.array([[0, 1, 99]], np.int32)
     with pytest.raises(native.MpmError):
         native.mpm_add_cloth(sim.ctx, g["x"], g["v"], bad, 1e-3, native.make_material(g["material"]))
+    sim.close()
+    # pins on plain particles: no tape, no batch
+    sim = native.Sim(scenes.cube_drop(n_side=8))
+    sim.set_pins([0, 5], np.zeros((2, 3)))
+    with pytest.raises(native.MpmError):
+        sim.tape_begin()
+    with pytest.raises(native.MpmError):
+        native.mpm_batch_create([sim.ctx])
+    sim.set_pins([], np.zeros((0, 3)))
+    sim.tape_begin()
+    sim.tape_end()
     sim.close()
