@@ -117,6 +117,60 @@ def test_pinned_cloth_substeps_match_the_oracle(native):
     sim.close()
 
 
+def test_box_bagging_step_matches_the_oracle(native):
+    """The cloth cradle (corners pinned) with the dynamic 8 cm box coming
+    down on it at 5 cm/s and sliding at 2 cm/s. Each of the step's 10
+    substeps (the box frozen) from the GPU's own state against the oracle's;
+    then one whole step of the library, whose rigid step (Eq. (3)) moves the
+    box with the step's impulses, against the oracle's rollout of the same
+    step."""
+    sc, dyn = scenes.box_bagging()
+    sc["bodies"][1]["v"] = np.array([0.02, 0.0, -0.05])
+    sgpu = native.solver_params(**SOLVER_GPU)
+    sim = native.Sim(sc)
+    bodies = sim.bodies()
+    contacts = 0
+    for k in range(sc["substeps"]):
+        st = sim.get_particles()
+        ost, info, osim, oimp, code = oracle_substep(sc, st, bodies, SOLVER_ORC)
+        assert code == O.OK
+        sim.impulses(reset=True)
+        stats = sim.step(n_substeps=1, solver=sgpu)
+        sim.set_bodies(bodies)  # frozen for the whole step (no rigid update here)
+        out = sim.get_particles()
+        assert stats.contacts_max == info.n_contacts
+        contacts = max(contacts, info.n_contacts)
+        assert rel_linf(out["v"], ost["v"]) < 1e-5, k
+        assert np.max(np.abs(out["x"] - ost["x"])) < 1e-7
+        if info.n_contacts:
+            imp = sim.impulses()
+            iscale = np.max(np.abs(oimp[:, :3]))
+            assert np.max(np.abs(imp[:, :3] - oimp[:, :3])) < 1e-4 * iscale
+    assert contacts > 20
+    sim.close()
+
+    sim = native.Sim(sc)
+    sim.set_dynamics(1, dyn)
+    st = sim.get_particles()
+    sim.step(solver=sgpu)
+    gb = sim.bodies()
+    cur, imp_total = st, np.zeros((len(bodies), 6))
+    for k in range(sc["substeps"]):
+        ost, info, osim, oimp, code = oracle_substep(sc, cur, bodies, SOLVER_ORC)
+        assert code == O.OK
+        imp_total += oimp
+        cur = {key: ost[key].astype(np.float32) for key in ("x", "v", "C", "F")}
+    dt = sc["h"] * sc["substeps"]
+    ob = O.rigid_dynamics_step(O.bodies_from_scene({"bodies": bodies})[1], dyn,
+                               sc["grid"]["gravity"], imp_total[1], dt)
+    dv_scale = np.linalg.norm(np.asarray(ob["v"]) - np.asarray(bodies[1]["v"]))
+    assert np.max(np.abs(np.asarray(gb[1]["v"]) - ob["v"])) <= 1e-4 * dv_scale + 1e-7
+    assert np.max(np.abs(np.asarray(gb[1]["p"]) - ob["p"])) < 1e-7
+    # the cloth pushed back: the box gained less downward speed than in free fall
+    assert gb[1]["v"][2] > bodies[1]["v"][2] - 9.81 * dt
+    sim.close()
+
+
 def test_cloth_drape_is_stable(native):
     sc = scenes.cloth_drape(n_side=24, spacing=4e-3, v0=(0.0, 0.0, -0.2))
     sim = native.Sim(sc)
