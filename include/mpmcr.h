@@ -519,7 +519,13 @@ mpm_status mpm_synchronize(mpm_ctx* ctx);
    device-wide barriers (default 4096; 0: always the cooperative launch).
    MPM_OPT_CLUSTER_BLOCKS: thread blocks (SMs) in that cluster, a power of two
    up to the largest the device schedules (0, the default: the largest, 16 on
-   GB300). */
+   GB300).
+   MPM_OPT_P2G_FORM: how a warp combines the contributions of particles that
+   share a cell: MPM_P2G_GATHER (0, the default; lane j sums node j of a
+   cell's stencil over the cell's particles, fastest at several particles per
+   cell) or MPM_P2G_SCATTER (1; each lane computes its own particle's 27
+   contributions and lanes of one cell combine them by shuffles, fastest at
+   about one particle per cell). Same results up to rounding order. */
 enum {
   MPM_OPT_PROFILE = 1,
   MPM_OPT_SORT_EVERY = 2,
@@ -529,8 +535,10 @@ enum {
   MPM_OPT_TEST_BARRIER_TIMEOUT = 6,
   MPM_OPT_TAPE_SOLUTIONS = 7,
   MPM_OPT_CLUSTER_CONTACTS = 8,
-  MPM_OPT_CLUSTER_BLOCKS = 9
+  MPM_OPT_CLUSTER_BLOCKS = 9,
+  MPM_OPT_P2G_FORM = 10
 };
+enum { MPM_P2G_GATHER = 0, MPM_P2G_SCATTER = 1 };
 mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value);
 
 /* Phases timed when profiling is on. */

@@ -400,7 +400,7 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
     launch_sparse_map(ctx->g, ctx->G, ctx->P[cur], n, ctx->slot_d, ctx->status, ctx->num_sms, s);
   }
   mark_phase(ctx, MPM_PHASE_P2G);
-  launch_p2g(pa, ctx->p2g_chunk, s);
+  launch_p2g(pa, ctx->p2g_chunk, ctx->p2g_form, s);
   mark_phase(ctx, MPM_PHASE_GRID);
   launch_grid(ctx->g, ctx->G, hf, ctx->num_sms, ctx->stats, s);
   if (warm_rec >= 0 && ctx->tape_pool)
@@ -1118,6 +1118,7 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
     k.sort_now = sort_now ? 1 : 0; k.solve_blocks = solve_blocks; k.h = hf; k.sp = sp;
     k.cluster_max = cluster_contacts(ctx);
     k.cluster_blocks = ctx->cluster_blocks;
+    k.p2g_form = ctx->p2g_form;
     k.rigid = dev_rigid ? 1 : 0;
     k.taping = ctx->taping && ctx->tape_pool ? 1 : 0;
     k.tape_pool = ctx->tape_pool;
@@ -1126,7 +1127,7 @@ mpm_status mpm_step(mpm_ctx* ctx, double h, int32_t n_substeps, const mpm_solver
                       o.chunk == k.chunk && o.sort_now == k.sort_now &&
                       o.solve_blocks == k.solve_blocks && o.h == k.h && o.taping == k.taping &&
                       o.cluster_max == k.cluster_max && o.cluster_blocks == k.cluster_blocks &&
-                      o.rigid == k.rigid &&
+                      o.rigid == k.rigid && o.p2g_form == k.p2g_form &&
                       o.tape_pool == k.tape_pool &&
                       memcmp(&o.sp, &k.sp, sizeof(k.sp)) == 0;
     if (!same) {
@@ -1839,6 +1840,11 @@ mpm_status mpm_set_option(mpm_ctx* ctx, int32_t option, int64_t value) {
       return MPM_OK;
     case MPM_OPT_GRAPHS:
       ctx->use_graphs = value != 0;
+      return MPM_OK;
+    case MPM_OPT_P2G_FORM:
+      if (value != MPM_P2G_GATHER && value != MPM_P2G_SCATTER)
+        return fail(ctx, MPM_ERR_INVALID_ARG, "P2G form must be MPM_P2G_GATHER or MPM_P2G_SCATTER");
+      ctx->p2g_form = (int)value;
       return MPM_OK;
     case MPM_OPT_TEST_BARRIER_TIMEOUT:
       ctx->wait_test = value != 0;

@@ -84,6 +84,7 @@ struct mpm_ctx {
     int n_substeps = 0, nb = 0, chunk = 0, sort_now = 0, solve_blocks = 0, taping = 0;
     int cluster_max = 0;
     int cluster_blocks = 0;
+    int p2g_form = 0;
     int rigid = 0;
     const void* tape_pool = nullptr;  // baked into the launches when taping
     float h = 0.f;
@@ -94,6 +95,7 @@ struct mpm_ctx {
   bool wait_test = false;    // MPM_OPT_TEST_BARRIER_TIMEOUT
   int sort_every = 1;
   int p2g_chunk = 256;
+  int p2g_form = 0;  // MPM_P2G_GATHER / MPM_P2G_SCATTER
   int64_t step_count = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, cudaEvent_t>> ev_marks;  // (phase starting at this event, event)

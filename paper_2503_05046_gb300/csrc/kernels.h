@@ -74,7 +74,8 @@ struct P2GArgs {
   const float* fext;   // cloth: per-particle mesh forces, 3 planes of fext_stride (null: none)
   long long fext_stride;
 };
-void launch_p2g(const P2GArgs& a, int chunk, cudaStream_t s);
+// form: MPM_P2G_GATHER or MPM_P2G_SCATTER
+void launch_p2g(const P2GArgs& a, int chunk, int form, cudaStream_t s);
 cudaError_t p2g_prepare();  // once per device: the kernel's shared-memory attributes
 
 // ---- grid.cu: active-block compaction and grid update ----

@@ -3,20 +3,27 @@
 // (Sec. V-B: one contact point per particle inside a rigid geometry, at the
 // start of the substep).
 //
-// GB300 layout: each warp takes a contiguous run of 32 x ITEMS cell-sorted
-// particles and accumulates their mass and momentum into a private
-// shared-memory tile of the bounding box of their stencils (one float4
-// (m, p) per node). Lanes whose particles share a base cell (adjacent after
-// the cell-ordered sort) first combine their 27 node contributions with a
-// segmented shuffle reduction (the warp-level pre-reduction of Sec. V-A);
-// the remaining lanes have distinct base cells, so within one node offset
-// they touch distinct nodes and update the private tile with plain
-// read-modify-write, no atomics. The tile is then flushed with one 16-byte
-// vector reduction (red.global.add.v4.f32) per touched node. A warp whose box
-// exceeds its tile (the Morton order jumps at a coarse cell boundary, or the
-// run straddles the edge of the material) reduces straight into the grid.
+// Two forms of the warp's work (MPM_OPT_P2G_FORM), same results up to
+// rounding order:
+//
+// Gather (the default, k_p2g_g): the warp stages its particles' transfer
+// data in shared memory and lane j sums node j of a cell's 27-node stencil
+// over the particles of that cell, into a window of the 6^3 nodes one 4^3
+// block's stencils reach, flushed with one red.global.add.v4.f32 per touched
+// node when the walk leaves the block (details at p2g_gather_block).
+//
+// Scatter (k_p2g): each warp takes a contiguous run of 32 x ITEMS
+// cell-sorted particles and accumulates their mass and momentum into a
+// private shared-memory tile of the bounding box of their stencils. Lanes
+// whose particles share a base cell first combine their 27 node
+// contributions with a segmented shuffle reduction (the warp-level
+// pre-reduction of Sec. V-A); the remaining lanes have distinct base cells,
+// so within one node offset they touch distinct nodes and update the tile
+// with plain read-modify-write. A warp whose box exceeds its tile reduces
+// straight into the grid.
+//
 // The Kirchhoff stress comes precomputed from the previous G2P, so no SVD
-// runs here. Particle planes are read with coalesced 4-byte loads.
+// runs here.
 #include "kernels.h"
 
 namespace mpmcr {
@@ -319,40 +326,295 @@ __device__ __forceinline__ void p2g_block(const P2GArgs& a, int block) {
   }
 }
 
+// ---- node-parallel gather form ----
+// The warp stages its 32 particles' transfer data in shared memory and walks
+// them in cell order. Lane j < 27 owns node j of the current cell's 27-node
+// stencil and adds w_jp (m_p, b_p - A'_p c_j) for every particle of the
+// cell's run, with b = m v (+ h f_ext) + A' f, A' = -dx (m C - h 4/dx^2 V tau),
+// f the particle's position in its base cell and c_j the node's offset from
+// the base (so that b - A' c = m v + A (x_j - x_p)). The particle's data come
+// by broadcast loads, its nine B-spline weights by three per-lane loads; no
+// shuffle reduction, and the lanes of one update hold distinct nodes.
+// A run's sums go into the warp's window: the 6^3 nodes that the stencils of
+// one 4^3 block's cells reach; the window is flushed to the grid (one vector
+// reduction per touched node) when the walk enters another block.
+constexpr int kWin = 216;     // 6^3 nodes of a block's stencils
+constexpr int kRecRows = 6;   // float4 rows of a particle record
+constexpr size_t kGatherSmem = sizeof(float4) * kWarps * (kWin + kRecRows * 32);
+
+// the window of block (bx, by, bz) to the grid; the window is zero afterwards.
+// hi*: the block's stencils reach into the next block along that axis.
+__device__ __forceinline__ void flush_window(const P2GArgs& a, const GridDev& g, float4* win,
+                                             int lane, int bx, int by, int bz, bool hx, bool hy,
+                                             bool hz) {
+  for (int t = lane; t < kWin; t += 32) {
+    const float4 q = win[t];
+    if (q.x != 0.0f || q.y != 0.0f || q.z != 0.0f || q.w != 0.0f) {
+      const int lz = t / 36, r = t - 36 * lz, ly = r / 6, lx = r - 6 * ly;
+      red_add_v4(a.G.mp + node_index(g, 4 * bx + lx, 4 * by + ly, 4 * bz + lz), q.x, q.y, q.z, q.w);
+      win[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  // the (up to 8) blocks the window's stencils reach (a sparse grid marked
+  // them before P2G)
+  if (!g.slot && lane < 8) {
+    const int ox = lane & 1, oy = (lane >> 1) & 1, oz = lane >> 2;
+    if ((!ox || hx) && (!oy || hy) && (!oz || hz))
+      a.G.mark[((bz + oz) * g.nby + (by + oy)) * g.nbx + (bx + ox)] = 1;
+  }
+  __syncwarp();
+}
+
+template <int ITEMS>
+__device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
+  extern __shared__ float4 s_dyn[];
+  __shared__ DevBody s_body[kMaxBodies];
+  const GridDev& g = a.g;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int first = (block * kWarps + warp) * 32 * ITEMS;
+  float4* win = s_dyn + warp * kWin;
+  float4* rec = s_dyn + kWarps * kWin + warp * (kRecRows * 32);  // [kRecRows][32]
+  const float* recf = reinterpret_cast<const float*>(rec);
+
+  for (int i = tid; i < a.nb * (int)(sizeof(DevBody) / 4); i += kThreads)
+    reinterpret_cast<float*>(s_body)[i] = reinterpret_cast<const float*>(a.bodies)[i];
+  for (int t = lane; t < kWin; t += 32) win[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  if (first >= a.n) return;
+  const float h = a.h;
+  const float dinv = 4.0f * g.inv_dx * g.inv_dx;
+
+  // this lane's node of a stencil: offsets c, the window offset of a block's
+  // cell (0,0,0), and the float offsets of its three weights in a record
+  const bool node_lane = lane < 27;
+  const int oc0 = lane % 3, oc1 = (lane / 3) % 3, oc2 = min(lane / 9, 2);
+  const float nc0 = -(float)oc0, nc1 = -(float)oc1, nc2 = -(float)oc2;
+  const int woff_node = (oc2 * 6 + oc1) * 6 + oc0;
+  // weight e = 3 axis + c at row 3 + (e + 1) / 4, component (e + 1) % 4
+  const int e0 = oc0, e1 = 3 + oc1, e2 = 6 + oc2;
+  const int wf0 = ((3 + (e0 + 1) / 4) * 32) * 4 + ((e0 + 1) & 3);
+  const int wf1 = ((3 + (e1 + 1) / 4) * 32) * 4 + ((e1 + 1) & 3);
+  const int wf2 = ((3 + (e2 + 1) / 4) * 32) * 4 + ((e2 + 1) & 3);
+
+  int wb = -1, wbx = 0, wby = 0, wbz = 0;  // the window's block
+  bool whx = false, why = false, whz = false;
+#pragma unroll 1
+  for (int it = 0; it < ITEMS; ++it) {
+    const int i = first + it * 32 + lane;
+    int key = -1, bkey = -1, base[3] = {0, 0, 0};
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0, r4 = r0, r5 = r0;
+    float xp[3] = {0.f, 0.f, 0.f};
+    bool valid = false;
+    if (i < a.n) {
+      Stencil st;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) xp[c] = a.P.x(c)[i];
+      stencil(g, xp[0], xp[1], xp[2], st);
+      if (!stencil_inside(g, st)) {
+        atomicOr(a.status, kStOutOfDomain);
+      } else {
+        valid = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) base[c] = st.base[c];
+        key = (base[2] * g.nby * 4 + base[1]) * (g.nbx * 4) + base[0];
+        bkey = ((base[2] >> 2) * g.nby + (base[1] >> 2)) * g.nbx + (base[0] >> 2);
+        const DevGroup gr = a.groups[a.P.grp[i]];
+        float tau[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) tau[c] = a.P.tau(c)[i];
+        // A' = -dx (m C - h (4/dx^2) V tau); b = m v (+ h f_ext) + A' f
+        const float sc = h * dinv * gr.vol;
+        const float tf[9] = {tau[0], tau[3], tau[4], tau[3], tau[1], tau[5], tau[4], tau[5], tau[2]};
+        float A[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) A[c] = -g.dx * (gr.mass * a.P.C(c)[i] - sc * tf[c]);
+        float mv[3] = {gr.mass * a.P.v(0)[i], gr.mass * a.P.v(1)[i], gr.mass * a.P.v(2)[i]};
+        if (a.fext) {  // cloth: + h f
+#pragma unroll
+          for (int c = 0; c < 3; ++c) mv[c] = fmaf(h, a.fext[c * a.fext_stride + i], mv[c]);
+        }
+        float b[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          b[c] = fmaf(A[3 * c], st.fx[0], fmaf(A[3 * c + 1], st.fx[1], fmaf(A[3 * c + 2], st.fx[2], mv[c])));
+        r0 = make_float4(b[0], b[1], b[2], gr.mass);
+        r1 = make_float4(A[0], A[1], A[2], A[3]);
+        r2 = make_float4(A[4], A[5], A[6], A[7]);
+        r3 = make_float4(A[8], st.w[0][0], st.w[0][1], st.w[0][2]);
+        r4 = make_float4(st.w[1][0], st.w[1][1], st.w[1][2], st.w[2][0]);
+        r5 = make_float4(st.w[2][1], st.w[2][2], 0.f, 0.f);
+      }
+    }
+    rec[lane] = r0;
+    rec[32 + lane] = r1;
+    rec[64 + lane] = r2;
+    rec[96 + lane] = r3;
+    rec[128 + lane] = r4;
+    rec[160 + lane] = r5;
+    __syncwarp();
+    // runs of equal base cell (contiguous in cell order; any order is
+    // correct, with more runs); invalid lanes carry key -1
+    for (int p = 0; p < 32;) {
+      const int kp = __shfl_sync(0xffffffffu, key, p);
+      const unsigned eq = __ballot_sync(0xffffffffu, key == kp) >> p;
+      const int len = ~eq == 0u ? 32 - p : __ffs(~eq) - 1;
+      if (kp >= 0) {
+        const int b0 = __shfl_sync(0xffffffffu, base[0], p), b1 = __shfl_sync(0xffffffffu, base[1], p),
+                  b2 = __shfl_sync(0xffffffffu, base[2], p);
+        const int kb = __shfl_sync(0xffffffffu, bkey, p);
+        if (kb != wb) {
+          if (wb >= 0) flush_window(a, g, win, lane, wbx, wby, wbz, whx, why, whz);
+          wb = kb;
+          wbx = b0 >> 2;
+          wby = b1 >> 2;
+          wbz = b2 >> 2;
+          whx = why = whz = false;
+        }
+        const int l0 = b0 & 3, l1 = b1 & 3, l2 = b2 & 3;
+        whx |= l0 >= 2;
+        why |= l1 >= 2;
+        whz |= l2 >= 2;
+        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+        const int pe = p + len;
+#pragma unroll 1
+        for (int q = p; q < pe; ++q) {
+          const float4 q0 = rec[q], q1 = rec[32 + q], q2 = rec[64 + q];
+          const float a8 = recf[(96 + q) * 4];
+          const float w = recf[wf0 + 4 * q] * recf[wf1 + 4 * q] * recf[wf2 + 4 * q];
+          const float m0 = fmaf(q1.x, nc0, fmaf(q1.y, nc1, fmaf(q1.z, nc2, q0.x)));
+          const float m1 = fmaf(q1.w, nc0, fmaf(q2.x, nc1, fmaf(q2.y, nc2, q0.y)));
+          const float m2 = fmaf(q2.z, nc0, fmaf(q2.w, nc1, fmaf(a8, nc2, q0.z)));
+          acc0 = fmaf(w, q0.w, acc0);
+          acc1 = fmaf(w, m0, acc1);
+          acc2 = fmaf(w, m1, acc2);
+          acc3 = fmaf(w, m2, acc3);
+        }
+        if (node_lane) {
+          float4* t = win + (l2 * 6 + l1) * 6 + l0 + woff_node;
+          const float4 o = *t;
+          *t = make_float4(o.x + acc0, o.y + acc1, o.z + acc2, o.w + acc3);
+        }
+        __syncwarp();
+      }
+      p += len;
+    }
+    // contact registration: bodies that may hold a particle of this item
+    // (the signed distance is 1-Lipschitz: a body whose distance at the
+    // centre of the item's box exceeds its half diagonal holds none), then a
+    // warp-aggregated append, one contact per (particle, body) pair with the
+    // particle strictly inside
+    int lo[3], hi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = __reduce_min_sync(0xffffffffu, valid ? base[c] : 0x7fffffff);
+      hi[c] = __reduce_max_sync(0xffffffffu, valid ? base[c] : -0x7fffffff);
+    }
+    bool cand_b = false;
+    if (hi[0] >= lo[0] && lane < a.nb) {
+      const float c0 = g.ox + g.dx * (0.5f * (lo[0] + hi[0]) + 1.0f);
+      const float c1 = g.oy + g.dx * (0.5f * (lo[1] + hi[1]) + 1.0f);
+      const float c2 = g.oz + g.dx * (0.5f * (lo[2] + hi[2]) + 1.0f);
+      const float h0 = 0.5f * g.dx * (hi[0] - lo[0] + 1), h1 = 0.5f * g.dx * (hi[1] - lo[1] + 1),
+                  h2 = 0.5f * g.dx * (hi[2] - lo[2] + 1);
+      float nrm[3];
+      const float phi = body_sdf(s_body[lane], c0, c1, c2, nrm);
+      cand_b = phi <= sqrtf(h0 * h0 + h1 * h1 + h2 * h2) * 1.001f + 1e-6f;
+    }
+    const unsigned cand = __ballot_sync(0xffffffffu, cand_b);
+    if (cand) {
+      float vp[3] = {0.f, 0.f, 0.f};
+      if (valid) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vp[c] = a.P.v(c)[i];
+      }
+      for (int b = 0; b < a.nb; ++b) {
+        if (!((cand >> b) & 1u)) continue;
+        float nrm[3] = {0.f, 0.f, 1.f};
+        float phi = 1.0f;
+        if (valid) {
+          phi = body_sdf(s_body[b], xp[0], xp[1], xp[2], nrm);
+          // near the surface the sign and the depth come from FP64
+          if (phi < 1e-6f + 1e-6f * (fabsf(xp[0]) + fabsf(xp[1]) + fabsf(xp[2])))
+            phi = (float)body_sdf_f64(s_body[b], xp[0], xp[1], xp[2]);
+        }
+        const bool hit = valid && phi < 0.0f;
+        const unsigned mask = __ballot_sync(0xffffffffu, hit);
+        if (mask == 0u) continue;
+        const int leader = __ffs(mask) - 1;
+        int slot0 = 0;
+        if (lane == leader) slot0 = atomicAdd(a.C.count, __popc(mask));
+        slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+        if (hit) {
+          const int slot = slot0 + __popc(mask & ((1u << lane) - 1u));
+          if (slot < a.C.cap) {
+            const DevBody& bd = s_body[b];
+            float vr[3];
+            body_velocity(bd, xp[0], xp[1], xp[2], vr);
+            const float vn0 = nrm[0] * (vp[0] - vr[0]) + nrm[1] * (vp[1] - vr[1]) + nrm[2] * (vp[2] - vr[2]);
+            const float phi0 = -phi;
+            const float n0 = normal_impulse(phi0, bd.k, bd.d, h, vn0);
+            a.C.xp[slot] = make_float4(xp[0], xp[1], xp[2], phi0);
+            a.C.nrm[slot] = make_float4(nrm[0], nrm[1], nrm[2], n0);
+            a.C.bias[slot] = make_float4(-vr[0], -vr[1], -vr[2], 0.f);
+            a.C.id[slot] = make_int2((int)a.P.pid[i], b);
+          } else {
+            atomicOr(a.status, kStCapacity);
+          }
+        }
+      }
+    }
+  }
+  if (wb >= 0) flush_window(a, g, win, lane, wbx, wby, wbz, whx, why, whz);
+}
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kThreads, 4) k_p2g_g(P2GArgs a) {
+  p2g_gather_block<ITEMS>(a, blockIdx.x);
+}
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kThreads, 4) k_p2g_g_batch(const P2GArgs* __restrict__ args,
+                                                             const int2* __restrict__ work) {
+  __shared__ P2GArgs s_a;
+  const int2 wk = work[blockIdx.x];
+  load_args(args + wk.x, s_a);
+  __syncthreads();
+  p2g_gather_block<ITEMS>(s_a, wk.y);
+}
+
 template <int ITEMS>
 __global__ void __launch_bounds__(kThreads, 4) k_p2g(P2GArgs a) {
   p2g_block<ITEMS>(a, blockIdx.x);
 }
 
-// Batched: thread block b is block work[b].y of scene work[b].x
 template <int ITEMS>
-__global__ void __launch_bounds__(kThreads, 4) k_p2g_batch(const P2GArgs* __restrict__ args,
-                                                           const int2* __restrict__ work) {
-  __shared__ P2GArgs s_a;
-  const int2 wk = work[blockIdx.x];
-  load_args(args + wk.x, s_a);
-  __syncthreads();
-  p2g_block<ITEMS>(s_a, wk.y);
-}
-
-template <int ITEMS>
-void launch_items(const P2GArgs& a, cudaStream_t s) {
+void launch_items(const P2GArgs& a, int form, cudaStream_t s) {
   const int per_block = kThreads * ITEMS;
-  k_p2g<ITEMS><<<(a.n + per_block - 1) / per_block, kThreads, kDynSmem, s>>>(a);
+  const int nblk = (a.n + per_block - 1) / per_block;
+  if (form == MPM_P2G_SCATTER)
+    k_p2g<ITEMS><<<nblk, kThreads, kDynSmem, s>>>(a);
+  else
+    k_p2g_g<ITEMS><<<nblk, kThreads, kGatherSmem, s>>>(a);
 }
 
 template <int ITEMS>
 cudaError_t prepare_items() {
+  // dynamic shared memory beyond 48 KB, and room for four blocks per SM
   cudaError_t e = cudaFuncSetAttribute(k_p2g<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kDynSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_p2g_batch<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kDynSmem);
-  if (e != cudaSuccess) return e;
-  // room for four blocks' tiles per SM
-  e = cudaFuncSetAttribute(k_p2g<ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_p2g_batch<ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    e = cudaFuncSetAttribute(k_p2g_g<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGatherSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_p2g_g_batch<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGatherSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_p2g<ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_p2g_g<ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_p2g_g_batch<ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
 }
 
 }  // namespace
@@ -376,21 +638,21 @@ int p2g_block_particles(int chunk) { return items_of(chunk) * kThreads; }
 void launch_p2g_batch(const P2GArgs* args, const int2* work, int n_work, int chunk, cudaStream_t s) {
   if (n_work <= 0) return;
   switch (items_of(chunk)) {
-    case 1: k_p2g_batch<1><<<n_work, kThreads, kDynSmem, s>>>(args, work); break;
-    case 2: k_p2g_batch<2><<<n_work, kThreads, kDynSmem, s>>>(args, work); break;
-    default: k_p2g_batch<4><<<n_work, kThreads, kDynSmem, s>>>(args, work); break;
+    case 1: k_p2g_g_batch<1><<<n_work, kThreads, kGatherSmem, s>>>(args, work); break;
+    case 2: k_p2g_g_batch<2><<<n_work, kThreads, kGatherSmem, s>>>(args, work); break;
+    default: k_p2g_g_batch<4><<<n_work, kThreads, kGatherSmem, s>>>(args, work); break;
   }
 }
 
-void launch_p2g(const P2GArgs& a, int chunk, cudaStream_t s) {
+void launch_p2g(const P2GArgs& a, int chunk, int form, cudaStream_t s) {
   if (a.n <= 0) return;
   const int items = chunk / kThreads;
   if (items <= 1)
-    launch_items<1>(a, s);
+    launch_items<1>(a, form, s);
   else if (items == 2)
-    launch_items<2>(a, s);
+    launch_items<2>(a, form, s);
   else
-    launch_items<4>(a, s);
+    launch_items<4>(a, form, s);
 }
 
 }  // namespace mpmcr

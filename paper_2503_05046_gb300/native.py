@@ -28,6 +28,8 @@ OPT_PROFILE, OPT_SORT_EVERY, OPT_P2G_CHUNK, OPT_GRAPHS, OPT_SOLVE_BLOCKS = 1, 2,
 OPT_TAPE_SOLUTIONS = 7
 OPT_CLUSTER_CONTACTS = 8
 OPT_CLUSTER_BLOCKS = 9
+OPT_P2G_FORM = 10
+P2G_GATHER, P2G_SCATTER = 0, 1
 OPT_TEST_BARRIER_TIMEOUT = 6
 BATCH_OPT_GRAPHS, BATCH_OPT_P2G_CHUNK, BATCH_OPT_G2P_THREADS, BATCH_OPT_GRID_PARTICLES = 1, 2, 3, 4
 BATCH_OPT_SOLVE_BLOCKS = 5
