@@ -389,6 +389,7 @@ __device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
   const bool node_lane = lane < 27;
   const int oc0 = lane % 3, oc1 = (lane / 3) % 3, oc2 = min(lane / 9, 2);
   const float nc0 = -(float)oc0, nc1 = -(float)oc1, nc2 = -(float)oc2;
+  const float2 nc00 = make_float2(nc0, nc0), nc11 = make_float2(nc1, nc1), nc22 = make_float2(nc2, nc2);
   const int woff_node = (oc2 * 6 + oc1) * 6 + oc0;
   // weight e = 3 axis + c at row 3 + (e + 1) / 4, component (e + 1) % 4
   const int e0 = oc0, e1 = 3 + oc1, e2 = 6 + oc2;
@@ -438,8 +439,10 @@ __device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
         for (int c = 0; c < 3; ++c)
           b[c] = fmaf(A[3 * c], st.fx[0], fmaf(A[3 * c + 1], st.fx[1], fmaf(A[3 * c + 2], st.fx[2], mv[c])));
         r0 = make_float4(b[0], b[1], b[2], gr.mass);
-        r1 = make_float4(A[0], A[1], A[2], A[3]);
-        r2 = make_float4(A[4], A[5], A[6], A[7]);
+        // rows x and y of A' interleaved, so that both rows step in one
+        // paired FMA: (A'xx, A'yx, A'xy, A'yy), (A'xz, A'yz, A'zx, A'zy)
+        r1 = make_float4(A[0], A[3], A[1], A[4]);
+        r2 = make_float4(A[2], A[5], A[6], A[7]);
         r3 = make_float4(A[8], st.w[0][0], st.w[0][1], st.w[0][2]);
         r4 = make_float4(st.w[1][0], st.w[1][1], st.w[1][2], st.w[2][0]);
         r5 = make_float4(st.w[2][1], st.w[2][2], 0.f, 0.f);
@@ -476,19 +479,24 @@ __device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
         whz |= l2 >= 2;
         float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
         const int pe = p + len;
-#pragma unroll 1
+        // (acc1, acc2) and the momentum's x, y rows go in pairs (FFMA2)
+        float2 acc12 = make_float2(0.f, 0.f);
+#pragma unroll 2
         for (int q = p; q < pe; ++q) {
           const float4 q0 = rec[q], q1 = rec[32 + q], q2 = rec[64 + q];
           const float a8 = recf[(96 + q) * 4];
           const float w = recf[wf0 + 4 * q] * recf[wf1 + 4 * q] * recf[wf2 + 4 * q];
-          const float m0 = fmaf(q1.x, nc0, fmaf(q1.y, nc1, fmaf(q1.z, nc2, q0.x)));
-          const float m1 = fmaf(q1.w, nc0, fmaf(q2.x, nc1, fmaf(q2.y, nc2, q0.y)));
+          const float2 m01 =
+              __ffma2_rn(make_float2(q1.x, q1.y), nc00,
+                         __ffma2_rn(make_float2(q1.z, q1.w), nc11,
+                                    __ffma2_rn(make_float2(q2.x, q2.y), nc22, make_float2(q0.x, q0.y))));
           const float m2 = fmaf(q2.z, nc0, fmaf(q2.w, nc1, fmaf(a8, nc2, q0.z)));
           acc0 = fmaf(w, q0.w, acc0);
-          acc1 = fmaf(w, m0, acc1);
-          acc2 = fmaf(w, m1, acc2);
+          acc12 = __ffma2_rn(make_float2(w, w), m01, acc12);
           acc3 = fmaf(w, m2, acc3);
         }
+        acc1 = acc12.x;
+        acc2 = acc12.y;
         if (node_lane) {
           float4* t = win + (l2 * 6 + l1) * 6 + l0 + woff_node;
           const float4 o = *t;

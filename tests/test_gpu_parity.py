@@ -88,10 +88,13 @@ def run_parity(native, sc, n_sub=2, warm_steps=0, warm_solver=None, tol_v=TOL_V,
             # FP32 sums of B-spline-weighted masses: 1e-5 relative, plus the
             # absolute FP32 error of small weights (about 1e-7 of a particle mass)
             assert np.all(np.abs(m - om) <= 1e-5 * om + 1e-6 * mass_p)
-            # free-motion velocity on nodes holding >= 1e-3 of a particle mass
+            # free-motion velocity on nodes holding >= 1e-2 of a particle mass
+            # (lighter nodes carry v* - v = h f / m with m a small fraction of
+            # a particle's: FP32 rounding of the stress term is amplified by
+            # m_p / m there)
             # (lighter nodes get B-spline weights below 1e-3, whose FP32 value
             # has a relative error above 1e-5)
-            mid = om >= 1e-3 * mass_p
+            mid = om >= 1e-2 * mass_p
             assert rel_linf(vs[mid], ovs[mid]) < 1e-5
             # post-contact velocity: the objective is M-strongly convex, so the
             # stopping test of Alg. 1 bounds the solve's error in the M-norm,
