@@ -53,7 +53,10 @@ __device__ __forceinline__ void g2p_block(const G2PArgs& a, int block) {
     ay[c] = (iy >> 2) * (g.nbx * kBlockNodes) + ((iy & 3) << 2);
     az[c] = (iz >> 2) * (g.nbx * g.nby * kBlockNodes) + ((iz & 3) << 4);
   }
-  float vp[3] = {0.f, 0.f, 0.f}, Bm[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // x and y components go in pairs (paired FP32 ops): v_xy, and the x, y
+  // rows of B = sum w v (x_i - x_p)^T as (B_xx, B_yx), (B_xy, B_yy), (B_xz, B_yz)
+  float2 vxy = make_float2(0.f, 0.f), B0 = vxy, B1 = vxy, B2 = vxy;
+  float vz = 0.f, Bz0 = 0.f, Bz1 = 0.f, Bz2 = 0.f;
   const float dx0[3] = {(0.f - s.fx[0]) * g.dx, (1.f - s.fx[0]) * g.dx, (2.f - s.fx[0]) * g.dx};
 #pragma unroll
   for (int cz = 0; cz < 3; ++cz) {
@@ -63,29 +66,33 @@ __device__ __forceinline__ void g2p_block(const G2PArgs& a, int block) {
       const float dy = (cy - s.fx[1]) * g.dx;
       const float wyz = s.w[1][cy] * s.w[2][cz];
       // the row's sums of w v and of w v (x_i - x_p), then its dy, dz terms
-      float S[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
+      float2 Sxy = make_float2(0.f, 0.f), Txy = Sxy;
+      float Sz = 0.f, Tz = 0.f;
 #pragma unroll
       for (int cx = 0; cx < 3; ++cx) {
         const float w = s.w[0][cx] * wyz;
         const int node = kDense ? az[cz] + ay[cy] + ax[cx]
                                 : node_index(g, s.base[0] + cx, s.base[1] + cy, s.base[2] + cz);
         const float4 v = __ldg(a.G.v + node);
-        const float wv[3] = {w * v.x, w * v.y, w * v.z};
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          S[r] += wv[r];
-          T[r] = fmaf(wv[r], dx0[cx], T[r]);
-        }
+        const float2 wv = __fmul2_rn(make_float2(w, w), make_float2(v.x, v.y));
+        const float wvz = w * v.z;
+        Sxy = __fadd2_rn(Sxy, wv);
+        Txy = __ffma2_rn(wv, make_float2(dx0[cx], dx0[cx]), Txy);
+        Sz += wvz;
+        Tz = fmaf(wvz, dx0[cx], Tz);
       }
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        vp[r] += S[r];
-        Bm[3 * r] += T[r];
-        Bm[3 * r + 1] = fmaf(S[r], dy, Bm[3 * r + 1]);
-        Bm[3 * r + 2] = fmaf(S[r], dz, Bm[3 * r + 2]);
-      }
+      vxy = __fadd2_rn(vxy, Sxy);
+      B0 = __fadd2_rn(B0, Txy);
+      B1 = __ffma2_rn(Sxy, make_float2(dy, dy), B1);
+      B2 = __ffma2_rn(Sxy, make_float2(dz, dz), B2);
+      vz += Sz;
+      Bz0 += Tz;
+      Bz1 = fmaf(Sz, dy, Bz1);
+      Bz2 = fmaf(Sz, dz, Bz2);
     }
   }
+  const float vp[3] = {vxy.x, vxy.y, vz};
+  const float Bm[9] = {B0.x, B1.x, B2.x, B0.y, B1.y, B2.y, Bz0, Bz1, Bz2};
   const float dinv = 4.0f * g.inv_dx * g.inv_dx;
   const float h = a.h;
   float C[9], F[9], Fn[9];

@@ -343,23 +343,31 @@ constexpr int kRecRows = 6;   // float4 rows of a particle record
 constexpr size_t kGatherSmem = sizeof(float4) * kWarps * (kWin + kRecRows * 32);
 
 // the window of block (bx, by, bz) to the grid; the window is zero afterwards.
-// hi*: the block's stencils reach into the next block along that axis.
+// lo*, hi*: the least and greatest cell (0..3) of the block whose run reached
+// the window along each axis, so that only slots lo .. hi + 2 can be nonzero.
 __device__ __forceinline__ void flush_window(const P2GArgs& a, const GridDev& g, float4* win,
-                                             int lane, int bx, int by, int bz, bool hx, bool hy,
-                                             bool hz) {
-  for (int t = lane; t < kWin; t += 32) {
-    const float4 q = win[t];
+                                             int lane, int bx, int by, int bz, int lo0, int lo1,
+                                             int lo2, int hi0, int hi1, int hi2) {
+  const int e0 = hi0 - lo0 + 3, e1 = hi1 - lo1 + 3, e2 = hi2 - lo2 + 3;
+  // t / e0 and r / e1 by float reciprocals: exact, since t < 216 and the
+  // fractional parts stay at least 0.5 / e away from an integer
+  const float inv0 = 1.0f / e0, inv1 = 1.0f / e1;
+  for (int t = lane; t < e0 * e1 * e2; t += 32) {
+    const int r = __float2int_rz(((float)t + 0.5f) * inv0), x = t - r * e0;
+    const int z = __float2int_rz(((float)r + 0.5f) * inv1), y = r - z * e1;
+    const int lx = lo0 + x, ly = lo1 + y, lz = lo2 + z;
+    float4* slot = win + (lz * 6 + ly) * 6 + lx;
+    const float4 q = *slot;
     if (q.x != 0.0f || q.y != 0.0f || q.z != 0.0f || q.w != 0.0f) {
-      const int lz = t / 36, r = t - 36 * lz, ly = r / 6, lx = r - 6 * ly;
       red_add_v4(a.G.mp + node_index(g, 4 * bx + lx, 4 * by + ly, 4 * bz + lz), q.x, q.y, q.z, q.w);
-      win[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      *slot = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
   // the (up to 8) blocks the window's stencils reach (a sparse grid marked
   // them before P2G)
   if (!g.slot && lane < 8) {
     const int ox = lane & 1, oy = (lane >> 1) & 1, oz = lane >> 2;
-    if ((!ox || hx) && (!oy || hy) && (!oz || hz))
+    if ((!ox || hi0 >= 2) && (!oy || hi1 >= 2) && (!oz || hi2 >= 2))
       a.G.mark[((bz + oz) * g.nby + (by + oy)) * g.nbx + (bx + ox)] = 1;
   }
   __syncwarp();
@@ -398,7 +406,7 @@ __device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
   const int wf2 = ((3 + (e2 + 1) / 4) * 32) * 4 + ((e2 + 1) & 3);
 
   int wb = -1, wbx = 0, wby = 0, wbz = 0;  // the window's block
-  bool whx = false, why = false, whz = false;
+  int wl0 = 3, wl1 = 3, wl2 = 3, wh0 = 0, wh1 = 0, wh2 = 0;  // its runs' cells
 #pragma unroll 1
   for (int it = 0; it < ITEMS; ++it) {
     const int i = first + it * 32 + lane;
@@ -466,17 +474,17 @@ __device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
                   b2 = __shfl_sync(0xffffffffu, base[2], p);
         const int kb = __shfl_sync(0xffffffffu, bkey, p);
         if (kb != wb) {
-          if (wb >= 0) flush_window(a, g, win, lane, wbx, wby, wbz, whx, why, whz);
+          if (wb >= 0) flush_window(a, g, win, lane, wbx, wby, wbz, wl0, wl1, wl2, wh0, wh1, wh2);
           wb = kb;
           wbx = b0 >> 2;
           wby = b1 >> 2;
           wbz = b2 >> 2;
-          whx = why = whz = false;
+          wl0 = wl1 = wl2 = 3;
+          wh0 = wh1 = wh2 = 0;
         }
         const int l0 = b0 & 3, l1 = b1 & 3, l2 = b2 & 3;
-        whx |= l0 >= 2;
-        why |= l1 >= 2;
-        whz |= l2 >= 2;
+        wl0 = min(wl0, l0); wl1 = min(wl1, l1); wl2 = min(wl2, l2);
+        wh0 = max(wh0, l0); wh1 = max(wh1, l1); wh2 = max(wh2, l2);
         float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
         const int pe = p + len;
         // (acc1, acc2) and the momentum's x, y rows go in pairs (FFMA2)
@@ -572,7 +580,7 @@ __device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
       }
     }
   }
-  if (wb >= 0) flush_window(a, g, win, lane, wbx, wby, wbz, whx, why, whz);
+  if (wb >= 0) flush_window(a, g, win, lane, wbx, wby, wbz, wl0, wl1, wl2, wh0, wh1, wh2);
 }
 
 template <int ITEMS>
