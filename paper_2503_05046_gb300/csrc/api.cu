@@ -348,7 +348,8 @@ void release(mpm_ctx* c) {
                   c->adj_out, c->adj_ids, c->adj_io, c->bw_buf, c->bw_gbar, c->bw_slot, c->bw_mat,
                   c->tape_pool, c->tape_recs, c->tape_counters, c->bw_snap, c->bw_gbody, c->dyn_d,
                   c->imp0_d, c->bodies_step_d, c->G.n_mapped, c->slot_d, c->cloth_tris_d,
-                  c->cloth_rest_d, c->cloth_f_d, c->slot_of_d, c->pin_ids_d, c->pin_v_d, c->pin_x_d};
+                  c->cloth_rest_d, c->cloth_f_d, c->slot_of_d, c->pin_ids_d, c->pin_v_d, c->pin_x_d,
+                  c->pin_mask_d};
   for (auto& t : c->tape)
     if (t.state) cudaFree(t.state);
   for (void* p : ptrs)
@@ -380,18 +381,12 @@ cudaError_t enqueue_substep(mpm_ctx* ctx, int cur, int nb, float hf, const mpm_s
   pa.status = ctx->status; pa.stats = ctx->stats;
   pa.fext = nullptr;
   pa.fext_stride = ctx->cap;
-  if (ctx->n_pins > 0) {
-    // pinned particles enter the substep on their prescribed motion
-    mark_phase(ctx, MPM_PHASE_P2G);
-    launch_pin_init(ctx->P[cur], ctx->slot_of_d, ctx->pin_ids_d, ctx->pin_v_d, ctx->pin_x_d,
-                    ctx->n_pins, ctx->pins_cap, s);
-  }
   if (!ctx->cloth_tris.empty()) {
     // cloth: the mesh forces at the substep's start positions
     mark_phase(ctx, MPM_PHASE_P2G);
-    launch_cloth_forces(ctx->P[cur], n, ctx->slot_of_d, ctx->cloth_tris_d, ctx->cloth_rest_d,
-                        (int)ctx->cloth_tris.size(), ctx->groups_d, ctx->cloth_f_d, ctx->cap, s);
-    launch_pin_forces(ctx->slot_of_d, ctx->pin_ids_d, ctx->n_pins, ctx->cloth_f_d, ctx->cap, s);
+    launch_cloth_forces(ctx->P[cur], ctx->slot_of_d, ctx->cloth_tris_d, ctx->cloth_rest_d,
+                        (int)ctx->cloth_tris.size(), ctx->groups_d,
+                        ctx->n_pins > 0 ? ctx->pin_mask_d : nullptr, ctx->cloth_f_d, ctx->cap, s);
     pa.fext = ctx->cloth_f_d;
   }
   if (ctx->g.slot) {
@@ -455,6 +450,11 @@ cudaError_t enqueue_step(mpm_ctx* ctx, int from, bool sort_now, int n_substeps, 
   // cloth triangles and pins find their particles through the id -> slot
   // map of the buffer the substeps run on
   if (!ctx->cloth_tris.empty() || ctx->n_pins > 0) launch_slot_map(ctx->P[cur], n, ctx->slot_of_d, s);
+  // pinned particles enter the step on their prescribed motion (start
+  // positions from the particles, which the caller may have set)
+  if (ctx->n_pins > 0 && n_substeps > 0)
+    launch_pin_init(ctx->P[cur], ctx->slot_of_d, ctx->pin_ids_d, ctx->pin_v_d, ctx->pin_x_d,
+                    ctx->n_pins, ctx->pins_cap, s);
   for (int k = 0; k < n_substeps; ++k) {
     const cudaError_t e = enqueue_substep(ctx, cur, nb, hf, sp, solve_blocks, true, s, ctx->taping);
     if (e != cudaSuccess) return e;
@@ -666,7 +666,7 @@ mpm_status mpm_create(const mpm_grid_spec* spec, void* cuda_stream, mpm_ctx** ou
        cudaMemset(ctx->impulses, 0, 6 * kMaxBodies * sizeof(double)) == cudaSuccess &&
        cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) return bail(MPM_ERR_CUDA);
-  if (p2g_prepare() != cudaSuccess) return bail(MPM_ERR_CUDA);
+  if (p2g_prepare() != cudaSuccess || sort_prepare() != cudaSuccess) return bail(MPM_ERR_CUDA);
   int occ = 0;
   if (solve_prepare() != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_kernel_ptr(), solve_block_size(),
@@ -809,7 +809,11 @@ mpm_status mpm_add_cloth(mpm_ctx* ctx, int64_t n_vertices, const float* x, const
                 cudaMemcpyHostToDevice));
   CU(cudaMemcpy(ctx->cloth_rest_d, ctx->cloth_rest.data(), ctx->cloth_rest.size() * sizeof(double),
                 cudaMemcpyHostToDevice));
-  if (!ctx->cloth_f_d) CU(dalloc(&ctx->cloth_f_d, (size_t)3 * ctx->cap));
+  if (!ctx->cloth_f_d) {
+    // zero once: every P2G leaves the planes zero for the next substep's forces
+    CU(dalloc(&ctx->cloth_f_d, (size_t)3 * ctx->cap));
+    CU(cudaMemsetAsync(ctx->cloth_f_d, 0, (size_t)3 * ctx->cap * sizeof(float), ctx->stream));
+  }
   if (!ctx->slot_of_d) CU(dalloc(&ctx->slot_of_d, (size_t)ctx->cap));
   // (graphs recorded before had no cloth pass)
   for (auto& e : ctx->gexec)
@@ -849,6 +853,8 @@ mpm_status mpm_set_pins(mpm_ctx* ctx, int64_t n_pins, const int64_t* ids, const 
     CU(dalloc(&ctx->pin_x_d, 3 * (size_t)n_pins));
     ctx->pins_cap = (int)n_pins;
   }
+  if (!ctx->pin_mask_d) CU(dalloc(&ctx->pin_mask_d, (size_t)ctx->cap));
+  CU(cudaMemsetAsync(ctx->pin_mask_d, 0, (size_t)ctx->cap, ctx->stream));
   if (n_pins > 0) {
     if (!ctx->slot_of_d) CU(dalloc(&ctx->slot_of_d, (size_t)ctx->cap));
     std::vector<int> id32((size_t)n_pins);
@@ -861,6 +867,9 @@ mpm_status mpm_set_pins(mpm_ctx* ctx, int64_t n_pins, const int64_t* ids, const 
                        ctx->stream));
     CU(cudaMemcpyAsync(ctx->pin_v_d, vp.data(), vp.size() * sizeof(float), cudaMemcpyHostToDevice,
                        ctx->stream));
+    std::vector<uint8_t> mask((size_t)ctx->n, 0);
+    for (int64_t j = 0; j < n_pins; ++j) mask[(size_t)ids[j]] = 1;
+    CU(cudaMemcpyAsync(ctx->pin_mask_d, mask.data(), mask.size(), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
   }
   ctx->n_pins = (int)n_pins;

@@ -5,21 +5,22 @@
 // R the polar factor of F (F = R S, S = sqrt(F^T F)), J = det S, times the
 // triangle's rest volume (rest area times the cloth's thickness). The forces
 // f = -dE/dx are recomputed at the start of every substep and P2G adds h f
-// to the vertices' momentum; the vertices
+// to the vertices' momentum (and leaves the force planes zero); the vertices
 // carry no stress of their own and collide (with bodies, with the cloth
 // itself, with other material) through the grid and the contact solve.
 //
 // One thread per triangle in FP64 (a few hundred operations: near rest
 // F - R is a small difference of O(1) terms, which FP32 would leave with a
-// relative error of 1e-4; GB300's FP64 rate is ample for a mesh), its three
-// forces added to the vertices' force planes with FP32 atomics.
+// relative error of 1e-4), its three forces added to the vertices' force
+// planes with FP32 atomics.
 //
 // Pinned particles (the held cloth corners of the same experiment): a
 // Dirichlet condition on the particle. A pinned particle enters every
-// substep with its prescribed velocity and C = 0 (its start position kept),
-// the mesh forces on it are dropped, and after G2P it is put back on its
-// path, x = x_start + h v_pin (F follows G2P). One thread per pin, through
-// the id -> slot map.
+// substep with its prescribed velocity and C = 0 (its start position kept:
+// taken from the particle at a step's first substep, carried between
+// substeps), the mesh forces on it are dropped, and after G2P it is put back
+// on its path, x = x_start + h v_pin (F follows G2P). One thread per pin,
+// through the id -> slot map.
 #include <cmath>
 
 #include "kernels.h"
@@ -31,7 +32,8 @@ namespace {
 __global__ void k_cloth_forces(Particles P, const int* __restrict__ slot_of,
                                const int4* __restrict__ tris, const double* __restrict__ rest,
                                int n_tris, const DevGroup* __restrict__ groups,
-                               float* __restrict__ f, long long stride) {
+                               const uint8_t* __restrict__ pinned, float* __restrict__ f,
+                               long long stride) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tris) return;
   const int4 tv = tris[t];
@@ -76,12 +78,14 @@ __global__ void k_cloth_forces(Particles P, const int* __restrict__ slot_of,
     g[c][0] = vol * (p0 * dmi[0] + p1 * dmi[1]);
     g[c][1] = vol * (p0 * dmi[2] + p1 * dmi[3]);
   }
+  // a pinned vertex is held: the mesh does not push it
+  const bool hold[3] = {pinned && pinned[tv.x], pinned && pinned[tv.y], pinned && pinned[tv.z]};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float* fc = f + (size_t)c * stride;
-    atomicAdd(fc + sl[0], (float)(g[c][0] + g[c][1]));
-    atomicAdd(fc + sl[1], (float)(-g[c][0]));
-    atomicAdd(fc + sl[2], (float)(-g[c][1]));
+    if (!hold[0]) atomicAdd(fc + sl[0], (float)(g[c][0] + g[c][1]));
+    if (!hold[1]) atomicAdd(fc + sl[1], (float)(-g[c][0]));
+    if (!hold[2]) atomicAdd(fc + sl[2], (float)(-g[c][1]));
   }
 }
 
@@ -100,17 +104,8 @@ __global__ void k_pin_init(Particles P, const int* __restrict__ slot_of, const i
   for (int c = 0; c < 9; ++c) P.C(c)[sl] = 0.f;
 }
 
-__global__ void k_pin_forces(const int* __restrict__ slot_of, const int* __restrict__ ids, int n_pins,
-                             float* __restrict__ f, long long stride) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n_pins) return;
-  const int sl = slot_of[ids[j]];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) f[(size_t)c * stride + sl] = 0.f;
-}
-
 __global__ void k_pins(Particles P, const int* __restrict__ slot_of, const int* __restrict__ ids,
-                       const float* __restrict__ v_pin, const float* __restrict__ x_pin, int n_pins,
+                       const float* __restrict__ v_pin, float* __restrict__ x_pin, int n_pins,
                        int cap, float h) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_pins) return;
@@ -118,7 +113,9 @@ __global__ void k_pins(Particles P, const int* __restrict__ slot_of, const int* 
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float vp = v_pin[j + c * cap];
-    P.x(c)[sl] = fmaf(h, vp, x_pin[j + c * cap]);
+    const float xp = fmaf(h, vp, x_pin[j + c * cap]);
+    P.x(c)[sl] = xp;
+    x_pin[j + c * cap] = xp;  // the next substep's start
     P.v(c)[sl] = vp;
   }
 #pragma unroll
@@ -152,13 +149,14 @@ void cloth_rest_shape(const double X0[3], const double X1[3], const double X2[3]
   out[4] = 0.5 * nn;
 }
 
-void launch_cloth_forces(const Particles& P, int n, const int* slot_of, const int4* tris,
-                         const double* rest, int n_tris, const DevGroup* groups, float* f,
-                         long long stride, cudaStream_t s) {
-  if (n > 0) cudaMemsetAsync(f, 0, 3 * (size_t)stride * sizeof(float), s);
+void launch_cloth_forces(const Particles& P, const int* slot_of, const int4* tris,
+                         const double* rest, int n_tris, const DevGroup* groups,
+                         const uint8_t* pinned, float* f, long long stride, cudaStream_t s) {
+  // one warp per block: a mesh of a few thousand triangles then spreads over
+  // as many SMs as it has warps, since each SM's FP64 pipe is narrow
   if (n_tris > 0)
-    k_cloth_forces<<<(n_tris + 127) / 128, 128, 0, s>>>(P, slot_of, tris, rest, n_tris, groups, f,
-                                                         stride);
+    k_cloth_forces<<<(n_tris + 31) / 32, 32, 0, s>>>(P, slot_of, tris, rest, n_tris, groups,
+                                                      pinned, f, stride);
 }
 
 void launch_pin_init(const Particles& P, const int* slot_of, const int* ids, const float* v_pin,
@@ -167,13 +165,8 @@ void launch_pin_init(const Particles& P, const int* slot_of, const int* ids, con
     k_pin_init<<<(n_pins + 127) / 128, 128, 0, s>>>(P, slot_of, ids, v_pin, x_pin, n_pins, cap);
 }
 
-void launch_pin_forces(const int* slot_of, const int* ids, int n_pins, float* f, long long stride,
-                       cudaStream_t s) {
-  if (n_pins > 0) k_pin_forces<<<(n_pins + 127) / 128, 128, 0, s>>>(slot_of, ids, n_pins, f, stride);
-}
-
 void launch_pins(const Particles& P, const int* slot_of, const int* ids, const float* v_pin,
-                 const float* x_pin, int n_pins, int cap, float h, cudaStream_t s) {
+                 float* x_pin, int n_pins, int cap, float h, cudaStream_t s) {
   if (n_pins > 0)
     k_pins<<<(n_pins + 127) / 128, 128, 0, s>>>(P, slot_of, ids, v_pin, x_pin, n_pins, cap, h);
 }

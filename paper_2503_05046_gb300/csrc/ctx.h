@@ -63,6 +63,7 @@ struct mpm_ctx {
   int* pin_ids_d = nullptr;
   float* pin_v_d = nullptr;
   float* pin_x_d = nullptr;
+  uint8_t* pin_mask_d = nullptr;  // by particle id: 1 if pinned (cap bytes)
   // particle id -> slot map of the buffer the substeps run on (cloth, pins)
   int* slot_of_d = nullptr;
   Contacts C{};

@@ -47,6 +47,7 @@ struct SortBuffers {
 };
 
 int sort_hist_len(int n);
+cudaError_t sort_prepare();  // once per device: the small-scene sort's shared memory
 // ---- sort.cu: block keys, LSD radix sort (8-bit digits), permutation ----
 void launch_sort(const GridDev& g, const Particles& src, const Particles& dst, int n,
                  SortBuffers& sb, cudaStream_t s);
@@ -71,7 +72,7 @@ struct P2GArgs {
   Contacts C;
   uint32_t* status;
   DevStats* stats;
-  const float* fext;   // cloth: per-particle mesh forces, 3 planes of fext_stride (null: none)
+  float* fext;  // cloth: per-particle mesh forces, 3 planes of fext_stride (null: none); P2G zeroes them
   long long fext_stride;
 };
 // form: MPM_P2G_GATHER or MPM_P2G_SCATTER
@@ -201,22 +202,22 @@ void launch_bar_out(const Particles& P, int n, const float* bar, float* x, float
 // rest shape of a triangle from its rest vertices: Dm^-1 (2x2 row-major), area
 // (mpm_add_cloth replaces the area by the rest volume, area * thickness)
 void cloth_rest_shape(const double X0[3], const double X1[3], const double X2[3], double out[5]);
-// f (3 planes of `stride` floats, slot order) = the mesh forces at the current
-// positions; tris: (particle ids, group); rest: Dm^-1 and rest volume per triangle
-void launch_cloth_forces(const Particles& P, int n, const int* slot_of, const int4* tris,
-                         const double* rest, int n_tris, const DevGroup* groups, float* f,
-                         long long stride, cudaStream_t s);
+// f (3 planes of `stride` floats, slot order, zero on entry: P2G zeroes what
+// it consumes) += the mesh forces at the current positions; tris: (particle
+// ids, group); rest: Dm^-1 and rest volume per triangle; pinned (by particle
+// id, may be null): vertices that get no force
+void launch_cloth_forces(const Particles& P, const int* slot_of, const int4* tris,
+                         const double* rest, int n_tris, const DevGroup* groups,
+                         const uint8_t* pinned, float* f, long long stride, cudaStream_t s);
 // pinned particles: ids[j] (found through slot_of) with prescribed velocity
 // (v_pin[j + c * cap]) and the substep's start position (x_pin[j + c * cap]).
-// init, at the substep's start: x_pin = the particle's x; its v = v_pin, C = 0
+// init, at a step's first substep: x_pin = the particle's x; its v = v_pin, C = 0
 void launch_pin_init(const Particles& P, const int* slot_of, const int* ids, const float* v_pin,
                      float* x_pin, int n_pins, int cap, cudaStream_t s);
-// the mesh forces on pinned vertices dropped (f: 3 planes of stride)
-void launch_pin_forces(const int* slot_of, const int* ids, int n_pins, float* f, long long stride,
-                       cudaStream_t s);
-// after G2P: the particle's x = x_pin + h v_pin, v = v_pin, C = 0
+// after G2P: the particle's x = x_pin + h v_pin (and x_pin, the next
+// substep's start), v = v_pin, C = 0
 void launch_pins(const Particles& P, const int* slot_of, const int* ids, const float* v_pin,
-                 const float* x_pin, int n_pins, int cap, float h, cudaStream_t s);
+                 float* x_pin, int n_pins, int cap, float h, cudaStream_t s);
 
 // ---- rigid.cu: the bodies' update after a time step (Eq. (3)-(4)) ----
 enum { kRigidStatic = 0, kRigidKinematic = 1, kRigidDynamic = 2 };

@@ -146,10 +146,11 @@ __device__ __forceinline__ void p2g_block(const P2GArgs& a, int block) {
         mvx = gr.mass * a.P.v(0)[i];
         mvy = gr.mass * a.P.v(1)[i];
         mvz = gr.mass * a.P.v(2)[i];
-        if (a.fext) {  // cloth: + h f
+        if (a.fext) {  // cloth: + h f, the force planes left zero for the next substep
           mvx = fmaf(h, a.fext[i], mvx);
           mvy = fmaf(h, a.fext[a.fext_stride + i], mvy);
           mvz = fmaf(h, a.fext[2 * a.fext_stride + i], mvz);
+          a.fext[i] = a.fext[a.fext_stride + i] = a.fext[2 * a.fext_stride + i] = 0.f;
         }
       }
       const int head = __ffs(peers) - 1, seg_end = 31 - __clz(peers);
@@ -216,10 +217,11 @@ __device__ __forceinline__ void p2g_block(const P2GArgs& a, int block) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) A[c] = gr.mass * a.P.C(c)[i] - sc * tf[c];
       float mvx = gr.mass * vp[0], mvy = gr.mass * vp[1], mvz = gr.mass * vp[2];
-      if (a.fext) {  // cloth: + h f
+      if (a.fext) {  // cloth: + h f, the force planes left zero for the next substep
         mvx = fmaf(h, a.fext[i], mvx);
         mvy = fmaf(h, a.fext[a.fext_stride + i], mvy);
         mvz = fmaf(h, a.fext[2 * a.fext_stride + i], mvz);
+        a.fext[i] = a.fext[a.fext_stride + i] = a.fext[2 * a.fext_stride + i] = 0.f;
       }
 #pragma unroll
       for (int cz = 0; cz < 3; ++cz) {
@@ -438,9 +440,12 @@ __device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
 #pragma unroll
         for (int c = 0; c < 9; ++c) A[c] = -g.dx * (gr.mass * a.P.C(c)[i] - sc * tf[c]);
         float mv[3] = {gr.mass * a.P.v(0)[i], gr.mass * a.P.v(1)[i], gr.mass * a.P.v(2)[i]};
-        if (a.fext) {  // cloth: + h f
+        if (a.fext) {  // cloth: + h f, the force planes left zero for the next substep
 #pragma unroll
-          for (int c = 0; c < 3; ++c) mv[c] = fmaf(h, a.fext[c * a.fext_stride + i], mv[c]);
+          for (int c = 0; c < 3; ++c) {
+            mv[c] = fmaf(h, a.fext[c * a.fext_stride + i], mv[c]);
+            a.fext[c * a.fext_stride + i] = 0.f;
+          }
         }
         float b[3];
 #pragma unroll

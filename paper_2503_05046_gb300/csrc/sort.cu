@@ -11,7 +11,10 @@
 // 128^3 grid has 15 + 6 key bits: three passes). Each pass is a
 // per-warp-tile histogram, an exclusive scan over (digit, tile), and a
 // stable per-warp scatter whose in-warp ranks come from __match_any_sync.
-// The permutation is then applied to every particle plane at once.
+// The permutation is then applied to every particle plane at once. Up to
+// 8,192 particles the keys are sorted by one thread block instead (a bitonic
+// network over (key, index) pairs in shared memory: the same order, two
+// launches in place of a dozen, which is what a small scene's step notices).
 #include "kernels.h"
 
 namespace mpmcr {
@@ -24,14 +27,14 @@ constexpr int kSortWarps = 4;         // warps per thread block
 constexpr int kScanChunk = 4096;      // elements per scan thread block
 constexpr int kScanThreads = 256;
 
-__global__ void k_keys(GridDev g, const float* __restrict__ x0, const float* __restrict__ x1,
-                       const float* __restrict__ x2, int n, uint32_t* __restrict__ keys,
-                       uint32_t* __restrict__ vals) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+constexpr int kSmallSortMax = 8192;      // particles sorted by one thread block
+constexpr int kSmallSortThreads = 1024;
+
+// the sort key of a particle at (x, y, z)
+__device__ __forceinline__ uint32_t sort_key(const GridDev& g, float x, float y, float z) {
   // the base node of the particle's stencil, as P2G computes it
   Stencil st;
-  stencil(g, x0[i], x1[i], x2[i], st);
+  stencil(g, x, y, z, st);
   int lim[3] = {g.nbx - 1, g.nby - 1, g.nbz - 1};
   uint32_t b[3], c[3];
 #pragma unroll
@@ -46,8 +49,46 @@ __global__ void k_keys(GridDev g, const float* __restrict__ x0, const float* __r
   uint32_t key = spread_bits3(b[0]) | (spread_bits3(b[1]) << 1) | (spread_bits3(b[2]) << 2);
   // cell within the block, x fastest (the order of the P2G tile), when it fits
   if (g.sort_cell_bits) key = (key << 6) | (c[2] << 4) | (c[1] << 2) | c[0];
-  keys[i] = key;
+  return key;
+}
+
+__global__ void k_keys(GridDev g, const float* __restrict__ x0, const float* __restrict__ x1,
+                       const float* __restrict__ x2, int n, uint32_t* __restrict__ keys,
+                       uint32_t* __restrict__ vals) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = sort_key(g, x0[i], x1[i], x2[i]);
   vals[i] = (uint32_t)i;
+}
+
+// Up to kSmallSortMax particles in one thread block: the (key, index) pairs,
+// each distinct thanks to the index, sorted by a bitonic network in shared
+// memory, so that the order is the stable radix sort's; the permutation goes
+// to vals. A small scene's sort is then one launch instead of a dozen.
+__global__ void __launch_bounds__(kSmallSortThreads) k_sort_small(
+    GridDev g, const float* __restrict__ x0, const float* __restrict__ x1,
+    const float* __restrict__ x2, int n, uint32_t* __restrict__ vals) {
+  extern __shared__ unsigned long long s_kv[];
+  int m = 1;
+  while (m < n) m <<= 1;
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    s_kv[i] = i < n ? ((unsigned long long)sort_key(g, x0[i], x1[i], x2[i]) << 32) | (unsigned)i
+                    : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < (m >> 1); t += blockDim.x) {
+        const int i = 2 * t - (t & (j - 1));  // t-th index with bit j clear; its partner i + j
+        const unsigned long long a = s_kv[i], b = s_kv[i + j];
+        if ((a > b) == ((i & k) == 0)) {
+          s_kv[i] = b;
+          s_kv[i + j] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) vals[i] = (uint32_t)s_kv[i];
 }
 
 __global__ void k_hist(const uint32_t* __restrict__ keys, int n, int shift, int n_tiles,
@@ -248,6 +289,11 @@ void exclusive_scan(uint32_t* data, int len, uint32_t* partial, cudaStream_t s) 
 
 }  // namespace
 
+cudaError_t sort_prepare() {
+  return cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(kSmallSortMax * sizeof(unsigned long long)));
+}
+
 int sort_hist_len(int n) {
   int n_tiles = (n + kWarpTile - 1) / kWarpTile;
   return kRadix * (n_tiles > 0 ? n_tiles : 1);
@@ -257,6 +303,14 @@ void launch_sort(const GridDev& g, const Particles& src, const Particles& dst, i
                  SortBuffers& sb, cudaStream_t s) {
   if (n <= 0) return;
   int tpb = 256;
+  if (n <= kSmallSortMax) {
+    int m = 1;
+    while (m < n) m <<= 1;
+    k_sort_small<<<1, kSmallSortThreads, m * sizeof(unsigned long long), s>>>(
+        g, src.x(0), src.x(1), src.x(2), n, sb.vals[0]);
+    k_permute<<<(n + tpb - 1) / tpb, tpb, 0, s>>>(src, dst, sb.vals[0], n);
+    return;
+  }
   k_keys<<<(n + tpb - 1) / tpb, tpb, 0, s>>>(g, src.x(0), src.x(1), src.x(2), n, sb.keys[0],
                                             sb.vals[0]);
   int key_bits = 3 * g.morton_bits + (g.sort_cell_bits ? 6 : 0);
