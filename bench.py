@@ -328,7 +328,9 @@ def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
     wl = workload_name(sc)
     out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GBps"], "peak": peak,
                        "peak_kind": peak_kind, "unit": "GB/s", "frac": kern[dom]["GBps"] / peak,
-                       "traffic": profiled_traffic(dom, wl, n),
+                       "traffic": profiled_traffic(
+                           dom if dom != "p2g" else "p2g_" + ("gather", "scatter")[p2g_form], wl, n),
+                       "form": ("gather", "scatter")[p2g_form] if dom == "p2g" else None,
                        "note": "the streaming kernel with the largest share of the step; the "
                                "contact solve (%.0f%% of the step) is latency-bound, its "
                                "bytes in kernels.solve" % (100.0 * phase_ms["solve"] /
@@ -466,6 +468,9 @@ def cloth_box_bagging(native, steps=40, warmup=3):
     N, h = sc["substeps"], sc["h"]
     for _ in range(warmup):
         sim.step(solver=solver, check=False)
+    from paper_2503_05046_gb300 import tune
+    form, _ = tune.tune_p2g_form(sim, solver, steps=2)
+    sim.step(solver=solver, check=False)  # records the step's graph again
     st0 = sim.get_particles()
     b0 = sim.bodies()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -494,6 +499,7 @@ def cloth_box_bagging(native, steps=40, warmup=3):
            "us_per_substep": 1e3 * ms / N, "particle_substeps_per_s": n * N / (ms * 1e-3),
            "real_time_rate": N * h / (ms * 1e-3), "eps_r": 5e-2, "contacts_max": contacts,
            "iters_per_substep": iters / max(subs, 1), "steps_not_converged": failed,
+           "p2g_form": ("gather", "scatter")[form],
            "box_drop_m": float(b0[1]["p"][2] - box_end["p"][2]),
            "paper": {"ms_per_step": 45.3, "particles": 2582, "substeps_per_step": 10,
                      "hardware": "RTX 4090, rigid and robot side included"}}
