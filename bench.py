@@ -211,7 +211,7 @@ def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
         sim.step(solver=solver, stats=False, check=False)
     # the P2G form that is faster on this workload, timed on ordinary steps
     from paper_2503_05046_gb300 import tune
-    p2g_form, form_table = tune.tune_p2g_form(sim, solver, steps=2)
+    (p2g_form, p2g_chunk), form_table = tune.tune_p2g_form(sim, solver, steps=2)
     sim.step(solver=solver, stats=False, check=False)  # records the step's graph again
     sim.step(n_substeps=0, solver=solver, check=False)  # drain warm-up status
 
@@ -281,8 +281,9 @@ def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
     act_nodes = st.active_blocks_max * 64
 
     out = {"value": value, "ms_per_step": ms / args.steps, "steps": args.steps,
-           "p2g_form": {"chosen": ("gather", "scatter")[p2g_form],
-                        "p2g_us_per_launch": {("gather", "scatter")[f]: 1e3 * t for f, t in form_table}},
+           "p2g_form": {"chosen": ("gather", "scatter")[p2g_form], "particles_per_block": p2g_chunk,
+                        "p2g_us_per_launch": {"%s_%d" % (("gather", "scatter")[f], c): 1e3 * t
+                                              for (f, c), t in form_table}},
            "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
                    "h2d_bytes_per_step": int(nb * C_sizeof_body(native)),
                    "d2h_bytes_per_step": int(12 * n + 48 * nb),
@@ -329,7 +330,8 @@ def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
     out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GBps"], "peak": peak,
                        "peak_kind": peak_kind, "unit": "GB/s", "frac": kern[dom]["GBps"] / peak,
                        "traffic": profiled_traffic(
-                           dom if dom != "p2g" else "p2g_" + ("gather", "scatter")[p2g_form], wl, n),
+                           dom if dom != "p2g" else "p2g_%s_%d" % (("gather", "scatter")[p2g_form], p2g_chunk),
+                           wl, n),
                        "form": ("gather", "scatter")[p2g_form] if dom == "p2g" else None,
                        "note": "the streaming kernel with the largest share of the step; the "
                                "contact solve (%.0f%% of the step) is latency-bound, its "
@@ -469,11 +471,12 @@ def cloth_box_bagging(native, steps=40, warmup=3):
     # start from the same state whichever form wins
     probe = native.Sim(sc)
     probe.set_dynamics(1, dyn)
-    form, _ = tune.tune_p2g_form(probe, solver, steps=2)
+    (form, chunk), _ = tune.tune_p2g_form(probe, solver, steps=2)
     probe.close()
     sim = native.Sim(sc)
     sim.set_dynamics(1, dyn)
     native.mpm_set_option(sim.ctx, native.OPT_P2G_FORM, form)
+    native.mpm_set_option(sim.ctx, native.OPT_P2G_CHUNK, chunk)
     for _ in range(warmup):
         sim.step(solver=solver, check=False)
     st0 = sim.get_particles()

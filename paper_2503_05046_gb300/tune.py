@@ -96,27 +96,31 @@ def tune_batch_launch(batch, h, n_substeps, solver, steps=2, p2g_chunks=(256, 51
     return best, table
 
 
-def tune_p2g_form(sim, solver, steps=1):
-    """Time the P2G launches of `steps` steps of one context with each P2G
-    form (phase events, so that the comparison does not depend on how the
-    rest of the steps, which advance the simulation, differ); apply and return
-    the faster form and the table of (form, P2G milliseconds per launch). The
-    gather form wins at several particles per cell, the scatter form near
-    one."""
+def tune_p2g_form(sim, solver, steps=1, candidates=((0, 256), (0, 1024), (1, 256))):
+    """Time the P2G launches of `steps` steps of one context for each
+    (form, particles per block) candidate: the gather form (0) at 256 and
+    1,024 particles per block, the scatter form (1) at 256 (phase events, so
+    that the comparison does not depend on how the rest of the steps, which
+    advance the simulation, differ). Apply and return the fastest
+    (form, chunk) and the table of ((form, chunk), P2G milliseconds per
+    launch). The gather form wins at several particles per cell, the scatter
+    form near one."""
     table = []
     native.mpm_set_option(sim.ctx, native.OPT_PROFILE, 1)
     try:
-        for form in (native.P2G_GATHER, native.P2G_SCATTER):
+        for form, chunk in candidates:
             native.mpm_set_option(sim.ctx, native.OPT_P2G_FORM, form)
+            native.mpm_set_option(sim.ctx, native.OPT_P2G_CHUNK, chunk)
             native.mpm_get_phase_times(sim.ctx, reset=True)
             for _ in range(steps):
                 native.mpm_step(sim.ctx, sim.scene["h"], sim.scene["substeps"], solver,
                                 want_stats=False)
             ms, n = native.mpm_get_phase_times(sim.ctx, reset=True)
-            table.append((form, ms["p2g"] / max(n["p2g"], 1)))
+            table.append(((form, chunk), ms["p2g"] / max(n["p2g"], 1)))
     finally:
         native.mpm_set_option(sim.ctx, native.OPT_PROFILE, 0)
     native.mpm_synchronize(sim.ctx)
-    form = min(table, key=lambda r: r[1])[0]
+    form, chunk = min(table, key=lambda r: r[1])[0]
     native.mpm_set_option(sim.ctx, native.OPT_P2G_FORM, form)
-    return form, table
+    native.mpm_set_option(sim.ctx, native.OPT_P2G_CHUNK, chunk)
+    return (form, chunk), table

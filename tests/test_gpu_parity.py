@@ -147,10 +147,18 @@ def test_normal_contact_parity_cooperative_launch(native):
     assert all(r[1] > 0 and r[6] == 0 for r in rep), rep
 
 
-@pytest.mark.parametrize("form", [0, 1])  # MPM_P2G_GATHER, MPM_P2G_SCATTER
-def test_sliding_contact_parity(native, form):
+# P2G (form, particles per block): MPM_P2G_GATHER at 256 and 1,024, MPM_P2G_SCATTER at 256
+P2G_SHAPES = [(0, 256), (0, 1024), (1, 256)]
+
+
+def p2g_options(native, shape):
+    return ((native.OPT_P2G_FORM, shape[0]), (native.OPT_P2G_CHUNK, shape[1]))
+
+
+@pytest.mark.parametrize("shape", P2G_SHAPES)
+def test_sliding_contact_parity(native, shape):
     rep = run_parity(native, scenes.cube_contact(n_side=8, v0=(0.05, 0.0, -0.05)), n_sub=2,
-                     options=((native.OPT_P2G_FORM, form),))
+                     options=p2g_options(native, shape))
     assert all(r[1] > 0 for r in rep)
 
 
@@ -160,14 +168,14 @@ def test_sand_paddle_parity(native):
     assert any(r[1] > 0 for r in rep)
 
 
-@pytest.mark.parametrize("form", [0, 1])
-def test_ragged_sizes_and_two_materials(native, form):
+@pytest.mark.parametrize("shape", P2G_SHAPES)
+def test_ragged_sizes_and_two_materials(native, shape):
     rng = np.random.default_rng(5)
     sc = scenes.cube_contact(n_side=7, v0=(0.0, 0.0, -0.05))
     sand = scenes.cube_group(5, 0.005, (-0.06, 0.0, 0.012), (0.0, 0.0, -0.02), dict(scenes.SAND),
                              jitter=1e-4, rng=rng)
     sc["groups"].append(sand)  # 343 + 125 particles: not a multiple of any tile
-    run_parity(native, sc, n_sub=2, options=((native.OPT_P2G_FORM, form),))
+    run_parity(native, sc, n_sub=2, options=p2g_options(native, shape))
 
 
 def test_empty_context_steps(native):
@@ -194,15 +202,15 @@ def test_sort_only_step_keeps_state_bit_exact(native):
     sim.close()
 
 
-@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("shape", P2G_SHAPES)
 @pytest.mark.parametrize("ppc", [1.0, 4.0])
-def test_random_sparse_sand_parity(native, ppc, form):
+def test_random_sparse_sand_parity(native, ppc, shape):
     """Sand sampled at random at about one (and four) particles per cell, as in
     the granular scooping benchmark, with the lowest particles starting in
     contact with the ground: both P2G forms on short and long same-cell runs,
     and G2P's Drucker-Prager update, off the lattice."""
     sc = scenes.sand_random(n_particles=8000, ppc=ppc, penetration=0.02 * 0.01)
-    rep = run_parity(native, sc, n_sub=3, options=((native.OPT_P2G_FORM, form),))
+    rep = run_parity(native, sc, n_sub=3, options=p2g_options(native, shape))
     assert any(r[1] > 0 for r in rep)
 
 
