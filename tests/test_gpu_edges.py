@@ -194,3 +194,22 @@ def test_dirichlet_layers_counted_by_hand(native, bc):
     inner = (i >= bc) & (i < 12 - bc) & (j >= bc) & (j < 12 - bc) & (k >= bc) & (k < 12 - bc)
     assert np.array_equal(moving, inner)
     assert np.allclose(vs[inner], [0.0, 0.0, -9.81e-4], rtol=1e-6, atol=1e-9)
+
+
+def test_launch_options_are_validated(native):
+    """Bad option values are refused and leave the context usable; a change of
+    P2G form or block size between steps keeps the state consistent (the
+    step graph is recorded again)."""
+    sim = native.Sim(scenes.cube_drop(n_side=8))
+    for opt, val in ((native.OPT_P2G_FORM, 2), (native.OPT_P2G_FORM, -1),
+                     (native.OPT_P2G_CHUNK, 300), (native.OPT_CLUSTER_BLOCKS, 3)):
+        with pytest.raises(native.MpmError):
+            native.mpm_set_option(sim.ctx, opt, val)
+    sim.step()
+    for form, chunk in ((1, 256), (0, 1024), (0, 256)):
+        native.mpm_set_option(sim.ctx, native.OPT_P2G_FORM, form)
+        native.mpm_set_option(sim.ctx, native.OPT_P2G_CHUNK, chunk)
+        st = sim.step()
+        assert st.substeps > 0
+    assert np.all(np.isfinite(sim.get_particles()["v"]))
+    sim.close()
