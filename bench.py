@@ -78,6 +78,24 @@ def max_over_ranks(value, ws):
     return float(t.item())
 
 
+def sum_over_ranks(value, ws):
+    """Sum of a float over the ranks of the default process group (identity at ws = 1)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
 def whole_job_value(units_per_rank, ws, max_seconds):
     """Units processed by all ranks divided by the slowest rank's time."""
     return units_per_rank * ws / max_seconds
@@ -158,17 +176,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_launches_per_step(res, n_substeps, n_bodies=0):
-    """Kernels one mpm_step launches: the radix sort (keys, five kernels per
-    8-bit digit pass, permutation), per substep P2G, block compaction, grid
-    update, the two solve kernels (the cluster one and the cooperative one,
-    of which the contact count picks one to work) and G2P, and with bodies
-    the rigid update after the substeps."""
-    blocks = max(-(-int(r) // 4) for r in res)
-    morton_bits = max((blocks - 1).bit_length(), 1)
-    key_bits = 3 * morton_bits + (6 if 3 * morton_bits + 6 <= 32 else 0)
-    passes = -(-key_bits // 8)
-    return (1 + 5 * passes + 1) + 6 * n_substeps + (1 if n_bodies > 0 else 0)
+SMALL_SORT_MAX = 8192  # particles the library sorts in one thread block
+
+
+def kernel_launches_per_step(res, n_substeps, n_bodies=0, n_particles=None):
+    """Kernels one mpm_step launches: the sort (above 8,192 particles the
+    radix sort: keys, five kernels per 8-bit digit pass, permutation; up to
+    it one sorting block and the permutation), per substep P2G, block
+    compaction, grid update, the two solve kernels (the cluster one and the
+    cooperative one, of which the contact count picks one to work) and G2P,
+    and with bodies the rigid update after the substeps."""
+    if n_particles is not None and n_particles <= SMALL_SORT_MAX:
+        sort = 2
+    else:
+        blocks = max(-(-int(r) // 4) for r in res)
+        morton_bits = max((blocks - 1).bit_length(), 1)
+        key_bits = 3 * morton_bits + (6 if 3 * morton_bits + 6 <= 32 else 0)
+        sort = 1 + 5 * (-(-key_bits // 8)) + 1
+    return sort + 6 * n_substeps + (1 if n_bodies > 0 else 0)
+
+
+def shard(n_items, rank, ws):
+    """The independent items (scenes) rank `rank` of `ws` takes: round robin,
+    so that scenes of random size spread evenly."""
+    return list(range(rank, n_items, ws))
 
 
 def workload_name(sc):
@@ -297,7 +328,7 @@ def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
                       "p2g_global_chunks": st.p2g_global_chunks,
                       "status_timed": native.STATUS_NAMES[code_timed],
                       "solve_us_per_substep": [u / max(st.substeps, 1) for u in st.solve_us]},
-           "launches_per_step": kernel_launches_per_step(sc["grid"]["res"], N, len(sc["bodies"]))}
+           "launches_per_step": kernel_launches_per_step(sc["grid"]["res"], N, len(sc["bodies"]), n)}
 
     peak, peak_kind = measured_peak_hbm()
     kern = {}
@@ -397,7 +428,7 @@ def run_ours(args):
         config=bench_config(sc2, n2, ws))}
     if not args.no_small:
         line["small_scenes"] = small_scene_latency(native)
-        line["batched"] = batched_throughput(native)
+        line["batched"] = batched_throughput(native, ws=ws, rank=rank)
         line["differentiation"] = differentiation(native)
         line["cloth"] = cloth_box_bagging(native)
     if rank == 0 and not args.no_cpu_baseline:
@@ -515,7 +546,7 @@ def cloth_box_bagging(native, steps=40, warmup=3):
     return out
 
 
-def batched_throughput(native, n_scenes=256, steps=3, warmup=2):
+def batched_throughput(native, n_scenes=256, steps=3, warmup=2, ws=1, rank=0):
     """Many independent scenes of uneven size (2k-64k particles each, elastic or
     sand, a gripper jaw and the ground) advanced three ways, each timed by the
     host clock around `steps` steps of every scene, synchronised on both sides:
@@ -527,13 +558,17 @@ def batched_throughput(native, n_scenes=256, steps=3, warmup=2):
       replaying its own step graph, enqueued one after another without
       waiting, SM cap of the solve and P2G block size by tune.tune_batch;
     - `loop_value`: the single-scene path looped (one scene at a time, every
-      step waited for, default options)."""
+      step waited for, default options).
+    On several GPUs the scenes are split round robin over the ranks (they
+    are independent: no collective but the timing), each rank times its
+    share and the values are all scenes over the slowest rank's time."""
     import torch
     from paper_2503_05046_gb300 import scenes, tune
-    scs = [scenes.batch_scene(i) for i in range(n_scenes)]
+    mine = shard(n_scenes, rank, ws)
+    scs = [scenes.batch_scene(i) for i in mine]
     h, N = scs[0]["h"], scs[0]["substeps"]
     solver = native.solver_params(eps_r=5e-2, max_iters=1000)
-    n_total = sum(scenes.n_particles(sc) for sc in scs)
+    n_total = int(sum_over_ranks(sum(scenes.n_particles(sc) for sc in scs), ws))
 
     # (1) one batch
     batch = native.Batch(scs, max_contacts=lambda sc: 2 * scenes.n_particles(sc))
@@ -542,11 +577,12 @@ def batched_throughput(native, n_scenes=256, steps=3, warmup=2):
         batch.step(h, N, solver)
     batch.synchronize(stats=False)
     torch.cuda.synchronize()
+    barrier(ws)
     t0 = time.perf_counter()
     for _ in range(steps):
         batch.step(h, N, solver)
     torch.cuda.synchronize()
-    t_persist = time.perf_counter() - t0
+    t_persist = max_over_ranks(time.perf_counter() - t0, ws)
     code_b, codes_b, stats_b = batch.synchronize()
     contacts_b = [s["contacts_max"] for s in stats_b]
     batch.close()
@@ -565,6 +601,7 @@ def batched_throughput(native, n_scenes=256, steps=3, warmup=2):
         torch.cuda.synchronize()
         for sim in sims:  # clear warm-up status (the touch-down substep may hit max_iters)
             native.mpm_synchronize(sim.ctx)
+        barrier(ws)
         t0 = time.perf_counter()
         for _ in range(steps):
             for sim, sc in zip(sims, scs):
@@ -572,7 +609,7 @@ def batched_throughput(native, n_scenes=256, steps=3, warmup=2):
                 if wait_each:
                     sim.torch_stream.synchronize()
         torch.cuda.synchronize()
-        return time.perf_counter() - t0
+        return max_over_ranks(time.perf_counter() - t0, ws)
 
     t_conc = run(solve_cap, False, chunk)
     codes = [native.mpm_synchronize(sim.ctx) for sim in sims]
@@ -586,6 +623,7 @@ def batched_throughput(native, n_scenes=256, steps=3, warmup=2):
              native.BATCH_OPT_GRID_PARTICLES: "grid_particles_per_block",
              native.BATCH_OPT_SOLVE_BLOCKS: "solve_blocks_per_scene"}
     return {"scenes": n_scenes, "particles": n_total, "steps": steps, "substeps_per_step": N,
+            "ranks": ws, "scenes_per_rank": len(mine),
             "value": v_persist, "unit": "scene-steps/s",
             "particle_substeps_per_s": n_total * N * steps / t_persist,
             "ms_per_step": 1e3 * t_persist / steps,

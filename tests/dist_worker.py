@@ -18,9 +18,12 @@ def main():
     seconds = 1.5 + rank  # rank r took 1.5 + r seconds
     worst = bench.max_over_ranks(seconds, ws)
     value = bench.whole_job_value(1000.0, ws, worst)
+    mine = bench.shard(10, rank, ws)
+    total = bench.sum_over_ranks(float(len(mine)), ws)
     dist.barrier()
     dist.destroy_process_group()
-    print(json.dumps({"rank": rank, "ws": ws, "max": worst, "value": value}))
+    print(json.dumps({"rank": rank, "ws": ws, "max": worst, "value": value, "shard": mine,
+                      "shard_total": total}))
 
 
 if __name__ == "__main__":

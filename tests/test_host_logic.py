@@ -39,6 +39,10 @@ def test_max_over_ranks_and_whole_job_value_gloo_two_ranks():
         assert o["ws"] == 2
         assert o["max"] == pytest.approx(2.5)          # the slowest rank's time
         assert o["value"] == pytest.approx(2 * 1000.0 / 2.5)  # all ranks' units / that time
+        assert o["shard_total"] == 10                   # scenes counted over the ranks
+    # the batched scenes split over the ranks: disjoint, together all of them
+    a, b = (set(o["shard"]) for o in sorted(outs, key=lambda o: o["rank"]))
+    assert not (a & b) and a | b == set(range(10))
 
 
 def test_single_rank_helpers_are_identities():
@@ -54,6 +58,13 @@ def test_single_rank_helpers_are_identities():
 ])
 def test_kernel_launch_count(res, n_sub, nb, expected):
     assert bench.kernel_launches_per_step(res, n_sub, nb) == expected
+
+
+def test_kernel_launch_count_small_scene():
+    # up to 8,192 particles the sort is one block and the permutation
+    assert bench.kernel_launches_per_step((64, 64, 64), 10, 2, n_particles=8000) == 2 + 60 + 1
+    assert bench.kernel_launches_per_step((64, 64, 64), 10, 2, n_particles=8193) == \
+        bench.kernel_launches_per_step((64, 64, 64), 10, 2)
 
 
 def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
