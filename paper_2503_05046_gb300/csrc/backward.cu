@@ -621,7 +621,8 @@ __global__ void k_reset_counters(GridArrays G, Contacts C, unsigned* bar) {
   *G.n_act = 0;
   *G.n_cnodes = 0;
   *G.pstar2 = 0.0;
-  for (int g = 0; g <= 256 / kBarGroup; ++g) bar[kBarStride * g] = 0u;
+  bar[0] = 0u;  // the solve's 64-bit barrier counter
+  bar[1] = 0u;
 }
 
 // ---- solutions of the taped substeps ---------------------------------------

@@ -35,7 +35,7 @@ __device__ __forceinline__ void g2p_block(const G2PArgs& a, int block) {
       *a.G.n_cnodes = 0;
       *a.G.pstar2 = 0.0;
     }
-    if (threadIdx.x <= 256 / kBarGroup) a.bar[kBarStride * threadIdx.x] = 0u;
+    if (threadIdx.x < 2) a.bar[threadIdx.x] = 0u;  // the solve's 64-bit barrier counter
   }
   const int i = block * (int)blockDim.x + threadIdx.x;
   if (i >= a.n) return;

@@ -10,11 +10,9 @@
 namespace mpmcr {
 
 constexpr int kRedDoubles = 4 * 256 * 16;  // contact-solve partial sums: 4 slots x 256 blocks x 16
-// device-wide barrier counters of the cooperative solves: the top counter,
-// then one per group of kBarGroup blocks, kBarStride words apart
-constexpr int kBarGroup = 16;
-constexpr int kBarStride = 32;
-constexpr int kBarWords = kBarStride * (1 + 256 / kBarGroup);
+// device-wide barrier of the cooperative solves: one 64-bit arrival counter
+// (words 0 and 1) on a line of its own
+constexpr int kBarWords = 32;
 
 // Statistics written by the device, read back by mpm_step.
 struct DevStats {

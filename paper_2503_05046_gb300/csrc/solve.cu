@@ -59,9 +59,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -93,16 +93,15 @@ __device__ __forceinline__ float2 ld_cluster_f2(const float2* p, unsigned rank) 
   return v;
 }
 
-// Device-wide barrier of the participating blocks, in two levels so that no
-// counter takes more than kBarGroup arrivals per barrier: block b arrives on
-// the counter of its group of kBarGroup blocks, and each group's last
-// arrival arrives on the top counter. Counters only grow: the k-th barrier
-// is complete when the top counter reaches (k + 1) x groups, which each block
-// reads off its own group ticket, so nothing is reset or published by the
-// last arriver. Thread 0 publishes its block's writes (fence), arrives, and
-// polls with a time limit (1 s of the global timer); on expiry it returns
-// false (the caller then returns; the other blocks expire at the same or
-// their next barrier). A single participating block needs only
+// Device-wide barrier of the participating blocks on one 64-bit arrival
+// counter that only grows: the k-th barrier is complete when it reaches
+// (k + 1) x blocks, which each block reads off its own ticket, so nothing is
+// reset or published by the last arriver. (A single counter measured faster
+// on GB300 than counters per group of 16 blocks: 1.3 against 2.1 us per
+// barrier of 152 blocks.) Thread 0 publishes its block's writes (fence),
+// arrives, and polls with a time limit (1 s of the global timer); on expiry
+// it returns false (the caller then returns; the other blocks expire at the
+// same or their next barrier). A single participating block needs only
 // __syncthreads; the blocks of one cluster use the cluster barrier.
 __device__ bool grid_sync(Barrier& B) {
   if (B.cluster) {
@@ -114,20 +113,14 @@ __device__ bool grid_sync(Barrier& B) {
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned g = B.blk / kBarGroup;
-    const unsigned gsize = min((unsigned)kBarGroup, B.n - g * kBarGroup);
-    const unsigned top_n = (B.n + kBarGroup - 1) / kBarGroup + B.extra;
+    unsigned long long* top = reinterpret_cast<unsigned long long*>(B.bar);
+    const unsigned long long per = (unsigned long long)B.n + B.extra;
     __threadfence();
-    const unsigned ticket = atomicAdd(&B.bar[kBarStride * (1 + g)], 1u);
-    const unsigned k = ticket / gsize;
-    if (ticket % gsize == gsize - 1) {  // the group's last arrival carries it upwards
-      __threadfence();
-      atomicAdd(&B.bar[0], 1u);
-    }
-    const unsigned target = (k + 1u) * top_n;
+    const unsigned long long ticket = atomicAdd(top, 1ull);
+    const unsigned long long target = (ticket / per + 1ull) * per;
     const unsigned long long t0 = global_ns();
     unsigned spins = 0;
-    while (ld_acquire(&B.bar[0]) < target) {
+    while (ld_acquire(top) < target) {
       ++spins;
       if (((spins & 63u) == 0u && global_ns() - t0 > kWaitLimitNs) || spins > kSpinCap) {
         atomicOr(B.status, kStTimeout);
