@@ -33,6 +33,7 @@ cores (its OpenMP build where it exists), one substep of the whole headline
 workload per bench step.
 """
 import argparse
+import functools
 import json
 import os
 import platform
@@ -246,7 +247,9 @@ def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
     sim.step(solver=solver, stats=False, check=False)  # records the step's graph again
     sim.step(n_substeps=0, solver=solver, check=False)  # drain warm-up status
 
-    def timed_steps(k):
+    def timed_steps(k, stats=None):
+        # stats: a list that takes each step's statistics (the read-back after
+        # a step waits for it; only the phase-timed pass asks for them)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
         torch.cuda.synchronize()
@@ -254,8 +257,10 @@ def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
             with torch.cuda.stream(stream):
                 flush.zero_()
             starts[i].record(stream)
-            native.mpm_step(sim.ctx, sc["h"], N, solver, want_stats=False)
+            _, st_i = native.mpm_step(sim.ctx, sc["h"], N, solver, want_stats=stats is not None)
             ends[i].record(stream)
+            if stats is not None:
+                stats.append(st_i)
         torch.cuda.synchronize()
         return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
@@ -305,11 +310,16 @@ def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
     restore()
     native.mpm_set_option(sim.ctx, native.OPT_PROFILE, 1)
     native.mpm_get_phase_times(sim.ctx, reset=True)
-    ms_prof = sum(timed_steps(args.steps))
+    prof_stats = []
+    ms_prof = sum(timed_steps(args.steps, prof_stats))
     phase_ms, phase_n = native.mpm_get_phase_times(sim.ctx, reset=True)
     native.mpm_set_option(sim.ctx, native.OPT_PROFILE, 0)
-    code_stats, st = sim.step(solver=solver, check=False)  # statistics (not timed)
-    act_nodes = st.active_blocks_max * 64
+    # solver statistics of the same steps as the phase times
+    subs_p = max(sum(x.substeps for x in prof_stats), 1)
+    iters_p = sum(x.iters_total for x in prof_stats)
+    ls_p = sum(x.ls_evals_total for x in prof_stats)
+    solve_us_p = [sum(x.solve_us[k] for x in prof_stats) / subs_p for k in range(5)]
+    act_nodes = max(x.active_blocks_max for x in prof_stats) * 64
 
     out = {"value": value, "ms_per_step": ms / args.steps, "steps": args.steps,
            "p2g_form": {"chosen": ("gather", "scatter")[p2g_form], "particles_per_block": p2g_chunk,
@@ -321,13 +331,18 @@ def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
                    "device_ms_same_steps": same_steps_ms, "host_ms": 1e3 * e2e_s},
            "ms_per_step_profiled": ms_prof / args.steps,
            "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
-           "solver": {"iters_per_substep": st.iters_total / max(st.substeps, 1),
-                      "ls_passes_per_iter": st.ls_evals_total / max(st.iters_total, 1),
-                      "contacts_max": st.contacts_max, "residual_max": st.residual_max,
-                      "active_blocks_max": st.active_blocks_max, "status_bits": st.status_bits,
-                      "p2g_global_chunks": st.p2g_global_chunks,
+           "solver": {"over": "the %d phase-timed steps" % len(prof_stats),
+                      "iters_per_substep": iters_p / subs_p,
+                      "ls_passes_per_iter": ls_p / max(iters_p, 1),
+                      "contacts_max": max(x.contacts_max for x in prof_stats),
+                      "residual_max": max(x.residual_max for x in prof_stats),
+                      "active_blocks_max": max(x.active_blocks_max for x in prof_stats),
+                      "status_bits": functools.reduce(lambda u, x: u | x.status_bits, prof_stats, 0),
+                      "p2g_global_chunks": sum(x.p2g_global_chunks for x in prof_stats),
                       "status_timed": native.STATUS_NAMES[code_timed],
-                      "solve_us_per_substep": [u / max(st.substeps, 1) for u in st.solve_us]},
+                      "solve_phases_us_per_substep": dict(zip(
+                          ("node_list", "gradient_hessian", "node_solve", "line_search", "impulses"),
+                          solve_us_p))},
            "launches_per_step": kernel_launches_per_step(sc["grid"]["res"], N, len(sc["bodies"]), n)}
 
     peak, peak_kind = measured_peak_hbm()
@@ -345,11 +360,12 @@ def measure_workload(native, sc, args, ws, stream_flush=True, tight=True):
     iters = out["solver"]["iters_per_substep"]
     # per QN iteration: 48 B per contact and 60 B per contact node (v, v*, m,
     # g, H, dv), the latter counted from the step's statistics
-    solve_bytes = iters * (SOLVE_BYTES_PER_CONTACT * st.contacts_max +
-                           SOLVE_BYTES_PER_NODE * st.contact_nodes_max)
+    solve_bytes = iters * (SOLVE_BYTES_PER_CONTACT * out["solver"]["contacts_max"] +
+                           SOLVE_BYTES_PER_NODE * max(x.contact_nodes_max for x in prof_stats))
     kern["solve"] = {"avg_us": solve_avg_s * 1e6, "launches": int(phase_n["solve"]),
                      "us_per_qn_iter": solve_avg_s * 1e6 / max(iters, 1e-9),
-                     "contacts": st.contacts_max, "contact_nodes": st.contact_nodes_max,
+                     "contacts": out["solver"]["contacts_max"],
+                     "contact_nodes": max(x.contact_nodes_max for x in prof_stats),
                      "bytes_per_launch": solve_bytes,
                      "GBps": solve_bytes / solve_avg_s / 1e9 if solve_avg_s > 0 else 0.0,
                      "frac": (solve_bytes / solve_avg_s / 1e9 / peak) if solve_avg_s > 0 else 0.0,

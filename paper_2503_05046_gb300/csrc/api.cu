@@ -98,7 +98,16 @@ DevBody to_dev(const mpm_rigid_body& b) {
   d.mu = b.mu;
   d.k = b.k;
   d.d = b.d;
-  d.bound = INFINITY;
+  // a ball around p that holds the geometry (the half-space has none)
+  if (b.shape == MPM_SPHERE)
+    d.bound = std::fabs(b.params[0]);
+  else if (b.shape == MPM_BOX)
+    d.bound = (float)std::sqrt((double)b.params[0] * b.params[0] + (double)b.params[1] * b.params[1] +
+                               (double)b.params[2] * b.params[2]) * 1.000001f;
+  else if (b.shape == MPM_CAPSULE)
+    d.bound = (std::fabs(b.params[0]) + std::fabs(b.params[1])) * 1.000001f;
+  else
+    d.bound = INFINITY;
   return d;
 }
 

@@ -37,6 +37,23 @@ constexpr int kWarpTileCap = 384;  // nodes per warp tile (6 KB)
 // dynamic shared memory: kWarps tiles of kWarpTileCap float4
 constexpr size_t kDynSmem = sizeof(float4) * kWarps * kWarpTileCap;
 
+// Whether body b may hold a point of the box with centre c and half extents
+// h. The signed distance is 1-Lipschitz, so a body whose distance at c exceeds
+// the half diagonal holds none. A body inside the ball of radius b.bound
+// around its origin is at least |c - p| - bound away from c, so the ball is
+// tried first (with slack, so it only rejects bodies the distance would
+// reject too) and the signed distance, whose branch differs between the
+// lanes' primitives, is evaluated only for the bodies that it leaves.
+__device__ __forceinline__ bool box_may_touch(const DevBody& b, float c0, float c1, float c2,
+                                              float h0, float h1, float h2) {
+  const float thr = sqrtf(h0 * h0 + h1 * h1 + h2 * h2) * 1.001f + 1e-6f;
+  const float r0 = c0 - b.p[0], r1 = c1 - b.p[1], r2 = c2 - b.p[2];
+  const float lim = (b.bound + thr) * 1.0001f + 1e-5f;  // inf for an unbounded body
+  if (r0 * r0 + r1 * r1 + r2 * r2 > lim * lim) return false;
+  float nrm[3];
+  return body_sdf(b, c0, c1, c2, nrm) <= thr;
+}
+
 // Block `block` of P2G over one scene's particles (a thread block of the
 // single-scene launch, or a work item of the batched one).
 template <int ITEMS>
@@ -98,9 +115,7 @@ __device__ __forceinline__ void p2g_block(const P2GArgs& a, int block) {
     const float c2 = g.oz + g.dx * (0.5f * (lo[2] + hi[2]) + 1.0f);
     const float h0 = 0.5f * g.dx * (hi[0] - lo[0] + 1), h1 = 0.5f * g.dx * (hi[1] - lo[1] + 1),
                 h2 = 0.5f * g.dx * (hi[2] - lo[2] + 1);
-    float nrm[3];
-    const float phi = body_sdf(s_body[lane], c0, c1, c2, nrm);
-    cand_b = phi <= sqrtf(h0 * h0 + h1 * h1 + h2 * h2) * 1.001f + 1e-6f;
+    cand_b = box_may_touch(s_body[lane], c0, c1, c2, h0, h1, h2);
   }
   const unsigned cand = __ballot_sync(0xffffffffu, cand_b);
   __syncwarp();
@@ -537,9 +552,7 @@ __device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
       const float c2 = g.oz + g.dx * (0.5f * (lo[2] + hi[2]) + 1.0f);
       const float h0 = 0.5f * g.dx * (hi[0] - lo[0] + 1), h1 = 0.5f * g.dx * (hi[1] - lo[1] + 1),
                   h2 = 0.5f * g.dx * (hi[2] - lo[2] + 1);
-      float nrm[3];
-      const float phi = body_sdf(s_body[lane], c0, c1, c2, nrm);
-      cand_b = phi <= sqrtf(h0 * h0 + h1 * h1 + h2 * h2) * 1.001f + 1e-6f;
+      cand_b = box_may_touch(s_body[lane], c0, c1, c2, h0, h1, h2);
     }
     const unsigned cand = __ballot_sync(0xffffffffu, cand_b);
     if (cand) {

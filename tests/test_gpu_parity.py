@@ -236,3 +236,70 @@ def test_cluster_split_line_search_parity(native):
     rep = run_parity(native, sc, n_sub=2, options=((native.OPT_CLUSTER_CONTACTS, 1 << 16),))
     assert all(r[1] > 4096 for r in rep), [r[1] for r in rep]
     assert all(r[5] == 1 and r[6] == 1 for r in rep), "the cluster solve did not run: %s" % rep
+
+
+def _support(shape, params, R, d):
+    """Offset from a body's origin to its point farthest along d (unit)."""
+    u = R.T @ d  # d in the body frame
+    if shape == scenes.BOX:
+        return R @ (np.sign(u) * np.asarray(params[:3]))
+    if shape == scenes.CAPSULE:
+        return R @ np.array([0.0, 0.0, np.sign(u[2]) * params[0]]) + params[1] * d
+    return params[0] * d  # sphere
+
+
+def _random_rotation(rng):
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    return q if np.linalg.det(q) > 0 else -q
+
+
+def extremes_scene(depth=8e-3, v0=(0.0, 0.0, 0.0)):
+    """A 14^3-particle elastic cube at 5 mm spacing (dx = 1 cm, the scale of
+    the other parity scenes) with rigid bodies whose extreme points (two
+    randomly rotated boxes' corners, a tilted capsule's end cap, a sphere's
+    pole) reach `depth` into four of its faces: the contacts sit where the
+    geometry is farthest from each body's origin. The bodies are frictionless:
+    deep contacts of a cube at rest stick, and the oracle's solve to 1e-10 then
+    takes over 10^5 iterations."""
+    rng = np.random.default_rng(31)
+    dx, spacing, n_side = 1e-2, 5e-3, 14
+    centre = np.array([0.0, 0.0, 0.06])
+    half = n_side * spacing / 2.0
+    g = scenes.cube_group(n_side, spacing, centre, v0, scenes.elastic(1.0e5, 0.3, 1000.0),
+                          jitter=1e-2 * spacing, rng=rng)
+    bodies = [scenes.body(scenes.HALFSPACE, mu=0.4)]
+    faces = [  # (direction into the cube, a point of the face, shape, params, rotation)
+        (np.array([-1.0, 0.0, 0.0]), centre + [half, 0.008, -0.004], scenes.BOX, (0.02, 0.03, 0.04),
+         _random_rotation(rng)),
+        (np.array([1.0, 0.0, 0.0]), centre + [-half, -0.008, 0.008], scenes.BOX, (0.015, 0.025, 0.035),
+         _random_rotation(rng)),
+        (np.array([0.0, 1.0, 0.0]), centre + [0.012, -half, 0.0], scenes.CAPSULE, (0.02, 0.01),
+         _random_rotation(rng)),
+        (np.array([0.0, 0.0, -1.0]), centre + [-0.008, 0.004, half], scenes.SPHERE, (0.015,), np.eye(3)),
+    ]
+    for d, face, shape, params, R in faces:
+        target = face + depth * d  # the extreme point, `depth` inside the face
+        p = target - _support(shape, params, R, d)
+        bodies.append(scenes.body(shape, params, p=p, R=R, mu=0.0))
+    grid = {"dx": dx, "res": (40, 40, 32), "origin": (-0.2, -0.2, -0.06),
+            "gravity": (0.0, 0.0, -9.81), "bc_layers": 3}
+    return {"name": "extremes_%d" % len(g["x"]), "grid": grid, "groups": [g], "bodies": bodies,
+            "h": 1e-4, "substeps": 1}
+
+
+@pytest.mark.parametrize("shape", P2G_SHAPES)
+def test_contacts_at_body_extremes_parity(native, shape):
+    """Contact detection skips a body for a warp whose particles all lie
+    outside a ball around the body's origin; the contact set must still be the
+    oracle's where the geometry is farthest from that origin."""
+    sc = extremes_scene()
+    rep = run_parity(native, sc, n_sub=1, options=p2g_options(native, shape))
+    assert rep[0][1] > 0
+    sim = native.Sim(sc)
+    for opt, val in p2g_options(native, shape):
+        native.mpm_set_option(sim.ctx, opt, val)
+    sim.step(n_substeps=1, solver=native.solver_params(**SOLVER_GPU))
+    _, b, _, _, _ = sim.contacts()
+    sim.close()
+    assert set(int(x) for x in b) >= {1, 2, 3, 4}, "every body has contacts"
