@@ -712,6 +712,8 @@ DevGroup make_group(const mpm_material& mat, float particle_volume) {
   const double E = mat.E, nu = mat.nu;
   gr.vol = particle_volume;
   gr.mass = (float)((double)mat.rho * (double)particle_volume);
+  gr.vol_m = (float)((double)gr.vol / (double)gr.mass);
+  gr.inv_m = (float)(1.0 / (double)gr.mass);
   gr.mu_l = (float)(E / (2.0 * (1.0 + nu)));
   gr.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
   const double sphi = std::sin((double)mat.friction_angle_deg * 3.14159265358979323846 / 180.0);

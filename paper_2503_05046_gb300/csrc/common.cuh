@@ -65,7 +65,7 @@ struct DevGroup {
   float mu_l, lam;        // Lame parameters
   float dp_alpha;         // Drucker-Prager cone slope
   int model;
-  float pad[2];
+  float vol_m, inv_m;     // vol / mass and 1 / mass (P2G's per-unit-mass record)
 };
 
 // Particle state, structure of arrays: one float plane per component, planes

@@ -346,12 +346,14 @@ __device__ __forceinline__ void p2g_block(const P2GArgs& a, int block) {
 // ---- node-parallel gather form ----
 // The warp stages its 32 particles' transfer data in shared memory and walks
 // them in cell order. Lane j < 27 owns node j of the current cell's 27-node
-// stencil and adds w_jp (m_p, b_p - A'_p c_j) for every particle of the
-// cell's run, with b = m v (+ h f_ext) + A' f, A' = -dx (m C - h 4/dx^2 V tau),
-// f the particle's position in its base cell and c_j the node's offset from
-// the base (so that b - A' c = m v + A (x_j - x_p)). The particle's data come
-// by broadcast loads, its nine B-spline weights by three per-lane loads; no
-// shuffle reduction, and the lanes of one update hold distinct nodes.
+// stencil and adds w_jp m_p (1, b_p - A_p c_j) for every particle of the
+// cell's run, with the per-unit-mass b = v (+ h f_ext / m) + A f and
+// A = -dx (C - h 4/dx^2 (V/m) tau), f the particle's position in its base cell
+// and c_j the node's offset from the base (so that m (b - A c) is the APIC
+// momentum m v + (m C - h 4/dx^2 V tau)(x_j - x_p)). The particle's data come
+// by broadcast loads; its weights are stored as the nine products m wx wy and
+// the three wz, so that a lane reads two and multiplies once. No shuffle
+// reduction, and the lanes of one update hold distinct nodes.
 // A run's sums go into the warp's window: the 6^3 nodes that the stencils of
 // one 4^3 block's cells reach; the window is flushed to the grid (one vector
 // reduction per touched node) when the walk enters another block.
@@ -416,11 +418,11 @@ __device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
   const float nc0 = -(float)oc0, nc1 = -(float)oc1, nc2 = -(float)oc2;
   const float2 nc00 = make_float2(nc0, nc0), nc11 = make_float2(nc1, nc1), nc22 = make_float2(nc2, nc2);
   const int woff_node = (oc2 * 6 + oc1) * 6 + oc0;
-  // weight e = 3 axis + c at row 3 + (e + 1) / 4, component (e + 1) % 4
-  const int e0 = oc0, e1 = 3 + oc1, e2 = 6 + oc2;
-  const int wf0 = ((3 + (e0 + 1) / 4) * 32) * 4 + ((e0 + 1) & 3);
-  const int wf1 = ((3 + (e1 + 1) / 4) * 32) * 4 + ((e1 + 1) & 3);
-  const int wf2 = ((3 + (e2 + 1) / 4) * 32) * 4 + ((e2 + 1) & 3);
+  // m wx wy of product e = oc0 + 3 oc1 at row 3 + e / 4, component e % 4;
+  // wz of oc2 at row 5, component 1 + oc2
+  const int exy = oc0 + 3 * oc1;
+  const int wfxy = ((3 + exy / 4) * 32) * 4 + (exy & 3);
+  const int wfz = (5 * 32) * 4 + 1 + oc2;
 
   int wb = -1, wbx = 0, wby = 0, wbz = 0;  // the window's block
   int wl0 = 3, wl1 = 3, wl2 = 3, wh0 = 0, wh1 = 0, wh2 = 0;  // its runs' cells
@@ -448,32 +450,42 @@ __device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
         float tau[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) tau[c] = a.P.tau(c)[i];
-        // A' = -dx (m C - h (4/dx^2) V tau); b = m v (+ h f_ext) + A' f
-        const float sc = h * dinv * gr.vol;
+        // per unit mass: A = A' / m = -dx (C - h (4/dx^2) (V/m) tau) and
+        // b = b' / m = v (+ h f_ext / m) + A f, with A' and b' of the sum
+        // w (b' - A' c) = w m (b - A c)
+        const float sc = h * dinv * gr.vol_m;
         const float tf[9] = {tau[0], tau[3], tau[4], tau[3], tau[1], tau[5], tau[4], tau[5], tau[2]};
         float A[9];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) A[c] = -g.dx * (gr.mass * a.P.C(c)[i] - sc * tf[c]);
-        float mv[3] = {gr.mass * a.P.v(0)[i], gr.mass * a.P.v(1)[i], gr.mass * a.P.v(2)[i]};
-        if (a.fext) {  // cloth: + h f, the force planes left zero for the next substep
+        for (int c = 0; c < 9; ++c) A[c] = -g.dx * (a.P.C(c)[i] - sc * tf[c]);
+        float vv[3] = {a.P.v(0)[i], a.P.v(1)[i], a.P.v(2)[i]};
+        if (a.fext) {  // cloth: + h f / m, the force planes left zero for the next substep
+          const float hm = h * gr.inv_m;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            mv[c] = fmaf(h, a.fext[c * a.fext_stride + i], mv[c]);
+            vv[c] = fmaf(hm, a.fext[c * a.fext_stride + i], vv[c]);
             a.fext[c * a.fext_stride + i] = 0.f;
           }
         }
         float b[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          b[c] = fmaf(A[3 * c], st.fx[0], fmaf(A[3 * c + 1], st.fx[1], fmaf(A[3 * c + 2], st.fx[2], mv[c])));
-        r0 = make_float4(b[0], b[1], b[2], gr.mass);
-        // rows x and y of A' interleaved, so that both rows step in one
-        // paired FMA: (A'xx, A'yx, A'xy, A'yy), (A'xz, A'yz, A'zx, A'zy)
+          b[c] = fmaf(A[3 * c], st.fx[0], fmaf(A[3 * c + 1], st.fx[1], fmaf(A[3 * c + 2], st.fx[2], vv[c])));
+        r0 = make_float4(b[0], b[1], b[2], A[8]);
+        // rows x and y of A interleaved, so that both rows step in one
+        // paired FMA: (Axx, Ayx, Axy, Ayy), (Axz, Ayz, Azx, Azy)
         r1 = make_float4(A[0], A[3], A[1], A[4]);
         r2 = make_float4(A[2], A[5], A[6], A[7]);
-        r3 = make_float4(A[8], st.w[0][0], st.w[0][1], st.w[0][2]);
-        r4 = make_float4(st.w[1][0], st.w[1][1], st.w[1][2], st.w[2][0]);
-        r5 = make_float4(st.w[2][1], st.w[2][2], 0.f, 0.f);
+        // weights: the nine products m wx wy (x fastest) and the three wz, so
+        // that a lane forms w m of its node with one multiply
+        {
+          float wxm[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) wxm[c] = gr.mass * st.w[0][c];
+          r3 = make_float4(wxm[0] * st.w[1][0], wxm[1] * st.w[1][0], wxm[2] * st.w[1][0], wxm[0] * st.w[1][1]);
+          r4 = make_float4(wxm[1] * st.w[1][1], wxm[2] * st.w[1][1], wxm[0] * st.w[1][2], wxm[1] * st.w[1][2]);
+          r5 = make_float4(wxm[2] * st.w[1][2], st.w[2][0], st.w[2][1], st.w[2][2]);
+        }
       }
     }
     rec[lane] = r0;
@@ -512,16 +524,16 @@ __device__ __forceinline__ void p2g_gather_block(const P2GArgs& a, int block) {
 #pragma unroll 2
         for (int q = p; q < pe; ++q) {
           const float4 q0 = rec[q], q1 = rec[32 + q], q2 = rec[64 + q];
-          const float a8 = recf[(96 + q) * 4];
-          const float w = recf[wf0 + 4 * q] * recf[wf1 + 4 * q] * recf[wf2 + 4 * q];
+          const float wm = recf[wfxy + 4 * q] * recf[wfz + 4 * q];  // w m
+          // b - A c (velocity units); the node receives w m and w m (b - A c)
           const float2 m01 =
               __ffma2_rn(make_float2(q1.x, q1.y), nc00,
                          __ffma2_rn(make_float2(q1.z, q1.w), nc11,
                                     __ffma2_rn(make_float2(q2.x, q2.y), nc22, make_float2(q0.x, q0.y))));
-          const float m2 = fmaf(q2.z, nc0, fmaf(q2.w, nc1, fmaf(a8, nc2, q0.z)));
-          acc0 = fmaf(w, q0.w, acc0);
-          acc12 = __ffma2_rn(make_float2(w, w), m01, acc12);
-          acc3 = fmaf(w, m2, acc3);
+          const float m2 = fmaf(q2.z, nc0, fmaf(q2.w, nc1, fmaf(q0.w, nc2, q0.z)));
+          acc0 += wm;
+          acc12 = __ffma2_rn(make_float2(wm, wm), m01, acc12);
+          acc3 = fmaf(wm, m2, acc3);
         }
         acc1 = acc12.x;
         acc2 = acc12.y;
