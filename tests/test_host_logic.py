@@ -189,3 +189,24 @@ def test_autograd_rollout_keeps_dynamics_and_start_bodies(monkeypatch):
     (xf.sum() + vf.sum()).backward()
     assert v0.grad.dtype == torch.float32 and torch.all(v0.grad == 1.0)
     assert E.grad.item() == 2.0 and mu.grad.item() == 4.0
+
+
+def test_traffic_table_covers_every_kernel_the_bench_reports():
+    """Every (kernel, workload) key bench.py may ask `profiles/traffic.txt` for
+    has a line: each P2G form and block size the tuner can choose, and G2P,
+    on both bench workloads; the scaled value is proportional to n."""
+    import inspect
+    from paper_2503_05046_gb300 import tune
+    cands = inspect.signature(tune.tune_p2g_form).parameters["candidates"].default
+    keys = ["p2g_%s_%d" % (("gather", "scatter")[f], c) for f, c in cands]
+    keys.append("g2p")
+    for wl, n in (("mixed_manipulation_4M", 3997168), ("granular_scoop_1M", 1000000)):
+        for k in keys:
+            t = bench.profiled_traffic(k, wl, n)
+            assert t is not None, (k, wl)
+            # within [0.5, 1.5] of the algorithmic bytes: a capture of this kernel
+            alg = (bench.G2P_BYTES_PER_PARTICLE * n if k == "g2p" else
+                   bench.P2G_BYTES_PER_PARTICLE * n)
+            assert 0.5 * alg < t < 1.5 * alg + 16 * 2e6, (k, wl, t, alg)
+            assert bench.profiled_traffic(k, wl, 2 * n) == pytest.approx(2 * t)
+    assert bench.profiled_traffic("p2g_gather_512", "mixed_manipulation_4M", 1) is None
