@@ -922,7 +922,7 @@ def oracle_available(openmp):
 def cpu_baseline(measured):
     """The FP64 oracle on the machine's host cores, on bounded samples of each
     workload from the state the GPU run left (one substep of the 4M and 1M
-    workloads), the 8k cube of SURVEY's first configuration whole (200
+    workloads), the 8,000-particle cube drop (cube_drop_8k) whole (200
     substeps) and one checkpoint interval (25 substeps) of the 65,536-particle
     differentiation workload: single-threaded (the oracle as written) and its
     OpenMP build over all host cores."""
