@@ -210,3 +210,32 @@ def test_traffic_table_covers_every_kernel_the_bench_reports():
             assert 0.5 * alg < t < 1.5 * alg + 16 * 2e6, (k, wl, t, alg)
             assert bench.profiled_traffic(k, wl, 2 * n) == pytest.approx(2 * t)
     assert bench.profiled_traffic("p2g_gather_512", "mixed_manipulation_4M", 1) is None
+
+
+def test_clock_sampler_parses_clocks_and_throttle_reasons(tmp_path):
+    """The nvidia-smi samples of the timed region: median SM clock, the
+    highest maximum clock, and every throttle reason seen Active (a run with
+    hw_slowdown or a thermal reason is rejected; sw_power_cap is kept)."""
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "clocks.csv")
+    with open(s.path, "w") as f:
+        f.write("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n")
+        f.write("0, 2055, 2070, 1010.0, 0x8, Active, Not Active, Not Active, Not Active\n")
+        f.write("0, [N/A], 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("a short line\n")
+
+    class FakeSmi:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s.proc = FakeSmi()
+    s.out = open(os.devnull, "w")
+    r = s.stop()
+    assert r == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0,
+                 "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
+    assert not os.path.exists(s.path)
+    assert bench.ClockSampler(0).stop() is None  # never started: no clock record
